@@ -1,0 +1,370 @@
+"""Benchmark: spin-flip attempts/s of replica-parallel Metropolis annealing.
+
+Default workload (N = 1): an 80 x 100 +-1 torus (the shape of the Gset
+spin-glass instance G65: 8,000 spins, 16,000 edges), 1,024 replicas packed 32
+per word, geometric beta 0.1 -> 5.0 over 10,000 sweeps, one instance per
+launch.  One step = one full anneal of that instance (all sweeps, energy and
+best-state tracking, result unpacking) = 8.19e10 attempts.
+
+  value      attempts/s, CUDA events around each step on the launching stream,
+             instance already resident on the device; L2 flushed between steps.
+  e2e        the same metric through the public C ABI with HOST buffers: each
+             step creates the instance from host couplings, anneals, and reads
+             final spins, energies and the best state back to the host.
+  roofline   the sweep kernel's algorithmic integer-instruction rate against
+             the issue peak of the integer units (bound "alu").
+  cpu_baseline  the CPU oracle on the host cores on a bounded replica sample.
+
+Other workloads: --config random (n = 10,000, m = 9,999 random graph, 256
+replicas), --config batch (512 uneven tori in one persistent kernel vs the
+one-launch-per-sweep plain form), --config served (Poisson request stream).
+
+--impl reference times the CPU oracle (the only reference this project has)
+on the same workload, metric and unit.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2311_09275_gb300 import inputs as I  # noqa: E402
+
+METRIC = "spin-flip attempts/s"
+UNIT = "attempts/s"
+# Integer instructions one attempt needs by the algorithm: a quarter of a
+# Philox4x32-10 block (10 rounds x (2 wide multiplies + 2 three-input XORs)
+# = 40 per 4 uniforms) plus one threshold compare.
+ALGO_OPS_PER_ATTEMPT = 40 / 4 + 1
+SMSP_PER_SM = 4
+LANES = 32
+
+
+def load_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            return json.load(f), "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle samples while the timed region runs."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.lines:
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx = float(parts[1])
+            except ValueError:
+                continue
+            for name, val in zip(names, parts[3:7]):
+                if val.lower().startswith("active"):
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_setup(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        import torch
+        backend = "nccl" if (torch.cuda.is_available() and args.impl != "reference") else "gloo"
+        if backend == "nccl":
+            torch.cuda.set_device(local)
+        dist.init_process_group(backend, init_method="env://")
+    return world, rank, local, dist
+
+
+def max_over_ranks(x: float, dist, device) -> float:
+    if dist is None:
+        return x
+    import torch
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def sum_over_ranks(x: float, dist, device) -> float:
+    if dist is None:
+        return x
+    import torch
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+def barrier(dist):
+    if dist is not None:
+        dist.barrier()
+
+
+def workload(config: str, rank: int, sweeps: int | None = None):
+    """The Solve of this rank.  Ranks anneal the same instance with their own
+    seeds (independent replicas: weak scaling, no exchange).  `sweeps`
+    shortens the schedule (profiling runs only; the benchmark line uses the
+    full 10,000)."""
+    if config == "torus":
+        sv = I.torus_80x100(sweeps=sweeps or 10000)
+        name = f"torus_80x100_R1024_S{sv.sweeps}_geometric_0.1_5.0"
+    elif config == "random":
+        sv = I.random_10000(sweeps=sweeps or 10000)
+        name = f"random_n10000_m9999_R256_S{sv.sweeps}_geometric_0.1_5.0"
+    else:
+        raise ValueError(config)
+    sv.seed = sv.seed + rank
+    return sv, name
+
+
+# ---------------------------------------------------------------- CPU oracle
+def cpu_oracle_rate(sv, budget_s: float = 12.0, max_replicas: int | None = None):
+    """Oracle attempts/s on the host cores over a bounded sample: the first
+    `cores` replicas of the workload, sweeps truncated to fit the budget."""
+    import oracle
+    cores = os.cpu_count() or 1
+    reps = min(sv.replicas, max_replicas or cores)
+    c = oracle.csr_of(sv.problem)
+    colour, _ = c.greedy_colouring()
+    # calibrate on a short prefix, then size the sample to the budget
+    probe = max(1, min(sv.sweeps, 20))
+    t0 = time.perf_counter()
+    oracle.anneal(c, reps, sv.betas[:probe], sv.seed, colour=colour, nthreads=cores)
+    dt = max(time.perf_counter() - t0, 1e-6)
+    rate = reps * sv.n * probe / dt
+    sweeps = int(max(1, min(sv.sweeps, budget_s * rate / (reps * sv.n))))
+    t0 = time.perf_counter()
+    oracle.anneal(c, reps, sv.betas[:sweeps], sv.seed, colour=colour, nthreads=cores)
+    dt = time.perf_counter() - t0
+    return {"value": reps * sv.n * sweeps / dt, "unit": UNIT, "cores": min(cores, reps),
+            "kind": "oracle",
+            "sample": f"replicas 0..{reps - 1} of {sv.replicas}, first {sweeps} of {sv.sweeps} "
+                      f"sweeps ({reps * sv.n * sweeps:.3g} attempts, {dt:.1f} s)"}
+
+
+def run_reference(args):
+    world, rank, local, dist = dist_setup(args)
+    if rank != 0:
+        return
+    sv, name = workload(args.config, 0, args.sweeps)
+    import oracle
+    cores = os.cpu_count() or 1
+    reps = min(sv.replicas, cores)
+    c = oracle.csr_of(sv.problem)
+    colour, _ = c.greedy_colouring()
+    # each step: `reps` replicas over a sweep prefix sized to ~per_step_s
+    probe = 10
+    t0 = time.perf_counter()
+    oracle.anneal(c, reps, sv.betas[:probe], sv.seed, colour=colour, nthreads=cores)
+    rate = reps * sv.n * probe / max(time.perf_counter() - t0, 1e-6)
+    per_step_s = 4.0
+    sweeps = int(max(1, min(sv.sweeps, per_step_s * rate / (reps * sv.n))))
+    for _ in range(args.warmup):
+        oracle.anneal(c, reps, sv.betas[:sweeps], sv.seed, colour=colour, nthreads=cores)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.anneal(c, reps, sv.betas[:sweeps], sv.seed, colour=colour, nthreads=cores)
+    dt = time.perf_counter() - t0
+    attempts = reps * sv.n * sweeps * args.steps
+    value = attempts / dt
+    sample = (f"each step: replicas 0..{reps - 1} of {sv.replicas}, first {sweeps} of "
+              f"{sv.sweeps} sweeps ({reps * sv.n * sweeps:.3g} attempts)")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
+            "data": "synthetic", "config": {"workload": name, "sample": sample},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": min(cores, reps),
+                             "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+# ---------------------------------------------------------------- GPU arm
+def run_gpu(args):
+    import torch
+    world, rank, local, dist = dist_setup(args)
+    assert torch.cuda.is_available(), "bench.py needs a CUDA device"
+    torch.cuda.set_device(local)
+    device = torch.device("cuda", local)
+    from paper_2311_09275_gb300 import isg
+
+    sv, name = workload(args.config, rank, args.sweeps)
+    stream = torch.cuda.current_stream()
+    p = isg.problem_of(sv.problem)
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.int32, device=device)  # 512 MB > L2
+
+    def step(time_kernels=True):
+        return isg.isg_anneal(p, sv.replicas, sv.betas, sv.seed, stream=stream,
+                              time_kernels=time_kernels)
+
+    for _ in range(args.warmup):
+        r = step()
+        r.final(spins=False)
+        r.close()
+
+    # ---- device-timed steps
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    results = []
+    barrier(dist)
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clocks:
+        wall0 = time.perf_counter()
+        for k in range(args.steps):
+            flush.fill_(k)
+            ev[k][0].record(stream)
+            results.append(step())
+            ev[k][1].record(stream)
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - wall0
+    barrier(dist)
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    kernel_ms, launches, sweep_launches = [], 0, 0
+    stats = None
+    for r in results:
+        stats = r.stats()
+        kernel_ms.append(stats["sweep_kernel_ms"])
+        launches += stats["launches"]
+        sweep_launches += stats["sweep_launches"]
+        r.close()
+    dev_s = max_over_ranks(sum(step_ms) / 1e3, dist, device)
+    attempts_rank = float(sv.attempts) * args.steps
+    attempts_all = sum_over_ranks(attempts_rank, dist, device)
+    value = attempts_all / dev_s
+
+    # ---- end to end through the C ABI with host buffers
+    e2e_steps = max(1, min(args.steps, 5))
+    h2d = d2h = 0
+    barrier(dist)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        q = isg.problem_of(sv.problem)                        # host couplings -> library
+        r = isg.isg_anneal(q, sv.replicas, sv.betas, sv.seed, stream=stream)
+        spins, energies, done = r.final(spins=True)           # D2H final state
+        be, br, bspins, per, hit = r.best(spins=True)         # D2H best state
+        r.close()
+        q.close()
+    torch.cuda.synchronize()
+    e2e_s = max_over_ranks(time.perf_counter() - t0, dist, device)
+    units = (sv.replicas + 31) // 32 if hasattr(sv.problem, "L") else (sv.replicas + 3) // 4
+    lanes = units * (32 if hasattr(sv.problem, "L") else 4)
+    if hasattr(sv.problem, "L"):
+        h2d = sv.n + 4 * 2 * sv.sweeps                        # coupling bits + thresholds
+    else:
+        h2d = 4 * (3 * sv.n + 4 * sv.problem.m + 32) + 4 * (sv.sweeps * 16)
+    d2h = spins.nbytes + bspins.nbytes + 4 * (2 * lanes + units + 1)
+    e2e_value = sum_over_ranks(float(sv.attempts) * e2e_steps, dist, device) / e2e_s
+
+    # ---- roofline of the sweep kernel (integer issue)
+    peaks, peak_src = load_peaks()
+    props = torch.cuda.get_device_properties(device)
+    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+    issue_peak = props.multi_processor_count * SMSP_PER_SM * LANES * sm_max * 1e6
+    k_ms = statistics.mean(kernel_ms)
+    achieved = ALGO_OPS_PER_ATTEMPT * float(sv.attempts) / (k_ms / 1e3)
+    traffic = None
+    tpath = os.path.join(ROOT, "profiles", "traffic.json")
+    if os.path.exists(tpath):
+        with open(tpath) as f:
+            traffic = json.load(f).get(name)
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * dev_s / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
+        "data": "synthetic",
+        "config": {"workload": name, "replicas": sv.replicas, "spins": sv.n,
+                   "sweeps": sv.sweeps, "attempts_per_step": sv.attempts,
+                   "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
+                   "l2": "flushed (512 MB write) before every timed step",
+                   "launch": {k: stats[k] for k in ("kernel", "ctas", "cluster_ctas", "threads")}},
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+                "d2h_bytes_per_step": int(d2h), "steps": e2e_steps},
+        "gpu_launches": launches,
+        "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": issue_peak / 1e12,
+                     "unit": "Tops/s", "frac": achieved / issue_peak, "traffic": traffic,
+                     "kernel": "torus_kernel" if hasattr(sv.problem, "L") else "csr_kernel",
+                     "kernel_ms": k_ms,
+                     "peak_source": f"{props.multi_processor_count} SMs x {SMSP_PER_SM} x "
+                                    f"{LANES} lanes x {sm_max:.0f} MHz ({peak_src} clock)"},
+        "clocks": clocks.summary(),
+        "wall_s": wall,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu:
+        line["cpu_baseline"] = cpu_oracle_rate(sv)
+    if rank == 0:
+        print(json.dumps(line))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--config", default="torus", choices=["torus", "random"])
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--sweeps", type=int, default=None,
+                    help="shorter schedule for profiling captures (default: the full workload)")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,223 @@
+/*
+ * isg.h -- C ABI of libisg: replica-parallel Metropolis annealing of sparse
+ * Ising / MaxCut instances on one NVIDIA GB300 (sm_103a).
+ *
+ * Problem (paper Sec. I, Sec. II.A and Table I): n binary spins s_i in {-1,+1}
+ * with integer pairwise couplings w_ij on a sparse graph -- a toroidal square
+ * grid with +-1 couplings (the 2D Edwards-Anderson spin glass form of the Gset
+ * torus instances) or an arbitrary sparse graph (e.g. unweighted MaxCut on a
+ * random graph, like G70).  The library minimises
+ *
+ *     E(s) = sum_{edges (i,j)} w_ij s_i s_j ,
+ *
+ * so the MaxCut value of Sec. II.A is cut(s) = (W_tot - E(s)) / 2 with
+ * W_tot = sum w_ij (returned by isg_problem_info).
+ *
+ * Method.  The paper's heuristic is iterative, counts its work in sweeps and
+ * withholds its details (Sec. III.A).  The library runs the computation such
+ * heuristics spend their time in: simulated annealing by single-spin-flip
+ * Metropolis sweeps over R independent replicas.  Sweep t (0-based) visits
+ * the colour classes in ascending order (torus: colour (r + c) mod 2; graphs:
+ * greedy colouring by ascending vertex id) and, for every vertex i of the
+ * class and every replica, computes h_i = sum_j w_ij s_j and the energy change
+ * d = -2 s_i h_i of flipping s_i; the flip is taken when d <= 0, or when
+ * u < floor(2^32 exp(-beta_t d)) for the replica's 32-bit uniform u.  The
+ * uniform of replica r at vertex i in sweep t is word (r mod 4) of
+ * Philox4x32-10(key = (seed mod 2^32, seed >> 32), counter = (i, t, r / 4, 0))
+ * (Salmon et al., SC'11); initial spins are s_i = +1 iff the top bit of word
+ * (r mod 4) of Philox4x32-10(key, (i, 0, r / 4, 1)) is set.  i is the vertex
+ * id as given by the caller.  Energies are tracked incrementally; each
+ * replica's best state is checked at the end of every sweep (strictly lower
+ * energy replaces it; the initial state is the first candidate).
+ * Results are a pure function of (instance, replicas, betas, seed): they do
+ * not depend on the kernel chosen, its blocking or the batch a solve is in.
+ *
+ * Conventions.
+ *  - All input arrays are caller-owned HOST memory and are copied; the caller
+ *    may free them when the call returns.  Handles are library-owned and are
+ *    released with the matching *_destroy call.
+ *  - Spins cross the boundary as int8 +1/-1, row-major [replica][vertex] in
+ *    the caller's vertex order.
+ *  - Every call returns a status and never aborts the process; on failure the
+ *    calling thread's message is available from isg_last_error().
+ *  - Device work runs on the current CUDA device at the time of the call, on
+ *    the given stream (NULL = the legacy default stream).  Calls that return
+ *    results to the host synchronise with that work.
+ */
+#ifndef ISG_H
+#define ISG_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    ISG_OK = 0,
+    ISG_EINVAL = 1,      /* invalid argument or instance */
+    ISG_ENOMEM = 2,      /* host or device allocation failed */
+    ISG_ECUDA = 3,       /* a CUDA call failed (no device, launch error, ...) */
+    ISG_ETIMEOUT = 4,    /* nothing ready within the requested time */
+    ISG_EBUSY = 5,       /* resource limit reached (server slots, memory budget) */
+    ISG_ECANCELLED = 6   /* the request was cancelled or the server stopped */
+} isg_status;
+
+typedef struct isg_problem isg_problem;
+typedef struct isg_result isg_result;
+typedef struct isg_server isg_server;
+
+/* Sentinel for "no target energy". */
+#define ISG_NO_TARGET INT64_MIN
+
+/* ---------------------------------------------------------------- problems */
+
+/* Instance from an undirected edge list (paper Sec. II.A: weighted MaxCut /
+ * Ising form).  n >= 1 vertices; m >= 0 edges (u[e], v[e]) with weight w[e].
+ * EINVAL: an endpoint outside [0, n), a self-loop, a repeated pair, or
+ * sum |w| >= 2^30 (energies are exact int32).  Zero weights are allowed. */
+isg_status isg_problem_create_edges(int32_t n, int64_t m, const int32_t *u, const int32_t *v,
+                                    const int32_t *w, isg_problem **out);
+
+/* Instance from a symmetric CSR: rowptr[n+1] (rowptr[0] = 0), col/w of
+ * rowptr[n] entries; entry (i, j, w) must have its mirror (j, i, w).
+ * Same validity rules as isg_problem_create_edges. */
+isg_status isg_problem_create_csr(int32_t n, const int64_t *rowptr, const int32_t *col,
+                                  const int32_t *w, isg_problem **out);
+
+/* L x W toroidal square grid (paper Sec. II.A, Table I: 2n edges, degree 4).
+ * Vertex i = r*W + c; j_right[i] couples i to (r, c+1 mod W) and j_down[i]
+ * couples i to (r+1 mod L, c); each coupling is +1 or -1.  L and W must be
+ * even (two-colour checkerboard) and >= 4 (no doubled edges). */
+isg_status isg_problem_create_torus(int32_t L, int32_t W, const int8_t *j_right,
+                                    const int8_t *j_down, isg_problem **out);
+
+/* Sizes of an instance.  Any output pointer may be NULL.  n_colors is the
+ * number of colour classes; colors[n] receives each vertex's class. */
+isg_status isg_problem_info(const isg_problem *p, int32_t *n, int64_t *m, int64_t *total_weight,
+                            int32_t *n_colors, int32_t *colors);
+
+void isg_problem_destroy(isg_problem *p);
+
+/* ---------------------------------------------------------------- annealing */
+
+/* Kernel families.  AUTO picks the multi-spin-coded torus kernel for tori and
+ * the CSR colour-class kernel otherwise; PLAIN runs one kernel launch per
+ * sweep (state kept in device memory between launches), the one-instance-per-
+ * launch baseline of the batched form. */
+typedef enum {
+    ISG_KERNEL_AUTO = 0,
+    ISG_KERNEL_TORUS_MSC = 1,
+    ISG_KERNEL_CSR = 2,
+    ISG_KERNEL_PLAIN = 3
+} isg_kernel;
+
+typedef struct {
+    int32_t kernel;        /* isg_kernel */
+    int32_t cluster_ctas;  /* CTAs that share one replica block; 0 = autotuned */
+    int32_t threads;       /* threads per CTA; 0 = autotuned */
+    int32_t time_kernels;  /* nonzero: time the sweep launches with CUDA events */
+} isg_options;
+
+/* Anneal R = replicas independent chains for S = sweeps sweeps at inverse
+ * temperatures betas[S] (finite, >= 0) with the given seed.  With
+ * target_energy != ISG_NO_TARGET the solve stops at the end of the first sweep
+ * t* at which the lowest best energy over all replicas is <= target_energy;
+ * the reported state is the state after sweep t*.  The work is enqueued on
+ * cuda_stream; *out receives a result handle (library-owned).
+ * EINVAL: R < 1, S < 1, a beta that is negative or not finite, an instance too
+ * large for the chosen kernel; ECUDA: no device or a launch failed. */
+isg_status isg_anneal(const isg_problem *p, int32_t replicas, const double *betas, int32_t sweeps,
+                      uint64_t seed, int64_t target_energy, void *cuda_stream, isg_result **out);
+
+/* isg_anneal with explicit kernel options (opts may be NULL = defaults). */
+isg_status isg_anneal_ex(const isg_problem *p, int32_t replicas, const double *betas,
+                         int32_t sweeps, uint64_t seed, int64_t target_energy,
+                         const isg_options *opts, void *cuda_stream, isg_result **out);
+
+/* Anneal count instances with one persistent kernel (work list ordered
+ * longest-first) captured in a CUDA graph.  All share replicas, betas and
+ * sweeps; seeds[k] and targets[k] (targets may be NULL = none) are per
+ * instance.  outs[count] receive one result handle each; every result equals
+ * the result of isg_anneal on that instance alone, bit for bit.  Tori only in
+ * this version (EINVAL otherwise). */
+isg_status isg_anneal_batch(const isg_problem *const *probs, int32_t count, int32_t replicas,
+                            const double *betas, int32_t sweeps, const uint64_t *seeds,
+                            const int64_t *targets, void *cuda_stream, isg_result **outs);
+
+/* Energies E(s) of R host configurations spins[R][n] (+-1) into energies[R],
+ * computed on the device (a check of the tracked energies). */
+isg_status isg_energy(const isg_problem *p, const int8_t *spins, int32_t replicas,
+                      int64_t *energies);
+
+/* Final state: spins[R][n] (may be NULL), energies[R] (may be NULL) and the
+ * number of sweeps run.  Waits for the solve to finish. */
+isg_status isg_result_final(const isg_result *r, int8_t *spins, int32_t *energies,
+                            int32_t *sweeps_done);
+
+/* Best state: the lowest best energy over replicas and its replica (ties go
+ * to the lowest replica index), that replica's best spins[n] (may be NULL),
+ * every replica's best energy per_replica_best[R] (may be NULL) and the first
+ * sweep at which the target was reached (-1 if none or no target). */
+isg_status isg_best(const isg_result *r, int32_t *best_energy, int32_t *best_replica,
+                    int8_t *best_spins, int32_t *per_replica_best, int32_t *hit_sweep);
+
+/* Sizes of a result: vertices n, replicas R and the sweep budget S.  Does not
+ * wait for the solve.  Any output pointer may be NULL. */
+isg_status isg_result_shape(const isg_result *r, int32_t *n, int32_t *replicas, int32_t *sweeps);
+
+/* All replicas' best states best_spins[R][n]. */
+isg_status isg_result_best_all(const isg_result *r, int8_t *best_spins);
+
+typedef struct {
+    float sweep_kernel_ms;   /* CUDA-event time of the sweep launches (time_kernels), else -1 */
+    int32_t launches;        /* kernel launches this solve made (all kernels of the library) */
+    int32_t sweep_launches;  /* launches of the sweep kernel */
+    int32_t kernel;          /* isg_kernel actually used */
+    int32_t ctas;            /* CTAs of the sweep kernel */
+    int32_t cluster_ctas;    /* CTAs per cluster */
+    int32_t threads;         /* threads per CTA */
+} isg_stats;
+
+isg_status isg_result_stats(const isg_result *r, isg_stats *stats);
+
+void isg_result_destroy(isg_result *r);
+
+/* ---------------------------------------------------------------- serving */
+
+/* A continuous-batching annealing server on the current device.  Requests
+ * are admitted while a slot is free and their device state fits in
+ * device_mem_budget bytes; admitted requests run together in chunks of
+ * sweeps_per_chunk sweeps of one persistent kernel; each runs until its
+ * target or its sweep budget.  A request's result equals isg_anneal of the
+ * same arguments, bit for bit.  max_slots >= 1, sweeps_per_chunk >= 1. */
+isg_status isg_server_create(size_t device_mem_budget, int32_t max_slots,
+                             int32_t sweeps_per_chunk, isg_server **out);
+
+/* Queue a request (the problem handle must outlive the request).  Returns at
+ * once with its id.  EINVAL on bad arguments; ECANCELLED after shutdown. */
+isg_status isg_server_submit(isg_server *s, const isg_problem *p, int32_t replicas,
+                             const double *betas, int32_t sweeps, uint64_t seed,
+                             int64_t target_energy, uint64_t *request_id);
+
+/* Wait up to timeout_s seconds for any finished request; on success returns
+ * its id and a result handle (owned by the caller).  ETIMEOUT if none. */
+isg_status isg_server_poll(isg_server *s, uint64_t *request_id, isg_result **out,
+                           double timeout_s);
+
+/* Stop the server; unfinished requests are dropped.  */
+isg_status isg_server_destroy(isg_server *s);
+
+/* ---------------------------------------------------------------- misc */
+
+/* Message of the last failed call on this thread ("" if none). */
+const char *isg_last_error(void);
+
+/* Library version string. */
+const char *isg_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

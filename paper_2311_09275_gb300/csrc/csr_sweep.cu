@@ -1,0 +1,386 @@
+// csr_sweep.cu -- colour-class Metropolis sweeps on arbitrary sparse graphs.
+//
+// Vertices are relabelled colour-major, so a colour class is a contiguous id
+// range and no two vertices of a class are adjacent: a class is updated in
+// parallel with no intra-class ordering.  Spins are int8 (+1/-1) packed four
+// replicas per uint32 ("quad"); one Philox block yields the four replicas'
+// uniforms of one vertex.
+//
+// Layout: a cluster of K CTAs owns Q replica quads of one instance.  Every
+// CTA keeps a full copy of those quads' spins in shared memory, updates 1/K
+// of each colour class and writes each new word to all K copies (distributed
+// shared memory); one cluster barrier separates the classes.  Neighbour
+// gathers are therefore always local shared-memory loads.
+#include <climits>
+
+#include "isg_device.cuh"
+#include "isg_kernels.h"
+
+namespace isg {
+namespace {
+
+__host__ __device__ __forceinline__ size_t align16(size_t x) { return (x + 15) & ~size_t(15); }
+
+struct CsrSmem {
+  size_t spin, part, lane_acc, flags, total;
+};
+
+__host__ __device__ __forceinline__ CsrSmem csr_layout(int n, int Q, int K) {
+  CsrSmem m;
+  m.spin = 0;
+  m.part = align16(sizeof(uint32_t) * (size_t)n * Q);
+  // two buffers of per-rank partial sums, alternating between publications,
+  // so a fast CTA never overwrites sums a slower peer is still reading
+  m.lane_acc = m.part + 2 * sizeof(int32_t) * 4 * (size_t)Q * K;
+  m.flags = m.lane_acc + sizeof(int32_t) * 4 * (size_t)Q;
+  m.total = align16(m.flags + sizeof(uint32_t) * 4 * (size_t)Q + 16);
+  return m;
+}
+
+__device__ __forceinline__ void sync_group(int K) {
+  if (K == 1)
+    __syncthreads();
+  else
+    cluster_barrier();
+}
+
+// Spin (+1/-1) of lane l of a packed word: byte l, sign-extended by moving it
+// to the top byte and shifting back arithmetically.
+__device__ __forceinline__ int32_t lane8(uint32_t w, int l) {
+  return ((int32_t)(w << (24 - 8 * l))) >> 24;
+}
+
+// Own slice of the id range [a, b) for rank k of K.
+__device__ __forceinline__ void own_range(int a, int b, int k, int K, int &lo, int &hi) {
+  const int len = b - a;
+  lo = a + (int)((int64_t)len * k / K);
+  hi = a + (int)((int64_t)len * (k + 1) / K);
+}
+
+// Per-lane int32 values summed over the CTA, published to every CTA of the
+// cluster as part[k][slot]; ends with the group barrier.  `vals[q][l]` is the
+// thread's contribution for quad slot q, lane l.
+template <int Q>
+__device__ __forceinline__ void publish(const int32_t (&vals)[Q][4], int32_t *lane_acc,
+                                        int32_t *part, int k, int K) {
+#pragma unroll
+  for (int q = 0; q < Q; ++q)
+#pragma unroll
+    for (int l = 0; l < 4; ++l) {
+      const int32_t s = __reduce_add_sync(0xFFFFFFFFu, vals[q][l]);
+      if (lane_id() == 0 && s != 0) atomicAdd(&lane_acc[q * 4 + l], s);
+    }
+  __syncthreads();
+  if (threadIdx.x < 4 * Q) {
+    const int32_t v = lane_acc[threadIdx.x];
+    lane_acc[threadIdx.x] = 0;
+    if (K == 1) {
+      part[threadIdx.x] = v;
+    } else {
+      for (int r = 0; r < K; ++r) peer_smem(part, (uint32_t)r)[k * 4 * Q + threadIdx.x] = v;
+    }
+  }
+  sync_group(K);
+}
+
+template <int Q>
+__device__ void csr_solve(const CsrSolve &s, int quad0, int k, int K, int t_begin, int t_end,
+                          int resume, uint8_t *smem) {
+  const int n = s.n;
+  const CsrSmem lay = csr_layout(n, Q, K);
+  uint32_t *spin = reinterpret_cast<uint32_t *>(smem + lay.spin);  // [Q][n]
+  int32_t *part = reinterpret_cast<int32_t *>(smem + lay.part);
+  int32_t *lane_acc = reinterpret_cast<int32_t *>(smem + lay.lane_acc);
+  volatile uint32_t *flags = reinterpret_cast<uint32_t *>(smem + lay.flags);
+  const PhiloxKey key{s.key0, s.key1};
+  const int lane = (int)lane_id();
+
+  if (resume && s.has_target && s.hit[quad0] >= 0) return;
+  if (resume && t_begin >= t_end) return;
+
+  // spins of the Q quads, relabelled order
+  for (int x = threadIdx.x; x < n * Q; x += blockDim.x) {
+    const int q = x / n;
+    const int v = x - q * n;
+    const int gq = quad0 + q;
+    uint32_t w;
+    if (gq >= s.quads) {
+      w = 0x01010101u;
+    } else if (resume) {
+      w = s.spins[(size_t)gq * n + v];
+    } else {
+      const uint4 u = philox10(make_uint4((uint32_t)s.orig[v], 0u, (uint32_t)gq, kTagInit), key);
+      w = ((u.x >> 31) ? 0x01u : 0xFFu) | (((u.y >> 31) ? 0x01u : 0xFFu) << 8) |
+          (((u.z >> 31) ? 0x01u : 0xFFu) << 16) | (((u.w >> 31) ? 0x01u : 0xFFu) << 24);
+    }
+    spin[x] = w;
+  }
+  if (threadIdx.x < 4 * Q) lane_acc[threadIdx.x] = 0;
+  __syncthreads();
+
+  // bookkeeping lanes: warp 0, lane = q * 4 + l
+  int32_t e = 0, e_best = 0;
+  const int my_q = lane >> 2;
+  const int my_r = 4 * (quad0 + my_q) + (lane & 3);
+  const bool valid = (lane < 4 * Q) && (quad0 + my_q < s.quads) && (my_r < s.replicas);
+
+  if (!resume) {
+    int32_t vals[Q][4];
+#pragma unroll
+    for (int q = 0; q < Q; ++q)
+#pragma unroll
+      for (int l = 0; l < 4; ++l) vals[q][l] = 0;
+    for (int c = 0; c < s.n_colours; ++c) {
+      int lo, hi;
+      own_range(s.class_start[c], s.class_start[c + 1], k, K, lo, hi);
+      for (int v = lo + threadIdx.x; v < hi; v += blockDim.x) {
+        const int p0 = s.rowptr[v], p1 = s.rowptr[v + 1];
+#pragma unroll
+        for (int q = 0; q < Q; ++q) {
+          const uint32_t sv = spin[q * n + v];
+          int32_t acc[4] = {0, 0, 0, 0};
+          for (int p = p0; p < p1; ++p) {
+            const int u = __ldg(&s.col[p]);
+            if (u <= v) continue;
+            const int32_t wv = __ldg(&s.wt[p]);
+            const uint32_t su = spin[q * n + u];
+#pragma unroll
+            for (int l = 0; l < 4; ++l) acc[l] += wv * lane8(sv, l) * lane8(su, l);
+          }
+#pragma unroll
+          for (int l = 0; l < 4; ++l) vals[q][l] += acc[l];
+        }
+#pragma unroll
+        for (int q = 0; q < Q; ++q)
+          if (quad0 + q < s.quads) s.best[(size_t)(quad0 + q) * n + v] = spin[q * n + v];
+      }
+    }
+    publish<Q>(vals, lane_acc, part, k, K);  // publication 0 uses buffer 0
+    if (threadIdx.x < 32) {
+      int32_t tot = 0;
+      if (lane < 4 * Q)
+        for (int r = 0; r < K; ++r) tot += part[r * 4 * Q + lane];
+      e = tot;
+      e_best = e;
+    }
+  } else if (threadIdx.x < 32 && valid) {
+    e = s.e_cur[my_r];
+    e_best = s.e_best[my_r];
+  }
+
+  const int kmax1 = s.kmax + 1;
+  int t = t_begin;
+  int hit = -1;
+  for (; t < t_end; ++t) {
+    const uint32_t *row = s.table + (size_t)t * kmax1;
+    int32_t de[Q][4];
+#pragma unroll
+    for (int q = 0; q < Q; ++q)
+#pragma unroll
+      for (int l = 0; l < 4; ++l) de[q][l] = 0;
+    for (int c = 0; c < s.n_colours; ++c) {
+      int lo, hi;
+      own_range(s.class_start[c], s.class_start[c + 1], k, K, lo, hi);
+      for (int v = lo + threadIdx.x; v < hi; v += blockDim.x) {
+        const int p0 = __ldg(&s.rowptr[v]), p1 = __ldg(&s.rowptr[v + 1]);
+        const uint32_t ov = (uint32_t)__ldg(&s.orig[v]);
+#pragma unroll
+        for (int q = 0; q < Q; ++q) {
+          const uint32_t sv = spin[q * n + v];
+          int32_t h[4] = {0, 0, 0, 0};
+          for (int p = p0; p < p1; ++p) {
+            const uint32_t su = spin[q * n + __ldg(&s.col[p])];
+            const int32_t wv = __ldg(&s.wt[p]);
+#pragma unroll
+            for (int l = 0; l < 4; ++l) h[l] += wv * lane8(su, l);
+          }
+          // half energy change kk = -s h per lane; lanes with kk > 0 are uphill
+          int32_t kk[4];
+          uint32_t up = 0u;
+#pragma unroll
+          for (int l = 0; l < 4; ++l) {
+            kk[l] = -lane8(sv, l) * h[l];
+            up |= (kk[l] > 0 ? 1u : 0u) << l;
+          }
+          uint32_t acc = ~up & 0xFu;  // downhill and level moves are always taken
+          if (up != 0u) {
+            const uint4 u =
+                philox10(make_uint4(ov, (uint32_t)t, (uint32_t)(quad0 + q), kTagSweep), key);
+            if ((up & 1u) && u.x < __ldg(&row[kk[0]])) acc |= 1u;
+            if ((up & 2u) && u.y < __ldg(&row[kk[1]])) acc |= 2u;
+            if ((up & 4u) && u.z < __ldg(&row[kk[2]])) acc |= 4u;
+            if ((up & 8u) && u.w < __ldg(&row[kk[3]])) acc |= 8u;
+          }
+          uint32_t flip = 0u;
+#pragma unroll
+          for (int l = 0; l < 4; ++l) {
+            if ((acc >> l) & 1u) {
+              flip |= 0xFEu << (8 * l);
+              de[q][l] += 2 * kk[l];
+            }
+          }
+          if (flip) {
+            const uint32_t sn = sv ^ flip;
+            if (K == 1) {
+              spin[q * n + v] = sn;
+            } else {
+              for (int r = 0; r < K; ++r) peer_smem(spin, (uint32_t)r)[q * n + v] = sn;
+            }
+          }
+        }
+      }
+      if (c + 1 < s.n_colours) sync_group(K);
+    }
+    // sweep t is publication t + 1 (the initial energy is publication 0)
+    int32_t *pbuf = part + ((t + 1) & 1) * 4 * Q * K;
+    publish<Q>(de, lane_acc, pbuf, k, K);
+    if (threadIdx.x < 32) {
+      int32_t tot = 0;
+      if (lane < 4 * Q)
+        for (int r = 0; r < K; ++r) tot += pbuf[r * 4 * Q + lane];
+      e += tot;
+      const bool better = valid && e < e_best;
+      if (better) e_best = e;
+      const uint32_t imp = __ballot_sync(0xFFFFFFFFu, better);
+      const int32_t mn = __reduce_min_sync(0xFFFFFFFFu, valid ? e_best : INT_MAX);
+      if (lane == 0) {
+        flags[0] = imp;
+        flags[1] = (s.has_target && mn <= s.target) ? 1u : 0u;
+      }
+    }
+    __syncthreads();
+    const uint32_t imp = flags[0];
+    const uint32_t stop = flags[1];
+    if (imp != 0u) {
+#pragma unroll
+      for (int q = 0; q < Q; ++q) {
+        const uint32_t m4 = (imp >> (4 * q)) & 0xFu;
+        if (m4 == 0u) continue;
+        const uint32_t bm = ((m4 & 1u) ? 0xFFu : 0u) | ((m4 & 2u) ? 0xFF00u : 0u) |
+                            ((m4 & 4u) ? 0xFF0000u : 0u) | ((m4 & 8u) ? 0xFF000000u : 0u);
+        uint32_t *gb = s.best + (size_t)(quad0 + q) * n;
+        for (int c = 0; c < s.n_colours; ++c) {
+          int lo, hi;
+          own_range(s.class_start[c], s.class_start[c + 1], k, K, lo, hi);
+          for (int v = lo + threadIdx.x; v < hi; v += blockDim.x)
+            gb[v] = (gb[v] & ~bm) | (spin[q * n + v] & bm);
+        }
+      }
+    }
+    if (stop) {
+      hit = t;
+      ++t;
+      break;
+    }
+  }
+
+  // write back own vertices (every CTA holds all; each writes its slice)
+  for (int c = 0; c < s.n_colours; ++c) {
+    int lo, hi;
+    own_range(s.class_start[c], s.class_start[c + 1], k, K, lo, hi);
+    for (int q = 0; q < Q; ++q) {
+      if (quad0 + q >= s.quads) continue;
+      for (int v = lo + threadIdx.x; v < hi; v += blockDim.x)
+        s.spins[(size_t)(quad0 + q) * n + v] = spin[q * n + v];
+    }
+  }
+  if (k == 0) {
+    if (threadIdx.x < 32 && valid) {
+      s.e_cur[my_r] = e;
+      s.e_best[my_r] = e_best;
+    }
+    if (threadIdx.x == 0) {
+      for (int q = 0; q < Q; ++q) {
+        if (quad0 + q >= s.quads) continue;
+        if (s.has_target && hit >= 0) s.hit[quad0 + q] = hit;
+        s.done[quad0 + q] = t;
+      }
+    }
+  }
+}
+
+template <int Q>
+__global__ void __launch_bounds__(512) csr_kernel(CsrSolve s, CsrLaunch l) {
+  extern __shared__ __align__(16) uint8_t smem[];
+  const int K = l.cluster;
+  const int k = (int)(blockIdx.x % K);
+  const int quad0 = (int)(blockIdx.x / K) * Q;
+  int t_end = l.t_end;
+  if (l.stop_from_hits) {
+    int m = INT_MAX;
+    for (int q = 0; q < s.quads; ++q)
+      if (s.hit[q] >= 0 && s.hit[q] < m) m = s.hit[q];
+    if (m != INT_MAX && m + 1 < t_end) t_end = m + 1;
+  }
+  csr_solve<Q>(s, quad0, k, K, l.t_begin, t_end, l.resume, smem);
+}
+
+template <typename Kern>
+cudaError_t launch_csr(Kern kernel, int grid, const CsrSolve &s, const CsrLaunch &l, size_t smem,
+                       cudaStream_t stream) {
+  cudaError_t err = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+  if (err != cudaSuccess) return err;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(l.threads);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = stream;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = l.cluster;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kernel, s, l);
+}
+
+__global__ void __launch_bounds__(512) csr_batch_kernel(const CsrBatchItem *items,
+                                                        const int32_t *count_dev,
+                                                        const int32_t *order, int32_t *next) {
+  extern __shared__ __align__(16) uint8_t smem[];
+  __shared__ int item;
+  const int count = *count_dev;
+  for (;;) {
+    if (threadIdx.x == 0) item = atomicAdd(next, 1);
+    __syncthreads();
+    const int it = item;
+    __syncthreads();
+    if (it >= count) break;
+    const CsrBatchItem u = items[order[it]];
+    csr_solve<1>(u.solve, u.quad, 0, 1, u.t_begin, u.t_end, u.resume, smem);
+    __syncthreads();
+  }
+}
+
+}  // namespace
+
+size_t csr_smem_bytes(int32_t n, int32_t quads_per_cta, int32_t cluster) {
+  return csr_layout(n, quads_per_cta, cluster).total;
+}
+
+cudaError_t csr_launch(const CsrSolve &s, const CsrLaunch &l, cudaStream_t stream) {
+  const int Q = l.quads_per_cta;
+  const size_t smem = csr_smem_bytes(s.n, Q, l.cluster);
+  const int groups = (s.quads + Q - 1) / Q;
+  const int grid = groups * l.cluster;
+  switch (Q) {
+    case 1: return launch_csr(csr_kernel<1>, grid, s, l, smem, stream);
+    case 2: return launch_csr(csr_kernel<2>, grid, s, l, smem, stream);
+    case 4: return launch_csr(csr_kernel<4>, grid, s, l, smem, stream);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+cudaError_t csr_batch_launch(const CsrBatchItem *items_dev, const int32_t *count_dev,
+                             const int32_t *order_dev, int32_t *next_dev, int32_t ctas,
+                             int32_t threads, size_t smem, cudaStream_t stream) {
+  cudaError_t err = cudaFuncSetAttribute(csr_batch_kernel,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (err != cudaSuccess) return err;
+  csr_batch_kernel<<<ctas, threads, smem, stream>>>(items_dev, count_dev, order_dev, next_dev);
+  return cudaGetLastError();
+}
+
+}  // namespace isg

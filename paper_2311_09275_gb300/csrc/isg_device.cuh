@@ -1,0 +1,133 @@
+// isg_device.cuh -- device building blocks shared by the annealing kernels:
+// the counter-based random numbers, bit-matrix column counts for multi-spin
+// coding, and thread-block-cluster helpers.
+#pragma once
+
+#include <cooperative_groups.h>
+#include <cstdint>
+
+namespace isg {
+
+namespace cg = cooperative_groups;
+
+// Counter tags of the two random streams (the fourth counter word).
+constexpr uint32_t kTagSweep = 0u;
+constexpr uint32_t kTagInit = 1u;
+
+// Philox4x32 with 10 rounds (Salmon, Moraes, Dror, Shaw, SC'11).  Each round
+// multiplies counter words 0 and 2 by two fixed odd constants (full 64-bit
+// products), and mixes the high halves with the other two words and the
+// round key; the key advances by two Weyl increments between rounds.  The
+// key is the same for every thread of a solve, so the ten round keys are
+// uniform values the compiler keeps out of the per-thread work.
+struct PhiloxKey {
+  uint32_t k0, k1;
+};
+
+__device__ __forceinline__ uint4 philox10(uint4 c, PhiloxKey key) {
+  constexpr uint32_t kMulA = 0xD2511F53u;
+  constexpr uint32_t kMulB = 0xCD9E8D57u;
+  constexpr uint32_t kWeylA = 0x9E3779B9u;
+  constexpr uint32_t kWeylB = 0xBB67AE85u;
+  uint32_t k0 = key.k0, k1 = key.k1;
+#pragma unroll
+  for (int round = 0; round < 10; ++round) {
+    const uint32_t hiA = __umulhi(kMulA, c.x), loA = kMulA * c.x;
+    const uint32_t hiB = __umulhi(kMulB, c.z), loB = kMulB * c.z;
+    c = make_uint4(hiB ^ c.y ^ k0, loB, hiA ^ c.w ^ k1, loA);
+    k0 += kWeylA;
+    k1 += kWeylB;
+  }
+  return c;
+}
+
+__device__ __forceinline__ uint32_t lane_id() { return threadIdx.x & 31u; }
+
+// 32x32 bit-matrix transpose across a warp: lane t enters with row t and
+// leaves with column t (bit j of the result = bit t of lane j's input).
+// Recursive swap of off-diagonal blocks, 16 -> 8 -> 4 -> 2 -> 1.
+__device__ __forceinline__ uint32_t warp_transpose32(uint32_t x) {
+  const uint32_t lane = lane_id();
+#pragma unroll
+  for (int j = 16; j >= 1; j >>= 1) {
+    const uint32_t m = (j == 16) ? 0x0000FFFFu
+                     : (j == 8)  ? 0x00FF00FFu
+                     : (j == 4)  ? 0x0F0F0F0Fu
+                     : (j == 2)  ? 0x33333333u
+                                 : 0x55555555u;
+    const uint32_t y = __shfl_xor_sync(0xFFFFFFFFu, x, j);
+    x = (lane & j) ? ((x & ~m) | ((y >> j) & m)) : ((x & m) | ((y << j) & ~m));
+  }
+  return x;
+}
+
+// Bit-sliced per-lane counter: plane k holds bit k of 32 independent counts
+// (one per bit position = one per replica of a multi-spin word).
+template <int NP>
+struct SlicedCounter {
+  uint32_t p[NP];
+
+  __device__ __forceinline__ void clear() {
+#pragma unroll
+    for (int k = 0; k < NP; ++k) p[k] = 0u;
+  }
+
+  // Adds the 3-bit per-lane value (x2 x1 x0).
+  __device__ __forceinline__ void add3(uint32_t x0, uint32_t x1, uint32_t x2) {
+    uint32_t c = p[0] & x0;
+    p[0] ^= x0;
+    uint32_t t = p[1] ^ x1;
+    uint32_t c2 = (p[1] & x1) | (t & c);
+    p[1] = t ^ c;
+    c = c2;
+    t = p[2] ^ x2;
+    c2 = (p[2] & x2) | (t & c);
+    p[2] = t ^ c;
+    c = c2;
+#pragma unroll
+    for (int k = 3; k < NP; ++k) {
+      const uint32_t cc = p[k] & c;
+      p[k] ^= c;
+      c = cc;
+    }
+  }
+
+  // Adds the 2-bit per-lane value (x1 x0).
+  __device__ __forceinline__ void add2(uint32_t x0, uint32_t x1) { add3(x0, x1, 0u); }
+
+  // Sum over the warp's 32 threads of the count of bit position `lane`
+  // (returned in that lane).  Must be called by all 32 lanes.
+  __device__ __forceinline__ int32_t warp_lane_total() const {
+    int32_t s = 0;
+#pragma unroll
+    for (int k = 0; k < NP; ++k) s += __popc(warp_transpose32(p[k])) << k;
+    return s;
+  }
+};
+
+// Cluster barrier with release/acquire ordering of shared-memory traffic
+// (including distributed shared memory) between the CTAs of the cluster.
+__device__ __forceinline__ void cluster_barrier() {
+  asm volatile("barrier.cluster.arrive.release.aligned;\n" ::: "memory");
+  asm volatile("barrier.cluster.wait.acquire.aligned;\n" ::: "memory");
+}
+
+__device__ __forceinline__ uint32_t cluster_rank() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;\n" : "=r"(r));
+  return r;
+}
+
+__device__ __forceinline__ uint32_t cluster_size() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %%cluster_nctarank;\n" : "=r"(r));
+  return r;
+}
+
+// Address of the same shared-memory object in CTA `rank` of the cluster.
+template <typename T>
+__device__ __forceinline__ T *peer_smem(T *local, uint32_t rank) {
+  return cg::this_cluster().map_shared_rank(local, rank);
+}
+
+}  // namespace isg

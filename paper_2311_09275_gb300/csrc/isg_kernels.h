@@ -1,0 +1,132 @@
+// isg_kernels.h -- interface between the host runtime (isg_runtime.cu) and
+// the annealing kernels (torus_msc.cu, csr_sweep.cu, aux_kernels.cu).
+// Plain structs of device pointers and sizes; no host-side logic here.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cstdint>
+
+namespace isg {
+
+// ---------------------------------------------------------------- torus, multi-spin coded
+// One replica word = 32 replicas packed bitwise (bit l of a word is replica
+// 32*word + l; bit 1 means spin +1).  State arrays are [word][L*W].
+struct TorusSolve {
+  int32_t L, W;
+  const uint8_t *cbits;      // [L*W] bit0: j_right == -1, bit1: j_down == -1
+  const uint32_t *table;     // [sweeps][2]: thresholds for energy changes 4 and 8
+  uint32_t key0, key1;       // Philox key (seed)
+  int32_t words;             // replica words of this solve
+  int32_t replicas;          // R (lanes >= R of the last word are padding)
+  uint32_t *spins;           // [words][L*W] state in/out
+  uint32_t *best;            // [words][L*W]
+  int32_t *e_cur;            // [words*32]
+  int32_t *e_best;           // [words*32]
+  int32_t *hit;              // [words] first sweep whose end met the target, else -1
+  int32_t *done;             // [words] sweeps completed
+  int32_t has_target;
+  int32_t target;
+};
+
+struct TorusLaunch {
+  int32_t t_begin, t_end;    // sweeps run by this launch
+  int32_t resume;            // 0: start from the initial (Philox) state
+  int32_t stop_from_hits;    // 1: end at min over words of hit[] + 1 (second pass)
+  int32_t cluster;           // CTAs per replica word (band split of the rows)
+  int32_t threads;
+};
+
+// Dynamic shared memory one CTA needs for a torus solve split over `cluster` CTAs.
+size_t torus_smem_bytes(int32_t L, int32_t W, int32_t cluster);
+// Largest number of sites a thread updates per sweep under this launch shape.
+int32_t torus_sites_per_thread(int32_t L, int32_t W, int32_t cluster, int32_t threads);
+cudaError_t torus_launch(const TorusSolve &s, const TorusLaunch &l, cudaStream_t stream);
+
+// Work units of the persistent kernels: one replica word of one torus, run by
+// one CTA over sweeps [t_begin, t_end).  Used by the batched and served forms.
+struct TorusBatchItem {
+  TorusSolve solve;
+  int32_t word;
+  int32_t t_begin, t_end;
+  int32_t resume;
+  int8_t *out;               // [R][n] final spins (+1/-1), written by batch_finish
+  int8_t *out_best;          // [R][n] best spins
+  int32_t *stop;             // hit sweep of the solve, -1 if none
+};
+// count_dev: number of units; order_dev: unit indices, longest first;
+// next_dev: zeroed work counter.
+cudaError_t torus_batch_launch(const TorusBatchItem *items_dev, const int32_t *count_dev,
+                               const int32_t *order_dev, int32_t *next_dev, int32_t ctas,
+                               int32_t threads, size_t smem, cudaStream_t stream);
+size_t torus_batch_max_smem(int32_t L, int32_t W);
+
+// ---------------------------------------------------------------- CSR colour classes
+// Vertices relabelled colour-major (class 0 first, ascending original id in a
+// class).  Spins are int8 packed four replicas per uint32 ("quad"), state
+// arrays [quad][n] in relabelled order.
+struct CsrSolve {
+  int32_t n;
+  int32_t n_colours;
+  const int32_t *class_start;  // [n_colours + 1] (relabelled ids)
+  const int32_t *rowptr;       // [n + 1]
+  const int32_t *col;          // [nnz] relabelled neighbour ids
+  const int32_t *wt;           // [nnz]
+  const int32_t *orig;         // [n] original id of each relabelled vertex
+  int32_t kmax;                // max_i sum_j |w_ij|
+  const uint32_t *table;       // [sweeps][kmax + 1]
+  uint32_t key0, key1;
+  int32_t quads;               // ceil(R / 4)
+  int32_t replicas;
+  uint32_t *spins;             // [quads][n]
+  uint32_t *best;              // [quads][n]
+  int32_t *e_cur;              // [quads*4]
+  int32_t *e_best;             // [quads*4]
+  int32_t *hit;                // [quads]
+  int32_t *done;               // [quads]
+  int32_t has_target;
+  int32_t target;
+};
+
+struct CsrLaunch {
+  int32_t t_begin, t_end;
+  int32_t resume;
+  int32_t stop_from_hits;
+  int32_t cluster;             // CTAs sharing one quad (each holds a full copy)
+  int32_t threads;
+  int32_t quads_per_cta;       // replica quads one CTA carries (1..8)
+};
+
+size_t csr_smem_bytes(int32_t n, int32_t quads_per_cta, int32_t cluster);
+cudaError_t csr_launch(const CsrSolve &s, const CsrLaunch &l, cudaStream_t stream);
+
+// Work unit: one replica quad of one instance, one CTA, sweeps [t_begin, t_end).
+struct CsrBatchItem {
+  CsrSolve solve;
+  int32_t quad;
+  int32_t t_begin, t_end;
+  int32_t resume;
+};
+cudaError_t csr_batch_launch(const CsrBatchItem *items_dev, const int32_t *count_dev,
+                             const int32_t *order_dev, int32_t *next_dev, int32_t ctas,
+                             int32_t threads, size_t smem, cudaStream_t stream);
+
+// ---------------------------------------------------------------- auxiliary kernels
+// Unpack multi-spin words [words][n] into int8 [R][n] (+1/-1).
+cudaError_t unpack_msc(const uint32_t *words, int32_t n, int32_t R, int8_t *out,
+                       cudaStream_t stream);
+// Unpack quads [quads][n] (relabelled order) into int8 [R][n] original order.
+cudaError_t unpack_quads(const uint32_t *quads, int32_t n, int32_t R, const int32_t *orig,
+                         int8_t *out, cudaStream_t stream);
+// Energies of R configurations spins[R][n] (int8) over a CSR (original ids):
+// per-block partial sums in scratch[R * blocks], then one sum per replica.
+cudaError_t energy_csr(const int64_t *rowptr, const int32_t *col, const int32_t *wt, int32_t n,
+                       const int8_t *spins, int32_t R, int64_t *scratch, int32_t blocks,
+                       int64_t *energies, cudaStream_t stream);
+// Unpack every batch item's state and stop sweep (one launch for the batch;
+// items with word 0 and R <= 32 replicas).
+cudaError_t batch_finish(const TorusBatchItem *items_dev, int32_t count, int32_t max_n,
+                         int32_t R, cudaStream_t stream);
+// Reduce per-word / per-quad hit sweeps to the solve's stop sweep.
+cudaError_t reduce_hits(const int32_t *hit, int32_t count, int32_t *out, cudaStream_t stream);
+
+}  // namespace isg

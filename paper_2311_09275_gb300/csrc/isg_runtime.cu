@@ -1,0 +1,856 @@
+// isg_runtime.cu -- host runtime behind the C ABI of include/isg.h: instance
+// building and validation, greedy colouring and colour-major relabelling,
+// acceptance tables, device residency, launch orchestration, results.
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <numeric>
+#include <string>
+#include <vector>
+
+#include "isg.h"
+#include "isg_kernels.h"
+#include "isg_runtime.h"
+
+namespace isg {
+
+thread_local std::string g_last_error;
+
+isg_status fail(isg_status st, const char *fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  g_last_error = buf;
+  return st;
+}
+
+isg_status cuda_fail(cudaError_t err, const char *what) {
+  return fail(ISG_ECUDA, "%s: %s", what, cudaGetErrorString(err));
+}
+
+#define ISG_CUDA(call)                                   \
+  do {                                                   \
+    cudaError_t err_ = (call);                           \
+    if (err_ != cudaSuccess) return cuda_fail(err_, #call); \
+  } while (0)
+
+// ------------------------------------------------------------------ problems
+
+namespace {
+
+isg_status finish_problem(isg_problem *p) {
+  // kmax and total weight
+  p->kmax = 0;
+  int64_t wsum = 0, wabs = 0;
+  for (int32_t i = 0; i < p->n; ++i) {
+    int64_t a = 0;
+    for (int64_t q = p->rowptr[i]; q < p->rowptr[i + 1]; ++q) {
+      a += std::llabs((long long)p->wt[q]);
+      if (p->col[q] > i) {
+        wsum += p->wt[q];
+        wabs += std::llabs((long long)p->wt[q]);
+      }
+    }
+    p->kmax = std::max<int64_t>(p->kmax, a);
+  }
+  if (wabs >= (int64_t(1) << 30))
+    return fail(ISG_EINVAL, "sum of |w| = %lld is >= 2^30 (int32 energies)", (long long)wabs);
+  p->total_weight = wsum;
+  p->m = p->rowptr[p->n] / 2;
+  // colouring
+  p->colour.assign(p->n, 0);
+  if (p->torus) {
+    for (int32_t i = 0; i < p->n; ++i) p->colour[i] = ((i / p->W) + (i % p->W)) & 1;
+    p->n_colours = 2;
+  } else {
+    std::vector<int32_t> used(p->n + 1, -1);
+    p->n_colours = 1;
+    for (int32_t v = 0; v < p->n; ++v) {
+      for (int64_t q = p->rowptr[v]; q < p->rowptr[v + 1]; ++q)
+        if (p->col[q] < v) used[p->colour[p->col[q]]] = v;
+      int32_t c = 0;
+      while (used[c] == v) ++c;
+      p->colour[v] = c;
+      p->n_colours = std::max(p->n_colours, c + 1);
+    }
+  }
+  // colour-major relabelling: order[new] = original id
+  p->class_start.assign(p->n_colours + 1, 0);
+  for (int32_t i = 0; i < p->n; ++i) p->class_start[p->colour[i] + 1]++;
+  for (int32_t c = 0; c < p->n_colours; ++c) p->class_start[c + 1] += p->class_start[c];
+  p->order.assign(p->n, 0);
+  std::vector<int32_t> fill(p->class_start.begin(), p->class_start.end() - 1);
+  std::vector<int32_t> inv(p->n);
+  for (int32_t i = 0; i < p->n; ++i) {
+    const int32_t nw = fill[p->colour[i]]++;
+    p->order[nw] = i;
+    inv[i] = nw;
+  }
+  p->rowptr_r.assign(p->n + 1, 0);
+  p->col_r.resize(p->rowptr[p->n]);
+  p->wt_r.resize(p->rowptr[p->n]);
+  for (int32_t v = 0; v < p->n; ++v) {
+    const int32_t i = p->order[v];
+    p->rowptr_r[v + 1] = p->rowptr_r[v] + (int32_t)(p->rowptr[i + 1] - p->rowptr[i]);
+    int32_t o = p->rowptr_r[v];
+    for (int64_t q = p->rowptr[i]; q < p->rowptr[i + 1]; ++q, ++o) {
+      p->col_r[o] = inv[p->col[q]];
+      p->wt_r[o] = p->wt[q];
+    }
+  }
+  return ISG_OK;
+}
+
+// Symmetric CSR from an edge list with validation (range, loops, duplicates).
+isg_status csr_from_edges(isg_problem *p, int32_t n, int64_t m, const int32_t *u, const int32_t *v,
+                          const int32_t *w) {
+  if (n < 1) return fail(ISG_EINVAL, "n must be >= 1 (got %d)", n);
+  if (m < 0) return fail(ISG_EINVAL, "m must be >= 0");
+  if (2 * m >= (int64_t(1) << 31)) return fail(ISG_EINVAL, "too many edges (2m >= 2^31)");
+  if (m > 0 && (!u || !v || !w)) return fail(ISG_EINVAL, "edge arrays must not be NULL");
+  p->n = n;
+  p->rowptr.assign(n + 1, 0);
+  for (int64_t e = 0; e < m; ++e) {
+    if (u[e] < 0 || u[e] >= n || v[e] < 0 || v[e] >= n)
+      return fail(ISG_EINVAL, "edge %lld has an endpoint outside [0, %d)", (long long)e, n);
+    if (u[e] == v[e]) return fail(ISG_EINVAL, "edge %lld is a self-loop", (long long)e);
+    p->rowptr[u[e] + 1]++;
+    p->rowptr[v[e] + 1]++;
+  }
+  for (int32_t i = 0; i < n; ++i) p->rowptr[i + 1] += p->rowptr[i];
+  p->col.resize(2 * m);
+  p->wt.resize(2 * m);
+  std::vector<int64_t> fill(p->rowptr.begin(), p->rowptr.end() - 1);
+  for (int64_t e = 0; e < m; ++e) {
+    p->col[fill[u[e]]] = v[e];
+    p->wt[fill[u[e]]++] = w[e];
+    p->col[fill[v[e]]] = u[e];
+    p->wt[fill[v[e]]++] = w[e];
+  }
+  std::vector<std::pair<int32_t, int32_t>> row;
+  for (int32_t i = 0; i < n; ++i) {
+    row.clear();
+    for (int64_t q = p->rowptr[i]; q < p->rowptr[i + 1]; ++q) row.emplace_back(p->col[q], p->wt[q]);
+    std::sort(row.begin(), row.end());
+    for (size_t k = 0; k < row.size(); ++k) {
+      if (k > 0 && row[k].first == row[k - 1].first)
+        return fail(ISG_EINVAL, "vertices %d and %d are joined by more than one edge", i,
+                    row[k].first);
+      p->col[p->rowptr[i] + k] = row[k].first;
+      p->wt[p->rowptr[i] + k] = row[k].second;
+    }
+  }
+  return ISG_OK;
+}
+
+void free_device(isg_problem *p) {
+  for (auto &d : p->dev) {
+    if (d.device < 0) continue;
+    int prev = 0;
+    cudaGetDevice(&prev);
+    cudaSetDevice(d.device);
+    cudaFree(d.cbits);
+    cudaFree(d.class_start);
+    cudaFree(d.rowptr);
+    cudaFree(d.col);
+    cudaFree(d.wt);
+    cudaFree(d.orig);
+    cudaFree(d.rowptr_o);
+    cudaFree(d.col_o);
+    cudaFree(d.wt_o);
+    cudaSetDevice(prev);
+  }
+  p->dev.clear();
+}
+
+template <typename T>
+cudaError_t upload(T **dst, const T *src, size_t count) {
+  const size_t bytes = sizeof(T) * std::max<size_t>(count, 1);
+  cudaError_t err = cudaMalloc((void **)dst, bytes);
+  if (err != cudaSuccess) return err;
+  if (count == 0) return cudaMemset(*dst, 0, bytes);
+  return cudaMemcpy(*dst, src, sizeof(T) * count, cudaMemcpyHostToDevice);
+}
+
+}  // namespace
+
+// Device-resident copy of an instance on the current device: each group of
+// arrays is uploaded once, on the first call that needs it.
+isg_status problem_device(const isg_problem *cp, unsigned need, const DeviceProblem **out) {
+  isg_problem *p = const_cast<isg_problem *>(cp);
+  int device = 0;
+  ISG_CUDA(cudaGetDevice(&device));
+  std::lock_guard<std::mutex> lock(p->mu);
+  DeviceProblem *d = nullptr;
+  for (auto &x : p->dev)
+    if (x.device == device) d = &x;
+  if (!d) {
+    if (p->dev.size() >= 64) return fail(ISG_EINVAL, "instance used on too many devices");
+    p->dev.emplace_back();
+    d = &p->dev.back();
+    d->device = device;
+  }
+  if (!p->torus) need &= ~unsigned(kNeedTorus);
+  cudaError_t err = cudaSuccess;
+  size_t bytes = 0;
+  if ((need & kNeedTorus) && !(d->have & kNeedTorus)) {
+    std::vector<uint8_t> cb(p->n);
+    for (int32_t i = 0; i < p->n; ++i)
+      cb[i] = (uint8_t)((p->jr[i] < 0 ? 1 : 0) | (p->jd[i] < 0 ? 2 : 0));
+    err = upload(&d->cbits, cb.data(), cb.size());
+    bytes += cb.size();
+    if (err == cudaSuccess) d->have |= kNeedTorus;
+  }
+  if (err == cudaSuccess && (need & kNeedCsr) && !(d->have & kNeedCsr)) {
+    err = upload(&d->class_start, p->class_start.data(), p->class_start.size());
+    if (err == cudaSuccess) err = upload(&d->rowptr, p->rowptr_r.data(), p->rowptr_r.size());
+    if (err == cudaSuccess) err = upload(&d->col, p->col_r.data(), p->col_r.size());
+    if (err == cudaSuccess) err = upload(&d->wt, p->wt_r.data(), p->wt_r.size());
+    if (err == cudaSuccess) err = upload(&d->orig, p->order.data(), p->order.size());
+    bytes += 4 * (p->class_start.size() + p->rowptr_r.size() + p->col_r.size() +
+                  p->wt_r.size() + p->order.size());
+    if (err == cudaSuccess) d->have |= kNeedCsr;
+  }
+  if (err == cudaSuccess && (need & kNeedEnergy) && !(d->have & kNeedEnergy)) {
+    err = upload(&d->rowptr_o, p->rowptr.data(), p->rowptr.size());
+    if (err == cudaSuccess) err = upload(&d->col_o, p->col.data(), p->col.size());
+    if (err == cudaSuccess) err = upload(&d->wt_o, p->wt.data(), p->wt.size());
+    bytes += 8 * p->rowptr.size() + 4 * (p->col.size() + p->wt.size());
+    if (err == cudaSuccess) d->have |= kNeedEnergy;
+  }
+  d->bytes_uploaded += bytes;
+  if (err != cudaSuccess) return cuda_fail(err, "uploading the instance");
+  *out = d;
+  return ISG_OK;
+}
+
+// ------------------------------------------------------------------ tables
+
+// T[t][k] = min(floor(2^32 exp(-beta_t * 2k)), 2^32 - 1) for the levels used.
+void build_table(const double *betas, int32_t sweeps, const std::vector<int32_t> &levels,
+                 std::vector<uint32_t> &out) {
+  out.resize((size_t)sweeps * levels.size());
+  for (int32_t t = 0; t < sweeps; ++t)
+    for (size_t j = 0; j < levels.size(); ++j) {
+      const double x = std::floor(std::ldexp(std::exp(-betas[t] * (double)(2 * levels[j])), 32));
+      out[(size_t)t * levels.size() + j] = x >= 4294967295.0 ? 4294967295u : (uint32_t)x;
+    }
+}
+
+isg_status check_betas(const double *betas, int32_t sweeps) {
+  if (!betas) return fail(ISG_EINVAL, "betas must not be NULL");
+  for (int32_t t = 0; t < sweeps; ++t)
+    if (!std::isfinite(betas[t]) || betas[t] < 0)
+      return fail(ISG_EINVAL, "beta[%d] = %g is not finite and >= 0", t, betas[t]);
+  return ISG_OK;
+}
+
+// ------------------------------------------------------------------ results
+
+isg_status result_alloc(isg_result *r, cudaStream_t stream) {
+  const size_t n = (size_t)r->n, R = (size_t)r->R, units = (size_t)r->units;
+  const size_t lanes = units * r->lanes;
+  auto al = [](size_t x) { return (x + 255) & ~size_t(255); };
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    const size_t o = off;
+    off += al(bytes);
+    return o;
+  };
+  const size_t o_spins = take(sizeof(uint32_t) * units * n);
+  const size_t o_best = take(sizeof(uint32_t) * units * n);
+  const size_t o_ecur = take(sizeof(int32_t) * lanes);
+  const size_t o_ebest = take(sizeof(int32_t) * lanes);
+  const size_t o_hit = take(sizeof(int32_t) * units);
+  const size_t o_done = take(sizeof(int32_t) * units);
+  const size_t o_stop = take(sizeof(int32_t));
+  const size_t o_out = take(R * n);
+  const size_t o_outb = take(R * n);
+  const size_t o_table = take(sizeof(uint32_t) * r->table_words);
+  r->bytes = off;
+  cudaError_t err = cudaMallocAsync(&r->base, off, stream);
+  if (err != cudaSuccess) {
+    r->base = nullptr;
+    return fail(ISG_ENOMEM, "device allocation of %zu bytes failed: %s", off,
+                cudaGetErrorString(err));
+  }
+  char *b = (char *)r->base;
+  r->d_spins = (uint32_t *)(b + o_spins);
+  r->d_best = (uint32_t *)(b + o_best);
+  r->d_e_cur = (int32_t *)(b + o_ecur);
+  r->d_e_best = (int32_t *)(b + o_ebest);
+  r->d_hit = (int32_t *)(b + o_hit);
+  r->d_done = (int32_t *)(b + o_done);
+  r->d_stop = (int32_t *)(b + o_stop);
+  r->d_out = (int8_t *)(b + o_out);
+  r->d_out_best = (int8_t *)(b + o_outb);
+  r->d_table = (uint32_t *)(b + o_table);
+  return ISG_OK;
+}
+
+isg_status result_sync(const isg_result *cr) {
+  isg_result *r = const_cast<isg_result *>(cr);
+  std::lock_guard<std::mutex> lock(r->mu);
+  if (r->synced) return r->sync_status;
+  r->synced = true;
+  int prev = 0;
+  cudaGetDevice(&prev);
+  cudaSetDevice(r->device);
+  cudaError_t err = cudaEventSynchronize(r->done);
+  const size_t lanes = (size_t)r->units * r->lanes;
+  r->h_e_cur.resize(lanes);
+  r->h_e_best.resize(lanes);
+  r->h_done.resize(r->units);
+  int32_t stop = -1;
+  if (err == cudaSuccess)
+    err = cudaMemcpy(r->h_e_cur.data(), r->d_e_cur, 4 * lanes, cudaMemcpyDeviceToHost);
+  if (err == cudaSuccess)
+    err = cudaMemcpy(r->h_e_best.data(), r->d_e_best, 4 * lanes, cudaMemcpyDeviceToHost);
+  if (err == cudaSuccess)
+    err = cudaMemcpy(r->h_done.data(), r->d_done, 4 * (size_t)r->units, cudaMemcpyDeviceToHost);
+  if (err == cudaSuccess) err = cudaMemcpy(&stop, r->d_stop, 4, cudaMemcpyDeviceToHost);
+  if (err == cudaSuccess && r->timed) err = cudaEventElapsedTime(&r->kernel_ms, r->t0, r->t1);
+  cudaSetDevice(prev);
+  if (err != cudaSuccess) {
+    r->sync_status = cuda_fail(err, "waiting for the solve");
+    return r->sync_status;
+  }
+  r->hit_sweep = r->has_target ? stop : -1;
+  r->sweeps_done = 0;
+  for (int32_t u = 0; u < r->units; ++u) r->sweeps_done = std::max(r->sweeps_done, r->h_done[u]);
+  r->sync_status = ISG_OK;
+  return ISG_OK;
+}
+
+void result_free(isg_result *r) {
+  if (!r) return;
+  int prev = 0;
+  cudaGetDevice(&prev);
+  cudaSetDevice(r->device);
+  if (r->done) cudaEventSynchronize(r->done);
+  if (r->base) cudaFreeAsync(r->base, r->stream);
+  if (r->done) cudaEventDestroy(r->done);
+  if (r->t0) cudaEventDestroy(r->t0);
+  if (r->t1) cudaEventDestroy(r->t1);
+  cudaSetDevice(prev);
+  delete r;
+}
+
+// ------------------------------------------------------------------ launch shapes
+
+int sm_count() {
+  static int cached = 0;
+  if (!cached) {
+    int dev = 0, v = 0;
+    cudaGetDevice(&dev);
+    if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || v < 1)
+      v = 152;
+    cached = v;
+  }
+  return cached;
+}
+
+int round_up(int x, int m) { return (x + m - 1) / m * m; }
+
+// Torus kernel shape: the smallest power-of-two cluster that puts at least
+// ~0.8 x SMs CTAs on the device (bands of >= 2 rows), then enough threads for
+// ~4 sites per thread per colour phase.
+void torus_shape(int L, int W, int words, int &cluster, int &threads) {
+  const int sms = sm_count();
+  if (cluster <= 0) {
+    cluster = 1;
+    while (cluster < 8 && words * cluster < (sms * 4) / 5 && L / (cluster * 2) >= 2) cluster *= 2;
+  }
+  if (threads <= 0) {
+    const int nr = (L + cluster - 1) / cluster;
+    const int per_phase = nr * (W / 2);
+    threads = std::min(512, std::max(64, round_up((per_phase + 3) / 4, 32)));
+  }
+}
+
+void csr_shape(int n, int quads, int max_class, int &cluster, int &threads, int &qpc) {
+  const int sms = sm_count();
+  if (qpc <= 0) qpc = 1;
+  if (cluster <= 0) {
+    const int groups = (quads + qpc - 1) / qpc;
+    cluster = 1;
+    while (cluster < 8 && groups * cluster < (sms * 4) / 5) cluster *= 2;
+  }
+  if (threads <= 0) {
+    const int per_phase = (max_class + cluster - 1) / cluster;
+    threads = std::min(512, std::max(64, round_up((per_phase + 2) / 3, 32)));
+  }
+  (void)n;
+}
+
+// ------------------------------------------------------------------ anneal
+
+isg_status anneal_impl(const isg_problem *p, int32_t R, const double *betas, int32_t S,
+                       uint64_t seed, int64_t target, const isg_options *opts, cudaStream_t stream,
+                       isg_result **out) {
+  if (!p || !out) return fail(ISG_EINVAL, "problem and out must not be NULL");
+  if (R < 1) return fail(ISG_EINVAL, "replicas must be >= 1 (got %d)", R);
+  if (S < 1) return fail(ISG_EINVAL, "sweeps must be >= 1 (got %d)", S);
+  isg_status st = check_betas(betas, S);
+  if (st != ISG_OK) return st;
+  isg_options o = {};
+  if (opts) o = *opts;
+  int kernel = o.kernel;
+  if (kernel == ISG_KERNEL_AUTO) kernel = p->torus ? ISG_KERNEL_TORUS_MSC : ISG_KERNEL_CSR;
+  if (kernel == ISG_KERNEL_TORUS_MSC && !p->torus)
+    return fail(ISG_EINVAL, "the multi-spin-coded kernel needs a torus instance");
+  const bool plain = kernel == ISG_KERNEL_PLAIN;
+  const bool msc = p->torus && (kernel == ISG_KERNEL_TORUS_MSC || plain);
+  if (o.cluster_ctas < 0 || o.cluster_ctas > 8)
+    return fail(ISG_EINVAL, "cluster_ctas must be in [0, 8]");
+  if (o.threads != 0 && (o.threads < 32 || o.threads > 512 || o.threads % 32))
+    return fail(ISG_EINVAL, "threads must be a multiple of 32 in [32, 512]");
+  const bool has_target = target != ISG_NO_TARGET;
+  if (has_target && (target < INT32_MIN || target > INT32_MAX))
+    return fail(ISG_EINVAL, "target energy outside the int32 range");
+
+  const DeviceProblem *dp = nullptr;
+  st = problem_device(p, msc ? kNeedTorus : kNeedCsr, &dp);
+  if (st != ISG_OK) return st;
+
+  isg_result *r = new isg_result();
+  ISG_CUDA(cudaGetDevice(&r->device));
+  r->stream = stream;
+  r->n = p->n;
+  r->R = R;
+  r->S = S;
+  r->has_target = has_target;
+  r->kernel = plain ? ISG_KERNEL_PLAIN : (msc ? ISG_KERNEL_TORUS_MSC : ISG_KERNEL_CSR);
+  r->msc = msc;
+  r->units = msc ? (R + 31) / 32 : (R + 3) / 4;
+  r->lanes = msc ? 32 : 4;
+  std::vector<int32_t> levels;
+  if (msc) {
+    levels = {2, 4};
+  } else {
+    for (int32_t k = 0; k <= p->kmax; ++k) levels.push_back(k);
+  }
+  std::vector<uint32_t> table;
+  build_table(betas, S, levels, table);
+  r->table_words = table.size();
+
+  st = result_alloc(r, stream);
+  if (st != ISG_OK) {
+    delete r;
+    return st;
+  }
+  cudaError_t err = cudaEventCreateWithFlags(&r->done, cudaEventDisableTiming);
+  if (err == cudaSuccess && o.time_kernels) {
+    r->timed = true;
+    err = cudaEventCreate(&r->t0);
+    if (err == cudaSuccess) err = cudaEventCreate(&r->t1);
+  }
+  if (err == cudaSuccess)
+    err = cudaMemcpyAsync(r->d_table, table.data(), 4 * table.size(), cudaMemcpyHostToDevice,
+                          stream);
+  if (err == cudaSuccess) err = cudaMemsetAsync(r->d_hit, 0xFF, 4 * (size_t)r->units, stream);
+  if (err != cudaSuccess) {
+    result_free(r);
+    return cuda_fail(err, "preparing the solve");
+  }
+
+  const uint32_t key0 = (uint32_t)(seed & 0xFFFFFFFFu), key1 = (uint32_t)(seed >> 32);
+  int launches = 0, sweep_launches = 0;
+  if (r->timed) cudaEventRecord(r->t0, stream);
+  if (msc) {
+    TorusSolve s = {};
+    s.L = p->L;
+    s.W = p->W;
+    s.cbits = dp->cbits;
+    s.table = r->d_table;
+    s.key0 = key0;
+    s.key1 = key1;
+    s.words = r->units;
+    s.replicas = R;
+    s.spins = r->d_spins;
+    s.best = r->d_best;
+    s.e_cur = r->d_e_cur;
+    s.e_best = r->d_e_best;
+    s.hit = r->d_hit;
+    s.done = r->d_done;
+    s.has_target = has_target;
+    s.target = has_target ? (int32_t)target : 0;
+    int cluster = plain ? 1 : o.cluster_ctas, threads = o.threads;
+    torus_shape(p->L, p->W, r->units, cluster, threads);
+    if (torus_smem_bytes(p->L, p->W, cluster) > 227 * 1024) {
+      result_free(r);
+      return fail(ISG_EINVAL, "torus %dx%d needs more shared memory than a CTA has", p->L, p->W);
+    }
+    if (p->L < cluster) cluster = 1;
+    r->ctas = r->units * cluster;
+    r->cluster = cluster;
+    r->threads = threads;
+    const int passes = (has_target && r->units > 1) ? 2 : 1;
+    for (int pass = 0; pass < passes && err == cudaSuccess; ++pass) {
+      TorusSolve sp = s;
+      if (pass == 1) sp.has_target = 0;
+      TorusLaunch l = {};
+      l.cluster = cluster;
+      l.threads = threads;
+      l.stop_from_hits = pass == 1;
+      if (plain) {
+        for (int32_t t = 0; t < S && err == cudaSuccess; ++t) {
+          l.t_begin = t;
+          l.t_end = t + 1;
+          l.resume = t > 0;
+          err = torus_launch(sp, l, stream);
+          ++launches;
+          ++sweep_launches;
+        }
+      } else {
+        l.t_begin = 0;
+        l.t_end = S;
+        l.resume = 0;
+        err = torus_launch(sp, l, stream);
+        ++launches;
+        ++sweep_launches;
+      }
+    }
+  } else {
+    if (csr_smem_bytes(p->n, 1, 1) > 227 * 1024) {
+      result_free(r);
+      return fail(ISG_EINVAL, "instance with n = %d needs more shared memory than a CTA has",
+                  p->n);
+    }
+    CsrSolve s = {};
+    s.n = p->n;
+    s.n_colours = p->n_colours;
+    s.class_start = dp->class_start;
+    s.rowptr = dp->rowptr;
+    s.col = dp->col;
+    s.wt = dp->wt;
+    s.orig = dp->orig;
+    s.kmax = p->kmax;
+    s.table = r->d_table;
+    s.key0 = key0;
+    s.key1 = key1;
+    s.quads = r->units;
+    s.replicas = R;
+    s.spins = r->d_spins;
+    s.best = r->d_best;
+    s.e_cur = r->d_e_cur;
+    s.e_best = r->d_e_best;
+    s.hit = r->d_hit;
+    s.done = r->d_done;
+    s.has_target = has_target;
+    s.target = has_target ? (int32_t)target : 0;
+    int max_class = 0;
+    for (int32_t c = 0; c < p->n_colours; ++c)
+      max_class = std::max(max_class, p->class_start[c + 1] - p->class_start[c]);
+    int cluster = plain ? 1 : o.cluster_ctas, threads = o.threads, qpc = 1;
+    csr_shape(p->n, r->units, max_class, cluster, threads, qpc);
+    r->ctas = ((r->units + qpc - 1) / qpc) * cluster;
+    r->cluster = cluster;
+    r->threads = threads;
+    const int groups = (r->units + qpc - 1) / qpc;
+    const int passes = (has_target && groups > 1) ? 2 : 1;
+    for (int pass = 0; pass < passes && err == cudaSuccess; ++pass) {
+      CsrSolve sp = s;
+      if (pass == 1) sp.has_target = 0;
+      CsrLaunch l = {};
+      l.cluster = cluster;
+      l.threads = threads;
+      l.quads_per_cta = qpc;
+      l.stop_from_hits = pass == 1;
+      if (plain) {
+        for (int32_t t = 0; t < S && err == cudaSuccess; ++t) {
+          l.t_begin = t;
+          l.t_end = t + 1;
+          l.resume = t > 0;
+          err = csr_launch(sp, l, stream);
+          ++launches;
+          ++sweep_launches;
+        }
+      } else {
+        l.t_begin = 0;
+        l.t_end = S;
+        l.resume = 0;
+        err = csr_launch(sp, l, stream);
+        ++launches;
+        ++sweep_launches;
+      }
+    }
+  }
+  if (r->timed && err == cudaSuccess) err = cudaEventRecord(r->t1, stream);
+  if (err == cudaSuccess) {
+    err = reduce_hits(r->d_hit, r->units, r->d_stop, stream);
+    ++launches;
+  }
+  if (err == cudaSuccess) {
+    if (msc) {
+      err = unpack_msc(r->d_spins, p->n, R, r->d_out, stream);
+      if (err == cudaSuccess) err = unpack_msc(r->d_best, p->n, R, r->d_out_best, stream);
+    } else {
+      err = unpack_quads(r->d_spins, p->n, R, dp->orig, r->d_out, stream);
+      if (err == cudaSuccess) err = unpack_quads(r->d_best, p->n, R, dp->orig, r->d_out_best, stream);
+    }
+    launches += 2;
+  }
+  if (err == cudaSuccess) err = cudaEventRecord(r->done, stream);
+  if (err != cudaSuccess) {
+    cudaStreamSynchronize(stream);
+    result_free(r);
+    return cuda_fail(err, "launching the sweeps");
+  }
+  r->launches = launches;
+  r->sweep_launches = sweep_launches;
+  *out = r;
+  return ISG_OK;
+}
+
+}  // namespace isg
+
+// ====================================================================== C ABI
+
+using namespace isg;
+
+extern "C" {
+
+const char *isg_last_error(void) { return g_last_error.c_str(); }
+
+const char *isg_version(void) { return "isg 0.1 (sm_103a)"; }
+
+isg_status isg_problem_create_edges(int32_t n, int64_t m, const int32_t *u, const int32_t *v,
+                                    const int32_t *w, isg_problem **out) {
+  if (!out) return fail(ISG_EINVAL, "out must not be NULL");
+  *out = nullptr;
+  isg_problem *p = new isg_problem();
+  isg_status st = csr_from_edges(p, n, m, u, v, w);
+  if (st == ISG_OK) st = finish_problem(p);
+  if (st != ISG_OK) {
+    delete p;
+    return st;
+  }
+  *out = p;
+  return ISG_OK;
+}
+
+isg_status isg_problem_create_csr(int32_t n, const int64_t *rowptr, const int32_t *col,
+                                  const int32_t *w, isg_problem **out) {
+  if (!out) return fail(ISG_EINVAL, "out must not be NULL");
+  *out = nullptr;
+  if (n < 1) return fail(ISG_EINVAL, "n must be >= 1 (got %d)", n);
+  if (!rowptr) return fail(ISG_EINVAL, "rowptr must not be NULL");
+  if (rowptr[0] != 0) return fail(ISG_EINVAL, "rowptr[0] must be 0");
+  for (int32_t i = 0; i < n; ++i)
+    if (rowptr[i + 1] < rowptr[i]) return fail(ISG_EINVAL, "rowptr must be non-decreasing");
+  const int64_t nnz = rowptr[n];
+  if (nnz % 2) return fail(ISG_EINVAL, "a symmetric CSR has an even number of entries");
+  if (nnz > 0 && (!col || !w)) return fail(ISG_EINVAL, "col and w must not be NULL");
+  // collect (i < j) entries, checking that each has its mirror with the same weight
+  std::vector<int32_t> eu, ev, ew;
+  for (int32_t i = 0; i < n; ++i)
+    for (int64_t q = rowptr[i]; q < rowptr[i + 1]; ++q) {
+      const int32_t j = col[q];
+      if (j < 0 || j >= n) return fail(ISG_EINVAL, "column %d outside [0, %d)", j, n);
+      if (j == i) return fail(ISG_EINVAL, "vertex %d has a self-loop", i);
+      bool mirrored = false;
+      for (int64_t z = rowptr[j]; z < rowptr[j + 1]; ++z)
+        if (col[z] == i && w[z] == w[q]) mirrored = true;
+      if (!mirrored)
+        return fail(ISG_EINVAL, "entry (%d, %d) has no mirror (%d, %d) of equal weight", i, j, j,
+                    i);
+      if (i < j) {
+        eu.push_back(i);
+        ev.push_back(j);
+        ew.push_back(w[q]);
+      }
+    }
+  if ((int64_t)eu.size() * 2 != nnz) return fail(ISG_EINVAL, "CSR entries are not symmetric");
+  return isg_problem_create_edges(n, (int64_t)eu.size(), eu.data(), ev.data(), ew.data(), out);
+}
+
+isg_status isg_problem_create_torus(int32_t L, int32_t W, const int8_t *j_right,
+                                    const int8_t *j_down, isg_problem **out) {
+  if (!out) return fail(ISG_EINVAL, "out must not be NULL");
+  *out = nullptr;
+  if (L < 4 || W < 4 || (L & 1) || (W & 1))
+    return fail(ISG_EINVAL, "torus sides must be even and >= 4 (got %d x %d)", L, W);
+  if ((int64_t)L * W >= (int64_t(1) << 28)) return fail(ISG_EINVAL, "torus too large");
+  if (!j_right || !j_down) return fail(ISG_EINVAL, "coupling arrays must not be NULL");
+  const int32_t n = L * W;
+  for (int32_t i = 0; i < n; ++i)
+    if ((j_right[i] != 1 && j_right[i] != -1) || (j_down[i] != 1 && j_down[i] != -1))
+      return fail(ISG_EINVAL, "torus coupling at site %d is not +1 or -1", i);
+  std::vector<int32_t> u(2 * (size_t)n), v(2 * (size_t)n), w(2 * (size_t)n);
+  for (int32_t r = 0; r < L; ++r)
+    for (int32_t c = 0; c < W; ++c) {
+      const int32_t i = r * W + c;
+      u[2 * i] = i;
+      v[2 * i] = r * W + (c + 1) % W;
+      w[2 * i] = j_right[i];
+      u[2 * i + 1] = i;
+      v[2 * i + 1] = ((r + 1) % L) * W + c;
+      w[2 * i + 1] = j_down[i];
+    }
+  isg_problem *p = new isg_problem();
+  p->torus = true;
+  p->L = L;
+  p->W = W;
+  p->jr.assign(j_right, j_right + n);
+  p->jd.assign(j_down, j_down + n);
+  isg_status st = csr_from_edges(p, n, 2 * (int64_t)n, u.data(), v.data(), w.data());
+  if (st == ISG_OK) st = finish_problem(p);
+  if (st != ISG_OK) {
+    delete p;
+    return st;
+  }
+  *out = p;
+  return ISG_OK;
+}
+
+isg_status isg_problem_info(const isg_problem *p, int32_t *n, int64_t *m, int64_t *total_weight,
+                            int32_t *n_colors, int32_t *colors) {
+  if (!p) return fail(ISG_EINVAL, "problem must not be NULL");
+  if (n) *n = p->n;
+  if (m) *m = p->m;
+  if (total_weight) *total_weight = p->total_weight;
+  if (n_colors) *n_colors = p->n_colours;
+  if (colors) std::copy(p->colour.begin(), p->colour.end(), colors);
+  return ISG_OK;
+}
+
+void isg_problem_destroy(isg_problem *p) {
+  if (!p) return;
+  free_device(p);
+  delete p;
+}
+
+isg_status isg_anneal(const isg_problem *p, int32_t replicas, const double *betas, int32_t sweeps,
+                      uint64_t seed, int64_t target_energy, void *cuda_stream, isg_result **out) {
+  return anneal_impl(p, replicas, betas, sweeps, seed, target_energy, nullptr,
+                     (cudaStream_t)cuda_stream, out);
+}
+
+isg_status isg_anneal_ex(const isg_problem *p, int32_t replicas, const double *betas,
+                         int32_t sweeps, uint64_t seed, int64_t target_energy,
+                         const isg_options *opts, void *cuda_stream, isg_result **out) {
+  return anneal_impl(p, replicas, betas, sweeps, seed, target_energy, opts,
+                     (cudaStream_t)cuda_stream, out);
+}
+
+isg_status isg_energy(const isg_problem *p, const int8_t *spins, int32_t replicas,
+                      int64_t *energies) {
+  if (!p || !spins || !energies) return fail(ISG_EINVAL, "arguments must not be NULL");
+  if (replicas < 1 || replicas > 65535) return fail(ISG_EINVAL, "replicas must be in [1, 65535]");
+  const DeviceProblem *dp = nullptr;
+  isg_status st = problem_device(p, kNeedEnergy, &dp);
+  if (st != ISG_OK) return st;
+  const int blocks = std::max(1, std::min(64, (p->n + 255) / 256));
+  const size_t sbytes = (size_t)replicas * p->n;
+  void *mem = nullptr;
+  cudaStream_t stream = 0;
+  const size_t need = ((sbytes + 255) & ~size_t(255)) + 8 * (size_t)replicas * blocks +
+                      8 * (size_t)replicas;
+  ISG_CUDA(cudaMallocAsync(&mem, need, stream));
+  int8_t *d_s = (int8_t *)mem;
+  int64_t *d_scratch = (int64_t *)((char *)mem + ((sbytes + 255) & ~size_t(255)));
+  int64_t *d_e = d_scratch + (size_t)replicas * blocks;
+  cudaError_t err = cudaMemcpyAsync(d_s, spins, sbytes, cudaMemcpyHostToDevice, stream);
+  if (err == cudaSuccess)
+    err = energy_csr(dp->rowptr_o, dp->col_o, dp->wt_o, p->n, d_s, replicas, d_scratch, blocks,
+                     d_e, stream);
+  if (err == cudaSuccess)
+    err = cudaMemcpyAsync(energies, d_e, 8 * (size_t)replicas, cudaMemcpyDeviceToHost, stream);
+  if (err == cudaSuccess) err = cudaStreamSynchronize(stream);
+  cudaFreeAsync(mem, stream);
+  if (err != cudaSuccess) return cuda_fail(err, "isg_energy");
+  return ISG_OK;
+}
+
+isg_status isg_result_final(const isg_result *r, int8_t *spins, int32_t *energies,
+                            int32_t *sweeps_done) {
+  if (!r) return fail(ISG_EINVAL, "result must not be NULL");
+  isg_status st = result_sync(r);
+  if (st != ISG_OK) return st;
+  if (spins) {
+    int prev = 0;
+    cudaGetDevice(&prev);
+    cudaSetDevice(r->device);
+    cudaError_t err = cudaMemcpy(spins, r->d_out, (size_t)r->R * r->n, cudaMemcpyDeviceToHost);
+    cudaSetDevice(prev);
+    if (err != cudaSuccess) return cuda_fail(err, "reading final spins");
+  }
+  if (energies)
+    for (int32_t k = 0; k < r->R; ++k) energies[k] = r->h_e_cur[k];
+  if (sweeps_done) *sweeps_done = r->sweeps_done;
+  return ISG_OK;
+}
+
+isg_status isg_best(const isg_result *r, int32_t *best_energy, int32_t *best_replica,
+                    int8_t *best_spins, int32_t *per_replica_best, int32_t *hit_sweep) {
+  if (!r) return fail(ISG_EINVAL, "result must not be NULL");
+  isg_status st = result_sync(r);
+  if (st != ISG_OK) return st;
+  int32_t be = INT32_MAX, br = 0;
+  for (int32_t k = 0; k < r->R; ++k)
+    if (r->h_e_best[k] < be) {
+      be = r->h_e_best[k];
+      br = k;
+    }
+  if (best_energy) *best_energy = be;
+  if (best_replica) *best_replica = br;
+  if (per_replica_best)
+    for (int32_t k = 0; k < r->R; ++k) per_replica_best[k] = r->h_e_best[k];
+  if (hit_sweep) *hit_sweep = r->hit_sweep;
+  if (best_spins) {
+    int prev = 0;
+    cudaGetDevice(&prev);
+    cudaSetDevice(r->device);
+    cudaError_t err = cudaMemcpy(best_spins, r->d_out_best + (size_t)br * r->n, (size_t)r->n,
+                                 cudaMemcpyDeviceToHost);
+    cudaSetDevice(prev);
+    if (err != cudaSuccess) return cuda_fail(err, "reading best spins");
+  }
+  return ISG_OK;
+}
+
+isg_status isg_result_shape(const isg_result *r, int32_t *n, int32_t *replicas, int32_t *sweeps) {
+  if (!r) return fail(ISG_EINVAL, "result must not be NULL");
+  if (n) *n = r->n;
+  if (replicas) *replicas = r->R;
+  if (sweeps) *sweeps = r->S;
+  return ISG_OK;
+}
+
+isg_status isg_result_best_all(const isg_result *r, int8_t *best_spins) {
+  if (!r || !best_spins) return fail(ISG_EINVAL, "arguments must not be NULL");
+  isg_status st = result_sync(r);
+  if (st != ISG_OK) return st;
+  int prev = 0;
+  cudaGetDevice(&prev);
+  cudaSetDevice(r->device);
+  cudaError_t err =
+      cudaMemcpy(best_spins, r->d_out_best, (size_t)r->R * r->n, cudaMemcpyDeviceToHost);
+  cudaSetDevice(prev);
+  if (err != cudaSuccess) return cuda_fail(err, "reading best spins");
+  return ISG_OK;
+}
+
+isg_status isg_result_stats(const isg_result *r, isg_stats *stats) {
+  if (!r || !stats) return fail(ISG_EINVAL, "arguments must not be NULL");
+  isg_status st = result_sync(r);
+  if (st != ISG_OK) return st;
+  stats->sweep_kernel_ms = r->timed ? r->kernel_ms : -1.0f;
+  stats->launches = r->launches;
+  stats->sweep_launches = r->sweep_launches;
+  stats->kernel = r->kernel;
+  stats->ctas = r->ctas;
+  stats->cluster_ctas = r->cluster;
+  stats->threads = r->threads;
+  return ISG_OK;
+}
+
+void isg_result_destroy(isg_result *r) { result_free(r); }
+
+}  // extern "C"

@@ -1,0 +1,401 @@
+// torus_msc.cu -- checkerboard Metropolis sweeps on L x W +-1 tori with
+// multi-spin coding: 32 replicas per uint32 word, one bit per replica.
+//
+// Per site and replica word the kernel forms the four "unsatisfied bond"
+// words (bond (i,j) is unsatisfied when w_ij s_i s_j = +1), counts them
+// bit-sliced (U = 0..4 per replica), and flips replicas with U >= 2 (energy
+// change d = 8 - 4U <= 0) outright and those with U = 1 (d = 4) or U = 0
+// (d = 8) when their Philox uniform is below the sweep's threshold.
+//
+// Layout: a cluster of K CTAs owns one replica word of one instance; CTA k
+// holds a band of rows plus one halo row above and below in shared memory.
+// Sites of one colour never neighbour each other, so a colour phase needs no
+// intra-phase synchronisation; updated band-edge rows are written straight
+// into the neighbouring CTA's halo (distributed shared memory), and one
+// cluster barrier separates the phases.  Per-replica energy changes are
+// accumulated in bit-sliced counters and reduced once per sweep.
+#include <climits>
+
+#include "isg_device.cuh"
+#include "isg_kernels.h"
+
+namespace isg {
+namespace {
+
+struct Band {
+  int r0, nr;
+};
+
+__host__ __device__ __forceinline__ Band band_of(int L, int K, int k) {
+  const int r0 = (int)((int64_t)k * L / K);
+  const int r1 = (int)((int64_t)(k + 1) * L / K);
+  return {r0, r1 - r0};
+}
+
+__host__ __device__ __forceinline__ size_t align16(size_t x) { return (x + 15) & ~size_t(15); }
+
+struct SmemLayout {
+  size_t spin, cb, part, lane_acc, flags, total;
+};
+
+__host__ __device__ __forceinline__ SmemLayout layout_of(int nr, int W, int K) {
+  SmemLayout m;
+  m.spin = 0;
+  m.cb = align16(m.spin + sizeof(uint32_t) * (size_t)(nr + 2) * W);
+  m.part = align16(m.cb + (size_t)(nr + 2) * W);
+  m.lane_acc = m.part + sizeof(int32_t) * 32 * (size_t)K;
+  m.flags = m.lane_acc + sizeof(int32_t) * 32;
+  m.total = align16(m.flags + sizeof(uint32_t) * 4);
+  return m;
+}
+
+__device__ __forceinline__ uint32_t sign_mask(uint32_t bit) { return 0u - (bit & 1u); }
+
+// Initial spins of sites i for the 32 replicas of `word`: bit l = top bit of
+// word (l mod 4) of Philox(i, 0, 8*word + l/4, init tag).
+__device__ __forceinline__ uint32_t initial_word(uint32_t i, uint32_t word, PhiloxKey key) {
+  uint32_t s = 0u;
+#pragma unroll
+  for (uint32_t q = 0; q < 8; ++q) {
+    const uint4 u = philox10(make_uint4(i, 0u, 8u * word + q, kTagInit), key);
+    s |= ((u.x >> 31) << (4 * q)) | ((u.y >> 31) << (4 * q + 1)) | ((u.z >> 31) << (4 * q + 2)) |
+         ((u.w >> 31) << (4 * q + 3));
+  }
+  return s;
+}
+
+__device__ __forceinline__ void sync_group(int K) {
+  if (K == 1)
+    __syncthreads();
+  else
+    cluster_barrier();
+}
+
+// Per-lane totals of the bit-sliced counters over the CTA, published to every
+// CTA of the cluster as part[k][lane]; ends with the group barrier.
+template <int NP>
+__device__ __forceinline__ void publish_lane_totals(const SlicedCounter<NP> &cnt, int32_t *lane_acc,
+                                                    int32_t *part, int k, int K) {
+  const int32_t tot = cnt.warp_lane_total();
+  atomicAdd(&lane_acc[lane_id()], tot);
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    const int32_t v = lane_acc[threadIdx.x];
+    lane_acc[threadIdx.x] = 0;
+    if (K == 1) {
+      part[threadIdx.x] = v;
+    } else {
+      for (int q = 0; q < K; ++q) peer_smem(part, (uint32_t)q)[k * 32 + threadIdx.x] = v;
+    }
+  }
+  sync_group(K);
+}
+
+// Anneal one replica word of one torus: this CTA is rank k of K.
+template <int NP, bool kTwoThresholds>
+__device__ __forceinline__ void sweep_phase(uint32_t *spin, const uint8_t *cb, uint32_t *up_peer,
+                                            uint32_t *down_peer, int W, int r0, int nr, int c,
+                                            uint32_t t, uint32_t word, PhiloxKey key, uint32_t T4,
+                                            uint32_t T8, SlicedCounter<NP> &cnt) {
+  const int half = W >> 1;
+  const int step_rows = blockDim.x / half;
+  const int step_cols = blockDim.x - step_rows * half;
+  int lr = 1 + (int)threadIdx.x / half;
+  int j = (int)threadIdx.x - (lr - 1) * half;
+  while (lr <= nr) {
+    const int gr = r0 + lr - 1;
+    const int col = 2 * j + ((c + gr) & 1);
+    const int x = lr * W + col;
+    const int xl = (col == 0) ? x + W - 1 : x - 1;
+    const int xr = (col == W - 1) ? x - W + 1 : x + 1;
+    const uint32_t s0 = spin[x];
+    const uint32_t cbx = cb[x];
+    const uint32_t a = ~(s0 ^ spin[xr] ^ sign_mask(cbx));
+    const uint32_t b = ~(s0 ^ spin[xl] ^ sign_mask(cb[xl]));
+    const uint32_t cu = ~(s0 ^ spin[x - W] ^ sign_mask(cb[x - W] >> 1));
+    const uint32_t d = ~(s0 ^ spin[x + W] ^ sign_mask(cbx >> 1));
+    // U = a + b + cu + d bit-sliced as (u2 u1 u0)
+    const uint32_t s1 = a ^ b, c1 = a & b, s2 = cu ^ d, c2 = cu & d;
+    const uint32_t u0 = s1 ^ s2;
+    const uint32_t u1 = (c1 ^ c2) | (s1 & s2);
+    const uint32_t u2 = c1 & c2;
+    const uint32_t eq0 = ~(u0 | u1 | u2);
+    const uint32_t eq1 = u0 & ~u1;
+    const uint32_t ge2 = u1 | u2;
+    // uniforms of the 32 replicas: 8 Philox blocks of 4
+    uint32_t r4 = 0u, r8 = 0u;
+    const uint32_t site = (uint32_t)(gr * W + col);
+#pragma unroll
+    for (uint32_t q = 0; q < 8; ++q) {
+      const uint4 u = philox10(make_uint4(site, t, 8u * word + q, kTagSweep), key);
+      r4 |= ((u.x < T4) ? 1u : 0u) << (4 * q);
+      r4 |= ((u.y < T4) ? 1u : 0u) << (4 * q + 1);
+      r4 |= ((u.z < T4) ? 1u : 0u) << (4 * q + 2);
+      r4 |= ((u.w < T4) ? 1u : 0u) << (4 * q + 3);
+      if (kTwoThresholds) {
+        r8 |= ((u.x < T8) ? 1u : 0u) << (4 * q);
+        r8 |= ((u.y < T8) ? 1u : 0u) << (4 * q + 1);
+        r8 |= ((u.z < T8) ? 1u : 0u) << (4 * q + 2);
+        r8 |= ((u.w < T8) ? 1u : 0u) << (4 * q + 3);
+      }
+    }
+    const uint32_t acc = ge2 | (eq1 & r4) | (eq0 & r8);
+    const uint32_t sn = s0 ^ acc;
+    spin[x] = sn;
+    if (lr == 1) up_peer[col] = sn;
+    if (lr == nr) down_peer[col] = sn;
+    // v = accepted ? 4 - U : 2  (the energy change is 4 (v - 2))
+    cnt.add3(acc & u0, (acc & (u0 ^ u1)) | ~acc, acc & eq0);
+    j += step_cols;
+    lr += step_rows;
+    if (j >= half) {
+      j -= half;
+      ++lr;
+    }
+  }
+}
+
+template <int NP>
+__device__ void torus_word(const TorusSolve &s, int word, int k, int K, int t_begin, int t_end,
+                           int resume, uint8_t *smem) {
+  const int L = s.L, W = s.W, n = L * W;
+  const Band band = band_of(L, K, k);
+  const int r0 = band.r0, nr = band.nr;
+  // every CTA of the cluster uses the layout of the tallest band, so that a
+  // shared-memory offset means the same array in every peer
+  const SmemLayout lay = layout_of((L + K - 1) / K, W, K);
+  uint32_t *spin = reinterpret_cast<uint32_t *>(smem + lay.spin);
+  uint8_t *cb = smem + lay.cb;
+  int32_t *part = reinterpret_cast<int32_t *>(smem + lay.part);
+  int32_t *lane_acc = reinterpret_cast<int32_t *>(smem + lay.lane_acc);
+  volatile uint32_t *flags = reinterpret_cast<uint32_t *>(smem + lay.flags);
+  const PhiloxKey key{s.key0, s.key1};
+  const uint32_t uword = (uint32_t)word;
+  const int rem = s.replicas - 32 * word;
+  const uint32_t valid = rem >= 32 ? 0xFFFFFFFFu : ((1u << rem) - 1u);
+  uint32_t *gspin = s.spins + (size_t)word * n;
+  uint32_t *gbest = s.best + (size_t)word * n;
+  const int lane = (int)lane_id();
+
+  if (resume && s.has_target && s.hit[word] >= 0) return;  // this solve already stopped
+  if (resume && t_begin >= t_end) return;                   // nothing left to run
+  if (!resume && s.has_target && k == 0 && threadIdx.x == 0) s.hit[word] = -1;
+
+  // band rows and halos: global row r0 - 1 + lr for lr = 0..nr+1
+  for (int x = threadIdx.x; x < (nr + 2) * W; x += blockDim.x) {
+    const int lr = x / W;
+    const int c = x - lr * W;
+    int gr = r0 - 1 + lr;
+    gr = gr < 0 ? gr + L : (gr >= L ? gr - L : gr);
+    const int i = gr * W + c;
+    cb[x] = s.cbits[i];
+    spin[x] = resume ? gspin[i] : initial_word((uint32_t)i, uword, key);
+  }
+  if (threadIdx.x < 32) lane_acc[threadIdx.x] = 0;
+  __syncthreads();
+
+  int32_t e = 0, e_best = 0;  // meaningful in warp 0, lane = replica bit
+  SlicedCounter<NP> cnt;
+  if (!resume) {
+    // E = sum over bonds of (+1 unsatisfied, -1 satisfied) = 2 U_tot - 2n
+    cnt.clear();
+    for (int idx = threadIdx.x; idx < nr * W; idx += blockDim.x) {
+      const int x = W + idx;
+      const int c = idx % W;
+      const uint32_t s0 = spin[x];
+      const uint32_t cbx = cb[x];
+      const uint32_t a = ~(s0 ^ spin[c == W - 1 ? x - W + 1 : x + 1] ^ sign_mask(cbx));
+      const uint32_t d = ~(s0 ^ spin[x + W] ^ sign_mask(cbx >> 1));
+      cnt.add2(a ^ d, a & d);
+      const int gr = r0 + idx / W;
+      gbest[gr * W + c] = s0;
+    }
+    publish_lane_totals<NP>(cnt, lane_acc, part, k, K);
+    if (threadIdx.x < 32) {
+      int32_t tot = 0;
+      for (int q = 0; q < K; ++q) tot += part[q * 32 + lane];
+      e = 2 * tot - 2 * n;
+      e_best = e;
+    }
+  } else if (threadIdx.x < 32) {
+    e = s.e_cur[word * 32 + lane];
+    e_best = s.e_best[word * 32 + lane];
+  }
+
+  const int kup = (k + K - 1) % K, kdown = (k + 1) % K;
+  uint32_t *up_peer = (K == 1 ? spin : peer_smem(spin, (uint32_t)kup)) +
+                      (size_t)(band_of(L, K, kup).nr + 1) * W;
+  uint32_t *down_peer = (K == 1 ? spin : peer_smem(spin, (uint32_t)kdown));
+
+  int t = t_begin;
+  int hit = -1;
+  for (; t < t_end; ++t) {
+    const uint32_t T4 = s.table[2 * t], T8 = s.table[2 * t + 1];
+    cnt.clear();
+    for (int c = 0; c < 2; ++c) {
+      if (T8 != 0u)
+        sweep_phase<NP, true>(spin, cb, up_peer, down_peer, W, r0, nr, c, (uint32_t)t, uword,
+                              key, T4, T8, cnt);
+      else
+        sweep_phase<NP, false>(spin, cb, up_peer, down_peer, W, r0, nr, c, (uint32_t)t, uword,
+                               key, T4, T8, cnt);
+      if (c == 0) sync_group(K);
+    }
+    publish_lane_totals<NP>(cnt, lane_acc, part, k, K);
+    if (threadIdx.x < 32) {
+      int32_t tot = 0;
+      for (int q = 0; q < K; ++q) tot += part[q * 32 + lane];
+      e += 4 * (tot - 2 * n);
+      const bool better = e < e_best;
+      if (better) e_best = e;
+      const uint32_t imp = __ballot_sync(0xFFFFFFFFu, better) & valid;
+      const int32_t mn = __reduce_min_sync(0xFFFFFFFFu, ((valid >> lane) & 1u) ? e_best : INT_MAX);
+      if (lane == 0) {
+        flags[0] = imp;
+        flags[1] = (s.has_target && mn <= s.target) ? 1u : 0u;
+      }
+    }
+    __syncthreads();
+    const uint32_t imp = flags[0];
+    const uint32_t stop = flags[1];
+    if (imp != 0u) {
+      for (int idx = threadIdx.x; idx < nr * W; idx += blockDim.x) {
+        const int g = r0 * W + idx;
+        gbest[g] = (gbest[g] & ~imp) | (spin[W + idx] & imp);
+      }
+    }
+    if (stop) {
+      hit = t;
+      ++t;
+      break;
+    }
+  }
+
+  for (int idx = threadIdx.x; idx < nr * W; idx += blockDim.x) gspin[r0 * W + idx] = spin[W + idx];
+  if (k == 0) {
+    if (threadIdx.x < 32) {
+      s.e_cur[word * 32 + lane] = e;
+      s.e_best[word * 32 + lane] = e_best;
+    }
+    if (threadIdx.x == 0) {
+      if (s.has_target && hit >= 0) s.hit[word] = hit;
+      s.done[word] = t;
+    }
+  }
+}
+
+template <int NP>
+__global__ void __launch_bounds__(512) torus_kernel(TorusSolve s, TorusLaunch l) {
+  extern __shared__ __align__(16) uint8_t smem[];
+  const int K = l.cluster;
+  const int k = (int)(blockIdx.x % K);
+  const int word = (int)(blockIdx.x / K);
+  int t_end = l.t_end;
+  if (l.stop_from_hits) {
+    int m = INT_MAX;
+    for (int w = 0; w < s.words; ++w)
+      if (s.hit[w] >= 0 && s.hit[w] < m) m = s.hit[w];
+    if (m != INT_MAX && m + 1 < t_end) t_end = m + 1;
+  }
+  torus_word<NP>(s, word, k, K, l.t_begin, t_end, l.resume, smem);
+}
+
+template <int NP>
+__global__ void __launch_bounds__(512) torus_batch_kernel(const TorusBatchItem *items,
+                                                          const int32_t *count_dev,
+                                                          const int32_t *order, int32_t *next) {
+  extern __shared__ __align__(16) uint8_t smem[];
+  __shared__ int item;
+  const int count = *count_dev;
+  for (;;) {
+    if (threadIdx.x == 0) item = atomicAdd(next, 1);
+    __syncthreads();
+    const int it = item;
+    __syncthreads();
+    if (it >= count) break;
+    const TorusBatchItem u = items[order[it]];
+    torus_word<NP>(u.solve, u.word, 0, 1, u.t_begin, u.t_end, u.resume, smem);
+    __syncthreads();
+  }
+}
+
+int np_for(int sites_per_thread_sweep, int sites_per_thread_band) {
+  const int need = 4 * sites_per_thread_sweep > 2 * sites_per_thread_band
+                       ? 4 * sites_per_thread_sweep
+                       : 2 * sites_per_thread_band;
+  if (need < (1 << 6)) return 6;
+  if (need < (1 << 8)) return 8;
+  if (need < (1 << 10)) return 10;
+  return -1;
+}
+
+template <typename Kern>
+cudaError_t launch_clustered(Kern kernel, int grid, int threads, size_t smem, int cluster,
+                             cudaStream_t stream, const TorusSolve &s, const TorusLaunch &l) {
+  cudaError_t err = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+  if (err != cudaSuccess) return err;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(threads);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = stream;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = cluster;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kernel, s, l);
+}
+
+}  // namespace
+
+size_t torus_smem_bytes(int32_t L, int32_t W, int32_t cluster) {
+  int nr_max = 0;
+  for (int k = 0; k < cluster; ++k) {
+    const int nr = band_of(L, cluster, k).nr;
+    if (nr > nr_max) nr_max = nr;
+  }
+  return layout_of(nr_max, W, cluster).total;
+}
+
+int32_t torus_sites_per_thread(int32_t L, int32_t W, int32_t cluster, int32_t threads) {
+  const int nr = (L + cluster - 1) / cluster;
+  const int per_phase = (nr * (W / 2) + threads - 1) / threads;
+  return 2 * per_phase;
+}
+
+cudaError_t torus_launch(const TorusSolve &s, const TorusLaunch &l, cudaStream_t stream) {
+  const int K = l.cluster;
+  const size_t smem = torus_smem_bytes(s.L, s.W, K);
+  const int nr = (s.L + K - 1) / K;
+  const int spt = torus_sites_per_thread(s.L, s.W, K, l.threads);
+  const int band_spt = (nr * s.W + l.threads - 1) / l.threads;
+  const int np = np_for(spt, band_spt);
+  const int grid = s.words * K;
+  switch (np) {
+    case 6: return launch_clustered(torus_kernel<6>, grid, l.threads, smem, K, stream, s, l);
+    case 8: return launch_clustered(torus_kernel<8>, grid, l.threads, smem, K, stream, s, l);
+    case 10: return launch_clustered(torus_kernel<10>, grid, l.threads, smem, K, stream, s, l);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+size_t torus_batch_max_smem(int32_t L, int32_t W) { return layout_of(L, W, 1).total; }
+
+cudaError_t torus_batch_launch(const TorusBatchItem *items_dev, const int32_t *count_dev,
+                               const int32_t *order_dev, int32_t *next_dev, int32_t ctas,
+                               int32_t threads, size_t smem, cudaStream_t stream) {
+  // ten counter planes hold 4 x sites-per-thread-per-sweep for every torus the
+  // batched forms accept (at most 127 sites per thread and colour phase)
+  cudaError_t err = cudaFuncSetAttribute(torus_batch_kernel<10>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (err != cudaSuccess) return err;
+  torus_batch_kernel<10><<<ctas, threads, smem, stream>>>(items_dev, count_dev, order_dev,
+                                                           next_dev);
+  return cudaGetLastError();
+}
+
+}  // namespace isg

@@ -1,0 +1,359 @@
+"""Python binding of libisg (the C ABI of ``include/isg.h``).
+
+Argument marshalling only: every step of the annealing path runs in the CUDA
+library.  Functions carry the C names; arrays are numpy; handles are opaque
+integers wrapped in small owner classes.  PyTorch is used for one thing: when
+no stream is given, work is enqueued on ``torch.cuda.current_stream()``.
+
+The library is built in-tree by ``paper_2311_09275_gb300.build``.  Importing
+this module without the built library raises ImportError: there is no
+fallback implementation.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_build", "libisg.so")
+if not os.path.exists(_LIB_PATH):
+    raise ImportError(f"libisg is not built ({_LIB_PATH}); run "
+                      "`python -c 'import __graft_entry__ as g; g.build()'` first")
+_lib = ctypes.CDLL(_LIB_PATH)
+
+ISG_OK, ISG_EINVAL, ISG_ENOMEM, ISG_ECUDA, ISG_ETIMEOUT, ISG_EBUSY, ISG_ECANCELLED = range(7)
+ISG_NO_TARGET = -(2 ** 63)
+KERNEL_AUTO, KERNEL_TORUS_MSC, KERNEL_CSR, KERNEL_PLAIN = range(4)
+
+_P = ctypes.c_void_p
+_i32, _i64, _u64, _dbl, _sz = ctypes.c_int32, ctypes.c_int64, ctypes.c_uint64, ctypes.c_double, \
+    ctypes.c_size_t
+
+
+class isg_options(ctypes.Structure):
+    _fields_ = [("kernel", _i32), ("cluster_ctas", _i32), ("threads", _i32),
+                ("time_kernels", _i32)]
+
+
+class isg_stats(ctypes.Structure):
+    _fields_ = [("sweep_kernel_ms", ctypes.c_float), ("launches", _i32),
+                ("sweep_launches", _i32), ("kernel", _i32), ("ctas", _i32),
+                ("cluster_ctas", _i32), ("threads", _i32)]
+
+
+def _sig(name, args, res=ctypes.c_int):
+    f = getattr(_lib, name)
+    f.argtypes = args
+    f.restype = res
+    return f
+
+
+_sig("isg_problem_create_edges", [_i32, _i64, _P, _P, _P, ctypes.POINTER(_P)])
+_sig("isg_problem_create_csr", [_i32, _P, _P, _P, ctypes.POINTER(_P)])
+_sig("isg_problem_create_torus", [_i32, _i32, _P, _P, ctypes.POINTER(_P)])
+_sig("isg_problem_info", [_P, _P, _P, _P, _P, _P])
+_sig("isg_problem_destroy", [_P], None)
+_sig("isg_anneal", [_P, _i32, _P, _i32, _u64, _i64, _P, ctypes.POINTER(_P)])
+_sig("isg_anneal_ex", [_P, _i32, _P, _i32, _u64, _i64, ctypes.POINTER(isg_options), _P,
+                       ctypes.POINTER(_P)])
+_sig("isg_anneal_batch", [_P, _i32, _i32, _P, _i32, _P, _P, _P, _P])
+_sig("isg_energy", [_P, _P, _i32, _P])
+_sig("isg_result_final", [_P, _P, _P, _P])
+_sig("isg_best", [_P, _P, _P, _P, _P, _P])
+_sig("isg_result_shape", [_P, _P, _P, _P])
+_sig("isg_result_best_all", [_P, _P])
+_sig("isg_result_stats", [_P, ctypes.POINTER(isg_stats)])
+_sig("isg_result_destroy", [_P], None)
+_sig("isg_server_create", [_sz, _i32, _i32, ctypes.POINTER(_P)])
+_sig("isg_server_submit", [_P, _P, _i32, _P, _i32, _u64, _i64, ctypes.POINTER(_u64)])
+_sig("isg_server_poll", [_P, ctypes.POINTER(_u64), ctypes.POINTER(_P), _dbl])
+_sig("isg_server_destroy", [_P])
+_sig("isg_last_error", [], ctypes.c_char_p)
+_sig("isg_version", [], ctypes.c_char_p)
+
+
+class IsgError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"isg status {status}: {message}")
+        self.status = status
+
+
+def _check(st: int):
+    if st != ISG_OK:
+        raise IsgError(st, (_lib.isg_last_error() or b"").decode())
+
+
+def _ptr(a: np.ndarray):
+    return a.ctypes.data_as(_P)
+
+
+def _arr(x, dtype):
+    return np.ascontiguousarray(np.asarray(x), dtype=dtype)
+
+
+def _stream(stream):
+    """Raw cudaStream_t: an int, a torch stream, or None = torch's current stream."""
+    if stream is None:
+        try:
+            import torch
+            if torch.cuda.is_available():
+                return torch.cuda.current_stream().cuda_stream
+        except ImportError:
+            pass
+        return 0
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+def library_path() -> str:
+    return _LIB_PATH
+
+
+def isg_version() -> str:
+    return _lib.isg_version().decode()
+
+
+# ------------------------------------------------------------------ problems
+class Problem:
+    """Owner of an isg_problem handle."""
+
+    def __init__(self, handle: int):
+        self.handle = handle
+        info = isg_problem_info(self)
+        self.n, self.m, self.total_weight, self.n_colors = (info["n"], info["m"],
+                                                            info["total_weight"],
+                                                            info["n_colors"])
+
+    def close(self):
+        if self.handle:
+            _lib.isg_problem_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def _h(x):
+    return x.handle if hasattr(x, "handle") else x
+
+
+def isg_problem_create_edges(n: int, u, v, w) -> Problem:
+    u, v, w = _arr(u, np.int32), _arr(v, np.int32), _arr(w, np.int32)
+    out = _P()
+    _check(_lib.isg_problem_create_edges(n, int(u.shape[0]), _ptr(u), _ptr(v), _ptr(w),
+                                         ctypes.byref(out)))
+    return Problem(out.value)
+
+
+def isg_problem_create_csr(n: int, rowptr, col, w) -> Problem:
+    rowptr, col, w = _arr(rowptr, np.int64), _arr(col, np.int32), _arr(w, np.int32)
+    out = _P()
+    _check(_lib.isg_problem_create_csr(n, _ptr(rowptr), _ptr(col), _ptr(w), ctypes.byref(out)))
+    return Problem(out.value)
+
+
+def isg_problem_create_torus(L: int, W: int, j_right, j_down) -> Problem:
+    jr, jd = _arr(j_right, np.int8), _arr(j_down, np.int8)
+    out = _P()
+    _check(_lib.isg_problem_create_torus(L, W, _ptr(jr), _ptr(jd), ctypes.byref(out)))
+    return Problem(out.value)
+
+
+def isg_problem_info(p, colors: bool = False) -> dict:
+    n, m, tw, nc = _i32(), _i64(), _i64(), _i32()
+    _check(_lib.isg_problem_info(_h(p), ctypes.byref(n), ctypes.byref(m), ctypes.byref(tw),
+                                 ctypes.byref(nc), None))
+    d = {"n": n.value, "m": m.value, "total_weight": tw.value, "n_colors": nc.value}
+    if colors:
+        c = np.zeros(n.value, dtype=np.int32)
+        _check(_lib.isg_problem_info(_h(p), None, None, None, None, _ptr(c)))
+        d["colors"] = c
+    return d
+
+
+def isg_problem_destroy(p):
+    if isinstance(p, Problem):
+        p.close()
+    else:
+        _lib.isg_problem_destroy(p)
+
+
+def problem_of(instance) -> Problem:
+    """libisg instance of a generator object from ``paper_2311_09275_gb300.inputs``."""
+    if hasattr(instance, "L"):
+        return isg_problem_create_torus(instance.L, instance.W, instance.j_right,
+                                        instance.j_down)
+    return isg_problem_create_edges(instance.n, instance.u, instance.v, instance.w)
+
+
+# ------------------------------------------------------------------ results
+class Result:
+    """Owner of an isg_result handle."""
+
+    def __init__(self, handle: int):
+        self.handle = handle
+        n, R, S = _i32(), _i32(), _i32()
+        _check(_lib.isg_result_shape(handle, ctypes.byref(n), ctypes.byref(R), ctypes.byref(S)))
+        self.n, self.replicas, self.sweeps = n.value, R.value, S.value
+
+    def final(self, spins: bool = True):
+        return isg_result_final(self, spins)
+
+    def best(self, spins: bool = True):
+        return isg_best(self, spins)
+
+    def best_all(self):
+        return isg_result_best_all(self)
+
+    def stats(self) -> dict:
+        return isg_result_stats(self)
+
+    def close(self):
+        if self.handle:
+            _lib.isg_result_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def isg_anneal(p, replicas: int, betas, seed: int, target=None, stream=None, kernel: int = 0,
+               cluster_ctas: int = 0, threads: int = 0, time_kernels: bool = False) -> Result:
+    b = _arr(betas, np.float64)
+    opts = isg_options(kernel, cluster_ctas, threads, 1 if time_kernels else 0)
+    out = _P()
+    _check(_lib.isg_anneal_ex(_h(p), int(replicas), _ptr(b), int(b.shape[0]),
+                              int(seed) & 0xFFFFFFFFFFFFFFFF,
+                              ISG_NO_TARGET if target is None else int(target),
+                              ctypes.byref(opts), _stream(stream), ctypes.byref(out)))
+    return Result(out.value)
+
+
+def isg_anneal_batch(problems, replicas: int, betas, seeds, targets=None, stream=None):
+    count = len(problems)
+    hs = (_P * count)(*[_h(p) for p in problems])
+    b = _arr(betas, np.float64)
+    sd = _arr([int(s) & 0xFFFFFFFFFFFFFFFF for s in seeds], np.uint64)
+    tg = None
+    if targets is not None:
+        tg = _arr([ISG_NO_TARGET if t is None else int(t) for t in targets], np.int64)
+    outs = (_P * count)()
+    _check(_lib.isg_anneal_batch(ctypes.cast(hs, _P), count, int(replicas), _ptr(b),
+                                 int(b.shape[0]), _ptr(sd), _ptr(tg) if tg is not None else None,
+                                 _stream(stream), ctypes.cast(outs, _P)))
+    return [Result(outs[k]) for k in range(count)]
+
+
+def isg_energy(p, spins) -> np.ndarray:
+    s = _arr(spins, np.int8)
+    if s.ndim == 1:
+        s = s[None, :]
+    e = np.zeros(s.shape[0], dtype=np.int64)
+    _check(_lib.isg_energy(_h(p), _ptr(s), int(s.shape[0]), _ptr(e)))
+    return e
+
+
+def isg_result_final(r: Result, spins: bool = True):
+    """(spins [R][n] int8 or None, energies [R] int32, sweeps_done)."""
+    sp = np.empty((r.replicas, r.n), dtype=np.int8) if spins else None
+    e = np.empty(r.replicas, dtype=np.int32)
+    done = _i32()
+    _check(_lib.isg_result_final(_h(r), _ptr(sp) if sp is not None else None, _ptr(e),
+                                 ctypes.byref(done)))
+    return sp, e, done.value
+
+
+def isg_best(r: Result, spins: bool = True):
+    """(best energy, best replica, its spins [n] or None, per-replica best [R], hit sweep)."""
+    be, br, hit = _i32(), _i32(), _i32()
+    sp = np.empty(r.n, dtype=np.int8) if spins else None
+    per = np.empty(r.replicas, dtype=np.int32)
+    _check(_lib.isg_best(_h(r), ctypes.byref(be), ctypes.byref(br),
+                         _ptr(sp) if sp is not None else None, _ptr(per), ctypes.byref(hit)))
+    return be.value, br.value, sp, per, hit.value
+
+
+def isg_result_best_all(r: Result) -> np.ndarray:
+    sp = np.empty((r.replicas, r.n), dtype=np.int8)
+    _check(_lib.isg_result_best_all(_h(r), _ptr(sp)))
+    return sp
+
+
+def isg_result_stats(r: Result) -> dict:
+    st = isg_stats()
+    _check(_lib.isg_result_stats(_h(r), ctypes.byref(st)))
+    return {f: getattr(st, f) for f, _ in isg_stats._fields_}
+
+
+def isg_result_destroy(r):
+    if isinstance(r, Result):
+        r.close()
+    else:
+        _lib.isg_result_destroy(r)
+
+
+# ------------------------------------------------------------------ serving
+class Server:
+    """Owner of an isg_server handle (continuous batching on the current device)."""
+
+    def __init__(self, device_mem_budget: int, max_slots: int, sweeps_per_chunk: int):
+        out = _P()
+        _check(_lib.isg_server_create(int(device_mem_budget), int(max_slots),
+                                      int(sweeps_per_chunk), ctypes.byref(out)))
+        self.handle = out.value
+
+    def submit(self, p, replicas: int, betas, seed: int, target=None) -> int:
+        return isg_server_submit(self, p, replicas, betas, seed, target)
+
+    def poll(self, timeout_s: float = 1.0):
+        return isg_server_poll(self, timeout_s)
+
+    def close(self):
+        if self.handle:
+            h, self.handle = self.handle, None
+            _check(_lib.isg_server_destroy(h))
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def isg_server_create(device_mem_budget: int, max_slots: int, sweeps_per_chunk: int) -> Server:
+    return Server(device_mem_budget, max_slots, sweeps_per_chunk)
+
+
+def isg_server_submit(s, p, replicas: int, betas, seed: int, target=None) -> int:
+    b = _arr(betas, np.float64)
+    rid = _u64()
+    _check(_lib.isg_server_submit(_h(s), _h(p), int(replicas), _ptr(b), int(b.shape[0]),
+                                  int(seed) & 0xFFFFFFFFFFFFFFFF,
+                                  ISG_NO_TARGET if target is None else int(target),
+                                  ctypes.byref(rid)))
+    return rid.value
+
+
+def isg_server_poll(s, timeout_s: float = 1.0):
+    """(request id, Result) of a finished request, or None after the timeout."""
+    rid, out = _u64(), _P()
+    st = _lib.isg_server_poll(_h(s), ctypes.byref(rid), ctypes.byref(out), float(timeout_s))
+    if st == ISG_ETIMEOUT:
+        return None
+    _check(st)
+    return rid.value, Result(out.value)
+
+
+def isg_server_destroy(s):
+    if isinstance(s, Server):
+        s.close()
+    else:
+        _check(_lib.isg_server_destroy(s))

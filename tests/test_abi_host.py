@@ -1,0 +1,102 @@
+"""Host-side checks of libisg that need no GPU: the library loads, exports every
+function include/isg.h declares, validates instances, and colours them as the
+oracle's independent greedy colouring does."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2311_09275_gb300 import inputs as I
+from conftest import ROOT
+
+
+@pytest.fixture(scope="module")
+def isg():
+    from paper_2311_09275_gb300 import build
+    build.build()
+    from paper_2311_09275_gb300 import isg as mod
+    return mod
+
+
+def _declared():
+    names = set()
+    for f in os.listdir(os.path.join(ROOT, "include")):
+        if f.endswith(".h"):
+            text = open(os.path.join(ROOT, "include", f)).read()
+            text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+            names |= set(re.findall(r"\b(isg_[a-z_0-9]+)\s*\(", text))
+    return names
+
+
+def test_every_declared_symbol_is_exported(isg):
+    names = _declared()
+    assert len(names) >= 20
+    lib = ctypes.CDLL(isg.library_path())
+    missing = [n for n in sorted(names) if not hasattr(lib, n)]
+    assert not missing, missing
+    assert "sm_103a" in isg.isg_version()
+
+
+def test_torus_validation(isg):
+    j = np.ones(36, np.int8)
+    with pytest.raises(isg.IsgError) as e:
+        isg.isg_problem_create_torus(5, 6, np.ones(30, np.int8), np.ones(30, np.int8))
+    assert e.value.status == isg.ISG_EINVAL and "even" in str(e.value)
+    with pytest.raises(isg.IsgError):
+        isg.isg_problem_create_torus(2, 18, j, j)
+    bad = j.copy()
+    bad[3] = 0
+    with pytest.raises(isg.IsgError):
+        isg.isg_problem_create_torus(6, 6, bad, j)
+    p = isg.isg_problem_create_torus(6, 6, j, j)
+    assert (p.n, p.m, p.total_weight, p.n_colors) == (36, 72, 72, 2)
+
+
+def test_edge_validation(isg):
+    E = isg.IsgError
+    with pytest.raises(E):
+        isg.isg_problem_create_edges(4, [0], [4], [1])        # out of range
+    with pytest.raises(E):
+        isg.isg_problem_create_edges(4, [2], [2], [1])        # self-loop
+    with pytest.raises(E):
+        isg.isg_problem_create_edges(4, [0, 1], [1, 0], [1, 1])  # duplicate pair
+    with pytest.raises(E):
+        isg.isg_problem_create_edges(0, [], [], [])
+    with pytest.raises(E):
+        isg.isg_problem_create_edges(3, [0, 1], [1, 2], [2 ** 29, 2 ** 29])  # |w| sum 2^30
+    p = isg.isg_problem_create_edges(5, [], [], [])          # no edges is fine
+    assert (p.n, p.m, p.n_colors) == (5, 0, 1)
+
+
+def test_csr_validation_and_equivalence(isg):
+    g = I.random_graph(50, 80, 3)
+    c = oracle.csr_of(g)
+    p = isg.isg_problem_create_csr(g.n, c.rowptr, c.col[:2 * g.m], c.wt[:2 * g.m])
+    q = isg.isg_problem_create_edges(g.n, g.u, g.v, g.w)
+    assert isg.isg_problem_info(p, colors=True)["colors"].tolist() == \
+        isg.isg_problem_info(q, colors=True)["colors"].tolist()
+    col = c.col[:2 * g.m].copy()
+    col[0] = (col[0] + 1) % g.n                               # breaks symmetry
+    with pytest.raises(isg.IsgError):
+        isg.isg_problem_create_csr(g.n, c.rowptr, col, c.wt[:2 * g.m])
+
+
+@pytest.mark.parametrize("n,m,seed", [(2000, 1999, 1), (10000, 9999, 1), (3000, 6000, 2)])
+def test_colouring_matches_oracle(isg, n, m, seed):
+    g = I.random_graph(n, m, seed)
+    p = isg.problem_of(g)
+    info = isg.isg_problem_info(p, colors=True)
+    col, nc = oracle.csr_of(g).greedy_colouring()
+    assert info["n_colors"] == nc
+    assert np.array_equal(info["colors"], col)
+    assert info["total_weight"] == int(g.w.sum()) and info["m"] == m
+
+
+def test_torus_colouring_is_checkerboard(isg):
+    t = I.torus(8, 12, 5)
+    info = isg.isg_problem_info(isg.problem_of(t), colors=True)
+    col, nc = oracle.csr_of(t).greedy_colouring()
+    assert info["n_colors"] == 2 and np.array_equal(info["colors"], col)

@@ -1,0 +1,282 @@
+"""GPU path vs the CPU oracle, element by element, on identical seeded inputs.
+
+Spins, energies, best energies, best states, stop sweep and sweep counts are
+integers: the bar is bit-exact equality.  Small cases cover every kernel
+family and launch shape (cluster splits, thread counts, ragged replica
+counts); the full-size cases run exactly the launch configuration the
+benchmark times and compare sampled replicas with the oracle plus
+properties that hold for every replica.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2311_09275_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def isg():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    from paper_2311_09275_gb300 import build
+    build.build()
+    from paper_2311_09275_gb300 import isg as mod
+    return mod
+
+
+def assert_same(res, orc, reps=None, check_done=True):
+    spins, e, done = res.final()
+    best = res.best_all()
+    be, br, bs, per, hit = res.best()
+    rows = list(range(res.replicas)) if reps is None else list(reps)
+    assert np.array_equal(e[rows], orc.e_final), "final energies differ"
+    assert np.array_equal(per[rows], orc.e_best), "best energies differ"
+    assert np.array_equal(spins[rows], orc.s_final), "final spins differ"
+    assert np.array_equal(best[rows], orc.s_best), "best spins differ"
+    if check_done:
+        assert done == orc.sweeps_done
+        assert hit == orc.hit_sweep
+    if reps is None:
+        ob, orr = orc.best
+        assert (be, br) == (ob, orr)
+        assert np.array_equal(bs, orc.s_best[orr])
+
+
+# ------------------------------------------------------------------ torus
+@pytest.mark.parametrize("kernel", [0, 2, 3])
+def test_torus_20x20_all_kernels_bit_exact(isg, kernel):
+    """20x20 torus, 64 replicas, linear beta 0.1 -> 3.0 over 1,000 sweeps."""
+    sv = I.torus_20x20()
+    p = isg.problem_of(sv.problem)
+    c = oracle.csr_of(sv.problem)
+    orc = oracle.anneal(c, sv.replicas, sv.betas, sv.seed, check_energy=True)
+    res = isg.isg_anneal(p, sv.replicas, sv.betas, sv.seed, kernel=kernel)
+    assert_same(res, orc)
+
+
+@pytest.mark.parametrize("L,W,R,cluster,threads", [
+    (4, 4, 1, 1, 32), (8, 6, 5, 2, 32), (8, 6, 33, 4, 64), (8, 10, 70, 8, 32),
+    (12, 10, 64, 4, 128), (6, 20, 37, 2, 64), (16, 14, 96, 0, 0), (10, 4, 31, 1, 64)])
+def test_torus_launch_shapes_bit_exact(isg, L, W, R, cluster, threads):
+    t = I.torus(L, W, 100 + L * W)
+    betas = I.geometric_betas(0.2, 4.0, 80)
+    p = isg.problem_of(t)
+    orc = oracle.anneal(oracle.csr_of(t), R, betas, 77, check_energy=True)
+    res = isg.isg_anneal(p, R, betas, 77, kernel=1, cluster_ctas=cluster, threads=threads)
+    assert_same(res, orc)
+    st = res.stats()
+    if cluster:
+        assert st["cluster_ctas"] == cluster
+
+
+def test_torus_beta_zero_and_huge(isg):
+    t = I.torus(8, 8, 3)
+    c = oracle.csr_of(t)
+    p = isg.problem_of(t)
+    for betas in (np.zeros(3), np.full(5, 1e3), np.array([0.0, 50.0, 0.0, 0.5])):
+        orc = oracle.anneal(c, 40, betas, 5)
+        assert_same(isg.isg_anneal(p, 40, betas, 5), orc)
+
+
+# ------------------------------------------------------------------ graphs
+GRAPHS = {
+    "random_sparse": lambda: I.random_graph(500, 700, 4),
+    "random_dense": lambda: I.random_graph(300, 2400, 5),
+    "isolated": lambda: I.random_graph(60, 12, 6),
+}
+
+
+def weighted_graph():
+    g = I.random_graph(300, 900, 7)
+    w = np.array([(-2, -1, 1, 2, 3)[k % 5] for k in range(g.m)], np.int32)
+    return I.Graph(g.n, g.u, g.v, w)
+
+
+@pytest.mark.parametrize("name", list(GRAPHS) + ["weighted"])
+@pytest.mark.parametrize("R,cluster", [(1, 1), (12, 2), (37, 4), (8, 0)])
+def test_graph_csr_bit_exact(isg, name, R, cluster):
+    g = weighted_graph() if name == "weighted" else GRAPHS[name]()
+    betas = I.geometric_betas(0.1, 5.0, 120)
+    orc = oracle.anneal(oracle.csr_of(g), R, betas, 31, check_energy=True)
+    res = isg.isg_anneal(isg.problem_of(g), R, betas, 31, kernel=2, cluster_ctas=cluster)
+    assert_same(res, orc)
+
+
+def test_graph_plain_kernel_bit_exact(isg):
+    g = weighted_graph()
+    betas = I.linear_betas(0.1, 3.0, 60)
+    orc = oracle.anneal(oracle.csr_of(g), 10, betas, 8)
+    assert_same(isg.isg_anneal(isg.problem_of(g), 10, betas, 8, kernel=3), orc)
+
+
+def test_single_vertex_and_edgeless(isg):
+    g = I.Graph(1, np.zeros(0, np.int32), np.zeros(0, np.int32), np.zeros(0, np.int32))
+    orc = oracle.anneal(oracle.csr_of(g), 6, np.full(4, 1.0), 2)
+    assert_same(isg.isg_anneal(isg.problem_of(g), 6, np.full(4, 1.0), 2), orc)
+
+
+def test_torus_via_csr_equals_msc(isg):
+    """The same torus given as an edge list (CSR kernel, greedy colouring)
+    matches the multi-spin-coded torus kernel bit for bit."""
+    t = I.torus(10, 12, 9)
+    betas = I.geometric_betas(0.1, 5.0, 200)
+    a = isg.isg_anneal(isg.problem_of(t), 40, betas, 3)
+    u, v, w = t.edges()
+    b = isg.isg_anneal(isg.isg_problem_create_edges(t.n, u, v, w), 40, betas, 3)
+    for x, y in zip(a.final(), b.final()):
+        assert np.array_equal(x, y)
+    assert np.array_equal(a.best_all(), b.best_all())
+
+
+# ------------------------------------------------------------------ targets
+@pytest.mark.parametrize("kind,R,kernel", [("torus", 20, 1), ("torus", 70, 1), ("torus", 70, 3),
+                                           ("graph", 3, 2), ("graph", 12, 2), ("graph", 12, 3)])
+def test_target_stop_bit_exact(isg, kind, R, kernel):
+    prob = I.torus(12, 10, 4) if kind == "torus" else I.random_graph(400, 800, 2)
+    betas = I.geometric_betas(0.1, 5.0, 300)
+    c = oracle.csr_of(prob)
+    full = oracle.anneal(c, R, betas, 9)
+    target = int(full.e_best.min()) + 4
+    orc = oracle.anneal(c, R, betas, 9, target=target)
+    assert orc.hit_sweep >= 0
+    res = isg.isg_anneal(isg.problem_of(prob), R, betas, 9, target=target, kernel=kernel)
+    assert_same(res, orc)
+    unreachable = oracle.anneal(c, R, betas, 9, target=-10 ** 6)
+    res2 = isg.isg_anneal(isg.problem_of(prob), R, betas, 9, target=-10 ** 6, kernel=kernel)
+    assert_same(res2, unreachable)
+
+
+# ------------------------------------------------------------------ energy
+def test_isg_energy_matches_oracle(isg):
+    g = weighted_graph()
+    c = oracle.csr_of(g)
+    rng = np.random.default_rng(0)
+    s = rng.choice(np.array([-1, 1], np.int8), size=(17, g.n))
+    e = isg.isg_energy(isg.problem_of(g), s)
+    assert e.tolist() == [c.energy(x) for x in s]
+
+
+# ------------------------------------------------------------------ batched
+def test_batch_matches_single_and_oracle(isg):
+    L, W = I.batch_sizes(24, seed=4)
+    L, W = L // 4 * 2, W // 4 * 2   # smaller even sides, 8..70
+    L, W = np.maximum(L, 4), np.maximum(W, 4)
+    tori = [I.torus(int(L[k]), int(W[k]), 1000 + k) for k in range(24)]
+    probs = [isg.problem_of(t) for t in tori]
+    betas = I.geometric_betas(0.1, 5.0, 150)
+    seeds = [k + 1 for k in range(24)]
+    for R in (32, 20):
+        outs = isg.isg_anneal_batch(probs, R, betas, seeds)
+        for k in range(24):
+            single = isg.isg_anneal(probs[k], R, betas, seeds[k])
+            for x, y in zip(outs[k].final(), single.final()):
+                assert np.array_equal(x, y)
+            assert np.array_equal(outs[k].best_all(), single.best_all())
+        for k in (0, 7, 23):
+            orc = oracle.anneal(oracle.csr_of(tori[k]), R, betas, seeds[k])
+            assert_same(outs[k], orc)
+
+
+def test_batch_with_targets(isg):
+    tori = [I.torus(8 + 2 * k, 10, 50 + k) for k in range(6)]
+    probs = [isg.problem_of(t) for t in tori]
+    betas = I.geometric_betas(0.1, 5.0, 200)
+    seeds = [3 + k for k in range(6)]
+    targets = []
+    for k, t in enumerate(tori):
+        full = oracle.anneal(oracle.csr_of(t), 32, betas, seeds[k])
+        targets.append(int(full.e_best.min()) + 2 if k % 2 == 0 else None)
+    outs = isg.isg_anneal_batch(probs, 32, betas, seeds, targets)
+    for k, t in enumerate(tori):
+        orc = oracle.anneal(oracle.csr_of(t), 32, betas, seeds[k], target=targets[k])
+        assert_same(outs[k], orc)
+
+
+# ------------------------------------------------------------------ served
+def test_server_results_equal_solo_runs(isg):
+    """Requests of different kinds and sizes, submitted together so that they
+    share chunks, each equal isg_anneal of the same request alone."""
+    betas = I.geometric_betas(0.1, 5.0, 240)
+    reqs = []
+    for k in range(10):
+        prob = I.torus(8 + 4 * (k % 3), 12, 70 + k) if k % 2 == 0 else \
+            I.random_graph(300 + 50 * k, 450 + 80 * k, 70 + k)
+        reqs.append((isg.problem_of(prob), prob, 32 if k % 3 else 20, 11 + k))
+    targets = []
+    for p, prob, R, seed in reqs:
+        full = isg.isg_anneal(p, R, betas, seed)
+        targets.append(full.best(spins=False)[0] + 2)
+    srv = isg.Server(1 << 30, 4, 37)
+    ids = {}
+    for k, (p, prob, R, seed) in enumerate(reqs):
+        ids[srv.submit(p, R, betas, seed, targets[k])] = k
+    got = {}
+    while len(got) < len(reqs):
+        out = srv.poll(30.0)
+        assert out is not None, "server timed out"
+        got[ids[out[0]]] = out[1]
+    srv.close()
+    for k, (p, prob, R, seed) in enumerate(reqs):
+        solo = isg.isg_anneal(p, R, betas, seed, target=targets[k])
+        a, b = got[k], solo
+        for x, y in zip(a.final(), b.final()):
+            assert np.array_equal(x, y)
+        assert np.array_equal(a.best_all(), b.best_all())
+        assert a.best(spins=False)[4] == b.best(spins=False)[4] >= 0
+    k = 1
+    orc = oracle.anneal(oracle.csr_of(reqs[k][1]), reqs[k][2], betas, reqs[k][3], target=targets[k])
+    assert_same(got[k], orc)
+
+
+# ------------------------------------------------------------------ full sizes
+@pytest.mark.slow
+def test_torus_80x100_full_size_sampled(isg):
+    """The benchmark's workload and launch shape: 80x100 torus, 1,024
+    replicas, 10,000 geometric sweeps.  Sampled replicas (first and last of
+    several words) against the oracle; every replica's tracked energies
+    against a full recompute."""
+    sv = I.torus_80x100()
+    p = isg.problem_of(sv.problem)
+    res = isg.isg_anneal(p, sv.replicas, sv.betas, sv.seed)
+    reps = [0, 1, 31, 32, 517, 1023]
+    orc = oracle.anneal(oracle.csr_of(sv.problem), reps, sv.betas, sv.seed)
+    assert_same(res, orc, reps=reps)
+    spins, e, done = res.final()
+    assert done == sv.sweeps
+    assert np.array_equal(isg.isg_energy(p, spins), e)
+    assert np.array_equal(isg.isg_energy(p, res.best_all()), res.best(spins=False)[3])
+
+
+@pytest.mark.slow
+def test_random_10000_full_size_sampled(isg):
+    sv = I.random_10000()
+    p = isg.problem_of(sv.problem)
+    res = isg.isg_anneal(p, sv.replicas, sv.betas, sv.seed)
+    reps = [0, 1, 2, 3, 130, 255]
+    orc = oracle.anneal(oracle.csr_of(sv.problem), reps, sv.betas, sv.seed)
+    assert_same(res, orc, reps=reps)
+    spins, e, _ = res.final()
+    assert np.array_equal(isg.isg_energy(p, spins), e)
+
+
+@pytest.mark.slow
+def test_batch_512_full_size_sampled(isg):
+    """512 uneven tori, 32 replicas, 2,000 sweeps in one persistent kernel:
+    sampled instances equal their one-instance-per-launch plain runs, and one
+    equals the oracle."""
+    batch = I.torus_batch()
+    probs = [isg.problem_of(sv.problem) for sv in batch]
+    outs = isg.isg_anneal_batch(probs, 32, batch[0].betas, [sv.seed for sv in batch])
+    sizes = [sv.n for sv in batch]
+    picks = [int(np.argmax(sizes)), int(np.argmin(sizes)), 100, 311]
+    for k in picks:
+        sv = batch[k]
+        plain = isg.isg_anneal(probs[k], 32, sv.betas, sv.seed, kernel=3)
+        for x, y in zip(outs[k].final(), plain.final()):
+            assert np.array_equal(x, y)
+        assert np.array_equal(outs[k].best_all(), plain.best_all())
+    k = 100
+    orc = oracle.anneal(oracle.csr_of(batch[k].problem), 32, batch[k].betas, batch[k].seed)
+    assert_same(outs[k], orc)
