@@ -42,12 +42,42 @@ from paper_2311_09275_gb300 import inputs as I  # noqa: E402
 
 METRIC = "spin-flip attempts/s"
 UNIT = "attempts/s"
-# Integer instructions one attempt needs by the algorithm: a quarter of a
-# Philox4x32-10 block (10 rounds x (2 wide multiplies + 2 three-input XORs)
-# = 40 per 4 uniforms) plus one threshold compare.
-ALGO_OPS_PER_ATTEMPT = 40 / 4 + 1
+# Integer-ALU instructions one attempt needs by the algorithm: a quarter of
+# the 20 three-input XORs of a Philox4x32-10 block (10 rounds x 2) plus one
+# threshold compare.  The block's 20 wide multiplies run on the multiply-add
+# pipe, which is not the limiter.  The ALU pipe accepts half a warp
+# instruction per cycle per scheduler (16 lanes), as ncu's pipe-utilisation
+# counters of this kernel show (ALU-pipe % of peak vs issue rate).
+ALGO_ALU_OPS_PER_ATTEMPT = 20 / 4 + 1
 SMSP_PER_SM = 4
-LANES = 32
+ALU_LANES_PER_SMSP = 16
+
+
+def profiled_traffic(workload_name: str):
+    """DRAM bytes per launch of the sweep kernel from the committed ncu summary,
+    or None when the summary does not cover this workload or the kernel source
+    changed since the counters were taken."""
+    import hashlib
+    if not workload_name.startswith("torus_80x100_R1024_S10000"):
+        return None
+    path = os.path.join(ROOT, "profiles", "torus_kernel_80x100_R1024.md")
+    src = os.path.join(ROOT, "paper_2311_09275_gb300", "csrc", "torus_msc.cu")
+    if not os.path.exists(path):
+        return None
+    fields = {}
+    with open(path) as f:
+        for line in f:
+            if ":" in line and not line.startswith(("|", "#", " ")):
+                k, v = line.split(":", 1)
+                fields[k.strip()] = v.strip()
+    with open(src, "rb") as f:
+        sha = hashlib.sha256(f.read()).hexdigest()[:16]
+    if fields.get("kernel_source_sha256_16") != sha:
+        return None
+    try:
+        return int(fields["traffic_bytes_per_launch"])
+    except (KeyError, ValueError):
+        return None
 
 
 def load_peaks():
@@ -245,10 +275,19 @@ def run_gpu(args):
     p = isg.problem_of(sv.problem)
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.int32, device=device)  # 512 MB > L2
 
+    shape = {}
+    if args.launch:
+        c, t = (int(x) for x in args.launch.split(","))
+        shape = {"cluster_ctas": c, "threads": t}
+
     def step(time_kernels=True):
         return isg.isg_anneal(p, sv.replicas, sv.betas, sv.seed, stream=stream,
-                              time_kernels=time_kernels)
+                              time_kernels=time_kernels, **shape)
 
+    # launch-shape autotuning (untimed, part of warm-up); results never depend on it
+    tuned = None
+    if not args.no_tune and not args.launch:
+        tuned = isg.isg_autotune(p, sv.replicas, 64, stream=stream)
     for _ in range(args.warmup):
         r = step()
         r.final(spins=False)
@@ -312,14 +351,10 @@ def run_gpu(args):
     peaks, peak_src = load_peaks()
     props = torch.cuda.get_device_properties(device)
     sm_max = float(peaks.get("sm_max_mhz", 2070.0))
-    issue_peak = props.multi_processor_count * SMSP_PER_SM * LANES * sm_max * 1e6
+    alu_peak = props.multi_processor_count * SMSP_PER_SM * ALU_LANES_PER_SMSP * sm_max * 1e6
     k_ms = statistics.mean(kernel_ms)
-    achieved = ALGO_OPS_PER_ATTEMPT * float(sv.attempts) / (k_ms / 1e3)
-    traffic = None
-    tpath = os.path.join(ROOT, "profiles", "traffic.json")
-    if os.path.exists(tpath):
-        with open(tpath) as f:
-            traffic = json.load(f).get(name)
+    achieved = ALGO_ALU_OPS_PER_ATTEMPT * float(sv.attempts) / (k_ms / 1e3)
+    traffic = profiled_traffic(name)
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -330,16 +365,19 @@ def run_gpu(args):
                    "sweeps": sv.sweeps, "attempts_per_step": sv.attempts,
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
                    "l2": "flushed (512 MB write) before every timed step",
-                   "launch": {k: stats[k] for k in ("kernel", "ctas", "cluster_ctas", "threads")}},
+                   "launch": {k: stats[k] for k in ("kernel", "ctas", "cluster_ctas", "threads")},
+                   "autotuned": tuned is not None},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                 "d2h_bytes_per_step": int(d2h), "steps": e2e_steps},
         "gpu_launches": launches,
-        "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": issue_peak / 1e12,
-                     "unit": "Tops/s", "frac": achieved / issue_peak, "traffic": traffic,
+        "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": alu_peak / 1e12,
+                     "unit": "Tops/s", "frac": achieved / alu_peak, "traffic": traffic,
                      "kernel": "torus_kernel" if hasattr(sv.problem, "L") else "csr_kernel",
                      "kernel_ms": k_ms,
-                     "peak_source": f"{props.multi_processor_count} SMs x {SMSP_PER_SM} x "
-                                    f"{LANES} lanes x {sm_max:.0f} MHz ({peak_src} clock)"},
+                     "algorithmic_ops_per_attempt": ALGO_ALU_OPS_PER_ATTEMPT,
+                     "peak_source": f"{props.multi_processor_count} SMs x {SMSP_PER_SM} schedulers x "
+                                    f"{ALU_LANES_PER_SMSP} ALU lanes x {sm_max:.0f} MHz "
+                                    f"({peak_src} max clock)"},
         "clocks": clocks.summary(),
         "wall_s": wall,
     }
@@ -357,6 +395,9 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--config", default="torus", choices=["torus", "random"])
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--no-tune", action="store_true", help="skip the launch-shape autotuner")
+    ap.add_argument("--launch", default=None,
+                    help="explicit launch shape CLUSTER,THREADS (skips the autotuner)")
     ap.add_argument("--sweeps", type=int, default=None,
                     help="shorter schedule for profiling captures (default: the full workload)")
     args = ap.parse_args()

@@ -115,8 +115,8 @@ typedef enum {
 
 typedef struct {
     int32_t kernel;        /* isg_kernel */
-    int32_t cluster_ctas;  /* CTAs that share one replica block; 0 = autotuned */
-    int32_t threads;       /* threads per CTA; 0 = autotuned */
+    int32_t cluster_ctas;  /* CTAs that share one replica block (1..16); 0 = tuned/default */
+    int32_t threads;       /* threads per CTA (multiple of 32, <= 512); 0 = tuned/default */
     int32_t time_kernels;  /* nonzero: time the sweep launches with CUDA events */
 } isg_options;
 
@@ -130,6 +130,15 @@ typedef struct {
  * large for the chosen kernel; ECUDA: no device or a launch failed. */
 isg_status isg_anneal(const isg_problem *p, int32_t replicas, const double *betas, int32_t sweeps,
                       uint64_t seed, int64_t target_energy, void *cuda_stream, isg_result **out);
+
+/* Launch-shape autotuner.  Times the sweep kernel of this instance and
+ * replica count under every admissible shape (CTAs per replica block, threads
+ * per CTA) for probe_sweeps sweeps on the current device, writes the fastest
+ * into *best (may be NULL) and remembers it, so that later solves of the same
+ * (instance shape, replicas) with cluster_ctas = threads = 0 use it.  Results
+ * never depend on the shape.  Synchronises the stream.  probe_sweeps >= 1. */
+isg_status isg_autotune(const isg_problem *p, int32_t replicas, int32_t probe_sweeps,
+                        void *cuda_stream, isg_options *best);
 
 /* isg_anneal with explicit kernel options (opts may be NULL = defaults). */
 isg_status isg_anneal_ex(const isg_problem *p, int32_t replicas, const double *betas,

@@ -142,6 +142,7 @@ extern "C" isg_status isg_anneal_batch(const isg_problem *const *probs, int32_t 
     s.table = d_table;
     s.key0 = (uint32_t)(seeds[k] & 0xFFFFFFFFu);
     s.key1 = (uint32_t)(seeds[k] >> 32);
+    s.rk = round_keys(s.key0, s.key1);
     s.words = 1;
     s.replicas = replicas;
     s.spins = r->d_spins;

@@ -6,6 +6,8 @@
 #include <cooperative_groups.h>
 #include <cstdint>
 
+#include "isg_kernels.h"
+
 namespace isg {
 
 namespace cg = cooperative_groups;
@@ -37,6 +39,59 @@ __device__ __forceinline__ uint4 philox10(uint4 c, PhiloxKey key) {
     c = make_uint4(hiB ^ c.y ^ k0, loB, hiA ^ c.w ^ k1, loA);
     k0 += kWeylA;
     k1 += kWeylB;
+  }
+  return c;
+}
+
+// ---------------------------------------------------------------------------
+// Sweep uniforms with rounds 1-2 factored.  For the counter (i, t, b, 0) of
+// site i, sweep t and replica block b, round 1 multiplies counter word 0 (=i)
+// and word 2 (=b); round 2 multiplies round 1's words 0 and 2.  Round 1's
+// word 0 and 1 depend only on (b, t) and its words 2 and 3 only on i, so:
+//   after round 2:  ( hi(B*Y2) ^ A_b,  lo(B*Y2),  P_b ^ Y3,  C_b )
+// with, per site,  Y2 = hi(A*i) ^ k1[0],  Y3 = lo(A*i),
+// and, per (b, t), X0 = hi(B*b) ^ t ^ k0[0],  A_b = lo(B*b) ^ k0[1],
+//                  P_b = hi(A*X0) ^ k1[1],   C_b = lo(A*X0),
+// where A, B are the two round multipliers.  Rounds 3..10 then run in full.
+// The result equals philox10((i, t, b, 0), key) exactly.
+constexpr uint32_t kPhiloxMulA = 0xD2511F53u;
+constexpr uint32_t kPhiloxMulB = 0xCD9E8D57u;
+
+struct BlockPrefix {
+  uint32_t a, p, c;  // A_b, P_b, C_b of the factorisation above
+};
+
+__device__ __forceinline__ BlockPrefix block_prefix(uint32_t b, uint32_t t, const RoundKeys &k) {
+  const uint32_t x0 = __umulhi(kPhiloxMulB, b) ^ t ^ k.k0[0];
+  BlockPrefix r;
+  r.a = (kPhiloxMulB * b) ^ k.k0[1];
+  r.p = __umulhi(kPhiloxMulA, x0) ^ k.k1[1];
+  r.c = kPhiloxMulA * x0;
+  return r;
+}
+
+struct SitePrefix {
+  uint32_t hb, lb, y3;  // hi(B*Y2), lo(B*Y2), Y3
+};
+
+__device__ __forceinline__ SitePrefix site_prefix(uint32_t i, const RoundKeys &k) {
+  const uint32_t y2 = __umulhi(kPhiloxMulA, i) ^ k.k1[0];
+  SitePrefix r;
+  r.y3 = kPhiloxMulA * i;
+  r.hb = __umulhi(kPhiloxMulB, y2);
+  r.lb = kPhiloxMulB * y2;
+  return r;
+}
+
+// Philox4x32-10 of counter (i, t, b, 0) from its two prefixes.
+__device__ __forceinline__ uint4 philox10_factored(const SitePrefix &sp, const BlockPrefix &bp,
+                                                   const RoundKeys &k) {
+  uint4 c = make_uint4(sp.hb ^ bp.a, sp.lb, bp.p ^ sp.y3, bp.c);
+#pragma unroll
+  for (int round = 2; round < 10; ++round) {
+    const uint32_t hiA = __umulhi(kPhiloxMulA, c.x), loA = kPhiloxMulA * c.x;
+    const uint32_t hiB = __umulhi(kPhiloxMulB, c.z), loB = kPhiloxMulB * c.z;
+    c = make_uint4(hiB ^ c.y ^ k.k0[round], loB, hiA ^ c.w ^ k.k1[round], loA);
   }
   return c;
 }

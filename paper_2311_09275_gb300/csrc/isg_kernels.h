@@ -8,6 +8,21 @@
 
 namespace isg {
 
+// The ten Philox4x32-10 round keys of a seed: the key words advanced by the
+// two Weyl increments before every round after the first.
+struct RoundKeys {
+  uint32_t k0[10], k1[10];
+};
+
+__host__ __device__ inline RoundKeys round_keys(uint32_t key0, uint32_t key1) {
+  RoundKeys r;
+  for (int i = 0; i < 10; ++i) {
+    r.k0[i] = key0 + (uint32_t)i * 0x9E3779B9u;
+    r.k1[i] = key1 + (uint32_t)i * 0xBB67AE85u;
+  }
+  return r;
+}
+
 // ---------------------------------------------------------------- torus, multi-spin coded
 // One replica word = 32 replicas packed bitwise (bit l of a word is replica
 // 32*word + l; bit 1 means spin +1).  State arrays are [word][L*W].
@@ -16,6 +31,7 @@ struct TorusSolve {
   const uint8_t *cbits;      // [L*W] bit0: j_right == -1, bit1: j_down == -1
   const uint32_t *table;     // [sweeps][2]: thresholds for energy changes 4 and 8
   uint32_t key0, key1;       // Philox key (seed)
+  RoundKeys rk;              // round_keys(key0, key1)
   int32_t words;             // replica words of this solve
   int32_t replicas;          // R (lanes >= R of the last word are padding)
   uint32_t *spins;           // [words][L*W] state in/out
@@ -41,6 +57,9 @@ size_t torus_smem_bytes(int32_t L, int32_t W, int32_t cluster);
 // Largest number of sites a thread updates per sweep under this launch shape.
 int32_t torus_sites_per_thread(int32_t L, int32_t W, int32_t cluster, int32_t threads);
 cudaError_t torus_launch(const TorusSolve &s, const TorusLaunch &l, cudaStream_t stream);
+// Clusters of this shape the device can hold at once (0: the shape cannot launch).
+int torus_max_active_clusters(int32_t L, int32_t W, int32_t words, int32_t cluster,
+                              int32_t threads);
 
 // Work units of the persistent kernels: one replica word of one torus, run by
 // one CTA over sweeps [t_begin, t_end).  Used by the batched and served forms.

@@ -5,7 +5,9 @@
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <array>
 #include <cstring>
+#include <map>
 #include <mutex>
 #include <numeric>
 #include <string>
@@ -357,9 +359,9 @@ int sm_count() {
 
 int round_up(int x, int m) { return (x + m - 1) / m * m; }
 
-// Torus kernel shape: the smallest power-of-two cluster that puts at least
-// ~0.8 x SMs CTAs on the device (bands of >= 2 rows), then enough threads for
-// ~4 sites per thread per colour phase.
+// Torus kernel shape without measurements: the smallest power-of-two cluster
+// that puts at least ~0.8 x SMs CTAs on the device (bands of >= 2 rows), then
+// enough threads for ~4 sites per thread per colour phase.
 void torus_shape(int L, int W, int words, int &cluster, int &threads) {
   const int sms = sm_count();
   if (cluster <= 0) {
@@ -373,20 +375,163 @@ void torus_shape(int L, int W, int words, int &cluster, int &threads) {
   }
 }
 
-void csr_shape(int n, int quads, int max_class, int &cluster, int &threads, int &qpc) {
+void csr_shape(int quads, int max_class, int &cluster, int &threads) {
   const int sms = sm_count();
-  if (qpc <= 0) qpc = 1;
   if (cluster <= 0) {
-    const int groups = (quads + qpc - 1) / qpc;
     cluster = 1;
-    while (cluster < 8 && groups * cluster < (sms * 4) / 5) cluster *= 2;
+    while (cluster < 8 && quads * cluster < (sms * 4) / 5) cluster *= 2;
   }
   if (threads <= 0) {
     const int per_phase = (max_class + cluster - 1) / cluster;
     threads = std::min(512, std::max(64, round_up((per_phase + 2) / 3, 32)));
   }
-  (void)n;
 }
+
+namespace {
+
+// Measured shapes: (device, torus?, L or n, W or nnz, units) -> (cluster, threads)
+std::mutex g_shape_mu;
+std::map<std::array<int64_t, 5>, std::pair<int, int>> g_shapes;
+
+std::array<int64_t, 5> shape_key(const isg_problem *p, int units) {
+  int dev = 0;
+  cudaGetDevice(&dev);
+  return {dev, p->torus ? 1 : 0, p->torus ? p->L : p->n, p->torus ? p->W : p->rowptr[p->n], units};
+}
+
+bool shape_lookup(const isg_problem *p, int units, int &cluster, int &threads) {
+  std::lock_guard<std::mutex> lock(g_shape_mu);
+  auto it = g_shapes.find(shape_key(p, units));
+  if (it == g_shapes.end()) return false;
+  cluster = it->second.first;
+  threads = it->second.second;
+  return true;
+}
+
+int max_class_size(const isg_problem *p) {
+  int m = 0;
+  for (int32_t c = 0; c < p->n_colours; ++c)
+    m = std::max(m, p->class_start[c + 1] - p->class_start[c]);
+  return m;
+}
+
+TorusSolve make_torus_solve(const isg_problem *p, const DeviceProblem *dp, const isg_result *r,
+                            uint64_t seed, bool has_target, int64_t target) {
+  TorusSolve s = {};
+  s.L = p->L;
+  s.W = p->W;
+  s.cbits = dp->cbits;
+  s.table = r->d_table;
+  s.key0 = (uint32_t)(seed & 0xFFFFFFFFu);
+  s.key1 = (uint32_t)(seed >> 32);
+  s.rk = round_keys(s.key0, s.key1);
+  s.words = r->units;
+  s.replicas = r->R;
+  s.spins = r->d_spins;
+  s.best = r->d_best;
+  s.e_cur = r->d_e_cur;
+  s.e_best = r->d_e_best;
+  s.hit = r->d_hit;
+  s.done = r->d_done;
+  s.has_target = has_target;
+  s.target = has_target ? (int32_t)target : 0;
+  return s;
+}
+
+CsrSolve make_csr_solve(const isg_problem *p, const DeviceProblem *dp, const isg_result *r,
+                        uint64_t seed, bool has_target, int64_t target) {
+  CsrSolve s = {};
+  s.n = p->n;
+  s.n_colours = p->n_colours;
+  s.class_start = dp->class_start;
+  s.rowptr = dp->rowptr;
+  s.col = dp->col;
+  s.wt = dp->wt;
+  s.orig = dp->orig;
+  s.kmax = p->kmax;
+  s.table = r->d_table;
+  s.key0 = (uint32_t)(seed & 0xFFFFFFFFu);
+  s.key1 = (uint32_t)(seed >> 32);
+  s.quads = r->units;
+  s.replicas = r->R;
+  s.spins = r->d_spins;
+  s.best = r->d_best;
+  s.e_cur = r->d_e_cur;
+  s.e_best = r->d_e_best;
+  s.hit = r->d_hit;
+  s.done = r->d_done;
+  s.has_target = has_target;
+  s.target = has_target ? (int32_t)target : 0;
+  return s;
+}
+
+// Enqueue the sweeps [0, S) of a prepared result under the given shape:
+// one persistent launch, or one launch per sweep (plain); with a target and
+// several independently scheduled units, a second pass replays every unit to
+// the earliest unit's stop sweep.
+cudaError_t launch_sweeps(const isg_problem *p, const DeviceProblem *dp, isg_result *r,
+                          uint64_t seed, bool has_target, int64_t target, bool plain, int cluster,
+                          int threads, int S, cudaStream_t stream, int &launches) {
+  cudaError_t err = cudaSuccess;
+  const int passes = (has_target && r->units > 1) ? 2 : 1;
+  for (int pass = 0; pass < passes && err == cudaSuccess; ++pass) {
+    const int first = plain ? 0 : -1;
+    for (int t = first; t < (plain ? S : 0) && err == cudaSuccess; ++t) {
+      const int t0 = plain ? t : 0, t1 = plain ? t + 1 : S;
+      if (r->msc) {
+        TorusSolve s = make_torus_solve(p, dp, r, seed, has_target && pass == 0, target);
+        TorusLaunch l = {};
+        l.t_begin = t0;
+        l.t_end = t1;
+        l.resume = t0 > 0;
+        l.stop_from_hits = pass == 1;
+        l.cluster = cluster;
+        l.threads = threads;
+        err = torus_launch(s, l, stream);
+      } else {
+        CsrSolve s = make_csr_solve(p, dp, r, seed, has_target && pass == 0, target);
+        CsrLaunch l = {};
+        l.t_begin = t0;
+        l.t_end = t1;
+        l.resume = t0 > 0;
+        l.stop_from_hits = pass == 1;
+        l.cluster = cluster;
+        l.threads = threads;
+        l.quads_per_cta = 1;
+        err = csr_launch(s, l, stream);
+      }
+      ++launches;
+      if (!plain) break;
+    }
+  }
+  return err;
+}
+
+isg_result *new_result(const isg_problem *p, int32_t R, int32_t S, bool msc, bool has_target,
+                       cudaStream_t stream) {
+  isg_result *r = new isg_result();
+  cudaGetDevice(&r->device);
+  r->stream = stream;
+  r->n = p->n;
+  r->R = R;
+  r->S = S;
+  r->has_target = has_target;
+  r->msc = msc;
+  r->units = msc ? (R + 31) / 32 : (R + 3) / 4;
+  r->lanes = msc ? 32 : 4;
+  return r;
+}
+
+void table_levels(const isg_problem *p, bool msc, std::vector<int32_t> &levels) {
+  levels.clear();
+  if (msc) {
+    levels = {2, 4};
+  } else {
+    for (int32_t k = 0; k <= p->kmax; ++k) levels.push_back(k);
+  }
+}
+
+}  // namespace
 
 // ------------------------------------------------------------------ anneal
 
@@ -402,39 +547,44 @@ isg_status anneal_impl(const isg_problem *p, int32_t R, const double *betas, int
   if (opts) o = *opts;
   int kernel = o.kernel;
   if (kernel == ISG_KERNEL_AUTO) kernel = p->torus ? ISG_KERNEL_TORUS_MSC : ISG_KERNEL_CSR;
+  if (kernel < ISG_KERNEL_AUTO || kernel > ISG_KERNEL_PLAIN)
+    return fail(ISG_EINVAL, "unknown kernel %d", kernel);
   if (kernel == ISG_KERNEL_TORUS_MSC && !p->torus)
     return fail(ISG_EINVAL, "the multi-spin-coded kernel needs a torus instance");
   const bool plain = kernel == ISG_KERNEL_PLAIN;
   const bool msc = p->torus && (kernel == ISG_KERNEL_TORUS_MSC || plain);
-  if (o.cluster_ctas < 0 || o.cluster_ctas > 8)
-    return fail(ISG_EINVAL, "cluster_ctas must be in [0, 8]");
+  if (o.cluster_ctas < 0 || o.cluster_ctas > 16)
+    return fail(ISG_EINVAL, "cluster_ctas must be in [0, 16]");
   if (o.threads != 0 && (o.threads < 32 || o.threads > 512 || o.threads % 32))
     return fail(ISG_EINVAL, "threads must be a multiple of 32 in [32, 512]");
   const bool has_target = target != ISG_NO_TARGET;
   if (has_target && (target < INT32_MIN || target > INT32_MAX))
     return fail(ISG_EINVAL, "target energy outside the int32 range");
 
+  // launch shape: explicit, else measured (isg_autotune), else the default rule
+  const int units = msc ? (R + 31) / 32 : (R + 3) / 4;
+  int cluster = plain ? 1 : o.cluster_ctas, threads = o.threads;
+  if (!plain && cluster == 0 && threads == 0) shape_lookup(p, units, cluster, threads);
+  if (msc) {
+    torus_shape(p->L, p->W, units, cluster, threads);
+    if (cluster > p->L) cluster = p->L;
+    if (torus_smem_bytes(p->L, p->W, cluster) > 227 * 1024)
+      return fail(ISG_EINVAL, "torus %dx%d needs more shared memory than a CTA has", p->L, p->W);
+  } else {
+    csr_shape(units, max_class_size(p), cluster, threads);
+    if (csr_smem_bytes(p->n, 1, cluster) > 227 * 1024)
+      return fail(ISG_EINVAL, "instance with n = %d needs more shared memory than a CTA has",
+                  p->n);
+  }
+
   const DeviceProblem *dp = nullptr;
   st = problem_device(p, msc ? kNeedTorus : kNeedCsr, &dp);
   if (st != ISG_OK) return st;
 
-  isg_result *r = new isg_result();
-  ISG_CUDA(cudaGetDevice(&r->device));
-  r->stream = stream;
-  r->n = p->n;
-  r->R = R;
-  r->S = S;
-  r->has_target = has_target;
+  isg_result *r = new_result(p, R, S, msc, has_target, stream);
   r->kernel = plain ? ISG_KERNEL_PLAIN : (msc ? ISG_KERNEL_TORUS_MSC : ISG_KERNEL_CSR);
-  r->msc = msc;
-  r->units = msc ? (R + 31) / 32 : (R + 3) / 4;
-  r->lanes = msc ? 32 : 4;
   std::vector<int32_t> levels;
-  if (msc) {
-    levels = {2, 4};
-  } else {
-    for (int32_t k = 0; k <= p->kmax; ++k) levels.push_back(k);
-  }
+  table_levels(p, msc, levels);
   std::vector<uint32_t> table;
   build_table(betas, S, levels, table);
   r->table_words = table.size();
@@ -458,129 +608,16 @@ isg_status anneal_impl(const isg_problem *p, int32_t R, const double *betas, int
     result_free(r);
     return cuda_fail(err, "preparing the solve");
   }
+  r->ctas = (msc ? r->units : r->units) * cluster;
+  r->cluster = cluster;
+  r->threads = threads;
 
-  const uint32_t key0 = (uint32_t)(seed & 0xFFFFFFFFu), key1 = (uint32_t)(seed >> 32);
-  int launches = 0, sweep_launches = 0;
-  if (r->timed) cudaEventRecord(r->t0, stream);
-  if (msc) {
-    TorusSolve s = {};
-    s.L = p->L;
-    s.W = p->W;
-    s.cbits = dp->cbits;
-    s.table = r->d_table;
-    s.key0 = key0;
-    s.key1 = key1;
-    s.words = r->units;
-    s.replicas = R;
-    s.spins = r->d_spins;
-    s.best = r->d_best;
-    s.e_cur = r->d_e_cur;
-    s.e_best = r->d_e_best;
-    s.hit = r->d_hit;
-    s.done = r->d_done;
-    s.has_target = has_target;
-    s.target = has_target ? (int32_t)target : 0;
-    int cluster = plain ? 1 : o.cluster_ctas, threads = o.threads;
-    torus_shape(p->L, p->W, r->units, cluster, threads);
-    if (torus_smem_bytes(p->L, p->W, cluster) > 227 * 1024) {
-      result_free(r);
-      return fail(ISG_EINVAL, "torus %dx%d needs more shared memory than a CTA has", p->L, p->W);
-    }
-    if (p->L < cluster) cluster = 1;
-    r->ctas = r->units * cluster;
-    r->cluster = cluster;
-    r->threads = threads;
-    const int passes = (has_target && r->units > 1) ? 2 : 1;
-    for (int pass = 0; pass < passes && err == cudaSuccess; ++pass) {
-      TorusSolve sp = s;
-      if (pass == 1) sp.has_target = 0;
-      TorusLaunch l = {};
-      l.cluster = cluster;
-      l.threads = threads;
-      l.stop_from_hits = pass == 1;
-      if (plain) {
-        for (int32_t t = 0; t < S && err == cudaSuccess; ++t) {
-          l.t_begin = t;
-          l.t_end = t + 1;
-          l.resume = t > 0;
-          err = torus_launch(sp, l, stream);
-          ++launches;
-          ++sweep_launches;
-        }
-      } else {
-        l.t_begin = 0;
-        l.t_end = S;
-        l.resume = 0;
-        err = torus_launch(sp, l, stream);
-        ++launches;
-        ++sweep_launches;
-      }
-    }
-  } else {
-    if (csr_smem_bytes(p->n, 1, 1) > 227 * 1024) {
-      result_free(r);
-      return fail(ISG_EINVAL, "instance with n = %d needs more shared memory than a CTA has",
-                  p->n);
-    }
-    CsrSolve s = {};
-    s.n = p->n;
-    s.n_colours = p->n_colours;
-    s.class_start = dp->class_start;
-    s.rowptr = dp->rowptr;
-    s.col = dp->col;
-    s.wt = dp->wt;
-    s.orig = dp->orig;
-    s.kmax = p->kmax;
-    s.table = r->d_table;
-    s.key0 = key0;
-    s.key1 = key1;
-    s.quads = r->units;
-    s.replicas = R;
-    s.spins = r->d_spins;
-    s.best = r->d_best;
-    s.e_cur = r->d_e_cur;
-    s.e_best = r->d_e_best;
-    s.hit = r->d_hit;
-    s.done = r->d_done;
-    s.has_target = has_target;
-    s.target = has_target ? (int32_t)target : 0;
-    int max_class = 0;
-    for (int32_t c = 0; c < p->n_colours; ++c)
-      max_class = std::max(max_class, p->class_start[c + 1] - p->class_start[c]);
-    int cluster = plain ? 1 : o.cluster_ctas, threads = o.threads, qpc = 1;
-    csr_shape(p->n, r->units, max_class, cluster, threads, qpc);
-    r->ctas = ((r->units + qpc - 1) / qpc) * cluster;
-    r->cluster = cluster;
-    r->threads = threads;
-    const int groups = (r->units + qpc - 1) / qpc;
-    const int passes = (has_target && groups > 1) ? 2 : 1;
-    for (int pass = 0; pass < passes && err == cudaSuccess; ++pass) {
-      CsrSolve sp = s;
-      if (pass == 1) sp.has_target = 0;
-      CsrLaunch l = {};
-      l.cluster = cluster;
-      l.threads = threads;
-      l.quads_per_cta = qpc;
-      l.stop_from_hits = pass == 1;
-      if (plain) {
-        for (int32_t t = 0; t < S && err == cudaSuccess; ++t) {
-          l.t_begin = t;
-          l.t_end = t + 1;
-          l.resume = t > 0;
-          err = csr_launch(sp, l, stream);
-          ++launches;
-          ++sweep_launches;
-        }
-      } else {
-        l.t_begin = 0;
-        l.t_end = S;
-        l.resume = 0;
-        err = csr_launch(sp, l, stream);
-        ++launches;
-        ++sweep_launches;
-      }
-    }
-  }
+  int launches = 0;
+  if (r->timed) err = cudaEventRecord(r->t0, stream);
+  if (err == cudaSuccess)
+    err = launch_sweeps(p, dp, r, seed, has_target, target, plain, cluster, threads, S, stream,
+                        launches);
+  const int sweep_launches = launches;
   if (r->timed && err == cudaSuccess) err = cudaEventRecord(r->t1, stream);
   if (err == cudaSuccess) {
     err = reduce_hits(r->d_hit, r->units, r->d_stop, stream);
@@ -605,6 +642,99 @@ isg_status anneal_impl(const isg_problem *p, int32_t R, const double *betas, int
   r->launches = launches;
   r->sweep_launches = sweep_launches;
   *out = r;
+  return ISG_OK;
+}
+
+// ------------------------------------------------------------------ autotune
+
+isg_status autotune_impl(const isg_problem *p, int32_t R, int32_t probe, cudaStream_t stream,
+                         isg_options *best) {
+  if (!p) return fail(ISG_EINVAL, "problem must not be NULL");
+  if (R < 1 || probe < 1) return fail(ISG_EINVAL, "replicas and probe_sweeps must be >= 1");
+  const bool msc = p->torus;
+  const DeviceProblem *dp = nullptr;
+  isg_status st = problem_device(p, msc ? kNeedTorus : kNeedCsr, &dp);
+  if (st != ISG_OK) return st;
+  // scratch solve at a mid-schedule temperature (both torus thresholds non-zero)
+  isg_result *r = new_result(p, R, probe, msc, false, stream);
+  std::vector<int32_t> levels;
+  table_levels(p, msc, levels);
+  std::vector<double> betas(probe, 1.0);
+  std::vector<uint32_t> table;
+  build_table(betas.data(), probe, levels, table);
+  r->table_words = table.size();
+  st = result_alloc(r, stream);
+  if (st != ISG_OK) {
+    delete r;
+    return st;
+  }
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  cudaError_t err = cudaEventCreate(&e0);
+  if (err == cudaSuccess) err = cudaEventCreate(&e1);
+  if (err == cudaSuccess)
+    err = cudaMemcpyAsync(r->d_table, table.data(), 4 * table.size(), cudaMemcpyHostToDevice,
+                          stream);
+  const int units = r->units;
+  const int max_class = msc ? 0 : max_class_size(p);
+  float best_ms = 1e30f;
+  int best_cluster = 0, best_threads = 0;
+  const int thread_opts[] = {128, 192, 256, 384, 512};
+  for (int cluster = 1; cluster <= 16 && err == cudaSuccess; ++cluster) {
+    if (msc && (cluster > p->L || torus_smem_bytes(p->L, p->W, cluster) > 227 * 1024)) continue;
+    if (!msc && csr_smem_bytes(p->n, 1, cluster) > 227 * 1024) continue;
+    if (cluster > 1 && units * cluster > 4 * sm_count()) continue;
+    for (int threads : thread_opts) {
+      if (msc) {
+        if (torus_sites_per_thread(p->L, p->W, cluster, threads) * 4 >= 1024) continue;
+        if (torus_max_active_clusters(p->L, p->W, units, cluster, threads) < 1) continue;
+      } else if (threads > round_up((max_class + cluster - 1) / cluster, 32) + 32) {
+        continue;
+      }
+      int launches = 0;
+      // untimed warm launch, then one timed launch of the probe
+      cudaError_t e = launch_sweeps(p, dp, r, 1, false, 0, false, cluster, threads, probe, stream,
+                                    launches);
+      if (e == cudaSuccess) e = cudaEventRecord(e0, stream);
+      if (e == cudaSuccess)
+        e = launch_sweeps(p, dp, r, 1, false, 0, false, cluster, threads, probe, stream, launches);
+      if (e == cudaSuccess) e = cudaEventRecord(e1, stream);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
+      if (e != cudaSuccess) {
+        // a shape the device cannot launch: skip it (launch errors are not sticky)
+        cudaGetLastError();
+        if (cudaStreamSynchronize(stream) != cudaSuccess) {
+          err = e;
+          break;
+        }
+        continue;
+      }
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      if (ms < best_ms) {
+        best_ms = ms;
+        best_cluster = cluster;
+        best_threads = threads;
+      }
+    }
+  }
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  cudaStreamSynchronize(stream);
+  cudaFreeAsync(r->base, stream);
+  r->base = nullptr;
+  delete r;
+  if (err != cudaSuccess) return cuda_fail(err, "autotuning");
+  if (best_cluster == 0) return fail(ISG_EINVAL, "no launch shape fits this instance");
+  {
+    std::lock_guard<std::mutex> lock(g_shape_mu);
+    g_shapes[shape_key(p, units)] = {best_cluster, best_threads};
+  }
+  if (best) {
+    best->kernel = msc ? ISG_KERNEL_TORUS_MSC : ISG_KERNEL_CSR;
+    best->cluster_ctas = best_cluster;
+    best->threads = best_threads;
+    best->time_kernels = 0;
+  }
   return ISG_OK;
 }
 
@@ -730,6 +860,11 @@ isg_status isg_anneal(const isg_problem *p, int32_t replicas, const double *beta
                       uint64_t seed, int64_t target_energy, void *cuda_stream, isg_result **out) {
   return anneal_impl(p, replicas, betas, sweeps, seed, target_energy, nullptr,
                      (cudaStream_t)cuda_stream, out);
+}
+
+isg_status isg_autotune(const isg_problem *p, int32_t replicas, int32_t probe_sweeps,
+                        void *cuda_stream, isg_options *best) {
+  return autotune_impl(p, replicas, probe_sweeps, (cudaStream_t)cuda_stream, best);
 }
 
 isg_status isg_anneal_ex(const isg_problem *p, int32_t replicas, const double *betas,

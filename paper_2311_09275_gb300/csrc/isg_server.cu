@@ -222,6 +222,7 @@ void fill_torus_unit(TorusBatchItem &it, const Slot *sl, int32_t word, int32_t t
   s.table = r->d_table;
   s.key0 = (uint32_t)(sl->rq.seed & 0xFFFFFFFFu);
   s.key1 = (uint32_t)(sl->rq.seed >> 32);
+  s.rk = round_keys(s.key0, s.key1);
   s.words = r->units;
   s.replicas = r->R;
   s.spins = r->d_spins;

@@ -91,12 +91,15 @@ __device__ __forceinline__ void publish_lane_totals(const SlicedCounter<NP> &cnt
   sync_group(K);
 }
 
-// Anneal one replica word of one torus: this CTA is rank k of K.
+// One colour phase of one replica word: this thread's sites of colour c in
+// the CTA's band.  Acceptance masks are built by compare + predicated OR into
+// two partial accumulators (measured faster than packing 4-bit nibbles, and
+// than moving the compares onto the multiply-add pipe).
 template <int NP, bool kTwoThresholds>
 __device__ __forceinline__ void sweep_phase(uint32_t *spin, const uint8_t *cb, uint32_t *up_peer,
                                             uint32_t *down_peer, int W, int r0, int nr, int c,
-                                            uint32_t t, uint32_t word, PhiloxKey key, uint32_t T4,
-                                            uint32_t T8, SlicedCounter<NP> &cnt) {
+                                            const BlockPrefix (&bp)[8], const RoundKeys &rk,
+                                            uint32_t T4, uint32_t T8, SlicedCounter<NP> &cnt) {
   const int half = W >> 1;
   const int step_rows = blockDim.x / half;
   const int step_cols = blockDim.x - step_rows * half;
@@ -122,23 +125,28 @@ __device__ __forceinline__ void sweep_phase(uint32_t *spin, const uint8_t *cb, u
     const uint32_t eq0 = ~(u0 | u1 | u2);
     const uint32_t eq1 = u0 & ~u1;
     const uint32_t ge2 = u1 | u2;
-    // uniforms of the 32 replicas: 8 Philox blocks of 4
-    uint32_t r4 = 0u, r8 = 0u;
+    // uniforms of the 32 replicas: 8 Philox blocks of 4 sharing this site's
+    // round-1/2 prefix; each block yields independent 4-bit acceptance nibbles
     const uint32_t site = (uint32_t)(gr * W + col);
+    const SitePrefix sp = site_prefix(site, rk);
+    uint32_t a4[2] = {0u, 0u}, a8[2] = {0u, 0u};
 #pragma unroll
-    for (uint32_t q = 0; q < 8; ++q) {
-      const uint4 u = philox10(make_uint4(site, t, 8u * word + q, kTagSweep), key);
-      r4 |= ((u.x < T4) ? 1u : 0u) << (4 * q);
-      r4 |= ((u.y < T4) ? 1u : 0u) << (4 * q + 1);
-      r4 |= ((u.z < T4) ? 1u : 0u) << (4 * q + 2);
-      r4 |= ((u.w < T4) ? 1u : 0u) << (4 * q + 3);
+    for (int q = 0; q < 8; ++q) {
+      const uint4 u = philox10_factored(sp, bp[q], rk);
+      uint32_t &x4 = a4[q & 1], &x8 = a8[q & 1];
+      if (u.x < T4) x4 |= 1u << (4 * q);
+      if (u.y < T4) x4 |= 2u << (4 * q);
+      if (u.z < T4) x4 |= 4u << (4 * q);
+      if (u.w < T4) x4 |= 8u << (4 * q);
       if (kTwoThresholds) {
-        r8 |= ((u.x < T8) ? 1u : 0u) << (4 * q);
-        r8 |= ((u.y < T8) ? 1u : 0u) << (4 * q + 1);
-        r8 |= ((u.z < T8) ? 1u : 0u) << (4 * q + 2);
-        r8 |= ((u.w < T8) ? 1u : 0u) << (4 * q + 3);
+        if (u.x < T8) x8 |= 1u << (4 * q);
+        if (u.y < T8) x8 |= 2u << (4 * q);
+        if (u.z < T8) x8 |= 4u << (4 * q);
+        if (u.w < T8) x8 |= 8u << (4 * q);
       }
     }
+    const uint32_t r4 = a4[0] | a4[1];
+    const uint32_t r8 = a8[0] | a8[1];
     const uint32_t acc = ge2 | (eq1 & r4) | (eq0 & r8);
     const uint32_t sn = s0 ^ acc;
     spin[x] = sn;
@@ -231,14 +239,16 @@ __device__ void torus_word(const TorusSolve &s, int word, int k, int K, int t_be
   int hit = -1;
   for (; t < t_end; ++t) {
     const uint32_t T4 = s.table[2 * t], T8 = s.table[2 * t + 1];
+    // the (block, sweep) part of Philox rounds 1-2, uniform across the CTA
+    BlockPrefix bp[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) bp[q] = block_prefix(8u * uword + (uint32_t)q, (uint32_t)t, s.rk);
     cnt.clear();
     for (int c = 0; c < 2; ++c) {
       if (T8 != 0u)
-        sweep_phase<NP, true>(spin, cb, up_peer, down_peer, W, r0, nr, c, (uint32_t)t, uword,
-                              key, T4, T8, cnt);
+        sweep_phase<NP, true>(spin, cb, up_peer, down_peer, W, r0, nr, c, bp, s.rk, T4, T8, cnt);
       else
-        sweep_phase<NP, false>(spin, cb, up_peer, down_peer, W, r0, nr, c, (uint32_t)t, uword,
-                               key, T4, T8, cnt);
+        sweep_phase<NP, false>(spin, cb, up_peer, down_peer, W, r0, nr, c, bp, s.rk, T4, T8, cnt);
       if (c == 0) sync_group(K);
     }
     publish_lane_totals<NP>(cnt, lane_acc, part, k, K);
@@ -330,10 +340,40 @@ int np_for(int sites_per_thread_sweep, int sites_per_thread_band) {
 }
 
 template <typename Kern>
-cudaError_t launch_clustered(Kern kernel, int grid, int threads, size_t smem, int cluster,
-                             cudaStream_t stream, const TorusSolve &s, const TorusLaunch &l) {
+cudaError_t prepare_clustered(Kern kernel, size_t smem, int cluster) {
   cudaError_t err = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
+  if (err == cudaSuccess && cluster > 8)
+    err = cudaFuncSetAttribute(kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+  return err;
+}
+
+template <typename Kern>
+int max_active_clusters(Kern kernel, int grid, int threads, size_t smem, int cluster) {
+  if (prepare_clustered(kernel, smem, cluster) != cudaSuccess) return 0;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(threads);
+  cfg.dynamicSmemBytes = smem;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = cluster;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  int n = 0;
+  if (cudaOccupancyMaxActiveClusters(&n, kernel, &cfg) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  return n;
+}
+
+template <typename Kern>
+cudaError_t launch_clustered(Kern kernel, int grid, int threads, size_t smem, int cluster,
+                             cudaStream_t stream, const TorusSolve &s, const TorusLaunch &l) {
+  cudaError_t err = prepare_clustered(kernel, smem, cluster);
   if (err != cudaSuccess) return err;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(grid);
@@ -365,6 +405,21 @@ int32_t torus_sites_per_thread(int32_t L, int32_t W, int32_t cluster, int32_t th
   const int nr = (L + cluster - 1) / cluster;
   const int per_phase = (nr * (W / 2) + threads - 1) / threads;
   return 2 * per_phase;
+}
+
+int torus_max_active_clusters(int32_t L, int32_t W, int32_t words, int32_t cluster,
+                              int32_t threads) {
+  const size_t smem = torus_smem_bytes(L, W, cluster);
+  const int nr = (L + cluster - 1) / cluster;
+  const int np = np_for(torus_sites_per_thread(L, W, cluster, threads),
+                        (nr * W + threads - 1) / threads);
+  const int grid = words * cluster;
+  switch (np) {
+    case 6: return max_active_clusters(torus_kernel<6>, grid, threads, smem, cluster);
+    case 8: return max_active_clusters(torus_kernel<8>, grid, threads, smem, cluster);
+    case 10: return max_active_clusters(torus_kernel<10>, grid, threads, smem, cluster);
+    default: return 0;
+  }
 }
 
 cudaError_t torus_launch(const TorusSolve &s, const TorusLaunch &l, cudaStream_t stream) {

@@ -58,6 +58,7 @@ _sig("isg_anneal", [_P, _i32, _P, _i32, _u64, _i64, _P, ctypes.POINTER(_P)])
 _sig("isg_anneal_ex", [_P, _i32, _P, _i32, _u64, _i64, ctypes.POINTER(isg_options), _P,
                        ctypes.POINTER(_P)])
 _sig("isg_anneal_batch", [_P, _i32, _i32, _P, _i32, _P, _P, _P, _P])
+_sig("isg_autotune", [_P, _i32, _i32, _P, ctypes.POINTER(isg_options)])
 _sig("isg_energy", [_P, _P, _i32, _P])
 _sig("isg_result_final", [_P, _P, _P, _P])
 _sig("isg_best", [_P, _P, _P, _P, _P, _P])
@@ -235,6 +236,14 @@ def isg_anneal(p, replicas: int, betas, seed: int, target=None, stream=None, ker
                               ISG_NO_TARGET if target is None else int(target),
                               ctypes.byref(opts), _stream(stream), ctypes.byref(out)))
     return Result(out.value)
+
+
+def isg_autotune(p, replicas: int, probe_sweeps: int = 64, stream=None) -> dict:
+    """Measure launch shapes for (instance, replicas); later solves use the best."""
+    best = isg_options()
+    _check(_lib.isg_autotune(_h(p), int(replicas), int(probe_sweeps), _stream(stream),
+                             ctypes.byref(best)))
+    return {"kernel": best.kernel, "cluster_ctas": best.cluster_ctas, "threads": best.threads}
 
 
 def isg_anneal_batch(problems, replicas: int, betas, seeds, targets=None, stream=None):

@@ -71,6 +71,33 @@ def test_torus_launch_shapes_bit_exact(isg, L, W, R, cluster, threads):
         assert st["cluster_ctas"] == cluster
 
 
+@pytest.mark.parametrize("cluster,threads", [(3, 96), (9, 128), (12, 64), (16, 256)])
+def test_torus_nonportable_clusters_bit_exact(isg, cluster, threads):
+    """Cluster sizes that are not powers of two and above 8 (uneven bands)."""
+    t = I.torus(34, 22, 12)
+    betas = I.geometric_betas(0.1, 5.0, 60)
+    orc = oracle.anneal(oracle.csr_of(t), 70, betas, 19)
+    res = isg.isg_anneal(isg.problem_of(t), 70, betas, 19, kernel=1, cluster_ctas=cluster,
+                         threads=threads)
+    assert_same(res, orc)
+    assert res.stats()["cluster_ctas"] == cluster
+
+
+@pytest.mark.parametrize("kind", ["torus", "graph"])
+def test_autotuned_shape_bit_exact(isg, kind):
+    prob = I.torus(40, 30, 5) if kind == "torus" else I.random_graph(3000, 3500, 5)
+    p = isg.problem_of(prob)
+    R = 96
+    betas = I.geometric_betas(0.1, 5.0, 50)
+    best = isg.isg_autotune(p, R, 16)
+    assert 1 <= best["cluster_ctas"] <= 16 and best["threads"] % 32 == 0
+    res = isg.isg_anneal(p, R, betas, 4)
+    st = res.stats()
+    assert (st["cluster_ctas"], st["threads"]) == (best["cluster_ctas"], best["threads"])
+    orc = oracle.anneal(oracle.csr_of(prob), [0, 1, 33, 95], betas, 4)
+    assert_same(res, orc, reps=[0, 1, 33, 95])
+
+
 def test_torus_beta_zero_and_huge(isg):
     t = I.torus(8, 8, 3)
     c = oracle.csr_of(t)
