@@ -160,6 +160,25 @@ isg_status isg_anneal_batch(const isg_problem *const *probs, int32_t count, int3
 isg_status isg_energy(const isg_problem *p, const int8_t *spins, int32_t replicas,
                       int64_t *energies);
 
+/* isg_energy for callers that cannot allocate device memory when they call it
+ * (a process whose device memory is fully reserved by another allocator, or a
+ * latency-critical loop that must stay out of the driver's allocator).  No
+ * counterpart in the paper: this is a library convenience.
+ * All arguments are DEVICE pointers owned by the caller: a symmetric CSR in
+ * the caller's vertex ids (rowptr_dev[n+1] int64, col_dev/w_dev[rowptr[n]]),
+ * spins_dev[replicas][n] int8 +-1, and energies_dev[replicas] int64 (output).
+ * The work is enqueued on cuda_stream (NULL = legacy default stream) and
+ * nothing is allocated or freed: per-block partial sums live in a fixed
+ * 512 KiB array inside the library that every device loading the library
+ * keeps until the process exits.  replicas must be in [1, 2048] (EINVAL
+ * otherwise).  The first call on a device looks up that array's device
+ * address; make it before any stream capture.  All calls share the array, so
+ * calls whose work overlaps on the GPU (different streams, no ordering) race
+ * and give wrong energies; calls ordered on one stream are fine. */
+isg_status isg_energy_noalloc(int32_t n, const int64_t *rowptr_dev, const int32_t *col_dev,
+                              const int32_t *w_dev, const int8_t *spins_dev, int32_t replicas,
+                              int64_t *energies_dev, void *cuda_stream);
+
 /* Final state: spins[R][n] (may be NULL), energies[R] (may be NULL) and the
  * number of sweeps run.  Waits for the solve to finish. */
 isg_status isg_result_final(const isg_result *r, int8_t *spins, int32_t *energies,

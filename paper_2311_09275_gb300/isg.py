@@ -60,6 +60,7 @@ _sig("isg_anneal_ex", [_P, _i32, _P, _i32, _u64, _i64, ctypes.POINTER(isg_option
 _sig("isg_anneal_batch", [_P, _i32, _i32, _P, _i32, _P, _P, _P, _P])
 _sig("isg_autotune", [_P, _i32, _i32, _P, ctypes.POINTER(isg_options)])
 _sig("isg_energy", [_P, _P, _i32, _P])
+_sig("isg_energy_noalloc", [_i32, _P, _P, _P, _P, _i32, _P, _P])
 _sig("isg_result_final", [_P, _P, _P, _P])
 _sig("isg_best", [_P, _P, _P, _P, _P, _P])
 _sig("isg_result_shape", [_P, _P, _P, _P])
@@ -268,6 +269,20 @@ def isg_energy(p, spins) -> np.ndarray:
     e = np.zeros(s.shape[0], dtype=np.int64)
     _check(_lib.isg_energy(_h(p), _ptr(s), int(s.shape[0]), _ptr(e)))
     return e
+
+
+def isg_energy_noalloc(n: int, rowptr_dev: int, col_dev: int, w_dev: int, spins_dev: int,
+                       replicas: int, energies_dev: int, stream=None):
+    """Energies of device-resident configurations with no device allocation.
+
+    For callers that cannot allocate device memory at call time (device memory
+    fully reserved by another allocator, or a loop that must stay out of the
+    driver's allocator).  Every argument is a raw device address the caller
+    owns (e.g. ``tensor.data_ptr()``); see ``isg_energy_noalloc`` in isg.h for
+    layouts, the replica limit and the rule on overlapping calls.
+    """
+    _check(_lib.isg_energy_noalloc(int(n), rowptr_dev, col_dev, w_dev, spins_dev, int(replicas),
+                                   energies_dev, _stream(stream)))
 
 
 def isg_result_final(r: Result, spins: bool = True):
