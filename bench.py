@@ -387,13 +387,147 @@ def run_gpu(args):
         print(json.dumps(line))
 
 
+# ---------------------------------------------------------------- batched form
+def run_batch(args):
+    """512 uneven tori (even L, W in [16, 140]), 32 replicas, 2,000 sweeps, in
+    one persistent kernel launched through a CUDA graph; against the plain form
+    (one instance per launch sequence, one launch per sweep) on a size-stratified
+    sample of the same instances, and against one persistent launch per instance."""
+    import torch
+    from paper_2311_09275_gb300 import isg
+    torch.cuda.set_device(0)
+    stream = torch.cuda.current_stream()
+    sweeps = args.sweeps or 2000
+    batch = I.torus_batch(sweeps=sweeps)
+    probs = [isg.problem_of(sv.problem) for sv in batch]
+    betas, seeds = batch[0].betas, [sv.seed for sv in batch]
+    attempts = float(sum(sv.attempts for sv in batch))
+    for _ in range(args.warmup):
+        for r in isg.isg_anneal_batch(probs, 32, betas, seeds, stream=stream):
+            r.close()
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    with ClockSampler(0) as clocks:
+        for k in range(args.steps):
+            ev[k][0].record(stream)
+            outs = isg.isg_anneal_batch(probs, 32, betas, seeds, stream=stream)
+            ev[k][1].record(stream)
+            torch.cuda.synchronize()
+            stats = outs[0].stats()
+            for r in outs:
+                r.close()
+    ms = [a.elapsed_time(b) for a, b in ev]
+    value = attempts * args.steps / (sum(ms) / 1e3)
+    # plain forms on a sample: every 32nd instance in size order
+    order = sorted(range(len(batch)), key=lambda k: batch[k].n)
+    sample = order[::32]
+    sample_attempts = float(sum(batch[k].attempts for k in sample))
+    rates = {}
+    for label, kernel in (("plain_one_launch_per_sweep", isg.KERNEL_PLAIN),
+                          ("one_persistent_launch_per_instance", isg.KERNEL_AUTO)):
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        rs = [isg.isg_anneal(probs[k], 32, betas, seeds[k], stream=stream, kernel=kernel)
+              for k in sample]
+        e1.record(stream)
+        torch.cuda.synchronize()
+        for r in rs:
+            r.close()
+        rates[label] = sample_attempts / (e0.elapsed_time(e1) / 1e3)
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": sum(ms) / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+            "config": {"workload": f"batch512_tori_L_W_even_16_140_R32_S{sweeps}_geometric_0.1_5.0",
+                       "attempts_per_step": attempts, "launch": "CUDA graph: 1 persistent kernel "
+                       f"({stats['ctas']} CTAs x {stats['threads']} threads) + 1 unpack",
+                       "l2": "working set of each CTA in shared memory; inputs ~12 MB"},
+            "plain": {"sample": f"{len(sample)} instances (every 32nd by size)",
+                      "attempts_per_s": rates,
+                      "batched_over_plain": {k: value / v for k, v in rates.items()}},
+            "gpu_launches": stats["launches"], "clocks": clocks.summary()}
+    print(json.dumps(line))
+
+
+# ---------------------------------------------------------------- served form
+def run_served(args):
+    """Poisson request stream (200/s): half +-1 tori 40..100 x 40..200, half
+    random graphs of 2,000..20,000 vertices and mean degree 2..4; 32 replicas,
+    10,000-sweep budget, target = the plain run's best over the full budget.
+    Reports p50/p99 time-to-target (arrival -> result) and throughput."""
+    import torch
+    from paper_2311_09275_gb300 import isg, metrics
+    torch.cuda.set_device(0)
+    count = args.requests
+    sweeps = args.sweeps or 10000
+    reqs = I.served_stream(count=count, sweeps=sweeps)
+    probs = [isg.problem_of(r.solve.problem) for r in reqs]
+    # targets from plain runs of the full budget (batched through a server, untimed)
+    srv = isg.Server(64 << 30, 512, 500)
+    ids = {srv.submit(p, r.solve.replicas, r.solve.betas, r.solve.seed): k
+           for k, (p, r) in enumerate(zip(probs, reqs))}
+    targets = [None] * count
+    while any(t is None for t in targets):
+        got = srv.poll(60.0)
+        assert got is not None, "target precomputation timed out"
+        k = ids[got[0]]
+        targets[k] = got[1].best(spins=False)[0]
+        got[1].close()
+    srv.close()
+    # timed served run
+    srv = isg.Server(args.mem_gb << 30, args.slots, args.chunk)
+    t_submit, t_done, hit, attempts = {}, {}, {}, 0.0
+    t0 = time.perf_counter()
+    k = 0
+    ids = {}
+    with ClockSampler(0) as clocks:
+        while len(t_done) < count:
+            now = time.perf_counter() - t0
+            while k < count and reqs[k].arrival_s <= now:
+                rid = srv.submit(probs[k], reqs[k].solve.replicas, reqs[k].solve.betas,
+                                 reqs[k].solve.seed, targets[k])
+                ids[rid] = k
+                t_submit[k] = t0 + reqs[k].arrival_s
+                k += 1
+            wait = (reqs[k].arrival_s - (time.perf_counter() - t0)) if k < count else 1.0
+            got = srv.poll(max(0.0, min(wait, 0.05)))
+            if got is None:
+                continue
+            j = ids[got[0]]
+            t_done[j] = time.perf_counter()
+            _, _, done = got[1].final(spins=False)
+            hit[j] = got[1].best(spins=False)[4]
+            attempts += reqs[j].solve.replicas * reqs[j].solve.n * done
+            got[1].close()
+    wall = time.perf_counter() - t0
+    srv.close()
+    ttt = [t_done[j] - t_submit[j] for j in range(count)]
+    line = {"metric": "time-to-target (served)", "value": metrics.percentile(ttt, 99), "unit": "s",
+            "n_gpus": 1, "steps": 1, "warmup": 0, "ms_per_step": wall * 1e3,
+            "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
+            "data": "synthetic",
+            "config": {"workload": f"served_poisson200_{count}req_R32_B{sweeps}",
+                       "slots": args.slots, "sweeps_per_chunk": args.chunk,
+                       "device_mem_budget_gb": args.mem_gb},
+            "ttt_p50_s": metrics.percentile(ttt, 50), "ttt_p99_s": metrics.percentile(ttt, 99),
+            "throughput_attempts_per_s": attempts / wall, "requests_per_s": count / wall,
+            "targets_hit": sum(1 for j in range(count) if hit[j] >= 0),
+            "clocks": clocks.summary()}
+    print(json.dumps(line))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--config", default="torus", choices=["torus", "random"])
+    ap.add_argument("--config", default="torus", choices=["torus", "random", "batch", "served"])
+    ap.add_argument("--requests", type=int, default=2000, help="served: number of requests")
+    ap.add_argument("--slots", type=int, default=256, help="served: maximum resident requests")
+    ap.add_argument("--chunk", type=int, default=250, help="served: sweeps per chunk")
+    ap.add_argument("--mem-gb", type=int, default=32, help="served: device memory budget (GB)")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-tune", action="store_true", help="skip the launch-shape autotuner")
     ap.add_argument("--launch", default=None,
@@ -403,6 +537,10 @@ def main():
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
+    elif args.config == "batch":
+        run_batch(args)
+    elif args.config == "served":
+        run_served(args)
     else:
         run_gpu(args)
 
