@@ -1,0 +1,51 @@
+"""Multi-process path of bench.py on CPU (gloo, world size 2): every rank anneals
+its own seed of the same workload (weak scaling, no data exchange), the job time
+is the maximum over ranks and the work is the sum over ranks."""
+import os
+import socket
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _free_port():
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _rank_main(rank, world, port, out_dir):
+    sys.path.insert(0, ROOT)
+    os.environ.update({"MASTER_ADDR": "127.0.0.1", "MASTER_PORT": str(port),
+                       "RANK": str(rank), "WORLD_SIZE": str(world), "LOCAL_RANK": str(rank)})
+    import torch
+    import bench
+
+    class A:
+        impl = "reference"     # forces the gloo backend in dist_setup
+    w, r, local, dist = bench.dist_setup(A())
+    assert (w, r) == (world, rank)
+    cpu = torch.device("cpu")
+    sv, name = bench.workload("torus", rank, sweeps=10)
+    t = 1.0 + 2.0 * rank                      # rank 1 is the slow one
+    tmax = bench.max_over_ranks(t, dist, cpu)
+    total = bench.sum_over_ranks(float(sv.attempts), dist, cpu)
+    bench.barrier(dist)
+    with open(os.path.join(out_dir, f"rank{rank}.txt"), "w") as f:
+        f.write(f"{tmax} {total} {sv.seed} {name}\n")
+    dist.destroy_process_group()
+
+
+def test_two_rank_weak_scaling_aggregation(tmp_path):
+    import torch.multiprocessing as mp
+    port = _free_port()
+    mp.start_processes(_rank_main, args=(2, port, str(tmp_path)), nprocs=2, join=True,
+                       start_method="spawn")
+    rows = [open(tmp_path / f"rank{r}.txt").read().split() for r in range(2)]
+    for tmax, total, seed, name in rows:
+        assert float(tmax) == 3.0
+        assert float(total) == 2 * 1024 * 8000 * 10
+    assert rows[0][2] != rows[1][2]          # ranks anneal different seeds
+    assert rows[0][3] == rows[1][3]          # of the same workload
