@@ -277,8 +277,10 @@ def run_gpu(args):
 
     shape = {}
     if args.launch:
-        c, t = (int(x) for x in args.launch.split(","))
-        shape = {"cluster_ctas": c, "threads": t}
+        parts = [int(x) for x in args.launch.split(",")]
+        shape = {"cluster_ctas": parts[0], "threads": parts[1]}
+        if len(parts) > 2:
+            shape["quads_per_cta"] = parts[2]
 
     def step(time_kernels=True):
         return isg.isg_anneal(p, sv.replicas, sv.betas, sv.seed, stream=stream,

@@ -118,6 +118,7 @@ typedef struct {
     int32_t cluster_ctas;  /* CTAs that share one replica block (1..16); 0 = tuned/default */
     int32_t threads;       /* threads per CTA (multiple of 32, <= 512); 0 = tuned/default */
     int32_t time_kernels;  /* nonzero: time the sweep launches with CUDA events */
+    int32_t quads_per_cta; /* colour-class kernel: replica quads per CTA (1, 2); 0 = tuned/default */
 } isg_options;
 
 /* Anneal R = replicas independent chains for S = sweeps sweeps at inverse

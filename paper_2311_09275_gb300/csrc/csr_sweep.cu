@@ -9,8 +9,15 @@
 // Layout: a cluster of K CTAs owns Q replica quads of one instance.  Every
 // CTA keeps a full copy of those quads' spins in shared memory, updates 1/K
 // of each colour class and writes each new word to all K copies (distributed
-// shared memory); one cluster barrier separates the classes.  Neighbour
-// gathers are therefore always local shared-memory loads.
+// shared memory); one cluster barrier separates the classes.  The slice of
+// each class a CTA owns is a contiguous id range, so its adjacency is a
+// contiguous slice of the CSR: when it fits, the CTA stages those slices
+// (row offsets, neighbour ids, weights, original ids) in shared memory once,
+// and every neighbour gather of the sweep loop is a shared-memory load.
+//
+// Local fields: for graphs whose weights are all +1, or all +1/-1, the four
+// lanes' counts of -1 neighbours are summed in one 32-bit add per neighbour
+// (one byte per lane, degree <= 255); general integer weights sum per lane.
 #include <climits>
 
 #include "isg_device.cuh"
@@ -22,15 +29,23 @@ namespace {
 __host__ __device__ __forceinline__ size_t align16(size_t x) { return (x + 15) & ~size_t(15); }
 
 struct CsrSmem {
-  size_t spin, part, lane_acc, flags, total;
+  size_t spin, lrow, lorig, lcol, lwt, ocls, trow, part, lane_acc, flags, total;
 };
 
-__host__ __device__ __forceinline__ CsrSmem csr_layout(int n, int Q, int K) {
+// own_n / own_nnz: the largest owned vertex / adjacency count of any rank
+// (0 = not staged); trow_n: threshold entries cached per sweep (0 = none).
+__host__ __device__ __forceinline__ CsrSmem csr_layout(int n, int Q, int K, int n_colours,
+                                                       int own_n, int own_nnz, bool weights,
+                                                       int trow_n) {
   CsrSmem m;
   m.spin = 0;
-  m.part = align16(sizeof(uint32_t) * (size_t)n * Q);
-  // two buffers of per-rank partial sums, alternating between publications,
-  // so a fast CTA never overwrites sums a slower peer is still reading
+  m.lrow = align16(sizeof(uint32_t) * (size_t)n * Q);
+  m.lorig = align16(m.lrow + (own_n ? sizeof(int32_t) * ((size_t)own_n + 1) : 0));
+  m.lcol = align16(m.lorig + sizeof(int32_t) * (size_t)own_n);
+  m.lwt = align16(m.lcol + sizeof(int32_t) * (size_t)own_nnz);
+  m.ocls = align16(m.lwt + (weights ? sizeof(int32_t) * (size_t)own_nnz : 0));
+  m.trow = align16(m.ocls + (own_n ? sizeof(int32_t) * ((size_t)n_colours + 1) : 0));
+  m.part = align16(m.trow + sizeof(uint32_t) * (size_t)trow_n);
   m.lane_acc = m.part + 2 * sizeof(int32_t) * 4 * (size_t)Q * K;
   m.flags = m.lane_acc + sizeof(int32_t) * 4 * (size_t)Q;
   m.total = align16(m.flags + sizeof(uint32_t) * 4 * (size_t)Q + 16);
@@ -44,8 +59,7 @@ __device__ __forceinline__ void sync_group(int K) {
     cluster_barrier();
 }
 
-// Spin (+1/-1) of lane l of a packed word: byte l, sign-extended by moving it
-// to the top byte and shifting back arithmetically.
+// Spin (+1/-1) of lane l of a packed word: byte l, sign-extended.
 __device__ __forceinline__ int32_t lane8(uint32_t w, int l) {
   return ((int32_t)(w << (24 - 8 * l))) >> 24;
 }
@@ -58,8 +72,7 @@ __device__ __forceinline__ void own_range(int a, int b, int k, int K, int &lo, i
 }
 
 // Per-lane int32 values summed over the CTA, published to every CTA of the
-// cluster as part[k][slot]; ends with the group barrier.  `vals[q][l]` is the
-// thread's contribution for quad slot q, lane l.
+// cluster as part[k][slot]; ends with the group barrier.
 template <int Q>
 __device__ __forceinline__ void publish(const int32_t (&vals)[Q][4], int32_t *lane_acc,
                                         int32_t *part, int k, int K) {
@@ -83,15 +96,91 @@ __device__ __forceinline__ void publish(const int32_t (&vals)[Q][4], int32_t *la
   sync_group(K);
 }
 
-template <int Q>
-__device__ void csr_solve(const CsrSolve &s, int quad0, int k, int K, int t_begin, int t_end,
-                          int resume, uint8_t *smem) {
+// Sources of one vertex's adjacency: staged in shared memory or global.
+struct Adj {
+  const int32_t *row;   // row offsets (local when staged)
+  const int32_t *col;   // neighbours (relabelled ids; bit 31 = negative weight in mode 1)
+  const int32_t *wt;    // weights (mode 2)
+  const int32_t *orig;  // original ids
+};
+
+// Half energy changes kk[l] = -s_l h_l of the Q quads of vertex v (row slot i).
+template <int Q, int MODE>
+__device__ __forceinline__ void fields(const uint32_t *spin, int n, int v, int p0, int p1,
+                                       const Adj &a, int32_t (&kk)[Q][4]) {
+  if (MODE == 2) {
+    int32_t h[Q][4];
+#pragma unroll
+    for (int q = 0; q < Q; ++q)
+#pragma unroll
+      for (int l = 0; l < 4; ++l) h[q][l] = 0;
+    for (int p = p0; p < p1; ++p) {
+      const int j = a.col[p];
+      const int32_t wv = a.wt[p];
+#pragma unroll
+      for (int q = 0; q < Q; ++q) {
+        const uint32_t su = spin[q * n + j];
+#pragma unroll
+        for (int l = 0; l < 4; ++l) h[q][l] += wv * lane8(su, l);
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < Q; ++q) {
+      const uint32_t sv = spin[q * n + v];
+#pragma unroll
+      for (int l = 0; l < 4; ++l) kk[q][l] = -lane8(sv, l) * h[q][l];
+    }
+  } else {
+    // count, per lane, the -1 spins among positive (and negative) neighbours
+    uint32_t cpos[Q], cneg[Q];
+#pragma unroll
+    for (int q = 0; q < Q; ++q) cpos[q] = cneg[q] = 0u;
+    int dneg = 0;
+    for (int p = p0; p < p1; ++p) {
+      const int e = a.col[p];
+      const int j = e & 0x7FFFFFFF;
+      const uint32_t neg = MODE == 1 ? (uint32_t)(e >> 31) : 0u;  // all ones if w = -1
+      if (MODE == 1) dneg -= (int)neg;
+#pragma unroll
+      for (int q = 0; q < Q; ++q) {
+        const uint32_t minus = (spin[q * n + j] >> 1) & 0x01010101u;  // 1 per lane with s = -1
+        if (MODE == 1) {
+          cneg[q] += minus & neg;
+          cpos[q] += minus & ~neg;
+        } else {
+          cpos[q] += minus;
+        }
+      }
+    }
+    const int dpos = (p1 - p0) - dneg;
+#pragma unroll
+    for (int q = 0; q < Q; ++q) {
+      const uint32_t sv = spin[q * n + v];
+#pragma unroll
+      for (int l = 0; l < 4; ++l) {
+        // h = (dpos - 2 * minus_pos) - (dneg - 2 * minus_neg)
+        int32_t h = dpos - 2 * (int32_t)((cpos[q] >> (8 * l)) & 0xFFu);
+        if (MODE == 1) h -= dneg - 2 * (int32_t)((cneg[q] >> (8 * l)) & 0xFFu);
+        const int32_t m = -(int32_t)((sv >> (8 * l + 1)) & 1u);  // -1 if s_l = -1
+        kk[q][l] = ((-h) ^ m) - m;                               // -s_l h
+      }
+    }
+  }
+}
+
+template <int Q, int MODE, bool STAGED>
+__device__ void csr_solve(const CsrSolve &s, const CsrLaunch &L, int quad0, int k, int K,
+                          int t_begin, int t_end, int resume, uint8_t *smem) {
   const int n = s.n;
-  const CsrSmem lay = csr_layout(n, Q, K);
+  const int trow_n = (s.kmax + 1 <= kCsrTableCache) ? s.kmax + 1 : 0;
+  const CsrSmem lay = csr_layout(n, Q, K, s.n_colours, STAGED ? L.own_n : 0,
+                                 STAGED ? L.own_nnz : 0, MODE == 2, trow_n);
   uint32_t *spin = reinterpret_cast<uint32_t *>(smem + lay.spin);  // [Q][n]
   int32_t *part = reinterpret_cast<int32_t *>(smem + lay.part);
   int32_t *lane_acc = reinterpret_cast<int32_t *>(smem + lay.lane_acc);
   volatile uint32_t *flags = reinterpret_cast<uint32_t *>(smem + lay.flags);
+  uint32_t *trow = reinterpret_cast<uint32_t *>(smem + lay.trow);
+  int32_t *ocls = reinterpret_cast<int32_t *>(smem + lay.ocls);
   const PhiloxKey key{s.key0, s.key1};
   const int lane = (int)lane_id();
 
@@ -115,6 +204,45 @@ __device__ void csr_solve(const CsrSolve &s, int quad0, int k, int K, int t_begi
     }
     spin[x] = w;
   }
+
+  // adjacency of the owned slices: staged copy (local row ids) or global
+  Adj adj;
+  if (STAGED) {
+    int32_t *lrow = reinterpret_cast<int32_t *>(smem + lay.lrow);
+    int32_t *lorig = reinterpret_cast<int32_t *>(smem + lay.lorig);
+    int32_t *lcol = reinterpret_cast<int32_t *>(smem + lay.lcol);
+    int32_t *lwt = reinterpret_cast<int32_t *>(smem + lay.lwt);
+    if (threadIdx.x == 0) {
+      int ov = 0;
+      for (int c = 0; c < s.n_colours; ++c) {
+        int lo, hi;
+        own_range(s.class_start[c], s.class_start[c + 1], k, K, lo, hi);
+        ocls[c] = ov;
+        ov += hi - lo;
+      }
+      ocls[s.n_colours] = ov;
+    }
+    __syncthreads();
+    int ebase = 0;
+    for (int c = 0; c < s.n_colours; ++c) {
+      int lo, hi;
+      own_range(s.class_start[c], s.class_start[c + 1], k, K, lo, hi);
+      const int ob = ocls[c];
+      const int e0 = s.rowptr[lo], e1 = s.rowptr[hi];
+      for (int i = threadIdx.x; i <= hi - lo; i += blockDim.x) {
+        lrow[ob + i] = s.rowptr[lo + i] - e0 + ebase;
+        if (i < hi - lo) lorig[ob + i] = s.orig[lo + i];
+      }
+      for (int p = threadIdx.x; p < e1 - e0; p += blockDim.x) {
+        lcol[ebase + p] = s.col[e0 + p];
+        if (MODE == 2) lwt[ebase + p] = s.wt[e0 + p];
+      }
+      ebase += e1 - e0;
+    }
+    adj = {lrow, lcol, lwt, lorig};
+  } else {
+    adj = {s.rowptr, s.col, s.wt, s.orig};
+  }
   if (threadIdx.x < 4 * Q) lane_acc[threadIdx.x] = 0;
   __syncthreads();
 
@@ -125,6 +253,7 @@ __device__ void csr_solve(const CsrSolve &s, int quad0, int k, int K, int t_begi
   const bool valid = (lane < 4 * Q) && (quad0 + my_q < s.quads) && (my_r < s.replicas);
 
   if (!resume) {
+    // E = sum over edges once (at the lower relabelled end), general per-lane sums
     int32_t vals[Q][4];
 #pragma unroll
     for (int q = 0; q < Q; ++q)
@@ -138,21 +267,16 @@ __device__ void csr_solve(const CsrSolve &s, int quad0, int k, int K, int t_begi
 #pragma unroll
         for (int q = 0; q < Q; ++q) {
           const uint32_t sv = spin[q * n + v];
-          int32_t acc[4] = {0, 0, 0, 0};
           for (int p = p0; p < p1; ++p) {
-            const int u = __ldg(&s.col[p]);
+            const int u = s.col[p] & 0x7FFFFFFF;
             if (u <= v) continue;
-            const int32_t wv = __ldg(&s.wt[p]);
+            const int32_t wv = s.wt[p];
             const uint32_t su = spin[q * n + u];
 #pragma unroll
-            for (int l = 0; l < 4; ++l) acc[l] += wv * lane8(sv, l) * lane8(su, l);
+            for (int l = 0; l < 4; ++l) vals[q][l] += wv * lane8(sv, l) * lane8(su, l);
           }
-#pragma unroll
-          for (int l = 0; l < 4; ++l) vals[q][l] += acc[l];
+          if (quad0 + q < s.quads) s.best[(size_t)(quad0 + q) * n + v] = sv;
         }
-#pragma unroll
-        for (int q = 0; q < Q; ++q)
-          if (quad0 + q < s.quads) s.best[(size_t)(quad0 + q) * n + v] = spin[q * n + v];
       }
     }
     publish<Q>(vals, lane_acc, part, k, K);  // publication 0 uses buffer 0
@@ -173,6 +297,13 @@ __device__ void csr_solve(const CsrSolve &s, int quad0, int k, int K, int t_begi
   int hit = -1;
   for (; t < t_end; ++t) {
     const uint32_t *row = s.table + (size_t)t * kmax1;
+    if (trow_n) {
+      // the sweep's thresholds: all threads finished the previous sweep's
+      // reads at the last barrier of that sweep
+      for (int i = threadIdx.x; i < trow_n; i += blockDim.x) trow[i] = row[i];
+      __syncthreads();
+      row = trow;
+    }
     int32_t de[Q][4];
 #pragma unroll
     for (int q = 0; q < Q; ++q)
@@ -181,46 +312,38 @@ __device__ void csr_solve(const CsrSolve &s, int quad0, int k, int K, int t_begi
     for (int c = 0; c < s.n_colours; ++c) {
       int lo, hi;
       own_range(s.class_start[c], s.class_start[c + 1], k, K, lo, hi);
+      const int ob = STAGED ? ocls[c] : lo;  // row slot of vertex lo
       for (int v = lo + threadIdx.x; v < hi; v += blockDim.x) {
-        const int p0 = __ldg(&s.rowptr[v]), p1 = __ldg(&s.rowptr[v + 1]);
-        const uint32_t ov = (uint32_t)__ldg(&s.orig[v]);
+        const int i = ob + (v - lo);
+        const int p0 = adj.row[i], p1 = adj.row[i + 1];
+        const uint32_t ov = (uint32_t)adj.orig[i];
+        int32_t kk[Q][4];
+        fields<Q, MODE>(spin, n, v, p0, p1, adj, kk);
 #pragma unroll
         for (int q = 0; q < Q; ++q) {
-          const uint32_t sv = spin[q * n + v];
-          int32_t h[4] = {0, 0, 0, 0};
-          for (int p = p0; p < p1; ++p) {
-            const uint32_t su = spin[q * n + __ldg(&s.col[p])];
-            const int32_t wv = __ldg(&s.wt[p]);
-#pragma unroll
-            for (int l = 0; l < 4; ++l) h[l] += wv * lane8(su, l);
-          }
-          // half energy change kk = -s h per lane; lanes with kk > 0 are uphill
-          int32_t kk[4];
+          // lanes with kk > 0 are uphill; the rest are always taken
           uint32_t up = 0u;
 #pragma unroll
-          for (int l = 0; l < 4; ++l) {
-            kk[l] = -lane8(sv, l) * h[l];
-            up |= (kk[l] > 0 ? 1u : 0u) << l;
-          }
-          uint32_t acc = ~up & 0xFu;  // downhill and level moves are always taken
+          for (int l = 0; l < 4; ++l) up |= (kk[q][l] > 0 ? 1u : 0u) << l;
+          uint32_t acc = ~up & 0xFu;
           if (up != 0u) {
             const uint4 u =
                 philox10(make_uint4(ov, (uint32_t)t, (uint32_t)(quad0 + q), kTagSweep), key);
-            if ((up & 1u) && u.x < __ldg(&row[kk[0]])) acc |= 1u;
-            if ((up & 2u) && u.y < __ldg(&row[kk[1]])) acc |= 2u;
-            if ((up & 4u) && u.z < __ldg(&row[kk[2]])) acc |= 4u;
-            if ((up & 8u) && u.w < __ldg(&row[kk[3]])) acc |= 8u;
+            if ((up & 1u) && u.x < row[kk[q][0]]) acc |= 1u;
+            if ((up & 2u) && u.y < row[kk[q][1]]) acc |= 2u;
+            if ((up & 4u) && u.z < row[kk[q][2]]) acc |= 4u;
+            if ((up & 8u) && u.w < row[kk[q][3]]) acc |= 8u;
           }
           uint32_t flip = 0u;
 #pragma unroll
           for (int l = 0; l < 4; ++l) {
             if ((acc >> l) & 1u) {
               flip |= 0xFEu << (8 * l);
-              de[q][l] += 2 * kk[l];
+              de[q][l] += 2 * kk[q][l];
             }
           }
           if (flip) {
-            const uint32_t sn = sv ^ flip;
+            const uint32_t sn = spin[q * n + v] ^ flip;
             if (K == 1) {
               spin[q * n + v] = sn;
             } else {
@@ -299,7 +422,7 @@ __device__ void csr_solve(const CsrSolve &s, int quad0, int k, int K, int t_begi
   }
 }
 
-template <int Q>
+template <int Q, int MODE, bool STAGED>
 __global__ void __launch_bounds__(512) csr_kernel(CsrSolve s, CsrLaunch l) {
   extern __shared__ __align__(16) uint8_t smem[];
   const int K = l.cluster;
@@ -312,7 +435,7 @@ __global__ void __launch_bounds__(512) csr_kernel(CsrSolve s, CsrLaunch l) {
       if (s.hit[q] >= 0 && s.hit[q] < m) m = s.hit[q];
     if (m != INT_MAX && m + 1 < t_end) t_end = m + 1;
   }
-  csr_solve<Q>(s, quad0, k, K, l.t_begin, t_end, l.resume, smem);
+  csr_solve<Q, MODE, STAGED>(s, l, quad0, k, K, l.t_begin, t_end, l.resume, smem);
 }
 
 template <typename Kern>
@@ -344,6 +467,7 @@ __global__ void __launch_bounds__(512) csr_batch_kernel(const CsrBatchItem *item
   extern __shared__ __align__(16) uint8_t smem[];
   __shared__ int item;
   const int count = *count_dev;
+  const CsrLaunch none = {};
   for (;;) {
     if (threadIdx.x == 0) item = atomicAdd(next, 1);
     __syncthreads();
@@ -351,28 +475,42 @@ __global__ void __launch_bounds__(512) csr_batch_kernel(const CsrBatchItem *item
     __syncthreads();
     if (it >= count) break;
     const CsrBatchItem u = items[order[it]];
-    csr_solve<1>(u.solve, u.quad, 0, 1, u.t_begin, u.t_end, u.resume, smem);
+    // field mode is per instance: dispatch (uniform across the CTA)
+    if (u.solve.mode == 0)
+      csr_solve<1, 0, false>(u.solve, none, u.quad, 0, 1, u.t_begin, u.t_end, u.resume, smem);
+    else if (u.solve.mode == 1)
+      csr_solve<1, 1, false>(u.solve, none, u.quad, 0, 1, u.t_begin, u.t_end, u.resume, smem);
+    else
+      csr_solve<1, 2, false>(u.solve, none, u.quad, 0, 1, u.t_begin, u.t_end, u.resume, smem);
     __syncthreads();
   }
 }
 
 }  // namespace
 
-size_t csr_smem_bytes(int32_t n, int32_t quads_per_cta, int32_t cluster) {
-  return csr_layout(n, quads_per_cta, cluster).total;
+size_t csr_smem_bytes(int32_t n, int32_t quads_per_cta, int32_t cluster, int32_t n_colours,
+                      int32_t own_n, int32_t own_nnz, int32_t mode, int32_t kmax) {
+  const int trow_n = (kmax + 1 <= kCsrTableCache) ? kmax + 1 : 0;
+  return csr_layout(n, quads_per_cta, cluster, n_colours, own_n, own_nnz, mode == 2, trow_n)
+      .total;
 }
 
 cudaError_t csr_launch(const CsrSolve &s, const CsrLaunch &l, cudaStream_t stream) {
   const int Q = l.quads_per_cta;
-  const size_t smem = csr_smem_bytes(s.n, Q, l.cluster);
+  const bool staged = l.own_n > 0;
+  const size_t smem = csr_smem_bytes(s.n, Q, l.cluster, s.n_colours, staged ? l.own_n : 0,
+                                     staged ? l.own_nnz : 0, s.mode, s.kmax);
   const int groups = (s.quads + Q - 1) / Q;
   const int grid = groups * l.cluster;
-  switch (Q) {
-    case 1: return launch_csr(csr_kernel<1>, grid, s, l, smem, stream);
-    case 2: return launch_csr(csr_kernel<2>, grid, s, l, smem, stream);
-    case 4: return launch_csr(csr_kernel<4>, grid, s, l, smem, stream);
-    default: return cudaErrorInvalidValue;
-  }
+#define ISG_CSR_CASE(QV, MV, SV)                                                    \
+  if (Q == QV && s.mode == MV && staged == SV)                                      \
+    return launch_csr(csr_kernel<QV, MV, SV>, grid, s, l, smem, stream);
+  ISG_CSR_CASE(1, 0, true) ISG_CSR_CASE(1, 1, true) ISG_CSR_CASE(1, 2, true)
+  ISG_CSR_CASE(1, 0, false) ISG_CSR_CASE(1, 1, false) ISG_CSR_CASE(1, 2, false)
+  ISG_CSR_CASE(2, 0, true) ISG_CSR_CASE(2, 1, true) ISG_CSR_CASE(2, 2, true)
+  ISG_CSR_CASE(2, 0, false) ISG_CSR_CASE(2, 1, false) ISG_CSR_CASE(2, 2, false)
+#undef ISG_CSR_CASE
+  return cudaErrorInvalidValue;
 }
 
 cudaError_t csr_batch_launch(const CsrBatchItem *items_dev, const int32_t *count_dev,

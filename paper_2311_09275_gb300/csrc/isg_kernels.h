@@ -104,6 +104,7 @@ struct CsrSolve {
   int32_t *done;               // [quads]
   int32_t has_target;
   int32_t target;
+  int32_t mode;                // weights: 0 all +1, 1 all +-1 (col bit 31 = -1), 2 general
 };
 
 struct CsrLaunch {
@@ -112,10 +113,16 @@ struct CsrLaunch {
   int32_t stop_from_hits;
   int32_t cluster;             // CTAs sharing one quad (each holds a full copy)
   int32_t threads;
-  int32_t quads_per_cta;       // replica quads one CTA carries (1..8)
+  int32_t quads_per_cta;       // replica quads one CTA carries (1 or 2)
+  int32_t own_n, own_nnz;      // largest owned slice of any rank; 0 = adjacency not staged
 };
 
-size_t csr_smem_bytes(int32_t n, int32_t quads_per_cta, int32_t cluster);
+// Threshold entries cached in shared memory per sweep (larger tables are read
+// from global memory).
+constexpr int kCsrTableCache = 256;
+
+size_t csr_smem_bytes(int32_t n, int32_t quads_per_cta, int32_t cluster, int32_t n_colours,
+                      int32_t own_n, int32_t own_nnz, int32_t mode, int32_t kmax);
 cudaError_t csr_launch(const CsrSolve &s, const CsrLaunch &l, cudaStream_t stream);
 
 // Work unit: one replica quad of one instance, one CTA, sweeps [t_begin, t_end).

@@ -105,6 +105,20 @@ isg_status finish_problem(isg_problem *p) {
       p->wt_r[o] = p->wt[q];
     }
   }
+  // field mode of the colour-class kernel: all weights +1, all +-1 (the sign
+  // rides in bit 31 of the relabelled neighbour id), or general; the packed
+  // per-lane counts of the first two need degrees <= 255
+  bool all_pos = true, all_unit = true;
+  int64_t max_deg = 0;
+  for (int32_t v = 0; v < p->n; ++v) max_deg = std::max<int64_t>(max_deg, p->rowptr[v + 1] - p->rowptr[v]);
+  for (int32_t w : p->wt) {
+    all_pos &= (w == 1);
+    all_unit &= (w == 1 || w == -1);
+  }
+  p->mode = max_deg > 255 ? 2 : (all_pos ? 0 : (all_unit ? 1 : 2));
+  if (p->mode == 1)
+    for (size_t o = 0; o < p->col_r.size(); ++o)
+      if (p->wt_r[o] < 0) p->col_r[o] = (int32_t)((uint32_t)p->col_r[o] | 0x80000000u);
   return ISG_OK;
 }
 
@@ -389,9 +403,9 @@ void csr_shape(int quads, int max_class, int &cluster, int &threads) {
 
 namespace {
 
-// Measured shapes: (device, torus?, L or n, W or nnz, units) -> (cluster, threads)
+// Measured shapes: (device, torus?, L or n, W or nnz, units) -> (cluster, threads, quads/CTA)
 std::mutex g_shape_mu;
-std::map<std::array<int64_t, 5>, std::pair<int, int>> g_shapes;
+std::map<std::array<int64_t, 5>, std::array<int, 3>> g_shapes;
 
 std::array<int64_t, 5> shape_key(const isg_problem *p, int units) {
   int dev = 0;
@@ -399,13 +413,38 @@ std::array<int64_t, 5> shape_key(const isg_problem *p, int units) {
   return {dev, p->torus ? 1 : 0, p->torus ? p->L : p->n, p->torus ? p->W : p->rowptr[p->n], units};
 }
 
-bool shape_lookup(const isg_problem *p, int units, int &cluster, int &threads) {
+bool shape_lookup(const isg_problem *p, int units, int &cluster, int &threads, int &qpc) {
   std::lock_guard<std::mutex> lock(g_shape_mu);
   auto it = g_shapes.find(shape_key(p, units));
   if (it == g_shapes.end()) return false;
-  cluster = it->second.first;
-  threads = it->second.second;
+  cluster = it->second[0];
+  threads = it->second[1];
+  qpc = it->second[2];
   return true;
+}
+
+// Owned-slice sizes of the colour-class kernel under a cluster split: the
+// largest number of vertices and of adjacency entries any rank owns.
+void csr_own_sizes(const isg_problem *p, int K, int &own_n, int &own_nnz) {
+  own_n = own_nnz = 0;
+  for (int k = 0; k < K; ++k) {
+    int64_t nv = 0, ne = 0;
+    for (int32_t c = 0; c < p->n_colours; ++c) {
+      const int64_t a = p->class_start[c], len = p->class_start[c + 1] - a;
+      const int64_t lo = a + len * k / K, hi = a + len * (k + 1) / K;
+      nv += hi - lo;
+      ne += p->rowptr_r[hi] - p->rowptr_r[lo];
+    }
+    own_n = std::max<int>(own_n, (int)nv);
+    own_nnz = std::max<int>(own_nnz, (int)ne);
+  }
+}
+
+// Shared memory of the colour-class kernel; staged = adjacency in shared memory.
+size_t csr_bytes(const isg_problem *p, int qpc, int K, bool staged) {
+  int own_n = 0, own_nnz = 0;
+  if (staged) csr_own_sizes(p, K, own_n, own_nnz);
+  return csr_smem_bytes(p->n, qpc, K, p->n_colours, own_n, own_nnz, p->mode, p->kmax);
 }
 
 int max_class_size(const isg_problem *p) {
@@ -462,17 +501,22 @@ CsrSolve make_csr_solve(const isg_problem *p, const DeviceProblem *dp, const isg
   s.done = r->d_done;
   s.has_target = has_target;
   s.target = has_target ? (int32_t)target : 0;
+  s.mode = p->mode;
   return s;
 }
 
 // Enqueue the sweeps [0, S) of a prepared result under the given shape:
 // one persistent launch, or one launch per sweep (plain); with a target and
 // several independently scheduled units, a second pass replays every unit to
-// the earliest unit's stop sweep.
+// the earliest unit's stop sweep.  Colour-class launches stage the owned
+// adjacency in shared memory whenever it fits.
 cudaError_t launch_sweeps(const isg_problem *p, const DeviceProblem *dp, isg_result *r,
                           uint64_t seed, bool has_target, int64_t target, bool plain, int cluster,
-                          int threads, int S, cudaStream_t stream, int &launches) {
+                          int threads, int qpc, int S, cudaStream_t stream, int &launches) {
   cudaError_t err = cudaSuccess;
+  int own_n = 0, own_nnz = 0;
+  if (!r->msc && csr_bytes(p, qpc, cluster, true) <= 227 * 1024)
+    csr_own_sizes(p, cluster, own_n, own_nnz);
   const int passes = (has_target && r->units > 1) ? 2 : 1;
   for (int pass = 0; pass < passes && err == cudaSuccess; ++pass) {
     const int first = plain ? 0 : -1;
@@ -497,7 +541,9 @@ cudaError_t launch_sweeps(const isg_problem *p, const DeviceProblem *dp, isg_res
         l.stop_from_hits = pass == 1;
         l.cluster = cluster;
         l.threads = threads;
-        l.quads_per_cta = 1;
+        l.quads_per_cta = qpc;
+        l.own_n = own_n;
+        l.own_nnz = own_nnz;
         err = csr_launch(s, l, stream);
       }
       ++launches;
@@ -562,17 +608,21 @@ isg_status anneal_impl(const isg_problem *p, int32_t R, const double *betas, int
     return fail(ISG_EINVAL, "target energy outside the int32 range");
 
   // launch shape: explicit, else measured (isg_autotune), else the default rule
+  if (o.quads_per_cta < 0 || o.quads_per_cta > 2)
+    return fail(ISG_EINVAL, "quads_per_cta must be 0, 1 or 2");
   const int units = msc ? (R + 31) / 32 : (R + 3) / 4;
-  int cluster = plain ? 1 : o.cluster_ctas, threads = o.threads;
-  if (!plain && cluster == 0 && threads == 0) shape_lookup(p, units, cluster, threads);
+  int cluster = plain ? 1 : o.cluster_ctas, threads = o.threads, qpc = o.quads_per_cta;
+  if (!plain && cluster == 0 && threads == 0 && qpc == 0)
+    shape_lookup(p, units, cluster, threads, qpc);
+  if (qpc <= 0 || plain) qpc = 1;
   if (msc) {
     torus_shape(p->L, p->W, units, cluster, threads);
     if (cluster > p->L) cluster = p->L;
     if (torus_smem_bytes(p->L, p->W, cluster) > 227 * 1024)
       return fail(ISG_EINVAL, "torus %dx%d needs more shared memory than a CTA has", p->L, p->W);
   } else {
-    csr_shape(units, max_class_size(p), cluster, threads);
-    if (csr_smem_bytes(p->n, 1, cluster) > 227 * 1024)
+    csr_shape((units + qpc - 1) / qpc, max_class_size(p), cluster, threads);
+    if (csr_bytes(p, qpc, cluster, false) > 227 * 1024)
       return fail(ISG_EINVAL, "instance with n = %d needs more shared memory than a CTA has",
                   p->n);
   }
@@ -608,14 +658,14 @@ isg_status anneal_impl(const isg_problem *p, int32_t R, const double *betas, int
     result_free(r);
     return cuda_fail(err, "preparing the solve");
   }
-  r->ctas = (msc ? r->units : r->units) * cluster;
+  r->ctas = (msc ? r->units : (r->units + qpc - 1) / qpc) * cluster;
   r->cluster = cluster;
   r->threads = threads;
 
   int launches = 0;
   if (r->timed) err = cudaEventRecord(r->t0, stream);
   if (err == cudaSuccess)
-    err = launch_sweeps(p, dp, r, seed, has_target, target, plain, cluster, threads, S, stream,
+    err = launch_sweeps(p, dp, r, seed, has_target, target, plain, cluster, threads, qpc, S, stream,
                         launches);
   const int sweep_launches = launches;
   if (r->timed && err == cudaSuccess) err = cudaEventRecord(r->t1, stream);
@@ -677,12 +727,14 @@ isg_status autotune_impl(const isg_problem *p, int32_t R, int32_t probe, cudaStr
   const int units = r->units;
   const int max_class = msc ? 0 : max_class_size(p);
   float best_ms = 1e30f;
-  int best_cluster = 0, best_threads = 0;
+  int best_cluster = 0, best_threads = 0, best_qpc = 1;
   const int thread_opts[] = {128, 192, 256, 384, 512};
+  for (int qpc = 1; qpc <= (msc ? 1 : 2) && err == cudaSuccess; ++qpc)
   for (int cluster = 1; cluster <= 16 && err == cudaSuccess; ++cluster) {
     if (msc && (cluster > p->L || torus_smem_bytes(p->L, p->W, cluster) > 227 * 1024)) continue;
-    if (!msc && csr_smem_bytes(p->n, 1, cluster) > 227 * 1024) continue;
-    if (cluster > 1 && units * cluster > 4 * sm_count()) continue;
+    if (!msc && csr_bytes(p, qpc, cluster, false) > 227 * 1024) continue;
+    const int groups = msc ? units : (units + qpc - 1) / qpc;
+    if (cluster > 1 && groups * cluster > 4 * sm_count()) continue;
     for (int threads : thread_opts) {
       if (msc) {
         if (torus_sites_per_thread(p->L, p->W, cluster, threads) * 4 >= 1024) continue;
@@ -692,11 +744,12 @@ isg_status autotune_impl(const isg_problem *p, int32_t R, int32_t probe, cudaStr
       }
       int launches = 0;
       // untimed warm launch, then one timed launch of the probe
-      cudaError_t e = launch_sweeps(p, dp, r, 1, false, 0, false, cluster, threads, probe, stream,
-                                    launches);
+      cudaError_t e = launch_sweeps(p, dp, r, 1, false, 0, false, cluster, threads, qpc, probe,
+                                    stream, launches);
       if (e == cudaSuccess) e = cudaEventRecord(e0, stream);
       if (e == cudaSuccess)
-        e = launch_sweeps(p, dp, r, 1, false, 0, false, cluster, threads, probe, stream, launches);
+        e = launch_sweeps(p, dp, r, 1, false, 0, false, cluster, threads, qpc, probe, stream,
+                          launches);
       if (e == cudaSuccess) e = cudaEventRecord(e1, stream);
       if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
       if (e != cudaSuccess) {
@@ -714,6 +767,7 @@ isg_status autotune_impl(const isg_problem *p, int32_t R, int32_t probe, cudaStr
         best_ms = ms;
         best_cluster = cluster;
         best_threads = threads;
+        best_qpc = qpc;
       }
     }
   }
@@ -727,13 +781,14 @@ isg_status autotune_impl(const isg_problem *p, int32_t R, int32_t probe, cudaStr
   if (best_cluster == 0) return fail(ISG_EINVAL, "no launch shape fits this instance");
   {
     std::lock_guard<std::mutex> lock(g_shape_mu);
-    g_shapes[shape_key(p, units)] = {best_cluster, best_threads};
+    g_shapes[shape_key(p, units)] = {best_cluster, best_threads, best_qpc};
   }
   if (best) {
     best->kernel = msc ? ISG_KERNEL_TORUS_MSC : ISG_KERNEL_CSR;
     best->cluster_ctas = best_cluster;
     best->threads = best_threads;
     best->time_kernels = 0;
+    best->quads_per_cta = msc ? 0 : best_qpc;
   }
   return ISG_OK;
 }

@@ -41,6 +41,7 @@ struct isg_problem {
   int32_t n = 0, L = 0, W = 0;
   int64_t m = 0, total_weight = 0;
   int32_t kmax = 0;                        // max_i sum_j |w_ij|
+  int32_t mode = 2;                        // weights: 0 all +1, 1 all +-1, 2 general (CsrSolve)
   std::vector<int8_t> jr, jd;              // torus couplings
   std::vector<int64_t> rowptr;             // CSR, original ids, rows sorted
   std::vector<int32_t> col, wt;

@@ -268,6 +268,7 @@ void fill_csr_unit(CsrBatchItem &it, const Slot *sl, int32_t quad, int32_t t_beg
   s.done = r->d_done;
   s.has_target = r->has_target;
   s.target = r->has_target ? (int32_t)sl->rq.target : 0;
+  s.mode = p->mode;
   it.quad = quad;
   it.t_begin = t_begin;
   it.t_end = t_end;
@@ -296,7 +297,7 @@ cudaError_t run_units(isg_server *s, const std::vector<Slot *> &slots,
       } else {
         fill_csr_unit(s->h_c[ic], sl, u, sl->t, t_end[k]);
         ord_c.emplace_back(p->n, (int32_t)ic++);
-        smem_c = std::max(smem_c, csr_smem_bytes(p->n, 1, 1));
+        smem_c = std::max(smem_c, csr_smem_bytes(p->n, 1, 1, p->n_colours, 0, 0, p->mode, p->kmax));
       }
     }
   }
@@ -509,7 +510,8 @@ isg_status isg_server_submit(isg_server *s, const isg_problem *p, int32_t replic
   if (st != ISG_OK) return st;
   if (target_energy != ISG_NO_TARGET && (target_energy < INT32_MIN || target_energy > INT32_MAX))
     return fail(ISG_EINVAL, "target energy outside the int32 range");
-  if (p->torus ? (p->n / 2 + 255) / 256 > 127 : csr_smem_bytes(p->n, 1, 1) > 227 * 1024)
+  if (p->torus ? (p->n / 2 + 255) / 256 > 127
+                : csr_smem_bytes(p->n, 1, 1, p->n_colours, 0, 0, p->mode, p->kmax) > 227 * 1024)
     return fail(ISG_EINVAL, "instance too large for the served kernels");
   if (p->torus && torus_batch_max_smem(p->L, p->W) > 227 * 1024)
     return fail(ISG_EINVAL, "torus too large for the served kernels");

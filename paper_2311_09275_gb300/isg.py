@@ -33,7 +33,7 @@ _i32, _i64, _u64, _dbl, _sz = ctypes.c_int32, ctypes.c_int64, ctypes.c_uint64, c
 
 class isg_options(ctypes.Structure):
     _fields_ = [("kernel", _i32), ("cluster_ctas", _i32), ("threads", _i32),
-                ("time_kernels", _i32)]
+                ("time_kernels", _i32), ("quads_per_cta", _i32)]
 
 
 class isg_stats(ctypes.Structure):
@@ -228,9 +228,10 @@ class Result:
 
 
 def isg_anneal(p, replicas: int, betas, seed: int, target=None, stream=None, kernel: int = 0,
-               cluster_ctas: int = 0, threads: int = 0, time_kernels: bool = False) -> Result:
+               cluster_ctas: int = 0, threads: int = 0, time_kernels: bool = False,
+               quads_per_cta: int = 0) -> Result:
     b = _arr(betas, np.float64)
-    opts = isg_options(kernel, cluster_ctas, threads, 1 if time_kernels else 0)
+    opts = isg_options(kernel, cluster_ctas, threads, 1 if time_kernels else 0, quads_per_cta)
     out = _P()
     _check(_lib.isg_anneal_ex(_h(p), int(replicas), _ptr(b), int(b.shape[0]),
                               int(seed) & 0xFFFFFFFFFFFFFFFF,
@@ -244,7 +245,8 @@ def isg_autotune(p, replicas: int, probe_sweeps: int = 64, stream=None) -> dict:
     best = isg_options()
     _check(_lib.isg_autotune(_h(p), int(replicas), int(probe_sweeps), _stream(stream),
                              ctypes.byref(best)))
-    return {"kernel": best.kernel, "cluster_ctas": best.cluster_ctas, "threads": best.threads}
+    return {"kernel": best.kernel, "cluster_ctas": best.cluster_ctas, "threads": best.threads,
+            "quads_per_cta": best.quads_per_cta}
 
 
 def isg_anneal_batch(problems, replicas: int, betas, seeds, targets=None, stream=None):
