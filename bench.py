@@ -527,7 +527,7 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--config", default="torus", choices=["torus", "random", "batch", "served"])
     ap.add_argument("--requests", type=int, default=2000, help="served: number of requests")
-    ap.add_argument("--slots", type=int, default=256, help="served: maximum resident requests")
+    ap.add_argument("--slots", type=int, default=512, help="served: maximum resident requests")
     ap.add_argument("--chunk", type=int, default=250, help="served: sweeps per chunk")
     ap.add_argument("--mem-gb", type=int, default=32, help="served: device memory budget (GB)")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")

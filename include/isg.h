@@ -102,15 +102,17 @@ void isg_problem_destroy(isg_problem *p);
 
 /* ---------------------------------------------------------------- annealing */
 
-/* Kernel families.  AUTO picks the multi-spin-coded torus kernel for tori and
- * the CSR colour-class kernel otherwise; PLAIN runs one kernel launch per
- * sweep (state kept in device memory between launches), the one-instance-per-
- * launch baseline of the batched form. */
+/* Kernel families.  AUTO picks the multi-spin-coded torus kernel for tori,
+ * the multi-spin-coded graph kernel for graphs whose weights are all +1 or -1
+ * and whose degrees are <= 63, and the int8 CSR colour-class kernel otherwise;
+ * PLAIN runs one kernel launch per sweep (state kept in device memory between
+ * launches), the one-instance-per-launch baseline of the batched form. */
 typedef enum {
     ISG_KERNEL_AUTO = 0,
     ISG_KERNEL_TORUS_MSC = 1,
     ISG_KERNEL_CSR = 2,
-    ISG_KERNEL_PLAIN = 3
+    ISG_KERNEL_PLAIN = 3,
+    ISG_KERNEL_GRAPH_MSC = 4
 } isg_kernel;
 
 typedef struct {
@@ -217,10 +219,12 @@ void isg_result_destroy(isg_result *r);
 
 /* A continuous-batching annealing server on the current device.  Requests
  * are admitted while a slot is free and their device state fits in
- * device_mem_budget bytes; admitted requests run together in chunks of
- * sweeps_per_chunk sweeps of one persistent kernel; each runs until its
- * target or its sweep budget.  A request's result equals isg_anneal of the
- * same arguments, bit for bit.  max_slots >= 1, sweeps_per_chunk >= 1. */
+ * device_mem_budget bytes; admitted requests run together in chunks of one
+ * persistent kernel launch; each runs until its target or its sweep budget.
+ * A chunk gives every request the same work: sweeps_per_chunk sweeps for a
+ * 10,000-spin instance, proportionally more for smaller ones (at least 1).
+ * A request's result equals isg_anneal of the same arguments, bit for bit.
+ * max_slots >= 1, sweeps_per_chunk >= 1. */
 isg_status isg_server_create(size_t device_mem_budget, int32_t max_slots,
                              int32_t sweeps_per_chunk, isg_server **out);
 

@@ -21,6 +21,20 @@ __global__ void unpack_msc_kernel(const uint32_t *__restrict__ words, int n, int
   }
 }
 
+// out[r][orig[v]] = bit (r mod 32) of words[r / 32][v] ? +1 : -1.
+__global__ void unpack_msc_relabel_kernel(const uint32_t *__restrict__ words, int n, int R,
+                                          const int32_t *__restrict__ orig,
+                                          int8_t *__restrict__ out) {
+  const int64_t total = (int64_t)n * R;
+  for (int64_t x = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; x < total;
+       x += (int64_t)gridDim.x * blockDim.x) {
+    const int r = (int)(x / n);
+    const int v = (int)(x - (int64_t)r * n);
+    const uint32_t w = words[(size_t)(r >> 5) * n + v];
+    out[(size_t)r * n + orig[v]] = ((w >> (r & 31)) & 1u) ? 1 : -1;
+  }
+}
+
 // out[r][orig[v]] = byte (r mod 4) of quads[r / 4][v] (int8 +1/-1).
 __global__ void unpack_quads_kernel(const uint32_t *__restrict__ quads, int n, int R,
                                     const int32_t *__restrict__ orig, int8_t *__restrict__ out) {
@@ -111,6 +125,13 @@ int grid_for(int64_t total, int threads) {
 cudaError_t unpack_msc(const uint32_t *words, int32_t n, int32_t R, int8_t *out,
                        cudaStream_t stream) {
   unpack_msc_kernel<<<grid_for((int64_t)n * R, 256), 256, 0, stream>>>(words, n, R, out);
+  return cudaGetLastError();
+}
+
+cudaError_t unpack_msc_relabel(const uint32_t *words, int32_t n, int32_t R, const int32_t *orig,
+                               int8_t *out, cudaStream_t stream) {
+  unpack_msc_relabel_kernel<<<grid_for((int64_t)n * R, 256), 256, 0, stream>>>(words, n, R, orig,
+                                                                               out);
   return cudaGetLastError();
 }
 

@@ -150,6 +150,32 @@ struct SlicedCounter {
   // Adds the 2-bit per-lane value (x1 x0).
   __device__ __forceinline__ void add2(uint32_t x0, uint32_t x1) { add3(x0, x1, 0u); }
 
+  // Adds 2^b to the lanes set in x (a carry enters at plane b).
+  __device__ __forceinline__ void add_at(int b, uint32_t x) {
+    uint32_t c = x;
+#pragma unroll
+    for (int k = 0; k < NP; ++k) {
+      if (k >= b) {
+        const uint32_t cc = p[k] & c;
+        p[k] ^= c;
+        c = cc;
+      }
+    }
+  }
+
+  // Adds the per-lane value whose bit-slices are a[0..NA-1].
+  template <int NA>
+  __device__ __forceinline__ void add_sliced(const uint32_t (&a)[NA]) {
+    uint32_t c = 0u;
+#pragma unroll
+    for (int k = 0; k < NP; ++k) {
+      const uint32_t ak = k < NA ? a[k] : 0u;
+      const uint32_t s = p[k] ^ ak ^ c;
+      c = (p[k] & ak) | (c & (p[k] ^ ak));
+      p[k] = s;
+    }
+  }
+
   // Sum over the warp's 32 threads of the count of bit position `lane`
   // (returned in that lane).  Must be called by all 32 lanes.
   __device__ __forceinline__ int32_t warp_lane_total() const {

@@ -136,7 +136,67 @@ cudaError_t csr_batch_launch(const CsrBatchItem *items_dev, const int32_t *count
                              const int32_t *order_dev, int32_t *next_dev, int32_t ctas,
                              int32_t threads, size_t smem, cudaStream_t stream);
 
+// ---------------------------------------------------------------- graphs, multi-spin coded
+// +-1-weighted graphs of degree <= 63: replica words like the torus kernel,
+// vertices relabelled colour-major like the colour-class kernel.  State
+// arrays are [word][n] in relabelled order.
+struct GraphMscSolve {
+  int32_t n;
+  int32_t n_colours;
+  const int32_t *class_start;  // [n_colours + 1]
+  const int32_t *rowptr;       // [n + 1]
+  const int32_t *col;          // relabelled neighbour ids, bit 31 set for weight -1
+  const int32_t *orig;         // [n]
+  const uint32_t *table;       // [sweeps][kmax1]: thresholds by half energy change k
+  int32_t kmax1;               // kmax + 1 (<= 64)
+  uint32_t key0, key1;
+  RoundKeys rk;
+  int32_t words;
+  int32_t replicas;
+  uint32_t *spins;             // [words][n]
+  uint32_t *best;              // [words][n]
+  int32_t *e_cur;              // [words*32]
+  int32_t *e_best;             // [words*32]
+  int32_t *hit;                // [words]
+  int32_t *done;               // [words]
+  int32_t has_target;
+  int32_t target;
+};
+
+struct GraphMscLaunch {
+  int32_t t_begin, t_end;
+  int32_t resume;
+  int32_t stop_from_hits;
+  int32_t cluster;             // CTAs sharing one word (each holds a full copy)
+  int32_t threads;
+  int32_t own_n, own_nnz;      // largest owned slice of any rank; 0 = adjacency not staged
+  int32_t planes;              // bit planes of the energy counters (6..14)
+};
+
+// Bit planes of the persistent unit kernel's energy counters: a unit's
+// (vertices per thread per sweep) x (max degree) must stay below 2^12.
+constexpr int kGraphMscBatchPlanes = 12;
+
+struct GraphMscItem {
+  GraphMscSolve solve;
+  int32_t word;
+  int32_t t_begin, t_end;
+  int32_t resume;
+};
+
+size_t gm_smem_bytes(int32_t n, int32_t cluster, int32_t n_colours, int32_t own_n,
+                     int32_t own_nnz, int32_t kmax1);
+// Smallest supported plane count holding counts up to max_count (-1: none).
+int gm_planes(int32_t max_count);
+cudaError_t gm_launch(const GraphMscSolve &s, const GraphMscLaunch &l, cudaStream_t stream);
+cudaError_t gm_batch_launch(const GraphMscItem *items_dev, const int32_t *count_dev,
+                            const int32_t *order_dev, int32_t *next_dev, int32_t ctas,
+                            int32_t threads, size_t smem, cudaStream_t stream);
+
 // ---------------------------------------------------------------- auxiliary kernels
+// Unpack words [words][n] in relabelled order into int8 [R][n] caller order.
+cudaError_t unpack_msc_relabel(const uint32_t *words, int32_t n, int32_t R, const int32_t *orig,
+                               int8_t *out, cudaStream_t stream);
 // Unpack multi-spin words [words][n] into int8 [R][n] (+1/-1).
 cudaError_t unpack_msc(const uint32_t *words, int32_t n, int32_t R, int8_t *out,
                        cudaStream_t stream);

@@ -116,6 +116,7 @@ isg_status finish_problem(isg_problem *p) {
     all_unit &= (w == 1 || w == -1);
   }
   p->mode = max_deg > 255 ? 2 : (all_pos ? 0 : (all_unit ? 1 : 2));
+  p->dmax = (int32_t)max_deg;
   if (p->mode == 1)
     for (size_t o = 0; o < p->col_r.size(); ++o)
       if (p->wt_r[o] < 0) p->col_r[o] = (int32_t)((uint32_t)p->col_r[o] | 0x80000000u);
@@ -403,23 +404,27 @@ void csr_shape(int quads, int max_class, int &cluster, int &threads) {
 
 namespace {
 
-// Measured shapes: (device, torus?, L or n, W or nnz, units) -> (cluster, threads, quads/CTA)
+// Measured choices: (device, torus?, L or n, W or nnz, replicas)
+//   -> (kernel, cluster, threads, quads/CTA)
 std::mutex g_shape_mu;
-std::map<std::array<int64_t, 5>, std::array<int, 3>> g_shapes;
+std::map<std::array<int64_t, 5>, std::array<int, 4>> g_shapes;
 
-std::array<int64_t, 5> shape_key(const isg_problem *p, int units) {
+std::array<int64_t, 5> shape_key(const isg_problem *p, int replicas) {
   int dev = 0;
   cudaGetDevice(&dev);
-  return {dev, p->torus ? 1 : 0, p->torus ? p->L : p->n, p->torus ? p->W : p->rowptr[p->n], units};
+  return {dev, p->torus ? 1 : 0, p->torus ? p->L : p->n, p->torus ? p->W : p->rowptr[p->n],
+          replicas};
 }
 
-bool shape_lookup(const isg_problem *p, int units, int &cluster, int &threads, int &qpc) {
+bool shape_lookup(const isg_problem *p, int replicas, int &kernel, int &cluster, int &threads,
+                  int &qpc) {
   std::lock_guard<std::mutex> lock(g_shape_mu);
-  auto it = g_shapes.find(shape_key(p, units));
+  auto it = g_shapes.find(shape_key(p, replicas));
   if (it == g_shapes.end()) return false;
-  cluster = it->second[0];
-  threads = it->second[1];
-  qpc = it->second[2];
+  kernel = it->second[0];
+  cluster = it->second[1];
+  threads = it->second[2];
+  qpc = it->second[3];
   return true;
 }
 
@@ -452,6 +457,36 @@ int max_class_size(const isg_problem *p) {
   for (int32_t c = 0; c < p->n_colours; ++c)
     m = std::max(m, p->class_start[c + 1] - p->class_start[c]);
   return m;
+}
+
+// The multi-spin graph kernel needs +-1 weights and degrees <= 63.
+bool graph_msc_ok(const isg_problem *p) { return p->mode <= 1 && p->dmax <= 63; }
+
+// Shared memory of the graph kernel; staged = adjacency in shared memory.
+size_t gm_bytes(const isg_problem *p, int K, bool staged) {
+  int own_n = 0, own_nnz = 0;
+  if (staged) csr_own_sizes(p, K, own_n, own_nnz);
+  return gm_smem_bytes(p->n, K, p->n_colours, own_n, own_nnz, p->kmax + 1);
+}
+
+// Energy-counter planes of the graph kernel: a thread's accepted degree sum
+// per sweep is at most (its vertices per sweep) x (max degree).
+int gm_planes_for(const isg_problem *p, int K, int threads) {
+  int own_n = 0, own_nnz = 0;
+  csr_own_sizes(p, K, own_n, own_nnz);
+  const int64_t per_thread = (own_n + threads - 1) / threads + p->n_colours;
+  const int64_t cnt = per_thread * std::max(1, p->dmax);
+  return cnt >= (1 << 30) ? -1 : gm_planes((int32_t)cnt);
+}
+
+void gm_shape(const isg_problem *p, int words, int &cluster, int &threads) {
+  const int sms = sm_count();
+  if (cluster <= 0) {
+    cluster = 1;
+    while (cluster < 16 && words * cluster * 2 <= sms && max_class_size(p) / (cluster * 2) >= 64)
+      cluster *= 2;
+  }
+  if (threads <= 0) threads = 256;
 }
 
 TorusSolve make_torus_solve(const isg_problem *p, const DeviceProblem *dp, const isg_result *r,
@@ -505,6 +540,33 @@ CsrSolve make_csr_solve(const isg_problem *p, const DeviceProblem *dp, const isg
   return s;
 }
 
+GraphMscSolve make_gm_solve(const isg_problem *p, const DeviceProblem *dp, const isg_result *r,
+                            uint64_t seed, bool has_target, int64_t target) {
+  GraphMscSolve s = {};
+  s.n = p->n;
+  s.n_colours = p->n_colours;
+  s.class_start = dp->class_start;
+  s.rowptr = dp->rowptr;
+  s.col = dp->col;
+  s.orig = dp->orig;
+  s.table = r->d_table;
+  s.kmax1 = p->kmax + 1;
+  s.key0 = (uint32_t)(seed & 0xFFFFFFFFu);
+  s.key1 = (uint32_t)(seed >> 32);
+  s.rk = round_keys(s.key0, s.key1);
+  s.words = r->units;
+  s.replicas = r->R;
+  s.spins = r->d_spins;
+  s.best = r->d_best;
+  s.e_cur = r->d_e_cur;
+  s.e_best = r->d_e_best;
+  s.hit = r->d_hit;
+  s.done = r->d_done;
+  s.has_target = has_target;
+  s.target = has_target ? (int32_t)target : 0;
+  return s;
+}
+
 // Enqueue the sweeps [0, S) of a prepared result under the given shape:
 // one persistent launch, or one launch per sweep (plain); with a target and
 // several independently scheduled units, a second pass replays every unit to
@@ -514,15 +576,34 @@ cudaError_t launch_sweeps(const isg_problem *p, const DeviceProblem *dp, isg_res
                           uint64_t seed, bool has_target, int64_t target, bool plain, int cluster,
                           int threads, int qpc, int S, cudaStream_t stream, int &launches) {
   cudaError_t err = cudaSuccess;
-  int own_n = 0, own_nnz = 0;
+  const bool gm = r->msc && r->relabelled;
+  int own_n = 0, own_nnz = 0, planes = 0;
   if (!r->msc && csr_bytes(p, qpc, cluster, true) <= 227 * 1024)
     csr_own_sizes(p, cluster, own_n, own_nnz);
+  if (gm) {
+    if (gm_bytes(p, cluster, true) <= 227 * 1024) csr_own_sizes(p, cluster, own_n, own_nnz);
+    planes = gm_planes_for(p, cluster, threads);
+    if (planes < 0) return cudaErrorInvalidConfiguration;
+  }
   const int passes = (has_target && r->units > 1) ? 2 : 1;
   for (int pass = 0; pass < passes && err == cudaSuccess; ++pass) {
     const int first = plain ? 0 : -1;
     for (int t = first; t < (plain ? S : 0) && err == cudaSuccess; ++t) {
       const int t0 = plain ? t : 0, t1 = plain ? t + 1 : S;
-      if (r->msc) {
+      if (gm) {
+        GraphMscSolve s = make_gm_solve(p, dp, r, seed, has_target && pass == 0, target);
+        GraphMscLaunch l = {};
+        l.t_begin = t0;
+        l.t_end = t1;
+        l.resume = t0 > 0;
+        l.stop_from_hits = pass == 1;
+        l.cluster = cluster;
+        l.threads = threads;
+        l.own_n = own_n;
+        l.own_nnz = own_nnz;
+        l.planes = planes;
+        err = gm_launch(s, l, stream);
+      } else if (r->msc) {
         TorusSolve s = make_torus_solve(p, dp, r, seed, has_target && pass == 0, target);
         TorusLaunch l = {};
         l.t_begin = t0;
@@ -568,9 +649,11 @@ isg_result *new_result(const isg_problem *p, int32_t R, int32_t S, bool msc, boo
   return r;
 }
 
-void table_levels(const isg_problem *p, bool msc, std::vector<int32_t> &levels) {
+// Threshold levels (half energy changes k) a kernel reads: the torus kernel
+// only k = 2 and 4, the graph kernels every k = 0..kmax.
+void table_levels(const isg_problem *p, bool torus_words, std::vector<int32_t> &levels) {
   levels.clear();
-  if (msc) {
+  if (torus_words) {
     levels = {2, 4};
   } else {
     for (int32_t k = 0; k <= p->kmax; ++k) levels.push_back(k);
@@ -578,6 +661,14 @@ void table_levels(const isg_problem *p, bool msc, std::vector<int32_t> &levels) 
 }
 
 }  // namespace
+
+// The persistent graph-unit kernel runs a whole replica word in one CTA: it
+// needs +-1 weights, degree <= 63, and counts that fit its fixed counter planes.
+bool served_graph_msc(const isg_problem *p, int threads) {
+  if (!graph_msc_ok(p)) return false;
+  const int64_t per_thread = (p->n + threads - 1) / threads + p->n_colours;
+  return per_thread * std::max(1, p->dmax) < (int64_t(1) << kGraphMscBatchPlanes);
+}
 
 // ------------------------------------------------------------------ anneal
 
@@ -592,13 +683,25 @@ isg_status anneal_impl(const isg_problem *p, int32_t R, const double *betas, int
   isg_options o = {};
   if (opts) o = *opts;
   int kernel = o.kernel;
-  if (kernel == ISG_KERNEL_AUTO) kernel = p->torus ? ISG_KERNEL_TORUS_MSC : ISG_KERNEL_CSR;
-  if (kernel < ISG_KERNEL_AUTO || kernel > ISG_KERNEL_PLAIN)
+  // AUTO with no explicit shape: the autotuner's measured choice if there is one
+  int t_kernel = 0, t_cluster = 0, t_threads = 0, t_qpc = 0;
+  const bool tuned = kernel == ISG_KERNEL_AUTO && o.cluster_ctas == 0 && o.threads == 0 &&
+                     o.quads_per_cta == 0 &&
+                     shape_lookup(p, R, t_kernel, t_cluster, t_threads, t_qpc);
+  if (tuned) kernel = t_kernel;
+  if (kernel == ISG_KERNEL_AUTO)
+    kernel = p->torus ? ISG_KERNEL_TORUS_MSC
+                      : (graph_msc_ok(p) ? ISG_KERNEL_GRAPH_MSC : ISG_KERNEL_CSR);
+  if (kernel < ISG_KERNEL_AUTO || kernel > ISG_KERNEL_GRAPH_MSC)
     return fail(ISG_EINVAL, "unknown kernel %d", kernel);
   if (kernel == ISG_KERNEL_TORUS_MSC && !p->torus)
-    return fail(ISG_EINVAL, "the multi-spin-coded kernel needs a torus instance");
+    return fail(ISG_EINVAL, "the multi-spin-coded torus kernel needs a torus instance");
+  if (kernel == ISG_KERNEL_GRAPH_MSC && !graph_msc_ok(p))
+    return fail(ISG_EINVAL, "the multi-spin-coded graph kernel needs weights +-1 and degree <= 63");
   const bool plain = kernel == ISG_KERNEL_PLAIN;
-  const bool msc = p->torus && (kernel == ISG_KERNEL_TORUS_MSC || plain);
+  const bool gm = kernel == ISG_KERNEL_GRAPH_MSC;
+  const bool tmsc = p->torus && (kernel == ISG_KERNEL_TORUS_MSC || plain);
+  const bool msc = tmsc || gm;  // 32-lane replica words
   if (o.cluster_ctas < 0 || o.cluster_ctas > 16)
     return fail(ISG_EINVAL, "cluster_ctas must be in [0, 16]");
   if (o.threads != 0 && (o.threads < 32 || o.threads > 512 || o.threads % 32))
@@ -612,14 +715,24 @@ isg_status anneal_impl(const isg_problem *p, int32_t R, const double *betas, int
     return fail(ISG_EINVAL, "quads_per_cta must be 0, 1 or 2");
   const int units = msc ? (R + 31) / 32 : (R + 3) / 4;
   int cluster = plain ? 1 : o.cluster_ctas, threads = o.threads, qpc = o.quads_per_cta;
-  if (!plain && cluster == 0 && threads == 0 && qpc == 0)
-    shape_lookup(p, units, cluster, threads, qpc);
+  if (tuned) {
+    cluster = t_cluster;
+    threads = t_threads;
+    qpc = t_qpc;
+  }
   if (qpc <= 0 || plain) qpc = 1;
-  if (msc) {
+  if (tmsc) {
     torus_shape(p->L, p->W, units, cluster, threads);
     if (cluster > p->L) cluster = p->L;
     if (torus_smem_bytes(p->L, p->W, cluster) > 227 * 1024)
       return fail(ISG_EINVAL, "torus %dx%d needs more shared memory than a CTA has", p->L, p->W);
+  } else if (gm) {
+    gm_shape(p, units, cluster, threads);
+    if (gm_bytes(p, cluster, false) > 227 * 1024)
+      return fail(ISG_EINVAL, "instance with n = %d needs more shared memory than a CTA has",
+                  p->n);
+    if (gm_planes_for(p, cluster, threads) < 0)
+      return fail(ISG_EINVAL, "too many vertices per thread for the graph kernel's counters");
   } else {
     csr_shape((units + qpc - 1) / qpc, max_class_size(p), cluster, threads);
     if (csr_bytes(p, qpc, cluster, false) > 227 * 1024)
@@ -628,13 +741,14 @@ isg_status anneal_impl(const isg_problem *p, int32_t R, const double *betas, int
   }
 
   const DeviceProblem *dp = nullptr;
-  st = problem_device(p, msc ? kNeedTorus : kNeedCsr, &dp);
+  st = problem_device(p, tmsc ? kNeedTorus : kNeedCsr, &dp);
   if (st != ISG_OK) return st;
 
   isg_result *r = new_result(p, R, S, msc, has_target, stream);
-  r->kernel = plain ? ISG_KERNEL_PLAIN : (msc ? ISG_KERNEL_TORUS_MSC : ISG_KERNEL_CSR);
+  r->relabelled = !tmsc;
+  r->kernel = kernel;
   std::vector<int32_t> levels;
-  table_levels(p, msc, levels);
+  table_levels(p, tmsc, levels);
   std::vector<uint32_t> table;
   build_table(betas, S, levels, table);
   r->table_words = table.size();
@@ -674,9 +788,13 @@ isg_status anneal_impl(const isg_problem *p, int32_t R, const double *betas, int
     ++launches;
   }
   if (err == cudaSuccess) {
-    if (msc) {
+    if (tmsc) {
       err = unpack_msc(r->d_spins, p->n, R, r->d_out, stream);
       if (err == cudaSuccess) err = unpack_msc(r->d_best, p->n, R, r->d_out_best, stream);
+    } else if (gm) {
+      err = unpack_msc_relabel(r->d_spins, p->n, R, dp->orig, r->d_out, stream);
+      if (err == cudaSuccess)
+        err = unpack_msc_relabel(r->d_best, p->n, R, dp->orig, r->d_out_best, stream);
     } else {
       err = unpack_quads(r->d_spins, p->n, R, dp->orig, r->d_out, stream);
       if (err == cudaSuccess) err = unpack_quads(r->d_best, p->n, R, dp->orig, r->d_out_best, stream);
@@ -701,12 +819,26 @@ isg_status autotune_impl(const isg_problem *p, int32_t R, int32_t probe, cudaStr
                          isg_options *best) {
   if (!p) return fail(ISG_EINVAL, "problem must not be NULL");
   if (R < 1 || probe < 1) return fail(ISG_EINVAL, "replicas and probe_sweeps must be >= 1");
-  const bool msc = p->torus;
+  // candidate kernel families: the torus kernel for tori; for +-1 graphs both
+  // the multi-spin graph kernel and the int8 colour-class kernel
+  std::vector<int> kernels;
+  if (p->torus)
+    kernels = {ISG_KERNEL_TORUS_MSC};
+  else if (graph_msc_ok(p))
+    kernels = {ISG_KERNEL_GRAPH_MSC, ISG_KERNEL_CSR};
+  else
+    kernels = {ISG_KERNEL_CSR};
+  float best_ms = 1e30f;
+  int best_kernel = 0, best_cluster = 0, best_threads = 0, best_qpc = 1;
+  for (const int kernel : kernels) {
+  const bool msc = kernel == ISG_KERNEL_TORUS_MSC;  // torus words
+  const bool gm = kernel == ISG_KERNEL_GRAPH_MSC;   // graph words
   const DeviceProblem *dp = nullptr;
   isg_status st = problem_device(p, msc ? kNeedTorus : kNeedCsr, &dp);
   if (st != ISG_OK) return st;
   // scratch solve at a mid-schedule temperature (both torus thresholds non-zero)
-  isg_result *r = new_result(p, R, probe, msc, false, stream);
+  isg_result *r = new_result(p, R, probe, msc || gm, false, stream);
+  r->relabelled = !msc;
   std::vector<int32_t> levels;
   table_levels(p, msc, levels);
   std::vector<double> betas(probe, 1.0);
@@ -726,20 +858,21 @@ isg_status autotune_impl(const isg_problem *p, int32_t R, int32_t probe, cudaStr
                           stream);
   const int units = r->units;
   const int max_class = msc ? 0 : max_class_size(p);
-  float best_ms = 1e30f;
-  int best_cluster = 0, best_threads = 0, best_qpc = 1;
   const int thread_opts[] = {128, 192, 256, 384, 512};
-  for (int qpc = 1; qpc <= (msc ? 1 : 2) && err == cudaSuccess; ++qpc)
+  for (int qpc = 1; qpc <= (msc || gm ? 1 : 2) && err == cudaSuccess; ++qpc)
   for (int cluster = 1; cluster <= 16 && err == cudaSuccess; ++cluster) {
     if (msc && (cluster > p->L || torus_smem_bytes(p->L, p->W, cluster) > 227 * 1024)) continue;
-    if (!msc && csr_bytes(p, qpc, cluster, false) > 227 * 1024) continue;
-    const int groups = msc ? units : (units + qpc - 1) / qpc;
+    if (gm && gm_bytes(p, cluster, false) > 227 * 1024) continue;
+    if (!msc && !gm && csr_bytes(p, qpc, cluster, false) > 227 * 1024) continue;
+    const int groups = msc || gm ? units : (units + qpc - 1) / qpc;
     if (cluster > 1 && groups * cluster > 4 * sm_count()) continue;
     for (int threads : thread_opts) {
       if (msc) {
         if (torus_sites_per_thread(p->L, p->W, cluster, threads) * 4 >= 1024) continue;
         if (torus_max_active_clusters(p->L, p->W, units, cluster, threads) < 1) continue;
       } else if (threads > round_up((max_class + cluster - 1) / cluster, 32) + 32) {
+        continue;
+      } else if (gm && gm_planes_for(p, cluster, threads) < 0) {
         continue;
       }
       int launches = 0;
@@ -765,6 +898,7 @@ isg_status autotune_impl(const isg_problem *p, int32_t R, int32_t probe, cudaStr
       cudaEventElapsedTime(&ms, e0, e1);
       if (ms < best_ms) {
         best_ms = ms;
+        best_kernel = kernel;
         best_cluster = cluster;
         best_threads = threads;
         best_qpc = qpc;
@@ -778,17 +912,18 @@ isg_status autotune_impl(const isg_problem *p, int32_t R, int32_t probe, cudaStr
   r->base = nullptr;
   delete r;
   if (err != cudaSuccess) return cuda_fail(err, "autotuning");
+  }  // kernel families
   if (best_cluster == 0) return fail(ISG_EINVAL, "no launch shape fits this instance");
   {
     std::lock_guard<std::mutex> lock(g_shape_mu);
-    g_shapes[shape_key(p, units)] = {best_cluster, best_threads, best_qpc};
+    g_shapes[shape_key(p, R)] = {best_kernel, best_cluster, best_threads, best_qpc};
   }
   if (best) {
-    best->kernel = msc ? ISG_KERNEL_TORUS_MSC : ISG_KERNEL_CSR;
+    best->kernel = best_kernel;
     best->cluster_ctas = best_cluster;
     best->threads = best_threads;
     best->time_kernels = 0;
-    best->quads_per_cta = msc ? 0 : best_qpc;
+    best->quads_per_cta = best_kernel == ISG_KERNEL_CSR ? best_qpc : 0;
   }
   return ISG_OK;
 }

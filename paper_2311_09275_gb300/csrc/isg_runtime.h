@@ -42,6 +42,7 @@ struct isg_problem {
   int64_t m = 0, total_weight = 0;
   int32_t kmax = 0;                        // max_i sum_j |w_ij|
   int32_t mode = 2;                        // weights: 0 all +1, 1 all +-1, 2 general (CsrSolve)
+  int32_t dmax = 0;                        // largest degree
   std::vector<int8_t> jr, jd;              // torus couplings
   std::vector<int64_t> rowptr;             // CSR, original ids, rows sorted
   std::vector<int32_t> col, wt;
@@ -62,7 +63,8 @@ struct isg_result {
   int32_t n = 0, R = 0, S = 0;
   bool has_target = false;
   int32_t kernel = 0;
-  bool msc = false;
+  bool msc = false;                        // 32-lane replica words (torus or graph kernel)
+  bool relabelled = false;                 // state in colour-major vertex order
   int32_t units = 0, lanes = 0;            // replica words (32 lanes) or quads (4 lanes)
   size_t table_words = 0;
   void *base = nullptr;                    // one device allocation holding everything
@@ -95,5 +97,6 @@ isg_status result_sync(const isg_result *r);
 void result_free(isg_result *r);
 int sm_count();
 void torus_shape(int L, int W, int words, int &cluster, int &threads);
+bool served_graph_msc(const isg_problem *p, int threads);
 
 }  // namespace isg

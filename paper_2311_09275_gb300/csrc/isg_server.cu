@@ -55,16 +55,18 @@ struct Slot {
   bool finished = false;
 };
 
+constexpr int kServeThreads = 256;
+
 size_t state_bytes_of(const isg_result *r) {
   // spins, best, e_cur, e_best are the leading, contiguous part of the allocation
   return (size_t)((char *)r->d_hit - (char *)r->base);
 }
 
 size_t request_bytes(const isg_problem *p, int32_t R, int32_t S) {
-  const bool msc = p->torus;
+  const bool msc = p->torus || served_graph_msc(p, kServeThreads);
   const size_t units = msc ? (R + 31) / 32 : (R + 3) / 4;
   const size_t lanes = units * (msc ? 32 : 4);
-  const size_t levels = msc ? 2 : (size_t)p->kmax + 1;
+  const size_t levels = p->torus ? 2 : (size_t)p->kmax + 1;
   auto al = [](size_t x) { return (x + 255) & ~size_t(255); };
   size_t b = 2 * al(4 * units * p->n) + 2 * al(4 * lanes) + 2 * al(4 * units) + al(4) +
              2 * al((size_t)R * p->n) + al(4 * levels * S);
@@ -92,11 +94,14 @@ struct isg_server {
   cudaStream_t stream = nullptr;
   std::vector<Slot *> active;
   size_t used = 0;
-  size_t cap_t = 0, cap_c = 0;
+  size_t cap_t = 0, cap_c = 0, cap_g = 0;
+  GraphMscItem *d_g = nullptr, *h_g = nullptr;
+  int32_t *d_ord_g = nullptr, *h_ord_g = nullptr;
   TorusBatchItem *d_t = nullptr, *h_t = nullptr;
   CsrBatchItem *d_c = nullptr, *h_c = nullptr;
   int32_t *d_ord_t = nullptr, *h_ord_t = nullptr, *d_ord_c = nullptr, *h_ord_c = nullptr;
-  int32_t *d_ctl = nullptr, *h_ctl = nullptr;  // [0] next_t, [1] next_c, [2] count_t, [3] count_c
+  // [0] next_t, [1] next_c, [2] count_t, [3] count_c, [4] next_g, [5] count_g
+  int32_t *d_ctl = nullptr, *h_ctl = nullptr;
   int32_t *h_status = nullptr;                 // per unit: hit, done
   size_t cap_status = 0;
   isg_status worker_error = ISG_OK;
@@ -105,8 +110,21 @@ struct isg_server {
 namespace isg {
 namespace {
 
-cudaError_t grow(isg_server *s, size_t nt, size_t nc, size_t nstatus) {
+cudaError_t grow(isg_server *s, size_t nt, size_t nc, size_t nstatus, size_t ng = 0) {
   cudaError_t err = cudaSuccess;
+  if (ng > s->cap_g) {
+    const size_t cap = std::max(ng, 2 * s->cap_g);
+    cudaFree(s->d_g);
+    cudaFreeHost(s->h_g);
+    cudaFree(s->d_ord_g);
+    cudaFreeHost(s->h_ord_g);
+    err = cudaMalloc(&s->d_g, sizeof(GraphMscItem) * cap);
+    if (err == cudaSuccess) err = cudaMallocHost(&s->h_g, sizeof(GraphMscItem) * cap);
+    if (err == cudaSuccess) err = cudaMalloc(&s->d_ord_g, 4 * cap);
+    if (err == cudaSuccess) err = cudaMallocHost(&s->h_ord_g, 4 * cap);
+    if (err != cudaSuccess) return err;
+    s->cap_g = cap;
+  }
   if (nt > s->cap_t) {
     const size_t cap = std::max(nt, 2 * s->cap_t);
     cudaFree(s->d_t);
@@ -163,12 +181,16 @@ void admit(isg_server *s) {
     r->R = sl->rq.R;
     r->S = sl->rq.S;
     r->has_target = sl->rq.target != ISG_NO_TARGET;
-    r->msc = p->torus;
-    r->kernel = r->msc ? ISG_KERNEL_TORUS_MSC : ISG_KERNEL_CSR;
+    // graphs with +-1 weights whose units fit the unit kernel's counters run
+    // multi-spin coded (one unit per 32 replicas), other graphs as int8 quads
+    const bool gm = !p->torus && served_graph_msc(p, kServeThreads);
+    r->msc = p->torus || gm;
+    r->relabelled = !p->torus;
+    r->kernel = p->torus ? ISG_KERNEL_TORUS_MSC : (gm ? ISG_KERNEL_GRAPH_MSC : ISG_KERNEL_CSR);
     r->units = r->msc ? (r->R + 31) / 32 : (r->R + 3) / 4;
     r->lanes = r->msc ? 32 : 4;
     std::vector<int32_t> levels;
-    if (r->msc)
+    if (p->torus)
       levels = {2, 4};
     else
       for (int32_t k = 0; k <= p->kmax; ++k) levels.push_back(k);
@@ -275,25 +297,63 @@ void fill_csr_unit(CsrBatchItem &it, const Slot *sl, int32_t quad, int32_t t_beg
   it.resume = t_begin > 0;
 }
 
+void fill_gm_unit(GraphMscItem &it, const Slot *sl, int32_t word, int32_t t_begin, int32_t t_end) {
+  const isg_result *r = sl->res;
+  const isg_problem *p = sl->rq.p;
+  GraphMscSolve &s = it.solve;
+  s = {};
+  s.n = p->n;
+  s.n_colours = p->n_colours;
+  s.class_start = sl->dp->class_start;
+  s.rowptr = sl->dp->rowptr;
+  s.col = sl->dp->col;
+  s.orig = sl->dp->orig;
+  s.table = r->d_table;
+  s.kmax1 = p->kmax + 1;
+  s.key0 = (uint32_t)(sl->rq.seed & 0xFFFFFFFFu);
+  s.key1 = (uint32_t)(sl->rq.seed >> 32);
+  s.rk = round_keys(s.key0, s.key1);
+  s.words = r->units;
+  s.replicas = r->R;
+  s.spins = r->d_spins;
+  s.best = r->d_best;
+  s.e_cur = r->d_e_cur;
+  s.e_best = r->d_e_best;
+  s.hit = r->d_hit;
+  s.done = r->d_done;
+  s.has_target = r->has_target;
+  s.target = r->has_target ? (int32_t)sl->rq.target : 0;
+  it.word = word;
+  it.t_begin = t_begin;
+  it.t_end = t_end;
+  it.resume = t_begin > 0;
+}
+
 // One launch of the unit kernels over the listed slots, sweeps [t, t_end) each.
 cudaError_t run_units(isg_server *s, const std::vector<Slot *> &slots,
                       const std::vector<int32_t> &t_end) {
-  size_t nt = 0, nc = 0;
-  for (size_t k = 0; k < slots.size(); ++k)
-    (slots[k]->res->msc ? nt : nc) += slots[k]->res->units;
-  cudaError_t err = grow(s, nt, nc, 0);
+  size_t nt = 0, nc = 0, ng = 0;
+  for (size_t k = 0; k < slots.size(); ++k) {
+    const isg_result *r = slots[k]->res;
+    (r->msc ? (r->relabelled ? ng : nt) : nc) += r->units;
+  }
+  cudaError_t err = grow(s, nt, nc, 0, ng);
   if (err != cudaSuccess) return err;
-  size_t it = 0, ic = 0;
-  size_t smem_t = 0, smem_c = 0;
-  std::vector<std::pair<int32_t, int32_t>> ord_t, ord_c;  // (size, index)
+  size_t it = 0, ic = 0, ig = 0;
+  size_t smem_t = 0, smem_c = 0, smem_g = 0;
+  std::vector<std::pair<int32_t, int32_t>> ord_t, ord_c, ord_g;  // (size, index)
   for (size_t k = 0; k < slots.size(); ++k) {
     Slot *sl = slots[k];
     const isg_problem *p = sl->rq.p;
     for (int32_t u = 0; u < sl->res->units; ++u) {
-      if (sl->res->msc) {
+      if (sl->res->msc && !sl->res->relabelled) {
         fill_torus_unit(s->h_t[it], sl, u, sl->t, t_end[k]);
         ord_t.emplace_back(p->n, (int32_t)it++);
         smem_t = std::max(smem_t, torus_batch_max_smem(p->L, p->W));
+      } else if (sl->res->msc) {
+        fill_gm_unit(s->h_g[ig], sl, u, sl->t, t_end[k]);
+        ord_g.emplace_back(p->n, (int32_t)ig++);
+        smem_g = std::max(smem_g, gm_smem_bytes(p->n, 1, p->n_colours, 0, 0, p->kmax + 1));
       } else {
         fill_csr_unit(s->h_c[ic], sl, u, sl->t, t_end[k]);
         ord_c.emplace_back(p->n, (int32_t)ic++);
@@ -306,13 +366,17 @@ cudaError_t run_units(isg_server *s, const std::vector<Slot *> &slots,
   };
   std::sort(ord_t.begin(), ord_t.end(), by_size);
   std::sort(ord_c.begin(), ord_c.end(), by_size);
+  std::sort(ord_g.begin(), ord_g.end(), by_size);
   for (size_t k = 0; k < ord_t.size(); ++k) s->h_ord_t[k] = ord_t[k].second;
   for (size_t k = 0; k < ord_c.size(); ++k) s->h_ord_c[k] = ord_c[k].second;
+  for (size_t k = 0; k < ord_g.size(); ++k) s->h_ord_g[k] = ord_g[k].second;
   s->h_ctl[0] = 0;
   s->h_ctl[1] = 0;
   s->h_ctl[2] = (int32_t)nt;
   s->h_ctl[3] = (int32_t)nc;
-  const int threads = 256;
+  s->h_ctl[4] = 0;
+  s->h_ctl[5] = (int32_t)ng;
+  const int threads = kServeThreads;
   if (nt) {
     err = cudaMemcpyAsync(s->d_t, s->h_t, sizeof(TorusBatchItem) * nt, cudaMemcpyHostToDevice,
                           s->stream);
@@ -325,20 +389,27 @@ cudaError_t run_units(isg_server *s, const std::vector<Slot *> &slots,
     if (err == cudaSuccess)
       err = cudaMemcpyAsync(s->d_ord_c, s->h_ord_c, 4 * nc, cudaMemcpyHostToDevice, s->stream);
   }
+  if (err == cudaSuccess && ng) {
+    err = cudaMemcpyAsync(s->d_g, s->h_g, sizeof(GraphMscItem) * ng, cudaMemcpyHostToDevice,
+                          s->stream);
+    if (err == cudaSuccess)
+      err = cudaMemcpyAsync(s->d_ord_g, s->h_ord_g, 4 * ng, cudaMemcpyHostToDevice, s->stream);
+  }
   if (err == cudaSuccess)
-    err = cudaMemcpyAsync(s->d_ctl, s->h_ctl, 16, cudaMemcpyHostToDevice, s->stream);
-  if (err == cudaSuccess && nt) {
-    const int per_sm = std::max(1, std::min<int>(4, (int)((228 * 1024) / (smem_t + 1024))));
-    const int ctas = (int)std::min<size_t>(nt, (size_t)sm_count() * per_sm);
-    err = torus_batch_launch(s->d_t, s->d_ctl + 2, s->d_ord_t, s->d_ctl + 0, ctas, threads, smem_t,
-                             s->stream);
-  }
-  if (err == cudaSuccess && nc) {
-    const int per_sm = std::max(1, std::min<int>(4, (int)((228 * 1024) / (smem_c + 1024))));
-    const int ctas = (int)std::min<size_t>(nc, (size_t)sm_count() * per_sm);
-    err = csr_batch_launch(s->d_c, s->d_ctl + 3, s->d_ord_c, s->d_ctl + 1, ctas, threads, smem_c,
-                           s->stream);
-  }
+    err = cudaMemcpyAsync(s->d_ctl, s->h_ctl, 24, cudaMemcpyHostToDevice, s->stream);
+  auto ctas_for = [](size_t units, size_t smem) {
+    const int per_sm = std::max(1, std::min<int>(4, (int)((228 * 1024) / (smem + 1024))));
+    return (int)std::min<size_t>(units, (size_t)sm_count() * per_sm);
+  };
+  if (err == cudaSuccess && nt)
+    err = torus_batch_launch(s->d_t, s->d_ctl + 2, s->d_ord_t, s->d_ctl + 0, ctas_for(nt, smem_t),
+                             threads, smem_t, s->stream);
+  if (err == cudaSuccess && ng)
+    err = gm_batch_launch(s->d_g, s->d_ctl + 5, s->d_ord_g, s->d_ctl + 4, ctas_for(ng, smem_g),
+                          threads, smem_g, s->stream);
+  if (err == cudaSuccess && nc)
+    err = csr_batch_launch(s->d_c, s->d_ctl + 3, s->d_ord_c, s->d_ctl + 1, ctas_for(nc, smem_c),
+                           threads, smem_c, s->stream);
   for (Slot *sl : slots) sl->res->sweep_launches += 1;
   return err;
 }
@@ -349,9 +420,13 @@ cudaError_t finish_slot(isg_server *s, Slot *sl) {
   int32_t *stop_host = &sl->stop;
   err = cudaMemcpyAsync(r->d_stop, stop_host, 4, cudaMemcpyHostToDevice, s->stream);
   if (err == cudaSuccess) {
-    if (r->msc) {
+    if (r->msc && !r->relabelled) {
       err = unpack_msc(r->d_spins, r->n, r->R, r->d_out, s->stream);
       if (err == cudaSuccess) err = unpack_msc(r->d_best, r->n, r->R, r->d_out_best, s->stream);
+    } else if (r->msc) {
+      err = unpack_msc_relabel(r->d_spins, r->n, r->R, sl->dp->orig, r->d_out, s->stream);
+      if (err == cudaSuccess)
+        err = unpack_msc_relabel(r->d_best, r->n, r->R, sl->dp->orig, r->d_out_best, s->stream);
     } else {
       err = unpack_quads(r->d_spins, r->n, r->R, sl->dp->orig, r->d_out, s->stream);
       if (err == cudaSuccess)
@@ -381,7 +456,10 @@ void worker_main(isg_server *s) {
     size_t nstatus = 0;
     for (size_t k = 0; k < s->active.size(); ++k) {
       Slot *sl = s->active[k];
-      t_end[k] = std::min(sl->t + s->chunk, sl->rq.S);
+      // chunks hold equal work per unit: sweeps_per_chunk is the count for a
+      // 10,000-spin instance, scaled inversely with the instance size
+      const int64_t sweeps = std::max<int64_t>(1, (int64_t)s->chunk * 10000 / sl->rq.p->n);
+      t_end[k] = (int32_t)std::min<int64_t>(sl->t + sweeps, sl->rq.S);
       sl->t_end = t_end[k];
       nstatus += 2 * (size_t)sl->res->units;
       if (sl->snap && err == cudaSuccess)
@@ -583,6 +661,10 @@ isg_status isg_server_destroy(isg_server *s) {
   cudaFreeHost(s->h_ord_t);
   cudaFree(s->d_ord_c);
   cudaFreeHost(s->h_ord_c);
+  cudaFree(s->d_g);
+  cudaFreeHost(s->h_g);
+  cudaFree(s->d_ord_g);
+  cudaFreeHost(s->h_ord_g);
   cudaFree(s->d_ctl);
   cudaFreeHost(s->h_ctl);
   cudaFreeHost(s->h_status);

@@ -131,6 +131,54 @@ def test_graph_csr_bit_exact(isg, name, R, cluster):
     assert_same(res, orc)
 
 
+def pm1_graph():
+    g = I.random_graph(400, 1100, 8)
+    w = np.where(I.draws(8, 7, np.arange(g.m)) >> np.uint64(63), 1, -1).astype(np.int32)
+    return I.Graph(g.n, g.u, g.v, w)
+
+
+@pytest.mark.parametrize("name", ["random_sparse", "random_dense", "isolated", "pm1"])
+@pytest.mark.parametrize("R,cluster,threads", [(1, 1, 64), (33, 3, 128), (70, 8, 96), (32, 16, 64),
+                                               (64, 0, 0)])
+def test_graph_msc_bit_exact(isg, name, R, cluster, threads):
+    """Multi-spin-coded graph kernel (weights +-1, degree <= 63)."""
+    g = pm1_graph() if name == "pm1" else GRAPHS[name]()
+    betas = I.geometric_betas(0.1, 5.0, 100)
+    orc = oracle.anneal(oracle.csr_of(g), R, betas, 13, check_energy=True)
+    res = isg.isg_anneal(isg.problem_of(g), R, betas, 13, kernel=4, cluster_ctas=cluster,
+                         threads=threads)
+    assert_same(res, orc)
+    assert res.stats()["kernel"] == 4
+
+
+def test_graph_auto_kernel_choice(isg):
+    unit = isg.isg_anneal(isg.problem_of(GRAPHS["random_sparse"]()), 8, np.full(3, 1.0), 1)
+    assert unit.stats()["kernel"] == 4           # +-1 weights -> multi-spin graph kernel
+    general = isg.isg_anneal(isg.problem_of(weighted_graph()), 8, np.full(3, 1.0), 1)
+    assert general.stats()["kernel"] == 2        # general weights -> int8 colour classes
+
+
+def test_torus_via_graph_msc_equals_torus_msc(isg):
+    t = I.torus(12, 10, 21)
+    betas = I.geometric_betas(0.1, 5.0, 150)
+    a = isg.isg_anneal(isg.problem_of(t), 64, betas, 5)
+    b = isg.isg_anneal(isg.problem_of(t), 64, betas, 5, kernel=4, cluster_ctas=2)
+    for x, y in zip(a.final(), b.final()):
+        assert np.array_equal(x, y)
+    assert np.array_equal(a.best_all(), b.best_all())
+
+
+@pytest.mark.parametrize("R", [20, 70])
+def test_graph_msc_target_stop(isg, R):
+    g = I.random_graph(600, 900, 3)
+    betas = I.geometric_betas(0.1, 5.0, 300)
+    c = oracle.csr_of(g)
+    target = int(oracle.anneal(c, R, betas, 2).e_best.min()) + 2
+    orc = oracle.anneal(c, R, betas, 2, target=target)
+    res = isg.isg_anneal(isg.problem_of(g), R, betas, 2, target=target, kernel=4, cluster_ctas=2)
+    assert_same(res, orc)
+
+
 def test_graph_plain_kernel_bit_exact(isg):
     g = weighted_graph()
     betas = I.linear_betas(0.1, 3.0, 60)
