@@ -11,8 +11,8 @@ best-state tracking, result unpacking) = 8.19e10 attempts.
   e2e        the same metric through the public C ABI with HOST buffers: each
              step creates the instance from host couplings, anneals, and reads
              final spins, energies and the best state back to the host.
-  roofline   the sweep kernel's algorithmic integer-instruction rate against
-             the issue peak of the integer units (bound "alu").
+  roofline   the sweep kernel's algorithmic integer-ALU instruction rate
+             against the integer ALU pipe's peak (bound "alu").
   cpu_baseline  the CPU oracle on the host cores on a bounded replica sample.
 
 Other workloads: --config random (n = 10,000, m = 9,999 random graph, 256

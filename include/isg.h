@@ -118,7 +118,8 @@ typedef enum {
 typedef struct {
     int32_t kernel;        /* isg_kernel */
     int32_t cluster_ctas;  /* CTAs that share one replica block (1..16); 0 = tuned/default */
-    int32_t threads;       /* threads per CTA (multiple of 32, <= 512); 0 = tuned/default */
+    int32_t threads;       /* threads per CTA (multiple of 32, <= 512; <= 1024 for the
+                              torus kernel); 0 = tuned/default */
     int32_t time_kernels;  /* nonzero: time the sweep launches with CUDA events */
     int32_t quads_per_cta; /* colour-class kernel: replica quads per CTA (1, 2); 0 = tuned/default */
 } isg_options;

@@ -26,6 +26,14 @@ struct PhiloxKey {
   uint32_t k0, k1;
 };
 
+// Full 64-bit product of two 32-bit words, written as one widening multiply
+// (measured faster than separate high- and low-half multiplies).
+__device__ __forceinline__ void mul_wide(uint32_t a, uint32_t b, uint32_t &hi, uint32_t &lo) {
+  const uint64_t p = (uint64_t)a * b;
+  hi = (uint32_t)(p >> 32);
+  lo = (uint32_t)p;
+}
+
 __device__ __forceinline__ uint4 philox10(uint4 c, PhiloxKey key) {
   constexpr uint32_t kMulA = 0xD2511F53u;
   constexpr uint32_t kMulB = 0xCD9E8D57u;
@@ -34,8 +42,9 @@ __device__ __forceinline__ uint4 philox10(uint4 c, PhiloxKey key) {
   uint32_t k0 = key.k0, k1 = key.k1;
 #pragma unroll
   for (int round = 0; round < 10; ++round) {
-    const uint32_t hiA = __umulhi(kMulA, c.x), loA = kMulA * c.x;
-    const uint32_t hiB = __umulhi(kMulB, c.z), loB = kMulB * c.z;
+    uint32_t hiA, loA, hiB, loB;
+    mul_wide(kMulA, c.x, hiA, loA);
+    mul_wide(kMulB, c.z, hiB, loB);
     c = make_uint4(hiB ^ c.y ^ k0, loB, hiA ^ c.w ^ k1, loA);
     k0 += kWeylA;
     k1 += kWeylB;
@@ -62,11 +71,14 @@ struct BlockPrefix {
 };
 
 __device__ __forceinline__ BlockPrefix block_prefix(uint32_t b, uint32_t t, const RoundKeys &k) {
-  const uint32_t x0 = __umulhi(kPhiloxMulB, b) ^ t ^ k.k0[0];
+  uint32_t hb, lb, hx, lx;
+  mul_wide(kPhiloxMulB, b, hb, lb);
+  const uint32_t x0 = hb ^ t ^ k.k0[0];
+  mul_wide(kPhiloxMulA, x0, hx, lx);
   BlockPrefix r;
-  r.a = (kPhiloxMulB * b) ^ k.k0[1];
-  r.p = __umulhi(kPhiloxMulA, x0) ^ k.k1[1];
-  r.c = kPhiloxMulA * x0;
+  r.a = lb ^ k.k0[1];
+  r.p = hx ^ k.k1[1];
+  r.c = lx;
   return r;
 }
 
@@ -75,11 +87,11 @@ struct SitePrefix {
 };
 
 __device__ __forceinline__ SitePrefix site_prefix(uint32_t i, const RoundKeys &k) {
-  const uint32_t y2 = __umulhi(kPhiloxMulA, i) ^ k.k1[0];
+  uint32_t hi;
   SitePrefix r;
-  r.y3 = kPhiloxMulA * i;
-  r.hb = __umulhi(kPhiloxMulB, y2);
-  r.lb = kPhiloxMulB * y2;
+  mul_wide(kPhiloxMulA, i, hi, r.y3);
+  const uint32_t y2 = hi ^ k.k1[0];
+  mul_wide(kPhiloxMulB, y2, r.hb, r.lb);
   return r;
 }
 
@@ -89,8 +101,9 @@ __device__ __forceinline__ uint4 philox10_factored(const SitePrefix &sp, const B
   uint4 c = make_uint4(sp.hb ^ bp.a, sp.lb, bp.p ^ sp.y3, bp.c);
 #pragma unroll
   for (int round = 2; round < 10; ++round) {
-    const uint32_t hiA = __umulhi(kPhiloxMulA, c.x), loA = kPhiloxMulA * c.x;
-    const uint32_t hiB = __umulhi(kPhiloxMulB, c.z), loB = kPhiloxMulB * c.z;
+    uint32_t hiA, loA, hiB, loB;
+    mul_wide(kPhiloxMulA, c.x, hiA, loA);
+    mul_wide(kPhiloxMulB, c.z, hiB, loB);
     c = make_uint4(hiB ^ c.y ^ k.k0[round], loB, hiA ^ c.w ^ k.k1[round], loA);
   }
   return c;

@@ -704,8 +704,10 @@ isg_status anneal_impl(const isg_problem *p, int32_t R, const double *betas, int
   const bool msc = tmsc || gm;  // 32-lane replica words
   if (o.cluster_ctas < 0 || o.cluster_ctas > 16)
     return fail(ISG_EINVAL, "cluster_ctas must be in [0, 16]");
-  if (o.threads != 0 && (o.threads < 32 || o.threads > 512 || o.threads % 32))
-    return fail(ISG_EINVAL, "threads must be a multiple of 32 in [32, 512]");
+  // the torus kernel has a 64-register build for CTAs of up to 1,024 threads
+  const int max_threads = tmsc ? 1024 : 512;
+  if (o.threads != 0 && (o.threads < 32 || o.threads > max_threads || o.threads % 32))
+    return fail(ISG_EINVAL, "threads must be a multiple of 32 in [32, %d]", max_threads);
   const bool has_target = target != ISG_NO_TARGET;
   if (has_target && (target < INT32_MIN || target > INT32_MAX))
     return fail(ISG_EINVAL, "target energy outside the int32 range");
@@ -858,7 +860,8 @@ isg_status autotune_impl(const isg_problem *p, int32_t R, int32_t probe, cudaStr
                           stream);
   const int units = r->units;
   const int max_class = msc ? 0 : max_class_size(p);
-  const int thread_opts[] = {128, 192, 256, 384, 512};
+  std::vector<int> thread_opts = {128, 192, 256, 384, 512};
+  if (msc) thread_opts.insert(thread_opts.end(), {640, 768, 1024});
   for (int qpc = 1; qpc <= (msc || gm ? 1 : 2) && err == cudaSuccess; ++qpc)
   for (int cluster = 1; cluster <= 16 && err == cudaSuccess; ++cluster) {
     if (msc && (cluster > p->L || torus_smem_bytes(p->L, p->W, cluster) > 227 * 1024)) continue;

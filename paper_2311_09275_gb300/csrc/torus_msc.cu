@@ -34,18 +34,21 @@ __host__ __device__ __forceinline__ Band band_of(int L, int K, int k) {
 
 __host__ __device__ __forceinline__ size_t align16(size_t x) { return (x + 15) & ~size_t(15); }
 
+// Per-warp lane totals of the energy counters are published to every CTA of
+// the cluster: part[k][warp][lane] for up to 32 warps per CTA.
+constexpr int kMaxWarps = 32;
+
 struct SmemLayout {
-  size_t spin, cb, part, lane_acc, flags, total;
+  size_t spin, best, cb, part, total;
 };
 
 __host__ __device__ __forceinline__ SmemLayout layout_of(int nr, int W, int K) {
   SmemLayout m;
   m.spin = 0;
-  m.cb = align16(m.spin + sizeof(uint32_t) * (size_t)(nr + 2) * W);
+  m.best = m.spin + sizeof(uint32_t) * (size_t)(nr + 2) * W;
+  m.cb = m.best + sizeof(uint32_t) * (size_t)nr * W;
   m.part = align16(m.cb + (size_t)(nr + 2) * W);
-  m.lane_acc = m.part + sizeof(int32_t) * 32 * (size_t)K;
-  m.flags = m.lane_acc + sizeof(int32_t) * 32;
-  m.total = align16(m.flags + sizeof(uint32_t) * 4);
+  m.total = align16(m.part + sizeof(int32_t) * 32 * kMaxWarps * (size_t)K);
   return m;
 }
 
@@ -71,35 +74,40 @@ __device__ __forceinline__ void sync_group(int K) {
     cluster_barrier();
 }
 
-// Per-lane totals of the bit-sliced counters over the CTA, published to every
-// CTA of the cluster as part[k][lane]; ends with the group barrier.
+// Sum over the whole cluster of the bit-sliced counters, per lane (= per
+// replica of the word): every warp publishes its lane totals to every CTA of
+// the cluster, one group barrier, then every warp adds them all up itself, so
+// that no CTA-wide barrier or serial section is needed.
 template <int NP>
-__device__ __forceinline__ void publish_lane_totals(const SlicedCounter<NP> &cnt, int32_t *lane_acc,
-                                                    int32_t *part, int k, int K) {
+__device__ __forceinline__ int32_t cluster_lane_sum(const SlicedCounter<NP> &cnt, int32_t *part,
+                                                    int k, int K) {
+  const int nw = (int)(blockDim.x >> 5);
+  const int slot = (k * nw + (int)(threadIdx.x >> 5)) * 32 + (int)lane_id();
   const int32_t tot = cnt.warp_lane_total();
-  atomicAdd(&lane_acc[lane_id()], tot);
-  __syncthreads();
-  if (threadIdx.x < 32) {
-    const int32_t v = lane_acc[threadIdx.x];
-    lane_acc[threadIdx.x] = 0;
-    if (K == 1) {
-      part[threadIdx.x] = v;
-    } else {
-      for (int q = 0; q < K; ++q) peer_smem(part, (uint32_t)q)[k * 32 + threadIdx.x] = v;
-    }
+  if (K == 1) {
+    part[slot] = tot;
+  } else {
+    for (int q = 0; q < K; ++q) peer_smem(part, (uint32_t)q)[slot] = tot;
   }
   sync_group(K);
+  int32_t sum = 0;
+  for (int j = 0; j < K * nw; ++j) sum += part[j * 32 + (int)lane_id()];
+  return sum;
 }
 
 // One colour phase of one replica word: this thread's sites of colour c in
 // the CTA's band.  Acceptance masks are built by compare + predicated OR into
 // two partial accumulators (measured faster than packing 4-bit nibbles, and
 // than moving the compares onto the multiply-add pipe).
+// Replicas in `imp` improved their best energy at the end of the previous
+// sweep; their best state is taken here, site by site, from the spins as they
+// stand before this phase updates them (unchanged since that sweep's end).
 template <int NP, bool kTwoThresholds>
-__device__ __forceinline__ void sweep_phase(uint32_t *spin, const uint8_t *cb, uint32_t *up_peer,
-                                            uint32_t *down_peer, int W, int r0, int nr, int c,
-                                            const BlockPrefix (&bp)[8], const RoundKeys &rk,
-                                            uint32_t T4, uint32_t T8, SlicedCounter<NP> &cnt) {
+__device__ __forceinline__ void sweep_phase(uint32_t *spin, uint32_t *best, const uint8_t *cb,
+                                            uint32_t *up_peer, uint32_t *down_peer, int W, int r0,
+                                            int nr, int c, const BlockPrefix (&bp)[8],
+                                            const RoundKeys &rk, uint32_t T4, uint32_t T8,
+                                            uint32_t imp, SlicedCounter<NP> &cnt) {
   const int half = W >> 1;
   const int step_rows = blockDim.x / half;
   const int step_cols = blockDim.x - step_rows * half;
@@ -112,6 +120,10 @@ __device__ __forceinline__ void sweep_phase(uint32_t *spin, const uint8_t *cb, u
     const int xl = (col == 0) ? x + W - 1 : x - 1;
     const int xr = (col == W - 1) ? x - W + 1 : x + 1;
     const uint32_t s0 = spin[x];
+    if (imp != 0u) {
+      uint32_t &bx = best[x - W];
+      bx = (bx & ~imp) | (s0 & imp);
+    }
     const uint32_t cbx = cb[x];
     const uint32_t a = ~(s0 ^ spin[xr] ^ sign_mask(cbx));
     const uint32_t b = ~(s0 ^ spin[xl] ^ sign_mask(cb[xl]));
@@ -173,10 +185,9 @@ __device__ void torus_word(const TorusSolve &s, int word, int k, int K, int t_be
   // shared-memory offset means the same array in every peer
   const SmemLayout lay = layout_of((L + K - 1) / K, W, K);
   uint32_t *spin = reinterpret_cast<uint32_t *>(smem + lay.spin);
+  uint32_t *best = reinterpret_cast<uint32_t *>(smem + lay.best);  // band rows only
   uint8_t *cb = smem + lay.cb;
   int32_t *part = reinterpret_cast<int32_t *>(smem + lay.part);
-  int32_t *lane_acc = reinterpret_cast<int32_t *>(smem + lay.lane_acc);
-  volatile uint32_t *flags = reinterpret_cast<uint32_t *>(smem + lay.flags);
   const PhiloxKey key{s.key0, s.key1};
   const uint32_t uword = (uint32_t)word;
   const int rem = s.replicas - 32 * word;
@@ -197,12 +208,15 @@ __device__ void torus_word(const TorusSolve &s, int word, int k, int K, int t_be
     gr = gr < 0 ? gr + L : (gr >= L ? gr - L : gr);
     const int i = gr * W + c;
     cb[x] = s.cbits[i];
-    spin[x] = resume ? gspin[i] : initial_word((uint32_t)i, uword, key);
+    const uint32_t v = resume ? gspin[i] : initial_word((uint32_t)i, uword, key);
+    spin[x] = v;
+    if (lr >= 1 && lr <= nr) best[x - W] = resume ? gbest[i] : v;
   }
-  if (threadIdx.x < 32) lane_acc[threadIdx.x] = 0;
-  __syncthreads();
+  // peers write into this CTA's halo rows only after every CTA has loaded them
+  sync_group(K);
 
-  int32_t e = 0, e_best = 0;  // meaningful in warp 0, lane = replica bit
+  // per-lane (replica) energies, kept identically by every warp
+  int32_t e = 0, e_best = 0;
   SlicedCounter<NP> cnt;
   if (!resume) {
     // E = sum over bonds of (+1 unsatisfied, -1 satisfied) = 2 U_tot - 2n
@@ -215,17 +229,10 @@ __device__ void torus_word(const TorusSolve &s, int word, int k, int K, int t_be
       const uint32_t a = ~(s0 ^ spin[c == W - 1 ? x - W + 1 : x + 1] ^ sign_mask(cbx));
       const uint32_t d = ~(s0 ^ spin[x + W] ^ sign_mask(cbx >> 1));
       cnt.add2(a ^ d, a & d);
-      const int gr = r0 + idx / W;
-      gbest[gr * W + c] = s0;
     }
-    publish_lane_totals<NP>(cnt, lane_acc, part, k, K);
-    if (threadIdx.x < 32) {
-      int32_t tot = 0;
-      for (int q = 0; q < K; ++q) tot += part[q * 32 + lane];
-      e = 2 * tot - 2 * n;
-      e_best = e;
-    }
-  } else if (threadIdx.x < 32) {
+    e = 2 * cluster_lane_sum<NP>(cnt, part, k, K) - 2 * n;
+    e_best = e;
+  } else {
     e = s.e_cur[word * 32 + lane];
     e_best = s.e_best[word * 32 + lane];
   }
@@ -237,8 +244,15 @@ __device__ void torus_word(const TorusSolve &s, int word, int k, int K, int t_be
 
   int t = t_begin;
   int hit = -1;
+  uint32_t imp = 0u;  // replicas whose best state is the state at the start of sweep t
+  // thresholds of the next sweep are loaded one sweep ahead
+  uint32_t T4n = s.table[2 * t], T8n = s.table[2 * t + 1];
   for (; t < t_end; ++t) {
-    const uint32_t T4 = s.table[2 * t], T8 = s.table[2 * t + 1];
+    const uint32_t T4 = T4n, T8 = T8n;
+    if (t + 1 < t_end) {
+      T4n = s.table[2 * t + 2];
+      T8n = s.table[2 * t + 3];
+    }
     // the (block, sweep) part of Philox rounds 1-2, uniform across the CTA
     BlockPrefix bp[8];
 #pragma unroll
@@ -246,42 +260,34 @@ __device__ void torus_word(const TorusSolve &s, int word, int k, int K, int t_be
     cnt.clear();
     for (int c = 0; c < 2; ++c) {
       if (T8 != 0u)
-        sweep_phase<NP, true>(spin, cb, up_peer, down_peer, W, r0, nr, c, bp, s.rk, T4, T8, cnt);
+        sweep_phase<NP, true>(spin, best, cb, up_peer, down_peer, W, r0, nr, c, bp, s.rk, T4, T8,
+                              imp, cnt);
       else
-        sweep_phase<NP, false>(spin, cb, up_peer, down_peer, W, r0, nr, c, bp, s.rk, T4, T8, cnt);
+        sweep_phase<NP, false>(spin, best, cb, up_peer, down_peer, W, r0, nr, c, bp, s.rk, T4, T8,
+                               imp, cnt);
       if (c == 0) sync_group(K);
     }
-    publish_lane_totals<NP>(cnt, lane_acc, part, k, K);
-    if (threadIdx.x < 32) {
-      int32_t tot = 0;
-      for (int q = 0; q < K; ++q) tot += part[q * 32 + lane];
-      e += 4 * (tot - 2 * n);
-      const bool better = e < e_best;
-      if (better) e_best = e;
-      const uint32_t imp = __ballot_sync(0xFFFFFFFFu, better) & valid;
-      const int32_t mn = __reduce_min_sync(0xFFFFFFFFu, ((valid >> lane) & 1u) ? e_best : INT_MAX);
-      if (lane == 0) {
-        flags[0] = imp;
-        flags[1] = (s.has_target && mn <= s.target) ? 1u : 0u;
+    e += 4 * (cluster_lane_sum<NP>(cnt, part, k, K) - 2 * n);
+    const bool better = e < e_best;
+    if (better) e_best = e;
+    imp = __ballot_sync(0xFFFFFFFFu, better) & valid;
+    if (s.has_target) {
+      const int32_t mn =
+          __reduce_min_sync(0xFFFFFFFFu, ((valid >> lane) & 1u) ? e_best : INT_MAX);
+      if (mn <= s.target) {
+        hit = t;
+        ++t;
+        break;
       }
-    }
-    __syncthreads();
-    const uint32_t imp = flags[0];
-    const uint32_t stop = flags[1];
-    if (imp != 0u) {
-      for (int idx = threadIdx.x; idx < nr * W; idx += blockDim.x) {
-        const int g = r0 * W + idx;
-        gbest[g] = (gbest[g] & ~imp) | (spin[W + idx] & imp);
-      }
-    }
-    if (stop) {
-      hit = t;
-      ++t;
-      break;
     }
   }
 
-  for (int idx = threadIdx.x; idx < nr * W; idx += blockDim.x) gspin[r0 * W + idx] = spin[W + idx];
+  // every phase update of the cluster precedes the last group barrier
+  for (int idx = threadIdx.x; idx < nr * W; idx += blockDim.x) {
+    const uint32_t v = spin[W + idx];
+    gspin[r0 * W + idx] = v;
+    gbest[r0 * W + idx] = (best[idx] & ~imp) | (v & imp);
+  }
   if (k == 0) {
     if (threadIdx.x < 32) {
       s.e_cur[word * 32 + lane] = e;
@@ -294,8 +300,9 @@ __device__ void torus_word(const TorusSolve &s, int word, int k, int K, int t_be
   }
 }
 
-template <int NP>
-__global__ void __launch_bounds__(512) torus_kernel(TorusSolve s, TorusLaunch l) {
+// MAXT = 1024 caps registers at 64 per thread so that 1,024 threads fit one SM
+template <int NP, int MAXT>
+__global__ void __launch_bounds__(MAXT, 1) torus_kernel(TorusSolve s, TorusLaunch l) {
   extern __shared__ __align__(16) uint8_t smem[];
   const int K = l.cluster;
   const int k = (int)(blockIdx.x % K);
@@ -414,10 +421,17 @@ int torus_max_active_clusters(int32_t L, int32_t W, int32_t words, int32_t clust
   const int np = np_for(torus_sites_per_thread(L, W, cluster, threads),
                         (nr * W + threads - 1) / threads);
   const int grid = words * cluster;
+  const bool wide = threads > 512;
   switch (np) {
-    case 6: return max_active_clusters(torus_kernel<6>, grid, threads, smem, cluster);
-    case 8: return max_active_clusters(torus_kernel<8>, grid, threads, smem, cluster);
-    case 10: return max_active_clusters(torus_kernel<10>, grid, threads, smem, cluster);
+    case 6:
+      return wide ? max_active_clusters(torus_kernel<6, 1024>, grid, threads, smem, cluster)
+                  : max_active_clusters(torus_kernel<6, 512>, grid, threads, smem, cluster);
+    case 8:
+      return wide ? max_active_clusters(torus_kernel<8, 1024>, grid, threads, smem, cluster)
+                  : max_active_clusters(torus_kernel<8, 512>, grid, threads, smem, cluster);
+    case 10:
+      return wide ? max_active_clusters(torus_kernel<10, 1024>, grid, threads, smem, cluster)
+                  : max_active_clusters(torus_kernel<10, 512>, grid, threads, smem, cluster);
     default: return 0;
   }
 }
@@ -430,10 +444,19 @@ cudaError_t torus_launch(const TorusSolve &s, const TorusLaunch &l, cudaStream_t
   const int band_spt = (nr * s.W + l.threads - 1) / l.threads;
   const int np = np_for(spt, band_spt);
   const int grid = s.words * K;
+  if (l.threads > 1024) return cudaErrorInvalidValue;
+  const bool wide = l.threads > 512;
   switch (np) {
-    case 6: return launch_clustered(torus_kernel<6>, grid, l.threads, smem, K, stream, s, l);
-    case 8: return launch_clustered(torus_kernel<8>, grid, l.threads, smem, K, stream, s, l);
-    case 10: return launch_clustered(torus_kernel<10>, grid, l.threads, smem, K, stream, s, l);
+    case 6:
+      return wide ? launch_clustered(torus_kernel<6, 1024>, grid, l.threads, smem, K, stream, s, l)
+                  : launch_clustered(torus_kernel<6, 512>, grid, l.threads, smem, K, stream, s, l);
+    case 8:
+      return wide ? launch_clustered(torus_kernel<8, 1024>, grid, l.threads, smem, K, stream, s, l)
+                  : launch_clustered(torus_kernel<8, 512>, grid, l.threads, smem, K, stream, s, l);
+    case 10:
+      return wide
+                 ? launch_clustered(torus_kernel<10, 1024>, grid, l.threads, smem, K, stream, s, l)
+                 : launch_clustered(torus_kernel<10, 512>, grid, l.threads, smem, K, stream, s, l);
     default: return cudaErrorInvalidValue;
   }
 }

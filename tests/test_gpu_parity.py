@@ -83,6 +83,20 @@ def test_torus_nonportable_clusters_bit_exact(isg, cluster, threads):
     assert res.stats()["cluster_ctas"] == cluster
 
 
+@pytest.mark.parametrize("L,W,R,cluster,threads", [
+    (40, 50, 64, 2, 1024), (34, 22, 70, 3, 640), (80, 100, 40, 4, 1024), (20, 20, 33, 1, 768)])
+def test_torus_wide_ctas_bit_exact(isg, L, W, R, cluster, threads):
+    """The 64-register build for CTAs of more than 512 threads."""
+    t = I.torus(L, W, 7 + L)
+    betas = I.geometric_betas(0.1, 5.0, 50)
+    orc = oracle.anneal(oracle.csr_of(t), R, betas, 23, check_energy=True)
+    res = isg.isg_anneal(isg.problem_of(t), R, betas, 23, kernel=1, cluster_ctas=cluster,
+                         threads=threads)
+    assert_same(res, orc)
+    st = res.stats()
+    assert st["threads"] == threads and st["cluster_ctas"] == cluster
+
+
 @pytest.mark.parametrize("kind", ["torus", "graph"])
 def test_autotuned_shape_bit_exact(isg, kind):
     prob = I.torus(40, 30, 5) if kind == "torus" else I.random_graph(3000, 3500, 5)
