@@ -30,7 +30,7 @@ constexpr int kPlanesU = 6;  // per-lane bond counts up to 63 (degree <= 63)
 __host__ __device__ __forceinline__ size_t align16(size_t x) { return (x + 15) & ~size_t(15); }
 
 struct GmSmem {
-  size_t spin, lrow, lorig, lcol, ocls, trow, part, lane_acc, flags, total;
+  size_t spin, lrow, lorig, lcol, ocls, trow, part, lane_acc, total;
 };
 
 __host__ __device__ __forceinline__ GmSmem gm_layout(int n, int K, int n_colours, int own_n,
@@ -42,10 +42,9 @@ __host__ __device__ __forceinline__ GmSmem gm_layout(int n, int K, int n_colours
   m.lcol = align16(m.lorig + sizeof(int32_t) * (size_t)own_n);
   m.ocls = align16(m.lcol + sizeof(int32_t) * (size_t)own_nnz);
   m.trow = align16(m.ocls + sizeof(int32_t) * ((size_t)n_colours + 1));
-  m.part = align16(m.trow + sizeof(uint32_t) * (size_t)kmax1);
+  m.part = align16(m.trow + 2 * sizeof(uint32_t) * (size_t)kmax1);
   m.lane_acc = m.part + 2 * sizeof(int32_t) * 32 * (size_t)K;
-  m.flags = m.lane_acc + sizeof(int32_t) * 32;
-  m.total = align16(m.flags + sizeof(uint32_t) * 4);
+  m.total = align16(m.lane_acc + sizeof(int32_t) * 32);
   return m;
 }
 
@@ -175,7 +174,6 @@ __device__ void gm_word(const GraphMscSolve &s, const GraphMscLaunch &L, int wor
   uint32_t *trow = reinterpret_cast<uint32_t *>(smem + lay.trow);
   int32_t *part = reinterpret_cast<int32_t *>(smem + lay.part);
   int32_t *lane_acc = reinterpret_cast<int32_t *>(smem + lay.lane_acc);
-  volatile uint32_t *flags = reinterpret_cast<uint32_t *>(smem + lay.flags);
   const PhiloxKey key{s.key0, s.key1};
   const uint32_t uword = (uint32_t)word;
   const int rem = s.replicas - 32 * word;
@@ -226,9 +224,14 @@ __device__ void gm_word(const GraphMscSolve &s, const GraphMscLaunch &L, int wor
     adj = {s.rowptr, s.col, s.orig};
   }
   if (threadIdx.x < 32) lane_acc[threadIdx.x] = 0;
-  __syncthreads();
+  // threshold rows: two buffers, the next sweep's row prefetched a sweep ahead
+  if (t_begin < t_end)
+    for (int x = threadIdx.x; x < s.kmax1; x += blockDim.x)
+      trow[(t_begin & 1) * s.kmax1 + x] = s.table[(size_t)t_begin * s.kmax1 + x];
+  // peers write into this CTA's copy of the word only after every CTA has loaded it
+  sync_group(K);
 
-  int32_t e = 0, e_best = 0;  // warp 0, lane = replica bit
+  int32_t e = 0, e_best = 0;  // per lane = replica bit, kept identically by every warp
   if (!resume) {
     // E = sum over bonds of (+1 unsatisfied, -1 satisfied), each bond once
     SlicedCounter<NP> cu;
@@ -251,24 +254,27 @@ __device__ void gm_word(const GraphMscSolve &s, const GraphMscLaunch &L, int wor
     }
     const int32_t tot = 2 * cu.warp_lane_total() - __reduce_add_sync(0xFFFFFFFFu, bonds);
     publish_lanes(tot, lane_acc, part, k, K);
-    if (threadIdx.x < 32) {
-      for (int r = 0; r < K; ++r) e += part[r * 32 + lane];
-      e_best = e;
-    }
-  } else if (threadIdx.x < 32) {
+    for (int r = 0; r < K; ++r) e += part[r * 32 + lane];
+    e_best = e;
+  } else {
     e = s.e_cur[word * 32 + lane];
     e_best = s.e_best[word * 32 + lane];
   }
 
   int t = t_begin;
   int hit = -1;
+  uint32_t imp = 0u;  // replicas whose best state is the state at the start of sweep t
+  const int x0 = (int)threadIdx.x, x1 = (int)(threadIdx.x + blockDim.x);
   for (; t < t_end; ++t) {
-    const uint32_t *grow = s.table + (size_t)t * s.kmax1;
-    for (int x = threadIdx.x; x < s.kmax1; x += blockDim.x) trow[x] = grow[x];
+    const uint32_t *row = trow + (t & 1) * s.kmax1;
+    // next sweep's thresholds (kmax1 <= 64 <= 2 x threads)
+    const bool more = t + 1 < t_end;
+    const uint32_t *gnext = s.table + (size_t)(t + 1) * s.kmax1;
+    const uint32_t p0 = (more && x0 < s.kmax1) ? gnext[x0] : 0u;
+    const uint32_t p1 = (more && x1 < s.kmax1) ? gnext[x1] : 0u;
     BlockPrefix bp[8];
 #pragma unroll
     for (int q = 0; q < 8; ++q) bp[q] = block_prefix(8u * uword + (uint32_t)q, (uint32_t)t, s.rk);
-    __syncthreads();
     SlicedCounter<NP> cd, cu;
     cd.clear();
     cu.clear();
@@ -277,7 +283,10 @@ __device__ void gm_word(const GraphMscSolve &s, const GraphMscLaunch &L, int wor
       own_range(s.class_start[c], s.class_start[c + 1], k, K, lo, hi);
       const int ob = ocls[c];
       for (int v = lo + threadIdx.x; v < hi; v += blockDim.x) {
-        const uint32_t sn = update_vertex<NP>(spin, v, ob + (v - lo), adj, trow, bp, s.rk, cd, cu);
+        // improved replicas take their best state from v as it stood at the
+        // end of the previous sweep (v has not been updated since)
+        if (imp != 0u) gbest[v] = (gbest[v] & ~imp) | (spin[v] & imp);
+        const uint32_t sn = update_vertex<NP>(spin, v, ob + (v - lo), adj, row, bp, s.rk, cd, cu);
         if (K == 1) {
           spin[v] = sn;
         } else {
@@ -286,44 +295,40 @@ __device__ void gm_word(const GraphMscSolve &s, const GraphMscLaunch &L, int wor
       }
       if (c + 1 < s.n_colours) sync_group(K);
     }
+    if (more) {
+      uint32_t *nrow = trow + ((t + 1) & 1) * s.kmax1;
+      if (x0 < s.kmax1) nrow[x0] = p0;
+      if (x1 < s.kmax1) nrow[x1] = p1;
+    }
     int32_t *pbuf = part + ((t + 1) & 1) * 32 * K;
     const int32_t tot = 2 * (cd.warp_lane_total() - 2 * cu.warp_lane_total());
     publish_lanes(tot, lane_acc, pbuf, k, K);
-    if (threadIdx.x < 32) {
-      int32_t dsum = 0;
-      for (int r = 0; r < K; ++r) dsum += pbuf[r * 32 + lane];
-      e += dsum;
-      const bool better = e < e_best;
-      if (better) e_best = e;
-      const uint32_t imp = __ballot_sync(0xFFFFFFFFu, better) & valid;
-      const int32_t mn = __reduce_min_sync(0xFFFFFFFFu, ((valid >> lane) & 1u) ? e_best : INT_MAX);
-      if (lane == 0) {
-        flags[0] = imp;
-        flags[1] = (s.has_target && mn <= s.target) ? 1u : 0u;
+    int32_t dsum = 0;
+    for (int r = 0; r < K; ++r) dsum += pbuf[r * 32 + lane];
+    e += dsum;
+    const bool better = e < e_best;
+    if (better) e_best = e;
+    imp = __ballot_sync(0xFFFFFFFFu, better) & valid;
+    if (s.has_target) {
+      const int32_t mn =
+          __reduce_min_sync(0xFFFFFFFFu, ((valid >> lane) & 1u) ? e_best : INT_MAX);
+      if (mn <= s.target) {
+        hit = t;
+        ++t;
+        break;
       }
-    }
-    __syncthreads();
-    const uint32_t imp = flags[0];
-    const uint32_t stop = flags[1];
-    if (imp != 0u) {
-      for (int c = 0; c < s.n_colours; ++c) {
-        int lo, hi;
-        own_range(s.class_start[c], s.class_start[c + 1], k, K, lo, hi);
-        for (int v = lo + threadIdx.x; v < hi; v += blockDim.x)
-          gbest[v] = (gbest[v] & ~imp) | (spin[v] & imp);
-      }
-    }
-    if (stop) {
-      hit = t;
-      ++t;
-      break;
     }
   }
 
+  // every update of the cluster precedes the last group barrier
   for (int c = 0; c < s.n_colours; ++c) {
     int lo, hi;
     own_range(s.class_start[c], s.class_start[c + 1], k, K, lo, hi);
-    for (int v = lo + threadIdx.x; v < hi; v += blockDim.x) gspin[v] = spin[v];
+    for (int v = lo + threadIdx.x; v < hi; v += blockDim.x) {
+      const uint32_t x = spin[v];
+      gspin[v] = x;
+      if (imp != 0u) gbest[v] = (gbest[v] & ~imp) | (x & imp);
+    }
   }
   if (k == 0) {
     if (threadIdx.x < 32) {

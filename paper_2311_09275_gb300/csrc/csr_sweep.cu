@@ -29,7 +29,7 @@ namespace {
 __host__ __device__ __forceinline__ size_t align16(size_t x) { return (x + 15) & ~size_t(15); }
 
 struct CsrSmem {
-  size_t spin, lrow, lorig, lcol, lwt, ocls, trow, part, lane_acc, flags, total;
+  size_t spin, lrow, lorig, lcol, lwt, ocls, trow, part, lane_acc, total;
 };
 
 // own_n / own_nnz: the largest owned vertex / adjacency count of any rank
@@ -45,10 +45,9 @@ __host__ __device__ __forceinline__ CsrSmem csr_layout(int n, int Q, int K, int 
   m.lwt = align16(m.lcol + sizeof(int32_t) * (size_t)own_nnz);
   m.ocls = align16(m.lwt + (weights ? sizeof(int32_t) * (size_t)own_nnz : 0));
   m.trow = align16(m.ocls + (own_n ? sizeof(int32_t) * ((size_t)n_colours + 1) : 0));
-  m.part = align16(m.trow + sizeof(uint32_t) * (size_t)trow_n);
+  m.part = align16(m.trow + 2 * sizeof(uint32_t) * (size_t)trow_n);
   m.lane_acc = m.part + 2 * sizeof(int32_t) * 4 * (size_t)Q * K;
-  m.flags = m.lane_acc + sizeof(int32_t) * 4 * (size_t)Q;
-  m.total = align16(m.flags + sizeof(uint32_t) * 4 * (size_t)Q + 16);
+  m.total = align16(m.lane_acc + sizeof(int32_t) * 4 * (size_t)Q);
   return m;
 }
 
@@ -94,6 +93,19 @@ __device__ __forceinline__ void publish(const int32_t (&vals)[Q][4], int32_t *la
     }
   }
   sync_group(K);
+}
+
+// Best-state blend of vertex v for the improved lanes (byte masks bm[q]); kept
+// out of line so that the rarely taken blend costs the sweep loop no registers.
+template <int Q>
+__device__ __noinline__ void blend_best(uint32_t *best, const uint32_t *spin, int n, int v,
+                                        int quad0, const uint32_t (&bm)[Q]) {
+#pragma unroll
+  for (int q = 0; q < Q; ++q) {
+    if (bm[q] == 0u) continue;
+    uint32_t &gb = best[(size_t)(quad0 + q) * n + v];
+    gb = (gb & ~bm[q]) | (spin[q * n + v] & bm[q]);
+  }
 }
 
 // Sources of one vertex's adjacency: staged in shared memory or global.
@@ -178,7 +190,6 @@ __device__ void csr_solve(const CsrSolve &s, const CsrLaunch &L, int quad0, int 
   uint32_t *spin = reinterpret_cast<uint32_t *>(smem + lay.spin);  // [Q][n]
   int32_t *part = reinterpret_cast<int32_t *>(smem + lay.part);
   int32_t *lane_acc = reinterpret_cast<int32_t *>(smem + lay.lane_acc);
-  volatile uint32_t *flags = reinterpret_cast<uint32_t *>(smem + lay.flags);
   uint32_t *trow = reinterpret_cast<uint32_t *>(smem + lay.trow);
   int32_t *ocls = reinterpret_cast<int32_t *>(smem + lay.ocls);
   const PhiloxKey key{s.key0, s.key1};
@@ -244,9 +255,15 @@ __device__ void csr_solve(const CsrSolve &s, const CsrLaunch &L, int quad0, int 
     adj = {s.rowptr, s.col, s.wt, s.orig};
   }
   if (threadIdx.x < 4 * Q) lane_acc[threadIdx.x] = 0;
-  __syncthreads();
+  const int kmax1 = s.kmax + 1;
+  // cached threshold rows: two buffers, the next sweep's row loaded a sweep ahead
+  if (trow_n && t_begin < t_end)
+    for (int i = threadIdx.x; i < trow_n; i += blockDim.x)
+      trow[(t_begin & 1) * trow_n + i] = s.table[(size_t)t_begin * kmax1 + i];
+  // peers write into this CTA's copy of the quads only after every CTA has loaded it
+  sync_group(K);
 
-  // bookkeeping lanes: warp 0, lane = q * 4 + l
+  // bookkeeping lanes: lane = q * 4 + l, kept identically by every warp
   int32_t e = 0, e_best = 0;
   const int my_q = lane >> 2;
   const int my_r = 4 * (quad0 + my_q) + (lane & 3);
@@ -280,29 +297,39 @@ __device__ void csr_solve(const CsrSolve &s, const CsrLaunch &L, int quad0, int 
       }
     }
     publish<Q>(vals, lane_acc, part, k, K);  // publication 0 uses buffer 0
-    if (threadIdx.x < 32) {
-      int32_t tot = 0;
-      if (lane < 4 * Q)
-        for (int r = 0; r < K; ++r) tot += part[r * 4 * Q + lane];
-      e = tot;
-      e_best = e;
-    }
-  } else if (threadIdx.x < 32 && valid) {
+    int32_t tot = 0;
+    if (lane < 4 * Q)
+      for (int r = 0; r < K; ++r) tot += part[r * 4 * Q + lane];
+    e = tot;
+    e_best = e;
+  } else if (valid) {
     e = s.e_cur[my_r];
     e_best = s.e_best[my_r];
   }
 
-  const int kmax1 = s.kmax + 1;
   int t = t_begin;
   int hit = -1;
+  uint32_t imp = 0u;  // lanes whose best state is the state at the start of sweep t
+  constexpr int kPre = 2;  // entries per thread prefetched in registers (the rest: at the end)
   for (; t < t_end; ++t) {
     const uint32_t *row = s.table + (size_t)t * kmax1;
+    const bool more = t + 1 < t_end;
+    uint32_t pre[kPre];
     if (trow_n) {
-      // the sweep's thresholds: all threads finished the previous sweep's
-      // reads at the last barrier of that sweep
-      for (int i = threadIdx.x; i < trow_n; i += blockDim.x) trow[i] = row[i];
-      __syncthreads();
-      row = trow;
+      row = trow + (t & 1) * trow_n;
+#pragma unroll
+      for (int j = 0; j < kPre; ++j) {
+        const int x = (int)threadIdx.x + j * (int)blockDim.x;
+        pre[j] = (more && x < trow_n) ? s.table[(size_t)(t + 1) * kmax1 + x] : 0u;
+      }
+    }
+    // byte masks of the improved lanes of each quad
+    uint32_t bm[Q];
+#pragma unroll
+    for (int q = 0; q < Q; ++q) {
+      const uint32_t m4 = (imp >> (4 * q)) & 0xFu;
+      bm[q] = ((m4 & 1u) ? 0xFFu : 0u) | ((m4 & 2u) ? 0xFF00u : 0u) |
+              ((m4 & 4u) ? 0xFF0000u : 0u) | ((m4 & 8u) ? 0xFF000000u : 0u);
     }
     int32_t de[Q][4];
 #pragma unroll
@@ -317,6 +344,11 @@ __device__ void csr_solve(const CsrSolve &s, const CsrLaunch &L, int quad0, int 
         const int i = ob + (v - lo);
         const int p0 = adj.row[i], p1 = adj.row[i + 1];
         const uint32_t ov = (uint32_t)adj.orig[i];
+        if (imp != 0u) {
+          // improved lanes take their best state from v as it stood at the end
+          // of the previous sweep (v has not been updated since)
+          blend_best<Q>(s.best, spin, n, v, quad0, bm);
+        }
         int32_t kk[Q][4];
         fields<Q, MODE>(spin, n, v, p0, p1, adj, kk);
 #pragma unroll
@@ -354,46 +386,52 @@ __device__ void csr_solve(const CsrSolve &s, const CsrLaunch &L, int quad0, int 
       }
       if (c + 1 < s.n_colours) sync_group(K);
     }
+    if (trow_n && more) {
+      // the other buffer's last reads were in the previous sweep
+      uint32_t *nrow = trow + ((t + 1) & 1) * trow_n;
+#pragma unroll
+      for (int j = 0; j < kPre; ++j) {
+        const int x = (int)threadIdx.x + j * (int)blockDim.x;
+        if (x < trow_n) nrow[x] = pre[j];
+      }
+      for (int x = (int)threadIdx.x + kPre * (int)blockDim.x; x < trow_n; x += blockDim.x)
+        nrow[x] = s.table[(size_t)(t + 1) * kmax1 + x];
+    }
     // sweep t is publication t + 1 (the initial energy is publication 0)
     int32_t *pbuf = part + ((t + 1) & 1) * 4 * Q * K;
     publish<Q>(de, lane_acc, pbuf, k, K);
-    if (threadIdx.x < 32) {
-      int32_t tot = 0;
-      if (lane < 4 * Q)
-        for (int r = 0; r < K; ++r) tot += pbuf[r * 4 * Q + lane];
-      e += tot;
-      const bool better = valid && e < e_best;
-      if (better) e_best = e;
-      const uint32_t imp = __ballot_sync(0xFFFFFFFFu, better);
+    int32_t tot = 0;
+    if (lane < 4 * Q)
+      for (int r = 0; r < K; ++r) tot += pbuf[r * 4 * Q + lane];
+    e += tot;
+    const bool better = valid && e < e_best;
+    if (better) e_best = e;
+    imp = __ballot_sync(0xFFFFFFFFu, better);
+    if (s.has_target) {
       const int32_t mn = __reduce_min_sync(0xFFFFFFFFu, valid ? e_best : INT_MAX);
-      if (lane == 0) {
-        flags[0] = imp;
-        flags[1] = (s.has_target && mn <= s.target) ? 1u : 0u;
+      if (mn <= s.target) {
+        hit = t;
+        ++t;
+        break;
       }
     }
-    __syncthreads();
-    const uint32_t imp = flags[0];
-    const uint32_t stop = flags[1];
-    if (imp != 0u) {
+  }
+
+  // every update of the cluster precedes the last group barrier
+  if (imp != 0u) {
 #pragma unroll
-      for (int q = 0; q < Q; ++q) {
-        const uint32_t m4 = (imp >> (4 * q)) & 0xFu;
-        if (m4 == 0u) continue;
-        const uint32_t bm = ((m4 & 1u) ? 0xFFu : 0u) | ((m4 & 2u) ? 0xFF00u : 0u) |
-                            ((m4 & 4u) ? 0xFF0000u : 0u) | ((m4 & 8u) ? 0xFF000000u : 0u);
-        uint32_t *gb = s.best + (size_t)(quad0 + q) * n;
-        for (int c = 0; c < s.n_colours; ++c) {
-          int lo, hi;
-          own_range(s.class_start[c], s.class_start[c + 1], k, K, lo, hi);
-          for (int v = lo + threadIdx.x; v < hi; v += blockDim.x)
-            gb[v] = (gb[v] & ~bm) | (spin[q * n + v] & bm);
-        }
+    for (int q = 0; q < Q; ++q) {
+      const uint32_t m4 = (imp >> (4 * q)) & 0xFu;
+      if (m4 == 0u) continue;
+      const uint32_t bmq = ((m4 & 1u) ? 0xFFu : 0u) | ((m4 & 2u) ? 0xFF00u : 0u) |
+                           ((m4 & 4u) ? 0xFF0000u : 0u) | ((m4 & 8u) ? 0xFF000000u : 0u);
+      uint32_t *gb = s.best + (size_t)(quad0 + q) * n;
+      for (int c = 0; c < s.n_colours; ++c) {
+        int lo, hi;
+        own_range(s.class_start[c], s.class_start[c + 1], k, K, lo, hi);
+        for (int v = lo + threadIdx.x; v < hi; v += blockDim.x)
+          gb[v] = (gb[v] & ~bmq) | (spin[q * n + v] & bmq);
       }
-    }
-    if (stop) {
-      hit = t;
-      ++t;
-      break;
     }
   }
 
