@@ -87,12 +87,37 @@ isg_status finish_problem(isg_problem *p) {
   for (int32_t c = 0; c < p->n_colours; ++c) p->class_start[c + 1] += p->class_start[c];
   p->order.assign(p->n, 0);
   std::vector<int32_t> fill(p->class_start.begin(), p->class_start.end() - 1);
-  std::vector<int32_t> inv(p->n);
-  for (int32_t i = 0; i < p->n; ++i) {
-    const int32_t nw = fill[p->colour[i]]++;
-    p->order[nw] = i;
-    inv[i] = nw;
+  for (int32_t i = 0; i < p->n; ++i) p->order[fill[p->colour[i]]++] = i;
+  if (!p->torus) {
+    // Inside a class the update order is free.  Vertices are taken in groups
+    // of 32 of similar degree (one warp's worth: uniform neighbour-loop trip
+    // counts), and the groups in bit-reversed order, so that every contiguous
+    // slice of a class (one CTA's share) holds a like mix of degrees.
+    std::vector<int32_t> cls, grp;
+    for (int32_t c = 0; c < p->n_colours; ++c) {
+      const int32_t a = p->class_start[c], b = p->class_start[c + 1];
+      cls.assign(p->order.begin() + a, p->order.begin() + b);
+      std::stable_sort(cls.begin(), cls.end(), [p](int32_t x, int32_t y) {
+        return p->rowptr[x + 1] - p->rowptr[x] > p->rowptr[y + 1] - p->rowptr[y];
+      });
+      const int32_t G = (b - a + 31) / 32;
+      int bits = 0;
+      while ((1 << bits) < G) ++bits;
+      auto rev = [bits](int32_t g) {
+        int32_t r = 0;
+        for (int k = 0; k < bits; ++k) r |= ((g >> k) & 1) << (bits - 1 - k);
+        return r;
+      };
+      grp.resize(G);
+      for (int32_t g = 0; g < G; ++g) grp[g] = g;
+      std::sort(grp.begin(), grp.end(), [&rev](int32_t x, int32_t y) { return rev(x) < rev(y); });
+      int32_t o = a;
+      for (int32_t g : grp)
+        for (int32_t j = 32 * g; j < std::min(32 * g + 32, b - a); ++j) p->order[o++] = cls[j];
+    }
   }
+  std::vector<int32_t> inv(p->n);
+  for (int32_t v = 0; v < p->n; ++v) inv[p->order[v]] = v;
   p->rowptr_r.assign(p->n + 1, 0);
   p->col_r.resize(p->rowptr[p->n]);
   p->wt_r.resize(p->rowptr[p->n]);

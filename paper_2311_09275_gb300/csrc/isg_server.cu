@@ -1,6 +1,6 @@
 // isg_server.cu -- continuous-batching annealing server.
 //
-// A native worker thread owns one non-blocking stream.  Requests wait in a
+// A native worker thread owns the server's non-blocking streams.  Requests wait in a
 // queue until a slot is free and their device state fits the memory budget;
 // then their state is allocated and they join the active set.  Every
 // iteration runs one chunk of sweeps for all active requests with the
@@ -90,8 +90,11 @@ struct isg_server {
   bool stopping = false;
   uint64_t next_id = 1;
   std::thread worker;
-  // worker-owned
+  // worker-owned; the graph unit kernels run on side streams, concurrently with
+  // the torus unit kernel, joined back into `stream` by events
   cudaStream_t stream = nullptr;
+  cudaStream_t side[2] = {nullptr, nullptr};
+  cudaEvent_t ev_in = nullptr, ev_side[2] = {nullptr, nullptr};
   std::vector<Slot *> active;
   size_t used = 0;
   size_t cap_t = 0, cap_c = 0, cap_g = 0;
@@ -401,15 +404,27 @@ cudaError_t run_units(isg_server *s, const std::vector<Slot *> &slots,
     const int per_sm = std::max(1, std::min<int>(4, (int)((228 * 1024) / (smem + 1024))));
     return (int)std::min<size_t>(units, (size_t)sm_count() * per_sm);
   };
+  // the three unit kinds run concurrently (each fills the SMs the others leave)
+  if (err == cudaSuccess && (ng || nc)) err = cudaEventRecord(s->ev_in, s->stream);
+  if (err == cudaSuccess && ng) {
+    err = cudaStreamWaitEvent(s->side[0], s->ev_in, 0);
+    if (err == cudaSuccess)
+      err = gm_batch_launch(s->d_g, s->d_ctl + 5, s->d_ord_g, s->d_ctl + 4, ctas_for(ng, smem_g),
+                            threads, smem_g, s->side[0]);
+    if (err == cudaSuccess) err = cudaEventRecord(s->ev_side[0], s->side[0]);
+  }
+  if (err == cudaSuccess && nc) {
+    err = cudaStreamWaitEvent(s->side[1], s->ev_in, 0);
+    if (err == cudaSuccess)
+      err = csr_batch_launch(s->d_c, s->d_ctl + 3, s->d_ord_c, s->d_ctl + 1, ctas_for(nc, smem_c),
+                             threads, smem_c, s->side[1]);
+    if (err == cudaSuccess) err = cudaEventRecord(s->ev_side[1], s->side[1]);
+  }
   if (err == cudaSuccess && nt)
     err = torus_batch_launch(s->d_t, s->d_ctl + 2, s->d_ord_t, s->d_ctl + 0, ctas_for(nt, smem_t),
                              threads, smem_t, s->stream);
-  if (err == cudaSuccess && ng)
-    err = gm_batch_launch(s->d_g, s->d_ctl + 5, s->d_ord_g, s->d_ctl + 4, ctas_for(ng, smem_g),
-                          threads, smem_g, s->stream);
-  if (err == cudaSuccess && nc)
-    err = csr_batch_launch(s->d_c, s->d_ctl + 3, s->d_ord_c, s->d_ctl + 1, ctas_for(nc, smem_c),
-                           threads, smem_c, s->stream);
+  if (err == cudaSuccess && ng) err = cudaStreamWaitEvent(s->stream, s->ev_side[0], 0);
+  if (err == cudaSuccess && nc) err = cudaStreamWaitEvent(s->stream, s->ev_side[1], 0);
   for (Slot *sl : slots) sl->res->sweep_launches += 1;
   return err;
 }
@@ -565,11 +580,22 @@ isg_status isg_server_create(size_t device_mem_budget, int32_t max_slots, int32_
   s->chunk = sweeps_per_chunk;
   cudaError_t err = cudaGetDevice(&s->device);
   if (err == cudaSuccess) err = cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking);
+  for (int i = 0; i < 2 && err == cudaSuccess; ++i) {
+    err = cudaStreamCreateWithFlags(&s->side[i], cudaStreamNonBlocking);
+    if (err == cudaSuccess) err = cudaEventCreateWithFlags(&s->ev_side[i], cudaEventDisableTiming);
+  }
+  if (err == cudaSuccess) err = cudaEventCreateWithFlags(&s->ev_in, cudaEventDisableTiming);
   if (err == cudaSuccess) err = cudaMalloc(&s->d_ctl, 64);
   if (err == cudaSuccess) err = cudaMallocHost(&s->h_ctl, 64);
   if (err != cudaSuccess) {
     if (s->stream) cudaStreamDestroy(s->stream);
+    for (int i = 0; i < 2; ++i) {
+      if (s->side[i]) cudaStreamDestroy(s->side[i]);
+      if (s->ev_side[i]) cudaEventDestroy(s->ev_side[i]);
+    }
+    if (s->ev_in) cudaEventDestroy(s->ev_in);
     cudaFree(s->d_ctl);
+    cudaFreeHost(s->h_ctl);
     delete s;
     return cuda_fail(err, "creating the server");
   }
@@ -668,6 +694,11 @@ isg_status isg_server_destroy(isg_server *s) {
   cudaFree(s->d_ctl);
   cudaFreeHost(s->h_ctl);
   cudaFreeHost(s->h_status);
+  for (int i = 0; i < 2; ++i) {
+    cudaStreamDestroy(s->side[i]);
+    cudaEventDestroy(s->ev_side[i]);
+  }
+  cudaEventDestroy(s->ev_in);
   cudaStreamDestroy(s->stream);
   cudaSetDevice(prev);
   const isg_status st = s->worker_error;
