@@ -44,40 +44,47 @@ METRIC = "spin-flip attempts/s"
 UNIT = "attempts/s"
 # Integer-ALU instructions one attempt needs by the algorithm: a quarter of
 # the 20 three-input XORs of a Philox4x32-10 block (10 rounds x 2) plus one
-# threshold compare.  The block's 20 wide multiplies run on the multiply-add
-# pipe, which is not the limiter.  The ALU pipe accepts half a warp
-# instruction per cycle per scheduler (16 lanes), as ncu's pipe-utilisation
-# counters of this kernel show (ALU-pipe % of peak vs issue rate).
+# threshold compare.  The ALU pipe accepts half a warp instruction per cycle
+# per scheduler (16 lanes), as ncu's pipe-utilisation counters show (ALU-pipe
+# % of peak vs issue rate).  The block's widening multiplies run on the
+# multiply pipe, which the same counters show as the busier of the two.
 ALGO_ALU_OPS_PER_ATTEMPT = 20 / 4 + 1
 SMSP_PER_SM = 4
 ALU_LANES_PER_SMSP = 16
+KERNEL_NAMES = {1: "torus_kernel", 2: "csr_kernel", 3: "plain per-sweep launches",
+                4: "gm_kernel"}
 
 
-def profiled_traffic(workload_name: str):
-    """DRAM bytes per launch of the sweep kernel from the committed ncu summary,
-    or None when the summary does not cover this workload or the kernel source
-    changed since the counters were taken."""
+def profiled_traffic(workload_name: str, kernel_name: str):
+    """DRAM bytes per launch of a sweep kernel from the committed ncu summaries
+    (profiles/*.md carrying `workload`, `kernel`, `kernel_sources`,
+    `kernel_source_sha256_16` and `traffic_bytes_per_launch` lines), or None when
+    no summary covers this workload and kernel or a source changed since."""
+    import glob
     import hashlib
-    if not workload_name.startswith("torus_80x100_R1024_S10000"):
-        return None
-    path = os.path.join(ROOT, "profiles", "torus_kernel_80x100_R1024.md")
-    src = os.path.join(ROOT, "paper_2311_09275_gb300", "csrc", "torus_msc.cu")
-    if not os.path.exists(path):
-        return None
-    fields = {}
-    with open(path) as f:
-        for line in f:
-            if ":" in line and not line.startswith(("|", "#", " ")):
-                k, v = line.split(":", 1)
-                fields[k.strip()] = v.strip()
-    with open(src, "rb") as f:
-        sha = hashlib.sha256(f.read()).hexdigest()[:16]
-    if fields.get("kernel_source_sha256_16") != sha:
-        return None
-    try:
-        return int(fields["traffic_bytes_per_launch"])
-    except (KeyError, ValueError):
-        return None
+    for path in sorted(glob.glob(os.path.join(ROOT, "profiles", "*.md"))):
+        fields = {}
+        with open(path) as f:
+            for line in f:
+                if ":" in line and not line.startswith(("|", "#", " ", "`")):
+                    k, v = line.split(":", 1)
+                    fields[k.strip()] = v.strip()
+        if fields.get("workload") != workload_name or fields.get("kernel") != kernel_name:
+            continue
+        h = hashlib.sha256()
+        for rel in fields.get("kernel_sources", "").split(","):
+            src = os.path.join(ROOT, "paper_2311_09275_gb300", "csrc", rel.strip())
+            if not rel.strip() or not os.path.exists(src):
+                return None
+            with open(src, "rb") as f:
+                h.update(f.read())
+        if fields.get("kernel_source_sha256_16") != h.hexdigest()[:16]:
+            return None
+        try:
+            return int(fields["traffic_bytes_per_launch"])
+        except (KeyError, ValueError):
+            return None
+    return None
 
 
 def load_peaks():
@@ -275,10 +282,10 @@ def run_gpu(args):
     p = isg.problem_of(sv.problem)
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.int32, device=device)  # 512 MB > L2
 
-    shape = {}
+    shape = {"kernel": args.kernel} if args.kernel else {}
     if args.launch:
         parts = [int(x) for x in args.launch.split(",")]
-        shape = {"cluster_ctas": parts[0], "threads": parts[1]}
+        shape.update({"cluster_ctas": parts[0], "threads": parts[1]})
         if len(parts) > 2:
             shape["quads_per_cta"] = parts[2]
 
@@ -288,7 +295,7 @@ def run_gpu(args):
 
     # launch-shape autotuning (untimed, part of warm-up); results never depend on it
     tuned = None
-    if not args.no_tune and not args.launch:
+    if not args.no_tune and not args.launch and not args.kernel:
         tuned = isg.isg_autotune(p, sv.replicas, 64, stream=stream)
     for _ in range(args.warmup):
         r = step()
@@ -356,7 +363,8 @@ def run_gpu(args):
     alu_peak = props.multi_processor_count * SMSP_PER_SM * ALU_LANES_PER_SMSP * sm_max * 1e6
     k_ms = statistics.mean(kernel_ms)
     achieved = ALGO_ALU_OPS_PER_ATTEMPT * float(sv.attempts) / (k_ms / 1e3)
-    traffic = profiled_traffic(name)
+    kname = KERNEL_NAMES.get(stats["kernel"], "sweep kernel")
+    traffic = profiled_traffic(name, kname)
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -374,7 +382,7 @@ def run_gpu(args):
         "gpu_launches": launches,
         "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": alu_peak / 1e12,
                      "unit": "Tops/s", "frac": achieved / alu_peak, "traffic": traffic,
-                     "kernel": "torus_kernel" if hasattr(sv.problem, "L") else "csr_kernel",
+                     "kernel": kname,
                      "kernel_ms": k_ms,
                      "algorithmic_ops_per_attempt": ALGO_ALU_OPS_PER_ATTEMPT,
                      "peak_source": f"{props.multi_processor_count} SMs x {SMSP_PER_SM} schedulers x "
@@ -532,6 +540,9 @@ def main():
     ap.add_argument("--mem-gb", type=int, default=32, help="served: device memory budget (GB)")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-tune", action="store_true", help="skip the launch-shape autotuner")
+    ap.add_argument("--kernel", type=int, default=0,
+                    help="kernel family (1 torus, 2 colour-class int8, 3 plain, 4 graph "
+                         "multi-spin; 0 = tuned)")
     ap.add_argument("--launch", default=None,
                     help="explicit launch shape CLUSTER,THREADS (skips the autotuner)")
     ap.add_argument("--sweeps", type=int, default=None,
