@@ -42,15 +42,15 @@ from paper_2311_09275_gb300 import inputs as I  # noqa: E402
 
 METRIC = "spin-flip attempts/s"
 UNIT = "attempts/s"
-# Integer-ALU instructions one attempt needs by the algorithm: a quarter of
-# the 20 three-input XORs of a Philox4x32-10 block (10 rounds x 2) plus one
-# threshold compare.  The ALU pipe accepts half a warp instruction per cycle
-# per scheduler (16 lanes), as ncu's pipe-utilisation counters show (ALU-pipe
-# % of peak vs issue rate).  The block's widening multiplies run on the
-# multiply pipe, which the same counters show as the busier of the two.
-ALGO_ALU_OPS_PER_ATTEMPT = 20 / 4 + 1
+# Integer instructions one attempt needs by the algorithm, per pipe: a quarter
+# of a Philox4x32-10 block (10 rounds x 2 three-input XORs on the logic pipe,
+# 10 rounds x 2 widening multiplies on the multiply pipe) plus one threshold
+# compare (logic pipe).  The roofline takes the pipe whose share of the work
+# needs the longer time at its measured rate (isg_integer_peaks).
+ALGO_LOP3_PER_ATTEMPT = 20 / 4 + 1
+ALGO_MAD_PER_ATTEMPT = 20 / 4
 SMSP_PER_SM = 4
-ALU_LANES_PER_SMSP = 16
+ALU_LANES_PER_SMSP = 16  # nominal: the logic pipe takes half a warp instruction per cycle
 KERNEL_NAMES = {1: "torus_kernel", 2: "csr_kernel", 3: "plain per-sweep launches",
                 4: "gm_kernel"}
 
@@ -357,12 +357,20 @@ def run_gpu(args):
     e2e_value = sum_over_ranks(float(sv.attempts) * e2e_steps, dist, device) / e2e_s
 
     # ---- roofline of the sweep kernel (integer issue)
-    peaks, peak_src = load_peaks()
+    pipes = isg.isg_integer_peaks(stream)
     props = torch.cuda.get_device_properties(device)
-    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
-    alu_peak = props.multi_processor_count * SMSP_PER_SM * ALU_LANES_PER_SMSP * sm_max * 1e6
+    peaks, _ = load_peaks()
+    nominal_lop3 = (props.multi_processor_count * SMSP_PER_SM * ALU_LANES_PER_SMSP *
+                    float(peaks.get("sm_max_mhz", 2070.0)) * 1e6)
     k_ms = statistics.mean(kernel_ms)
-    achieved = ALGO_ALU_OPS_PER_ATTEMPT * float(sv.attempts) / (k_ms / 1e3)
+    rate = float(sv.attempts) / (k_ms / 1e3)                  # attempts/s of the sweep kernel
+    t_lop3 = ALGO_LOP3_PER_ATTEMPT / pipes["lop3_per_s"]      # s per attempt at each pipe's peak
+    t_mad = ALGO_MAD_PER_ATTEMPT / pipes["mad_wide_per_s"]
+    if t_lop3 >= t_mad:
+        pipe, ops, peak = "lop3 (logic pipe)", ALGO_LOP3_PER_ATTEMPT, pipes["lop3_per_s"]
+    else:
+        pipe, ops, peak = "mad.wide.u32 (multiply pipe)", ALGO_MAD_PER_ATTEMPT, pipes["mad_wide_per_s"]
+    achieved = ops * rate
     kname = KERNEL_NAMES.get(stats["kernel"], "sweep kernel")
     traffic = profiled_traffic(name, kname)
 
@@ -380,14 +388,19 @@ def run_gpu(args):
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                 "d2h_bytes_per_step": int(d2h), "steps": e2e_steps},
         "gpu_launches": launches,
-        "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": alu_peak / 1e12,
-                     "unit": "Tops/s", "frac": achieved / alu_peak, "traffic": traffic,
-                     "kernel": kname,
-                     "kernel_ms": k_ms,
-                     "algorithmic_ops_per_attempt": ALGO_ALU_OPS_PER_ATTEMPT,
-                     "peak_source": f"{props.multi_processor_count} SMs x {SMSP_PER_SM} schedulers x "
-                                    f"{ALU_LANES_PER_SMSP} ALU lanes x {sm_max:.0f} MHz "
-                                    f"({peak_src} max clock)"},
+        "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": peak / 1e12,
+                     "unit": "T instr/s", "frac": achieved / peak, "traffic": traffic,
+                     "kernel": kname, "kernel_ms": k_ms, "pipe": pipe,
+                     "algorithmic_per_attempt": {"lop3": ALGO_LOP3_PER_ATTEMPT,
+                                                 "mad.wide": ALGO_MAD_PER_ATTEMPT},
+                     "frac_per_pipe": {"lop3": ALGO_LOP3_PER_ATTEMPT * rate / pipes["lop3_per_s"],
+                                       "mad.wide": ALGO_MAD_PER_ATTEMPT * rate /
+                                       pipes["mad_wide_per_s"]},
+                     "peak_source": f"measured on this GPU by isg_integer_peaks: lop3 "
+                                    f"{pipes['lop3_per_s'] / 1e12:.2f}T/s, mad.wide "
+                                    f"{pipes['mad_wide_per_s'] / 1e12:.2f}T/s "
+                                    f"({props.multi_processor_count} SMs)",
+                     "nominal_lop3_peak": nominal_lop3 / 1e12},
         "clocks": clocks.summary(),
         "wall_s": wall,
     }

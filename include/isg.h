@@ -245,6 +245,16 @@ isg_status isg_server_destroy(isg_server *s);
 
 /* ---------------------------------------------------------------- misc */
 
+/* Measured throughput of the two integer instructions the sweep kernels are
+ * built from, on the current device: three-input logic ops (lop3) and
+ * widening 32x32->64 multiply-adds (mad.wide.u32), in thread-instructions per
+ * second over the whole device.  The paper has no counterpart: these are the
+ * denominators of the sweep kernels' roofline.  Runs two short kernels
+ * (about 10 ms each) on cuda_stream (NULL = legacy default stream) and
+ * synchronises with them; allocates 4 bytes per CTA, stream-ordered.  EINVAL
+ * for NULL outputs, ECUDA if a launch fails. */
+isg_status isg_integer_peaks(void *cuda_stream, double *lop3_per_s, double *mad_wide_per_s);
+
 /* Message of the last failed call on this thread ("" if none). */
 const char *isg_last_error(void);
 

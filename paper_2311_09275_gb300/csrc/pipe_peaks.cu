@@ -1,0 +1,117 @@
+// pipe_peaks.cu -- throughput of the two integer instructions the sweep kernels
+// are made of, measured on the device at hand: the three-input logic op
+// (lop3: Philox's XORs, the spin logic, the threshold masks) and the widening
+// 32x32->64 multiply-add (mad.wide.u32: Philox's products).  These rates are
+// the denominators of the sweep kernels' roofline.
+//
+// Each thread runs eight independent chains, one instruction per chain and
+// step; every step's eight results depend only on the previous step, so the
+// pipes, not latencies, set the rate once each SM holds enough warps.
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "isg.h"
+#include "isg_runtime.h"
+
+namespace isg {
+namespace {
+
+constexpr int kChains = 8;
+constexpr int kUnroll = 16;  // steps per loop iteration
+
+__device__ __forceinline__ uint32_t lop3_xor(uint32_t a, uint32_t b, uint32_t c) {
+  uint32_t d;
+  asm volatile("lop3.b32 %0, %1, %2, %3, 0x96;" : "=r"(d) : "r"(a), "r"(b), "r"(c));
+  return d;
+}
+
+__device__ __forceinline__ uint64_t mad_wide(uint32_t a, uint32_t b, uint64_t c) {
+  uint64_t d;
+  asm volatile("mad.wide.u32 %0, %1, %2, %3;" : "=l"(d) : "r"(a), "r"(b), "l"(c));
+  return d;
+}
+
+__global__ void __launch_bounds__(256) lop3_rate_kernel(uint32_t *sink, int iters, uint32_t seed) {
+  uint32_t x[kChains];
+#pragma unroll
+  for (int k = 0; k < kChains; ++k) x[k] = seed * (threadIdx.x + 1u) + 0x9E3779B9u * k;
+  for (int i = 0; i < iters; ++i) {
+#pragma unroll
+    for (int u = 0; u < kUnroll; ++u) {
+      uint32_t y[kChains];
+#pragma unroll
+      for (int k = 0; k < kChains; ++k)
+        y[k] = lop3_xor(x[k], x[(k + 1) % kChains], x[(k + 3) % kChains]);
+#pragma unroll
+      for (int k = 0; k < kChains; ++k) x[k] = y[k];
+    }
+  }
+  uint32_t acc = 0u;
+#pragma unroll
+  for (int k = 0; k < kChains; ++k) acc ^= x[k];
+  if (acc == seed) sink[blockIdx.x] = acc;  // keeps the chains live
+}
+
+__global__ void __launch_bounds__(256) mad_rate_kernel(uint32_t *sink, int iters, uint32_t seed) {
+  uint64_t r[kChains];
+  const uint32_t mul = 0xD2511F53u ^ (seed & 1u);
+#pragma unroll
+  for (int k = 0; k < kChains; ++k) r[k] = (uint64_t)(seed + threadIdx.x) << 32 | (k + 1u);
+  for (int i = 0; i < iters; ++i) {
+#pragma unroll
+    for (int u = 0; u < kUnroll; ++u) {
+#pragma unroll
+      for (int k = 0; k < kChains; ++k) r[k] = mad_wide((uint32_t)(r[k] >> 32), mul, r[k]);
+    }
+  }
+  uint64_t acc = 0u;
+#pragma unroll
+  for (int k = 0; k < kChains; ++k) acc ^= r[k];
+  if ((uint32_t)acc == seed) sink[blockIdx.x] = (uint32_t)(acc >> 32);
+}
+
+}  // namespace
+}  // namespace isg
+
+using namespace isg;
+
+extern "C" isg_status isg_integer_peaks(void *cuda_stream, double *lop3_per_s,
+                                        double *mad_wide_per_s) {
+  if (!lop3_per_s || !mad_wide_per_s) return fail(ISG_EINVAL, "outputs must not be NULL");
+  cudaStream_t stream = (cudaStream_t)cuda_stream;
+  const int blocks = sm_count() * 8, threads = 256, iters = 2048;
+  const double per_launch = (double)blocks * threads * iters * kUnroll * kChains;
+  uint32_t *sink = nullptr;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  cudaError_t err = cudaMallocAsync(&sink, 4 * (size_t)blocks, stream);
+  if (err == cudaSuccess) err = cudaEventCreate(&e0);
+  if (err == cudaSuccess) err = cudaEventCreate(&e1);
+  double rate[2] = {0.0, 0.0};
+  for (int which = 0; which < 2 && err == cudaSuccess; ++which) {
+    float best_ms = 1e30f;
+    for (int rep = 0; rep < 3 && err == cudaSuccess; ++rep) {  // first run warms up
+      err = cudaEventRecord(e0, stream);
+      if (err == cudaSuccess) {
+        if (which == 0)
+          lop3_rate_kernel<<<blocks, threads, 0, stream>>>(sink, iters, 12345u);
+        else
+          mad_rate_kernel<<<blocks, threads, 0, stream>>>(sink, iters, 12345u);
+        err = cudaGetLastError();
+      }
+      if (err == cudaSuccess) err = cudaEventRecord(e1, stream);
+      if (err == cudaSuccess) err = cudaEventSynchronize(e1);
+      float ms = 0.f;
+      if (err == cudaSuccess) err = cudaEventElapsedTime(&ms, e0, e1);
+      if (err == cudaSuccess && rep > 0 && ms < best_ms) best_ms = ms;
+    }
+    if (err == cudaSuccess) rate[which] = per_launch / (best_ms * 1e-3);
+  }
+  if (sink) cudaFreeAsync(sink, stream);
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  if (err != cudaSuccess) return cuda_fail(err, "measuring integer pipe rates");
+  *lop3_per_s = rate[0];
+  *mad_wide_per_s = rate[1];
+  return ISG_OK;
+}

@@ -71,6 +71,7 @@ _sig("isg_server_create", [_sz, _i32, _i32, ctypes.POINTER(_P)])
 _sig("isg_server_submit", [_P, _P, _i32, _P, _i32, _u64, _i64, ctypes.POINTER(_u64)])
 _sig("isg_server_poll", [_P, ctypes.POINTER(_u64), ctypes.POINTER(_P), _dbl])
 _sig("isg_server_destroy", [_P])
+_sig("isg_integer_peaks", [_P, ctypes.POINTER(_dbl), ctypes.POINTER(_dbl)])
 _sig("isg_last_error", [], ctypes.c_char_p)
 _sig("isg_version", [], ctypes.c_char_p)
 
@@ -285,6 +286,13 @@ def isg_energy_noalloc(n: int, rowptr_dev: int, col_dev: int, w_dev: int, spins_
     """
     _check(_lib.isg_energy_noalloc(int(n), rowptr_dev, col_dev, w_dev, spins_dev, int(replicas),
                                    energies_dev, _stream(stream)))
+
+
+def isg_integer_peaks(stream=None) -> dict:
+    """Measured device-wide rates (thread-instructions/s) of lop3 and mad.wide.u32."""
+    a, b = _dbl(), _dbl()
+    _check(_lib.isg_integer_peaks(_stream(stream), ctypes.byref(a), ctypes.byref(b)))
+    return {"lop3_per_s": a.value, "mad_wide_per_s": b.value}
 
 
 def isg_result_final(r: Result, spins: bool = True):
