@@ -207,27 +207,36 @@ def workload(config: str, rank: int, sweeps: int | None = None):
 
 # ---------------------------------------------------------------- CPU oracle
 def cpu_oracle_rate(sv, budget_s: float = 12.0, max_replicas: int | None = None):
-    """Oracle attempts/s on the host cores over a bounded sample: the first
-    `cores` replicas of the workload, sweeps truncated to fit the budget."""
+    """Oracle attempts/s on the host cores over a bounded sample of the workload:
+    whole replicas (a multiple of the core count, one thread per replica block)
+    over a sweep prefix, sized to about budget_s seconds; plus the rate of one
+    thread on one replica."""
     import oracle
     cores = os.cpu_count() or 1
-    reps = min(sv.replicas, max_replicas or cores)
     c = oracle.csr_of(sv.problem)
     colour, _ = c.greedy_colouring()
     # calibrate on a short prefix, then size the sample to the budget
+    reps = min(sv.replicas, max_replicas or cores)
     probe = max(1, min(sv.sweeps, 20))
     t0 = time.perf_counter()
     oracle.anneal(c, reps, sv.betas[:probe], sv.seed, colour=colour, nthreads=cores)
-    dt = max(time.perf_counter() - t0, 1e-6)
-    rate = reps * sv.n * probe / dt
+    rate = reps * sv.n * probe / max(time.perf_counter() - t0, 1e-6)
     sweeps = int(max(1, min(sv.sweeps, budget_s * rate / (reps * sv.n))))
+    if sweeps == sv.sweeps and max_replicas is None:
+        fit = int(budget_s * rate / (sv.n * sv.sweeps) // cores) * cores
+        reps = max(reps, min(sv.replicas, fit))
     t0 = time.perf_counter()
     oracle.anneal(c, reps, sv.betas[:sweeps], sv.seed, colour=colour, nthreads=cores)
     dt = time.perf_counter() - t0
+    one_sweeps = int(max(1, min(sv.sweeps, 2.0 * rate / cores / sv.n)))
+    t1 = time.perf_counter()
+    oracle.anneal(c, 1, sv.betas[:one_sweeps], sv.seed, colour=colour, nthreads=1)
+    one = sv.n * one_sweeps / (time.perf_counter() - t1)
     return {"value": reps * sv.n * sweeps / dt, "unit": UNIT, "cores": min(cores, reps),
-            "kind": "oracle",
+            "kind": "oracle", "single_thread_value": one,
             "sample": f"replicas 0..{reps - 1} of {sv.replicas}, first {sweeps} of {sv.sweeps} "
-                      f"sweeps ({reps * sv.n * sweeps:.3g} attempts, {dt:.1f} s)"}
+                      f"sweeps ({reps * sv.n * sweeps:.3g} attempts, {dt:.1f} s); single thread: "
+                      f"replica 0, {one_sweeps} sweeps"}
 
 
 def run_reference(args):
@@ -501,6 +510,7 @@ def run_served(args):
     # timed served run
     srv = isg.Server(args.mem_gb << 30, args.slots, args.chunk)
     t_submit, t_done, hit, attempts = {}, {}, {}, 0.0
+    check = {j: None for j in range(0, count, max(1, count // 16))}
     t0 = time.perf_counter()
     k = 0
     ids = {}
@@ -522,9 +532,24 @@ def run_served(args):
             _, _, done = got[1].final(spins=False)
             hit[j] = got[1].best(spins=False)[4]
             attempts += reqs[j].solve.replicas * reqs[j].solve.n * done
-            got[1].close()
+            if j in check:
+                check[j] = got[1]  # compared with a solo run after the timed region
+            else:
+                got[1].close()
     wall = time.perf_counter() - t0
+    sstats = srv.stats()
     srv.close()
+    # bit-exactness in the mix: sampled requests against the same request alone
+    exact = 0
+    for j, res in check.items():
+        r = reqs[j].solve
+        solo = isg.isg_anneal(probs[j], r.replicas, r.betas, r.seed, target=targets[j])
+        same = all(np.array_equal(a, b) for a, b in zip(res.final(), solo.final()))
+        same = same and np.array_equal(res.best_all(), solo.best_all())
+        same = same and res.best(spins=False)[4] == solo.best(spins=False)[4]
+        exact += int(same)
+        res.close()
+        solo.close()
     ttt = [t_done[j] - t_submit[j] for j in range(count)]
     line = {"metric": "time-to-target (served)", "value": metrics.percentile(ttt, 99), "unit": "s",
             "n_gpus": 1, "steps": 1, "warmup": 0, "ms_per_step": wall * 1e3,
@@ -536,6 +561,8 @@ def run_served(args):
             "ttt_p50_s": metrics.percentile(ttt, 50), "ttt_p99_s": metrics.percentile(ttt, 99),
             "throughput_attempts_per_s": attempts / wall, "requests_per_s": count / wall,
             "targets_hit": sum(1 for j in range(count) if hit[j] >= 0),
+            "peak_resident_slots": sstats["peak_active"], "chunk_passes": sstats["passes"],
+            "bit_exact_vs_alone": f"{exact}/{len(check)} sampled requests",
             "clocks": clocks.summary()}
     print(json.dumps(line))
 

@@ -243,7 +243,31 @@ isg_status isg_server_poll(isg_server *s, uint64_t *request_id, isg_result **out
 /* Stop the server; unfinished requests are dropped.  */
 isg_status isg_server_destroy(isg_server *s);
 
+typedef struct {
+    int64_t submitted;    /* requests accepted by isg_server_submit */
+    int64_t completed;    /* requests handed to isg_server_poll's queue */
+    int32_t queued;       /* waiting for a slot or memory now */
+    int32_t active;       /* resident now */
+    int32_t peak_active;  /* most requests resident at once so far */
+    int64_t passes;       /* chunk passes run (one launch of the unit kernels each) */
+    int64_t replays;      /* passes re-run to a multi-unit request's stop sweep */
+} isg_server_stats;
+
+/* Counters of the server (a consistent snapshot).  EINVAL for NULL. */
+isg_status isg_server_get_stats(isg_server *s, isg_server_stats *out);
+
 /* ---------------------------------------------------------------- misc */
+
+/* The acceptance thresholds the kernels use, computed on the host exactly as
+ * the solve paths compute them: out[t * (kmax + 1) + k] =
+ * min(floor(2^32 exp(-betas[t] * 2k)), 2^32 - 1) for sweeps t < sweeps and
+ * half energy changes k = 0..kmax (an uphill flip of energy change d = 2k is
+ * taken when its uniform u < out[t][k]).  FP64 with the C library's exp.
+ * out is caller-owned host memory of sweeps * (kmax + 1) words.  EINVAL for
+ * NULL pointers, sweeps < 1, kmax < 0 or a beta that is not finite and >= 0.
+ * No device work. */
+isg_status isg_acceptance_table(const double *betas, int32_t sweeps, int32_t kmax,
+                                uint32_t *out);
 
 /* Measured throughput of the two integer instructions the sweep kernels are
  * built from, on the current device: three-input logic ops (lop3) and

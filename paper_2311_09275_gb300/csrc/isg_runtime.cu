@@ -968,6 +968,21 @@ const char *isg_last_error(void) { return g_last_error.c_str(); }
 
 const char *isg_version(void) { return "isg 0.1 (sm_103a)"; }
 
+isg_status isg_acceptance_table(const double *betas, int32_t sweeps, int32_t kmax,
+                                uint32_t *out) {
+  if (!betas || !out) return fail(ISG_EINVAL, "betas and out must not be NULL");
+  if (sweeps < 1) return fail(ISG_EINVAL, "sweeps must be >= 1 (got %d)", sweeps);
+  if (kmax < 0) return fail(ISG_EINVAL, "kmax must be >= 0 (got %d)", kmax);
+  const isg_status st = check_betas(betas, sweeps);
+  if (st != ISG_OK) return st;
+  std::vector<int32_t> levels(kmax + 1);
+  std::iota(levels.begin(), levels.end(), 0);
+  std::vector<uint32_t> table;
+  build_table(betas, sweeps, levels, table);
+  std::copy(table.begin(), table.end(), out);
+  return ISG_OK;
+}
+
 isg_status isg_problem_create_edges(int32_t n, int64_t m, const int32_t *u, const int32_t *v,
                                     const int32_t *w, isg_problem **out) {
   if (!out) return fail(ISG_EINVAL, "out must not be NULL");

@@ -108,6 +108,9 @@ struct isg_server {
   int32_t *h_status = nullptr;                 // per unit: hit, done
   size_t cap_status = 0;
   isg_status worker_error = ISG_OK;
+  // counters (under mu)
+  int64_t n_submitted = 0, n_completed = 0, n_passes = 0, n_replays = 0;
+  int32_t n_active = 0, peak_active = 0;
 };
 
 namespace isg {
@@ -223,6 +226,7 @@ void admit(isg_server *s) {
       if (sl->snap) cudaFreeAsync(sl->snap, s->stream);
       std::lock_guard<std::mutex> lock(s->mu);
       s->done.emplace_back(sl->rq.id, r);
+      ++s->n_completed;
       s->cv_done.notify_all();
       delete sl;
       continue;
@@ -232,6 +236,9 @@ void admit(isg_server *s) {
     r->threads = 256;
     s->used += sl->rq.bytes;
     s->active.push_back(sl);
+    std::lock_guard<std::mutex> lock(s->mu);
+    s->n_active = (int32_t)s->active.size();
+    s->peak_active = std::max(s->peak_active, s->n_active);
   }
 }
 
@@ -483,6 +490,10 @@ void worker_main(isg_server *s) {
     }
     if (err == cudaSuccess) err = grow(s, 0, 0, nstatus);
     if (err == cudaSuccess) err = run_units(s, s->active, t_end);
+    {
+      std::lock_guard<std::mutex> lock(s->mu);
+      ++s->n_passes;
+    }
     size_t off = 0;
     for (Slot *sl : s->active) {
       const int32_t u = sl->res->units;
@@ -535,6 +546,8 @@ void worker_main(isg_server *s) {
           err = cudaMemsetAsync(sl->res->d_hit, 0xFF, 4 * (size_t)sl->res->units, s->stream);
       }
       if (err == cudaSuccess) err = run_units(s, redo, redo_end);
+      std::lock_guard<std::mutex> lock(s->mu);
+      ++s->n_replays;
     }
     std::vector<Slot *> keep;
     std::vector<Slot *> fin;
@@ -555,9 +568,14 @@ void worker_main(isg_server *s) {
       sl->res->stream = nullptr;  // later frees go to the legacy stream
       std::lock_guard<std::mutex> lock(s->mu);
       s->done.emplace_back(sl->rq.id, sl->res);
+      ++s->n_completed;
       delete sl;
     }
     s->active.swap(keep);
+    {
+      std::lock_guard<std::mutex> lock(s->mu);
+      s->n_active = (int32_t)s->active.size();
+    }
     if (!fin.empty()) s->cv_done.notify_all();
   }
 }
@@ -633,6 +651,7 @@ isg_status isg_server_submit(isg_server *s, const isg_problem *p, int32_t replic
   if (s->stopping) return fail(ISG_ECANCELLED, "server is shutting down");
   rq.id = s->next_id++;
   *request_id = rq.id;
+  ++s->n_submitted;
   s->queue.push_back(std::move(rq));
   s->cv_work.notify_one();
   return ISG_OK;
@@ -653,6 +672,19 @@ isg_status isg_server_poll(isg_server *s, uint64_t *request_id, isg_result **out
   *request_id = s->done.front().first;
   *out = s->done.front().second;
   s->done.pop_front();
+  return ISG_OK;
+}
+
+isg_status isg_server_get_stats(isg_server *s, isg_server_stats *out) {
+  if (!s || !out) return fail(ISG_EINVAL, "arguments must not be NULL");
+  std::lock_guard<std::mutex> lock(s->mu);
+  out->submitted = s->n_submitted;
+  out->completed = s->n_completed;
+  out->queued = (int32_t)s->queue.size();
+  out->active = s->n_active;
+  out->peak_active = s->peak_active;
+  out->passes = s->n_passes;
+  out->replays = s->n_replays;
   return ISG_OK;
 }
 

@@ -42,6 +42,11 @@ class isg_stats(ctypes.Structure):
                 ("cluster_ctas", _i32), ("threads", _i32)]
 
 
+class isg_server_stats(ctypes.Structure):
+    _fields_ = [("submitted", _i64), ("completed", _i64), ("queued", _i32), ("active", _i32),
+                ("peak_active", _i32), ("passes", _i64), ("replays", _i64)]
+
+
 def _sig(name, args, res=ctypes.c_int):
     f = getattr(_lib, name)
     f.argtypes = args
@@ -71,7 +76,9 @@ _sig("isg_server_create", [_sz, _i32, _i32, ctypes.POINTER(_P)])
 _sig("isg_server_submit", [_P, _P, _i32, _P, _i32, _u64, _i64, ctypes.POINTER(_u64)])
 _sig("isg_server_poll", [_P, ctypes.POINTER(_u64), ctypes.POINTER(_P), _dbl])
 _sig("isg_server_destroy", [_P])
+_sig("isg_server_get_stats", [_P, ctypes.POINTER(isg_server_stats)])
 _sig("isg_integer_peaks", [_P, ctypes.POINTER(_dbl), ctypes.POINTER(_dbl)])
+_sig("isg_acceptance_table", [_P, _i32, _i32, _P])
 _sig("isg_last_error", [], ctypes.c_char_p)
 _sig("isg_version", [], ctypes.c_char_p)
 
@@ -288,6 +295,14 @@ def isg_energy_noalloc(n: int, rowptr_dev: int, col_dev: int, w_dev: int, spins_
                                    energies_dev, _stream(stream)))
 
 
+def isg_acceptance_table(betas, kmax: int) -> np.ndarray:
+    """[S][kmax + 1] uint32 thresholds the solve paths use (host computation)."""
+    b = _arr(betas, np.float64)
+    out = np.empty((b.shape[0], kmax + 1), dtype=np.uint32)
+    _check(_lib.isg_acceptance_table(_ptr(b), int(b.shape[0]), int(kmax), _ptr(out)))
+    return out
+
+
 def isg_integer_peaks(stream=None) -> dict:
     """Measured device-wide rates (thread-instructions/s) of lop3 and mad.wide.u32."""
     a, b = _dbl(), _dbl()
@@ -350,6 +365,9 @@ class Server:
     def poll(self, timeout_s: float = 1.0):
         return isg_server_poll(self, timeout_s)
 
+    def stats(self) -> dict:
+        return isg_server_get_stats(self)
+
     def close(self):
         if self.handle:
             h, self.handle = self.handle, None
@@ -364,6 +382,12 @@ class Server:
 
 def isg_server_create(device_mem_budget: int, max_slots: int, sweeps_per_chunk: int) -> Server:
     return Server(device_mem_budget, max_slots, sweeps_per_chunk)
+
+
+def isg_server_get_stats(s) -> dict:
+    st = isg_server_stats()
+    _check(_lib.isg_server_get_stats(_h(s), ctypes.byref(st)))
+    return {k: getattr(st, k) for k, _ in isg_server_stats._fields_}
 
 
 def isg_server_submit(s, p, replicas: int, betas, seed: int, target=None) -> int:

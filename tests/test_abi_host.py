@@ -100,3 +100,27 @@ def test_torus_colouring_is_checkerboard(isg):
     info = isg.isg_problem_info(isg.problem_of(t), colors=True)
     col, nc = oracle.csr_of(t).greedy_colouring()
     assert info["n_colors"] == 2 and np.array_equal(info["colors"], col)
+
+
+@pytest.mark.parametrize("kind", ["linear", "geometric", "extremes"])
+def test_acceptance_table_equals_oracle(isg, kind):
+    """The library's thresholds equal the oracle's, bit for bit (table parity)."""
+    if kind == "linear":
+        betas, kmax = I.linear_betas(0.1, 3.0, 1000), 4
+    elif kind == "geometric":
+        betas, kmax = I.geometric_betas(0.1, 5.0, 10000), 8
+    else:
+        betas, kmax = np.array([0.0, 1e-12, 0.5, 11.0, 1e3, 1e300]), 63
+    lib = isg.isg_acceptance_table(betas, kmax)
+    orc = oracle.accept_table(betas, kmax)
+    assert lib.dtype == np.uint32 and lib.shape == orc.shape
+    assert np.array_equal(lib, orc)
+
+
+def test_acceptance_table_rejects_bad_input(isg):
+    with pytest.raises(isg.IsgError):
+        isg.isg_acceptance_table(np.array([0.5, np.nan]), 2)
+    with pytest.raises(isg.IsgError):
+        isg.isg_acceptance_table(np.array([-0.1]), 2)
+    with pytest.raises(isg.IsgError):
+        isg.isg_acceptance_table(np.array([0.5]), -1)

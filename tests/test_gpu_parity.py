@@ -306,6 +306,10 @@ def test_server_results_equal_solo_runs(isg):
         out = srv.poll(30.0)
         assert out is not None, "server timed out"
         got[ids[out[0]]] = out[1]
+    st = srv.stats()
+    assert st["submitted"] == st["completed"] == len(reqs)
+    assert st["queued"] == 0 and st["active"] == 0
+    assert 1 <= st["peak_active"] <= 4 and st["passes"] >= 1
     srv.close()
     for k, (p, prob, R, seed) in enumerate(reqs):
         solo = isg.isg_anneal(p, R, betas, seed, target=targets[k])
