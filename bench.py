@@ -567,13 +567,85 @@ def run_served(args):
     print(json.dumps(line))
 
 
+# ---------------------------------------------------------------- paper-style TTT
+QUALITY_LEVELS = (0.99, 0.995, 0.997, 0.999, 1.0)
+HEADLINE_QUALITY = 0.995
+
+
+def run_ttt(args):
+    """Sweeps-to-target and time-to-target (Sec. II.B, eq. (1)-(2)) on synthetic
+    stand-ins with the shapes of Table I.  Each replica is one trial (one run of
+    the schedule).  The target stands in for the best-known value: the best
+    energy of a reference solve with four times the sweep budget and its own
+    seed.  P_s = fraction of the budget run's replicas whose best energy is at
+    or below the target; r from eq. (1); sweeps-to-target = budget x r;
+    TTT = t_trial x r with t_trial the device time of one replica's run when
+    all replicas share the GPU (kernel time / replicas), and the time until
+    at least one of a batch of all replicas succeeds with 99 %.  Targets: cut
+    values at several fractions of the reference cut (solution quality)."""
+    import torch
+    from paper_2311_09275_gb300 import isg, metrics
+    torch.cuda.set_device(0)
+    stream = torch.cuda.current_stream()
+    sweeps = args.sweeps or 10000
+    R = 1024
+    betas = I.geometric_betas(0.1, 5.0, sweeps)
+    ref_betas = I.geometric_betas(0.1, 5.0, 4 * sweeps)
+    rows = []
+    with ClockSampler(0) as clocks:
+        for label, prob in I.table1_stand_ins():
+            p = isg.problem_of(prob)
+            total_w = p.total_weight
+            ref = isg.isg_anneal(p, R, ref_betas, 7777, stream=stream)
+            target = int(ref.best(spins=False)[0])
+            ref.close()
+            res = isg.isg_anneal(p, R, betas, 1, stream=stream, time_kernels=True)
+            per = res.best(spins=False)[3]
+            k_s = res.stats()["sweep_kernel_ms"] / 1e3
+            res.close()
+            row = {"instance": label, "n": p.n, "run_s": k_s,
+                   "mean_best_energy": float(np.mean(per)), "targets": []}
+            # targets at fractions of the reference cut (solution quality, Sec. II.B):
+            # cut >= ceil(q * reference cut), i.e. E <= W - 2 ceil(q * cut_ref)
+            cut_ref = metrics.cut_value(total_w, target)
+            for q in QUALITY_LEVELS:
+                cut_t = int(np.ceil(q * cut_ref - 1e-9))
+                tgt = total_w - 2 * cut_t
+                ps = float(np.mean(per <= tgt))
+                p_batch = 1.0 - (1.0 - ps) ** R
+                fin = (lambda x: x if np.isfinite(x) else None)
+                row["targets"].append({
+                    "quality": q, "target_cut": cut_t, "target_energy": tgt, "p_success": ps,
+                    "repetitions": fin(metrics.repetitions(ps)),
+                    "sweeps_to_target": fin(metrics.sweeps_to_target(sweeps, ps)),
+                    "ttt_s_per_trial": fin(metrics.time_to_target(k_s / R, ps)),
+                    "ttt_s_batch": fin(metrics.time_to_target(k_s, p_batch))})
+            # MaxCut form (Sec. II.A): cut = (W - E) / 2; quality = cut / reference cut
+            row["mean_quality"] = ((total_w - float(np.mean(per))) / 2.0 /
+                                   metrics.cut_value(total_w, target))
+            rows.append(row)
+            p.close()
+    head = next(t for t in rows[0]["targets"] if t["quality"] == HEADLINE_QUALITY)
+    line = {"metric": "sweeps-to-target (99%)", "value": head["sweeps_to_target"],
+            "unit": "sweeps", "n_gpus": 1, "steps": 1, "warmup": 0,
+            "ms_per_step": 1e3 * sum(x["run_s"] for x in rows), "higher_is_better": False,
+            "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+            "config": {"workload": f"table1_stand_ins_R{R}_S{sweeps}_geometric_0.1_5.0",
+                       "target": "best of a 4x-budget reference solve (1,024 replicas, seed 7777)",
+                       "value_is": f"{rows[0]['instance']}, target cut = {HEADLINE_QUALITY} x "
+                                   f"reference cut"},
+            "instances": rows, "clocks": clocks.summary()}
+    print(json.dumps(line))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--config", default="torus", choices=["torus", "random", "batch", "served"])
+    ap.add_argument("--config", default="torus",
+                    choices=["torus", "random", "batch", "served", "ttt"])
     ap.add_argument("--requests", type=int, default=2000, help="served: number of requests")
     ap.add_argument("--slots", type=int, default=512, help="served: maximum resident requests")
     ap.add_argument("--chunk", type=int, default=250, help="served: sweeps per chunk")
@@ -594,6 +666,8 @@ def main():
         run_batch(args)
     elif args.config == "served":
         run_served(args)
+    elif args.config == "ttt":
+        run_ttt(args)
     else:
         run_gpu(args)
 

@@ -67,13 +67,13 @@ def _load():
         lib.orc_greedy_colouring.argtypes = [i32, P, P, P]
         lib.orc_greedy_colouring.restype = i32
         lib.orc_accept_table.argtypes = [i32, P, i32, P]
-        lib.orc_energy.argtypes = [i32, P, P, P, P]
+        lib.orc_energy.argtypes = [i32, P, P, P, P, P]
         lib.orc_energy.restype = i64
-        lib.orc_anneal.argtypes = [i32, P, P, P, P, i32, i32, P, i32, P, u64, ctypes.c_int, i64,
+        lib.orc_anneal.argtypes = [i32, P, P, P, P, P, i32, i32, P, i32, P, u64, ctypes.c_int, i64,
                                    u64, ctypes.c_int, ctypes.c_int, P, P, P, P, P, P]
         lib.orc_anneal.restype = ctypes.c_int
         lib.orc_initial_spins.argtypes = [i32, i32, P, u64, P]
-        lib.orc_enumerate.argtypes = [i32, P, P, P, P, P]
+        lib.orc_enumerate.argtypes = [i32, P, P, P, P, P, P]
         lib.orc_enumerate.restype = i64
         _lib = lib
         return lib
@@ -97,10 +97,14 @@ def philox4x32_10(ctr, key) -> np.ndarray:
 
 
 class Csr:
-    """Symmetric CSR built by the oracle from an edge list (neighbours ascending)."""
+    """Symmetric CSR built by the oracle from an edge list (neighbours ascending),
+    with optional integer local fields h[n] (E gains sum_i h_i s_i)."""
 
-    def __init__(self, n: int, u, v, w):
+    def __init__(self, n: int, u, v, w, h=None):
         u, v, w = _arr(u, np.int32), _arr(v, np.int32), _arr(w, np.int32)
+        self.field = None if h is None else _arr(h, np.int32)
+        if self.field is not None and self.field.shape != (n,):
+            raise ValueError("fields need one entry per vertex")
         m = int(u.shape[0])
         self.n = int(n)
         self.m = m
@@ -113,9 +117,13 @@ class Csr:
             raise ValueError("invalid edge list (range, self-loop or duplicate)")
         self.total_weight = int(w.astype(np.int64).sum())
 
+    def _fp(self):
+        return _p(self.field) if self.field is not None else None
+
     def energy(self, s) -> int:
         s = _arr(s, np.int8)
-        return int(_load().orc_energy(self.n, _p(self.rowptr), _p(self.col), _p(self.wt), _p(s)))
+        return int(_load().orc_energy(self.n, _p(self.rowptr), _p(self.col), _p(self.wt),
+                                      self._fp(), _p(s)))
 
     def greedy_colouring(self):
         colour = np.zeros(self.n, dtype=np.int32)
@@ -123,11 +131,13 @@ class Csr:
         return colour, int(nc)
 
     def kmax(self) -> int:
-        """max_i sum_j |w_ij|: the largest half energy change of one flip."""
+        """max_i (sum_j |w_ij| + |h_i|): the largest half energy change of one flip."""
         deg = np.diff(self.rowptr)
         rows = np.repeat(np.arange(self.n), deg)
         sums = np.zeros(self.n, dtype=np.int64)
         np.add.at(sums, rows, np.abs(self.wt[: 2 * self.m].astype(np.int64)))
+        if self.field is not None:
+            sums += np.abs(self.field.astype(np.int64))
         return int(sums.max()) if self.n else 0
 
     def enumerate(self, histogram: bool = False):
@@ -136,10 +146,12 @@ class Csr:
         if self.n > 30:
             raise ValueError("enumeration needs n <= 30")
         wabs = int(np.abs(self.wt[: 2 * self.m].astype(np.int64)).sum() // 2)
+        if self.field is not None:
+            wabs += int(np.abs(self.field.astype(np.int64)).sum())
         argmin = np.zeros(self.n, dtype=np.int8)
         hist = np.zeros(2 * wabs + 1, dtype=np.uint64) if histogram else None
-        e = _load().orc_enumerate(self.n, _p(self.rowptr), _p(self.col), _p(self.wt), _p(argmin),
-                                  _p(hist) if hist is not None else None)
+        e = _load().orc_enumerate(self.n, _p(self.rowptr), _p(self.col), _p(self.wt), self._fp(),
+                                  _p(argmin), _p(hist) if hist is not None else None)
         if histogram:
             return int(e), argmin, hist, -wabs
         return int(e), argmin
@@ -160,7 +172,7 @@ def csr_of(problem) -> Csr:
     """Oracle CSR of an instance from the input generators (torus or graph)."""
     if hasattr(problem, "L"):
         return torus_csr(problem.L, problem.W, problem.j_right, problem.j_down)
-    return Csr(problem.n, problem.u, problem.v, problem.w)
+    return Csr(problem.n, problem.u, problem.v, problem.w, getattr(problem, "h", None))
 
 
 def accept_table(betas, kmax: int) -> np.ndarray:
@@ -220,7 +232,7 @@ def anneal(csr: Csr, replicas, betas, seed: int, colour=None, target=None,
     done = ctypes.c_int32(0)
     if nthreads <= 0:
         nthreads = min(os.cpu_count() or 1, k)
-    rc = _load().orc_anneal(n, _p(csr.rowptr), _p(csr.col), _p(csr.wt), _p(colour), nc, k,
+    rc = _load().orc_anneal(n, _p(csr.rowptr), _p(csr.col), _p(csr.wt), csr._fp(), _p(colour), nc, k,
                             _p(reps), S, _p(b), int(seed), 1 if target is not None else 0,
                             int(target) if target is not None else 0, int(shuffle_seed),
                             1 if check_energy else 0, int(nthreads), _p(s_final), _p(e_final),

@@ -162,11 +162,13 @@ void orc_accept_table(int32_t sweeps, const double *betas, int32_t kmax, uint32_
 }
 
 int64_t orc_energy(int32_t n, const int64_t *rowptr, const int32_t *col, const int32_t *wt,
-                   const int8_t *s) {
+                   const int32_t *field, const int8_t *s) {
     int64_t e = 0;
-    for (int32_t i = 0; i < n; ++i)
+    for (int32_t i = 0; i < n; ++i) {
         for (int64_t p = rowptr[i]; p < rowptr[i + 1]; ++p)
             if (col[p] > i) e += (int64_t)wt[p] * s[i] * s[col[p]];
+        if (field) e += (int64_t)field[i] * s[i];
+    }
     return e;
 }
 
@@ -178,6 +180,7 @@ typedef struct {
     const int64_t *rowptr;
     const int32_t *col;
     const int32_t *wt;
+    const int32_t *field;       /* local fields h_i, or NULL */
     const int32_t *order;       /* vertices grouped by colour class */
     const int64_t *class_start; /* n_colours + 1 entries */
     int32_t n_colours;
@@ -206,7 +209,7 @@ static void orc_run_replica(orc_job *J, int32_t k) {
     int8_t *best = J->s_best + (int64_t)k * n;
     for (int32_t i = 0; i < n; ++i)
         s[i] = (orc_draw(J->seed, (uint32_t)i, 0u, r, ORC_TAG_INIT) >> 31) ? 1 : -1;
-    int64_t e = orc_energy(n, J->rowptr, J->col, J->wt, s);
+    int64_t e = orc_energy(n, J->rowptr, J->col, J->wt, J->field, s);
     int64_t e_best = e;
     memcpy(best, s, (size_t)n);
     J->hit[k] = -1;
@@ -215,7 +218,7 @@ static void orc_run_replica(orc_job *J, int32_t k) {
         for (int32_t c = 0; c < J->n_colours; ++c) {
             for (int64_t q = J->class_start[c]; q < J->class_start[c + 1]; ++q) {
                 int32_t i = J->order[q];
-                int64_t h = 0;
+                int64_t h = J->field ? J->field[i] : 0;
                 for (int64_t p = J->rowptr[i]; p < J->rowptr[i + 1]; ++p)
                     h += (int64_t)J->wt[p] * s[J->col[p]];
                 int64_t kk = -(int64_t)s[i] * h; /* energy change of the flip is 2*kk */
@@ -230,7 +233,7 @@ static void orc_run_replica(orc_job *J, int32_t k) {
                 }
             }
         }
-        if (J->check_energy && orc_energy(n, J->rowptr, J->col, J->wt, s) != e) {
+        if (J->check_energy && orc_energy(n, J->rowptr, J->col, J->wt, J->field, s) != e) {
             J->status = -2;
             return;
         }
@@ -283,7 +286,7 @@ static int orc_run_pass(orc_job *proto, int32_t n_rep, int nthreads) {
 }
 
 int orc_anneal(int32_t n, const int64_t *rowptr, const int32_t *col, const int32_t *wt,
-               const int32_t *colour, int32_t n_colours,
+               const int32_t *field, const int32_t *colour, int32_t n_colours,
                int32_t n_rep, const int32_t *rep_ids, int32_t sweeps, const double *betas,
                uint64_t seed, int has_target, int64_t target, uint64_t shuffle_seed,
                int check_energy, int nthreads,
@@ -292,10 +295,11 @@ int orc_anneal(int32_t n, const int64_t *rowptr, const int32_t *col, const int32
     if (n < 1 || n_rep < 1 || sweeps < 1 || n_colours < 1) return -1;
     for (int32_t i = 0; i < n; ++i)
         if (colour[i] < 0 || colour[i] >= n_colours) return -1;
-    /* kmax = max_i sum_j |w_ij| bounds the energy change of any single flip by 2*kmax */
+    /* kmax = max_i (sum_j |w_ij| + |h_i|) bounds the energy change of any
+     * single flip by 2*kmax */
     int64_t kmax = 0;
     for (int32_t i = 0; i < n; ++i) {
-        int64_t a = 0;
+        int64_t a = field ? llabs((long long)field[i]) : 0;
         for (int64_t p = rowptr[i]; p < rowptr[i + 1]; ++p) a += llabs((long long)wt[p]);
         if (a > kmax) kmax = a;
     }
@@ -327,7 +331,7 @@ int orc_anneal(int32_t n, const int64_t *rowptr, const int32_t *col, const int32
     int32_t *hit = (int32_t *)malloc(sizeof(int32_t) * (size_t)n_rep);
     orc_job job;
     memset(&job, 0, sizeof(job));
-    job.n = n; job.rowptr = rowptr; job.col = col; job.wt = wt;
+    job.n = n; job.rowptr = rowptr; job.col = col; job.wt = wt; job.field = field;
     job.order = order; job.class_start = class_start; job.n_colours = n_colours;
     job.table = table; job.kmax = (int32_t)kmax; job.seed = seed; job.betas = betas;
     job.check_energy = check_energy; job.has_target = has_target; job.target = target;
@@ -362,22 +366,23 @@ int orc_anneal(int32_t n, const int64_t *rowptr, const int32_t *col, const int32
 /* Exhaustive enumeration in Gray-code order: state g differs from g-1 in the
  * spin of index ctz(g), so each step costs one local-field evaluation. */
 int64_t orc_enumerate(int32_t n, const int64_t *rowptr, const int32_t *col, const int32_t *wt,
-                      int8_t *argmin, uint64_t *hist) {
+                      const int32_t *field, int8_t *argmin, uint64_t *hist) {
     int8_t *s = (int8_t *)malloc((size_t)n);
     int64_t wabs = 0;
     for (int32_t i = 0; i < n; ++i) {
         s[i] = -1;
+        if (field) wabs += llabs((long long)field[i]);
         for (int64_t p = rowptr[i]; p < rowptr[i + 1]; ++p)
             if (col[p] > i) wabs += llabs((long long)wt[p]);
     }
-    int64_t e = orc_energy(n, rowptr, col, wt, s);
+    int64_t e = orc_energy(n, rowptr, col, wt, field, s);
     int64_t e_min = e;
     uint64_t g_min = 0;
     if (hist) hist[e + wabs]++;
     uint64_t count = (uint64_t)1 << n;
     for (uint64_t g = 1; g < count; ++g) {
         int32_t j = __builtin_ctzll(g);
-        int64_t h = 0;
+        int64_t h = field ? field[j] : 0;
         for (int64_t p = rowptr[j]; p < rowptr[j + 1]; ++p) h += (int64_t)wt[p] * s[col[p]];
         e += -2 * (int64_t)s[j] * h;
         s[j] = (int8_t)(-s[j]);

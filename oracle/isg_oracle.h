@@ -9,7 +9,10 @@
  * Problem (paper Sec. I and Sec. II.A): binary spins s_i in {-1,+1}, pairwise
  * integer couplings w_ij on a sparse graph; MaxCut value
  * cut(s) = sum_{(i,j)} w_ij (1 - s_i s_j) / 2.  The oracle minimises
- * E(s) = sum_{(i,j)} w_ij s_i s_j, so cut = (W_tot - E) / 2.
+ * E(s) = sum_{(i,j)} w_ij s_i s_j, so cut = (W_tot - E) / 2.  Optional integer
+ * local fields h_i (the sparse QUBO and independent-set forms of Sec. I and
+ * Sec. II.C, which lack spin-reversal symmetry) add sum_i h_i s_i to E; every
+ * `field` argument below may be NULL for none.
  *
  * Method: the paper's own heuristic ("Cosm", Sec. III.A) is undisclosed; it is
  * iterative and counts its work in sweeps.  The computation reproduced here is
@@ -47,13 +50,15 @@ int32_t orc_greedy_colouring(int32_t n, const int64_t *rowptr, const int32_t *co
  * for k = 0..kmax (energy increase d = 2k), in FP64. */
 void orc_accept_table(int32_t sweeps, const double *betas, int32_t kmax, uint32_t *table);
 
-/* E(s) = sum over edges w_ij s_i s_j for one configuration s[0..n-1] (+/-1). */
+/* E(s) = sum over edges w_ij s_i s_j + sum_i h_i s_i for one configuration
+ * s[0..n-1] (+/-1). */
 int64_t orc_energy(int32_t n, const int64_t *rowptr, const int32_t *col, const int32_t *wt,
-                   const int8_t *s);
+                   const int32_t *field, const int8_t *s);
 
 /* Metropolis annealing, one independent chain per listed replica.
  *
- * Inputs: CSR (rowptr, col, wt), colour[n] (classes 0..n_colours-1), the
+ * Inputs: CSR (rowptr, col, wt), fields (or NULL; the local field of vertex i
+ * is h_i + sum_j w_ij s_j), colour[n] (classes 0..n_colours-1), the
  * replica indices to run (rep_ids[0..n_rep-1], each < 2^31), sweeps S,
  * betas[S], seed, optional target (has_target != 0), shuffle_seed (0 = sites
  * of a class in ascending id; otherwise a seeded shuffle of each class, which
@@ -66,7 +71,7 @@ int64_t orc_energy(int32_t n, const int64_t *rowptr, const int32_t *col, const i
  * replica of the solve must be listed.  Returns 0, -1 on bad arguments, -2 on
  * an energy-tracking mismatch. */
 int orc_anneal(int32_t n, const int64_t *rowptr, const int32_t *col, const int32_t *wt,
-               const int32_t *colour, int32_t n_colours,
+               const int32_t *field, const int32_t *colour, int32_t n_colours,
                int32_t n_rep, const int32_t *rep_ids, int32_t sweeps, const double *betas,
                uint64_t seed, int has_target, int64_t target, uint64_t shuffle_seed,
                int check_energy, int nthreads,
@@ -80,9 +85,9 @@ void orc_initial_spins(int32_t n, int32_t n_rep, const int32_t *rep_ids, uint64_
  * Returns the minimum energy; writes one minimising state to argmin (if not
  * NULL) and, if hist is not NULL, the number of states with energy
  * E = e_lo + k into hist[k] for k = 0..(e_hi - e_lo) where
- * e_lo = -sum|w|, e_hi = +sum|w|. */
+ * e_lo = -(sum|w| + sum|h|), e_hi = -e_lo. */
 int64_t orc_enumerate(int32_t n, const int64_t *rowptr, const int32_t *col, const int32_t *wt,
-                      int8_t *argmin, uint64_t *hist);
+                      const int32_t *field, int8_t *argmin, uint64_t *hist);
 
 #ifdef __cplusplus
 }

@@ -39,6 +39,7 @@ STREAM_EDGES = 2
 STREAM_SIZES = 3
 STREAM_ARRIVALS = 4
 STREAM_KIND = 5
+STREAM_POINTS = 6
 
 
 def _mix64(z: np.ndarray) -> np.ndarray:
@@ -109,11 +110,13 @@ class Torus:
 
 @dataclasses.dataclass
 class Graph:
-    """Undirected weighted graph given as an edge list with n vertices."""
+    """Undirected weighted graph given as an edge list with n vertices, and
+    optional integer local fields h[n] (None: no fields)."""
     n: int
     u: np.ndarray
     v: np.ndarray
     w: np.ndarray
+    h: np.ndarray | None = None
 
     @property
     def m(self) -> int:
@@ -227,6 +230,67 @@ def torus_80x100(sweeps: int = 10000, replicas: int = 1024) -> Solve:
 def random_10000(sweeps: int = 10000, replicas: int = 256) -> Solve:
     """n = 10,000, m = 9,999 unweighted random graph (the G70 shape), 256 replicas."""
     return Solve(random_graph(10000, 9999, 1), replicas, geometric_betas(0.1, 5.0, sweeps), 1)
+
+
+def geometric_graph(n: int, mean_degree: float, seed: int) -> Graph:
+    """Random geometric graph: n points uniform in the unit square (two draws
+    each), an edge between every pair closer than r, with n pi r^2 =
+    mean_degree (boundary effects make the realised mean slightly lower)."""
+    k = np.arange(n, dtype=np.uint64)
+    x = uniform_float(seed, STREAM_POINTS, 2 * k)
+    y = uniform_float(seed, STREAM_POINTS, 2 * k + np.uint64(1))
+    r = math.sqrt(mean_degree / (math.pi * n))
+    cells = max(1, int(1.0 / r))
+    cx = np.minimum((x * cells).astype(np.int64), cells - 1)
+    cy = np.minimum((y * cells).astype(np.int64), cells - 1)
+    cell = cx * cells + cy
+    order = np.argsort(cell, kind="stable")
+    start = np.searchsorted(cell[order], np.arange(cells * cells + 1))
+    us, vs = [], []
+    for dx in (-1, 0, 1):
+        for dy in (-1, 0, 1):
+            nx, ny = cx + dx, cy + dy
+            ok = (nx >= 0) & (nx < cells) & (ny >= 0) & (ny < cells)
+            for i in np.nonzero(ok)[0]:
+                c = nx[i] * cells + ny[i]
+                js = order[start[c]:start[c + 1]]
+                js = js[js > i]
+                d2 = (x[js] - x[i]) ** 2 + (y[js] - y[i]) ** 2
+                js = js[d2 < r * r]
+                us.append(np.full(js.shape[0], i))
+                vs.append(js)
+    u = np.concatenate(us) if us else np.zeros(0, np.int64)
+    v = np.concatenate(vs) if vs else np.zeros(0, np.int64)
+    e = np.lexsort((v, u))
+    u, v = u[e].astype(np.int32), v[e].astype(np.int32)
+    return Graph(n, u, v, np.ones(u.shape[0], dtype=np.int32))
+
+
+def independent_set_instance(g: Graph) -> Graph:
+    """Maximum independent set of g as an Ising instance with local fields.
+
+    With x_i = (1 + s_i)/2, the penalty form  -sum_i x_i + 2 sum_(i,j) x_i x_j
+    (minimised by a maximum independent set) equals (E + m - n) / 2 for
+    E(s) = sum_(i,j) s_i s_j + sum_i (deg_i - 1) s_i: couplings +1, fields
+    h_i = deg_i - 1.  The set of a configuration is {i : s_i = +1}."""
+    deg = np.bincount(np.concatenate([g.u, g.v]), minlength=g.n).astype(np.int32)
+    return Graph(g.n, g.u, g.v, np.ones(g.m, dtype=np.int32), deg - 1)
+
+
+def table1_stand_ins():
+    """Synthetic stand-ins with the shapes of the Gset instances of Table I:
+    +/-1 tori with the listed variable counts (sides 80..200 x 100; the side
+    split is an assumption, the table gives only n and m = 2n) and an
+    unweighted random graph with n = 10,000, m = 9,999 (G70's shape).  The
+    second 10,000-variable torus (G72's row) takes another coupling seed.
+    Returns (label, problem) pairs; labels name the row whose shape is used."""
+    return [("G65-shape 80x100", torus(80, 100, 65)),
+            ("G66-shape 90x100", torus(90, 100, 66)),
+            ("G67-shape 100x100", torus(100, 100, 67)),
+            ("G70-shape n10000 m9999", random_graph(10000, 9999, 70)),
+            ("G72-shape 100x100", torus(100, 100, 72)),
+            ("G77-shape 140x100", torus(140, 100, 77)),
+            ("G81-shape 200x100", torus(200, 100, 81))]
 
 
 def batch_sizes(count: int = 512, seed: int = 4):
