@@ -199,6 +199,9 @@ def workload(config: str, rank: int, sweeps: int | None = None):
     elif config == "random":
         sv = I.random_10000(sweeps=sweeps or 10000)
         name = f"random_n10000_m9999_R256_S{sv.sweeps}_geometric_0.1_5.0"
+    elif config == "mis":
+        sv = I.independent_set_10000(sweeps=sweeps or 10000)
+        name = f"independent_set_geometric_n10000_deg6_R256_S{sv.sweeps}_geometric_0.1_5.0"
     else:
         raise ValueError(config)
     sv.seed = sv.seed + rank
@@ -352,17 +355,14 @@ def run_gpu(args):
         r = isg.isg_anneal(q, sv.replicas, sv.betas, sv.seed, stream=stream)
         spins, energies, done = r.final(spins=True)           # D2H final state
         be, br, bspins, per, hit = r.best(spins=True)         # D2H best state
+        h2d = r.stats()["h2d_bytes"]                          # instance arrays + thresholds
         r.close()
         q.close()
     torch.cuda.synchronize()
     e2e_s = max_over_ranks(time.perf_counter() - t0, dist, device)
-    units = (sv.replicas + 31) // 32 if hasattr(sv.problem, "L") else (sv.replicas + 3) // 4
-    lanes = units * (32 if hasattr(sv.problem, "L") else 4)
-    if hasattr(sv.problem, "L"):
-        h2d = sv.n + 4 * 2 * sv.sweeps                        # coupling bits + thresholds
-    else:
-        h2d = 4 * (3 * sv.n + 4 * sv.problem.m + 32) + 4 * (sv.sweeps * 16)
-    d2h = spins.nbytes + bspins.nbytes + 4 * (2 * lanes + units + 1)
+    # spins and energies read back: final [R][n] + energies [R] + sweeps, best [n] +
+    # per-replica best [R] + energy, replica, hit
+    d2h = spins.nbytes + energies.nbytes + 4 + bspins.nbytes + per.nbytes + 12
     e2e_value = sum_over_ranks(float(sv.attempts) * e2e_steps, dist, device) / e2e_s
 
     # ---- roofline of the sweep kernel (integer issue)
@@ -645,7 +645,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--config", default="torus",
-                    choices=["torus", "random", "batch", "served", "ttt"])
+                    choices=["torus", "random", "mis", "batch", "served", "ttt"])
     ap.add_argument("--requests", type=int, default=2000, help="served: number of requests")
     ap.add_argument("--slots", type=int, default=512, help="served: maximum resident requests")
     ap.add_argument("--chunk", type=int, default=250, help="served: sweeps per chunk")

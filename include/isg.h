@@ -80,6 +80,18 @@ typedef struct isg_server isg_server;
 isg_status isg_problem_create_edges(int32_t n, int64_t m, const int32_t *u, const int32_t *v,
                                     const int32_t *w, isg_problem **out);
 
+/* The same with integer local fields h[n] (NULL = none): the energy becomes
+ * E(s) = sum_(i,j) w_ij s_i s_j + sum_i h_i s_i, the form of sparse QUBO and of
+ * independent-set problems (Sec. I; Sec. II.C notes they lack spin-reversal
+ * symmetry).  A flip of i changes E by -2 s_i (h_i + sum_j w_ij s_j).  Such
+ * instances run on the int8 colour-class kernel (ISG_KERNEL_CSR or
+ * ISG_KERNEL_PLAIN; the multi-spin kernels reject them).  total_weight of
+ * isg_problem_info stays sum w, so the MaxCut identity cut = (W - E) / 2 does
+ * not apply.  EINVAL as isg_problem_create_edges, with sum |w| + sum |h| >= 2^30
+ * in place of the weight bound.  h is copied. */
+isg_status isg_problem_create_fields(int32_t n, int64_t m, const int32_t *u, const int32_t *v,
+                                     const int32_t *w, const int32_t *h, isg_problem **out);
+
 /* Instance from a symmetric CSR: rowptr[n+1] (rowptr[0] = 0), col/w of
  * rowptr[n] entries; entry (i, j, w) must have its mirror (j, i, w).
  * Same validity rules as isg_problem_create_edges. */
@@ -160,7 +172,8 @@ isg_status isg_anneal_batch(const isg_problem *const *probs, int32_t count, int3
                             const int64_t *targets, void *cuda_stream, isg_result **outs);
 
 /* Energies E(s) of R host configurations spins[R][n] (+-1) into energies[R],
- * computed on the device (a check of the tracked energies). */
+ * computed on the device (a check of the tracked energies); local fields
+ * included. */
 isg_status isg_energy(const isg_problem *p, const int8_t *spins, int32_t replicas,
                       int64_t *energies);
 
@@ -169,7 +182,8 @@ isg_status isg_energy(const isg_problem *p, const int8_t *spins, int32_t replica
  * latency-critical loop that must stay out of the driver's allocator).  No
  * counterpart in the paper: this is a library convenience.
  * All arguments are DEVICE pointers owned by the caller: a symmetric CSR in
- * the caller's vertex ids (rowptr_dev[n+1] int64, col_dev/w_dev[rowptr[n]]),
+ * the caller's vertex ids (rowptr_dev[n+1] int64, col_dev/w_dev[rowptr[n]];
+ * couplings only: local fields are not part of this energy),
  * spins_dev[replicas][n] int8 +-1, and energies_dev[replicas] int64 (output).
  * The work is enqueued on cuda_stream (NULL = legacy default stream) and
  * nothing is allocated or freed: per-block partial sums live in a fixed
@@ -210,6 +224,8 @@ typedef struct {
     int32_t ctas;            /* CTAs of the sweep kernel */
     int32_t cluster_ctas;    /* CTAs per cluster */
     int32_t threads;         /* threads per CTA */
+    int64_t h2d_bytes;       /* host-to-device bytes the solve copied: its threshold table
+                                and the instance arrays uploaded for it (0 if resident) */
 } isg_stats;
 
 isg_status isg_result_stats(const isg_result *r, isg_stats *stats);

@@ -52,7 +52,8 @@ __global__ void unpack_quads_kernel(const uint32_t *__restrict__ quads, int n, i
 // sum_{j > i} w_ij s_i s_j for replica r (edges counted once, at the lower end).
 __global__ void energy_partial_kernel(const int64_t *__restrict__ rowptr,
                                       const int32_t *__restrict__ col,
-                                      const int32_t *__restrict__ wt, int n,
+                                      const int32_t *__restrict__ wt,
+                                      const int32_t *__restrict__ field, int n,
                                       const int8_t *__restrict__ spins, int64_t *scratch) {
   const int r = blockIdx.y;
   const int8_t *s = spins + (size_t)r * n;
@@ -63,6 +64,7 @@ __global__ void energy_partial_kernel(const int64_t *__restrict__ rowptr,
       const int j = col[p];
       if (j > i) acc += (int64_t)wt[p] * si * s[j];
     }
+    if (field) acc += (int64_t)field[i] * si;
   }
   __shared__ int64_t red[32];
   for (int off = 16; off > 0; off >>= 1) acc += __shfl_down_sync(0xFFFFFFFFu, acc, off);
@@ -143,8 +145,9 @@ cudaError_t unpack_quads(const uint32_t *quads, int32_t n, int32_t R, const int3
 
 cudaError_t energy_csr(const int64_t *rowptr, const int32_t *col, const int32_t *wt, int32_t n,
                        const int8_t *spins, int32_t R, int64_t *scratch, int32_t blocks,
-                       int64_t *energies, cudaStream_t stream) {
-  energy_partial_kernel<<<dim3(blocks, R), 256, 0, stream>>>(rowptr, col, wt, n, spins, scratch);
+                       int64_t *energies, cudaStream_t stream, const int32_t *field) {
+  energy_partial_kernel<<<dim3(blocks, R), 256, 0, stream>>>(rowptr, col, wt, field, n, spins,
+                                                               scratch);
   cudaError_t err = cudaGetLastError();
   if (err != cudaSuccess) return err;
   energy_finish_kernel<<<(R + 255) / 256, 256, 0, stream>>>(scratch, blocks, R, energies);

@@ -116,16 +116,17 @@ struct Adj {
   const int32_t *orig;  // original ids
 };
 
-// Half energy changes kk[l] = -s_l h_l of the Q quads of vertex v (row slot i).
+// Half energy changes kk[l] = -s_l h_l of the Q quads of vertex v (row slot
+// i), where h_l = hv + sum_j w_vj s_j (hv: the vertex's local field, or 0).
 template <int Q, int MODE>
 __device__ __forceinline__ void fields(const uint32_t *spin, int n, int v, int p0, int p1,
-                                       const Adj &a, int32_t (&kk)[Q][4]) {
+                                       const Adj &a, int32_t hv, int32_t (&kk)[Q][4]) {
   if (MODE == 2) {
     int32_t h[Q][4];
 #pragma unroll
     for (int q = 0; q < Q; ++q)
 #pragma unroll
-      for (int l = 0; l < 4; ++l) h[q][l] = 0;
+      for (int l = 0; l < 4; ++l) h[q][l] = hv;
     for (int p = p0; p < p1; ++p) {
       const int j = a.col[p];
       const int32_t wv = a.wt[p];
@@ -170,8 +171,8 @@ __device__ __forceinline__ void fields(const uint32_t *spin, int n, int v, int p
       const uint32_t sv = spin[q * n + v];
 #pragma unroll
       for (int l = 0; l < 4; ++l) {
-        // h = (dpos - 2 * minus_pos) - (dneg - 2 * minus_neg)
-        int32_t h = dpos - 2 * (int32_t)((cpos[q] >> (8 * l)) & 0xFFu);
+        // h = hv + (dpos - 2 * minus_pos) - (dneg - 2 * minus_neg)
+        int32_t h = hv + dpos - 2 * (int32_t)((cpos[q] >> (8 * l)) & 0xFFu);
         if (MODE == 1) h -= dneg - 2 * (int32_t)((cneg[q] >> (8 * l)) & 0xFFu);
         const int32_t m = -(int32_t)((sv >> (8 * l + 1)) & 1u);  // -1 if s_l = -1
         kk[q][l] = ((-h) ^ m) - m;                               // -s_l h
@@ -292,6 +293,11 @@ __device__ void csr_solve(const CsrSolve &s, const CsrLaunch &L, int quad0, int 
 #pragma unroll
             for (int l = 0; l < 4; ++l) vals[q][l] += wv * lane8(sv, l) * lane8(su, l);
           }
+          if (s.field) {
+            const int32_t hv = s.field[v];
+#pragma unroll
+            for (int l = 0; l < 4; ++l) vals[q][l] += hv * lane8(sv, l);
+          }
           if (quad0 + q < s.quads) s.best[(size_t)(quad0 + q) * n + v] = sv;
         }
       }
@@ -350,7 +356,7 @@ __device__ void csr_solve(const CsrSolve &s, const CsrLaunch &L, int quad0, int 
           blend_best<Q>(s.best, spin, n, v, quad0, bm);
         }
         int32_t kk[Q][4];
-        fields<Q, MODE>(spin, n, v, p0, p1, adj, kk);
+        fields<Q, MODE>(spin, n, v, p0, p1, adj, s.field ? __ldg(&s.field[v]) : 0, kk);
 #pragma unroll
         for (int q = 0; q < Q; ++q) {
           // lanes with kk > 0 are uphill; the rest are always taken

@@ -91,7 +91,8 @@ struct CsrSolve {
   const int32_t *col;          // [nnz] relabelled neighbour ids
   const int32_t *wt;           // [nnz]
   const int32_t *orig;         // [n] original id of each relabelled vertex
-  int32_t kmax;                // max_i sum_j |w_ij|
+  const int32_t *field;        // [n] local fields h (relabelled order), or nullptr
+  int32_t kmax;                // max_i (sum_j |w_ij| + |h_i|)
   const uint32_t *table;       // [sweeps][kmax + 1]
   uint32_t key0, key1;
   int32_t quads;               // ceil(R / 4)
@@ -207,7 +208,8 @@ cudaError_t unpack_quads(const uint32_t *quads, int32_t n, int32_t R, const int3
 // per-block partial sums in scratch[R * blocks], then one sum per replica.
 cudaError_t energy_csr(const int64_t *rowptr, const int32_t *col, const int32_t *wt, int32_t n,
                        const int8_t *spins, int32_t R, int64_t *scratch, int32_t blocks,
-                       int64_t *energies, cudaStream_t stream);
+                       int64_t *energies, cudaStream_t stream,
+                       const int32_t *field = nullptr);
 // Unpack every batch item's state and stop sweep (one launch for the batch;
 // items with word 0 and R <= 32 replicas).
 cudaError_t batch_finish(const TorusBatchItem *items_dev, int32_t count, int32_t max_n,

@@ -50,7 +50,8 @@ isg_status finish_problem(isg_problem *p) {
   p->kmax = 0;
   int64_t wsum = 0, wabs = 0;
   for (int32_t i = 0; i < p->n; ++i) {
-    int64_t a = 0;
+    int64_t a = p->field.empty() ? 0 : std::llabs((long long)p->field[i]);
+    wabs += a;
     for (int64_t q = p->rowptr[i]; q < p->rowptr[i + 1]; ++q) {
       a += std::llabs((long long)p->wt[q]);
       if (p->col[q] > i) {
@@ -61,7 +62,8 @@ isg_status finish_problem(isg_problem *p) {
     p->kmax = std::max<int64_t>(p->kmax, a);
   }
   if (wabs >= (int64_t(1) << 30))
-    return fail(ISG_EINVAL, "sum of |w| = %lld is >= 2^30 (int32 energies)", (long long)wabs);
+    return fail(ISG_EINVAL, "sum of |w| + |h| = %lld is >= 2^30 (int32 energies)",
+                (long long)wabs);
   p->total_weight = wsum;
   p->m = p->rowptr[p->n] / 2;
   // colouring
@@ -118,6 +120,11 @@ isg_status finish_problem(isg_problem *p) {
   }
   std::vector<int32_t> inv(p->n);
   for (int32_t v = 0; v < p->n; ++v) inv[p->order[v]] = v;
+  p->field_r.clear();
+  if (!p->field.empty()) {
+    p->field_r.resize(p->n);
+    for (int32_t v = 0; v < p->n; ++v) p->field_r[v] = p->field[p->order[v]];
+  }
   p->rowptr_r.assign(p->n + 1, 0);
   p->col_r.resize(p->rowptr[p->n]);
   p->wt_r.resize(p->rowptr[p->n]);
@@ -205,6 +212,8 @@ void free_device(isg_problem *p) {
     cudaFree(d.rowptr_o);
     cudaFree(d.col_o);
     cudaFree(d.wt_o);
+    cudaFree(d.field_r);
+    cudaFree(d.field_o);
     cudaSetDevice(prev);
   }
   p->dev.clear();
@@ -223,7 +232,8 @@ cudaError_t upload(T **dst, const T *src, size_t count) {
 
 // Device-resident copy of an instance on the current device: each group of
 // arrays is uploaded once, on the first call that needs it.
-isg_status problem_device(const isg_problem *cp, unsigned need, const DeviceProblem **out) {
+isg_status problem_device(const isg_problem *cp, unsigned need, const DeviceProblem **out,
+                          size_t *uploaded) {
   isg_problem *p = const_cast<isg_problem *>(cp);
   int device = 0;
   ISG_CUDA(cudaGetDevice(&device));
@@ -254,18 +264,23 @@ isg_status problem_device(const isg_problem *cp, unsigned need, const DeviceProb
     if (err == cudaSuccess) err = upload(&d->col, p->col_r.data(), p->col_r.size());
     if (err == cudaSuccess) err = upload(&d->wt, p->wt_r.data(), p->wt_r.size());
     if (err == cudaSuccess) err = upload(&d->orig, p->order.data(), p->order.size());
+    if (err == cudaSuccess && !p->field_r.empty())
+      err = upload(&d->field_r, p->field_r.data(), p->field_r.size());
     bytes += 4 * (p->class_start.size() + p->rowptr_r.size() + p->col_r.size() +
-                  p->wt_r.size() + p->order.size());
+                  p->wt_r.size() + p->order.size() + p->field_r.size());
     if (err == cudaSuccess) d->have |= kNeedCsr;
   }
   if (err == cudaSuccess && (need & kNeedEnergy) && !(d->have & kNeedEnergy)) {
     err = upload(&d->rowptr_o, p->rowptr.data(), p->rowptr.size());
     if (err == cudaSuccess) err = upload(&d->col_o, p->col.data(), p->col.size());
     if (err == cudaSuccess) err = upload(&d->wt_o, p->wt.data(), p->wt.size());
-    bytes += 8 * p->rowptr.size() + 4 * (p->col.size() + p->wt.size());
+    if (err == cudaSuccess && !p->field.empty())
+      err = upload(&d->field_o, p->field.data(), p->field.size());
+    bytes += 8 * p->rowptr.size() + 4 * (p->col.size() + p->wt.size() + p->field.size());
     if (err == cudaSuccess) d->have |= kNeedEnergy;
   }
   d->bytes_uploaded += bytes;
+  if (uploaded) *uploaded = bytes;
   if (err != cudaSuccess) return cuda_fail(err, "uploading the instance");
   *out = d;
   return ISG_OK;
@@ -485,7 +500,9 @@ int max_class_size(const isg_problem *p) {
 }
 
 // The multi-spin graph kernel needs +-1 weights and degrees <= 63.
-bool graph_msc_ok(const isg_problem *p) { return p->mode <= 1 && p->dmax <= 63; }
+bool graph_msc_ok(const isg_problem *p) {
+  return p->mode <= 1 && p->dmax <= 63 && p->field.empty();
+}
 
 // Shared memory of the graph kernel; staged = adjacency in shared memory.
 size_t gm_bytes(const isg_problem *p, int K, bool staged) {
@@ -547,6 +564,7 @@ CsrSolve make_csr_solve(const isg_problem *p, const DeviceProblem *dp, const isg
   s.col = dp->col;
   s.wt = dp->wt;
   s.orig = dp->orig;
+  s.field = dp->field_r;
   s.kmax = p->kmax;
   s.table = r->d_table;
   s.key0 = (uint32_t)(seed & 0xFFFFFFFFu);
@@ -722,7 +740,8 @@ isg_status anneal_impl(const isg_problem *p, int32_t R, const double *betas, int
   if (kernel == ISG_KERNEL_TORUS_MSC && !p->torus)
     return fail(ISG_EINVAL, "the multi-spin-coded torus kernel needs a torus instance");
   if (kernel == ISG_KERNEL_GRAPH_MSC && !graph_msc_ok(p))
-    return fail(ISG_EINVAL, "the multi-spin-coded graph kernel needs weights +-1 and degree <= 63");
+    return fail(ISG_EINVAL,
+                "the multi-spin-coded graph kernel needs weights +-1, degree <= 63 and no fields");
   const bool plain = kernel == ISG_KERNEL_PLAIN;
   const bool gm = kernel == ISG_KERNEL_GRAPH_MSC;
   const bool tmsc = p->torus && (kernel == ISG_KERNEL_TORUS_MSC || plain);
@@ -768,10 +787,12 @@ isg_status anneal_impl(const isg_problem *p, int32_t R, const double *betas, int
   }
 
   const DeviceProblem *dp = nullptr;
-  st = problem_device(p, tmsc ? kNeedTorus : kNeedCsr, &dp);
+  size_t uploaded = 0;
+  st = problem_device(p, tmsc ? kNeedTorus : kNeedCsr, &dp, &uploaded);
   if (st != ISG_OK) return st;
 
   isg_result *r = new_result(p, R, S, msc, has_target, stream);
+  r->h2d_bytes = (int64_t)uploaded;
   r->relabelled = !tmsc;
   r->kernel = kernel;
   std::vector<int32_t> levels;
@@ -779,6 +800,7 @@ isg_status anneal_impl(const isg_problem *p, int32_t R, const double *betas, int
   std::vector<uint32_t> table;
   build_table(betas, S, levels, table);
   r->table_words = table.size();
+  r->h2d_bytes += 4 * (int64_t)table.size();
 
   st = result_alloc(r, stream);
   if (st != ISG_OK) {
@@ -998,6 +1020,22 @@ isg_status isg_problem_create_edges(int32_t n, int64_t m, const int32_t *u, cons
   return ISG_OK;
 }
 
+isg_status isg_problem_create_fields(int32_t n, int64_t m, const int32_t *u, const int32_t *v,
+                                    const int32_t *w, const int32_t *h, isg_problem **out) {
+  if (!out) return fail(ISG_EINVAL, "out must not be NULL");
+  *out = nullptr;
+  isg_problem *p = new isg_problem();
+  isg_status st = csr_from_edges(p, n, m, u, v, w);
+  if (st == ISG_OK && h) p->field.assign(h, h + n);
+  if (st == ISG_OK) st = finish_problem(p);
+  if (st != ISG_OK) {
+    delete p;
+    return st;
+  }
+  *out = p;
+  return ISG_OK;
+}
+
 isg_status isg_problem_create_csr(int32_t n, const int64_t *rowptr, const int32_t *col,
                                   const int32_t *w, isg_problem **out) {
   if (!out) return fail(ISG_EINVAL, "out must not be NULL");
@@ -1127,7 +1165,7 @@ isg_status isg_energy(const isg_problem *p, const int8_t *spins, int32_t replica
   cudaError_t err = cudaMemcpyAsync(d_s, spins, sbytes, cudaMemcpyHostToDevice, stream);
   if (err == cudaSuccess)
     err = energy_csr(dp->rowptr_o, dp->col_o, dp->wt_o, p->n, d_s, replicas, d_scratch, blocks,
-                     d_e, stream);
+                     d_e, stream, dp->field_o);
   if (err == cudaSuccess)
     err = cudaMemcpyAsync(energies, d_e, 8 * (size_t)replicas, cudaMemcpyDeviceToHost, stream);
   if (err == cudaSuccess) err = cudaStreamSynchronize(stream);
@@ -1216,6 +1254,7 @@ isg_status isg_result_stats(const isg_result *r, isg_stats *stats) {
   stats->ctas = r->ctas;
   stats->cluster_ctas = r->cluster;
   stats->threads = r->threads;
+  stats->h2d_bytes = r->h2d_bytes;
   return ISG_OK;
 }
 

@@ -28,10 +28,12 @@ struct DeviceProblem {
   int32_t *rowptr = nullptr;
   int32_t *col = nullptr;
   int32_t *wt = nullptr;
+  int32_t *field_r = nullptr;      // local fields, relabelled order (nullptr: none)
   int32_t *orig = nullptr;         // relabelled -> original id
   int64_t *rowptr_o = nullptr;     // CSR in original ids (energy checks)
   int32_t *col_o = nullptr;
   int32_t *wt_o = nullptr;
+  int32_t *field_o = nullptr;      // local fields, original order (nullptr: none)
 };
 
 }  // namespace isg
@@ -40,17 +42,19 @@ struct isg_problem {
   bool torus = false;
   int32_t n = 0, L = 0, W = 0;
   int64_t m = 0, total_weight = 0;
-  int32_t kmax = 0;                        // max_i sum_j |w_ij|
+  int32_t kmax = 0;                        // max_i (sum_j |w_ij| + |h_i|)
   int32_t mode = 2;                        // weights: 0 all +1, 1 all +-1, 2 general (CsrSolve)
   int32_t dmax = 0;                        // largest degree
   std::vector<int8_t> jr, jd;              // torus couplings
   std::vector<int64_t> rowptr;             // CSR, original ids, rows sorted
   std::vector<int32_t> col, wt;
+  std::vector<int32_t> field;              // local fields h (empty: none)
   std::vector<int32_t> colour;
   int32_t n_colours = 0;
   std::vector<int32_t> order;              // relabelled -> original
   std::vector<int32_t> class_start;
   std::vector<int32_t> rowptr_r, col_r, wt_r;  // relabelled CSR
+  std::vector<int32_t> field_r;            // relabelled fields (empty: none)
   std::mutex mu;
   std::deque<isg::DeviceProblem> dev;      // one per device; element addresses stay valid
 };
@@ -75,6 +79,7 @@ struct isg_result {
           *d_stop = nullptr;
   int8_t *d_out = nullptr, *d_out_best = nullptr;  // [R][n] +-1, original vertex order
   int32_t launches = 0, sweep_launches = 0, ctas = 0, cluster = 0, threads = 0;
+  int64_t h2d_bytes = 0;                   // table + instance arrays uploaded for this solve
   // filled on first synchronisation
   std::mutex mu;
   bool synced = false;
@@ -88,7 +93,8 @@ namespace isg {
 
 isg_status fail(isg_status st, const char *fmt, ...);
 isg_status cuda_fail(cudaError_t err, const char *what);
-isg_status problem_device(const isg_problem *p, unsigned need, const DeviceProblem **out);
+isg_status problem_device(const isg_problem *p, unsigned need, const DeviceProblem **out,
+                          size_t *uploaded = nullptr);
 isg_status check_betas(const double *betas, int32_t sweeps);
 void build_table(const double *betas, int32_t sweeps, const std::vector<int32_t> &levels,
                  std::vector<uint32_t> &out);

@@ -286,6 +286,7 @@ void fill_csr_unit(CsrBatchItem &it, const Slot *sl, int32_t quad, int32_t t_beg
   s.col = sl->dp->col;
   s.wt = sl->dp->wt;
   s.orig = sl->dp->orig;
+  s.field = sl->dp->field_r;
   s.kmax = p->kmax;
   s.table = r->d_table;
   s.key0 = (uint32_t)(sl->rq.seed & 0xFFFFFFFFu);

@@ -293,6 +293,13 @@ def table1_stand_ins():
             ("G81-shape 200x100", torus(200, 100, 81))]
 
 
+def independent_set_10000(sweeps: int = 10000, replicas: int = 256) -> Solve:
+    """Maximum independent set on a random geometric graph (n = 10,000, mean
+    degree 6) in the local-field form, 256 replicas, geometric beta 0.1->5.0."""
+    g = independent_set_instance(geometric_graph(10000, 6.0, 1))
+    return Solve(g, replicas, geometric_betas(0.1, 5.0, sweeps), 1)
+
+
 def batch_sizes(count: int = 512, seed: int = 4):
     """Even side lengths L, W uniform over {16, 18, ..., 140} for ``count`` tori."""
     k = np.arange(count, dtype=np.uint64)

@@ -39,7 +39,7 @@ class isg_options(ctypes.Structure):
 class isg_stats(ctypes.Structure):
     _fields_ = [("sweep_kernel_ms", ctypes.c_float), ("launches", _i32),
                 ("sweep_launches", _i32), ("kernel", _i32), ("ctas", _i32),
-                ("cluster_ctas", _i32), ("threads", _i32)]
+                ("cluster_ctas", _i32), ("threads", _i32), ("h2d_bytes", _i64)]
 
 
 class isg_server_stats(ctypes.Structure):
@@ -56,6 +56,7 @@ def _sig(name, args, res=ctypes.c_int):
 
 _sig("isg_problem_create_edges", [_i32, _i64, _P, _P, _P, ctypes.POINTER(_P)])
 _sig("isg_problem_create_csr", [_i32, _P, _P, _P, ctypes.POINTER(_P)])
+_sig("isg_problem_create_fields", [_i32, _i64, _P, _P, _P, _P, ctypes.POINTER(_P)])
 _sig("isg_problem_create_torus", [_i32, _i32, _P, _P, ctypes.POINTER(_P)])
 _sig("isg_problem_info", [_P, _P, _P, _P, _P, _P])
 _sig("isg_problem_destroy", [_P], None)
@@ -160,6 +161,18 @@ def isg_problem_create_edges(n: int, u, v, w) -> Problem:
     return Problem(out.value)
 
 
+def isg_problem_create_fields(n: int, u, v, w, h) -> Problem:
+    u, v, w = _arr(u, np.int32), _arr(v, np.int32), _arr(w, np.int32)
+    hh = None if h is None else _arr(h, np.int32)
+    if hh is not None and hh.shape != (n,):
+        raise ValueError("fields need one entry per vertex")
+    out = _P()
+    _check(_lib.isg_problem_create_fields(n, int(u.shape[0]), _ptr(u), _ptr(v), _ptr(w),
+                                          _ptr(hh) if hh is not None else None,
+                                          ctypes.byref(out)))
+    return Problem(out.value)
+
+
 def isg_problem_create_csr(n: int, rowptr, col, w) -> Problem:
     rowptr, col, w = _arr(rowptr, np.int64), _arr(col, np.int32), _arr(w, np.int32)
     out = _P()
@@ -198,6 +211,9 @@ def problem_of(instance) -> Problem:
     if hasattr(instance, "L"):
         return isg_problem_create_torus(instance.L, instance.W, instance.j_right,
                                         instance.j_down)
+    if getattr(instance, "h", None) is not None:
+        return isg_problem_create_fields(instance.n, instance.u, instance.v, instance.w,
+                                         instance.h)
     return isg_problem_create_edges(instance.n, instance.u, instance.v, instance.w)
 
 

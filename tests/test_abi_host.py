@@ -124,3 +124,18 @@ def test_acceptance_table_rejects_bad_input(isg):
         isg.isg_acceptance_table(np.array([-0.1]), 2)
     with pytest.raises(isg.IsgError):
         isg.isg_acceptance_table(np.array([0.5]), -1)
+
+
+def test_fields_validation_and_info(isg):
+    g = I.random_graph(30, 40, 3)
+    h = np.arange(30, dtype=np.int32) - 15
+    p = isg.isg_problem_create_fields(30, g.u, g.v, g.w, h)
+    assert (p.n, p.m, p.total_weight) == (30, 40, 40)  # total_weight stays sum w
+    q = isg.isg_problem_create_fields(30, g.u, g.v, g.w, None)  # no fields = plain edges
+    assert (q.n, q.m) == (30, 40)
+    with pytest.raises(ValueError):
+        isg.isg_problem_create_fields(30, g.u, g.v, g.w, h[:10])
+    with pytest.raises(isg.IsgError):  # sum |w| + sum |h| >= 2^30
+        isg.isg_problem_create_fields(30, g.u, g.v, g.w, np.full(30, 1 << 26, np.int32))
+    with pytest.raises(isg.IsgError):  # bad edge still rejected
+        isg.isg_problem_create_fields(3, [0], [0], [1], [0, 0, 0])

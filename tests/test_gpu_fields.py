@@ -1,0 +1,120 @@
+"""Local fields on the GPU (int8 colour-class kernel) against the oracle,
+element by element: E = sum w s s + sum h s; independent-set instances,
+general weights with fields, +-1 weights with fields, targets, isg_energy,
+the served path, and the multi-spin kernels' refusal."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2311_09275_gb300 import inputs as I
+from test_gpu_parity import assert_same
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def isg():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    from paper_2311_09275_gb300 import build
+    build.build()
+    from paper_2311_09275_gb300 import isg as mod
+    return mod
+
+
+def mis(n=600, deg=6.0, seed=3):
+    return I.independent_set_instance(I.geometric_graph(n, deg, seed))
+
+
+def general_with_fields(seed=4):
+    g = I.random_graph(350, 900, seed)
+    w = np.array([(-2, -1, 1, 2, 3)[k % 5] for k in range(g.m)], np.int32)
+    h = np.array([(-4, 0, 1, 3, -1, 2)[i % 6] for i in range(g.n)], np.int32)
+    return I.Graph(g.n, g.u, g.v, w, h)
+
+
+def pm1_with_fields(seed=5):
+    g = I.random_graph(300, 700, seed)
+    w = np.where(I.draws(seed, 7, np.arange(g.m)) >> np.uint64(63), 1, -1).astype(np.int32)
+    h = np.array([(1, -1, 0, 2)[i % 4] for i in range(g.n)], np.int32)
+    return I.Graph(g.n, g.u, g.v, w, h)
+
+
+CASES = {"mis": mis, "general": general_with_fields, "pm1": pm1_with_fields}
+
+
+@pytest.mark.parametrize("name", list(CASES))
+@pytest.mark.parametrize("R,cluster,qpc", [(1, 1, 1), (13, 2, 1), (37, 4, 2), (64, 0, 0)])
+def test_fields_csr_bit_exact(isg, name, R, cluster, qpc):
+    g = CASES[name]()
+    betas = I.geometric_betas(0.1, 5.0, 120)
+    orc = oracle.anneal(oracle.csr_of(g), R, betas, 17, check_energy=True)
+    res = isg.isg_anneal(isg.problem_of(g), R, betas, 17, kernel=2, cluster_ctas=cluster,
+                         quads_per_cta=qpc)
+    assert_same(res, orc)
+
+
+def test_fields_auto_and_plain_kernels(isg):
+    g = mis(300, 5.0, 8)
+    betas = I.geometric_betas(0.1, 5.0, 60)
+    orc = oracle.anneal(oracle.csr_of(g), 24, betas, 2)
+    p = isg.problem_of(g)
+    auto = isg.isg_anneal(p, 24, betas, 2)
+    assert auto.stats()["kernel"] == 2          # fields -> int8 colour-class kernel
+    assert_same(auto, orc)
+    assert_same(isg.isg_anneal(p, 24, betas, 2, kernel=3), orc)
+    with pytest.raises(isg.IsgError):
+        isg.isg_anneal(p, 24, betas, 2, kernel=4)  # the multi-spin kernel has no fields
+
+
+@pytest.mark.parametrize("R", [8, 40])
+def test_fields_target_stop(isg, R):
+    g = general_with_fields(9)
+    betas = I.geometric_betas(0.1, 5.0, 200)
+    c = oracle.csr_of(g)
+    full = oracle.anneal(c, R, betas, 6)
+    target = full.best[0] + 4
+    orc = oracle.anneal(c, R, betas, 6, target=target)
+    res = isg.isg_anneal(isg.problem_of(g), R, betas, 6, target=target, kernel=2, cluster_ctas=2)
+    assert_same(res, orc)
+    assert orc.hit_sweep >= 0
+
+
+def test_fields_energy_matches_oracle(isg):
+    g = general_with_fields(10)
+    c = oracle.csr_of(g)
+    rng = np.random.default_rng(1)
+    s = np.where(rng.random((9, g.n)) < 0.5, 1, -1).astype(np.int8)
+    e = isg.isg_energy(isg.problem_of(g), s)
+    assert [int(x) for x in e] == [c.energy(row) for row in s]
+
+
+def test_fields_independent_set_valid_and_near_maximum(isg):
+    """Annealed independent-set instances give valid sets (no edge inside)
+    whose energy equals the oracle's for the same seed."""
+    gg = I.geometric_graph(2000, 6.0, 11)
+    g = I.independent_set_instance(gg)
+    betas = I.geometric_betas(0.1, 5.0, 400)
+    res = isg.isg_anneal(isg.problem_of(g), 64, betas, 3)
+    be, br, bs, per, hit = res.best()
+    chosen = bs > 0
+    assert not np.any(chosen[gg.u] & chosen[gg.v])
+    orc = oracle.anneal(oracle.csr_of(g), [br], betas, 3)
+    assert int(orc.e_best[0]) == be and np.array_equal(orc.s_best[0], bs)
+    # the set size follows from the energy: E = -2|I| - m + n for a valid set
+    assert be == -2 * int(chosen.sum()) - gg.m + gg.n
+
+
+def test_fields_served_equals_solo(isg):
+    g = general_with_fields(12)
+    p = isg.problem_of(g)
+    betas = I.geometric_betas(0.1, 5.0, 150)
+    srv = isg.Server(1 << 30, 4, 40)
+    rid = srv.submit(p, 20, betas, 5)
+    got = srv.poll(30.0)
+    srv.close()
+    assert got[0] == rid
+    solo = isg.isg_anneal(p, 20, betas, 5)
+    for x, y in zip(got[1].final(), solo.final()):
+        assert np.array_equal(x, y)
+    assert np.array_equal(got[1].best_all(), solo.best_all())
