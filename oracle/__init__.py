@@ -73,6 +73,9 @@ def _load():
                                    u64, ctypes.c_int, ctypes.c_int, P, P, P, P, P, P]
         lib.orc_anneal.restype = ctypes.c_int
         lib.orc_initial_spins.argtypes = [i32, i32, P, u64, P]
+        lib.orc_parallel_tempering.argtypes = [i32, P, P, P, P, P, i32, i32, P, i32, i32, u64,
+                                               ctypes.c_int, P, P, P, P, P, P]
+        lib.orc_parallel_tempering.restype = ctypes.c_int
         lib.orc_enumerate.argtypes = [i32, P, P, P, P, P, P]
         lib.orc_enumerate.restype = i64
         _lib = lib
@@ -242,3 +245,46 @@ def anneal(csr: Csr, replicas, betas, seed: int, colour=None, target=None,
     if rc != 0:
         raise ValueError("bad arguments to the oracle")
     return AnnealResult(reps, s_final, e_final, s_best, e_best, int(hit.value), int(done.value))
+
+
+class TemperingResult:
+    """Per replica r = 32 k + c (slot k, chain c): final and best states and
+    energies; exchange counts per slot pair."""
+
+    def __init__(self, s_final, e_final, s_best, e_best, accepted, attempted):
+        self.s_final, self.e_final = s_final, e_final
+        self.s_best, self.e_best = s_best, e_best
+        self.accepted, self.attempted = accepted, attempted
+
+    @property
+    def best(self):
+        k = int(np.argmin(self.e_best))  # argmin takes the lowest index among ties
+        return int(self.e_best[k]), k
+
+
+def parallel_tempering(csr: Csr, betas, rounds: int, per_round: int, seed: int, colour=None,
+                       nthreads: int = 0) -> TemperingResult:
+    """Parallel tempering over len(betas) slots x 32 chains (see isg_oracle.h)."""
+    if colour is None:
+        colour, nc = csr.greedy_colouring()
+    else:
+        colour = _arr(colour, np.int32)
+        nc = int(colour.max()) + 1
+    b = _arr(betas, np.float64)
+    K = int(b.shape[0])
+    R = 32 * K
+    s_final = np.zeros((R, csr.n), dtype=np.int8)
+    s_best = np.zeros((R, csr.n), dtype=np.int8)
+    e_final = np.zeros(R, dtype=np.int32)
+    e_best = np.zeros(R, dtype=np.int32)
+    acc = np.zeros(max(K - 1, 1), dtype=np.int64)
+    att = np.zeros(max(K - 1, 1), dtype=np.int64)
+    if nthreads <= 0:
+        nthreads = min(os.cpu_count() or 1, 32)
+    rc = _load().orc_parallel_tempering(
+        csr.n, _p(csr.rowptr), _p(csr.col), _p(csr.wt), csr._fp(), _p(colour), nc, K, _p(b),
+        int(rounds), int(per_round), int(seed), int(nthreads), _p(s_final), _p(e_final),
+        _p(s_best), _p(e_best), _p(acc), _p(att))
+    if rc != 0:
+        raise ValueError("bad arguments to the oracle")
+    return TemperingResult(s_final, e_final, s_best, e_best, acc[: K - 1], att[: K - 1])

@@ -52,6 +52,7 @@ void orc_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t ou
  * spins.  i is the vertex id of the instance as given. */
 #define ORC_TAG_SWEEP 0u
 #define ORC_TAG_INIT 1u
+#define ORC_TAG_EXCHANGE 2u
 
 static uint32_t orc_draw(uint64_t seed, uint32_t i, uint32_t t, uint32_t r, uint32_t tag) {
     uint32_t ctr[4] = {i, t, r >> 2, tag};
@@ -360,6 +361,175 @@ int orc_anneal(int32_t n, const int64_t *rowptr, const int32_t *col, const int32
     free(class_start);
     free(table);
     return status;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Parallel tempering (Sec. II.C: replicas at different temperatures that
+ * exchange configurations across temperatures).  32 independent ladders
+ * ("chains" c = 0..31); replica r = 32 k + c sits at temperature slot k with
+ * inverse temperature betas[k].  Round q: every replica runs `per_round`
+ * sweeps (global sweep index t = q * per_round + j, the annealing sweep at
+ * beta_k); then, for every slot pair (k, k+1) with k = q mod 2, k+1 < K, and
+ * every chain, the two configurations (and their energies) are exchanged
+ * with probability min(1, exp(a)), a = (beta_k - beta_{k+1}) (E_k - E_{k+1}):
+ * always when a >= 0, else when the exchange uniform u < floor(2^32 exp(a)),
+ * u = word (c mod 4) of Philox(seed, (k, q, c / 4, 2)).  Best states stay
+ * with the slot and are checked at sweep ends. */
+
+typedef struct {
+    int32_t n, K, rounds, per_round, n_colours;
+    const int64_t *rowptr;
+    const int32_t *col, *wt, *field, *order;
+    const int64_t *class_start;
+    const double *betas;
+    const uint32_t *table; /* [K][kmax + 1]: slot k's Metropolis thresholds */
+    int32_t kmax;
+    uint64_t seed;
+    int32_t c_begin, c_end;
+    int8_t *s_final, *s_best;
+    int32_t *e_final, *e_best;
+    int64_t *accepted, *attempted; /* [32][K - 1] per chain, summed by the caller */
+} orc_pt_job;
+
+static void orc_pt_chain(orc_pt_job *J, int32_t c) {
+    const int32_t n = J->n, K = J->K;
+    int64_t *e = (int64_t *)malloc(sizeof(int64_t) * (size_t)K);
+    int64_t *eb = (int64_t *)malloc(sizeof(int64_t) * (size_t)K);
+    int8_t *tmp = (int8_t *)malloc((size_t)n);
+    for (int32_t k = 0; k < K; ++k) {
+        const uint32_t r = (uint32_t)(32 * k + c);
+        int8_t *s = J->s_final + (int64_t)r * n;
+        for (int32_t i = 0; i < n; ++i)
+            s[i] = (orc_draw(J->seed, (uint32_t)i, 0u, r, ORC_TAG_INIT) >> 31) ? 1 : -1;
+        e[k] = orc_energy(n, J->rowptr, J->col, J->wt, J->field, s);
+        eb[k] = e[k];
+        memcpy(J->s_best + (int64_t)r * n, s, (size_t)n);
+    }
+    for (int32_t q = 0; q < J->rounds; ++q) {
+        for (int32_t k = 0; k < K; ++k) {
+            const uint32_t r = (uint32_t)(32 * k + c);
+            int8_t *s = J->s_final + (int64_t)r * n;
+            const uint32_t *row = J->table + (int64_t)k * (J->kmax + 1);
+            for (int32_t j = 0; j < J->per_round; ++j) {
+                const uint32_t t = (uint32_t)(q * J->per_round + j);
+                for (int32_t cc = 0; cc < J->n_colours; ++cc)
+                    for (int64_t z = J->class_start[cc]; z < J->class_start[cc + 1]; ++z) {
+                        const int32_t i = J->order[z];
+                        int64_t h = J->field ? J->field[i] : 0;
+                        for (int64_t p = J->rowptr[i]; p < J->rowptr[i + 1]; ++p)
+                            h += (int64_t)J->wt[p] * s[J->col[p]];
+                        const int64_t kk = -(int64_t)s[i] * h;
+                        if (kk <= 0 || orc_draw(J->seed, (uint32_t)i, t, r, ORC_TAG_SWEEP) < row[kk]) {
+                            s[i] = (int8_t)(-s[i]);
+                            e[k] += 2 * kk;
+                        }
+                    }
+                if (e[k] < eb[k]) {
+                    eb[k] = e[k];
+                    memcpy(J->s_best + (int64_t)r * n, s, (size_t)n);
+                }
+            }
+        }
+        for (int32_t k = q % 2; k + 1 < K; k += 2) {
+            const double a = (J->betas[k] - J->betas[k + 1]) * (double)(e[k] - e[k + 1]);
+            int swap = a >= 0.0;
+            if (!swap) {
+                const double x = floor(ldexp(exp(a), 32));
+                const uint32_t thr = x >= 4294967295.0 ? 4294967295u : (uint32_t)x;
+                swap = orc_draw(J->seed, (uint32_t)k, (uint32_t)q, (uint32_t)c, ORC_TAG_EXCHANGE) < thr;
+            }
+            J->attempted[(int64_t)c * (K - 1) + k]++;
+            if (swap) {
+                J->accepted[(int64_t)c * (K - 1) + k]++;
+                int8_t *a_s = J->s_final + (int64_t)(32 * k + c) * n;
+                int8_t *b_s = J->s_final + (int64_t)(32 * (k + 1) + c) * n;
+                memcpy(tmp, a_s, (size_t)n);
+                memcpy(a_s, b_s, (size_t)n);
+                memcpy(b_s, tmp, (size_t)n);
+                const int64_t te = e[k];
+                e[k] = e[k + 1];
+                e[k + 1] = te;
+            }
+        }
+    }
+    for (int32_t k = 0; k < K; ++k) {
+        J->e_final[32 * k + c] = (int32_t)e[k];
+        J->e_best[32 * k + c] = (int32_t)eb[k];
+    }
+    free(e);
+    free(eb);
+    free(tmp);
+}
+
+static void *orc_pt_worker(void *arg) {
+    orc_pt_job *J = (orc_pt_job *)arg;
+    for (int32_t c = J->c_begin; c < J->c_end; ++c) orc_pt_chain(J, c);
+    return NULL;
+}
+
+int orc_parallel_tempering(int32_t n, const int64_t *rowptr, const int32_t *col, const int32_t *wt,
+                           const int32_t *field, const int32_t *colour, int32_t n_colours,
+                           int32_t K, const double *betas, int32_t rounds, int32_t per_round,
+                           uint64_t seed, int nthreads, int8_t *s_final, int32_t *e_final,
+                           int8_t *s_best, int32_t *e_best, int64_t *accepted,
+                           int64_t *attempted) {
+    if (n < 1 || K < 1 || rounds < 1 || per_round < 1 || n_colours < 1) return -1;
+    for (int32_t i = 0; i < n; ++i)
+        if (colour[i] < 0 || colour[i] >= n_colours) return -1;
+    int64_t kmax = 0;
+    for (int32_t i = 0; i < n; ++i) {
+        int64_t a = field ? llabs((long long)field[i]) : 0;
+        for (int64_t p = rowptr[i]; p < rowptr[i + 1]; ++p) a += llabs((long long)wt[p]);
+        if (a > kmax) kmax = a;
+    }
+    uint32_t *table = (uint32_t *)malloc(sizeof(uint32_t) * (size_t)K * (size_t)(kmax + 1));
+    orc_accept_table(K, betas, (int32_t)kmax, table);
+    int64_t *class_start = (int64_t *)calloc((size_t)n_colours + 1, sizeof(int64_t));
+    for (int32_t i = 0; i < n; ++i) class_start[colour[i] + 1]++;
+    for (int32_t c = 0; c < n_colours; ++c) class_start[c + 1] += class_start[c];
+    int32_t *order = (int32_t *)malloc(sizeof(int32_t) * (size_t)n);
+    int64_t *fill = (int64_t *)malloc(sizeof(int64_t) * (size_t)n_colours);
+    for (int32_t c = 0; c < n_colours; ++c) fill[c] = class_start[c];
+    for (int32_t i = 0; i < n; ++i) order[fill[colour[i]]++] = i;
+    free(fill);
+    const int32_t pairs = K > 1 ? K - 1 : 1;
+    int64_t *acc = (int64_t *)calloc((size_t)32 * pairs, sizeof(int64_t));
+    int64_t *att = (int64_t *)calloc((size_t)32 * pairs, sizeof(int64_t));
+
+    if (nthreads < 1) nthreads = 1;
+    if (nthreads > 32) nthreads = 32;
+    orc_pt_job *jobs = (orc_pt_job *)malloc(sizeof(orc_pt_job) * (size_t)nthreads);
+    pthread_t *th = (pthread_t *)malloc(sizeof(pthread_t) * (size_t)nthreads);
+    for (int w = 0; w < nthreads; ++w) {
+        orc_pt_job *J = &jobs[w];
+        memset(J, 0, sizeof(*J));
+        J->n = n; J->K = K; J->rounds = rounds; J->per_round = per_round;
+        J->n_colours = n_colours; J->rowptr = rowptr; J->col = col; J->wt = wt;
+        J->field = field; J->order = order; J->class_start = class_start; J->betas = betas;
+        J->table = table; J->kmax = (int32_t)kmax; J->seed = seed;
+        J->c_begin = 32 * w / nthreads; J->c_end = 32 * (w + 1) / nthreads;
+        J->s_final = s_final; J->s_best = s_best; J->e_final = e_final; J->e_best = e_best;
+        J->accepted = acc; J->attempted = att;
+    }
+    for (int w = 1; w < nthreads; ++w) pthread_create(&th[w], NULL, orc_pt_worker, &jobs[w]);
+    orc_pt_worker(&jobs[0]);
+    for (int w = 1; w < nthreads; ++w) pthread_join(th[w], NULL);
+    for (int32_t k = 0; k + 1 < K; ++k) {
+        accepted[k] = 0;
+        attempted[k] = 0;
+        for (int32_t c = 0; c < 32; ++c) {
+            accepted[k] += acc[(int64_t)c * (K - 1) + k];
+            attempted[k] += att[(int64_t)c * (K - 1) + k];
+        }
+    }
+    free(jobs);
+    free(th);
+    free(acc);
+    free(att);
+    free(order);
+    free(class_start);
+    free(table);
+    return 0;
 }
 
 /* ------------------------------------------------------------------------ */

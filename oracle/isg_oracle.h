@@ -78,6 +78,23 @@ int orc_anneal(int32_t n, const int64_t *rowptr, const int32_t *col, const int32
                int8_t *s_final, int32_t *e_final, int8_t *s_best, int32_t *e_best,
                int32_t *hit_sweep, int32_t *sweeps_done);
 
+/* Parallel tempering over K temperature slots x 32 independent chains
+ * (replica r = 32 k + c at betas[k]): `rounds` rounds of `per_round` sweeps
+ * each, every round followed by configuration exchanges between slot pairs
+ * (k, k+1), k = round mod 2, accepted with probability
+ * min(1, exp((beta_k - beta_{k+1}) (E_k - E_{k+1}))) by the exchange uniform
+ * (tag 2, counter (k, round, c / 4, 2), word c mod 4) against
+ * floor(2^32 exp(.)).  Outputs per replica ([32K][n] spins): s_final, e_final,
+ * s_best, e_best (best states stay with the slot, checked at sweep ends);
+ * accepted[k] / attempted[k] exchange counts of pair (k, k+1), k < K-1.
+ * Returns 0, or -1 on bad arguments. */
+int orc_parallel_tempering(int32_t n, const int64_t *rowptr, const int32_t *col, const int32_t *wt,
+                           const int32_t *field, const int32_t *colour, int32_t n_colours,
+                           int32_t K, const double *betas, int32_t rounds, int32_t per_round,
+                           uint64_t seed, int nthreads, int8_t *s_final, int32_t *e_final,
+                           int8_t *s_best, int32_t *e_best, int64_t *accepted,
+                           int64_t *attempted);
+
 /* Initial spins of the listed replicas (the state before sweep 0). */
 void orc_initial_spins(int32_t n, int32_t n_rep, const int32_t *rep_ids, uint64_t seed, int8_t *s);
 
