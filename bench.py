@@ -567,6 +567,53 @@ def run_served(args):
     print(json.dumps(line))
 
 
+# ---------------------------------------------------------------- parallel tempering
+def run_pt(args):
+    """Parallel tempering on the 80x100 torus: 32 temperature slots (geometric
+    beta 0.2 -> 3.0) x 32 chains = 1,024 replicas, 1,000 rounds of 10 sweeps
+    with an exchange step after each round (10,000 sweeps, the annealing
+    workload's attempt count).  Device time covers sweeps and exchanges."""
+    import torch
+    from paper_2311_09275_gb300 import isg
+    torch.cuda.set_device(0)
+    stream = torch.cuda.current_stream()
+    K, per_round = 32, 10
+    rounds = (args.sweeps or 10000) // per_round
+    betas = I.geometric_betas(0.2, 3.0, K)
+    t = I.torus(80, 100, 1)
+    p = isg.problem_of(t)
+    attempts = 32.0 * K * t.L * t.W * rounds * per_round
+    for _ in range(args.warmup):
+        isg.isg_parallel_tempering(p, betas, rounds, per_round, 1, stream=stream).close()
+    torch.cuda.synchronize()
+    ms, res = [], None
+    with ClockSampler(0) as clocks:
+        for k in range(args.steps):
+            r = isg.isg_parallel_tempering(p, betas, rounds, per_round, 1 + k, stream=stream,
+                                           time_kernels=True)
+            ms.append(r.stats()["sweep_kernel_ms"])
+            if res is not None:
+                res.close()
+            res = r
+    acc, att = isg.isg_result_exchanges(res, K - 1)
+    st = res.stats()
+    best = res.best(spins=False)
+    res.close()
+    dev_s = sum(ms) / 1e3
+    line = {"metric": METRIC, "value": attempts * args.steps / dev_s, "unit": UNIT, "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dev_s / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
+            "data": "synthetic",
+            "config": {"workload": f"tempering_torus_80x100_K{K}x32_rounds{rounds}x{per_round}"
+                                   f"_geometric_0.2_3.0", "attempts_per_step": attempts,
+                       "launch": {k: st[k] for k in ("kernel", "ctas", "cluster_ctas", "threads")},
+                       "l2": "state of each word in shared memory during a round"},
+            "exchange_acceptance": [round(float(a) / float(b), 4) for a, b in zip(acc, att)],
+            "best_energy": int(best[0]), "gpu_launches": st["launches"],
+            "clocks": clocks.summary()}
+    print(json.dumps(line))
+
+
 # ---------------------------------------------------------------- paper-style TTT
 QUALITY_LEVELS = (0.99, 0.995, 0.997, 0.999, 1.0)
 HEADLINE_QUALITY = 0.995
@@ -645,7 +692,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--config", default="torus",
-                    choices=["torus", "random", "mis", "batch", "served", "ttt"])
+                    choices=["torus", "random", "mis", "batch", "served", "ttt", "pt"])
     ap.add_argument("--requests", type=int, default=2000, help="served: number of requests")
     ap.add_argument("--slots", type=int, default=512, help="served: maximum resident requests")
     ap.add_argument("--chunk", type=int, default=250, help="served: sweeps per chunk")
@@ -668,6 +715,8 @@ def main():
         run_served(args)
     elif args.config == "ttt":
         run_ttt(args)
+    elif args.config == "pt":
+        run_pt(args)
     else:
         run_gpu(args)
 

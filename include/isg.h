@@ -171,6 +171,34 @@ isg_status isg_anneal_batch(const isg_problem *const *probs, int32_t count, int3
                             const double *betas, int32_t sweeps, const uint64_t *seeds,
                             const int64_t *targets, void *cuda_stream, isg_result **outs);
 
+/* Parallel tempering (Sec. II.C: replicas at different temperatures that
+ * exchange configurations) on a torus instance.  temperatures = K slots with
+ * inverse temperatures betas[K] (finite, >= 0, any order), 32 independent
+ * chains per slot: R = 32 K replicas, replica r = 32 k + c is chain c at slot
+ * k.  Each of `rounds` rounds runs sweeps_per_round sweeps of every replica at
+ * its slot's beta (sweep t = round * sweeps_per_round + j draws the annealing
+ * uniforms of replica r), then exchanges the configurations (and energies) of
+ * chain c between slots k and k+1, for k = round mod 2, 2 + round mod 2, ...,
+ * with probability min(1, exp((beta_k - beta_{k+1}) (E_k - E_{k+1}))): always
+ * when the exponent is >= 0, else when the uniform word (c mod 4) of
+ * Philox(seed, (k, round, c / 4, 2)) is below floor(2^32 exp(exponent)), FP64
+ * on the host.  Best states and energies stay with the slot (checked at sweep
+ * ends).  No target.  The result is read like isg_anneal's (R = 32 K, S =
+ * rounds * sweeps_per_round); exchange counts by isg_result_exchanges.  opts
+ * may be NULL (kernel AUTO or TORUS_MSC; cluster/threads as isg_anneal).
+ * EINVAL: not a torus, K outside [1, 4096], rounds or sweeps_per_round < 1,
+ * a bad beta. */
+isg_status isg_parallel_tempering(const isg_problem *p, int32_t temperatures,
+                                  const double *betas, int32_t rounds, int32_t sweeps_per_round,
+                                  uint64_t seed, const isg_options *opts, void *cuda_stream,
+                                  isg_result **out);
+
+/* Exchange counts of a parallel-tempering result: accepted[k] and attempted[k]
+ * for slot pairs (k, k+1), k < pairs = K - 1 (EINVAL for another pairs value,
+ * and for results of other calls unless pairs = 0).  Waits for the solve. */
+isg_status isg_result_exchanges(const isg_result *r, int64_t *accepted, int64_t *attempted,
+                                int32_t pairs);
+
 /* Energies E(s) of R host configurations spins[R][n] (+-1) into energies[R],
  * computed on the device (a check of the tracked energies); local fields
  * included. */

@@ -140,6 +140,8 @@ extern "C" isg_status isg_anneal_batch(const isg_problem *const *probs, int32_t 
     s.W = p->W;
     s.cbits = dp->cbits;
     s.table = d_table;
+    s.table_ws = 0;
+    s.table_ts = 2;
     s.key0 = (uint32_t)(seeds[k] & 0xFFFFFFFFu);
     s.key1 = (uint32_t)(seeds[k] >> 32);
     s.rk = round_keys(s.key0, s.key1);

@@ -29,7 +29,9 @@ __host__ __device__ inline RoundKeys round_keys(uint32_t key0, uint32_t key1) {
 struct TorusSolve {
   int32_t L, W;
   const uint8_t *cbits;      // [L*W] bit0: j_right == -1, bit1: j_down == -1
-  const uint32_t *table;     // [sweeps][2]: thresholds for energy changes 4 and 8
+  const uint32_t *table;     // thresholds for energy changes 4 and 8 of word w, sweep t at
+                             // table[w * table_ws + t * table_ts + {0, 1}]
+  int32_t table_ws, table_ts;  // annealing: 0, 2 (one schedule); tempering: 2, 0 (one beta per word)
   uint32_t key0, key1;       // Philox key (seed)
   RoundKeys rk;              // round_keys(key0, key1)
   int32_t words;             // replica words of this solve
@@ -206,6 +208,16 @@ cudaError_t unpack_quads(const uint32_t *quads, int32_t n, int32_t R, const int3
                          int8_t *out, cudaStream_t stream);
 // Energies of R configurations spins[R][n] (int8) over a CSR (original ids):
 // per-block partial sums in scratch[R * blocks], then one sum per replica.
+// Parallel tempering: exchange configurations between replica words k and
+// k+1 (k = parity, parity + 2, ...; k + 1 < K), lane by lane, after round
+// `round`.  sgn[k] = sign of beta_k - beta_{k+1}; xtable[k][d] = threshold of
+// an exchange whose energy difference |E_k - E_{k+1}| = d < xlen raises the
+// exponent's magnitude (0 beyond xlen); accepted[k] counts exchanges.
+cudaError_t pt_exchange(uint32_t *spins, int32_t *e_cur, int32_t n, int32_t K, int32_t parity,
+                        int32_t round, uint32_t key0, uint32_t key1, const int8_t *sgn,
+                        const uint32_t *xtable, int32_t xlen, unsigned long long *accepted,
+                        cudaStream_t stream);
+
 cudaError_t energy_csr(const int64_t *rowptr, const int32_t *col, const int32_t *wt, int32_t n,
                        const int8_t *spins, int32_t R, int64_t *scratch, int32_t blocks,
                        int64_t *energies, cudaStream_t stream,

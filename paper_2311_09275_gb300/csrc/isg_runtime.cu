@@ -391,6 +391,7 @@ void result_free(isg_result *r) {
   cudaSetDevice(r->device);
   if (r->done) cudaEventSynchronize(r->done);
   if (r->base) cudaFreeAsync(r->base, r->stream);
+  if (r->pt_mem) cudaFreeAsync(r->pt_mem, r->stream);
   if (r->done) cudaEventDestroy(r->done);
   if (r->t0) cudaEventDestroy(r->t0);
   if (r->t1) cudaEventDestroy(r->t1);
@@ -538,6 +539,8 @@ TorusSolve make_torus_solve(const isg_problem *p, const DeviceProblem *dp, const
   s.W = p->W;
   s.cbits = dp->cbits;
   s.table = r->d_table;
+  s.table_ws = 0;
+  s.table_ts = 2;
   s.key0 = (uint32_t)(seed & 0xFFFFFFFFu);
   s.key1 = (uint32_t)(seed >> 32);
   s.rk = round_keys(s.key0, s.key1);
@@ -855,6 +858,157 @@ isg_status anneal_impl(const isg_problem *p, int32_t R, const double *betas, int
     cudaStreamSynchronize(stream);
     result_free(r);
     return cuda_fail(err, "launching the sweeps");
+  }
+  r->launches = launches;
+  r->sweep_launches = sweep_launches;
+  *out = r;
+  return ISG_OK;
+}
+
+// ------------------------------------------------------------------ tempering
+
+// Parallel tempering on a torus: word k = temperature slot k (32 chains), one
+// torus-kernel launch of `per_round` sweeps per round at each word's own beta,
+// then the exchange kernel over the pairs of the round's parity.
+isg_status tempering_impl(const isg_problem *p, int32_t K, const double *betas, int32_t rounds,
+                          int32_t per_round, uint64_t seed, const isg_options *opts,
+                          cudaStream_t stream, isg_result **out) {
+  if (!out) return fail(ISG_EINVAL, "out must not be NULL");
+  *out = nullptr;
+  if (!p) return fail(ISG_EINVAL, "problem must not be NULL");
+  if (!p->torus) return fail(ISG_EINVAL, "parallel tempering runs on torus instances");
+  if (K < 1 || K > 4096) return fail(ISG_EINVAL, "temperatures must be in [1, 4096]");
+  if (rounds < 1 || per_round < 1 || (int64_t)rounds * per_round > INT32_MAX)
+    return fail(ISG_EINVAL, "rounds and sweeps_per_round must be >= 1 (product < 2^31)");
+  isg_status st = check_betas(betas, K);
+  if (st != ISG_OK) return st;
+  isg_options o = {};
+  if (opts) o = *opts;
+  if (o.kernel != ISG_KERNEL_AUTO && o.kernel != ISG_KERNEL_TORUS_MSC)
+    return fail(ISG_EINVAL, "parallel tempering uses the multi-spin torus kernel");
+  if (o.cluster_ctas < 0 || o.cluster_ctas > 16)
+    return fail(ISG_EINVAL, "cluster_ctas must be in [0, 16]");
+  if (o.threads != 0 && (o.threads < 32 || o.threads > 1024 || o.threads % 32))
+    return fail(ISG_EINVAL, "threads must be a multiple of 32 in [32, 1024]");
+  const int32_t R = 32 * K, S = rounds * per_round;
+  int cluster = o.cluster_ctas, threads = o.threads;
+  int t_kernel = 0, t_cluster = 0, t_threads = 0, t_qpc = 0;
+  if (cluster == 0 && threads == 0 && shape_lookup(p, R, t_kernel, t_cluster, t_threads, t_qpc) &&
+      t_kernel == ISG_KERNEL_TORUS_MSC) {
+    cluster = t_cluster;
+    threads = t_threads;
+  }
+  torus_shape(p->L, p->W, K, cluster, threads);
+  if (cluster > p->L) cluster = p->L;
+  if (torus_smem_bytes(p->L, p->W, cluster) > 227 * 1024)
+    return fail(ISG_EINVAL, "torus %dx%d needs more shared memory than a CTA has", p->L, p->W);
+
+  const DeviceProblem *dp = nullptr;
+  size_t uploaded = 0;
+  st = problem_device(p, kNeedTorus, &dp, &uploaded);
+  if (st != ISG_OK) return st;
+  isg_result *r = new_result(p, R, S, true, false, stream);
+  r->h2d_bytes = (int64_t)uploaded;
+  r->relabelled = false;
+  r->kernel = ISG_KERNEL_TORUS_MSC;
+  std::vector<uint32_t> table;  // [K][2]: slot k's thresholds for energy changes 4 and 8
+  build_table(betas, K, {2, 4}, table);
+  r->table_words = table.size();
+
+  // exchange thresholds: pair k, |E_k - E_{k+1}| = d in the direction that
+  // makes a = (beta_k - beta_{k+1}) (E_k - E_{k+1}) negative; the table ends
+  // where every pair's threshold has reached 0 (|E| <= 2n on a torus)
+  const int32_t pairs = K - 1;
+  const int64_t dmax = 4 * (int64_t)p->n;
+  std::vector<int8_t> sgn(std::max(pairs, 1), 0);
+  int64_t xlen = 1;
+  for (int32_t k = 0; k < pairs; ++k) {
+    const double db = betas[k] - betas[k + 1];
+    sgn[k] = db > 0 ? 1 : (db < 0 ? -1 : 0);
+    for (int64_t d = xlen; d <= dmax && sgn[k] != 0; ++d) {
+      const double a = db * (double)(-(int64_t)sgn[k] * d);
+      if (std::floor(std::ldexp(std::exp(a), 32)) < 1.0) break;
+      xlen = d + 1;
+    }
+  }
+  std::vector<uint32_t> xtable((size_t)std::max(pairs, 1) * xlen, 0u);
+  for (int32_t k = 0; k < pairs; ++k)
+    for (int64_t d = 0; d < xlen && sgn[k] != 0; ++d) {
+      const double a = (betas[k] - betas[k + 1]) * (double)(-(int64_t)sgn[k] * d);
+      const double x = std::floor(std::ldexp(std::exp(a), 32));
+      xtable[(size_t)k * xlen + d] = x >= 4294967295.0 ? 4294967295u : (uint32_t)x;
+    }
+  r->h2d_bytes += 4 * (int64_t)(table.size() + xtable.size()) + (int64_t)sgn.size();
+
+  st = result_alloc(r, stream);
+  if (st != ISG_OK) {
+    delete r;
+    return st;
+  }
+  const size_t o_acc = 0, o_x = 8 * (size_t)std::max(pairs, 1);
+  const size_t o_sgn = o_x + 4 * xtable.size();
+  cudaError_t err = cudaMallocAsync(&r->pt_mem, o_sgn + sgn.size(), stream);
+  if (err == cudaSuccess) err = cudaEventCreateWithFlags(&r->done, cudaEventDisableTiming);
+  if (err == cudaSuccess && o.time_kernels) {
+    r->timed = true;
+    err = cudaEventCreate(&r->t0);
+    if (err == cudaSuccess) err = cudaEventCreate(&r->t1);
+  }
+  char *pm = (char *)r->pt_mem;
+  r->d_accepted = (unsigned long long *)(pm + o_acc);
+  r->pt_pairs = pairs;
+  r->pt_attempted.assign(std::max(pairs, 0), 0);
+  for (int32_t q = 0; q < rounds; ++q)
+    for (int32_t k = q % 2; k + 1 < K; k += 2) r->pt_attempted[k] += 32;
+  if (err == cudaSuccess) err = cudaMemsetAsync(pm + o_acc, 0, o_x, stream);
+  if (err == cudaSuccess)
+    err = cudaMemcpyAsync(pm + o_x, xtable.data(), 4 * xtable.size(), cudaMemcpyHostToDevice,
+                          stream);
+  if (err == cudaSuccess)
+    err = cudaMemcpyAsync(pm + o_sgn, sgn.data(), sgn.size(), cudaMemcpyHostToDevice, stream);
+  if (err == cudaSuccess)
+    err = cudaMemcpyAsync(r->d_table, table.data(), 4 * table.size(), cudaMemcpyHostToDevice,
+                          stream);
+  if (err == cudaSuccess) err = cudaMemsetAsync(r->d_hit, 0xFF, 4 * (size_t)r->units, stream);
+  if (err != cudaSuccess) {
+    cudaStreamSynchronize(stream);
+    result_free(r);
+    return cuda_fail(err, "preparing parallel tempering");
+  }
+  r->ctas = K * cluster;
+  r->cluster = cluster;
+  r->threads = threads;
+
+  TorusSolve s = make_torus_solve(p, dp, r, seed, false, 0);
+  s.table_ws = 2;  // one row of thresholds per word, the same every sweep
+  s.table_ts = 0;
+  int launches = 0;
+  if (r->timed) err = cudaEventRecord(r->t0, stream);
+  for (int32_t q = 0; q < rounds && err == cudaSuccess; ++q) {
+    TorusLaunch l = {};
+    l.t_begin = q * per_round;
+    l.t_end = (q + 1) * per_round;
+    l.resume = q > 0;
+    l.cluster = cluster;
+    l.threads = threads;
+    err = torus_launch(s, l, stream);
+    if (err == cudaSuccess)
+      err = pt_exchange(r->d_spins, r->d_e_cur, p->n, K, q % 2, q, s.key0, s.key1,
+                        (const int8_t *)(pm + o_sgn), (const uint32_t *)(pm + o_x), (int32_t)xlen,
+                        r->d_accepted, stream);
+    launches += 2;
+  }
+  const int sweep_launches = rounds;
+  if (r->timed && err == cudaSuccess) err = cudaEventRecord(r->t1, stream);
+  if (err == cudaSuccess) err = reduce_hits(r->d_hit, r->units, r->d_stop, stream);
+  if (err == cudaSuccess) err = unpack_msc(r->d_spins, p->n, R, r->d_out, stream);
+  if (err == cudaSuccess) err = unpack_msc(r->d_best, p->n, R, r->d_out_best, stream);
+  launches += 3;
+  if (err == cudaSuccess) err = cudaEventRecord(r->done, stream);
+  if (err != cudaSuccess) {
+    cudaStreamSynchronize(stream);
+    result_free(r);
+    return cuda_fail(err, "launching parallel tempering");
   }
   r->launches = launches;
   r->sweep_launches = sweep_launches;
@@ -1240,6 +1394,37 @@ isg_status isg_result_best_all(const isg_result *r, int8_t *best_spins) {
       cudaMemcpy(best_spins, r->d_out_best, (size_t)r->R * r->n, cudaMemcpyDeviceToHost);
   cudaSetDevice(prev);
   if (err != cudaSuccess) return cuda_fail(err, "reading best spins");
+  return ISG_OK;
+}
+
+isg_status isg_parallel_tempering(const isg_problem *p, int32_t temperatures,
+                                  const double *betas, int32_t rounds, int32_t sweeps_per_round,
+                                  uint64_t seed, const isg_options *opts, void *cuda_stream,
+                                  isg_result **out) {
+  return tempering_impl(p, temperatures, betas, rounds, sweeps_per_round, seed, opts,
+                        (cudaStream_t)cuda_stream, out);
+}
+
+isg_status isg_result_exchanges(const isg_result *r, int64_t *accepted, int64_t *attempted,
+                                int32_t pairs) {
+  if (!r) return fail(ISG_EINVAL, "result must not be NULL");
+  if (pairs != r->pt_pairs || (pairs > 0 && (!accepted || !attempted)))
+    return fail(ISG_EINVAL, "the result has %d exchange pairs", r->pt_pairs);
+  isg_status st = result_sync(r);
+  if (st != ISG_OK) return st;
+  if (pairs <= 0) return ISG_OK;
+  std::vector<unsigned long long> acc(pairs);
+  int prev = 0;
+  cudaGetDevice(&prev);
+  cudaSetDevice(r->device);
+  cudaError_t err = cudaMemcpy(acc.data(), r->d_accepted, 8 * (size_t)pairs,
+                               cudaMemcpyDeviceToHost);
+  cudaSetDevice(prev);
+  if (err != cudaSuccess) return cuda_fail(err, "reading exchange counts");
+  for (int32_t k = 0; k < pairs; ++k) {
+    accepted[k] = (int64_t)acc[k];
+    attempted[k] = r->pt_attempted[k];
+  }
   return ISG_OK;
 }
 

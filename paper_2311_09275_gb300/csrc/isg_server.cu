@@ -252,6 +252,8 @@ void fill_torus_unit(TorusBatchItem &it, const Slot *sl, int32_t word, int32_t t
   s.W = p->W;
   s.cbits = sl->dp->cbits;
   s.table = r->d_table;
+  s.table_ws = 0;
+  s.table_ts = 2;
   s.key0 = (uint32_t)(sl->rq.seed & 0xFFFFFFFFu);
   s.key1 = (uint32_t)(sl->rq.seed >> 32);
   s.rk = round_keys(s.key0, s.key1);

@@ -246,12 +246,13 @@ __device__ void torus_word(const TorusSolve &s, int word, int k, int K, int t_be
   int hit = -1;
   uint32_t imp = 0u;  // replicas whose best state is the state at the start of sweep t
   // thresholds of the next sweep are loaded one sweep ahead
-  uint32_t T4n = s.table[2 * t], T8n = s.table[2 * t + 1];
+  const uint32_t *trow = s.table + (size_t)word * s.table_ws;
+  uint32_t T4n = trow[(size_t)t * s.table_ts], T8n = trow[(size_t)t * s.table_ts + 1];
   for (; t < t_end; ++t) {
     const uint32_t T4 = T4n, T8 = T8n;
     if (t + 1 < t_end) {
-      T4n = s.table[2 * t + 2];
-      T8n = s.table[2 * t + 3];
+      T4n = trow[(size_t)(t + 1) * s.table_ts];
+      T8n = trow[(size_t)(t + 1) * s.table_ts + 1];
     }
     // the (block, sweep) part of Philox rounds 1-2, uniform across the CTA
     BlockPrefix bp[8];

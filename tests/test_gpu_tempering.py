@@ -1,0 +1,74 @@
+"""Parallel tempering on the GPU (multi-spin torus kernel + exchange kernel)
+against the oracle, replica by replica: final and best states, energies and
+exchange counts."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2311_09275_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def isg():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    from paper_2311_09275_gb300 import build
+    build.build()
+    from paper_2311_09275_gb300 import isg as mod
+    return mod
+
+
+def assert_same_pt(res, orc, pairs):
+    spins, e, done = res.final()
+    assert np.array_equal(e, orc.e_final), "final energies differ"
+    assert np.array_equal(spins, orc.s_final), "final spins differ"
+    assert np.array_equal(res.best_all(), orc.s_best), "best spins differ"
+    assert np.array_equal(res.best(spins=False)[3], orc.e_best), "best energies differ"
+    from paper_2311_09275_gb300 import isg as mod
+    acc, att = mod.isg_result_exchanges(res, pairs)
+    assert np.array_equal(acc, orc.accepted) and np.array_equal(att, orc.attempted)
+
+
+@pytest.mark.parametrize("L,W,betas,rounds,per_round,cluster,threads", [
+    (12, 10, [0.2, 0.5, 0.9, 1.6], 7, 3, 0, 0),
+    (20, 16, [0.1, 0.3, 0.45, 0.8, 2.0], 6, 2, 2, 64),
+    (8, 6, [1.5, 0.4, 0.9], 9, 1, 1, 32),        # unordered ladder
+    (16, 14, [0.7], 5, 4, 4, 0),                 # one slot: no exchanges
+    (10, 12, [0.6, 0.6, 0.6, 0.6], 8, 2, 0, 0),  # equal temperatures
+])
+def test_tempering_bit_exact(isg, L, W, betas, rounds, per_round, cluster, threads):
+    t = I.torus(L, W, 40 + L)
+    c = oracle.csr_of(t)
+    orc = oracle.parallel_tempering(c, betas, rounds, per_round, 13)
+    res = isg.isg_parallel_tempering(isg.problem_of(t), betas, rounds, per_round, 13,
+                                     cluster_ctas=cluster, threads=threads)
+    assert_same_pt(res, orc, len(betas) - 1)
+    if len(set(betas)) == 1 and len(betas) > 1:
+        assert np.array_equal(orc.accepted, orc.attempted)
+
+
+def test_tempering_full_size_ladder(isg):
+    """80x100 torus, 8 slots (256 replicas), 4 rounds of 5 sweeps."""
+    t = I.torus(80, 100, 1)
+    betas = I.geometric_betas(0.2, 3.0, 8)
+    orc = oracle.parallel_tempering(oracle.csr_of(t), betas, 4, 5, 21)
+    res = isg.isg_parallel_tempering(isg.problem_of(t), betas, 4, 5, 21)
+    assert_same_pt(res, orc, 7)
+
+
+def test_tempering_rejects_bad_input(isg):
+    g = isg.problem_of(I.random_graph(50, 60, 1))
+    with pytest.raises(isg.IsgError):
+        isg.isg_parallel_tempering(g, [0.5, 1.0], 2, 2, 1)   # graphs: not in this version
+    t = isg.problem_of(I.torus(8, 8, 1))
+    with pytest.raises(isg.IsgError):
+        isg.isg_parallel_tempering(t, [], 2, 2, 1)
+    with pytest.raises(isg.IsgError):
+        isg.isg_parallel_tempering(t, [0.5, np.inf], 2, 2, 1)
+    with pytest.raises(isg.IsgError):
+        isg.isg_parallel_tempering(t, [0.5, 1.0], 0, 2, 1)
+    res = isg.isg_anneal(t, 8, np.full(3, 0.5), 1)
+    with pytest.raises(isg.IsgError):
+        isg.isg_result_exchanges(res, 3)                    # no exchange pairs there
