@@ -95,6 +95,11 @@ struct isg_server {
   cudaStream_t stream = nullptr;
   cudaStream_t side[2] = {nullptr, nullptr};
   cudaEvent_t ev_in = nullptr, ev_side[2] = {nullptr, nullptr};
+  // pass balancing: each unit kind's kernel time in the last pass (timing
+  // events) sets its sweeps-per-chunk factor so that all kinds end together
+  cudaEvent_t ev_k0[3] = {nullptr, nullptr, nullptr}, ev_k1[3] = {nullptr, nullptr, nullptr};
+  bool kind_timed[3] = {false, false, false};
+  double kind_scale[3] = {1.0, 1.0, 1.0};
   std::vector<Slot *> active;
   size_t used = 0;
   size_t cap_t = 0, cap_c = 0, cap_g = 0;
@@ -342,9 +347,13 @@ void fill_gm_unit(GraphMscItem &it, const Slot *sl, int32_t word, int32_t t_begi
   it.resume = t_begin > 0;
 }
 
-// One launch of the unit kernels over the listed slots, sweeps [t, t_end) each.
+// Unit kind of a slot: 0 torus words, 1 graph words, 2 graph quads.
+int kind_of(const Slot *sl) { return sl->res->msc ? (sl->res->relabelled ? 1 : 0) : 2; }
+
+// One launch of the unit kernels over the listed slots, sweeps [t, t_end) each;
+// with `timed`, each kind's kernel is bracketed by timing events.
 cudaError_t run_units(isg_server *s, const std::vector<Slot *> &slots,
-                      const std::vector<int32_t> &t_end) {
+                      const std::vector<int32_t> &t_end, bool timed = false) {
   size_t nt = 0, nc = 0, ng = 0;
   for (size_t k = 0; k < slots.size(); ++k) {
     const isg_result *r = slots[k]->res;
@@ -415,28 +424,63 @@ cudaError_t run_units(isg_server *s, const std::vector<Slot *> &slots,
     return (int)std::min<size_t>(units, (size_t)sm_count() * per_sm);
   };
   // the three unit kinds run concurrently (each fills the SMs the others leave)
+  for (int k = 0; k < 3; ++k) s->kind_timed[k] = false;
+  auto mark = [&](int k, bool begin, cudaStream_t st) {
+    if (!timed || err != cudaSuccess) return;
+    err = cudaEventRecord(begin ? s->ev_k0[k] : s->ev_k1[k], st);
+    if (!begin && err == cudaSuccess) s->kind_timed[k] = true;
+  };
   if (err == cudaSuccess && (ng || nc)) err = cudaEventRecord(s->ev_in, s->stream);
   if (err == cudaSuccess && ng) {
     err = cudaStreamWaitEvent(s->side[0], s->ev_in, 0);
+    mark(1, true, s->side[0]);
     if (err == cudaSuccess)
       err = gm_batch_launch(s->d_g, s->d_ctl + 5, s->d_ord_g, s->d_ctl + 4, ctas_for(ng, smem_g),
                             threads, smem_g, s->side[0]);
+    mark(1, false, s->side[0]);
     if (err == cudaSuccess) err = cudaEventRecord(s->ev_side[0], s->side[0]);
   }
   if (err == cudaSuccess && nc) {
     err = cudaStreamWaitEvent(s->side[1], s->ev_in, 0);
+    mark(2, true, s->side[1]);
     if (err == cudaSuccess)
       err = csr_batch_launch(s->d_c, s->d_ctl + 3, s->d_ord_c, s->d_ctl + 1, ctas_for(nc, smem_c),
                              threads, smem_c, s->side[1]);
+    mark(2, false, s->side[1]);
     if (err == cudaSuccess) err = cudaEventRecord(s->ev_side[1], s->side[1]);
   }
-  if (err == cudaSuccess && nt)
+  if (err == cudaSuccess && nt) {
+    mark(0, true, s->stream);
     err = torus_batch_launch(s->d_t, s->d_ctl + 2, s->d_ord_t, s->d_ctl + 0, ctas_for(nt, smem_t),
                              threads, smem_t, s->stream);
+    mark(0, false, s->stream);
+  }
   if (err == cudaSuccess && ng) err = cudaStreamWaitEvent(s->stream, s->ev_side[0], 0);
   if (err == cudaSuccess && nc) err = cudaStreamWaitEvent(s->stream, s->ev_side[1], 0);
   for (Slot *sl : slots) sl->res->sweep_launches += 1;
   return err;
+}
+
+// After a timed pass: scale each kind's chunk so that its kernel would have
+// taken as long as the slowest kind's (bounded steps, bounded factors).
+void balance_kinds(isg_server *s) {
+  float ms[3] = {0.f, 0.f, 0.f}, mx = 0.f;
+  int n = 0;
+  for (int k = 0; k < 3; ++k) {
+    if (!s->kind_timed[k]) continue;
+    if (cudaEventElapsedTime(&ms[k], s->ev_k0[k], s->ev_k1[k]) != cudaSuccess || ms[k] <= 0.f) {
+      s->kind_timed[k] = false;
+      continue;
+    }
+    mx = std::max(mx, ms[k]);
+    ++n;
+  }
+  if (n < 2) return;
+  for (int k = 0; k < 3; ++k) {
+    if (!s->kind_timed[k]) continue;
+    const double f = std::min(4.0, std::max(0.5, (double)mx / ms[k]));
+    s->kind_scale[k] = std::min(64.0, std::max(1.0 / 16, s->kind_scale[k] * f));
+  }
 }
 
 cudaError_t finish_slot(isg_server *s, Slot *sl) {
@@ -482,8 +526,10 @@ void worker_main(isg_server *s) {
     for (size_t k = 0; k < s->active.size(); ++k) {
       Slot *sl = s->active[k];
       // chunks hold equal work per unit: sweeps_per_chunk is the count for a
-      // 10,000-spin instance, scaled inversely with the instance size
-      const int64_t sweeps = std::max<int64_t>(1, (int64_t)s->chunk * 10000 / sl->rq.p->n);
+      // 10,000-spin instance, scaled inversely with the instance size and by
+      // the unit kind's balance factor
+      const int64_t sweeps = std::max<int64_t>(
+          1, (int64_t)((double)s->chunk * 10000.0 / sl->rq.p->n * s->kind_scale[kind_of(sl)]));
       t_end[k] = (int32_t)std::min<int64_t>(sl->t + sweeps, sl->rq.S);
       sl->t_end = t_end[k];
       nstatus += 2 * (size_t)sl->res->units;
@@ -492,7 +538,7 @@ void worker_main(isg_server *s) {
                               s->stream);
     }
     if (err == cudaSuccess) err = grow(s, 0, 0, nstatus);
-    if (err == cudaSuccess) err = run_units(s, s->active, t_end);
+    if (err == cudaSuccess) err = run_units(s, s->active, t_end, true);
     {
       std::lock_guard<std::mutex> lock(s->mu);
       ++s->n_passes;
@@ -509,6 +555,7 @@ void worker_main(isg_server *s) {
       off += 2 * (size_t)u;
     }
     if (err == cudaSuccess) err = cudaStreamSynchronize(s->stream);
+    if (err == cudaSuccess) balance_kinds(s);
     if (err != cudaSuccess) {
       s->worker_error = cuda_fail(err, "server chunk");
       std::lock_guard<std::mutex> lock(s->mu);
@@ -606,6 +653,10 @@ isg_status isg_server_create(size_t device_mem_budget, int32_t max_slots, int32_
     if (err == cudaSuccess) err = cudaEventCreateWithFlags(&s->ev_side[i], cudaEventDisableTiming);
   }
   if (err == cudaSuccess) err = cudaEventCreateWithFlags(&s->ev_in, cudaEventDisableTiming);
+  for (int k = 0; k < 3 && err == cudaSuccess; ++k) {
+    err = cudaEventCreate(&s->ev_k0[k]);
+    if (err == cudaSuccess) err = cudaEventCreate(&s->ev_k1[k]);
+  }
   if (err == cudaSuccess) err = cudaMalloc(&s->d_ctl, 64);
   if (err == cudaSuccess) err = cudaMallocHost(&s->h_ctl, 64);
   if (err != cudaSuccess) {
@@ -615,6 +666,10 @@ isg_status isg_server_create(size_t device_mem_budget, int32_t max_slots, int32_
       if (s->ev_side[i]) cudaEventDestroy(s->ev_side[i]);
     }
     if (s->ev_in) cudaEventDestroy(s->ev_in);
+    for (int k = 0; k < 3; ++k) {
+      if (s->ev_k0[k]) cudaEventDestroy(s->ev_k0[k]);
+      if (s->ev_k1[k]) cudaEventDestroy(s->ev_k1[k]);
+    }
     cudaFree(s->d_ctl);
     cudaFreeHost(s->h_ctl);
     delete s;
@@ -734,6 +789,10 @@ isg_status isg_server_destroy(isg_server *s) {
     cudaEventDestroy(s->ev_side[i]);
   }
   cudaEventDestroy(s->ev_in);
+  for (int k = 0; k < 3; ++k) {
+    cudaEventDestroy(s->ev_k0[k]);
+    cudaEventDestroy(s->ev_k1[k]);
+  }
   cudaStreamDestroy(s->stream);
   cudaSetDevice(prev);
   const isg_status st = s->worker_error;
