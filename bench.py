@@ -246,6 +246,11 @@ def run_reference(args):
     world, rank, local, dist = dist_setup(args)
     if rank != 0:
         return
+    if args.config not in ("torus", "random", "mis"):
+        print(json.dumps({"impl": "reference", "unavailable":
+                          f"the oracle arm times the single-instance workloads (torus, random, "
+                          f"mis); --config {args.config} has no oracle timing line"}))
+        return
     sv, name = workload(args.config, 0, args.sweeps)
     import oracle
     cores = os.cpu_count() or 1
