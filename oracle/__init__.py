@@ -73,8 +73,8 @@ def _load():
                                    u64, ctypes.c_int, ctypes.c_int, P, P, P, P, P, P]
         lib.orc_anneal.restype = ctypes.c_int
         lib.orc_initial_spins.argtypes = [i32, i32, P, u64, P]
-        lib.orc_parallel_tempering.argtypes = [i32, P, P, P, P, P, i32, i32, P, i32, i32, u64,
-                                               ctypes.c_int, P, P, P, P, P, P]
+        lib.orc_parallel_tempering.argtypes = [i32, P, P, P, P, P, i32, i32, P, i32, i32, i32,
+                                               u64, ctypes.c_int, P, P, P, P, P, P, P]
         lib.orc_parallel_tempering.restype = ctypes.c_int
         lib.orc_enumerate.argtypes = [i32, P, P, P, P, P, P]
         lib.orc_enumerate.restype = i64
@@ -251,10 +251,11 @@ class TemperingResult:
     """Per replica r = 32 k + c (slot k, chain c): final and best states and
     energies; exchange counts per slot pair."""
 
-    def __init__(self, s_final, e_final, s_best, e_best, accepted, attempted):
+    def __init__(self, s_final, e_final, s_best, e_best, accepted, attempted, flipped):
         self.s_final, self.e_final = s_final, e_final
         self.s_best, self.e_best = s_best, e_best
         self.accepted, self.attempted = accepted, attempted
+        self.flipped = flipped
 
     @property
     def best(self):
@@ -263,8 +264,9 @@ class TemperingResult:
 
 
 def parallel_tempering(csr: Csr, betas, rounds: int, per_round: int, seed: int, colour=None,
-                       nthreads: int = 0) -> TemperingResult:
-    """Parallel tempering over len(betas) slots x 32 chains (see isg_oracle.h)."""
+                       nthreads: int = 0, icm_slots: int = 0) -> TemperingResult:
+    """Parallel tempering over len(betas) slots x 32 chains, with Houdayer
+    cluster moves on the last icm_slots slots (see isg_oracle.h)."""
     if colour is None:
         colour, nc = csr.greedy_colouring()
     else:
@@ -279,12 +281,14 @@ def parallel_tempering(csr: Csr, betas, rounds: int, per_round: int, seed: int, 
     e_best = np.zeros(R, dtype=np.int32)
     acc = np.zeros(max(K - 1, 1), dtype=np.int64)
     att = np.zeros(max(K - 1, 1), dtype=np.int64)
+    flipped = np.zeros(K, dtype=np.int64)
     if nthreads <= 0:
-        nthreads = min(os.cpu_count() or 1, 32)
+        nthreads = min(os.cpu_count() or 1, 16)
     rc = _load().orc_parallel_tempering(
         csr.n, _p(csr.rowptr), _p(csr.col), _p(csr.wt), csr._fp(), _p(colour), nc, K, _p(b),
-        int(rounds), int(per_round), int(seed), int(nthreads), _p(s_final), _p(e_final),
-        _p(s_best), _p(e_best), _p(acc), _p(att))
+        int(rounds), int(per_round), int(icm_slots), int(seed), int(nthreads), _p(s_final),
+        _p(e_final), _p(s_best), _p(e_best), _p(acc), _p(att), _p(flipped))
     if rc != 0:
         raise ValueError("bad arguments to the oracle")
-    return TemperingResult(s_final, e_final, s_best, e_best, acc[: K - 1], att[: K - 1])
+    return TemperingResult(s_final, e_final, s_best, e_best, acc[: K - 1], att[: K - 1],
+                           flipped)

@@ -53,6 +53,7 @@ void orc_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t ou
 #define ORC_TAG_SWEEP 0u
 #define ORC_TAG_INIT 1u
 #define ORC_TAG_EXCHANGE 2u
+#define ORC_TAG_CLUSTER 3u
 
 static uint32_t orc_draw(uint64_t seed, uint32_t i, uint32_t t, uint32_t r, uint32_t tag) {
     uint32_t ctr[4] = {i, t, r >> 2, tag};
@@ -389,91 +390,169 @@ typedef struct {
     int8_t *s_final, *s_best;
     int32_t *e_final, *e_best;
     int64_t *accepted, *attempted; /* [32][K - 1] per chain, summed by the caller */
+    int32_t icm_slots;             /* Houdayer moves on slots k >= K - icm_slots */
+    int64_t *flipped;              /* [K] sites flipped by cluster moves (per chain pair) */
 } orc_pt_job;
 
-static void orc_pt_chain(orc_pt_job *J, int32_t c) {
-    const int32_t n = J->n, K = J->K;
-    int64_t *e = (int64_t *)malloc(sizeof(int64_t) * (size_t)K);
-    int64_t *eb = (int64_t *)malloc(sizeof(int64_t) * (size_t)K);
-    int8_t *tmp = (int8_t *)malloc((size_t)n);
-    for (int32_t k = 0; k < K; ++k) {
-        const uint32_t r = (uint32_t)(32 * k + c);
-        int8_t *s = J->s_final + (int64_t)r * n;
-        for (int32_t i = 0; i < n; ++i)
-            s[i] = (orc_draw(J->seed, (uint32_t)i, 0u, r, ORC_TAG_INIT) >> 31) ? 1 : -1;
-        e[k] = orc_energy(n, J->rowptr, J->col, J->wt, J->field, s);
-        eb[k] = e[k];
-        memcpy(J->s_best + (int64_t)r * n, s, (size_t)n);
+/* Houdayer cluster move on chains a and b of one slot (Sec. II.C's replica
+ * cluster moves): the sites where the two configurations differ span a
+ * subgraph; one of them is drawn (the (u mod D)-th differing site in vertex
+ * order, D their number, u word 0 of Philox(seed, (k, q, m, 3)) for pair m),
+ * its connected component in that subgraph is the cluster, and both chains
+ * flip it - i.e. they exchange their spins on the cluster, which leaves
+ * E_a + E_b unchanged.  Returns the cluster size (0 when a = b). */
+static int64_t orc_houdayer(const orc_pt_job *J, int8_t *sa, int8_t *sb, uint32_t k, uint32_t q,
+                            uint32_t m, int32_t *stack, uint8_t *in) {
+    const int32_t n = J->n;
+    int64_t D = 0;
+    for (int32_t i = 0; i < n; ++i) D += sa[i] != sb[i];
+    if (D == 0) return 0;
+    uint32_t ctr[4] = {k, q, m, ORC_TAG_CLUSTER};
+    uint32_t key[2] = {(uint32_t)(J->seed & 0xFFFFFFFFu), (uint32_t)(J->seed >> 32)};
+    uint32_t out[4];
+    orc_philox4x32_10(ctr, key, out);
+    int64_t pick = (int64_t)(out[0] % (uint64_t)D), seen = 0;
+    int32_t root = -1;
+    for (int32_t i = 0; i < n && root < 0; ++i)
+        if (sa[i] != sb[i] && seen++ == pick) root = i;
+    memset(in, 0, (size_t)n);
+    int64_t top = 0, size = 0;
+    stack[top++] = root;
+    in[root] = 1;
+    while (top > 0) {
+        const int32_t i = stack[--top];
+        ++size;
+        for (int64_t p = J->rowptr[i]; p < J->rowptr[i + 1]; ++p) {
+            const int32_t j = J->col[p];
+            if (!in[j] && sa[j] != sb[j]) {
+                in[j] = 1;
+                stack[top++] = j;
+            }
+        }
     }
-    for (int32_t q = 0; q < J->rounds; ++q) {
+    for (int32_t i = 0; i < n; ++i)
+        if (in[i]) {
+            sa[i] = (int8_t)(-sa[i]);
+            sb[i] = (int8_t)(-sb[i]);
+        }
+    return size;
+}
+
+/* The chains of one pair (c = 2m, 2m + 1) run together: cluster moves couple
+ * them; chains of different pairs never interact. */
+static void orc_pt_pair(orc_pt_job *J, int32_t m) {
+    const int32_t n = J->n, K = J->K;
+    int64_t *e = (int64_t *)malloc(sizeof(int64_t) * 2 * (size_t)K);   /* [2][K] */
+    int64_t *eb = (int64_t *)malloc(sizeof(int64_t) * 2 * (size_t)K);
+    int8_t *tmp = (int8_t *)malloc((size_t)n);
+    int32_t *stack = (int32_t *)malloc(sizeof(int32_t) * (size_t)n);
+    uint8_t *in = (uint8_t *)malloc((size_t)n);
+    for (int32_t h = 0; h < 2; ++h)
         for (int32_t k = 0; k < K; ++k) {
-            const uint32_t r = (uint32_t)(32 * k + c);
+            const uint32_t r = (uint32_t)(32 * k + 2 * m + h);
             int8_t *s = J->s_final + (int64_t)r * n;
-            const uint32_t *row = J->table + (int64_t)k * (J->kmax + 1);
-            for (int32_t j = 0; j < J->per_round; ++j) {
-                const uint32_t t = (uint32_t)(q * J->per_round + j);
-                for (int32_t cc = 0; cc < J->n_colours; ++cc)
-                    for (int64_t z = J->class_start[cc]; z < J->class_start[cc + 1]; ++z) {
-                        const int32_t i = J->order[z];
-                        int64_t h = J->field ? J->field[i] : 0;
-                        for (int64_t p = J->rowptr[i]; p < J->rowptr[i + 1]; ++p)
-                            h += (int64_t)J->wt[p] * s[J->col[p]];
-                        const int64_t kk = -(int64_t)s[i] * h;
-                        if (kk <= 0 || orc_draw(J->seed, (uint32_t)i, t, r, ORC_TAG_SWEEP) < row[kk]) {
-                            s[i] = (int8_t)(-s[i]);
-                            e[k] += 2 * kk;
+            for (int32_t i = 0; i < n; ++i)
+                s[i] = (orc_draw(J->seed, (uint32_t)i, 0u, r, ORC_TAG_INIT) >> 31) ? 1 : -1;
+            e[h * K + k] = orc_energy(n, J->rowptr, J->col, J->wt, J->field, s);
+            eb[h * K + k] = e[h * K + k];
+            memcpy(J->s_best + (int64_t)r * n, s, (size_t)n);
+        }
+    for (int32_t q = 0; q < J->rounds; ++q) {
+        /* sweeps of every replica at its slot's beta */
+        for (int32_t h = 0; h < 2; ++h)
+            for (int32_t k = 0; k < K; ++k) {
+                const uint32_t r = (uint32_t)(32 * k + 2 * m + h);
+                int8_t *s = J->s_final + (int64_t)r * n;
+                const uint32_t *row = J->table + (int64_t)k * (J->kmax + 1);
+                for (int32_t j = 0; j < J->per_round; ++j) {
+                    const uint32_t t = (uint32_t)(q * J->per_round + j);
+                    for (int32_t cc = 0; cc < J->n_colours; ++cc)
+                        for (int64_t z = J->class_start[cc]; z < J->class_start[cc + 1]; ++z) {
+                            const int32_t i = J->order[z];
+                            int64_t hf = J->field ? J->field[i] : 0;
+                            for (int64_t p = J->rowptr[i]; p < J->rowptr[i + 1]; ++p)
+                                hf += (int64_t)J->wt[p] * s[J->col[p]];
+                            const int64_t kk = -(int64_t)s[i] * hf;
+                            if (kk <= 0 ||
+                                orc_draw(J->seed, (uint32_t)i, t, r, ORC_TAG_SWEEP) < row[kk]) {
+                                s[i] = (int8_t)(-s[i]);
+                                e[h * K + k] += 2 * kk;
+                            }
                         }
+                    if (e[h * K + k] < eb[h * K + k]) {
+                        eb[h * K + k] = e[h * K + k];
+                        memcpy(J->s_best + (int64_t)r * n, s, (size_t)n);
                     }
-                if (e[k] < eb[k]) {
-                    eb[k] = e[k];
-                    memcpy(J->s_best + (int64_t)r * n, s, (size_t)n);
+                }
+            }
+        /* Houdayer cluster moves between the pair's two chains on the last
+         * icm_slots slots */
+        for (int32_t k = K - J->icm_slots; k < K; ++k) {
+            if (k < 0) continue;
+            int8_t *sa = J->s_final + (int64_t)(32 * k + 2 * m) * n;
+            int8_t *sb = J->s_final + (int64_t)(32 * k + 2 * m + 1) * n;
+            const int64_t size = orc_houdayer(J, sa, sb, (uint32_t)k, (uint32_t)q, (uint32_t)m,
+                                              stack, in);
+            if (size > 0) {
+                e[k] = orc_energy(n, J->rowptr, J->col, J->wt, J->field, sa);
+                e[K + k] = orc_energy(n, J->rowptr, J->col, J->wt, J->field, sb);
+                J->flipped[(int64_t)m * K + k] += size;
+            }
+        }
+        /* exchanges between neighbouring slots, chain by chain */
+        for (int32_t h = 0; h < 2; ++h) {
+            const int32_t c = 2 * m + h;
+            int64_t *ec = e + h * K;
+            for (int32_t k = q % 2; k + 1 < K; k += 2) {
+                const double a = (J->betas[k] - J->betas[k + 1]) * (double)(ec[k] - ec[k + 1]);
+                int swap = a >= 0.0;
+                if (!swap) {
+                    const double x = floor(ldexp(exp(a), 32));
+                    const uint32_t thr = x >= 4294967295.0 ? 4294967295u : (uint32_t)x;
+                    swap = orc_draw(J->seed, (uint32_t)k, (uint32_t)q, (uint32_t)c,
+                                    ORC_TAG_EXCHANGE) < thr;
+                }
+                J->attempted[(int64_t)c * (K - 1) + k]++;
+                if (swap) {
+                    J->accepted[(int64_t)c * (K - 1) + k]++;
+                    int8_t *a_s = J->s_final + (int64_t)(32 * k + c) * n;
+                    int8_t *b_s = J->s_final + (int64_t)(32 * (k + 1) + c) * n;
+                    memcpy(tmp, a_s, (size_t)n);
+                    memcpy(a_s, b_s, (size_t)n);
+                    memcpy(b_s, tmp, (size_t)n);
+                    const int64_t te = ec[k];
+                    ec[k] = ec[k + 1];
+                    ec[k + 1] = te;
                 }
             }
         }
-        for (int32_t k = q % 2; k + 1 < K; k += 2) {
-            const double a = (J->betas[k] - J->betas[k + 1]) * (double)(e[k] - e[k + 1]);
-            int swap = a >= 0.0;
-            if (!swap) {
-                const double x = floor(ldexp(exp(a), 32));
-                const uint32_t thr = x >= 4294967295.0 ? 4294967295u : (uint32_t)x;
-                swap = orc_draw(J->seed, (uint32_t)k, (uint32_t)q, (uint32_t)c, ORC_TAG_EXCHANGE) < thr;
-            }
-            J->attempted[(int64_t)c * (K - 1) + k]++;
-            if (swap) {
-                J->accepted[(int64_t)c * (K - 1) + k]++;
-                int8_t *a_s = J->s_final + (int64_t)(32 * k + c) * n;
-                int8_t *b_s = J->s_final + (int64_t)(32 * (k + 1) + c) * n;
-                memcpy(tmp, a_s, (size_t)n);
-                memcpy(a_s, b_s, (size_t)n);
-                memcpy(b_s, tmp, (size_t)n);
-                const int64_t te = e[k];
-                e[k] = e[k + 1];
-                e[k + 1] = te;
-            }
+    }
+    for (int32_t h = 0; h < 2; ++h)
+        for (int32_t k = 0; k < K; ++k) {
+            J->e_final[32 * k + 2 * m + h] = (int32_t)e[h * K + k];
+            J->e_best[32 * k + 2 * m + h] = (int32_t)eb[h * K + k];
         }
-    }
-    for (int32_t k = 0; k < K; ++k) {
-        J->e_final[32 * k + c] = (int32_t)e[k];
-        J->e_best[32 * k + c] = (int32_t)eb[k];
-    }
     free(e);
     free(eb);
     free(tmp);
+    free(stack);
+    free(in);
 }
 
 static void *orc_pt_worker(void *arg) {
     orc_pt_job *J = (orc_pt_job *)arg;
-    for (int32_t c = J->c_begin; c < J->c_end; ++c) orc_pt_chain(J, c);
+    for (int32_t m = J->c_begin; m < J->c_end; ++m) orc_pt_pair(J, m);
     return NULL;
 }
 
 int orc_parallel_tempering(int32_t n, const int64_t *rowptr, const int32_t *col, const int32_t *wt,
                            const int32_t *field, const int32_t *colour, int32_t n_colours,
                            int32_t K, const double *betas, int32_t rounds, int32_t per_round,
-                           uint64_t seed, int nthreads, int8_t *s_final, int32_t *e_final,
-                           int8_t *s_best, int32_t *e_best, int64_t *accepted,
-                           int64_t *attempted) {
+                           int32_t icm_slots, uint64_t seed, int nthreads, int8_t *s_final,
+                           int32_t *e_final, int8_t *s_best, int32_t *e_best, int64_t *accepted,
+                           int64_t *attempted, int64_t *flipped) {
     if (n < 1 || K < 1 || rounds < 1 || per_round < 1 || n_colours < 1) return -1;
+    if (icm_slots < 0 || icm_slots > K) return -1;
     for (int32_t i = 0; i < n; ++i)
         if (colour[i] < 0 || colour[i] >= n_colours) return -1;
     int64_t kmax = 0;
@@ -495,9 +574,10 @@ int orc_parallel_tempering(int32_t n, const int64_t *rowptr, const int32_t *col,
     const int32_t pairs = K > 1 ? K - 1 : 1;
     int64_t *acc = (int64_t *)calloc((size_t)32 * pairs, sizeof(int64_t));
     int64_t *att = (int64_t *)calloc((size_t)32 * pairs, sizeof(int64_t));
+    int64_t *flp = (int64_t *)calloc((size_t)16 * K, sizeof(int64_t));
 
     if (nthreads < 1) nthreads = 1;
-    if (nthreads > 32) nthreads = 32;
+    if (nthreads > 16) nthreads = 16;
     orc_pt_job *jobs = (orc_pt_job *)malloc(sizeof(orc_pt_job) * (size_t)nthreads);
     pthread_t *th = (pthread_t *)malloc(sizeof(pthread_t) * (size_t)nthreads);
     for (int w = 0; w < nthreads; ++w) {
@@ -507,9 +587,9 @@ int orc_parallel_tempering(int32_t n, const int64_t *rowptr, const int32_t *col,
         J->n_colours = n_colours; J->rowptr = rowptr; J->col = col; J->wt = wt;
         J->field = field; J->order = order; J->class_start = class_start; J->betas = betas;
         J->table = table; J->kmax = (int32_t)kmax; J->seed = seed;
-        J->c_begin = 32 * w / nthreads; J->c_end = 32 * (w + 1) / nthreads;
+        J->c_begin = 16 * w / nthreads; J->c_end = 16 * (w + 1) / nthreads;  /* chain pairs */
         J->s_final = s_final; J->s_best = s_best; J->e_final = e_final; J->e_best = e_best;
-        J->accepted = acc; J->attempted = att;
+        J->accepted = acc; J->attempted = att; J->icm_slots = icm_slots; J->flipped = flp;
     }
     for (int w = 1; w < nthreads; ++w) pthread_create(&th[w], NULL, orc_pt_worker, &jobs[w]);
     orc_pt_worker(&jobs[0]);
@@ -522,6 +602,11 @@ int orc_parallel_tempering(int32_t n, const int64_t *rowptr, const int32_t *col,
             attempted[k] += att[(int64_t)c * (K - 1) + k];
         }
     }
+    for (int32_t k = 0; k < K; ++k) {
+        flipped[k] = 0;
+        for (int32_t m = 0; m < 16; ++m) flipped[k] += flp[(int64_t)m * K + k];
+    }
+    free(flp);
     free(jobs);
     free(th);
     free(acc);

@@ -87,13 +87,20 @@ int orc_anneal(int32_t n, const int64_t *rowptr, const int32_t *col, const int32
  * floor(2^32 exp(.)).  Outputs per replica ([32K][n] spins): s_final, e_final,
  * s_best, e_best (best states stay with the slot, checked at sweep ends);
  * accepted[k] / attempted[k] exchange counts of pair (k, k+1), k < K-1.
+ * With icm_slots > 0, every round's sweeps are followed (before the
+ * exchanges) by one Houdayer cluster move per chain pair (2m, 2m+1), m < 16,
+ * on each of the last icm_slots slots: a site where the two differ is drawn
+ * (the (u mod D)-th in vertex order, u word 0 of Philox(seed, (k, round, m,
+ * 3)), D the number of such sites), its connected component among the
+ * differing sites is flipped in both chains, and their energies are
+ * recomputed; flipped[k] sums the cluster sizes of slot k.
  * Returns 0, or -1 on bad arguments. */
 int orc_parallel_tempering(int32_t n, const int64_t *rowptr, const int32_t *col, const int32_t *wt,
                            const int32_t *field, const int32_t *colour, int32_t n_colours,
                            int32_t K, const double *betas, int32_t rounds, int32_t per_round,
-                           uint64_t seed, int nthreads, int8_t *s_final, int32_t *e_final,
-                           int8_t *s_best, int32_t *e_best, int64_t *accepted,
-                           int64_t *attempted);
+                           int32_t icm_slots, uint64_t seed, int nthreads, int8_t *s_final,
+                           int32_t *e_final, int8_t *s_best, int32_t *e_best, int64_t *accepted,
+                           int64_t *attempted, int64_t *flipped);
 
 /* Initial spins of the listed replicas (the state before sweep 0). */
 void orc_initial_spins(int32_t n, int32_t n_rep, const int32_t *rep_ids, uint64_t seed, int8_t *s);
