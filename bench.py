@@ -588,19 +588,22 @@ def run_pt(args):
     t = I.torus(80, 100, 1)
     p = isg.problem_of(t)
     attempts = 32.0 * K * t.L * t.W * rounds * per_round
+    icm = args.icm
     for _ in range(args.warmup):
-        isg.isg_parallel_tempering(p, betas, rounds, per_round, 1, stream=stream).close()
+        isg.isg_parallel_tempering(p, betas, rounds, per_round, 1, stream=stream,
+                                   icm_slots=icm).close()
     torch.cuda.synchronize()
     ms, res = [], None
     with ClockSampler(0) as clocks:
         for k in range(args.steps):
             r = isg.isg_parallel_tempering(p, betas, rounds, per_round, 1 + k, stream=stream,
-                                           time_kernels=True)
+                                           time_kernels=True, icm_slots=icm)
             ms.append(r.stats()["sweep_kernel_ms"])
             if res is not None:
                 res.close()
             res = r
     acc, att = isg.isg_result_exchanges(res, K - 1)
+    flips = isg.isg_result_cluster_flips(res, K)
     st = res.stats()
     best = res.best(spins=False)
     res.close()
@@ -610,11 +613,13 @@ def run_pt(args):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
             "data": "synthetic",
             "config": {"workload": f"tempering_torus_80x100_K{K}x32_rounds{rounds}x{per_round}"
-                                   f"_geometric_0.2_3.0", "attempts_per_step": attempts,
+                                   f"_geometric_0.2_3.0" + (f"_houdayer{icm}" if icm else ""),
+                       "attempts_per_step": attempts, "cluster_move_slots": icm,
                        "launch": {k: st[k] for k in ("kernel", "ctas", "cluster_ctas", "threads")},
                        "l2": "state of each word in shared memory during a round"},
             "exchange_acceptance": [round(float(a) / float(b), 4) for a, b in zip(acc, att)],
             "best_energy": int(best[0]), "gpu_launches": st["launches"],
+            "cluster_sites_flipped_per_round": [round(float(f) / rounds, 2) for f in flips],
             "clocks": clocks.summary()}
     print(json.dumps(line))
 
@@ -709,6 +714,8 @@ def main():
                          "multi-spin; 0 = tuned)")
     ap.add_argument("--launch", default=None,
                     help="explicit launch shape CLUSTER,THREADS (skips the autotuner)")
+    ap.add_argument("--icm", type=int, default=0,
+                    help="pt: Houdayer cluster moves on the last ICM temperature slots")
     ap.add_argument("--sweeps", type=int, default=None,
                     help="shorter schedule for profiling captures (default: the full workload)")
     args = ap.parse_args()

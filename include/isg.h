@@ -183,15 +183,28 @@ isg_status isg_anneal_batch(const isg_problem *const *probs, int32_t count, int3
  * when the exponent is >= 0, else when the uniform word (c mod 4) of
  * Philox(seed, (k, round, c / 4, 2)) is below floor(2^32 exp(exponent)), FP64
  * on the host.  Best states and energies stay with the slot (checked at sweep
- * ends).  No target.  The result is read like isg_anneal's (R = 32 K, S =
- * rounds * sweeps_per_round); exchange counts by isg_result_exchanges.  opts
+ * ends).  No target.  With icm_slots > 0, each round's sweeps are followed,
+ * before the exchanges, by a Houdayer cluster move (Sec. II.C's replica
+ * cluster moves) in each chain pair (2m, 2m+1) of the last icm_slots slots:
+ * the sites where the pair differs span a subgraph; the (u mod D)-th of them
+ * in vertex order (D their number, u = word 0 of Philox(seed, (k, round, m,
+ * 3))) seeds the cluster, its connected component among the differing sites,
+ * which both chains flip (exchanging their spins there, so E_a + E_b is
+ * unchanged); the chains' energies are then recomputed.  The result is read
+ * like isg_anneal's (R = 32 K, S = rounds * sweeps_per_round); exchange counts
+ * by isg_result_exchanges, cluster sizes by isg_result_cluster_flips.  opts
  * may be NULL (kernel AUTO or TORUS_MSC; cluster/threads as isg_anneal).
  * EINVAL: not a torus, K outside [1, 4096], rounds or sweeps_per_round < 1,
- * a bad beta. */
+ * a bad beta, icm_slots outside [0, K], or icm_slots > 0 with n > 28,544. */
 isg_status isg_parallel_tempering(const isg_problem *p, int32_t temperatures,
                                   const double *betas, int32_t rounds, int32_t sweeps_per_round,
-                                  uint64_t seed, const isg_options *opts, void *cuda_stream,
-                                  isg_result **out);
+                                  int32_t icm_slots, uint64_t seed, const isg_options *opts,
+                                  void *cuda_stream, isg_result **out);
+
+/* Sizes of the cluster moves of a parallel-tempering result: flipped[k] =
+ * sites flipped per chain of a pair, summed over pairs and rounds, for each of
+ * the `temperatures` slots.  EINVAL for another slot count.  Waits. */
+isg_status isg_result_cluster_flips(const isg_result *r, int64_t *flipped, int32_t temperatures);
 
 /* Exchange counts of a parallel-tempering result: accepted[k] and attempted[k]
  * for slot pairs (k, k+1), k < pairs = K - 1 (EINVAL for another pairs value,

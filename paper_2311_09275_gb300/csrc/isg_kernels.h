@@ -218,6 +218,13 @@ cudaError_t pt_exchange(uint32_t *spins, int32_t *e_cur, int32_t n, int32_t K, i
                         const uint32_t *xtable, int32_t xlen, unsigned long long *accepted,
                         cudaStream_t stream);
 
+// Parallel tempering: one Houdayer cluster move per chain pair (lanes 2m,
+// 2m+1) on slot words k0 .. k0+slots-1 of an L x W torus state; flipped[k]
+// gains the cluster sizes.  Needs 8 L W bytes of shared memory per CTA.
+cudaError_t pt_cluster(uint32_t *spins, int32_t *e_cur, const uint8_t *cbits, int32_t L,
+                       int32_t W, int32_t k0, int32_t slots, int32_t round, uint32_t key0,
+                       uint32_t key1, unsigned long long *flipped, cudaStream_t stream);
+
 cudaError_t energy_csr(const int64_t *rowptr, const int32_t *col, const int32_t *wt, int32_t n,
                        const int8_t *spins, int32_t R, int64_t *scratch, int32_t blocks,
                        int64_t *energies, cudaStream_t stream,

@@ -871,8 +871,8 @@ isg_status anneal_impl(const isg_problem *p, int32_t R, const double *betas, int
 // torus-kernel launch of `per_round` sweeps per round at each word's own beta,
 // then the exchange kernel over the pairs of the round's parity.
 isg_status tempering_impl(const isg_problem *p, int32_t K, const double *betas, int32_t rounds,
-                          int32_t per_round, uint64_t seed, const isg_options *opts,
-                          cudaStream_t stream, isg_result **out) {
+                          int32_t per_round, int32_t icm_slots, uint64_t seed,
+                          const isg_options *opts, cudaStream_t stream, isg_result **out) {
   if (!out) return fail(ISG_EINVAL, "out must not be NULL");
   *out = nullptr;
   if (!p) return fail(ISG_EINVAL, "problem must not be NULL");
@@ -882,6 +882,9 @@ isg_status tempering_impl(const isg_problem *p, int32_t K, const double *betas, 
     return fail(ISG_EINVAL, "rounds and sweeps_per_round must be >= 1 (product < 2^31)");
   isg_status st = check_betas(betas, K);
   if (st != ISG_OK) return st;
+  if (icm_slots < 0 || icm_slots > K) return fail(ISG_EINVAL, "icm_slots must be in [0, K]");
+  if (icm_slots > 0 && 8 * (size_t)p->n > 227 * 1024 - 4096)
+    return fail(ISG_EINVAL, "cluster moves need 8 bytes of shared memory per site (n <= 28544)");
   isg_options o = {};
   if (opts) o = *opts;
   if (o.kernel != ISG_KERNEL_AUTO && o.kernel != ISG_KERNEL_TORUS_MSC)
@@ -945,7 +948,8 @@ isg_status tempering_impl(const isg_problem *p, int32_t K, const double *betas, 
     delete r;
     return st;
   }
-  const size_t o_acc = 0, o_x = 8 * (size_t)std::max(pairs, 1);
+  const size_t o_acc = 0, o_flip = 8 * (size_t)std::max(pairs, 1);
+  const size_t o_x = o_flip + 8 * (size_t)K;
   const size_t o_sgn = o_x + 4 * xtable.size();
   cudaError_t err = cudaMallocAsync(&r->pt_mem, o_sgn + sgn.size(), stream);
   if (err == cudaSuccess) err = cudaEventCreateWithFlags(&r->done, cudaEventDisableTiming);
@@ -956,7 +960,9 @@ isg_status tempering_impl(const isg_problem *p, int32_t K, const double *betas, 
   }
   char *pm = (char *)r->pt_mem;
   r->d_accepted = (unsigned long long *)(pm + o_acc);
+  r->d_flipped = (unsigned long long *)(pm + o_flip);
   r->pt_pairs = pairs;
+  r->pt_slots = K;
   r->pt_attempted.assign(std::max(pairs, 0), 0);
   for (int32_t q = 0; q < rounds; ++q)
     for (int32_t k = q % 2; k + 1 < K; k += 2) r->pt_attempted[k] += 32;
@@ -993,10 +999,13 @@ isg_status tempering_impl(const isg_problem *p, int32_t K, const double *betas, 
     l.threads = threads;
     err = torus_launch(s, l, stream);
     if (err == cudaSuccess)
+      err = pt_cluster(r->d_spins, r->d_e_cur, dp->cbits, p->L, p->W, K - icm_slots, icm_slots,
+                       q, s.key0, s.key1, r->d_flipped, stream);
+    if (err == cudaSuccess)
       err = pt_exchange(r->d_spins, r->d_e_cur, p->n, K, q % 2, q, s.key0, s.key1,
                         (const int8_t *)(pm + o_sgn), (const uint32_t *)(pm + o_x), (int32_t)xlen,
                         r->d_accepted, stream);
-    launches += 2;
+    launches += icm_slots > 0 ? 3 : 2;
   }
   const int sweep_launches = rounds;
   if (r->timed && err == cudaSuccess) err = cudaEventRecord(r->t1, stream);
@@ -1399,10 +1408,28 @@ isg_status isg_result_best_all(const isg_result *r, int8_t *best_spins) {
 
 isg_status isg_parallel_tempering(const isg_problem *p, int32_t temperatures,
                                   const double *betas, int32_t rounds, int32_t sweeps_per_round,
-                                  uint64_t seed, const isg_options *opts, void *cuda_stream,
-                                  isg_result **out) {
-  return tempering_impl(p, temperatures, betas, rounds, sweeps_per_round, seed, opts,
+                                  int32_t icm_slots, uint64_t seed, const isg_options *opts,
+                                  void *cuda_stream, isg_result **out) {
+  return tempering_impl(p, temperatures, betas, rounds, sweeps_per_round, icm_slots, seed, opts,
                         (cudaStream_t)cuda_stream, out);
+}
+
+isg_status isg_result_cluster_flips(const isg_result *r, int64_t *flipped, int32_t temperatures) {
+  if (!r || !flipped) return fail(ISG_EINVAL, "arguments must not be NULL");
+  if (temperatures != r->pt_slots || temperatures < 1)
+    return fail(ISG_EINVAL, "the result has %d temperature slots", r->pt_slots);
+  isg_status st = result_sync(r);
+  if (st != ISG_OK) return st;
+  std::vector<unsigned long long> f(temperatures);
+  int prev = 0;
+  cudaGetDevice(&prev);
+  cudaSetDevice(r->device);
+  cudaError_t err = cudaMemcpy(f.data(), r->d_flipped, 8 * (size_t)temperatures,
+                               cudaMemcpyDeviceToHost);
+  cudaSetDevice(prev);
+  if (err != cudaSuccess) return cuda_fail(err, "reading cluster-move sizes");
+  for (int32_t k = 0; k < temperatures; ++k) flipped[k] = (int64_t)f[k];
+  return ISG_OK;
 }
 
 isg_status isg_result_exchanges(const isg_result *r, int64_t *accepted, int64_t *attempted,

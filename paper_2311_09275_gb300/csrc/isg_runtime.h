@@ -83,7 +83,8 @@ struct isg_result {
   // parallel tempering: exchange tables and counters (one allocation), pairs K - 1
   void *pt_mem = nullptr;
   unsigned long long *d_accepted = nullptr;
-  int32_t pt_pairs = 0;
+  unsigned long long *d_flipped = nullptr;  // [K] cluster-move sizes per slot
+  int32_t pt_pairs = 0, pt_slots = 0;
   std::vector<int64_t> pt_attempted;
   // filled on first synchronisation
   std::mutex mu;

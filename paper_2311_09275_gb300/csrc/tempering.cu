@@ -55,7 +55,168 @@ __global__ void __launch_bounds__(256) pt_exchange_kernel(
   }
 }
 
+// Houdayer cluster moves on one slot word per CTA (slots k0 + blockIdx.x):
+// chains 2m and 2m+1 (lanes) form pair m.  D[i] holds, at bit 2m, whether
+// the pair differs at site i; C[i] grows, at the same bits, the connected
+// component of the drawn differing site among differing sites.  Both chains
+// then flip C, and the word's 32 energies are recomputed.
+template <int NP>
+__global__ void __launch_bounds__(1024) pt_cluster_kernel(uint32_t *spins, int32_t *e_cur,
+                                                          const uint8_t *cbits, int L, int W,
+                                                          int k0, int round, PhiloxKey key,
+                                                          unsigned long long *flipped) {
+  extern __shared__ __align__(16) uint32_t sm[];
+  const int n = L * W;
+  const int k = k0 + (int)blockIdx.x;
+  uint32_t *D = sm, *C = sm + n;
+  __shared__ int32_t wsum[32][16];
+  __shared__ int64_t pick[16];
+  __shared__ int changed;
+  uint32_t *word = spins + (size_t)k * n;
+  const int nt = (int)blockDim.x, tid = (int)threadIdx.x;
+  const int chunk = (n + nt - 1) / nt;
+  const int i0 = min(n, tid * chunk), i1 = min(n, i0 + chunk);
+  // 1. differing sites per pair, and this thread's count of them per pair
+  int32_t cnt[16];
+#pragma unroll
+  for (int m = 0; m < 16; ++m) cnt[m] = 0;
+  for (int i = i0; i < i1; ++i) {
+    const uint32_t w = word[i];
+    const uint32_t d = (w ^ (w >> 1)) & 0x55555555u;
+    D[i] = d;
+    C[i] = 0u;
+#pragma unroll
+    for (int m = 0; m < 16; ++m) cnt[m] += (d >> (2 * m)) & 1u;
+  }
+  // 2. exclusive prefix of the counts over threads (warp scan, then warp totals)
+  const int lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
+  int32_t pre[16];
+#pragma unroll
+  for (int m = 0; m < 16; ++m) {
+    int32_t x = cnt[m];
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int32_t y = __shfl_up_sync(0xFFFFFFFFu, x, o);
+      if (lane >= o) x += y;
+    }
+    pre[m] = x - cnt[m];
+    if (lane == 31) wsum[warp][m] = x;
+  }
+  __syncthreads();
+  if (tid < 16) {
+    int64_t tot = 0;
+    for (int w = 0; w < nw; ++w) {
+      const int32_t v = wsum[w][tid];
+      wsum[w][tid] = (int32_t)tot;  // exclusive offset of warp w
+      tot += v;
+    }
+    // 3. the drawn site of pair m: the (u mod D)-th differing site
+    if (tot > 0) {
+      const uint4 u = philox10(make_uint4((uint32_t)k, (uint32_t)round, (uint32_t)tid, 3u), key);
+      pick[tid] = (int64_t)((uint64_t)u.x % (uint64_t)tot);
+    } else {
+      pick[tid] = -1;
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int m = 0; m < 16; ++m) {
+    const int64_t p = pick[m];
+    const int64_t lo = (int64_t)wsum[warp][m] + pre[m];
+    if (p >= lo && p < lo + cnt[m]) {
+      int64_t seen = lo;
+      for (int i = i0; i < i1; ++i)
+        if ((D[i] >> (2 * m)) & 1u) {
+          if (seen == p) {
+            C[i] |= 1u << (2 * m);
+            break;
+          }
+          ++seen;
+        }
+    }
+  }
+  __syncthreads();
+  // 4. grow the clusters to their components (bits only ever get set, so the
+  //    in-place passes reach the same fixed point in any order)
+  for (;;) {
+    if (tid == 0) changed = 0;
+    __syncthreads();
+    int any = 0;
+    for (int i = i0; i < i1; ++i) {
+      const int r = i / W, c = i - r * W;
+      const int il = r * W + (c == 0 ? W - 1 : c - 1), ir = r * W + (c == W - 1 ? 0 : c + 1);
+      const int iu = (r == 0 ? L - 1 : r - 1) * W + c, id = (r == L - 1 ? 0 : r + 1) * W + c;
+      const uint32_t nb = C[il] | C[ir] | C[iu] | C[id];
+      const uint32_t cur = C[i];
+      const uint32_t nw2 = cur | (D[i] & nb);
+      if (nw2 != cur) {
+        C[i] = nw2;
+        any = 1;
+      }
+    }
+    if (any) changed = 1;
+    __syncthreads();
+    const int again = changed;
+    __syncthreads();
+    if (!again) break;
+  }
+  // 5. flip the clusters in both chains; recount the word's unsatisfied bonds
+  SlicedCounter<NP> cntu;
+  cntu.clear();
+  unsigned long long flips = 0;
+  for (int i = i0; i < i1; ++i) {
+    const uint32_t cl = C[i];
+    flips += __popc(cl);
+    if (cl) word[i] ^= cl | (cl << 1);
+  }
+  __syncthreads();  // global writes of this CTA visible to its own threads
+  for (int i = i0; i < i1; ++i) {
+    const int r = i / W, c = i - r * W;
+    const int ir = r * W + (c == W - 1 ? 0 : c + 1), id = (r == L - 1 ? 0 : r + 1) * W + c;
+    const uint32_t s0 = word[i];
+    const uint32_t cb = cbits[i];
+    const uint32_t a = ~(s0 ^ word[ir] ^ (0u - (cb & 1u)));
+    const uint32_t d = ~(s0 ^ word[id] ^ (0u - ((cb >> 1) & 1u)));
+    cntu.add2(a ^ d, a & d);
+  }
+  const int32_t tot = cntu.warp_lane_total();
+  __shared__ int32_t lane_tot[32];
+  if (tid < 32) lane_tot[tid] = 0;
+  __syncthreads();
+  atomicAdd(&lane_tot[lane], tot);
+  for (int o = 16; o > 0; o >>= 1) flips += __shfl_down_sync(0xFFFFFFFFu, flips, o);
+  if (lane == 0 && flips) atomicAdd(&flipped[k], flips);
+  __syncthreads();
+  if (tid < 32) e_cur[32 * k + tid] = 2 * lane_tot[tid] - 2 * n;  // E = 2 U - 2n (torus)
+}
+
 }  // namespace
+
+cudaError_t pt_cluster(uint32_t *spins, int32_t *e_cur, const uint8_t *cbits, int32_t L,
+                       int32_t W, int32_t k0, int32_t slots, int32_t round, uint32_t key0,
+                       uint32_t key1, unsigned long long *flipped, cudaStream_t stream) {
+  if (slots <= 0) return cudaSuccess;
+  const int threads = 1024;
+  const size_t smem = 8 * (size_t)L * W;
+  const int per_thread = (L * W + threads - 1) / threads;  // sites per thread, 2 bonds each
+  cudaError_t err;
+  if (2 * per_thread < (1 << 6)) {
+    err = cudaFuncSetAttribute(pt_cluster_kernel<6>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)smem);
+    if (err == cudaSuccess)
+      pt_cluster_kernel<6><<<slots, threads, smem, stream>>>(spins, e_cur, cbits, L, W, k0, round,
+                                                             PhiloxKey{key0, key1}, flipped);
+  } else {
+    err = cudaFuncSetAttribute(pt_cluster_kernel<10>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)smem);
+    if (err == cudaSuccess)
+      pt_cluster_kernel<10><<<slots, threads, smem, stream>>>(spins, e_cur, cbits, L, W, k0,
+                                                              round, PhiloxKey{key0, key1},
+                                                              flipped);
+  }
+  if (err != cudaSuccess) return err;
+  return cudaGetLastError();
+}
 
 cudaError_t pt_exchange(uint32_t *spins, int32_t *e_cur, int32_t n, int32_t K, int32_t parity,
                         int32_t round, uint32_t key0, uint32_t key1, const int8_t *sgn,

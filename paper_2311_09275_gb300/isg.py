@@ -80,8 +80,9 @@ _sig("isg_server_destroy", [_P])
 _sig("isg_server_get_stats", [_P, ctypes.POINTER(isg_server_stats)])
 _sig("isg_integer_peaks", [_P, ctypes.POINTER(_dbl), ctypes.POINTER(_dbl)])
 _sig("isg_acceptance_table", [_P, _i32, _i32, _P])
-_sig("isg_parallel_tempering", [_P, _i32, _P, _i32, _i32, _u64, ctypes.POINTER(isg_options), _P,
-                                ctypes.POINTER(_P)])
+_sig("isg_parallel_tempering", [_P, _i32, _P, _i32, _i32, _i32, _u64,
+                                ctypes.POINTER(isg_options), _P, ctypes.POINTER(_P)])
+_sig("isg_result_cluster_flips", [_P, _P, _i32])
 _sig("isg_result_exchanges", [_P, _P, _P, _i32])
 _sig("isg_last_error", [], ctypes.c_char_p)
 _sig("isg_version", [], ctypes.c_char_p)
@@ -316,14 +317,16 @@ def isg_energy_noalloc(n: int, rowptr_dev: int, col_dev: int, w_dev: int, spins_
 
 def isg_parallel_tempering(p, betas, rounds: int, sweeps_per_round: int, seed: int,
                            stream=None, cluster_ctas: int = 0, threads: int = 0,
-                           time_kernels: bool = False) -> "Result":
-    """Parallel tempering over len(betas) slots x 32 chains (replica r = 32 k + c)."""
+                           time_kernels: bool = False, icm_slots: int = 0) -> "Result":
+    """Parallel tempering over len(betas) slots x 32 chains (replica r = 32 k + c),
+    with Houdayer cluster moves on the last icm_slots slots."""
     b = _arr(betas, np.float64)
     opts = isg_options(0, cluster_ctas, threads, 1 if time_kernels else 0, 0)
     out = _P()
     _check(_lib.isg_parallel_tempering(_h(p), int(b.shape[0]), _ptr(b), int(rounds),
-                                       int(sweeps_per_round), int(seed) & 0xFFFFFFFFFFFFFFFF,
-                                       ctypes.byref(opts), _stream(stream), ctypes.byref(out)))
+                                       int(sweeps_per_round), int(icm_slots),
+                                       int(seed) & 0xFFFFFFFFFFFFFFFF, ctypes.byref(opts),
+                                       _stream(stream), ctypes.byref(out)))
     res = Result(out.value)
     res.pairs = int(b.shape[0]) - 1
     return res
@@ -335,6 +338,13 @@ def isg_result_exchanges(r, pairs: int):
     att = np.zeros(max(pairs, 1), dtype=np.int64)
     _check(_lib.isg_result_exchanges(_h(r), _ptr(acc), _ptr(att), int(pairs)))
     return acc[:pairs], att[:pairs]
+
+
+def isg_result_cluster_flips(r, temperatures: int) -> np.ndarray:
+    """Sites flipped by cluster moves per slot (summed over pairs and rounds)."""
+    f = np.zeros(temperatures, dtype=np.int64)
+    _check(_lib.isg_result_cluster_flips(_h(r), _ptr(f), int(temperatures)))
+    return f
 
 
 def isg_acceptance_table(betas, kmax: int) -> np.ndarray:

@@ -72,3 +72,29 @@ def test_tempering_rejects_bad_input(isg):
     res = isg.isg_anneal(t, 8, np.full(3, 0.5), 1)
     with pytest.raises(isg.IsgError):
         isg.isg_result_exchanges(res, 3)                    # no exchange pairs there
+
+
+@pytest.mark.parametrize("L,W,betas,rounds,per_round,icm", [
+    (12, 10, [0.3, 0.8, 1.5, 2.5], 6, 3, 2),
+    (20, 16, [0.5, 1.0, 2.0], 5, 2, 3),
+    (8, 6, [1.2], 9, 1, 1),
+    (40, 30, [0.4, 0.9, 1.6, 2.4, 3.0], 4, 4, 5),
+])
+def test_tempering_with_cluster_moves_bit_exact(isg, L, W, betas, rounds, per_round, icm):
+    t = I.torus(L, W, 60 + L)
+    c = oracle.csr_of(t)
+    orc = oracle.parallel_tempering(c, betas, rounds, per_round, 29, icm_slots=icm)
+    res = isg.isg_parallel_tempering(isg.problem_of(t), betas, rounds, per_round, 29,
+                                     icm_slots=icm)
+    assert_same_pt(res, orc, len(betas) - 1)
+    assert np.array_equal(isg.isg_result_cluster_flips(res, len(betas)), orc.flipped)
+    assert orc.flipped[len(betas) - icm:].sum() > 0
+
+
+def test_cluster_moves_full_size(isg):
+    t = I.torus(80, 100, 1)
+    betas = I.geometric_betas(0.5, 3.0, 6)
+    orc = oracle.parallel_tempering(oracle.csr_of(t), betas, 3, 4, 8, icm_slots=3)
+    res = isg.isg_parallel_tempering(isg.problem_of(t), betas, 3, 4, 8, icm_slots=3)
+    assert_same_pt(res, orc, 5)
+    assert np.array_equal(isg.isg_result_cluster_flips(res, 6), orc.flipped)
