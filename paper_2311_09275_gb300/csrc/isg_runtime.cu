@@ -392,6 +392,9 @@ void result_free(isg_result *r) {
   if (r->done) cudaEventSynchronize(r->done);
   if (r->base) cudaFreeAsync(r->base, r->stream);
   if (r->pt_mem) cudaFreeAsync(r->pt_mem, r->stream);
+  if (r->pt_exec) cudaGraphExecDestroy(r->pt_exec);
+  if (r->pt_graph) cudaGraphDestroy(r->pt_graph);
+  if (r->pt_capture) cudaStreamDestroy(r->pt_capture);
   if (r->done) cudaEventDestroy(r->done);
   if (r->t0) cudaEventDestroy(r->t0);
   if (r->t1) cudaEventDestroy(r->t1);
@@ -989,24 +992,41 @@ isg_status tempering_impl(const isg_problem *p, int32_t K, const double *betas, 
   s.table_ws = 2;  // one row of thresholds per word, the same every sweep
   s.table_ts = 0;
   int launches = 0;
-  if (r->timed) err = cudaEventRecord(r->t0, stream);
-  for (int32_t q = 0; q < rounds && err == cudaSuccess; ++q) {
-    TorusLaunch l = {};
-    l.t_begin = q * per_round;
-    l.t_end = (q + 1) * per_round;
-    l.resume = q > 0;
-    l.cluster = cluster;
-    l.threads = threads;
-    err = torus_launch(s, l, stream);
-    if (err == cudaSuccess)
-      err = pt_cluster(r->d_spins, r->d_e_cur, dp->cbits, p->L, p->W, K - icm_slots, icm_slots,
-                       q, s.key0, s.key1, r->d_flipped, stream);
-    if (err == cudaSuccess)
-      err = pt_exchange(r->d_spins, r->d_e_cur, p->n, K, q % 2, q, s.key0, s.key1,
-                        (const int8_t *)(pm + o_sgn), (const uint32_t *)(pm + o_x), (int32_t)xlen,
-                        r->d_accepted, stream);
-    launches += icm_slots > 0 ? 3 : 2;
+  // the rounds are captured once on a private stream and launched as one CUDA
+  // graph on the caller's stream (a few microseconds per round instead of a
+  // host launch sequence)
+  auto enqueue_rounds = [&](cudaStream_t st) {
+    cudaError_t e = cudaSuccess;
+    for (int32_t q = 0; q < rounds && e == cudaSuccess; ++q) {
+      TorusLaunch l = {};
+      l.t_begin = q * per_round;
+      l.t_end = (q + 1) * per_round;
+      l.resume = q > 0;
+      l.cluster = cluster;
+      l.threads = threads;
+      e = torus_launch(s, l, st);
+      if (e == cudaSuccess)
+        e = pt_cluster(r->d_spins, r->d_e_cur, dp->cbits, p->L, p->W, K - icm_slots, icm_slots,
+                       q, s.key0, s.key1, r->d_flipped, st);
+      if (e == cudaSuccess)
+        e = pt_exchange(r->d_spins, r->d_e_cur, p->n, K, q % 2, q, s.key0, s.key1,
+                        (const int8_t *)(pm + o_sgn), (const uint32_t *)(pm + o_x),
+                        (int32_t)xlen, r->d_accepted, st);
+    }
+    return e;
+  };
+  if (err == cudaSuccess) err = cudaStreamCreateWithFlags(&r->pt_capture, cudaStreamNonBlocking);
+  if (err == cudaSuccess)
+    err = cudaStreamBeginCapture(r->pt_capture, cudaStreamCaptureModeThreadLocal);
+  if (err == cudaSuccess) {
+    const cudaError_t e1 = enqueue_rounds(r->pt_capture);
+    err = cudaStreamEndCapture(r->pt_capture, &r->pt_graph);
+    if (err == cudaSuccess) err = e1;
   }
+  if (err == cudaSuccess) err = cudaGraphInstantiate(&r->pt_exec, r->pt_graph, 0);
+  if (r->timed && err == cudaSuccess) err = cudaEventRecord(r->t0, stream);
+  if (err == cudaSuccess) err = cudaGraphLaunch(r->pt_exec, stream);
+  launches += rounds * (icm_slots > 0 ? 3 : 2);
   const int sweep_launches = rounds;
   if (r->timed && err == cudaSuccess) err = cudaEventRecord(r->t1, stream);
   if (err == cudaSuccess) err = reduce_hits(r->d_hit, r->units, r->d_stop, stream);

@@ -85,6 +85,9 @@ struct isg_result {
   unsigned long long *d_accepted = nullptr;
   unsigned long long *d_flipped = nullptr;  // [K] cluster-move sizes per slot
   int32_t pt_pairs = 0, pt_slots = 0;
+  cudaGraph_t pt_graph = nullptr;          // the rounds, captured once and launched as a graph
+  cudaGraphExec_t pt_exec = nullptr;
+  cudaStream_t pt_capture = nullptr;
   std::vector<int64_t> pt_attempted;
   // filled on first synchronisation
   std::mutex mu;

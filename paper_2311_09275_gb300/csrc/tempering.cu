@@ -55,6 +55,59 @@ __global__ void __launch_bounds__(256) pt_exchange_kernel(
   }
 }
 
+// One warp spreads cluster bits along a ring of `len` sites (base + x*stride,
+// x = 0..len-1, closed by a wrap edge) through runs of differing sites, in
+// both directions.  Each lane owns a segment; a segment maps an incoming
+// carry k to G | (P & k) (G: its carry out from k = 0, P: AND of its D), and
+// these maps compose associatively, so a warp scan of them gives every lane
+// its incoming carry; the wrap carry is the whole ring's G (the least fixed
+// point of k = G | (P & k)).  Returns whether a bit was set.
+__device__ bool ring_spread(uint32_t *C, const uint32_t *D, int base, int len, int stride) {
+  const int lane = (int)(threadIdx.x & 31u);
+  const int seg = (len + 31) / 32;
+  const int x0 = min(len, lane * seg), x1 = min(len, x0 + seg);
+  bool changed = false;
+  for (int dir = 0; dir < 2; ++dir) {
+    uint32_t g = 0u, pm = 0xFFFFFFFFu;
+    for (int x = x0; x < x1; ++x) {
+      const int i = base + (dir == 0 ? x : len - 1 - x) * stride;
+      const uint32_t d = D[i];
+      g = C[i] | (d & g);
+      pm &= d;
+    }
+    // inclusive scan of (g, pm) in lane order: later (g, pm) after earlier (g', pm')
+    uint32_t G = g, Pm = pm;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t Ge = __shfl_up_sync(0xFFFFFFFFu, G, o);
+      const uint32_t Pe = __shfl_up_sync(0xFFFFFFFFu, Pm, o);
+      if (lane >= o) {
+        G = G | (Pm & Ge);
+        Pm = Pm & Pe;
+      }
+    }
+    const uint32_t g_all = __shfl_sync(0xFFFFFFFFu, G, 31);
+    uint32_t ge = __shfl_up_sync(0xFFFFFFFFu, G, 1), pe = __shfl_up_sync(0xFFFFFFFFu, Pm, 1);
+    if (lane == 0) {
+      ge = 0u;
+      pe = 0xFFFFFFFFu;
+    }
+    uint32_t carry = ge | (pe & g_all);
+    for (int x = x0; x < x1; ++x) {
+      const int i = base + (dir == 0 ? x : len - 1 - x) * stride;
+      const uint32_t cur = C[i];
+      const uint32_t v = cur | (D[i] & carry);
+      if (v != cur) {
+        C[i] = v;
+        changed = true;
+      }
+      carry = v;
+    }
+    __syncwarp();
+  }
+  return changed;
+}
+
 // Houdayer cluster moves on one slot word per CTA (slots k0 + blockIdx.x):
 // chains 2m and 2m+1 (lanes) form pair m.  D[i] holds, at bit 2m, whether
 // the pair differs at site i; C[i] grows, at the same bits, the connected
@@ -136,29 +189,23 @@ __global__ void __launch_bounds__(1024) pt_cluster_kernel(uint32_t *spins, int32
     }
   }
   __syncthreads();
-  // 4. grow the clusters to their components (bits only ever get set, so the
-  //    in-place passes reach the same fixed point in any order)
-  for (;;) {
+  // 4. grow the clusters to their components (bits only ever get set, so any
+  //    order of passes reaches the same fixed point).  Passes alternate
+  //    between rows and columns, one warp per ring, and spread the bits along
+  //    whole runs of differing sites at once; the number of passes follows the
+  //    number of turns of the clusters' paths, not their length.
+  for (int pass = 0, quiet = 0; quiet < 2; ++pass) {
     if (tid == 0) changed = 0;
     __syncthreads();
-    int any = 0;
-    for (int i = i0; i < i1; ++i) {
-      const int r = i / W, c = i - r * W;
-      const int il = r * W + (c == 0 ? W - 1 : c - 1), ir = r * W + (c == W - 1 ? 0 : c + 1);
-      const int iu = (r == 0 ? L - 1 : r - 1) * W + c, id = (r == L - 1 ? 0 : r + 1) * W + c;
-      const uint32_t nb = C[il] | C[ir] | C[iu] | C[id];
-      const uint32_t cur = C[i];
-      const uint32_t nw2 = cur | (D[i] & nb);
-      if (nw2 != cur) {
-        C[i] = nw2;
-        any = 1;
-      }
-    }
+    const bool rows = (pass & 1) == 0;
+    const int rings = rows ? L : W;
+    bool any = false;
+    for (int g = warp; g < rings; g += nw)
+      any |= rows ? ring_spread(C, D, g * W, W, 1) : ring_spread(C, D, g, L, W);
     if (any) changed = 1;
     __syncthreads();
-    const int again = changed;
+    quiet = changed ? 0 : quiet + 1;  // stop after a row pass and a column pass change nothing
     __syncthreads();
-    if (!again) break;
   }
   // 5. flip the clusters in both chains; recount the word's unsatisfied bonds
   SlicedCounter<NP> cntu;
