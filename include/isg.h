@@ -172,7 +172,10 @@ isg_status isg_anneal_batch(const isg_problem *const *probs, int32_t count, int3
                             const int64_t *targets, void *cuda_stream, isg_result **outs);
 
 /* Parallel tempering (Sec. II.C: replicas at different temperatures that
- * exchange configurations) on a torus instance.  temperatures = K slots with
+ * exchange configurations) on a torus instance, or on a graph with weights
+ * +-1, degree <= 63 and no fields (the multi-spin graph kernel; vertex order
+ * inside the state is the library's, results come back in the caller's
+ * vertex order as everywhere else).  temperatures = K slots with
  * inverse temperatures betas[K] (finite, >= 0, any order), 32 independent
  * chains per slot: R = 32 K replicas, replica r = 32 k + c is chain c at slot
  * k.  Each of `rounds` rounds runs sweeps_per_round sweeps of every replica at
@@ -194,8 +197,9 @@ isg_status isg_anneal_batch(const isg_problem *const *probs, int32_t count, int3
  * like isg_anneal's (R = 32 K, S = rounds * sweeps_per_round); exchange counts
  * by isg_result_exchanges, cluster sizes by isg_result_cluster_flips.  opts
  * may be NULL (kernel AUTO or TORUS_MSC; cluster/threads as isg_anneal).
- * EINVAL: not a torus, K outside [1, 4096], rounds or sweeps_per_round < 1,
- * a bad beta, icm_slots outside [0, K], or icm_slots > 0 with n > 28,544. */
+ * EINVAL: neither a torus nor such a graph, K outside [1, 4096], rounds or
+ * sweeps_per_round < 1, a bad beta, icm_slots outside [0, K], icm_slots > 0 on
+ * a graph (cluster moves: tori only) or with n > 28,544. */
 isg_status isg_parallel_tempering(const isg_problem *p, int32_t temperatures,
                                   const double *betas, int32_t rounds, int32_t sweeps_per_round,
                                   int32_t icm_slots, uint64_t seed, const isg_options *opts,

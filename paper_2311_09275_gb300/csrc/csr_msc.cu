@@ -174,6 +174,7 @@ __device__ void gm_word(const GraphMscSolve &s, const GraphMscLaunch &L, int wor
   uint32_t *trow = reinterpret_cast<uint32_t *>(smem + lay.trow);
   int32_t *part = reinterpret_cast<int32_t *>(smem + lay.part);
   int32_t *lane_acc = reinterpret_cast<int32_t *>(smem + lay.lane_acc);
+  const uint32_t *wtab = s.table + (size_t)word * s.table_ws;  // this word's threshold rows
   const PhiloxKey key{s.key0, s.key1};
   const uint32_t uword = (uint32_t)word;
   const int rem = s.replicas - 32 * word;
@@ -227,7 +228,7 @@ __device__ void gm_word(const GraphMscSolve &s, const GraphMscLaunch &L, int wor
   // threshold rows: two buffers, the next sweep's row prefetched a sweep ahead
   if (t_begin < t_end)
     for (int x = threadIdx.x; x < s.kmax1; x += blockDim.x)
-      trow[(t_begin & 1) * s.kmax1 + x] = s.table[(size_t)t_begin * s.kmax1 + x];
+      trow[(t_begin & 1) * s.kmax1 + x] = wtab[(size_t)t_begin * s.table_ts + x];
   // peers write into this CTA's copy of the word only after every CTA has loaded it
   sync_group(K);
 
@@ -269,7 +270,7 @@ __device__ void gm_word(const GraphMscSolve &s, const GraphMscLaunch &L, int wor
     const uint32_t *row = trow + (t & 1) * s.kmax1;
     // next sweep's thresholds (kmax1 <= 64 <= 2 x threads)
     const bool more = t + 1 < t_end;
-    const uint32_t *gnext = s.table + (size_t)(t + 1) * s.kmax1;
+    const uint32_t *gnext = wtab + (size_t)(t + 1) * s.table_ts;
     const uint32_t p0 = (more && x0 < s.kmax1) ? gnext[x0] : 0u;
     const uint32_t p1 = (more && x1 < s.kmax1) ? gnext[x1] : 0u;
     BlockPrefix bp[8];

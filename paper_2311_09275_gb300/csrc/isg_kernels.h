@@ -150,7 +150,9 @@ struct GraphMscSolve {
   const int32_t *rowptr;       // [n + 1]
   const int32_t *col;          // relabelled neighbour ids, bit 31 set for weight -1
   const int32_t *orig;         // [n]
-  const uint32_t *table;       // [sweeps][kmax1]: thresholds by half energy change k
+  const uint32_t *table;       // thresholds by half energy change k of word w, sweep t at
+                               // table[w * table_ws + t * table_ts + k]
+  int32_t table_ws, table_ts;  // annealing: 0, kmax1; tempering: kmax1, 0
   int32_t kmax1;               // kmax + 1 (<= 64)
   uint32_t key0, key1;
   RoundKeys rk;

@@ -600,6 +600,8 @@ GraphMscSolve make_gm_solve(const isg_problem *p, const DeviceProblem *dp, const
   s.orig = dp->orig;
   s.table = r->d_table;
   s.kmax1 = p->kmax + 1;
+  s.table_ws = 0;
+  s.table_ts = s.kmax1;
   s.key0 = (uint32_t)(seed & 0xFFFFFFFFu);
   s.key1 = (uint32_t)(seed >> 32);
   s.rk = round_keys(s.key0, s.key1);
@@ -879,19 +881,26 @@ isg_status tempering_impl(const isg_problem *p, int32_t K, const double *betas, 
   if (!out) return fail(ISG_EINVAL, "out must not be NULL");
   *out = nullptr;
   if (!p) return fail(ISG_EINVAL, "problem must not be NULL");
-  if (!p->torus) return fail(ISG_EINVAL, "parallel tempering runs on torus instances");
+  // tori run on the multi-spin torus kernel, +-1 graphs on the multi-spin graph kernel
+  const bool gm = !p->torus;
+  if (gm && !graph_msc_ok(p))
+    return fail(ISG_EINVAL,
+                "parallel tempering needs a torus, or a graph with weights +-1, degree <= 63 "
+                "and no fields");
   if (K < 1 || K > 4096) return fail(ISG_EINVAL, "temperatures must be in [1, 4096]");
   if (rounds < 1 || per_round < 1 || (int64_t)rounds * per_round > INT32_MAX)
     return fail(ISG_EINVAL, "rounds and sweeps_per_round must be >= 1 (product < 2^31)");
   isg_status st = check_betas(betas, K);
   if (st != ISG_OK) return st;
   if (icm_slots < 0 || icm_slots > K) return fail(ISG_EINVAL, "icm_slots must be in [0, K]");
+  if (icm_slots > 0 && gm) return fail(ISG_EINVAL, "cluster moves run on torus instances");
   if (icm_slots > 0 && 8 * (size_t)p->n > 227 * 1024 - 4096)
     return fail(ISG_EINVAL, "cluster moves need 8 bytes of shared memory per site (n <= 28544)");
   isg_options o = {};
   if (opts) o = *opts;
-  if (o.kernel != ISG_KERNEL_AUTO && o.kernel != ISG_KERNEL_TORUS_MSC)
-    return fail(ISG_EINVAL, "parallel tempering uses the multi-spin torus kernel");
+  const int mkernel = gm ? ISG_KERNEL_GRAPH_MSC : ISG_KERNEL_TORUS_MSC;
+  if (o.kernel != ISG_KERNEL_AUTO && o.kernel != mkernel)
+    return fail(ISG_EINVAL, "parallel tempering uses the multi-spin kernels");
   if (o.cluster_ctas < 0 || o.cluster_ctas > 16)
     return fail(ISG_EINVAL, "cluster_ctas must be in [0, 16]");
   if (o.threads != 0 && (o.threads < 32 || o.threads > 1024 || o.threads % 32))
@@ -900,32 +909,48 @@ isg_status tempering_impl(const isg_problem *p, int32_t K, const double *betas, 
   int cluster = o.cluster_ctas, threads = o.threads;
   int t_kernel = 0, t_cluster = 0, t_threads = 0, t_qpc = 0;
   if (cluster == 0 && threads == 0 && shape_lookup(p, R, t_kernel, t_cluster, t_threads, t_qpc) &&
-      t_kernel == ISG_KERNEL_TORUS_MSC) {
+      t_kernel == mkernel) {
     cluster = t_cluster;
     threads = t_threads;
   }
-  torus_shape(p->L, p->W, K, cluster, threads);
-  if (cluster > p->L) cluster = p->L;
-  if (torus_smem_bytes(p->L, p->W, cluster) > 227 * 1024)
-    return fail(ISG_EINVAL, "torus %dx%d needs more shared memory than a CTA has", p->L, p->W);
+  int own_n = 0, own_nnz = 0, planes = 0;
+  if (!gm) {
+    torus_shape(p->L, p->W, K, cluster, threads);
+    if (cluster > p->L) cluster = p->L;
+    if (torus_smem_bytes(p->L, p->W, cluster) > 227 * 1024)
+      return fail(ISG_EINVAL, "torus %dx%d needs more shared memory than a CTA has", p->L, p->W);
+  } else {
+    gm_shape(p, K, cluster, threads);
+    if (gm_bytes(p, cluster, false) > 227 * 1024)
+      return fail(ISG_EINVAL, "instance with n = %d needs more shared memory than a CTA has",
+                  p->n);
+    planes = gm_planes_for(p, cluster, threads);
+    if (planes < 0)
+      return fail(ISG_EINVAL, "too many vertices per thread for the graph kernel's counters");
+    if (gm_bytes(p, cluster, true) <= 227 * 1024) csr_own_sizes(p, cluster, own_n, own_nnz);
+  }
 
   const DeviceProblem *dp = nullptr;
   size_t uploaded = 0;
-  st = problem_device(p, kNeedTorus, &dp, &uploaded);
+  st = problem_device(p, gm ? kNeedCsr : kNeedTorus, &dp, &uploaded);
   if (st != ISG_OK) return st;
   isg_result *r = new_result(p, R, S, true, false, stream);
   r->h2d_bytes = (int64_t)uploaded;
-  r->relabelled = false;
-  r->kernel = ISG_KERNEL_TORUS_MSC;
-  std::vector<uint32_t> table;  // [K][2]: slot k's thresholds for energy changes 4 and 8
-  build_table(betas, K, {2, 4}, table);
+  r->relabelled = gm;
+  r->kernel = mkernel;
+  // [K][levels]: slot k's thresholds (torus: energy changes 4 and 8; graphs:
+  // every half energy change k = 0..kmax)
+  std::vector<int32_t> levels;
+  table_levels(p, !gm, levels);
+  std::vector<uint32_t> table;
+  build_table(betas, K, levels, table);
   r->table_words = table.size();
 
   // exchange thresholds: pair k, |E_k - E_{k+1}| = d in the direction that
   // makes a = (beta_k - beta_{k+1}) (E_k - E_{k+1}) negative; the table ends
-  // where every pair's threshold has reached 0 (|E| <= 2n on a torus)
+  // where every pair's threshold has reached 0 (|E| <= sum |w|)
   const int32_t pairs = K - 1;
-  const int64_t dmax = 4 * (int64_t)p->n;
+  const int64_t dmax = gm ? 2 * (int64_t)p->m : 4 * (int64_t)p->n;
   std::vector<int8_t> sgn(std::max(pairs, 1), 0);
   int64_t xlen = 1;
   for (int32_t k = 0; k < pairs; ++k) {
@@ -988,9 +1013,19 @@ isg_status tempering_impl(const isg_problem *p, int32_t K, const double *betas, 
   r->cluster = cluster;
   r->threads = threads;
 
-  TorusSolve s = make_torus_solve(p, dp, r, seed, false, 0);
-  s.table_ws = 2;  // one row of thresholds per word, the same every sweep
-  s.table_ts = 0;
+  // one row of thresholds per word, the same every sweep
+  TorusSolve s = {};
+  GraphMscSolve gs = {};
+  if (!gm) {
+    s = make_torus_solve(p, dp, r, seed, false, 0);
+    s.table_ws = 2;
+    s.table_ts = 0;
+  } else {
+    gs = make_gm_solve(p, dp, r, seed, false, 0);
+    gs.table_ws = gs.kmax1;
+    gs.table_ts = 0;
+  }
+  const uint32_t key0 = (uint32_t)(seed & 0xFFFFFFFFu), key1 = (uint32_t)(seed >> 32);
   int launches = 0;
   // the rounds are captured once on a private stream and launched as one CUDA
   // graph on the caller's stream (a few microseconds per round instead of a
@@ -998,18 +1033,31 @@ isg_status tempering_impl(const isg_problem *p, int32_t K, const double *betas, 
   auto enqueue_rounds = [&](cudaStream_t st) {
     cudaError_t e = cudaSuccess;
     for (int32_t q = 0; q < rounds && e == cudaSuccess; ++q) {
-      TorusLaunch l = {};
-      l.t_begin = q * per_round;
-      l.t_end = (q + 1) * per_round;
-      l.resume = q > 0;
-      l.cluster = cluster;
-      l.threads = threads;
-      e = torus_launch(s, l, st);
-      if (e == cudaSuccess)
+      if (!gm) {
+        TorusLaunch l = {};
+        l.t_begin = q * per_round;
+        l.t_end = (q + 1) * per_round;
+        l.resume = q > 0;
+        l.cluster = cluster;
+        l.threads = threads;
+        e = torus_launch(s, l, st);
+      } else {
+        GraphMscLaunch l = {};
+        l.t_begin = q * per_round;
+        l.t_end = (q + 1) * per_round;
+        l.resume = q > 0;
+        l.cluster = cluster;
+        l.threads = threads;
+        l.own_n = own_n;
+        l.own_nnz = own_nnz;
+        l.planes = planes;
+        e = gm_launch(gs, l, st);
+      }
+      if (e == cudaSuccess && icm_slots > 0)
         e = pt_cluster(r->d_spins, r->d_e_cur, dp->cbits, p->L, p->W, K - icm_slots, icm_slots,
-                       q, s.key0, s.key1, r->d_flipped, st);
+                       q, key0, key1, r->d_flipped, st);
       if (e == cudaSuccess)
-        e = pt_exchange(r->d_spins, r->d_e_cur, p->n, K, q % 2, q, s.key0, s.key1,
+        e = pt_exchange(r->d_spins, r->d_e_cur, p->n, K, q % 2, q, key0, key1,
                         (const int8_t *)(pm + o_sgn), (const uint32_t *)(pm + o_x),
                         (int32_t)xlen, r->d_accepted, st);
     }
@@ -1030,8 +1078,12 @@ isg_status tempering_impl(const isg_problem *p, int32_t K, const double *betas, 
   const int sweep_launches = rounds;
   if (r->timed && err == cudaSuccess) err = cudaEventRecord(r->t1, stream);
   if (err == cudaSuccess) err = reduce_hits(r->d_hit, r->units, r->d_stop, stream);
-  if (err == cudaSuccess) err = unpack_msc(r->d_spins, p->n, R, r->d_out, stream);
-  if (err == cudaSuccess) err = unpack_msc(r->d_best, p->n, R, r->d_out_best, stream);
+  if (err == cudaSuccess)
+    err = gm ? unpack_msc_relabel(r->d_spins, p->n, R, dp->orig, r->d_out, stream)
+             : unpack_msc(r->d_spins, p->n, R, r->d_out, stream);
+  if (err == cudaSuccess)
+    err = gm ? unpack_msc_relabel(r->d_best, p->n, R, dp->orig, r->d_out_best, stream)
+             : unpack_msc(r->d_best, p->n, R, r->d_out_best, stream);
   launches += 3;
   if (err == cudaSuccess) err = cudaEventRecord(r->done, stream);
   if (err != cudaSuccess) {

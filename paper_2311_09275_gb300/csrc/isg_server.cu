@@ -328,6 +328,8 @@ void fill_gm_unit(GraphMscItem &it, const Slot *sl, int32_t word, int32_t t_begi
   s.orig = sl->dp->orig;
   s.table = r->d_table;
   s.kmax1 = p->kmax + 1;
+  s.table_ws = 0;
+  s.table_ts = s.kmax1;
   s.key0 = (uint32_t)(sl->rq.seed & 0xFFFFFFFFu);
   s.key1 = (uint32_t)(sl->rq.seed >> 32);
   s.rk = round_keys(s.key0, s.key1);

@@ -59,9 +59,13 @@ def test_tempering_full_size_ladder(isg):
 
 
 def test_tempering_rejects_bad_input(isg):
+    gw = I.random_graph(50, 60, 1)
+    gw = I.Graph(gw.n, gw.u, gw.v, np.full(gw.m, 2, np.int32))
+    with pytest.raises(isg.IsgError):
+        isg.isg_parallel_tempering(isg.problem_of(gw), [0.5, 1.0], 2, 2, 1)  # weights not +-1
     g = isg.problem_of(I.random_graph(50, 60, 1))
     with pytest.raises(isg.IsgError):
-        isg.isg_parallel_tempering(g, [0.5, 1.0], 2, 2, 1)   # graphs: not in this version
+        isg.isg_parallel_tempering(g, [0.5, 1.0], 2, 2, 1, icm_slots=1)  # cluster moves: tori
     t = isg.problem_of(I.torus(8, 8, 1))
     with pytest.raises(isg.IsgError):
         isg.isg_parallel_tempering(t, [], 2, 2, 1)
@@ -98,3 +102,23 @@ def test_cluster_moves_full_size(isg):
     res = isg.isg_parallel_tempering(isg.problem_of(t), betas, 3, 4, 8, icm_slots=3)
     assert_same_pt(res, orc, 5)
     assert np.array_equal(isg.isg_result_cluster_flips(res, 6), orc.flipped)
+
+
+def _pm1(n, m, seed):
+    g = I.random_graph(n, m, seed)
+    w = np.where(I.draws(seed, 7, np.arange(g.m)) >> np.uint64(63), 1, -1).astype(np.int32)
+    return I.Graph(g.n, g.u, g.v, w)
+
+
+@pytest.mark.parametrize("make,betas,rounds,per_round,cluster,threads", [
+    (lambda: I.random_graph(500, 700, 3), [0.2, 0.6, 1.2, 2.0], 6, 3, 0, 0),
+    (lambda: _pm1(400, 1000, 4), [0.3, 0.5, 0.9], 5, 2, 3, 128),
+    (lambda: I.random_graph(10000, 9999, 1), I.geometric_betas(0.2, 3.0, 6), 3, 4, 0, 0),
+])
+def test_tempering_on_graphs_bit_exact(isg, make, betas, rounds, per_round, cluster, threads):
+    g = make()
+    orc = oracle.parallel_tempering(oracle.csr_of(g), betas, rounds, per_round, 31)
+    res = isg.isg_parallel_tempering(isg.problem_of(g), betas, rounds, per_round, 31,
+                                     cluster_ctas=cluster, threads=threads)
+    assert res.stats()["kernel"] == 4
+    assert_same_pt(res, orc, len(betas) - 1)
