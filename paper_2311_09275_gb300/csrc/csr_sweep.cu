@@ -293,7 +293,7 @@ __device__ void csr_solve(const CsrSolve &s, const CsrLaunch &L, int quad0, int 
 #pragma unroll
             for (int l = 0; l < 4; ++l) vals[q][l] += wv * lane8(sv, l) * lane8(su, l);
           }
-          if (s.field) {
+          if (MODE == 2 && s.field) {
             const int32_t hv = s.field[v];
 #pragma unroll
             for (int l = 0; l < 4; ++l) vals[q][l] += hv * lane8(sv, l);
@@ -356,7 +356,9 @@ __device__ void csr_solve(const CsrSolve &s, const CsrLaunch &L, int quad0, int 
           blend_best<Q>(s.best, spin, n, v, quad0, bm);
         }
         int32_t kk[Q][4];
-        fields<Q, MODE>(spin, n, v, p0, p1, adj, s.field ? __ldg(&s.field[v]) : 0, kk);
+        // local fields ride only with general weights (field instances run in mode 2)
+        fields<Q, MODE>(spin, n, v, p0, p1, adj,
+                        (MODE == 2 && s.field) ? __ldg(&s.field[v]) : 0, kk);
 #pragma unroll
         for (int q = 0; q < Q; ++q) {
           // lanes with kk > 0 are uphill; the rest are always taken

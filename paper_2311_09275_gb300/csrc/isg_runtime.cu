@@ -147,7 +147,9 @@ isg_status finish_problem(isg_problem *p) {
     all_pos &= (w == 1);
     all_unit &= (w == 1 || w == -1);
   }
-  p->mode = max_deg > 255 ? 2 : (all_pos ? 0 : (all_unit ? 1 : 2));
+  // instances with local fields take the general path (the field enters the
+  // per-lane sums, which the packed counts of modes 0 and 1 do not carry)
+  p->mode = (max_deg > 255 || !p->field.empty()) ? 2 : (all_pos ? 0 : (all_unit ? 1 : 2));
   p->dmax = (int32_t)max_deg;
   if (p->mode == 1)
     for (size_t o = 0; o < p->col_r.size(); ++o)
