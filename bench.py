@@ -372,6 +372,7 @@ def run_gpu(args):
 
     # ---- roofline of the sweep kernel (integer issue)
     pipes = isg.isg_integer_peaks(stream)
+    philox = isg.isg_philox_rates(stream)
     props = torch.cuda.get_device_properties(device)
     peaks, _ = load_peaks()
     nominal_lop3 = (props.multi_processor_count * SMSP_PER_SM * ALU_LANES_PER_SMSP *
@@ -414,7 +415,13 @@ def run_gpu(args):
                                     f"{pipes['lop3_per_s'] / 1e12:.2f}T/s, mad.wide "
                                     f"{pipes['mad_wide_per_s'] / 1e12:.2f}T/s "
                                     f"({props.multi_processor_count} SMs)",
-                     "nominal_lop3_peak": nominal_lop3 / 1e12},
+                     "nominal_lop3_peak": nominal_lop3 / 1e12,
+                     # the sweeps' own Philox code alone (and with the threshold masks):
+                     # one uniform per attempt, so an upper bound on the attempt rate
+                     "random_number_ceiling": {
+                         "uniforms_per_s": philox["uniforms_per_s"],
+                         "with_masks_per_s": philox["masked_per_s"],
+                         "frac": rate / philox["masked_per_s"]}},
         "clocks": clocks.summary(),
         "wall_s": wall,
     }

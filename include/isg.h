@@ -343,6 +343,15 @@ isg_status isg_acceptance_table(const double *betas, int32_t sweeps, int32_t kma
  * for NULL outputs, ECUDA if a launch fails. */
 isg_status isg_integer_peaks(void *cuda_stream, double *lop3_per_s, double *mad_wide_per_s);
 
+/* Measured rates, on the current device, of the sweep kernels' random numbers
+ * alone: uniforms per second of the factored Philox4x32-10 stream the sweeps
+ * draw (per site: the round-1/2 prefix and 8 blocks = 32 uniforms), without
+ * (uniforms_per_s) and with (masked_per_s) the two threshold masks the torus
+ * sweep builds from them.  Every attempt needs one uniform, so these bound a
+ * sweep's attempts/s from above.  No counterpart in the paper: a roofline aid.
+ * Runs two short kernels on cuda_stream and synchronises.  EINVAL for NULL. */
+isg_status isg_philox_rates(void *cuda_stream, double *uniforms_per_s, double *masked_per_s);
+
 /* Message of the last failed call on this thread ("" if none). */
 const char *isg_last_error(void);
 

@@ -6,12 +6,15 @@
 //
 // Each thread runs eight independent chains, one instruction per chain and
 // step; every step's eight results depend only on the previous step, so the
-// pipes, not latencies, set the rate once each SM holds enough warps.
+// pipes, not latencies, set the rate once each SM holds enough warps.  A
+// second pair of kernels runs the sweeps' own Philox code alone, an upper
+// bound on any sweep's rate.
 #include <cuda_runtime.h>
 
 #include <cstdint>
 
 #include "isg.h"
+#include "isg_device.cuh"
 #include "isg_runtime.h"
 
 namespace isg {
@@ -71,10 +74,95 @@ __global__ void __launch_bounds__(256) mad_rate_kernel(uint32_t *sink, int iters
   if ((uint32_t)acc == seed) sink[blockIdx.x] = (uint32_t)(acc >> 32);
 }
 
+// The sweep's random numbers alone: per site the round-1/2 prefix and eight
+// factored Philox4x32-10 blocks (32 uniforms), folded so none is dropped.
+// With kMasks, the uniforms are also turned into the sweep's two threshold
+// masks.  Their rates bound a sweep from above: every attempt needs one
+// uniform.
+template <bool kMasks>
+__global__ void __launch_bounds__(512) philox_rate_kernel(RoundKeys rk, int sites, uint32_t T4,
+                                                          uint32_t T8, uint32_t *sink) {
+  BlockPrefix bp[8];
+#pragma unroll
+  for (int q = 0; q < 8; ++q) bp[q] = block_prefix(24u + q, 7u, rk);
+  uint32_t acc = 0u;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < sites; i += gridDim.x * blockDim.x) {
+    const SitePrefix sp = site_prefix((uint32_t)i, rk);
+    uint32_t a4[2] = {0u, 0u}, a8[2] = {0u, 0u};
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const uint4 u = philox10_factored(sp, bp[q], rk);
+      if (kMasks) {
+        uint32_t &x4 = a4[q & 1], &x8 = a8[q & 1];
+        if (u.x < T4) x4 |= 1u << (4 * q);
+        if (u.y < T4) x4 |= 2u << (4 * q);
+        if (u.z < T4) x4 |= 4u << (4 * q);
+        if (u.w < T4) x4 |= 8u << (4 * q);
+        if (u.x < T8) x8 |= 1u << (4 * q);
+        if (u.y < T8) x8 |= 2u << (4 * q);
+        if (u.z < T8) x8 |= 4u << (4 * q);
+        if (u.w < T8) x8 |= 8u << (4 * q);
+      } else {
+        acc ^= u.x ^ u.y ^ u.z ^ u.w;
+      }
+    }
+    acc ^= (a4[0] | a4[1]) ^ (a8[0] | a8[1]);
+  }
+  if (acc == 0x12345678u) sink[blockIdx.x] = acc;
+}
+
+template <typename Launch>
+cudaError_t best_ms_of(Launch launch, cudaStream_t stream, float &best_ms) {
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  cudaError_t err = cudaEventCreate(&e0);
+  if (err == cudaSuccess) err = cudaEventCreate(&e1);
+  best_ms = 1e30f;
+  for (int rep = 0; rep < 3 && err == cudaSuccess; ++rep) {  // the first run warms up
+    err = cudaEventRecord(e0, stream);
+    if (err == cudaSuccess) err = launch();
+    if (err == cudaSuccess) err = cudaEventRecord(e1, stream);
+    if (err == cudaSuccess) err = cudaEventSynchronize(e1);
+    float ms = 0.f;
+    if (err == cudaSuccess) err = cudaEventElapsedTime(&ms, e0, e1);
+    if (err == cudaSuccess && rep > 0 && ms < best_ms) best_ms = ms;
+  }
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  return err;
+}
+
 }  // namespace
 }  // namespace isg
 
 using namespace isg;
+
+extern "C" isg_status isg_philox_rates(void *cuda_stream, double *uniforms_per_s,
+                                       double *masked_per_s) {
+  if (!uniforms_per_s || !masked_per_s) return fail(ISG_EINVAL, "outputs must not be NULL");
+  cudaStream_t stream = (cudaStream_t)cuda_stream;
+  const int blocks = sm_count() * 2, threads = 512, sites = sm_count() * 512 * 64;
+  uint32_t *sink = nullptr;
+  cudaError_t err = cudaMallocAsync(&sink, 4 * (size_t)blocks, stream);
+  const RoundKeys rk = round_keys(1u, 0u);
+  float ms0 = 0.f, ms1 = 0.f;
+  if (err == cudaSuccess)
+    err = best_ms_of([&] {
+      philox_rate_kernel<false><<<blocks, threads, 0, stream>>>(rk, sites, 0x40000000u,
+                                                                 0x10000000u, sink);
+      return cudaGetLastError();
+    }, stream, ms0);
+  if (err == cudaSuccess)
+    err = best_ms_of([&] {
+      philox_rate_kernel<true><<<blocks, threads, 0, stream>>>(rk, sites, 0x40000000u,
+                                                                0x10000000u, sink);
+      return cudaGetLastError();
+    }, stream, ms1);
+  if (sink) cudaFreeAsync(sink, stream);
+  if (err != cudaSuccess) return cuda_fail(err, "measuring the Philox rates");
+  *uniforms_per_s = 32.0 * sites / (ms0 * 1e-3);
+  *masked_per_s = 32.0 * sites / (ms1 * 1e-3);
+  return ISG_OK;
+}
 
 extern "C" isg_status isg_integer_peaks(void *cuda_stream, double *lop3_per_s,
                                         double *mad_wide_per_s) {

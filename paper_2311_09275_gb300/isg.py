@@ -80,6 +80,7 @@ _sig("isg_server_destroy", [_P])
 _sig("isg_server_get_stats", [_P, ctypes.POINTER(isg_server_stats)])
 _sig("isg_integer_peaks", [_P, ctypes.POINTER(_dbl), ctypes.POINTER(_dbl)])
 _sig("isg_acceptance_table", [_P, _i32, _i32, _P])
+_sig("isg_philox_rates", [_P, ctypes.POINTER(_dbl), ctypes.POINTER(_dbl)])
 _sig("isg_parallel_tempering", [_P, _i32, _P, _i32, _i32, _i32, _u64,
                                 ctypes.POINTER(isg_options), _P, ctypes.POINTER(_P)])
 _sig("isg_result_cluster_flips", [_P, _P, _i32])
@@ -353,6 +354,13 @@ def isg_acceptance_table(betas, kmax: int) -> np.ndarray:
     out = np.empty((b.shape[0], kmax + 1), dtype=np.uint32)
     _check(_lib.isg_acceptance_table(_ptr(b), int(b.shape[0]), int(kmax), _ptr(out)))
     return out
+
+
+def isg_philox_rates(stream=None) -> dict:
+    """Measured uniforms/s of the sweeps' Philox stream alone and with the threshold masks."""
+    a, b = _dbl(), _dbl()
+    _check(_lib.isg_philox_rates(_stream(stream), ctypes.byref(a), ctypes.byref(b)))
+    return {"uniforms_per_s": a.value, "masked_per_s": b.value}
 
 
 def isg_integer_peaks(stream=None) -> dict:
