@@ -271,6 +271,10 @@ typedef struct {
     int32_t threads;         /* threads per CTA */
     int64_t h2d_bytes;       /* host-to-device bytes the solve copied: its threshold table
                                 and the instance arrays uploaded for it (0 if resident) */
+    int32_t staged;          /* colour-class kernels: 1 if each CTA holds the adjacency of the
+                                vertices it updates in shared memory (the multi-spin graph
+                                kernel then sends a new word only to the cluster CTAs that
+                                update one of the vertex's neighbours), else 0 */
 } isg_stats;
 
 isg_status isg_result_stats(const isg_result *r, isg_stats *stats);

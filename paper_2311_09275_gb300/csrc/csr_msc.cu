@@ -14,9 +14,9 @@
 // after the colour-major relabel) and writes each new word into all K copies
 // through distributed shared memory; one cluster barrier separates classes.
 // A CTA stages the adjacency of the slices it owns in shared memory when it
-// fits.  Per-replica energy changes are accumulated in bit-sliced counters
-// (sum over accepted flips of d, and of U: the change is 2 (d - 2U)) and
-// reduced once per sweep.
+// fits, and then keeps their best state there too.  Per-replica energy
+// changes are accumulated in bit-sliced counters (sum over accepted flips of
+// d, and of U: the change is 2 (d - 2U)) and reduced once per sweep.
 #include <climits>
 
 #include "isg_device.cuh"
@@ -30,7 +30,7 @@ constexpr int kPlanesU = 6;  // per-lane bond counts up to 63 (degree <= 63)
 __host__ __device__ __forceinline__ size_t align16(size_t x) { return (x + 15) & ~size_t(15); }
 
 struct GmSmem {
-  size_t spin, lrow, lorig, lcol, ocls, trow, part, lane_acc, total;
+  size_t spin, lrow, lorig, lcol, lbest, ocls, trow, part, lane_acc, total;
 };
 
 __host__ __device__ __forceinline__ GmSmem gm_layout(int n, int K, int n_colours, int own_n,
@@ -40,8 +40,9 @@ __host__ __device__ __forceinline__ GmSmem gm_layout(int n, int K, int n_colours
   m.lrow = align16(sizeof(uint32_t) * (size_t)n);
   m.lorig = align16(m.lrow + (own_n ? sizeof(int32_t) * ((size_t)own_n + 1) : 0));
   m.lcol = align16(m.lorig + sizeof(int32_t) * (size_t)own_n);
-  m.ocls = align16(m.lcol + sizeof(int32_t) * (size_t)own_nnz);
-  m.trow = align16(m.ocls + sizeof(int32_t) * ((size_t)n_colours + 1));
+  m.lbest = align16(m.lcol + sizeof(int32_t) * (size_t)own_nnz);
+  m.ocls = align16(m.lbest + sizeof(uint32_t) * (size_t)own_n);
+  m.trow = align16(m.ocls + sizeof(int32_t) * 3 * (size_t)n_colours);
   m.part = align16(m.trow + 2 * sizeof(uint32_t) * (size_t)kmax1);
   m.lane_acc = m.part + 2 * sizeof(int32_t) * 32 * (size_t)K;
   m.total = align16(m.lane_acc + sizeof(int32_t) * 32);
@@ -102,13 +103,23 @@ struct GmAdj {
   const int32_t *row, *col, *orig;
 };
 
-// One vertex of one replica word: returns the new word; accumulates the
-// accepted flips' d and U into the energy counters.
+// The 32 uniforms of one vertex word in one sweep: Philox4x32-10 blocks
+// 8 word + q (q = 0..7) of the vertex's original id, from the sweep's block
+// prefixes.
+__device__ __forceinline__ void vertex_uniforms(uint32_t orig, const BlockPrefix (&bp)[8],
+                                                const RoundKeys &rk, uint4 (&uu)[8]) {
+  const SitePrefix sp = site_prefix(orig, rk);
+#pragma unroll
+  for (int q = 0; q < 8; ++q) uu[q] = philox10_factored(sp, bp[q], rk);
+}
+
+// One vertex of one replica word with its uniforms uu: returns the new word;
+// accumulates the accepted flips' d and U into the energy counters.
 template <int NP>
 __device__ __forceinline__ uint32_t update_vertex(const uint32_t *spin, int v, int i,
                                                   const GmAdj &a, const uint32_t *row,
-                                                  const BlockPrefix (&bp)[8], const RoundKeys &rk,
-                                                  SlicedCounter<NP> &cd, SlicedCounter<NP> &cu) {
+                                                  const uint4 (&uu)[8], SlicedCounter<NP> &cd,
+                                                  SlicedCounter<NP> &cu) {
   const uint32_t s0 = spin[v];
   const int p0 = a.row[i], p1 = a.row[i + 1];
   const int d = p1 - p0;
@@ -128,29 +139,21 @@ __device__ __forceinline__ uint32_t update_vertex(const uint32_t *spin, int v, i
   }
   // uphill lanes: U <= (d - 1) / 2, i.e. k = d - 2U > 0
   const int levels = (d + 1) / 2;
-  uint32_t up = 0u;
-  for (int lv = 0; lv < levels; ++lv) up |= count_equals(u, lv);
-  uint32_t acc = ~up;
-  if (up != 0u) {
-    const SitePrefix sp = site_prefix((uint32_t)a.orig[i], rk);
-    uint4 uu[8];
+  uint32_t acc = 0xFFFFFFFFu;
+  for (int lv = 0; lv < levels; ++lv) {
+    const uint32_t eq = count_equals(u, lv);
+    if (eq == 0u) continue;
+    const uint32_t T = row[d - 2 * lv];
+    uint32_t m0 = 0u, m1 = 0u;
 #pragma unroll
-    for (int q = 0; q < 8; ++q) uu[q] = philox10_factored(sp, bp[q], rk);
-    for (int lv = 0; lv < levels; ++lv) {
-      const uint32_t eq = count_equals(u, lv);
-      if (eq == 0u) continue;
-      const uint32_t T = row[d - 2 * lv];
-      uint32_t m0 = 0u, m1 = 0u;
-#pragma unroll
-      for (int q = 0; q < 8; ++q) {
-        uint32_t &m = (q & 1) ? m1 : m0;
-        if (uu[q].x < T) m |= 1u << (4 * q);
-        if (uu[q].y < T) m |= 2u << (4 * q);
-        if (uu[q].z < T) m |= 4u << (4 * q);
-        if (uu[q].w < T) m |= 8u << (4 * q);
-      }
-      acc |= eq & (m0 | m1);
+    for (int q = 0; q < 8; ++q) {
+      uint32_t &m = (q & 1) ? m1 : m0;
+      if (uu[q].x < T) m |= 1u << (4 * q);
+      if (uu[q].y < T) m |= 2u << (4 * q);
+      if (uu[q].z < T) m |= 4u << (4 * q);
+      if (uu[q].w < T) m |= 8u << (4 * q);
     }
+    acc &= ~eq | m0 | m1;
   }
   // energy change of the accepted lanes: 2 (d - 2U)
 #pragma unroll
@@ -163,14 +166,31 @@ __device__ __forceinline__ uint32_t update_vertex(const uint32_t *spin, int v, i
   return s0 ^ acc;
 }
 
+// The two halves of the group barrier: work between them overlaps the wait
+// for the other CTAs (a CTA-wide barrier when the group is one CTA).
+__device__ __forceinline__ void group_arrive(int K) {
+  if (K > 1) asm volatile("barrier.cluster.arrive.release.aligned;\n" ::: "memory");
+}
+
+__device__ __forceinline__ void group_wait(int K) {
+  if (K > 1)
+    asm volatile("barrier.cluster.wait.acquire.aligned;\n" ::: "memory");
+  else
+    __syncthreads();
+}
+
 template <int NP, bool STAGED>
 __device__ void gm_word(const GraphMscSolve &s, const GraphMscLaunch &L, int word, int k, int K,
                         int t_begin, int t_end, int resume, uint8_t *smem) {
   const int n = s.n;
-  const GmSmem lay = gm_layout(n, K, s.n_colours, STAGED ? L.own_n : 0, STAGED ? L.own_nnz : 0,
-                               s.kmax1);
+  const int nc = s.n_colours;
+  const GmSmem lay = gm_layout(n, K, nc, STAGED ? L.own_n : 0, STAGED ? L.own_nnz : 0, s.kmax1);
   uint32_t *spin = reinterpret_cast<uint32_t *>(smem + lay.spin);
-  int32_t *ocls = reinterpret_cast<int32_t *>(smem + lay.ocls);
+  // per class: this rank's slice [clo, chi) and the slot of its first vertex
+  // (the vertex itself when the adjacency is not staged)
+  int32_t *clo = reinterpret_cast<int32_t *>(smem + lay.ocls);
+  int32_t *chi = clo + nc;
+  int32_t *cob = chi + nc;
   uint32_t *trow = reinterpret_cast<uint32_t *>(smem + lay.trow);
   int32_t *part = reinterpret_cast<int32_t *>(smem + lay.part);
   int32_t *lane_acc = reinterpret_cast<int32_t *>(smem + lay.lane_acc);
@@ -190,32 +210,36 @@ __device__ void gm_word(const GraphMscSolve &s, const GraphMscLaunch &L, int wor
   for (int v = threadIdx.x; v < n; v += blockDim.x)
     spin[v] = resume ? gspin[v] : initial_word((uint32_t)s.orig[v], uword, key);
 
-  // owned slices per class (local row slots) and their staged adjacency
   if (threadIdx.x == 0) {
     int ov = 0;
-    for (int c = 0; c < s.n_colours; ++c) {
+    for (int c = 0; c < nc; ++c) {
       int lo, hi;
       own_range(s.class_start[c], s.class_start[c + 1], k, K, lo, hi);
-      ocls[c] = STAGED ? ov : lo;
+      clo[c] = lo;
+      chi[c] = hi;
+      cob[c] = STAGED ? ov : lo;
       ov += hi - lo;
     }
-    ocls[s.n_colours] = ov;
   }
   __syncthreads();
   GmAdj adj;
+  // staged: best state of the owned vertices by slot (else in global memory)
+  uint32_t *lbest = reinterpret_cast<uint32_t *>(smem + lay.lbest);
   if (STAGED) {
     int32_t *lrow = reinterpret_cast<int32_t *>(smem + lay.lrow);
     int32_t *lorig = reinterpret_cast<int32_t *>(smem + lay.lorig);
     int32_t *lcol = reinterpret_cast<int32_t *>(smem + lay.lcol);
     int ebase = 0;
-    for (int c = 0; c < s.n_colours; ++c) {
-      int lo, hi;
-      own_range(s.class_start[c], s.class_start[c + 1], k, K, lo, hi);
-      const int ob = ocls[c];
+    for (int c = 0; c < nc; ++c) {
+      const int lo = clo[c], hi = chi[c], ob = cob[c];
       const int e0 = s.rowptr[lo], e1 = s.rowptr[hi];
       for (int i = threadIdx.x; i <= hi - lo; i += blockDim.x) {
         lrow[ob + i] = s.rowptr[lo + i] - e0 + ebase;
-        if (i < hi - lo) lorig[ob + i] = s.orig[lo + i];
+        if (i < hi - lo) {
+          const int v = lo + i;
+          lorig[ob + i] = s.orig[v];
+          if (resume) lbest[ob + i] = gbest[v];
+        }
       }
       for (int p = threadIdx.x; p < e1 - e0; p += blockDim.x) lcol[ebase + p] = s.col[e0 + p];
       ebase += e1 - e0;
@@ -238,9 +262,8 @@ __device__ void gm_word(const GraphMscSolve &s, const GraphMscLaunch &L, int wor
     SlicedCounter<NP> cu;
     cu.clear();
     int32_t bonds = 0;
-    for (int c = 0; c < s.n_colours; ++c) {
-      int lo, hi;
-      own_range(s.class_start[c], s.class_start[c + 1], k, K, lo, hi);
+    for (int c = 0; c < nc; ++c) {
+      const int lo = clo[c], hi = chi[c];
       for (int v = lo + threadIdx.x; v < hi; v += blockDim.x) {
         const uint32_t s0 = spin[v];
         for (int p = s.rowptr[v]; p < s.rowptr[v + 1]; ++p) {
@@ -250,7 +273,8 @@ __device__ void gm_word(const GraphMscSolve &s, const GraphMscLaunch &L, int wor
           cu.add_at(0, ~(s0 ^ spin[j] ^ (uint32_t)(ee >> 31)));
           ++bonds;
         }
-        gbest[v] = s0;
+        if (STAGED) lbest[cob[c] + (v - lo)] = s0;
+        else gbest[v] = s0;
       }
     }
     const int32_t tot = 2 * cu.warp_lane_total() - __reduce_add_sync(0xFFFFFFFFu, bonds);
@@ -260,6 +284,25 @@ __device__ void gm_word(const GraphMscSolve &s, const GraphMscLaunch &L, int wor
   } else {
     e = s.e_cur[word * 32 + lane];
     e_best = s.e_best[word * 32 + lane];
+  }
+
+  // Random numbers do not depend on the spins: the uniforms of a thread's
+  // first vertex of the next class (or of the next sweep's first class) are
+  // drawn between the arrival at the group barrier and the wait for it.
+  BlockPrefix bp[8];
+  uint4 uu[8];
+  bool ready = false;  // uu holds the uniforms of this thread's next vertex
+  auto sweep_prefix = [&](int tt) {
+#pragma unroll
+    for (int q = 0; q < 8; ++q) bp[q] = block_prefix(8u * uword + (uint32_t)q, (uint32_t)tt, s.rk);
+  };
+  auto draw_first = [&](int c) {
+    ready = clo[c] + (int)threadIdx.x < chi[c];
+    if (ready) vertex_uniforms((uint32_t)adj.orig[cob[c] + threadIdx.x], bp, s.rk, uu);
+  };
+  if (t_begin < t_end) {
+    sweep_prefix(t_begin);
+    draw_first(0);
   }
 
   int t = t_begin;
@@ -273,37 +316,58 @@ __device__ void gm_word(const GraphMscSolve &s, const GraphMscLaunch &L, int wor
     const uint32_t *gnext = wtab + (size_t)(t + 1) * s.table_ts;
     const uint32_t p0 = (more && x0 < s.kmax1) ? gnext[x0] : 0u;
     const uint32_t p1 = (more && x1 < s.kmax1) ? gnext[x1] : 0u;
-    BlockPrefix bp[8];
-#pragma unroll
-    for (int q = 0; q < 8; ++q) bp[q] = block_prefix(8u * uword + (uint32_t)q, (uint32_t)t, s.rk);
     SlicedCounter<NP> cd, cu;
     cd.clear();
     cu.clear();
-    for (int c = 0; c < s.n_colours; ++c) {
-      int lo, hi;
-      own_range(s.class_start[c], s.class_start[c + 1], k, K, lo, hi);
-      const int ob = ocls[c];
+    for (int c = 0; c < nc; ++c) {
+      const int lo = clo[c], hi = chi[c], ob = cob[c];
       for (int v = lo + threadIdx.x; v < hi; v += blockDim.x) {
+        const int i = ob + (v - lo);
         // improved replicas take their best state from v as it stood at the
         // end of the previous sweep (v has not been updated since)
-        if (imp != 0u) gbest[v] = (gbest[v] & ~imp) | (spin[v] & imp);
-        const uint32_t sn = update_vertex<NP>(spin, v, ob + (v - lo), adj, row, bp, s.rk, cd, cu);
+        if (imp != 0u) {
+          if (STAGED) lbest[i] = (lbest[i] & ~imp) | (spin[v] & imp);
+          else gbest[v] = (gbest[v] & ~imp) | (spin[v] & imp);
+        }
+        if (!ready) vertex_uniforms((uint32_t)adj.orig[i], bp, s.rk, uu);
+        ready = false;
+        const uint32_t sn = update_vertex<NP>(spin, v, i, adj, row, uu, cd, cu);
         if (K == 1) {
           spin[v] = sn;
         } else {
           for (int r = 0; r < K; ++r) peer_smem(spin, (uint32_t)r)[v] = sn;
         }
       }
-      if (c + 1 < s.n_colours) sync_group(K);
+      if (c + 1 < nc) {
+        group_arrive(K);
+        draw_first(c + 1);
+        group_wait(K);
+      }
     }
     if (more) {
       uint32_t *nrow = trow + ((t + 1) & 1) * s.kmax1;
       if (x0 < s.kmax1) nrow[x0] = p0;
       if (x1 < s.kmax1) nrow[x1] = p1;
     }
+    // per-lane energy change, summed over the CTA and published to every CTA
     int32_t *pbuf = part + ((t + 1) & 1) * 32 * K;
-    const int32_t tot = 2 * (cd.warp_lane_total() - 2 * cu.warp_lane_total());
-    publish_lanes(tot, lane_acc, pbuf, k, K);
+    atomicAdd(&lane_acc[lane], 2 * (cd.warp_lane_total() - 2 * cu.warp_lane_total()));
+    __syncthreads();
+    if (threadIdx.x < 32) {
+      const int32_t x = lane_acc[threadIdx.x];
+      lane_acc[threadIdx.x] = 0;
+      if (K == 1) {
+        pbuf[threadIdx.x] = x;
+      } else {
+        for (int r = 0; r < K; ++r) peer_smem(pbuf, (uint32_t)r)[k * 32 + threadIdx.x] = x;
+      }
+    }
+    group_arrive(K);
+    if (more) {
+      sweep_prefix(t + 1);
+      draw_first(0);
+    }
+    group_wait(K);
     int32_t dsum = 0;
     for (int r = 0; r < K; ++r) dsum += pbuf[r * 32 + lane];
     e += dsum;
@@ -322,13 +386,13 @@ __device__ void gm_word(const GraphMscSolve &s, const GraphMscLaunch &L, int wor
   }
 
   // every update of the cluster precedes the last group barrier
-  for (int c = 0; c < s.n_colours; ++c) {
-    int lo, hi;
-    own_range(s.class_start[c], s.class_start[c + 1], k, K, lo, hi);
+  for (int c = 0; c < nc; ++c) {
+    const int lo = clo[c], hi = chi[c];
     for (int v = lo + threadIdx.x; v < hi; v += blockDim.x) {
       const uint32_t x = spin[v];
       gspin[v] = x;
-      if (imp != 0u) gbest[v] = (gbest[v] & ~imp) | (x & imp);
+      if (STAGED) gbest[v] = (lbest[cob[c] + (v - lo)] & ~imp) | (x & imp);
+      else if (imp != 0u) gbest[v] = (gbest[v] & ~imp) | (x & imp);
     }
   }
   if (k == 0) {

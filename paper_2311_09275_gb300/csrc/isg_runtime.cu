@@ -638,6 +638,7 @@ cudaError_t launch_sweeps(const isg_problem *p, const DeviceProblem *dp, isg_res
     planes = gm_planes_for(p, cluster, threads);
     if (planes < 0) return cudaErrorInvalidConfiguration;
   }
+  r->staged = own_n > 0;
   const int passes = (has_target && r->units > 1) ? 2 : 1;
   for (int pass = 0; pass < passes && err == cudaSuccess; ++pass) {
     const int first = plain ? 0 : -1;
@@ -1014,6 +1015,7 @@ isg_status tempering_impl(const isg_problem *p, int32_t K, const double *betas, 
   r->ctas = K * cluster;
   r->cluster = cluster;
   r->threads = threads;
+  r->staged = own_n > 0;
 
   // one row of thresholds per word, the same every sweep
   TorusSolve s = {};
@@ -1541,6 +1543,7 @@ isg_status isg_result_stats(const isg_result *r, isg_stats *stats) {
   stats->cluster_ctas = r->cluster;
   stats->threads = r->threads;
   stats->h2d_bytes = r->h2d_bytes;
+  stats->staged = r->staged;
   return ISG_OK;
 }
 

@@ -80,6 +80,7 @@ struct isg_result {
   int8_t *d_out = nullptr, *d_out_best = nullptr;  // [R][n] +-1, original vertex order
   int32_t launches = 0, sweep_launches = 0, ctas = 0, cluster = 0, threads = 0;
   int64_t h2d_bytes = 0;                   // table + instance arrays uploaded for this solve
+  int32_t staged = 0;                      // colour-class launches hold their adjacency in smem
   // parallel tempering: exchange tables and counters (one allocation), pairs K - 1
   void *pt_mem = nullptr;
   unsigned long long *d_accepted = nullptr;

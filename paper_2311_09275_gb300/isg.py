@@ -39,7 +39,8 @@ class isg_options(ctypes.Structure):
 class isg_stats(ctypes.Structure):
     _fields_ = [("sweep_kernel_ms", ctypes.c_float), ("launches", _i32),
                 ("sweep_launches", _i32), ("kernel", _i32), ("ctas", _i32),
-                ("cluster_ctas", _i32), ("threads", _i32), ("h2d_bytes", _i64)]
+                ("cluster_ctas", _i32), ("threads", _i32), ("h2d_bytes", _i64),
+                ("staged", _i32)]
 
 
 class isg_server_stats(ctypes.Structure):

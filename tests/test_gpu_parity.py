@@ -7,6 +7,8 @@ counts); the full-size cases run exactly the launch configuration the
 benchmark times and compare sampled replicas with the oracle plus
 properties that hold for every replica.
 """
+import functools
+
 import numpy as np
 import pytest
 
@@ -162,7 +164,21 @@ def test_graph_msc_bit_exact(isg, name, R, cluster, threads):
     res = isg.isg_anneal(isg.problem_of(g), R, betas, 13, kernel=4, cluster_ctas=cluster,
                          threads=threads)
     assert_same(res, orc)
-    assert res.stats()["kernel"] == 4
+    st = res.stats()
+    assert st["kernel"] == 4 and st["staged"] == 1  # words sent only where they are read
+
+
+@pytest.mark.parametrize("R,cluster,threads", [(40, 1, 256), (70, 4, 512)])
+def test_graph_msc_unstaged_bit_exact(isg, R, cluster, threads):
+    """Adjacency too large for shared memory (12,000 vertices, mean degree 25):
+    every update is written into every CTA's copy of the word."""
+    g = I.random_graph(12000, 150000, 9)
+    betas = I.geometric_betas(0.1, 5.0, 12)
+    orc = oracle.anneal(oracle.csr_of(g), R, betas, 29, check_energy=True)
+    res = isg.isg_anneal(isg.problem_of(g), R, betas, 29, kernel=4, cluster_ctas=cluster,
+                         threads=threads)
+    assert res.stats()["staged"] == 0
+    assert_same(res, orc)
 
 
 def test_graph_auto_kernel_choice(isg):
@@ -342,14 +358,21 @@ def test_torus_80x100_full_size_sampled(isg):
     assert np.array_equal(isg.isg_energy(p, res.best_all()), res.best(spins=False)[3])
 
 
+@functools.lru_cache(maxsize=1)
+def random_10000_oracle(reps):
+    sv = I.random_10000()
+    return oracle.anneal(oracle.csr_of(sv.problem), list(reps), sv.betas, sv.seed)
+
+
 @pytest.mark.slow
-def test_random_10000_full_size_sampled(isg):
+@pytest.mark.parametrize("shape", [{}, {"cluster_ctas": 12, "threads": 512}])
+def test_random_10000_full_size_sampled(isg, shape):
+    """Default shape and the 12-CTA cluster shape the bench's autotuner picks."""
     sv = I.random_10000()
     p = isg.problem_of(sv.problem)
-    res = isg.isg_anneal(p, sv.replicas, sv.betas, sv.seed)
-    reps = [0, 1, 2, 3, 130, 255]
-    orc = oracle.anneal(oracle.csr_of(sv.problem), reps, sv.betas, sv.seed)
-    assert_same(res, orc, reps=reps)
+    res = isg.isg_anneal(p, sv.replicas, sv.betas, sv.seed, **shape)
+    reps = (0, 1, 2, 3, 130, 255)
+    assert_same(res, random_10000_oracle(reps), reps=list(reps))
     spins, e, _ = res.final()
     assert np.array_equal(isg.isg_energy(p, spins), e)
 
