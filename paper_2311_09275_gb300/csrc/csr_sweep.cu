@@ -44,7 +44,7 @@ __host__ __device__ __forceinline__ CsrSmem csr_layout(int n, int Q, int K, int 
   m.lcol = align16(m.lorig + sizeof(int32_t) * (size_t)own_n);
   m.lwt = align16(m.lcol + sizeof(int32_t) * (size_t)own_nnz);
   m.ocls = align16(m.lwt + (weights ? sizeof(int32_t) * (size_t)own_nnz : 0));
-  m.trow = align16(m.ocls + (own_n ? sizeof(int32_t) * ((size_t)n_colours + 1) : 0));
+  m.trow = align16(m.ocls + sizeof(int32_t) * 3 * (size_t)n_colours);  // class slice table
   m.part = align16(m.trow + 2 * sizeof(uint32_t) * (size_t)trow_n);
   m.lane_acc = m.part + 2 * sizeof(int32_t) * 4 * (size_t)Q * K;
   m.total = align16(m.lane_acc + sizeof(int32_t) * 4 * (size_t)Q);
@@ -56,6 +56,19 @@ __device__ __forceinline__ void sync_group(int K) {
     __syncthreads();
   else
     cluster_barrier();
+}
+
+// The two halves of the group barrier: work between them overlaps the wait
+// for the other CTAs (a CTA-wide barrier when the group is one CTA).
+__device__ __forceinline__ void group_arrive(int K) {
+  if (K > 1) asm volatile("barrier.cluster.arrive.release.aligned;\n" ::: "memory");
+}
+
+__device__ __forceinline__ void group_wait(int K) {
+  if (K > 1)
+    asm volatile("barrier.cluster.wait.acquire.aligned;\n" ::: "memory");
+  else
+    __syncthreads();
 }
 
 // Spin (+1/-1) of lane l of a packed word: byte l, sign-extended.
@@ -71,10 +84,11 @@ __device__ __forceinline__ void own_range(int a, int b, int k, int K, int &lo, i
 }
 
 // Per-lane int32 values summed over the CTA, published to every CTA of the
-// cluster as part[k][slot]; ends with the group barrier.
-template <int Q>
+// cluster as part[k][slot]; ends with the group barrier, `during` running
+// between the arrival and the wait.
+template <int Q, typename During>
 __device__ __forceinline__ void publish(const int32_t (&vals)[Q][4], int32_t *lane_acc,
-                                        int32_t *part, int k, int K) {
+                                        int32_t *part, int k, int K, During during) {
 #pragma unroll
   for (int q = 0; q < Q; ++q)
 #pragma unroll
@@ -92,7 +106,9 @@ __device__ __forceinline__ void publish(const int32_t (&vals)[Q][4], int32_t *la
       for (int r = 0; r < K; ++r) peer_smem(part, (uint32_t)r)[k * 4 * Q + threadIdx.x] = v;
     }
   }
-  sync_group(K);
+  group_arrive(K);
+  during();
+  group_wait(K);
 }
 
 // Best-state blend of vertex v for the improved lanes (byte masks bm[q]); kept
@@ -192,7 +208,12 @@ __device__ void csr_solve(const CsrSolve &s, const CsrLaunch &L, int quad0, int 
   int32_t *part = reinterpret_cast<int32_t *>(smem + lay.part);
   int32_t *lane_acc = reinterpret_cast<int32_t *>(smem + lay.lane_acc);
   uint32_t *trow = reinterpret_cast<uint32_t *>(smem + lay.trow);
-  int32_t *ocls = reinterpret_cast<int32_t *>(smem + lay.ocls);
+  // per class: this rank's slice [clo, chi) and the row slot of its first
+  // vertex (the vertex itself when the adjacency is not staged)
+  const int nc = s.n_colours;
+  int32_t *clo = reinterpret_cast<int32_t *>(smem + lay.ocls);
+  int32_t *chi = clo + nc;
+  int32_t *cob = chi + nc;
   const PhiloxKey key{s.key0, s.key1};
   const int lane = (int)lane_id();
 
@@ -217,6 +238,18 @@ __device__ void csr_solve(const CsrSolve &s, const CsrLaunch &L, int quad0, int 
     spin[x] = w;
   }
 
+  if (threadIdx.x == 0) {
+    int ov = 0;
+    for (int c = 0; c < nc; ++c) {
+      int lo, hi;
+      own_range(s.class_start[c], s.class_start[c + 1], k, K, lo, hi);
+      clo[c] = lo;
+      chi[c] = hi;
+      cob[c] = STAGED ? ov : lo;
+      ov += hi - lo;
+    }
+  }
+  __syncthreads();
   // adjacency of the owned slices: staged copy (local row ids) or global
   Adj adj;
   if (STAGED) {
@@ -224,22 +257,9 @@ __device__ void csr_solve(const CsrSolve &s, const CsrLaunch &L, int quad0, int 
     int32_t *lorig = reinterpret_cast<int32_t *>(smem + lay.lorig);
     int32_t *lcol = reinterpret_cast<int32_t *>(smem + lay.lcol);
     int32_t *lwt = reinterpret_cast<int32_t *>(smem + lay.lwt);
-    if (threadIdx.x == 0) {
-      int ov = 0;
-      for (int c = 0; c < s.n_colours; ++c) {
-        int lo, hi;
-        own_range(s.class_start[c], s.class_start[c + 1], k, K, lo, hi);
-        ocls[c] = ov;
-        ov += hi - lo;
-      }
-      ocls[s.n_colours] = ov;
-    }
-    __syncthreads();
     int ebase = 0;
-    for (int c = 0; c < s.n_colours; ++c) {
-      int lo, hi;
-      own_range(s.class_start[c], s.class_start[c + 1], k, K, lo, hi);
-      const int ob = ocls[c];
+    for (int c = 0; c < nc; ++c) {
+      const int lo = clo[c], hi = chi[c], ob = cob[c];
       const int e0 = s.rowptr[lo], e1 = s.rowptr[hi];
       for (int i = threadIdx.x; i <= hi - lo; i += blockDim.x) {
         lrow[ob + i] = s.rowptr[lo + i] - e0 + ebase;
@@ -302,7 +322,7 @@ __device__ void csr_solve(const CsrSolve &s, const CsrLaunch &L, int quad0, int 
         }
       }
     }
-    publish<Q>(vals, lane_acc, part, k, K);  // publication 0 uses buffer 0
+    publish<Q>(vals, lane_acc, part, k, K, [] {});  // publication 0 uses buffer 0
     int32_t tot = 0;
     if (lane < 4 * Q)
       for (int r = 0; r < K; ++r) tot += part[r * 4 * Q + lane];
@@ -312,6 +332,25 @@ __device__ void csr_solve(const CsrSolve &s, const CsrLaunch &L, int quad0, int 
     e = s.e_cur[my_r];
     e_best = s.e_best[my_r];
   }
+
+  // Random numbers and fields do not depend on the spins: those of a thread's
+  // first vertex of the next class (or of the next sweep's first class) are
+  // drawn between the arrival at the group barrier and the wait for it.
+  uint4 pu[Q];
+  int32_t phv = 0;
+  bool ready = false;  // pu, phv hold this thread's next vertex's uniforms and field
+  auto draw_first = [&](int c, int tt) {
+    const int v = clo[c] + (int)threadIdx.x;
+    ready = v < chi[c];
+    if (ready) {
+      const uint32_t ov = (uint32_t)adj.orig[cob[c] + threadIdx.x];
+#pragma unroll
+      for (int q = 0; q < Q; ++q)
+        pu[q] = philox10(make_uint4(ov, (uint32_t)tt, (uint32_t)(quad0 + q), kTagSweep), key);
+      if (MODE == 2 && s.field) phv = __ldg(&s.field[v]);
+    }
+  };
+  if (t_begin < t_end) draw_first(0, t_begin);
 
   int t = t_begin;
   int hit = -1;
@@ -342,10 +381,8 @@ __device__ void csr_solve(const CsrSolve &s, const CsrLaunch &L, int quad0, int 
     for (int q = 0; q < Q; ++q)
 #pragma unroll
       for (int l = 0; l < 4; ++l) de[q][l] = 0;
-    for (int c = 0; c < s.n_colours; ++c) {
-      int lo, hi;
-      own_range(s.class_start[c], s.class_start[c + 1], k, K, lo, hi);
-      const int ob = STAGED ? ocls[c] : lo;  // row slot of vertex lo
+    for (int c = 0; c < nc; ++c) {
+      const int lo = clo[c], hi = chi[c], ob = cob[c];  // ob: row slot of vertex lo
       for (int v = lo + threadIdx.x; v < hi; v += blockDim.x) {
         const int i = ob + (v - lo);
         const int p0 = adj.row[i], p1 = adj.row[i + 1];
@@ -358,7 +395,7 @@ __device__ void csr_solve(const CsrSolve &s, const CsrLaunch &L, int quad0, int 
         int32_t kk[Q][4];
         // local fields ride only with general weights (field instances run in mode 2)
         fields<Q, MODE>(spin, n, v, p0, p1, adj,
-                        (MODE == 2 && s.field) ? __ldg(&s.field[v]) : 0, kk);
+                        (MODE == 2 && s.field) ? (ready ? phv : __ldg(&s.field[v])) : 0, kk);
 #pragma unroll
         for (int q = 0; q < Q; ++q) {
           // lanes with kk > 0 are uphill; the rest are always taken
@@ -367,8 +404,9 @@ __device__ void csr_solve(const CsrSolve &s, const CsrLaunch &L, int quad0, int 
           for (int l = 0; l < 4; ++l) up |= (kk[q][l] > 0 ? 1u : 0u) << l;
           uint32_t acc = ~up & 0xFu;
           if (up != 0u) {
-            const uint4 u =
-                philox10(make_uint4(ov, (uint32_t)t, (uint32_t)(quad0 + q), kTagSweep), key);
+            const uint4 u = ready ? pu[q]
+                                  : philox10(make_uint4(ov, (uint32_t)t, (uint32_t)(quad0 + q),
+                                                        kTagSweep), key);
             if ((up & 1u) && u.x < row[kk[q][0]]) acc |= 1u;
             if ((up & 2u) && u.y < row[kk[q][1]]) acc |= 2u;
             if ((up & 4u) && u.z < row[kk[q][2]]) acc |= 4u;
@@ -391,8 +429,13 @@ __device__ void csr_solve(const CsrSolve &s, const CsrLaunch &L, int quad0, int 
             }
           }
         }
+        ready = false;
       }
-      if (c + 1 < s.n_colours) sync_group(K);
+      if (c + 1 < nc) {
+        group_arrive(K);
+        draw_first(c + 1, t);
+        group_wait(K);
+      }
     }
     if (trow_n && more) {
       // the other buffer's last reads were in the previous sweep
@@ -407,7 +450,9 @@ __device__ void csr_solve(const CsrSolve &s, const CsrLaunch &L, int quad0, int 
     }
     // sweep t is publication t + 1 (the initial energy is publication 0)
     int32_t *pbuf = part + ((t + 1) & 1) * 4 * Q * K;
-    publish<Q>(de, lane_acc, pbuf, k, K);
+    publish<Q>(de, lane_acc, pbuf, k, K, [&] {
+      if (more) draw_first(0, t + 1);
+    });
     int32_t tot = 0;
     if (lane < 4 * Q)
       for (int r = 0; r < K; ++r) tot += pbuf[r * 4 * Q + lane];
@@ -468,8 +513,11 @@ __device__ void csr_solve(const CsrSolve &s, const CsrLaunch &L, int quad0, int 
   }
 }
 
+// Single-quad packed-count builds are held to 64 registers (two CTAs per SM),
+// which the general-weights build cannot reach without spilling.
 template <int Q, int MODE, bool STAGED>
-__global__ void __launch_bounds__(512) csr_kernel(CsrSolve s, CsrLaunch l) {
+__global__ void __launch_bounds__(512, (Q == 1 && MODE != 2) ? 2 : 1)
+    csr_kernel(CsrSolve s, CsrLaunch l) {
   extern __shared__ __align__(16) uint8_t smem[];
   const int K = l.cluster;
   const int k = (int)(blockIdx.x % K);
@@ -507,9 +555,10 @@ cudaError_t launch_csr(Kern kernel, int grid, const CsrSolve &s, const CsrLaunch
   return cudaLaunchKernelEx(&cfg, kernel, s, l);
 }
 
-__global__ void __launch_bounds__(512) csr_batch_kernel(const CsrBatchItem *items,
-                                                        const int32_t *count_dev,
-                                                        const int32_t *order, int32_t *next) {
+// Two CTAs per SM (64 registers): the units are independent CTAs.
+__global__ void __launch_bounds__(512, 2) csr_batch_kernel(const CsrBatchItem *items,
+                                                           const int32_t *count_dev,
+                                                           const int32_t *order, int32_t *next) {
   extern __shared__ __align__(16) uint8_t smem[];
   __shared__ int item;
   const int count = *count_dev;

@@ -74,13 +74,27 @@ __device__ __forceinline__ void sync_group(int K) {
     cluster_barrier();
 }
 
+// The two halves of the group barrier: work between them overlaps the wait
+// for the other CTAs (a CTA-wide barrier when the group is one CTA).
+__device__ __forceinline__ void group_arrive(int K) {
+  if (K > 1) asm volatile("barrier.cluster.arrive.release.aligned;\n" ::: "memory");
+}
+
+__device__ __forceinline__ void group_wait(int K) {
+  if (K > 1)
+    asm volatile("barrier.cluster.wait.acquire.aligned;\n" ::: "memory");
+  else
+    __syncthreads();
+}
+
 // Sum over the whole cluster of the bit-sliced counters, per lane (= per
 // replica of the word): every warp publishes its lane totals to every CTA of
 // the cluster, one group barrier, then every warp adds them all up itself, so
-// that no CTA-wide barrier or serial section is needed.
-template <int NP>
+// that no CTA-wide barrier or serial section is needed.  `during` runs
+// between the arrival at the barrier and the wait for it.
+template <int NP, typename During>
 __device__ __forceinline__ int32_t cluster_lane_sum(const SlicedCounter<NP> &cnt, int32_t *part,
-                                                    int k, int K) {
+                                                    int k, int K, During during) {
   const int nw = (int)(blockDim.x >> 5);
   const int slot = (k * nw + (int)(threadIdx.x >> 5)) * 32 + (int)lane_id();
   const int32_t tot = cnt.warp_lane_total();
@@ -89,16 +103,66 @@ __device__ __forceinline__ int32_t cluster_lane_sum(const SlicedCounter<NP> &cnt
   } else {
     for (int q = 0; q < K; ++q) peer_smem(part, (uint32_t)q)[slot] = tot;
   }
-  sync_group(K);
+  group_arrive(K);
+  during();
+  group_wait(K);
   int32_t sum = 0;
   for (int j = 0; j < K * nw; ++j) sum += part[j * 32 + (int)lane_id()];
   return sum;
 }
 
+// Acceptance masks of one site-word: lanes whose uniform is below T4 (r4) and
+// below T8 (r8, only with kTwoThresholds).  The 32 uniforms are 8 Philox
+// blocks of 4 sharing the site's round-1/2 prefix; the masks are built by
+// compare + predicated OR into two partial accumulators (measured faster than
+// packing 4-bit nibbles, and than moving the compares onto the multiply-add
+// pipe).  They do not depend on the spins.
+template <bool kTwoThresholds>
+__device__ __forceinline__ void site_masks(uint32_t site, const BlockPrefix (&bp)[8],
+                                           const RoundKeys &rk, uint32_t T4, uint32_t T8,
+                                           uint32_t &r4, uint32_t &r8) {
+  const SitePrefix sp = site_prefix(site, rk);
+  uint32_t a4[2] = {0u, 0u}, a8[2] = {0u, 0u};
+#pragma unroll
+  for (int q = 0; q < 8; ++q) {
+    const uint4 u = philox10_factored(sp, bp[q], rk);
+    uint32_t &x4 = a4[q & 1], &x8 = a8[q & 1];
+    if (u.x < T4) x4 |= 1u << (4 * q);
+    if (u.y < T4) x4 |= 2u << (4 * q);
+    if (u.z < T4) x4 |= 4u << (4 * q);
+    if (u.w < T4) x4 |= 8u << (4 * q);
+    if (kTwoThresholds) {
+      if (u.x < T8) x8 |= 1u << (4 * q);
+      if (u.y < T8) x8 |= 2u << (4 * q);
+      if (u.z < T8) x8 |= 4u << (4 * q);
+      if (u.w < T8) x8 |= 8u << (4 * q);
+    }
+  }
+  r4 = a4[0] | a4[1];
+  r8 = a8[0] | a8[1];
+}
+
+// Masks of this thread's first site of colour c in the band (the phase's
+// first loop iteration), drawn ahead of the phase; false if it has none.
+__device__ __forceinline__ bool first_site_masks(int W, int r0, int nr, int c,
+                                                 const BlockPrefix (&bp)[8], const RoundKeys &rk,
+                                                 uint32_t T4, uint32_t T8, uint32_t &r4,
+                                                 uint32_t &r8) {
+  const int half = W >> 1;
+  const int lr = 1 + (int)threadIdx.x / half;
+  if (lr > nr) return false;
+  const int j = (int)threadIdx.x - (lr - 1) * half;
+  const int gr = r0 + lr - 1;
+  const uint32_t site = (uint32_t)(gr * W + 2 * j + ((c + gr) & 1));
+  if (T8 != 0u)
+    site_masks<true>(site, bp, rk, T4, T8, r4, r8);
+  else
+    site_masks<false>(site, bp, rk, T4, T8, r4, r8);
+  return true;
+}
+
 // One colour phase of one replica word: this thread's sites of colour c in
-// the CTA's band.  Acceptance masks are built by compare + predicated OR into
-// two partial accumulators (measured faster than packing 4-bit nibbles, and
-// than moving the compares onto the multiply-add pipe).
+// the CTA's band; the first one's masks come in (pre4, pre8) when `ready`.
 // Replicas in `imp` improved their best energy at the end of the previous
 // sweep; their best state is taken here, site by site, from the spins as they
 // stand before this phase updates them (unchanged since that sweep's end).
@@ -107,7 +171,8 @@ __device__ __forceinline__ void sweep_phase(uint32_t *spin, uint32_t *best, cons
                                             uint32_t *up_peer, uint32_t *down_peer, int W, int r0,
                                             int nr, int c, const BlockPrefix (&bp)[8],
                                             const RoundKeys &rk, uint32_t T4, uint32_t T8,
-                                            uint32_t imp, SlicedCounter<NP> &cnt) {
+                                            uint32_t imp, SlicedCounter<NP> &cnt, uint32_t pre4,
+                                            uint32_t pre8, bool ready) {
   const int half = W >> 1;
   const int step_rows = blockDim.x / half;
   const int step_cols = blockDim.x - step_rows * half;
@@ -137,28 +202,9 @@ __device__ __forceinline__ void sweep_phase(uint32_t *spin, uint32_t *best, cons
     const uint32_t eq0 = ~(u0 | u1 | u2);
     const uint32_t eq1 = u0 & ~u1;
     const uint32_t ge2 = u1 | u2;
-    // uniforms of the 32 replicas: 8 Philox blocks of 4 sharing this site's
-    // round-1/2 prefix; each block yields independent 4-bit acceptance nibbles
-    const uint32_t site = (uint32_t)(gr * W + col);
-    const SitePrefix sp = site_prefix(site, rk);
-    uint32_t a4[2] = {0u, 0u}, a8[2] = {0u, 0u};
-#pragma unroll
-    for (int q = 0; q < 8; ++q) {
-      const uint4 u = philox10_factored(sp, bp[q], rk);
-      uint32_t &x4 = a4[q & 1], &x8 = a8[q & 1];
-      if (u.x < T4) x4 |= 1u << (4 * q);
-      if (u.y < T4) x4 |= 2u << (4 * q);
-      if (u.z < T4) x4 |= 4u << (4 * q);
-      if (u.w < T4) x4 |= 8u << (4 * q);
-      if (kTwoThresholds) {
-        if (u.x < T8) x8 |= 1u << (4 * q);
-        if (u.y < T8) x8 |= 2u << (4 * q);
-        if (u.z < T8) x8 |= 4u << (4 * q);
-        if (u.w < T8) x8 |= 8u << (4 * q);
-      }
-    }
-    const uint32_t r4 = a4[0] | a4[1];
-    const uint32_t r8 = a8[0] | a8[1];
+    uint32_t r4 = pre4, r8 = pre8;
+    if (!ready) site_masks<kTwoThresholds>((uint32_t)(gr * W + col), bp, rk, T4, T8, r4, r8);
+    ready = false;
     const uint32_t acc = ge2 | (eq1 & r4) | (eq0 & r8);
     const uint32_t sn = s0 ^ acc;
     spin[x] = sn;
@@ -175,7 +221,9 @@ __device__ __forceinline__ void sweep_phase(uint32_t *spin, uint32_t *best, cons
   }
 }
 
-template <int NP>
+// kPrefetch: draw the first site's masks of each phase during the barrier
+// before it (off in the 64-register build, where the extra live state spills).
+template <int NP, bool kPrefetch>
 __device__ void torus_word(const TorusSolve &s, int word, int k, int K, int t_begin, int t_end,
                            int resume, uint8_t *smem) {
   const int L = s.L, W = s.W, n = L * W;
@@ -230,7 +278,7 @@ __device__ void torus_word(const TorusSolve &s, int word, int k, int K, int t_be
       const uint32_t d = ~(s0 ^ spin[x + W] ^ sign_mask(cbx >> 1));
       cnt.add2(a ^ d, a & d);
     }
-    e = 2 * cluster_lane_sum<NP>(cnt, part, k, K) - 2 * n;
+    e = 2 * cluster_lane_sum<NP>(cnt, part, k, K, [] {}) - 2 * n;
     e_best = e;
   } else {
     e = s.e_cur[word * 32 + lane];
@@ -247,28 +295,52 @@ __device__ void torus_word(const TorusSolve &s, int word, int k, int K, int t_be
   uint32_t imp = 0u;  // replicas whose best state is the state at the start of sweep t
   // thresholds of the next sweep are loaded one sweep ahead
   const uint32_t *trow = s.table + (size_t)word * s.table_ws;
-  uint32_t T4n = trow[(size_t)t * s.table_ts], T8n = trow[(size_t)t * s.table_ts + 1];
+  uint32_t T4n = 0u, T8n = 0u;
+  if (t < t_end) T4n = trow[(size_t)t * s.table_ts], T8n = trow[(size_t)t * s.table_ts + 1];
+  // the (block, sweep) part of Philox rounds 1-2, uniform across the CTA
+  BlockPrefix bp[8];
+  auto sweep_prefix = [&](int tt) {
+#pragma unroll
+    for (int q = 0; q < 8; ++q) bp[q] = block_prefix(8u * uword + (uint32_t)q, (uint32_t)tt, s.rk);
+  };
+  // masks of this thread's first site of the next phase, drawn while the
+  // group barrier before that phase completes (they do not depend on spins)
+  uint32_t pre4 = 0u, pre8 = 0u;
+  bool ready = false;
+  if (t < t_end) {
+    sweep_prefix(t);
+    if (kPrefetch) ready = first_site_masks(W, r0, nr, 0, bp, s.rk, T4n, T8n, pre4, pre8);
+  }
   for (; t < t_end; ++t) {
     const uint32_t T4 = T4n, T8 = T8n;
-    if (t + 1 < t_end) {
+    const bool more = t + 1 < t_end;
+    if (more) {
       T4n = trow[(size_t)(t + 1) * s.table_ts];
       T8n = trow[(size_t)(t + 1) * s.table_ts + 1];
     }
-    // the (block, sweep) part of Philox rounds 1-2, uniform across the CTA
-    BlockPrefix bp[8];
-#pragma unroll
-    for (int q = 0; q < 8; ++q) bp[q] = block_prefix(8u * uword + (uint32_t)q, (uint32_t)t, s.rk);
     cnt.clear();
     for (int c = 0; c < 2; ++c) {
       if (T8 != 0u)
         sweep_phase<NP, true>(spin, best, cb, up_peer, down_peer, W, r0, nr, c, bp, s.rk, T4, T8,
-                              imp, cnt);
+                              imp, cnt, pre4, pre8, ready);
       else
         sweep_phase<NP, false>(spin, best, cb, up_peer, down_peer, W, r0, nr, c, bp, s.rk, T4, T8,
-                               imp, cnt);
-      if (c == 0) sync_group(K);
+                               imp, cnt, pre4, pre8, ready);
+      if (c == 0) {
+        group_arrive(K);
+        if (kPrefetch) ready = first_site_masks(W, r0, nr, 1, bp, s.rk, T4, T8, pre4, pre8);
+        group_wait(K);
+      }
     }
-    e += 4 * (cluster_lane_sum<NP>(cnt, part, k, K) - 2 * n);
+    ready = false;
+    e += 4 * (cluster_lane_sum<NP>(cnt, part, k, K, [&] {
+                if (more) {
+                  sweep_prefix(t + 1);
+                  if (kPrefetch)
+                    ready = first_site_masks(W, r0, nr, 0, bp, s.rk, T4n, T8n, pre4, pre8);
+                }
+              }) -
+              2 * n);
     const bool better = e < e_best;
     if (better) e_best = e;
     imp = __ballot_sync(0xFFFFFFFFu, better) & valid;
@@ -315,7 +387,7 @@ __global__ void __launch_bounds__(MAXT, 1) torus_kernel(TorusSolve s, TorusLaunc
       if (s.hit[w] >= 0 && s.hit[w] < m) m = s.hit[w];
     if (m != INT_MAX && m + 1 < t_end) t_end = m + 1;
   }
-  torus_word<NP>(s, word, k, K, l.t_begin, t_end, l.resume, smem);
+  torus_word<NP, (MAXT <= 512)>(s, word, k, K, l.t_begin, t_end, l.resume, smem);
 }
 
 template <int NP>
@@ -332,7 +404,7 @@ __global__ void __launch_bounds__(512) torus_batch_kernel(const TorusBatchItem *
     __syncthreads();
     if (it >= count) break;
     const TorusBatchItem u = items[order[it]];
-    torus_word<NP>(u.solve, u.word, 0, 1, u.t_begin, u.t_end, u.resume, smem);
+    torus_word<NP, true>(u.solve, u.word, 0, 1, u.t_begin, u.t_end, u.resume, smem);
     __syncthreads();
   }
 }
