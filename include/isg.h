@@ -84,8 +84,11 @@ isg_status isg_problem_create_edges(int32_t n, int64_t m, const int32_t *u, cons
  * E(s) = sum_(i,j) w_ij s_i s_j + sum_i h_i s_i, the form of sparse QUBO and of
  * independent-set problems (Sec. I; Sec. II.C notes they lack spin-reversal
  * symmetry).  A flip of i changes E by -2 s_i (h_i + sum_j w_ij s_j).  Such
- * instances run on the int8 colour-class kernel (ISG_KERNEL_CSR or
- * ISG_KERNEL_PLAIN; the multi-spin kernels reject them).  total_weight of
+ * instances run on the int8 colour-class kernel (ISG_KERNEL_CSR, PLAIN, and
+ * AUTO's choice) and, when every weight is +1 and deg_i + |h_i| <= 63 for all
+ * i, also on the multi-spin graph kernel (ISG_KERNEL_GRAPH_MSC, which counts
+ * h_i s_i as |h_i| extra bonds; parallel tempering uses it); the torus kernel
+ * rejects them.  total_weight of
  * isg_problem_info stays sum w, so the MaxCut identity cut = (W - E) / 2 does
  * not apply.  EINVAL as isg_problem_create_edges, with sum |w| + sum |h| >= 2^30
  * in place of the weight bound.  h is copied. */
@@ -115,8 +118,10 @@ void isg_problem_destroy(isg_problem *p);
 /* ---------------------------------------------------------------- annealing */
 
 /* Kernel families.  AUTO picks the multi-spin-coded torus kernel for tori,
- * the multi-spin-coded graph kernel for graphs whose weights are all +1 or -1
- * and whose degrees are <= 63, and the int8 CSR colour-class kernel otherwise;
+ * the multi-spin-coded graph kernel for graphs without local fields whose
+ * weights are all +1 or -1 and whose degrees are <= 63, and the int8 CSR
+ * colour-class kernel otherwise (GRAPH_MSC also takes fields when every weight
+ * is +1 and degree + |h| <= 63);
  * PLAIN runs one kernel launch per sweep (state kept in device memory between
  * launches), the one-instance-per-launch baseline of the batched form. */
 typedef enum {
@@ -173,7 +178,8 @@ isg_status isg_anneal_batch(const isg_problem *const *probs, int32_t count, int3
 
 /* Parallel tempering (Sec. II.C: replicas at different temperatures that
  * exchange configurations) on a torus instance, or on a graph with weights
- * +-1, degree <= 63 and no fields (the multi-spin graph kernel; vertex order
+ * +-1 and degree <= 63, or with local fields, weights all +1 and
+ * degree + |h| <= 63 (the multi-spin graph kernel; vertex order
  * inside the state is the library's, results come back in the caller's
  * vertex order as everywhere else).  temperatures = K slots with
  * inverse temperatures betas[K] (finite, >= 0, any order), 32 independent

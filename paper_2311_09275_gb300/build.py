@@ -19,8 +19,8 @@ BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(BUILD, "libisg.so")
 
 SOURCES = ["isg_runtime.cu", "isg_batch.cu", "isg_server.cu", "torus_msc.cu", "csr_sweep.cu",
-           "aux_kernels.cu", "isg_noalloc.cu", "csr_msc.cu", "pipe_peaks.cu",
-           "tempering.cu"]
+           "aux_kernels.cu", "isg_noalloc.cu", "csr_msc.cu", "csr_msc_fields.cu",
+           "pipe_peaks.cu", "tempering.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

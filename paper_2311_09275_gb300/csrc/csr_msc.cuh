@@ -1,0 +1,525 @@
+// csr_msc.cuh -- colour-class Metropolis sweeps on +-1-weighted sparse graphs
+// with multi-spin coding: 32 replicas per uint32 word, one bit per replica.
+//
+// Per vertex v of degree d and replica word, the kernel forms one
+// "unsatisfied bond" word per neighbour (bond (v,j) is unsatisfied when
+// w_vj s_v s_j = +1), counts them bit-sliced (U = 0..d per replica), and
+// flips a replica when its half energy change k = d - 2U is <= 0, or when its
+// Philox uniform is below the sweep's threshold for k.  The uphill replicas
+// of a vertex sit at a few levels U = 0..(d-1)/2; each occupied level costs
+// one threshold mask over the 32 uniforms.
+//
+// Layout: a cluster of K CTAs owns one replica word; every CTA keeps the
+// whole word in shared memory, updates 1/K of each colour class (contiguous
+// after the colour-major relabel) and writes each new word into all K copies
+// through distributed shared memory; one cluster barrier separates classes.
+// A CTA stages the adjacency of the slices it owns in shared memory when it
+// fits, and then keeps their best state there too.  Per-replica energy
+// changes are accumulated in bit-sliced counters (sum over accepted flips of
+// d, and of U: the change is 2 (d - 2U)) and reduced once per sweep.
+//
+// Local fields (instances whose weights are all +1): the term h s of vertex
+// v counts as |h| extra bonds to a fixed +1 spin with coupling sign(h), so d
+// becomes d + |h| and U gains |h| in the replicas where h s = +|h|; the
+// kernel is otherwise unchanged (build FIELD).
+#pragma once
+
+#include <climits>
+
+#include "isg_device.cuh"
+#include "isg_kernels.h"
+
+namespace isg {
+namespace {
+
+constexpr int kPlanesU = 6;  // per-lane bond counts up to 63 (degree <= 63)
+
+__host__ __device__ __forceinline__ size_t align16(size_t x) { return (x + 15) & ~size_t(15); }
+
+struct GmSmem {
+  size_t spin, lrow, lorig, lcol, lbest, lfield, ocls, trow, part, lane_acc, total;
+};
+
+__host__ __device__ __forceinline__ GmSmem gm_layout(int n, int K, int n_colours, int own_n,
+                                                     int own_nnz, int kmax1, bool fields) {
+  GmSmem m;
+  m.spin = 0;
+  m.lrow = align16(sizeof(uint32_t) * (size_t)n);
+  m.lorig = align16(m.lrow + (own_n ? sizeof(int32_t) * ((size_t)own_n + 1) : 0));
+  m.lcol = align16(m.lorig + sizeof(int32_t) * (size_t)own_n);
+  m.lbest = align16(m.lcol + sizeof(int32_t) * (size_t)own_nnz);
+  m.lfield = align16(m.lbest + sizeof(uint32_t) * (size_t)own_n);
+  m.ocls = align16(m.lfield + (fields ? sizeof(int32_t) * (size_t)own_n : 0));
+  m.trow = align16(m.ocls + sizeof(int32_t) * 3 * (size_t)n_colours);
+  m.part = align16(m.trow + 2 * sizeof(uint32_t) * (size_t)kmax1);
+  m.lane_acc = m.part + 2 * sizeof(int32_t) * 32 * (size_t)K;
+  m.total = align16(m.lane_acc + sizeof(int32_t) * 32);
+  return m;
+}
+
+__device__ __forceinline__ void sync_group(int K) {
+  if (K == 1)
+    __syncthreads();
+  else
+    cluster_barrier();
+}
+
+__device__ __forceinline__ void own_range(int a, int b, int k, int K, int &lo, int &hi) {
+  const int len = b - a;
+  lo = a + (int)((int64_t)len * k / K);
+  hi = a + (int)((int64_t)len * (k + 1) / K);
+}
+
+// Per-lane int32 contributions summed over the CTA and published to every CTA
+// of the cluster as part[k][lane]; ends with the group barrier.
+__device__ __forceinline__ void publish_lanes(int32_t v, int32_t *lane_acc, int32_t *part, int k,
+                                              int K) {
+  atomicAdd(&lane_acc[lane_id()], v);
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    const int32_t x = lane_acc[threadIdx.x];
+    lane_acc[threadIdx.x] = 0;
+    if (K == 1) {
+      part[threadIdx.x] = x;
+    } else {
+      for (int r = 0; r < K; ++r) peer_smem(part, (uint32_t)r)[k * 32 + threadIdx.x] = x;
+    }
+  }
+  sync_group(K);
+}
+
+__device__ __forceinline__ uint32_t initial_word(uint32_t i, uint32_t word, PhiloxKey key) {
+  uint32_t s = 0u;
+#pragma unroll
+  for (uint32_t q = 0; q < 8; ++q) {
+    const uint4 u = philox10(make_uint4(i, 0u, 8u * word + q, kTagInit), key);
+    s |= ((u.x >> 31) << (4 * q)) | ((u.y >> 31) << (4 * q + 1)) | ((u.z >> 31) << (4 * q + 2)) |
+         ((u.w >> 31) << (4 * q + 3));
+  }
+  return s;
+}
+
+// Lanes whose bit-sliced count equals v.
+__device__ __forceinline__ uint32_t count_equals(const uint32_t (&u)[kPlanesU], int v) {
+  uint32_t eq = 0xFFFFFFFFu;
+#pragma unroll
+  for (int p = 0; p < kPlanesU; ++p) eq &= ((v >> p) & 1) ? u[p] : ~u[p];
+  return eq;
+}
+
+struct GmAdj {
+  const int32_t *row, *col, *orig;
+};
+
+// The 32 uniforms of one vertex word in one sweep: Philox4x32-10 blocks
+// 8 word + q (q = 0..7) of the vertex's original id, from the sweep's block
+// prefixes.
+__device__ __forceinline__ void vertex_uniforms(uint32_t orig, const BlockPrefix (&bp)[8],
+                                                const RoundKeys &rk, uint4 (&uu)[8]) {
+  const SitePrefix sp = site_prefix(orig, rk);
+#pragma unroll
+  for (int q = 0; q < 8; ++q) uu[q] = philox10_factored(sp, bp[q], rk);
+}
+
+// Lanes where the field term h s of a vertex with word s0 is +|h| (bit 1 =
+// spin +1), counted as unsatisfied extra bonds.
+__device__ __forceinline__ uint32_t field_unsat(uint32_t s0, int32_t hv) {
+  return hv > 0 ? s0 : ~s0;
+}
+
+// One vertex of one replica word with its uniforms uu (and, FIELD, its local
+// field hv): returns the new word; accumulates the accepted flips' d and U
+// into the energy counters.
+template <int NP, bool FIELD>
+__device__ __forceinline__ uint32_t update_vertex(const uint32_t *spin, int v, int i,
+                                                  const GmAdj &a, const uint32_t *row,
+                                                  const uint4 (&uu)[8], int32_t hv,
+                                                  SlicedCounter<NP> &cd, SlicedCounter<NP> &cu) {
+  const uint32_t s0 = spin[v];
+  const int p0 = a.row[i], p1 = a.row[i + 1];
+  int d = p1 - p0;
+  uint32_t u[kPlanesU];
+#pragma unroll
+  for (int p = 0; p < kPlanesU; ++p) u[p] = 0u;
+  for (int p = p0; p < p1; ++p) {
+    const int e = a.col[p];
+    const uint32_t neg = (uint32_t)(e >> 31);            // all ones for weight -1
+    uint32_t c = ~(s0 ^ spin[e & 0x7FFFFFFF] ^ neg);     // unsatisfied bond
+#pragma unroll
+    for (int q = 0; q < kPlanesU; ++q) {
+      const uint32_t cc = u[q] & c;
+      u[q] ^= c;
+      c = cc;
+    }
+  }
+  if (FIELD && hv != 0) {
+    // |h| extra bonds, unsatisfied in the lanes of field_unsat
+    const uint32_t f = field_unsat(s0, hv);
+    const int ha = hv > 0 ? hv : -hv;
+#pragma unroll
+    for (int b = 0; b < kPlanesU; ++b) {
+      if ((ha >> b) & 1) {
+        uint32_t c = f;
+#pragma unroll
+        for (int q = b; q < kPlanesU; ++q) {
+          const uint32_t cc = u[q] & c;
+          u[q] ^= c;
+          c = cc;
+        }
+      }
+    }
+    d += ha;
+  }
+  // uphill lanes: U <= (d - 1) / 2, i.e. k = d - 2U > 0
+  const int levels = (d + 1) / 2;
+  uint32_t acc = 0xFFFFFFFFu;
+  for (int lv = 0; lv < levels; ++lv) {
+    const uint32_t eq = count_equals(u, lv);
+    if (eq == 0u) continue;
+    const uint32_t T = row[d - 2 * lv];
+    uint32_t m0 = 0u, m1 = 0u;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      uint32_t &m = (q & 1) ? m1 : m0;
+      if (uu[q].x < T) m |= 1u << (4 * q);
+      if (uu[q].y < T) m |= 2u << (4 * q);
+      if (uu[q].z < T) m |= 4u << (4 * q);
+      if (uu[q].w < T) m |= 8u << (4 * q);
+    }
+    acc &= ~eq | m0 | m1;
+  }
+  // energy change of the accepted lanes: 2 (d - 2U)
+#pragma unroll
+  for (int b = 0; b < 7; ++b)
+    if ((d >> b) & 1) cd.add_at(b, acc);
+  uint32_t ua[kPlanesU];
+#pragma unroll
+  for (int p = 0; p < kPlanesU; ++p) ua[p] = u[p] & acc;
+  cu.add_sliced(ua);
+  return s0 ^ acc;
+}
+
+// The two halves of the group barrier: work between them overlaps the wait
+// for the other CTAs (a CTA-wide barrier when the group is one CTA).
+__device__ __forceinline__ void group_arrive(int K) {
+  if (K > 1) asm volatile("barrier.cluster.arrive.release.aligned;\n" ::: "memory");
+}
+
+__device__ __forceinline__ void group_wait(int K) {
+  if (K > 1)
+    asm volatile("barrier.cluster.wait.acquire.aligned;\n" ::: "memory");
+  else
+    __syncthreads();
+}
+
+template <int NP, bool STAGED, bool FIELD>
+__device__ void gm_word(const GraphMscSolve &s, const GraphMscLaunch &L, int word, int k, int K,
+                        int t_begin, int t_end, int resume, uint8_t *smem) {
+  const int n = s.n;
+  const int nc = s.n_colours;
+  const GmSmem lay = gm_layout(n, K, nc, STAGED ? L.own_n : 0, STAGED ? L.own_nnz : 0, s.kmax1,
+                               FIELD);
+  const bool has_field = FIELD && s.field != nullptr;
+  uint32_t *spin = reinterpret_cast<uint32_t *>(smem + lay.spin);
+  // per class: this rank's slice [clo, chi) and the slot of its first vertex
+  // (the vertex itself when the adjacency is not staged)
+  int32_t *clo = reinterpret_cast<int32_t *>(smem + lay.ocls);
+  int32_t *chi = clo + nc;
+  int32_t *cob = chi + nc;
+  uint32_t *trow = reinterpret_cast<uint32_t *>(smem + lay.trow);
+  int32_t *part = reinterpret_cast<int32_t *>(smem + lay.part);
+  int32_t *lane_acc = reinterpret_cast<int32_t *>(smem + lay.lane_acc);
+  const uint32_t *wtab = s.table + (size_t)word * s.table_ws;  // this word's threshold rows
+  const PhiloxKey key{s.key0, s.key1};
+  const uint32_t uword = (uint32_t)word;
+  const int rem = s.replicas - 32 * word;
+  const uint32_t valid = rem >= 32 ? 0xFFFFFFFFu : ((1u << rem) - 1u);
+  uint32_t *gspin = s.spins + (size_t)word * n;
+  uint32_t *gbest = s.best + (size_t)word * n;
+  const int lane = (int)lane_id();
+
+  if (resume && s.has_target && s.hit[word] >= 0) return;
+  if (resume && t_begin >= t_end) return;
+  if (!resume && s.has_target && k == 0 && threadIdx.x == 0) s.hit[word] = -1;
+
+  for (int v = threadIdx.x; v < n; v += blockDim.x)
+    spin[v] = resume ? gspin[v] : initial_word((uint32_t)s.orig[v], uword, key);
+
+  if (threadIdx.x == 0) {
+    int ov = 0;
+    for (int c = 0; c < nc; ++c) {
+      int lo, hi;
+      own_range(s.class_start[c], s.class_start[c + 1], k, K, lo, hi);
+      clo[c] = lo;
+      chi[c] = hi;
+      cob[c] = STAGED ? ov : lo;
+      ov += hi - lo;
+    }
+  }
+  __syncthreads();
+  GmAdj adj;
+  // staged: best state (and fields) of the owned vertices by slot (else in
+  // global memory)
+  uint32_t *lbest = reinterpret_cast<uint32_t *>(smem + lay.lbest);
+  int32_t *lfield = reinterpret_cast<int32_t *>(smem + lay.lfield);
+  if (STAGED) {
+    int32_t *lrow = reinterpret_cast<int32_t *>(smem + lay.lrow);
+    int32_t *lorig = reinterpret_cast<int32_t *>(smem + lay.lorig);
+    int32_t *lcol = reinterpret_cast<int32_t *>(smem + lay.lcol);
+    int ebase = 0;
+    for (int c = 0; c < nc; ++c) {
+      const int lo = clo[c], hi = chi[c], ob = cob[c];
+      const int e0 = s.rowptr[lo], e1 = s.rowptr[hi];
+      for (int i = threadIdx.x; i <= hi - lo; i += blockDim.x) {
+        lrow[ob + i] = s.rowptr[lo + i] - e0 + ebase;
+        if (i < hi - lo) {
+          const int v = lo + i;
+          lorig[ob + i] = s.orig[v];
+          if (resume) lbest[ob + i] = gbest[v];
+          if (FIELD) lfield[ob + i] = has_field ? s.field[v] : 0;
+        }
+      }
+      for (int p = threadIdx.x; p < e1 - e0; p += blockDim.x) lcol[ebase + p] = s.col[e0 + p];
+      ebase += e1 - e0;
+    }
+    adj = {lrow, lcol, lorig};
+  } else {
+    adj = {s.rowptr, s.col, s.orig};
+  }
+  if (threadIdx.x < 32) lane_acc[threadIdx.x] = 0;
+  // threshold rows: two buffers, the next sweep's row prefetched a sweep ahead
+  if (t_begin < t_end)
+    for (int x = threadIdx.x; x < s.kmax1; x += blockDim.x)
+      trow[(t_begin & 1) * s.kmax1 + x] = wtab[(size_t)t_begin * s.table_ts + x];
+  // peers write into this CTA's copy of the word only after every CTA has loaded it
+  sync_group(K);
+
+  int32_t e = 0, e_best = 0;  // per lane = replica bit, kept identically by every warp
+  if (!resume) {
+    // E = sum over bonds of (+1 unsatisfied, -1 satisfied), each bond once
+    SlicedCounter<NP> cu;
+    cu.clear();
+    int32_t bonds = 0;
+    for (int c = 0; c < nc; ++c) {
+      const int lo = clo[c], hi = chi[c];
+      for (int v = lo + threadIdx.x; v < hi; v += blockDim.x) {
+        const uint32_t s0 = spin[v];
+        for (int p = s.rowptr[v]; p < s.rowptr[v + 1]; ++p) {
+          const int ee = s.col[p];
+          const int j = ee & 0x7FFFFFFF;
+          if (j <= v) continue;
+          cu.add_at(0, ~(s0 ^ spin[j] ^ (uint32_t)(ee >> 31)));
+          ++bonds;
+        }
+        if (has_field) {
+          // h s = +|h| or -|h|: |h| bonds, unsatisfied in the lanes of field_unsat
+          const int32_t hv = s.field[v];
+          const int ha = hv > 0 ? hv : -hv;
+          const uint32_t f = field_unsat(s0, hv);
+#pragma unroll
+          for (int b = 0; b < kPlanesU; ++b)
+            if ((ha >> b) & 1) cu.add_at(b, f);
+          bonds += ha;
+        }
+        if (STAGED) lbest[cob[c] + (v - lo)] = s0;
+        else gbest[v] = s0;
+      }
+    }
+    const int32_t tot = 2 * cu.warp_lane_total() - __reduce_add_sync(0xFFFFFFFFu, bonds);
+    publish_lanes(tot, lane_acc, part, k, K);
+    for (int r = 0; r < K; ++r) e += part[r * 32 + lane];
+    e_best = e;
+  } else {
+    e = s.e_cur[word * 32 + lane];
+    e_best = s.e_best[word * 32 + lane];
+  }
+
+  // Random numbers do not depend on the spins: the uniforms of a thread's
+  // first vertex of the next class (or of the next sweep's first class) are
+  // drawn between the arrival at the group barrier and the wait for it.
+  BlockPrefix bp[8];
+  uint4 uu[8];
+  bool ready = false;  // uu holds the uniforms of this thread's next vertex
+  auto sweep_prefix = [&](int tt) {
+#pragma unroll
+    for (int q = 0; q < 8; ++q) bp[q] = block_prefix(8u * uword + (uint32_t)q, (uint32_t)tt, s.rk);
+  };
+  auto draw_first = [&](int c) {
+    ready = clo[c] + (int)threadIdx.x < chi[c];
+    if (ready) vertex_uniforms((uint32_t)adj.orig[cob[c] + threadIdx.x], bp, s.rk, uu);
+  };
+  if (t_begin < t_end) {
+    sweep_prefix(t_begin);
+    draw_first(0);
+  }
+
+  int t = t_begin;
+  int hit = -1;
+  uint32_t imp = 0u;  // replicas whose best state is the state at the start of sweep t
+  const int x0 = (int)threadIdx.x, x1 = (int)(threadIdx.x + blockDim.x);
+  for (; t < t_end; ++t) {
+    const uint32_t *row = trow + (t & 1) * s.kmax1;
+    // next sweep's thresholds (kmax1 <= 64 <= 2 x threads)
+    const bool more = t + 1 < t_end;
+    const uint32_t *gnext = wtab + (size_t)(t + 1) * s.table_ts;
+    const uint32_t p0 = (more && x0 < s.kmax1) ? gnext[x0] : 0u;
+    const uint32_t p1 = (more && x1 < s.kmax1) ? gnext[x1] : 0u;
+    SlicedCounter<NP> cd, cu;
+    cd.clear();
+    cu.clear();
+    for (int c = 0; c < nc; ++c) {
+      const int lo = clo[c], hi = chi[c], ob = cob[c];
+      for (int v = lo + threadIdx.x; v < hi; v += blockDim.x) {
+        const int i = ob + (v - lo);
+        // improved replicas take their best state from v as it stood at the
+        // end of the previous sweep (v has not been updated since)
+        if (imp != 0u) {
+          if (STAGED) lbest[i] = (lbest[i] & ~imp) | (spin[v] & imp);
+          else gbest[v] = (gbest[v] & ~imp) | (spin[v] & imp);
+        }
+        if (!ready) vertex_uniforms((uint32_t)adj.orig[i], bp, s.rk, uu);
+        ready = false;
+        const int32_t hv = !has_field ? 0 : (STAGED ? lfield[i] : __ldg(&s.field[v]));
+        const uint32_t sn = update_vertex<NP, FIELD>(spin, v, i, adj, row, uu, hv, cd, cu);
+        if (K == 1) {
+          spin[v] = sn;
+        } else {
+          for (int r = 0; r < K; ++r) peer_smem(spin, (uint32_t)r)[v] = sn;
+        }
+      }
+      if (c + 1 < nc) {
+        group_arrive(K);
+        draw_first(c + 1);
+        group_wait(K);
+      }
+    }
+    if (more) {
+      uint32_t *nrow = trow + ((t + 1) & 1) * s.kmax1;
+      if (x0 < s.kmax1) nrow[x0] = p0;
+      if (x1 < s.kmax1) nrow[x1] = p1;
+    }
+    // per-lane energy change, summed over the CTA and published to every CTA
+    int32_t *pbuf = part + ((t + 1) & 1) * 32 * K;
+    atomicAdd(&lane_acc[lane], 2 * (cd.warp_lane_total() - 2 * cu.warp_lane_total()));
+    __syncthreads();
+    if (threadIdx.x < 32) {
+      const int32_t x = lane_acc[threadIdx.x];
+      lane_acc[threadIdx.x] = 0;
+      if (K == 1) {
+        pbuf[threadIdx.x] = x;
+      } else {
+        for (int r = 0; r < K; ++r) peer_smem(pbuf, (uint32_t)r)[k * 32 + threadIdx.x] = x;
+      }
+    }
+    group_arrive(K);
+    if (more) {
+      sweep_prefix(t + 1);
+      draw_first(0);
+    }
+    group_wait(K);
+    int32_t dsum = 0;
+    for (int r = 0; r < K; ++r) dsum += pbuf[r * 32 + lane];
+    e += dsum;
+    const bool better = e < e_best;
+    if (better) e_best = e;
+    imp = __ballot_sync(0xFFFFFFFFu, better) & valid;
+    if (s.has_target) {
+      const int32_t mn =
+          __reduce_min_sync(0xFFFFFFFFu, ((valid >> lane) & 1u) ? e_best : INT_MAX);
+      if (mn <= s.target) {
+        hit = t;
+        ++t;
+        break;
+      }
+    }
+  }
+
+  // every update of the cluster precedes the last group barrier
+  for (int c = 0; c < nc; ++c) {
+    const int lo = clo[c], hi = chi[c];
+    for (int v = lo + threadIdx.x; v < hi; v += blockDim.x) {
+      const uint32_t x = spin[v];
+      gspin[v] = x;
+      if (STAGED) gbest[v] = (lbest[cob[c] + (v - lo)] & ~imp) | (x & imp);
+      else if (imp != 0u) gbest[v] = (gbest[v] & ~imp) | (x & imp);
+    }
+  }
+  if (k == 0) {
+    if (threadIdx.x < 32) {
+      s.e_cur[word * 32 + lane] = e;
+      s.e_best[word * 32 + lane] = e_best;
+    }
+    if (threadIdx.x == 0) {
+      if (s.has_target && hit >= 0) s.hit[word] = hit;
+      s.done[word] = t;
+    }
+  }
+}
+
+template <int NP, bool STAGED, bool FIELD>
+__global__ void __launch_bounds__(512) gm_kernel(GraphMscSolve s, GraphMscLaunch l) {
+  extern __shared__ __align__(16) uint8_t smem[];
+  const int K = l.cluster;
+  const int k = (int)(blockIdx.x % K);
+  const int word = (int)(blockIdx.x / K);
+  int t_end = l.t_end;
+  if (l.stop_from_hits) {
+    int m = INT_MAX;
+    for (int w = 0; w < s.words; ++w)
+      if (s.hit[w] >= 0 && s.hit[w] < m) m = s.hit[w];
+    if (m != INT_MAX && m + 1 < t_end) t_end = m + 1;
+  }
+  gm_word<NP, STAGED, FIELD>(s, l, word, k, K, l.t_begin, t_end, l.resume, smem);
+}
+
+template <typename Kern>
+cudaError_t launch_gm(Kern kernel, int grid, const GraphMscSolve &s, const GraphMscLaunch &l,
+                      size_t smem, cudaStream_t stream) {
+  cudaError_t err = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+  if (err == cudaSuccess && l.cluster > 8)
+    err = cudaFuncSetAttribute(kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+  if (err != cudaSuccess) return err;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(l.threads);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = stream;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = l.cluster;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kernel, s, l);
+}
+
+// Launch of the sweep kernel for the solve's shape; FIELD selects the build
+// that adds local fields.
+template <bool FIELD>
+cudaError_t gm_launch_impl(const GraphMscSolve &s, const GraphMscLaunch &l, cudaStream_t stream) {
+  const bool staged = l.own_n > 0;
+  const size_t smem = gm_layout(s.n, l.cluster, s.n_colours, staged ? l.own_n : 0,
+                                staged ? l.own_nnz : 0, s.kmax1, FIELD)
+                          .total;
+  const int grid = s.words * l.cluster;
+  switch (l.planes * 2 + (staged ? 1 : 0)) {
+#define ISG_GM_CASE(NPV)                                                                     \
+  case NPV * 2 + 1:                                                                          \
+    return launch_gm(gm_kernel<NPV, true, FIELD>, grid, s, l, smem, stream);                 \
+  case NPV * 2:                                                                              \
+    return launch_gm(gm_kernel<NPV, false, FIELD>, grid, s, l, smem, stream);
+    ISG_GM_CASE(6) ISG_GM_CASE(8) ISG_GM_CASE(10) ISG_GM_CASE(12) ISG_GM_CASE(14)
+#undef ISG_GM_CASE
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+}  // namespace
+
+// The local-field builds (compiled in their own translation unit).
+cudaError_t gm_launch_fields(const GraphMscSolve &s, const GraphMscLaunch &l,
+                             cudaStream_t stream);
+
+}  // namespace isg

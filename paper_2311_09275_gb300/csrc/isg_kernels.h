@@ -140,9 +140,10 @@ cudaError_t csr_batch_launch(const CsrBatchItem *items_dev, const int32_t *count
                              int32_t threads, size_t smem, cudaStream_t stream);
 
 // ---------------------------------------------------------------- graphs, multi-spin coded
-// +-1-weighted graphs of degree <= 63: replica words like the torus kernel,
-// vertices relabelled colour-major like the colour-class kernel.  State
-// arrays are [word][n] in relabelled order.
+// +-1-weighted graphs (all weights +1 when there are local fields) with
+// degree + |h| <= 63: replica words like the torus kernel, vertices
+// relabelled colour-major like the colour-class kernel.  State arrays are
+// [word][n] in relabelled order.
 struct GraphMscSolve {
   int32_t n;
   int32_t n_colours;
@@ -150,6 +151,7 @@ struct GraphMscSolve {
   const int32_t *rowptr;       // [n + 1]
   const int32_t *col;          // relabelled neighbour ids, bit 31 set for weight -1
   const int32_t *orig;         // [n]
+  const int32_t *field;        // [n] local fields h (relabelled order), or nullptr
   const uint32_t *table;       // thresholds by half energy change k of word w, sweep t at
                                // table[w * table_ws + t * table_ts + k]
   int32_t table_ws, table_ts;  // annealing: 0, kmax1; tempering: kmax1, 0
@@ -189,8 +191,9 @@ struct GraphMscItem {
   int32_t resume;
 };
 
+// fields: the instance has local fields (staged slices then hold them too).
 size_t gm_smem_bytes(int32_t n, int32_t cluster, int32_t n_colours, int32_t own_n,
-                     int32_t own_nnz, int32_t kmax1);
+                     int32_t own_nnz, int32_t kmax1, bool fields);
 // Smallest supported plane count holding counts up to max_count (-1: none).
 int gm_planes(int32_t max_count);
 cudaError_t gm_launch(const GraphMscSolve &s, const GraphMscLaunch &l, cudaStream_t stream);

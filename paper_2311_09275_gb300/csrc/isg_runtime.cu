@@ -151,6 +151,7 @@ isg_status finish_problem(isg_problem *p) {
   // per-lane sums, which the packed counts of modes 0 and 1 do not carry)
   p->mode = (max_deg > 255 || !p->field.empty()) ? 2 : (all_pos ? 0 : (all_unit ? 1 : 2));
   p->dmax = (int32_t)max_deg;
+  p->unit_pos = all_pos;
   if (p->mode == 1)
     for (size_t o = 0; o < p->col_r.size(); ++o)
       if (p->wt_r[o] < 0) p->col_r[o] = (int32_t)((uint32_t)p->col_r[o] | 0x80000000u);
@@ -505,25 +506,26 @@ int max_class_size(const isg_problem *p) {
   return m;
 }
 
-// The multi-spin graph kernel needs +-1 weights and degrees <= 63.
+// The multi-spin graph kernel needs +-1 weights (all +1 with local fields,
+// which it counts as |h| extra bonds) and degree + |h| <= 63 (= kmax).
 bool graph_msc_ok(const isg_problem *p) {
-  return p->mode <= 1 && p->dmax <= 63 && p->field.empty();
+  return p->kmax <= 63 && (p->field.empty() ? p->mode <= 1 : p->unit_pos);
 }
 
 // Shared memory of the graph kernel; staged = adjacency in shared memory.
 size_t gm_bytes(const isg_problem *p, int K, bool staged) {
   int own_n = 0, own_nnz = 0;
   if (staged) csr_own_sizes(p, K, own_n, own_nnz);
-  return gm_smem_bytes(p->n, K, p->n_colours, own_n, own_nnz, p->kmax + 1);
+  return gm_smem_bytes(p->n, K, p->n_colours, own_n, own_nnz, p->kmax + 1, !p->field.empty());
 }
 
 // Energy-counter planes of the graph kernel: a thread's accepted degree sum
-// per sweep is at most (its vertices per sweep) x (max degree).
+// per sweep is at most (its vertices per sweep) x (max degree + |h|).
 int gm_planes_for(const isg_problem *p, int K, int threads) {
   int own_n = 0, own_nnz = 0;
   csr_own_sizes(p, K, own_n, own_nnz);
   const int64_t per_thread = (own_n + threads - 1) / threads + p->n_colours;
-  const int64_t cnt = per_thread * std::max(1, p->dmax);
+  const int64_t cnt = per_thread * std::max(1, p->kmax);
   return cnt >= (1 << 30) ? -1 : gm_planes((int32_t)cnt);
 }
 
@@ -600,6 +602,7 @@ GraphMscSolve make_gm_solve(const isg_problem *p, const DeviceProblem *dp, const
   s.rowptr = dp->rowptr;
   s.col = dp->col;
   s.orig = dp->orig;
+  s.field = dp->field_r;
   s.table = r->d_table;
   s.kmax1 = p->kmax + 1;
   s.table_ws = 0;
@@ -717,11 +720,13 @@ void table_levels(const isg_problem *p, bool torus_words, std::vector<int32_t> &
 }  // namespace
 
 // The persistent graph-unit kernel runs a whole replica word in one CTA: it
-// needs +-1 weights, degree <= 63, and counts that fit its fixed counter planes.
+// needs an instance without fields that the multi-spin graph kernel takes
+// (field instances are served as int8 quads, as AUTO runs them), and counts
+// that fit its fixed counter planes.
 bool served_graph_msc(const isg_problem *p, int threads) {
-  if (!graph_msc_ok(p)) return false;
+  if (!graph_msc_ok(p) || !p->field.empty()) return false;
   const int64_t per_thread = (p->n + threads - 1) / threads + p->n_colours;
-  return per_thread * std::max(1, p->dmax) < (int64_t(1) << kGraphMscBatchPlanes);
+  return per_thread * std::max(1, p->kmax) < (int64_t(1) << kGraphMscBatchPlanes);
 }
 
 // ------------------------------------------------------------------ anneal
@@ -744,15 +749,19 @@ isg_status anneal_impl(const isg_problem *p, int32_t R, const double *betas, int
                      shape_lookup(p, R, t_kernel, t_cluster, t_threads, t_qpc);
   if (tuned) kernel = t_kernel;
   if (kernel == ISG_KERNEL_AUTO)
+    // instances with fields run faster on the int8 kernel (d + |h| costs the
+    // multi-spin kernel a threshold mask per level)
     kernel = p->torus ? ISG_KERNEL_TORUS_MSC
-                      : (graph_msc_ok(p) ? ISG_KERNEL_GRAPH_MSC : ISG_KERNEL_CSR);
+                      : (graph_msc_ok(p) && p->field.empty() ? ISG_KERNEL_GRAPH_MSC
+                                                             : ISG_KERNEL_CSR);
   if (kernel < ISG_KERNEL_AUTO || kernel > ISG_KERNEL_GRAPH_MSC)
     return fail(ISG_EINVAL, "unknown kernel %d", kernel);
   if (kernel == ISG_KERNEL_TORUS_MSC && !p->torus)
     return fail(ISG_EINVAL, "the multi-spin-coded torus kernel needs a torus instance");
   if (kernel == ISG_KERNEL_GRAPH_MSC && !graph_msc_ok(p))
     return fail(ISG_EINVAL,
-                "the multi-spin-coded graph kernel needs weights +-1, degree <= 63 and no fields");
+                "the multi-spin-coded graph kernel needs weights +-1 (all +1 with local fields) "
+                "and degree + |h| <= 63");
   const bool plain = kernel == ISG_KERNEL_PLAIN;
   const bool gm = kernel == ISG_KERNEL_GRAPH_MSC;
   const bool tmsc = p->torus && (kernel == ISG_KERNEL_TORUS_MSC || plain);
@@ -888,8 +897,8 @@ isg_status tempering_impl(const isg_problem *p, int32_t K, const double *betas, 
   const bool gm = !p->torus;
   if (gm && !graph_msc_ok(p))
     return fail(ISG_EINVAL,
-                "parallel tempering needs a torus, or a graph with weights +-1, degree <= 63 "
-                "and no fields");
+                "parallel tempering needs a torus, or a graph with weights +-1 (all +1 with "
+                "local fields) and degree + |h| <= 63");
   if (K < 1 || K > 4096) return fail(ISG_EINVAL, "temperatures must be in [1, 4096]");
   if (rounds < 1 || per_round < 1 || (int64_t)rounds * per_round > INT32_MAX)
     return fail(ISG_EINVAL, "rounds and sweeps_per_round must be >= 1 (product < 2^31)");

@@ -45,6 +45,7 @@ struct isg_problem {
   int32_t kmax = 0;                        // max_i (sum_j |w_ij| + |h_i|)
   int32_t mode = 2;                        // weights: 0 all +1, 1 all +-1, 2 general (CsrSolve)
   int32_t dmax = 0;                        // largest degree
+  bool unit_pos = false;                   // every weight is +1
   std::vector<int8_t> jr, jd;              // torus couplings
   std::vector<int64_t> rowptr;             // CSR, original ids, rows sorted
   std::vector<int32_t> col, wt;

@@ -326,6 +326,7 @@ void fill_gm_unit(GraphMscItem &it, const Slot *sl, int32_t word, int32_t t_begi
   s.rowptr = sl->dp->rowptr;
   s.col = sl->dp->col;
   s.orig = sl->dp->orig;
+  s.field = sl->dp->field_r;
   s.table = r->d_table;
   s.kmax1 = p->kmax + 1;
   s.table_ws = 0;
@@ -377,7 +378,8 @@ cudaError_t run_units(isg_server *s, const std::vector<Slot *> &slots,
       } else if (sl->res->msc) {
         fill_gm_unit(s->h_g[ig], sl, u, sl->t, t_end[k]);
         ord_g.emplace_back(p->n, (int32_t)ig++);
-        smem_g = std::max(smem_g, gm_smem_bytes(p->n, 1, p->n_colours, 0, 0, p->kmax + 1));
+        smem_g = std::max(smem_g, gm_smem_bytes(p->n, 1, p->n_colours, 0, 0, p->kmax + 1,
+                                                !p->field.empty()));
       } else {
         fill_csr_unit(s->h_c[ic], sl, u, sl->t, t_end[k]);
         ord_c.emplace_back(p->n, (int32_t)ic++);

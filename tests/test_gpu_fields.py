@@ -1,7 +1,10 @@
-"""Local fields on the GPU (int8 colour-class kernel) against the oracle,
-element by element: E = sum w s s + sum h s; independent-set instances,
-general weights with fields, +-1 weights with fields, targets, isg_energy,
-the served path, and the multi-spin kernels' refusal."""
+"""Local fields on the GPU against the oracle, element by element:
+E = sum w s s + sum h s.  The int8 colour-class kernel (any weights) and the
+multi-spin graph kernel (all weights +1, degree + |h| <= 63): independent-set
+instances, general weights with fields, +-1 weights with fields, targets,
+isg_energy, the served path, parallel tempering, and the refusals."""
+import functools
+
 import numpy as np
 import pytest
 
@@ -40,6 +43,13 @@ def pm1_with_fields(seed=5):
     return I.Graph(g.n, g.u, g.v, w, h)
 
 
+def unit_with_fields(seed=6):
+    """All weights +1, fields of both signs and zero (|h| <= 3)."""
+    g = I.random_graph(400, 1000, seed)
+    h = np.array([(-3, 0, 2, -1, 1, 3, 0, -2)[i % 8] for i in range(g.n)], np.int32)
+    return I.Graph(g.n, g.u, g.v, np.ones(g.m, np.int32), h)
+
+
 CASES = {"mis": mis, "general": general_with_fields, "pm1": pm1_with_fields}
 
 
@@ -54,6 +64,34 @@ def test_fields_csr_bit_exact(isg, name, R, cluster, qpc):
     assert_same(res, orc)
 
 
+@pytest.mark.parametrize("name", ["mis", "unit"])
+@pytest.mark.parametrize("R,cluster,threads", [(1, 1, 64), (33, 3, 128), (70, 8, 96), (64, 0, 0)])
+def test_fields_graph_msc_bit_exact(isg, name, R, cluster, threads):
+    """Multi-spin graph kernel with local fields (|h| extra bonds per vertex)."""
+    g = mis() if name == "mis" else unit_with_fields()
+    betas = I.geometric_betas(0.1, 5.0, 120)
+    orc = oracle.anneal(oracle.csr_of(g), R, betas, 19, check_energy=True)
+    res = isg.isg_anneal(isg.problem_of(g), R, betas, 19, kernel=4, cluster_ctas=cluster,
+                         threads=threads)
+    assert_same(res, orc)
+    assert res.stats()["kernel"] == 4 and res.stats()["staged"] == 1
+
+
+@pytest.mark.parametrize("R,cluster,threads", [(40, 1, 256), (70, 4, 512)])
+def test_fields_graph_msc_unstaged_bit_exact(isg, R, cluster, threads):
+    """Fields read from global memory: 12,000 vertices of mean degree 25 with
+    |h| <= 2 (adjacency too large to stage)."""
+    g = I.random_graph(12000, 150000, 13)
+    h = np.array([(1, -2, 0, 2, -1)[i % 5] for i in range(g.n)], np.int32)
+    g = I.Graph(g.n, g.u, g.v, np.ones(g.m, np.int32), h)
+    betas = I.geometric_betas(0.1, 5.0, 12)
+    orc = oracle.anneal(oracle.csr_of(g), R, betas, 23, check_energy=True)
+    res = isg.isg_anneal(isg.problem_of(g), R, betas, 23, kernel=4, cluster_ctas=cluster,
+                         threads=threads)
+    assert res.stats()["staged"] == 0
+    assert_same(res, orc)
+
+
 def test_fields_auto_and_plain_kernels(isg):
     g = mis(300, 5.0, 8)
     betas = I.geometric_betas(0.1, 5.0, 60)
@@ -62,9 +100,35 @@ def test_fields_auto_and_plain_kernels(isg):
     auto = isg.isg_anneal(p, 24, betas, 2)
     assert auto.stats()["kernel"] == 2          # fields -> int8 colour-class kernel
     assert_same(auto, orc)
+    assert_same(isg.isg_anneal(p, 24, betas, 2, kernel=4), orc)
     assert_same(isg.isg_anneal(p, 24, betas, 2, kernel=3), orc)
-    with pytest.raises(isg.IsgError):
-        isg.isg_anneal(p, 24, betas, 2, kernel=4)  # the multi-spin kernel has no fields
+
+
+def test_fields_outside_graph_msc(isg):
+    """+-1 weights with fields, or degree + |h| > 63: the multi-spin kernel
+    refuses and the automatic choice is the int8 kernel."""
+    betas = I.geometric_betas(0.1, 5.0, 40)
+    g = I.random_graph(200, 500, 3)
+    big = I.Graph(g.n, g.u, g.v, np.ones(g.m, np.int32),
+                  np.where(np.arange(g.n) == 7, 60, 1).astype(np.int32))
+    for inst in (pm1_with_fields(), big):
+        p = isg.problem_of(inst)
+        with pytest.raises(isg.IsgError):
+            isg.isg_anneal(p, 8, betas, 2, kernel=4)
+        res = isg.isg_anneal(p, 8, betas, 2)
+        assert res.stats()["kernel"] == 2
+        assert_same(res, oracle.anneal(oracle.csr_of(inst), 8, betas, 2))
+
+
+@pytest.mark.parametrize("R", [20, 70])
+def test_fields_graph_msc_target_stop(isg, R):
+    g = mis(500, 6.0, 21)
+    betas = I.geometric_betas(0.1, 5.0, 300)
+    c = oracle.csr_of(g)
+    target = int(oracle.anneal(c, R, betas, 4).e_best.min()) + 2
+    orc = oracle.anneal(c, R, betas, 4, target=target)
+    res = isg.isg_anneal(isg.problem_of(g), R, betas, 4, target=target, kernel=4, cluster_ctas=2)
+    assert_same(res, orc)
 
 
 @pytest.mark.parametrize("R", [8, 40])
@@ -105,8 +169,10 @@ def test_fields_independent_set_valid_and_near_maximum(isg):
     assert be == -2 * int(chosen.sum()) - gg.m + gg.n
 
 
-def test_fields_served_equals_solo(isg):
-    g = general_with_fields(12)
+@pytest.mark.parametrize("make", [lambda: general_with_fields(12), lambda: mis(400, 6.0, 12)])
+def test_fields_served_equals_solo(isg, make):
+    """Served int8 quads of field instances equal one-instance solves."""
+    g = make()
     p = isg.problem_of(g)
     betas = I.geometric_betas(0.1, 5.0, 150)
     srv = isg.Server(1 << 30, 4, 40)
@@ -118,3 +184,26 @@ def test_fields_served_equals_solo(isg):
     for x, y in zip(got[1].final(), solo.final()):
         assert np.array_equal(x, y)
     assert np.array_equal(got[1].best_all(), solo.best_all())
+
+
+@functools.lru_cache(maxsize=1)
+def independent_set_10000_oracle(reps):
+    sv = I.independent_set_10000()
+    return oracle.anneal(oracle.csr_of(sv.problem), list(reps), sv.betas, sv.seed)
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("shape", [{}, {"kernel": 4, "cluster_ctas": 12, "threads": 512},
+                                   {"kernel": 2, "cluster_ctas": 4, "threads": 512,
+                                    "quads_per_cta": 2}])
+def test_independent_set_10000_full_size_sampled(isg, shape):
+    """The benchmark's independent-set workload (10,000 vertices, 256 replicas,
+    10,000 sweeps) on both kernel families: sampled replicas equal the oracle,
+    and every replica's energy equals isg_energy of its state."""
+    sv = I.independent_set_10000()
+    p = isg.problem_of(sv.problem)
+    res = isg.isg_anneal(p, sv.replicas, sv.betas, sv.seed, **shape)
+    reps = (0, 5, 31, 32, 200, 255)
+    assert_same(res, independent_set_10000_oracle(reps), reps=list(reps))
+    spins, e, _ = res.final()
+    assert np.array_equal(isg.isg_energy(p, spins), e)

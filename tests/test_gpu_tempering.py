@@ -114,6 +114,9 @@ def _pm1(n, m, seed):
     (lambda: I.random_graph(500, 700, 3), [0.2, 0.6, 1.2, 2.0], 6, 3, 0, 0),
     (lambda: _pm1(400, 1000, 4), [0.3, 0.5, 0.9], 5, 2, 3, 128),
     (lambda: I.random_graph(10000, 9999, 1), I.geometric_betas(0.2, 3.0, 6), 3, 4, 0, 0),
+    # local fields (independent set): exchanges see E = sum s s + sum h s
+    (lambda: I.independent_set_instance(I.geometric_graph(400, 6.0, 5)), [0.3, 0.8, 1.5, 2.5],
+     5, 3, 2, 128),
 ])
 def test_tempering_on_graphs_bit_exact(isg, make, betas, rounds, per_round, cluster, threads):
     g = make()
