@@ -18,7 +18,10 @@
  * heuristics spend their time in: simulated annealing by single-spin-flip
  * Metropolis sweeps over R independent replicas.  Sweep t (0-based) visits
  * the colour classes in ascending order (torus: colour (r + c) mod 2; graphs:
- * greedy colouring by ascending vertex id) and, for every vertex i of the
+ * the smallest-last colouring -- repeatedly remove a vertex of smallest
+ * remaining degree, the smallest id among ties, colour in the reverse of that
+ * order with the smallest colour no coloured neighbour has, and number the
+ * classes by their smallest vertex) and, for every vertex i of the
  * class and every replica, computes h_i = sum_j w_ij s_j and the energy change
  * d = -2 s_i h_i of flipping s_i; the flip is taken when d <= 0, or when
  * u < floor(2^32 exp(-beta_t d)) for the replica's 32-bit uniform u.  The

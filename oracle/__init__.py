@@ -14,7 +14,8 @@ Readings of the paper used here (the paper withholds its method, Sec. III.A):
 * E(s) = sum_{(i,j)} w_ij s_i s_j is minimised, so the MaxCut value of
   Sec. II.A is cut = (W_tot - E) / 2.
 * One sweep visits every vertex once, colour class by colour class in
-  ascending class order; the flip of vertex i changes E by d = -2 s_i h_i with
+  ascending class order (classes: the checkerboard on a torus, the
+  smallest-last colouring on a graph, Csr.colouring); the flip of vertex i changes E by d = -2 s_i h_i with
   h_i = sum_j w_ij s_j and is accepted when d <= 0 or when the replica's
   32-bit uniform is below floor(2^32 exp(-beta_t d)).
 * A replica's best state is checked at sweep boundaries only (strict
@@ -66,6 +67,8 @@ def _load():
         lib.orc_torus_edges.argtypes = [i32, i32, P, P, P, P, P]
         lib.orc_greedy_colouring.argtypes = [i32, P, P, P]
         lib.orc_greedy_colouring.restype = i32
+        lib.orc_smallest_last_colouring.argtypes = [i32, P, P, P]
+        lib.orc_smallest_last_colouring.restype = i32
         lib.orc_accept_table.argtypes = [i32, P, i32, P]
         lib.orc_energy.argtypes = [i32, P, P, P, P, P]
         lib.orc_energy.restype = i64
@@ -106,6 +109,7 @@ class Csr:
     def __init__(self, n: int, u, v, w, h=None):
         u, v, w = _arr(u, np.int32), _arr(v, np.int32), _arr(w, np.int32)
         self.field = None if h is None else _arr(h, np.int32)
+        self.torus_shape = None  # (L, W) when built by torus_csr
         if self.field is not None and self.field.shape != (n,):
             raise ValueError("fields need one entry per vertex")
         m = int(u.shape[0])
@@ -131,6 +135,18 @@ class Csr:
     def greedy_colouring(self):
         colour = np.zeros(self.n, dtype=np.int32)
         nc = _load().orc_greedy_colouring(self.n, _p(self.rowptr), _p(self.col), _p(colour))
+        return colour, int(nc)
+
+    def colouring(self):
+        """The sweep's colour classes: on a torus the checkerboard (r + c) mod 2;
+        on a graph the smallest-last colouring with classes numbered by their
+        smallest vertex (orc_smallest_last_colouring)."""
+        if self.torus_shape is not None:
+            r, c = np.divmod(np.arange(self.n), self.torus_shape[1])
+            return ((r + c) % 2).astype(np.int32), 2
+        colour = np.zeros(self.n, dtype=np.int32)
+        nc = _load().orc_smallest_last_colouring(self.n, _p(self.rowptr), _p(self.col),
+                                                 _p(colour))
         return colour, int(nc)
 
     def kmax(self) -> int:
@@ -168,7 +184,9 @@ def torus_csr(L: int, W: int, j_right, j_down) -> Csr:
     v = np.zeros(2 * n, dtype=np.int32)
     w = np.zeros(2 * n, dtype=np.int32)
     _load().orc_torus_edges(L, W, _p(jr), _p(jd), _p(u), _p(v), _p(w))
-    return Csr(n, u, v, w)
+    c = Csr(n, u, v, w)
+    c.torus_shape = (L, W)
+    return c
 
 
 def csr_of(problem) -> Csr:
@@ -215,10 +233,10 @@ def anneal(csr: Csr, replicas, betas, seed: int, colour=None, target=None,
     """Run the colour-ordered Metropolis schedule on the listed replicas.
 
     ``replicas`` is an int (all replicas 0..R-1) or a list of replica indices.
-    ``colour`` defaults to the oracle's greedy colouring.
+    ``colour`` defaults to the oracle's smallest-last colouring (Csr.colouring).
     """
     if colour is None:
-        colour, nc = csr.greedy_colouring()
+        colour, nc = csr.colouring()
     else:
         colour = _arr(colour, np.int32)
         nc = int(colour.max()) + 1
@@ -268,7 +286,7 @@ def parallel_tempering(csr: Csr, betas, rounds: int, per_round: int, seed: int, 
     """Parallel tempering over len(betas) slots x 32 chains, with Houdayer
     cluster moves on the last icm_slots slots (see isg_oracle.h)."""
     if colour is None:
-        colour, nc = csr.greedy_colouring()
+        colour, nc = csr.colouring()
     else:
         colour = _arr(colour, np.int32)
         nc = int(colour.max()) + 1

@@ -150,6 +150,51 @@ int32_t orc_greedy_colouring(int32_t n, const int64_t *rowptr, const int32_t *co
     return n_colours;
 }
 
+int32_t orc_smallest_last_colouring(int32_t n, const int64_t *rowptr, const int32_t *col,
+                                    int32_t *colour) {
+    int64_t *deg = (int64_t *)malloc(sizeof(int64_t) * ((size_t)n + 1));
+    int32_t *order = (int32_t *)malloc(sizeof(int32_t) * ((size_t)n + 1));
+    uint8_t *removed = (uint8_t *)calloc((size_t)n + 1, 1);
+    int32_t *used = (int32_t *)malloc(sizeof(int32_t) * ((size_t)n + 1));
+    for (int32_t v = 0; v < n; ++v) deg[v] = rowptr[v + 1] - rowptr[v];
+    /* removal order: each step scans every vertex still present for the
+     * smallest remaining degree (first, i.e. smallest, id among ties) */
+    for (int32_t step = 0; step < n; ++step) {
+        int32_t best = -1;
+        for (int32_t v = 0; v < n; ++v)
+            if (!removed[v] && (best < 0 || deg[v] < deg[best])) best = v;
+        removed[best] = 1;
+        order[step] = best;
+        for (int64_t p = rowptr[best]; p < rowptr[best + 1]; ++p)
+            if (!removed[col[p]]) --deg[col[p]];
+    }
+    /* colour in reverse removal order: smallest colour no coloured neighbour has */
+    for (int32_t v = 0; v < n; ++v) colour[v] = -1;
+    for (int32_t c = 0; c <= n; ++c) used[c] = -1;
+    int32_t n_colours = 0;
+    for (int32_t step = n - 1; step >= 0; --step) {
+        const int32_t v = order[step];
+        for (int64_t p = rowptr[v]; p < rowptr[v + 1]; ++p)
+            if (colour[col[p]] >= 0) used[colour[col[p]]] = v;
+        int32_t c = 0;
+        while (used[c] == v) ++c;
+        colour[v] = c;
+        if (c + 1 > n_colours) n_colours = c + 1;
+    }
+    /* number the classes by their smallest vertex */
+    int32_t *rename = used;
+    for (int32_t c = 0; c < n_colours; ++c) rename[c] = -1;
+    int32_t next = 0;
+    for (int32_t v = 0; v < n; ++v)
+        if (rename[colour[v]] < 0) rename[colour[v]] = next++;
+    for (int32_t v = 0; v < n; ++v) colour[v] = rename[colour[v]];
+    free(deg);
+    free(order);
+    free(removed);
+    free(used);
+    return n_colours;
+}
+
 /* ------------------------------------------------------------------------ */
 /* Acceptance table: a move that raises the energy by d > 0 is accepted with
  * probability exp(-beta_t d); the threshold on a 32-bit uniform u is

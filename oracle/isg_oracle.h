@@ -46,6 +46,16 @@ void orc_torus_edges(int32_t L, int32_t W, const int8_t *j_right, const int8_t *
  * not used by a neighbour u < v.  Returns the number of colours. */
 int32_t orc_greedy_colouring(int32_t n, const int64_t *rowptr, const int32_t *col, int32_t *colour);
 
+/* Smallest-last colouring (Matula and Beck, J. ACM 30(3), 1983), the colour
+ * classes of the sweep on graphs: repeatedly remove, from the graph that is
+ * left, a vertex of smallest remaining degree (the smallest id among ties);
+ * colour the vertices in the reverse of that removal order, each with the
+ * smallest c >= 0 that no already coloured neighbour has; then number the
+ * classes in increasing order of their smallest vertex.  At most degeneracy + 1
+ * colours.  Returns the number of colours. */
+int32_t orc_smallest_last_colouring(int32_t n, const int64_t *rowptr, const int32_t *col,
+                                    int32_t *colour);
+
 /* Acceptance thresholds: table[t*(kmax+1) + k] = min(floor(2^32 exp(-beta_t * 2k)), 2^32-1)
  * for k = 0..kmax (energy increase d = 2k), in FP64. */
 void orc_accept_table(int32_t sweeps, const double *betas, int32_t kmax, uint32_t *table);

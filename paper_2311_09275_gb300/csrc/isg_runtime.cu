@@ -1,5 +1,5 @@
 // isg_runtime.cu -- host runtime behind the C ABI of include/isg.h: instance
-// building and validation, greedy colouring and colour-major relabelling,
+// building and validation, smallest-last colouring and colour-major relabelling,
 // acceptance tables, device residency, launch orchestration, results.
 #include <algorithm>
 #include <cmath>
@@ -10,6 +10,7 @@
 #include <map>
 #include <mutex>
 #include <numeric>
+#include <set>
 #include <string>
 #include <vector>
 
@@ -72,16 +73,54 @@ isg_status finish_problem(isg_problem *p) {
     for (int32_t i = 0; i < p->n; ++i) p->colour[i] = ((i / p->W) + (i % p->W)) & 1;
     p->n_colours = 2;
   } else {
-    std::vector<int32_t> used(p->n + 1, -1);
+    // smallest-last order (Matula and Beck 1983): repeatedly remove a vertex of
+    // smallest remaining degree, the smallest id among ties; vertices still
+    // present are kept in ordered buckets by remaining degree
+    const int32_t n = p->n;
+    std::vector<int32_t> deg(n), order;
+    order.reserve(n);
+    int32_t dtop = 0;
+    for (int32_t v = 0; v < n; ++v) {
+      deg[v] = (int32_t)(p->rowptr[v + 1] - p->rowptr[v]);
+      dtop = std::max(dtop, deg[v]);
+    }
+    std::vector<std::set<int32_t>> bucket(dtop + 1);
+    for (int32_t v = 0; v < n; ++v) bucket[deg[v]].insert(v);
+    std::vector<char> removed(n, 0);
+    int32_t dmin = 0;
+    for (int32_t step = 0; step < n; ++step) {
+      while (bucket[dmin].empty()) ++dmin;
+      const int32_t v = *bucket[dmin].begin();
+      bucket[dmin].erase(bucket[dmin].begin());
+      removed[v] = 1;
+      order.push_back(v);
+      for (int64_t q = p->rowptr[v]; q < p->rowptr[v + 1]; ++q) {
+        const int32_t u = p->col[q];
+        if (removed[u]) continue;
+        bucket[deg[u]].erase(u);
+        bucket[--deg[u]].insert(u);
+        dmin = std::min(dmin, deg[u]);
+      }
+    }
+    // colour in reverse removal order (smallest colour no coloured neighbour
+    // has), then number the classes by their smallest vertex
+    std::vector<int32_t> used(n + 1, -1);
+    std::fill(p->colour.begin(), p->colour.end(), -1);
     p->n_colours = 1;
-    for (int32_t v = 0; v < p->n; ++v) {
+    for (int32_t step = n - 1; step >= 0; --step) {
+      const int32_t v = order[step];
       for (int64_t q = p->rowptr[v]; q < p->rowptr[v + 1]; ++q)
-        if (p->col[q] < v) used[p->colour[p->col[q]]] = v;
+        if (p->colour[p->col[q]] >= 0) used[p->colour[p->col[q]]] = v;
       int32_t c = 0;
       while (used[c] == v) ++c;
       p->colour[v] = c;
       p->n_colours = std::max(p->n_colours, c + 1);
     }
+    std::vector<int32_t> rename(p->n_colours, -1);
+    int32_t next = 0;
+    for (int32_t v = 0; v < n; ++v)
+      if (rename[p->colour[v]] < 0) rename[p->colour[v]] = next++;
+    for (int32_t v = 0; v < n; ++v) p->colour[v] = rename[p->colour[v]];
   }
   // colour-major relabelling: order[new] = original id
   p->class_start.assign(p->n_colours + 1, 0);

@@ -1,6 +1,6 @@
 """Host-side checks of libisg that need no GPU: the library loads, exports every
 function include/isg.h declares, validates instances, and colours them as the
-oracle's independent greedy colouring does."""
+oracle's independent smallest-last colouring does."""
 import ctypes
 import os
 import re
@@ -84,12 +84,13 @@ def test_csr_validation_and_equivalence(isg):
         isg.isg_problem_create_csr(g.n, c.rowptr, col, c.wt[:2 * g.m])
 
 
-@pytest.mark.parametrize("n,m,seed", [(2000, 1999, 1), (10000, 9999, 1), (3000, 6000, 2)])
+@pytest.mark.parametrize("n,m,seed", [(2000, 1999, 1), (10000, 9999, 1), (3000, 6000, 2),
+                                      (500, 20000, 3), (12000, 150000, 9)])
 def test_colouring_matches_oracle(isg, n, m, seed):
     g = I.random_graph(n, m, seed)
     p = isg.problem_of(g)
     info = isg.isg_problem_info(p, colors=True)
-    col, nc = oracle.csr_of(g).greedy_colouring()
+    col, nc = oracle.csr_of(g).colouring()
     assert info["n_colors"] == nc
     assert np.array_equal(info["colors"], col)
     assert info["total_weight"] == int(g.w.sum()) and info["m"] == m
@@ -98,7 +99,11 @@ def test_colouring_matches_oracle(isg, n, m, seed):
 def test_torus_colouring_is_checkerboard(isg):
     t = I.torus(8, 12, 5)
     info = isg.isg_problem_info(isg.problem_of(t), colors=True)
-    col, nc = oracle.csr_of(t).greedy_colouring()
+    col, nc = oracle.csr_of(t).colouring()
+    assert info["n_colors"] == 2 and np.array_equal(info["colors"], col)
+    # the same torus as a plain edge list: smallest-last gives the same checkerboard
+    u, v, w = t.edges()
+    info = isg.isg_problem_info(isg.isg_problem_create_edges(t.n, u, v, w), colors=True)
     assert info["n_colors"] == 2 and np.array_equal(info["colors"], col)
 
 
@@ -139,3 +144,12 @@ def test_fields_validation_and_info(isg):
         isg.isg_problem_create_fields(30, g.u, g.v, g.w, np.full(30, 1 << 26, np.int32))
     with pytest.raises(isg.IsgError):  # bad edge still rejected
         isg.isg_problem_create_fields(3, [0], [0], [1], [0, 0, 0])
+
+
+def test_colouring_matches_oracle_on_geometric_and_fields(isg):
+    """Geometric graphs (many equal degrees, so the tie rule decides) and an
+    independent-set instance with fields colour as the oracle does."""
+    for g in (I.geometric_graph(3000, 6.0, 4), I.independent_set_instance(I.geometric_graph(2000, 9.0, 5))):
+        info = isg.isg_problem_info(isg.problem_of(g), colors=True)
+        col, nc = oracle.csr_of(g).colouring()
+        assert info["n_colors"] == nc and np.array_equal(info["colors"], col)

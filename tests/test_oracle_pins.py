@@ -187,6 +187,73 @@ def test_greedy_colouring_is_proper_on_random_graphs():
         assert nc <= c.kmax() + 1
 
 
+def _graph(n, edges):
+    u = np.array([a for a, b in edges], np.int32)
+    v = np.array([b for a, b in edges], np.int32)
+    return oracle.Csr(n, u, v, np.ones(len(edges), np.int32))
+
+
+def _degeneracy(c):
+    """Brute force: the largest minimum degree over all vertex subsets."""
+    adj = [set(c.col[c.rowptr[i]:c.rowptr[i + 1]].tolist()) for i in range(c.n)]
+    best = 0
+    for mask in range(1, 1 << c.n):
+        sub = [i for i in range(c.n) if (mask >> i) & 1]
+        s = set(sub)
+        best = max(best, min(len(adj[i] & s) for i in sub))
+    return best
+
+
+def test_smallest_last_small_closed_forms():
+    """Hand-derived colourings.  C5: removal order 0,1,2,3,4 (all ties go to the
+    smallest id), reverse colouring gives [2,1,0,1,0], numbering by smallest
+    vertex [0,1,2,1,2].  Star with hub 0: removal 1,2,3, then hub 0 (degree 1
+    ties with leaf 4, smaller id), then 4: two classes {0}, {1..4}.  K5: five."""
+    col, nc = _graph(5, [(i, (i + 1) % 5) for i in range(5)]).colouring()
+    assert col.tolist() == [0, 1, 2, 1, 2] and nc == 3
+    col, nc = _graph(5, [(0, i) for i in range(1, 5)]).colouring()
+    assert col.tolist() == [0, 1, 1, 1, 1] and nc == 2
+    col, nc = _graph(5, [(a, b) for a in range(5) for b in range(a + 1, 5)]).colouring()
+    assert col.tolist() == [0, 1, 2, 3, 4] and nc == 5
+    # odd wheel (hub 0, rim 1..5): chromatic number 4, degeneracy 3
+    c = _graph(6, [(0, i) for i in range(1, 6)] + [(i, i % 5 + 1) for i in range(1, 6)])
+    col, nc = c.colouring()
+    assert nc == 4 and _proper(c, col)
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_smallest_last_within_degeneracy_plus_one(seed):
+    """At most degeneracy + 1 colours (the property of the smallest-last order;
+    a largest-first or id order breaks it on some of these graphs), proper, and
+    classes numbered by their smallest vertex."""
+    g = I.random_graph(11, 18 + 3 * seed, 100 + seed)
+    c = oracle.csr_of(g)
+    col, nc = c.colouring()
+    assert _proper(c, col)
+    assert nc <= _degeneracy(c) + 1
+    firsts = [int(np.flatnonzero(col == k)[0]) for k in range(nc)]
+    assert firsts == sorted(firsts) and set(col.tolist()) == set(range(nc))
+
+
+@pytest.mark.parametrize("L,W", [(4, 4), (6, 10), (10, 12), (20, 20), (80, 100)])
+def test_smallest_last_on_even_torus_edges_is_checkerboard(L, W):
+    """A torus given as a plain edge list gets the checkerboard, (r + c) even first."""
+    t = I.torus(L, W, 7)
+    u, v, w = t.edges()
+    col, nc = oracle.Csr(t.n, u, v, w).colouring()
+    r, c = np.divmod(np.arange(L * W), W)
+    assert nc == 2 and np.array_equal(col, (r + c) % 2)
+
+
+def test_smallest_last_is_proper_on_random_graphs():
+    for seed in (1, 2):
+        g = I.random_graph(2000, 4000, seed)
+        c = oracle.csr_of(g)
+        col, nc = c.colouring()
+        assert _proper(c, col)
+        assert nc <= c.kmax() + 1
+
+
 # ------------------------------------------------------ Metropolis sampling
 def _chi2_p(observed, expected):
     from scipy import stats
