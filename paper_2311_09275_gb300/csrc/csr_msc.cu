@@ -22,8 +22,8 @@ __global__ void __launch_bounds__(512) gm_batch_kernel(const GraphMscItem *items
     __syncthreads();
     if (it >= count) break;
     const GraphMscItem u = items[order[it]];
-    gm_word<kGraphMscBatchPlanes, false, false>(u.solve, none, u.word, 0, 1, u.t_begin, u.t_end,
-                                                u.resume, smem);
+    gm_word<kGraphMscBatchPlanes, false, false, false>(u.solve, none, u.word, 0, 1, u.t_begin,
+                                                       u.t_end, u.resume, smem);
     __syncthreads();
   }
 }

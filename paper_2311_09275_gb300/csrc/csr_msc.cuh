@@ -127,13 +127,14 @@ __device__ __forceinline__ uint32_t field_unsat(uint32_t s0, int32_t hv) {
   return hv > 0 ? s0 : ~s0;
 }
 
-// One vertex of one replica word with its uniforms uu (and, FIELD, its local
-// field hv): returns the new word; accumulates the accepted flips' d and U
-// into the energy counters.
-template <int NP, bool FIELD>
+// One vertex of one replica word (and, FIELD, its local field hv): its 32
+// uniforms are pre (drawn by the caller), or with LAZY filled by draw(uu)
+// only when some replica is uphill.  Returns the new word; accumulates the
+// accepted flips' d and U into the energy counters.
+template <int NP, bool FIELD, bool LAZY, typename Draw>
 __device__ __forceinline__ uint32_t update_vertex(const uint32_t *spin, int v, int i,
                                                   const GmAdj &a, const uint32_t *row,
-                                                  const uint4 (&uu)[8], int32_t hv,
+                                                  const uint4 (&pre)[8], Draw draw, int32_t hv,
                                                   SlicedCounter<NP> &cd, SlicedCounter<NP> &cu) {
   const uint32_t s0 = spin[v];
   const int p0 = a.row[i], p1 = a.row[i + 1];
@@ -170,13 +171,10 @@ __device__ __forceinline__ uint32_t update_vertex(const uint32_t *spin, int v, i
     }
     d += ha;
   }
-  // uphill lanes: U <= (d - 1) / 2, i.e. k = d - 2U > 0
+  // uphill lanes: U <= (d - 1) / 2, i.e. k = d - 2U > 0; those at level U
+  // flip when their uniform is below the threshold of k = d - 2U
   const int levels = (d + 1) / 2;
-  uint32_t acc = 0xFFFFFFFFu;
-  for (int lv = 0; lv < levels; ++lv) {
-    const uint32_t eq = count_equals(u, lv);
-    if (eq == 0u) continue;
-    const uint32_t T = row[d - 2 * lv];
+  auto below = [&](const uint4 (&uu)[8], uint32_t T) {
     uint32_t m0 = 0u, m1 = 0u;
 #pragma unroll
     for (int q = 0; q < 8; ++q) {
@@ -186,7 +184,27 @@ __device__ __forceinline__ uint32_t update_vertex(const uint32_t *spin, int v, i
       if (uu[q].z < T) m |= 4u << (4 * q);
       if (uu[q].w < T) m |= 8u << (4 * q);
     }
-    acc &= ~eq | m0 | m1;
+    return m0 | m1;
+  };
+  uint32_t acc;
+  if (LAZY) {
+    uint32_t up = 0u;
+    for (int lv = 0; lv < levels; ++lv) up |= count_equals(u, lv);
+    acc = ~up;
+    if (up != 0u) {
+      uint4 uu[8];
+      draw(uu);
+      for (int lv = 0; lv < levels; ++lv) {
+        const uint32_t eq = count_equals(u, lv);
+        if (eq != 0u) acc |= eq & below(uu, row[d - 2 * lv]);
+      }
+    }
+  } else {
+    acc = 0xFFFFFFFFu;
+    for (int lv = 0; lv < levels; ++lv) {
+      const uint32_t eq = count_equals(u, lv);
+      if (eq != 0u) acc &= ~eq | below(pre, row[d - 2 * lv]);
+    }
   }
   // energy change of the accepted lanes: 2 (d - 2U)
 #pragma unroll
@@ -212,7 +230,9 @@ __device__ __forceinline__ void group_wait(int K) {
     __syncthreads();
 }
 
-template <int NP, bool STAGED, bool FIELD>
+// PREFETCH: draw the next phase's first uniforms during the group barrier
+// (off in the unit kernel, whose CTA-wide barrier leaves nothing to overlap).
+template <int NP, bool STAGED, bool FIELD, bool PREFETCH = true>
 __device__ void gm_word(const GraphMscSolve &s, const GraphMscLaunch &L, int word, int k, int K,
                         int t_begin, int t_end, int resume, uint8_t *smem) {
   const int n = s.n;
@@ -345,10 +365,11 @@ __device__ void gm_word(const GraphMscSolve &s, const GraphMscLaunch &L, int wor
     for (int q = 0; q < 8; ++q) bp[q] = block_prefix(8u * uword + (uint32_t)q, (uint32_t)tt, s.rk);
   };
   auto draw_first = [&](int c) {
+    if (!PREFETCH) return;
     ready = clo[c] + (int)threadIdx.x < chi[c];
     if (ready) vertex_uniforms((uint32_t)adj.orig[cob[c] + threadIdx.x], bp, s.rk, uu);
   };
-  if (t_begin < t_end) {
+  if (PREFETCH && t_begin < t_end) {
     sweep_prefix(t_begin);
     draw_first(0);
   }
@@ -364,6 +385,7 @@ __device__ void gm_word(const GraphMscSolve &s, const GraphMscLaunch &L, int wor
     const uint32_t *gnext = wtab + (size_t)(t + 1) * s.table_ts;
     const uint32_t p0 = (more && x0 < s.kmax1) ? gnext[x0] : 0u;
     const uint32_t p1 = (more && x1 < s.kmax1) ? gnext[x1] : 0u;
+    if (!PREFETCH) sweep_prefix(t);
     SlicedCounter<NP> cd, cu;
     cd.clear();
     cu.clear();
@@ -377,10 +399,14 @@ __device__ void gm_word(const GraphMscSolve &s, const GraphMscLaunch &L, int wor
           if (STAGED) lbest[i] = (lbest[i] & ~imp) | (spin[v] & imp);
           else gbest[v] = (gbest[v] & ~imp) | (spin[v] & imp);
         }
-        if (!ready) vertex_uniforms((uint32_t)adj.orig[i], bp, s.rk, uu);
-        ready = false;
         const int32_t hv = !has_field ? 0 : (STAGED ? lfield[i] : __ldg(&s.field[v]));
-        const uint32_t sn = update_vertex<NP, FIELD>(spin, v, i, adj, row, uu, hv, cd, cu);
+        auto draw = [&](uint4 (&out)[8]) {
+          vertex_uniforms((uint32_t)adj.orig[i], bp, s.rk, out);
+        };
+        if (PREFETCH && !ready) vertex_uniforms((uint32_t)adj.orig[i], bp, s.rk, uu);
+        ready = false;
+        const uint32_t sn =
+            update_vertex<NP, FIELD, !PREFETCH>(spin, v, i, adj, row, uu, draw, hv, cd, cu);
         if (K == 1) {
           spin[v] = sn;
         } else {
@@ -412,7 +438,7 @@ __device__ void gm_word(const GraphMscSolve &s, const GraphMscLaunch &L, int wor
       }
     }
     group_arrive(K);
-    if (more) {
+    if (PREFETCH && more) {
       sweep_prefix(t + 1);
       draw_first(0);
     }

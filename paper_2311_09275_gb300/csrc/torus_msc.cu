@@ -307,9 +307,9 @@ __device__ void torus_word(const TorusSolve &s, int word, int k, int K, int t_be
   // group barrier before that phase completes (they do not depend on spins)
   uint32_t pre4 = 0u, pre8 = 0u;
   bool ready = false;
-  if (t < t_end) {
+  if (kPrefetch && t < t_end) {
     sweep_prefix(t);
-    if (kPrefetch) ready = first_site_masks(W, r0, nr, 0, bp, s.rk, T4n, T8n, pre4, pre8);
+    ready = first_site_masks(W, r0, nr, 0, bp, s.rk, T4n, T8n, pre4, pre8);
   }
   for (; t < t_end; ++t) {
     const uint32_t T4 = T4n, T8 = T8n;
@@ -318,6 +318,7 @@ __device__ void torus_word(const TorusSolve &s, int word, int k, int K, int t_be
       T4n = trow[(size_t)(t + 1) * s.table_ts];
       T8n = trow[(size_t)(t + 1) * s.table_ts + 1];
     }
+    if (!kPrefetch) sweep_prefix(t);
     cnt.clear();
     for (int c = 0; c < 2; ++c) {
       if (T8 != 0u)
@@ -334,10 +335,9 @@ __device__ void torus_word(const TorusSolve &s, int word, int k, int K, int t_be
     }
     ready = false;
     e += 4 * (cluster_lane_sum<NP>(cnt, part, k, K, [&] {
-                if (more) {
+                if (kPrefetch && more) {
                   sweep_prefix(t + 1);
-                  if (kPrefetch)
-                    ready = first_site_masks(W, r0, nr, 0, bp, s.rk, T4n, T8n, pre4, pre8);
+                  ready = first_site_masks(W, r0, nr, 0, bp, s.rk, T4n, T8n, pre4, pre8);
                 }
               }) -
               2 * n);
@@ -390,8 +390,10 @@ __global__ void __launch_bounds__(MAXT, 1) torus_kernel(TorusSolve s, TorusLaunc
   torus_word<NP, (MAXT <= 512)>(s, word, k, K, l.t_begin, t_end, l.resume, smem);
 }
 
+// One CTA per unit with a CTA-wide barrier (nothing to overlap): no mask
+// prefetch, so that the kernel stays at 64 registers and two CTAs per SM.
 template <int NP>
-__global__ void __launch_bounds__(512) torus_batch_kernel(const TorusBatchItem *items,
+__global__ void __launch_bounds__(512, 2) torus_batch_kernel(const TorusBatchItem *items,
                                                           const int32_t *count_dev,
                                                           const int32_t *order, int32_t *next) {
   extern __shared__ __align__(16) uint8_t smem[];
@@ -404,7 +406,7 @@ __global__ void __launch_bounds__(512) torus_batch_kernel(const TorusBatchItem *
     __syncthreads();
     if (it >= count) break;
     const TorusBatchItem u = items[order[it]];
-    torus_word<NP, true>(u.solve, u.word, 0, 1, u.t_begin, u.t_end, u.resume, smem);
+    torus_word<NP, false>(u.solve, u.word, 0, 1, u.t_begin, u.t_end, u.resume, smem);
     __syncthreads();
   }
 }
