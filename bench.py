@@ -188,11 +188,15 @@ def barrier(dist):
         dist.barrier()
 
 
-def workload(config: str, rank: int, sweeps: int | None = None):
+COLOURINGS = {"greedy": 0, "smallest-last": 1}
+
+
+def workload(config: str, rank: int, sweeps: int | None = None, colouring: str = "greedy"):
     """The Solve of this rank.  Ranks anneal the same instance with their own
     seeds (independent replicas: weak scaling, no exchange).  `sweeps`
     shortens the schedule (profiling runs only; the benchmark line uses the
-    full 10,000)."""
+    full 10,000).  A graph workload coloured other than greedy by id names its
+    colouring."""
     if config == "torus":
         sv = I.torus_80x100(sweeps=sweeps or 10000)
         name = f"torus_80x100_R1024_S{sv.sweeps}_geometric_0.1_5.0"
@@ -204,12 +208,21 @@ def workload(config: str, rank: int, sweeps: int | None = None):
         name = f"independent_set_geometric_n10000_deg6_R256_S{sv.sweeps}_geometric_0.1_5.0"
     else:
         raise ValueError(config)
+    if colouring != "greedy" and config != "torus":
+        name += "_" + colouring.replace("-", "_")
     sv.seed = sv.seed + rank
     return sv, name
 
 
+def oracle_colour(c, colouring: str):
+    """The oracle's colour classes for the library's colouring of the same instance."""
+    return (c.smallest_last_colouring() if colouring == "smallest-last" and c.torus_shape is None
+            else c.colouring())[0]
+
+
 # ---------------------------------------------------------------- CPU oracle
-def cpu_oracle_rate(sv, budget_s: float = 12.0, max_replicas: int | None = None):
+def cpu_oracle_rate(sv, budget_s: float = 12.0, max_replicas: int | None = None,
+                    colouring: str = "greedy"):
     """Oracle attempts/s on the host cores over a bounded sample of the workload:
     whole replicas (a multiple of the core count, one thread per replica block)
     over a sweep prefix, sized to about budget_s seconds; plus the rate of one
@@ -217,7 +230,7 @@ def cpu_oracle_rate(sv, budget_s: float = 12.0, max_replicas: int | None = None)
     import oracle
     cores = os.cpu_count() or 1
     c = oracle.csr_of(sv.problem)
-    colour, _ = c.greedy_colouring()
+    colour = oracle_colour(c, colouring)
     # calibrate on a short prefix, then size the sample to the budget
     reps = min(sv.replicas, max_replicas or cores)
     probe = max(1, min(sv.sweeps, 20))
@@ -251,12 +264,12 @@ def run_reference(args):
                           f"the oracle arm times the single-instance workloads (torus, random, "
                           f"mis); --config {args.config} has no oracle timing line"}))
         return
-    sv, name = workload(args.config, 0, args.sweeps)
+    sv, name = workload(args.config, 0, args.sweeps, args.colouring)
     import oracle
     cores = os.cpu_count() or 1
     reps = min(sv.replicas, cores)
     c = oracle.csr_of(sv.problem)
-    colour, _ = c.greedy_colouring()
+    colour = oracle_colour(c, args.colouring)
     # each step: `reps` replicas over a sweep prefix sized to ~per_step_s
     probe = 10
     t0 = time.perf_counter()
@@ -294,9 +307,9 @@ def run_gpu(args):
     device = torch.device("cuda", local)
     from paper_2311_09275_gb300 import isg
 
-    sv, name = workload(args.config, rank, args.sweeps)
+    sv, name = workload(args.config, rank, args.sweeps, args.colouring)
     stream = torch.cuda.current_stream()
-    p = isg.problem_of(sv.problem)
+    p = isg.problem_of(sv.problem, colouring=COLOURINGS[args.colouring])
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.int32, device=device)  # 512 MB > L2
 
     shape = {"kernel": args.kernel} if args.kernel else {}
@@ -356,7 +369,7 @@ def run_gpu(args):
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for _ in range(e2e_steps):
-        q = isg.problem_of(sv.problem)                        # host couplings -> library
+        q = isg.problem_of(sv.problem, colouring=COLOURINGS[args.colouring])  # host -> library
         r = isg.isg_anneal(q, sv.replicas, sv.betas, sv.seed, stream=stream)
         spins, energies, done = r.final(spins=True)           # D2H final state
         be, br, bspins, per, hit = r.best(spins=True)         # D2H best state
@@ -426,7 +439,7 @@ def run_gpu(args):
         "wall_s": wall,
     }
     if rank == 0 and world == 1 and not args.no_cpu:
-        line["cpu_baseline"] = cpu_oracle_rate(sv)
+        line["cpu_baseline"] = cpu_oracle_rate(sv, colouring=args.colouring)
     if rank == 0:
         print(json.dumps(line))
 
@@ -708,6 +721,8 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--colouring", default="greedy", choices=list(COLOURINGS),
+                    help="colour classes of a graph workload (default: greedy by id)")
     ap.add_argument("--config", default="torus",
                     choices=["torus", "random", "mis", "batch", "served", "ttt", "pt"])
     ap.add_argument("--requests", type=int, default=2000, help="served: number of requests")

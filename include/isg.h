@@ -18,10 +18,8 @@
  * heuristics spend their time in: simulated annealing by single-spin-flip
  * Metropolis sweeps over R independent replicas.  Sweep t (0-based) visits
  * the colour classes in ascending order (torus: colour (r + c) mod 2; graphs:
- * the smallest-last colouring -- repeatedly remove a vertex of smallest
- * remaining degree, the smallest id among ties, colour in the reverse of that
- * order with the smallest colour no coloured neighbour has, and number the
- * classes by their smallest vertex) and, for every vertex i of the
+ * greedy colouring by ascending vertex id, or the smallest-last colouring
+ * selected by isg_problem_set_colouring) and, for every vertex i of the
  * class and every replica, computes h_i = sum_j w_ij s_j and the energy change
  * d = -2 s_i h_i of flipping s_i; the flip is taken when d <= 0, or when
  * u < floor(2^32 exp(-beta_t d)) for the replica's 32-bit uniform u.  The
@@ -115,6 +113,27 @@ isg_status isg_problem_create_torus(int32_t L, int32_t W, const int8_t *j_right,
  * number of colour classes; colors[n] receives each vertex's class. */
 isg_status isg_problem_info(const isg_problem *p, int32_t *n, int64_t *m, int64_t *total_weight,
                             int32_t *n_colors, int32_t *colors);
+
+/* Colourings of a graph's sweep classes.  GREEDY (the default): for v = 0..n-1,
+ * colour[v] = the smallest c >= 0 that no neighbour u < v has.  SMALLEST_LAST
+ * (Matula and Beck, J. ACM 30(3), 1983): repeatedly remove a vertex of
+ * smallest remaining degree (the smallest id among ties), colour the vertices
+ * in the reverse of that removal order, each with the smallest c >= 0 that no
+ * already coloured neighbour has, and number the classes in increasing order
+ * of their smallest vertex; at most degeneracy + 1 classes (sparse random
+ * graphs: 3 where greedy gives 5), and every class is one cluster-wide phase
+ * per sweep.  Both are valid Metropolis sweep orders; they give different
+ * (equally valid) chains. */
+typedef enum {
+    ISG_COLOURING_GREEDY = 0,
+    ISG_COLOURING_SMALLEST_LAST = 1
+} isg_colouring;
+
+/* Re-colours a graph instance with `method` (an isg_colouring).  Call it before
+ * the instance's first solve or submission: EBUSY once the instance holds
+ * device state.  EINVAL: NULL, an unknown method, or a torus (tori keep their
+ * (r + c) mod 2 checkerboard). */
+isg_status isg_problem_set_colouring(isg_problem *p, int32_t method);
 
 void isg_problem_destroy(isg_problem *p);
 

@@ -14,8 +14,8 @@ Readings of the paper used here (the paper withholds its method, Sec. III.A):
 * E(s) = sum_{(i,j)} w_ij s_i s_j is minimised, so the MaxCut value of
   Sec. II.A is cut = (W_tot - E) / 2.
 * One sweep visits every vertex once, colour class by colour class in
-  ascending class order (classes: the checkerboard on a torus, the
-  smallest-last colouring on a graph, Csr.colouring); the flip of vertex i changes E by d = -2 s_i h_i with
+  ascending class order (classes: the checkerboard on a torus, greedy by
+  ascending id on a graph, Csr.colouring; or a colouring passed in); the flip of vertex i changes E by d = -2 s_i h_i with
   h_i = sum_j w_ij s_j and is accepted when d <= 0 or when the replica's
   32-bit uniform is below floor(2^32 exp(-beta_t d)).
 * A replica's best state is checked at sweep boundaries only (strict
@@ -137,17 +137,21 @@ class Csr:
         nc = _load().orc_greedy_colouring(self.n, _p(self.rowptr), _p(self.col), _p(colour))
         return colour, int(nc)
 
-    def colouring(self):
-        """The sweep's colour classes: on a torus the checkerboard (r + c) mod 2;
-        on a graph the smallest-last colouring with classes numbered by their
-        smallest vertex (orc_smallest_last_colouring)."""
-        if self.torus_shape is not None:
-            r, c = np.divmod(np.arange(self.n), self.torus_shape[1])
-            return ((r + c) % 2).astype(np.int32), 2
+    def smallest_last_colouring(self):
+        """Smallest-last order, classes numbered by their smallest vertex
+        (orc_smallest_last_colouring): the library's optional colouring."""
         colour = np.zeros(self.n, dtype=np.int32)
         nc = _load().orc_smallest_last_colouring(self.n, _p(self.rowptr), _p(self.col),
                                                  _p(colour))
         return colour, int(nc)
+
+    def colouring(self):
+        """The sweep's default colour classes: on a torus the checkerboard
+        (r + c) mod 2, on a graph the greedy colouring by ascending id."""
+        if self.torus_shape is not None:
+            r, c = np.divmod(np.arange(self.n), self.torus_shape[1])
+            return ((r + c) % 2).astype(np.int32), 2
+        return self.greedy_colouring()
 
     def kmax(self) -> int:
         """max_i (sum_j |w_ij| + |h_i|): the largest half energy change of one flip."""
@@ -233,7 +237,7 @@ def anneal(csr: Csr, replicas, betas, seed: int, colour=None, target=None,
     """Run the colour-ordered Metropolis schedule on the listed replicas.
 
     ``replicas`` is an int (all replicas 0..R-1) or a list of replica indices.
-    ``colour`` defaults to the oracle's smallest-last colouring (Csr.colouring).
+    ``colour`` defaults to Csr.colouring (greedy by id; the torus checkerboard).
     """
     if colour is None:
         colour, nc = csr.colouring()

@@ -1,5 +1,5 @@
 // isg_runtime.cu -- host runtime behind the C ABI of include/isg.h: instance
-// building and validation, smallest-last colouring and colour-major relabelling,
+// building and validation, colouring and colour-major relabelling,
 // acceptance tables, device residency, launch orchestration, results.
 #include <algorithm>
 #include <cmath>
@@ -46,6 +46,8 @@ isg_status cuda_fail(cudaError_t err, const char *what) {
 
 namespace {
 
+isg_status colour_and_relabel(isg_problem *p);
+
 isg_status finish_problem(isg_problem *p) {
   // kmax and total weight
   p->kmax = 0;
@@ -67,60 +69,86 @@ isg_status finish_problem(isg_problem *p) {
                 (long long)wabs);
   p->total_weight = wsum;
   p->m = p->rowptr[p->n] / 2;
-  // colouring
+  return colour_and_relabel(p);
+}
+
+// Greedy colouring by ascending id: colour[v] is the smallest c >= 0 that no
+// neighbour u < v has.
+void colour_greedy(isg_problem *p) {
+  std::vector<int32_t> used(p->n + 1, -1);
+  p->n_colours = 1;
+  for (int32_t v = 0; v < p->n; ++v) {
+    for (int64_t q = p->rowptr[v]; q < p->rowptr[v + 1]; ++q)
+      if (p->col[q] < v) used[p->colour[p->col[q]]] = v;
+    int32_t c = 0;
+    while (used[c] == v) ++c;
+    p->colour[v] = c;
+    p->n_colours = std::max(p->n_colours, c + 1);
+  }
+}
+
+// Smallest-last colouring (Matula and Beck 1983): repeatedly remove a vertex
+// of smallest remaining degree, the smallest id among ties (vertices still
+// present are kept in ordered buckets by remaining degree); colour in the
+// reverse removal order with the smallest colour no coloured neighbour has;
+// number the classes by their smallest vertex.
+void colour_smallest_last(isg_problem *p) {
+  const int32_t n = p->n;
+  std::vector<int32_t> deg(n), order;
+  order.reserve(n);
+  int32_t dtop = 0;
+  for (int32_t v = 0; v < n; ++v) {
+    deg[v] = (int32_t)(p->rowptr[v + 1] - p->rowptr[v]);
+    dtop = std::max(dtop, deg[v]);
+  }
+  std::vector<std::set<int32_t>> bucket(dtop + 1);
+  for (int32_t v = 0; v < n; ++v) bucket[deg[v]].insert(v);
+  std::vector<char> removed(n, 0);
+  int32_t dmin = 0;
+  for (int32_t step = 0; step < n; ++step) {
+    while (bucket[dmin].empty()) ++dmin;
+    const int32_t v = *bucket[dmin].begin();
+    bucket[dmin].erase(bucket[dmin].begin());
+    removed[v] = 1;
+    order.push_back(v);
+    for (int64_t q = p->rowptr[v]; q < p->rowptr[v + 1]; ++q) {
+      const int32_t u = p->col[q];
+      if (removed[u]) continue;
+      bucket[deg[u]].erase(u);
+      bucket[--deg[u]].insert(u);
+      dmin = std::min(dmin, deg[u]);
+    }
+  }
+  std::vector<int32_t> used(n + 1, -1);
+  std::fill(p->colour.begin(), p->colour.end(), -1);
+  p->n_colours = 1;
+  for (int32_t step = n - 1; step >= 0; --step) {
+    const int32_t v = order[step];
+    for (int64_t q = p->rowptr[v]; q < p->rowptr[v + 1]; ++q)
+      if (p->colour[p->col[q]] >= 0) used[p->colour[p->col[q]]] = v;
+    int32_t c = 0;
+    while (used[c] == v) ++c;
+    p->colour[v] = c;
+    p->n_colours = std::max(p->n_colours, c + 1);
+  }
+  std::vector<int32_t> rename(p->n_colours, -1);
+  int32_t next = 0;
+  for (int32_t v = 0; v < n; ++v)
+    if (rename[p->colour[v]] < 0) rename[p->colour[v]] = next++;
+  for (int32_t v = 0; v < n; ++v) p->colour[v] = rename[p->colour[v]];
+}
+
+// Colour classes (the problem's colouring method) and everything derived from
+// them: the colour-major relabelling, relabelled CSR and fields, kernel modes.
+isg_status colour_and_relabel(isg_problem *p) {
   p->colour.assign(p->n, 0);
   if (p->torus) {
     for (int32_t i = 0; i < p->n; ++i) p->colour[i] = ((i / p->W) + (i % p->W)) & 1;
     p->n_colours = 2;
+  } else if (p->colouring == ISG_COLOURING_SMALLEST_LAST) {
+    colour_smallest_last(p);
   } else {
-    // smallest-last order (Matula and Beck 1983): repeatedly remove a vertex of
-    // smallest remaining degree, the smallest id among ties; vertices still
-    // present are kept in ordered buckets by remaining degree
-    const int32_t n = p->n;
-    std::vector<int32_t> deg(n), order;
-    order.reserve(n);
-    int32_t dtop = 0;
-    for (int32_t v = 0; v < n; ++v) {
-      deg[v] = (int32_t)(p->rowptr[v + 1] - p->rowptr[v]);
-      dtop = std::max(dtop, deg[v]);
-    }
-    std::vector<std::set<int32_t>> bucket(dtop + 1);
-    for (int32_t v = 0; v < n; ++v) bucket[deg[v]].insert(v);
-    std::vector<char> removed(n, 0);
-    int32_t dmin = 0;
-    for (int32_t step = 0; step < n; ++step) {
-      while (bucket[dmin].empty()) ++dmin;
-      const int32_t v = *bucket[dmin].begin();
-      bucket[dmin].erase(bucket[dmin].begin());
-      removed[v] = 1;
-      order.push_back(v);
-      for (int64_t q = p->rowptr[v]; q < p->rowptr[v + 1]; ++q) {
-        const int32_t u = p->col[q];
-        if (removed[u]) continue;
-        bucket[deg[u]].erase(u);
-        bucket[--deg[u]].insert(u);
-        dmin = std::min(dmin, deg[u]);
-      }
-    }
-    // colour in reverse removal order (smallest colour no coloured neighbour
-    // has), then number the classes by their smallest vertex
-    std::vector<int32_t> used(n + 1, -1);
-    std::fill(p->colour.begin(), p->colour.end(), -1);
-    p->n_colours = 1;
-    for (int32_t step = n - 1; step >= 0; --step) {
-      const int32_t v = order[step];
-      for (int64_t q = p->rowptr[v]; q < p->rowptr[v + 1]; ++q)
-        if (p->colour[p->col[q]] >= 0) used[p->colour[p->col[q]]] = v;
-      int32_t c = 0;
-      while (used[c] == v) ++c;
-      p->colour[v] = c;
-      p->n_colours = std::max(p->n_colours, c + 1);
-    }
-    std::vector<int32_t> rename(p->n_colours, -1);
-    int32_t next = 0;
-    for (int32_t v = 0; v < n; ++v)
-      if (rename[p->colour[v]] < 0) rename[p->colour[v]] = next++;
-    for (int32_t v = 0; v < n; ++v) p->colour[v] = rename[p->colour[v]];
+    colour_greedy(p);
   }
   // colour-major relabelling: order[new] = original id
   p->class_start.assign(p->n_colours + 1, 0);
@@ -1407,6 +1435,19 @@ isg_status isg_problem_info(const isg_problem *p, int32_t *n, int64_t *m, int64_
   if (n_colors) *n_colors = p->n_colours;
   if (colors) std::copy(p->colour.begin(), p->colour.end(), colors);
   return ISG_OK;
+}
+
+isg_status isg_problem_set_colouring(isg_problem *p, int32_t method) {
+  if (!p) return fail(ISG_EINVAL, "problem must not be NULL");
+  if (method != ISG_COLOURING_GREEDY && method != ISG_COLOURING_SMALLEST_LAST)
+    return fail(ISG_EINVAL, "unknown colouring %d", method);
+  if (p->torus) return fail(ISG_EINVAL, "a torus keeps its (r + c) mod 2 checkerboard");
+  std::lock_guard<std::mutex> lock(p->mu);
+  if (!p->dev.empty())
+    return fail(ISG_EBUSY, "the instance already has device state: set the colouring before "
+                           "its first solve");
+  p->colouring = method;
+  return colour_and_relabel(p);
 }
 
 void isg_problem_destroy(isg_problem *p) {

@@ -50,6 +50,7 @@ struct isg_problem {
   std::vector<int64_t> rowptr;             // CSR, original ids, rows sorted
   std::vector<int32_t> col, wt;
   std::vector<int32_t> field;              // local fields h (empty: none)
+  int32_t colouring = 0;                   // isg_colouring of a graph's classes
   std::vector<int32_t> colour;
   int32_t n_colours = 0;
   std::vector<int32_t> order;              // relabelled -> original

@@ -60,6 +60,7 @@ _sig("isg_problem_create_csr", [_i32, _P, _P, _P, ctypes.POINTER(_P)])
 _sig("isg_problem_create_fields", [_i32, _i64, _P, _P, _P, _P, ctypes.POINTER(_P)])
 _sig("isg_problem_create_torus", [_i32, _i32, _P, _P, ctypes.POINTER(_P)])
 _sig("isg_problem_info", [_P, _P, _P, _P, _P, _P])
+_sig("isg_problem_set_colouring", [_P, _i32])
 _sig("isg_problem_destroy", [_P], None)
 _sig("isg_anneal", [_P, _i32, _P, _i32, _u64, _i64, _P, ctypes.POINTER(_P)])
 _sig("isg_anneal_ex", [_P, _i32, _P, _i32, _u64, _i64, ctypes.POINTER(isg_options), _P,
@@ -205,6 +206,14 @@ def isg_problem_info(p, colors: bool = False) -> dict:
     return d
 
 
+COLOURING_GREEDY, COLOURING_SMALLEST_LAST = 0, 1
+
+
+def isg_problem_set_colouring(p, method: int):
+    """Colour classes of a graph instance: 0 greedy by id (default), 1 smallest-last."""
+    _check(_lib.isg_problem_set_colouring(_h(p), int(method)))
+
+
 def isg_problem_destroy(p):
     if isinstance(p, Problem):
         p.close()
@@ -212,15 +221,20 @@ def isg_problem_destroy(p):
         _lib.isg_problem_destroy(p)
 
 
-def problem_of(instance) -> Problem:
-    """libisg instance of a generator object from ``paper_2311_09275_gb300.inputs``."""
+def problem_of(instance, colouring: int = COLOURING_GREEDY) -> Problem:
+    """libisg instance of a generator object from ``paper_2311_09275_gb300.inputs``
+    (graphs coloured by ``colouring``, an isg_colouring)."""
     if hasattr(instance, "L"):
         return isg_problem_create_torus(instance.L, instance.W, instance.j_right,
                                         instance.j_down)
     if getattr(instance, "h", None) is not None:
-        return isg_problem_create_fields(instance.n, instance.u, instance.v, instance.w,
-                                         instance.h)
-    return isg_problem_create_edges(instance.n, instance.u, instance.v, instance.w)
+        p = isg_problem_create_fields(instance.n, instance.u, instance.v, instance.w,
+                                      instance.h)
+    else:
+        p = isg_problem_create_edges(instance.n, instance.u, instance.v, instance.w)
+    if colouring != COLOURING_GREEDY:
+        isg_problem_set_colouring(p, colouring)
+    return p
 
 
 # ------------------------------------------------------------------ results

@@ -90,7 +90,7 @@ def test_colouring_matches_oracle(isg, n, m, seed):
     g = I.random_graph(n, m, seed)
     p = isg.problem_of(g)
     info = isg.isg_problem_info(p, colors=True)
-    col, nc = oracle.csr_of(g).colouring()
+    col, nc = oracle.csr_of(g).greedy_colouring()
     assert info["n_colors"] == nc
     assert np.array_equal(info["colors"], col)
     assert info["total_weight"] == int(g.w.sum()) and info["m"] == m
@@ -99,12 +99,15 @@ def test_colouring_matches_oracle(isg, n, m, seed):
 def test_torus_colouring_is_checkerboard(isg):
     t = I.torus(8, 12, 5)
     info = isg.isg_problem_info(isg.problem_of(t), colors=True)
-    col, nc = oracle.csr_of(t).colouring()
+    col, nc = oracle.csr_of(t).greedy_colouring()
     assert info["n_colors"] == 2 and np.array_equal(info["colors"], col)
-    # the same torus as a plain edge list: smallest-last gives the same checkerboard
+    # the same torus as a plain edge list, either colouring: the same checkerboard
     u, v, w = t.edges()
-    info = isg.isg_problem_info(isg.isg_problem_create_edges(t.n, u, v, w), colors=True)
-    assert info["n_colors"] == 2 and np.array_equal(info["colors"], col)
+    for method in (0, 1):
+        q = isg.isg_problem_create_edges(t.n, u, v, w)
+        isg.isg_problem_set_colouring(q, method)
+        info = isg.isg_problem_info(q, colors=True)
+        assert info["n_colors"] == 2 and np.array_equal(info["colors"], col)
 
 
 @pytest.mark.parametrize("kind", ["linear", "geometric", "extremes"])
@@ -146,10 +149,37 @@ def test_fields_validation_and_info(isg):
         isg.isg_problem_create_fields(3, [0], [0], [1], [0, 0, 0])
 
 
+@pytest.mark.parametrize("n,m,seed", [(2000, 1999, 1), (10000, 9999, 1), (3000, 6000, 2),
+                                      (500, 20000, 3), (12000, 150000, 9)])
+def test_smallest_last_colouring_matches_oracle(isg, n, m, seed):
+    g = I.random_graph(n, m, seed)
+    p = isg.problem_of(g, colouring=1)
+    info = isg.isg_problem_info(p, colors=True)
+    col, nc = oracle.csr_of(g).smallest_last_colouring()
+    assert info["n_colors"] == nc and np.array_equal(info["colors"], col)
+
+
 def test_colouring_matches_oracle_on_geometric_and_fields(isg):
     """Geometric graphs (many equal degrees, so the tie rule decides) and an
-    independent-set instance with fields colour as the oracle does."""
+    independent-set instance with fields colour as the oracle does, both ways."""
     for g in (I.geometric_graph(3000, 6.0, 4), I.independent_set_instance(I.geometric_graph(2000, 9.0, 5))):
         info = isg.isg_problem_info(isg.problem_of(g), colors=True)
-        col, nc = oracle.csr_of(g).colouring()
+        col, nc = oracle.csr_of(g).greedy_colouring()
         assert info["n_colors"] == nc and np.array_equal(info["colors"], col)
+        info = isg.isg_problem_info(isg.problem_of(g, colouring=1), colors=True)
+        col, nc = oracle.csr_of(g).smallest_last_colouring()
+        assert info["n_colors"] == nc and np.array_equal(info["colors"], col)
+
+
+def test_set_colouring_rejects(isg):
+    t = I.torus(8, 8, 1)
+    with pytest.raises(isg.IsgError):
+        isg.isg_problem_set_colouring(isg.problem_of(t), 1)  # tori keep the checkerboard
+    p = isg.problem_of(I.random_graph(50, 80, 2))
+    with pytest.raises(isg.IsgError):
+        isg.isg_problem_set_colouring(p, 7)
+    isg.isg_problem_set_colouring(p, 1)
+    isg.isg_problem_set_colouring(p, 0)  # back to greedy
+    g = I.random_graph(50, 80, 2)
+    info = isg.isg_problem_info(p, colors=True)
+    assert np.array_equal(info["colors"], oracle.csr_of(g).greedy_colouring()[0])

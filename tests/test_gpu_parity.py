@@ -358,6 +358,24 @@ def test_torus_80x100_full_size_sampled(isg):
     assert np.array_equal(isg.isg_energy(p, res.best_all()), res.best(spins=False)[3])
 
 
+@pytest.mark.parametrize("kernel,cluster,threads", [(4, 12, 512), (4, 3, 128), (2, 4, 256),
+                                                   (3, 0, 0)])
+def test_smallest_last_colouring_bit_exact(isg, kernel, cluster, threads):
+    """Instances re-coloured smallest-last run those classes, bit for bit with the
+    oracle given the oracle's own smallest-last colouring."""
+    g = I.random_graph(3000, 2999, 5)
+    c = oracle.csr_of(g)
+    col, nc = c.smallest_last_colouring()
+    betas = I.geometric_betas(0.1, 5.0, 150)
+    orc = oracle.anneal(c, 40, betas, 7, colour=col, check_energy=True)
+    p = isg.problem_of(g, colouring=isg.COLOURING_SMALLEST_LAST)
+    assert isg.isg_problem_info(p)["n_colors"] == nc
+    res = isg.isg_anneal(p, 40, betas, 7, kernel=kernel, cluster_ctas=cluster, threads=threads)
+    assert_same(res, orc)
+    with pytest.raises(isg.IsgError):
+        isg.isg_problem_set_colouring(p, isg.COLOURING_GREEDY)  # device state exists now
+
+
 @functools.lru_cache(maxsize=1)
 def random_10000_oracle(reps):
     sv = I.random_10000()
@@ -396,3 +414,17 @@ def test_batch_512_full_size_sampled(isg):
     k = 100
     orc = oracle.anneal(oracle.csr_of(batch[k].problem), 32, batch[k].betas, batch[k].seed)
     assert_same(outs[k], orc)
+
+
+@pytest.mark.slow
+def test_random_10000_smallest_last_full_size_sampled(isg):
+    """The random-graph workload re-coloured smallest-last (3 classes) at the
+    12-CTA shape: sampled replicas equal the oracle run on the same classes."""
+    sv = I.random_10000()
+    c = oracle.csr_of(sv.problem)
+    col, nc = c.smallest_last_colouring()
+    reps = [0, 7, 64, 255]
+    orc = oracle.anneal(c, reps, sv.betas, sv.seed, colour=col)
+    p = isg.problem_of(sv.problem, colouring=isg.COLOURING_SMALLEST_LAST)
+    res = isg.isg_anneal(p, sv.replicas, sv.betas, sv.seed, cluster_ctas=12, threads=512)
+    assert_same(res, orc, reps=reps)

@@ -209,15 +209,15 @@ def test_smallest_last_small_closed_forms():
     smallest id), reverse colouring gives [2,1,0,1,0], numbering by smallest
     vertex [0,1,2,1,2].  Star with hub 0: removal 1,2,3, then hub 0 (degree 1
     ties with leaf 4, smaller id), then 4: two classes {0}, {1..4}.  K5: five."""
-    col, nc = _graph(5, [(i, (i + 1) % 5) for i in range(5)]).colouring()
+    col, nc = _graph(5, [(i, (i + 1) % 5) for i in range(5)]).smallest_last_colouring()
     assert col.tolist() == [0, 1, 2, 1, 2] and nc == 3
-    col, nc = _graph(5, [(0, i) for i in range(1, 5)]).colouring()
+    col, nc = _graph(5, [(0, i) for i in range(1, 5)]).smallest_last_colouring()
     assert col.tolist() == [0, 1, 1, 1, 1] and nc == 2
-    col, nc = _graph(5, [(a, b) for a in range(5) for b in range(a + 1, 5)]).colouring()
+    col, nc = _graph(5, [(a, b) for a in range(5) for b in range(a + 1, 5)]).smallest_last_colouring()
     assert col.tolist() == [0, 1, 2, 3, 4] and nc == 5
     # odd wheel (hub 0, rim 1..5): chromatic number 4, degeneracy 3
     c = _graph(6, [(0, i) for i in range(1, 6)] + [(i, i % 5 + 1) for i in range(1, 6)])
-    col, nc = c.colouring()
+    col, nc = c.smallest_last_colouring()
     assert nc == 4 and _proper(c, col)
 
 
@@ -228,7 +228,7 @@ def test_smallest_last_within_degeneracy_plus_one(seed):
     classes numbered by their smallest vertex."""
     g = I.random_graph(11, 18 + 3 * seed, 100 + seed)
     c = oracle.csr_of(g)
-    col, nc = c.colouring()
+    col, nc = c.smallest_last_colouring()
     assert _proper(c, col)
     assert nc <= _degeneracy(c) + 1
     firsts = [int(np.flatnonzero(col == k)[0]) for k in range(nc)]
@@ -240,7 +240,7 @@ def test_smallest_last_on_even_torus_edges_is_checkerboard(L, W):
     """A torus given as a plain edge list gets the checkerboard, (r + c) even first."""
     t = I.torus(L, W, 7)
     u, v, w = t.edges()
-    col, nc = oracle.Csr(t.n, u, v, w).colouring()
+    col, nc = oracle.Csr(t.n, u, v, w).smallest_last_colouring()
     r, c = np.divmod(np.arange(L * W), W)
     assert nc == 2 and np.array_equal(col, (r + c) % 2)
 
@@ -249,7 +249,7 @@ def test_smallest_last_is_proper_on_random_graphs():
     for seed in (1, 2):
         g = I.random_graph(2000, 4000, seed)
         c = oracle.csr_of(g)
-        col, nc = c.colouring()
+        col, nc = c.smallest_last_colouring()
         assert _proper(c, col)
         assert nc <= c.kmax() + 1
 
