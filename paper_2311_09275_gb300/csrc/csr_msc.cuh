@@ -206,10 +206,11 @@ __device__ __forceinline__ uint32_t update_vertex(const uint32_t *spin, int v, i
       if (eq != 0u) acc &= ~eq | below(pre, row[d - 2 * lv]);
     }
   }
-  // energy change of the accepted lanes: 2 (d - 2U)
+  // energy change of the accepted lanes: 2 (d - 2U); d <= 63 (6 bits)
+  uint32_t da[kPlanesU];
 #pragma unroll
-  for (int b = 0; b < 7; ++b)
-    if ((d >> b) & 1) cd.add_at(b, acc);
+  for (int b = 0; b < kPlanesU; ++b) da[b] = ((d >> b) & 1) ? acc : 0u;
+  cd.add_sliced(da);
   uint32_t ua[kPlanesU];
 #pragma unroll
   for (int p = 0; p < kPlanesU; ++p) ua[p] = u[p] & acc;
@@ -410,7 +411,8 @@ __device__ void gm_word(const GraphMscSolve &s, const GraphMscLaunch &L, int wor
         if (K == 1) {
           spin[v] = sn;
         } else {
-          for (int r = 0; r < K; ++r) peer_smem(spin, (uint32_t)r)[v] = sn;
+          const uint32_t a = (uint32_t)__cvta_generic_to_shared(spin + v);
+          for (int r = 0; r < K; ++r) st_cluster_u32(a, (uint32_t)r, sn);
         }
       }
       if (c + 1 < nc) {

@@ -224,4 +224,12 @@ __device__ __forceinline__ T *peer_smem(T *local, uint32_t rank) {
   return cg::this_cluster().map_shared_rank(local, rank);
 }
 
+// Store v at shared-memory address a (a CTA-local shared address) of CTA
+// `rank` of the cluster, through the 32-bit cluster window.
+__device__ __forceinline__ void st_cluster_u32(uint32_t a, uint32_t rank, uint32_t v) {
+  uint32_t ra;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;\n" : "=r"(ra) : "r"(a), "r"(rank));
+  asm volatile("st.shared::cluster.u32 [%0], %1;\n" ::"r"(ra), "r"(v));
+}
+
 }  // namespace isg
