@@ -425,8 +425,7 @@ __device__ void csr_solve(const CsrSolve &s, const CsrLaunch &L, int quad0, int 
             if (K == 1) {
               spin[q * n + v] = sn;
             } else {
-              const uint32_t a = (uint32_t)__cvta_generic_to_shared(spin + q * n + v);
-              for (int r = 0; r < K; ++r) st_cluster_u32(a, (uint32_t)r, sn);
+              for (int r = 0; r < K; ++r) peer_smem(spin, (uint32_t)r)[q * n + v] = sn;
             }
           }
         }
