@@ -61,8 +61,11 @@ __global__ void __launch_bounds__(256) pt_exchange_kernel(
 // carry k to G | (P & k) (G: its carry out from k = 0, P: AND of its D), and
 // these maps compose associatively, so a warp scan of them gives every lane
 // its incoming carry; the wrap carry is the whole ring's G (the least fixed
-// point of k = G | (P & k)).  Returns whether a bit was set.
-__device__ bool ring_spread(uint32_t *C, const uint32_t *D, int base, int len, int stride) {
+// point of k = G | (P & k)).  A site at ring position x that gains a bit
+// marks ring x of the other orientation in `mark` (one bit per ring).
+// Returns whether a bit was set.
+__device__ bool ring_spread(uint32_t *C, const uint32_t *D, int base, int len, int stride,
+                            uint32_t *mark) {
   const int lane = (int)(threadIdx.x & 31u);
   const int seg = (len + 31) / 32;
   const int x0 = min(len, lane * seg), x1 = min(len, x0 + seg);
@@ -93,16 +96,27 @@ __device__ bool ring_spread(uint32_t *C, const uint32_t *D, int base, int len, i
       pe = 0xFFFFFFFFu;
     }
     uint32_t carry = ge | (pe & g_all);
+    // marks gathered per mark word along the segment, one atomic per word
+    int mw = -1;
+    uint32_t mm = 0u;
     for (int x = x0; x < x1; ++x) {
-      const int i = base + (dir == 0 ? x : len - 1 - x) * stride;
+      const int pos = dir == 0 ? x : len - 1 - x;
+      const int i = base + pos * stride;
       const uint32_t cur = C[i];
       const uint32_t v = cur | (D[i] & carry);
       if (v != cur) {
         C[i] = v;
         changed = true;
+        if ((pos >> 5) != mw) {
+          if (mm) atomicOr(&mark[mw], mm);
+          mw = pos >> 5;
+          mm = 0u;
+        }
+        mm |= 1u << (pos & 31);
       }
       carry = v;
     }
+    if (mm) atomicOr(&mark[mw], mm);
     __syncwarp();
   }
   return changed;
@@ -122,6 +136,10 @@ __global__ void __launch_bounds__(1024) pt_cluster_kernel(uint32_t *spins, int32
   const int n = L * W;
   const int k = k0 + (int)blockIdx.x;
   uint32_t *D = sm, *C = sm + n;
+  // rings (rows, columns) holding sites that gained a bit since the ring was
+  // last spread: only those can spread further
+  const int rwords = (L + 31) / 32, cwords = (W + 31) / 32;
+  uint32_t *rdirty = sm + 2 * n, *cdirty = rdirty + rwords;
   __shared__ int32_t wsum[32][16];
   __shared__ int64_t pick[16];
   __shared__ int changed;
@@ -129,6 +147,7 @@ __global__ void __launch_bounds__(1024) pt_cluster_kernel(uint32_t *spins, int32
   const int nt = (int)blockDim.x, tid = (int)threadIdx.x;
   const int chunk = (n + nt - 1) / nt;
   const int i0 = min(n, tid * chunk), i1 = min(n, i0 + chunk);
+  for (int w = (int)threadIdx.x; w < rwords + cwords; w += (int)blockDim.x) rdirty[w] = 0u;
   // 1. differing sites per pair, and this thread's count of them per pair
   int32_t cnt[16];
 #pragma unroll
@@ -182,6 +201,8 @@ __global__ void __launch_bounds__(1024) pt_cluster_kernel(uint32_t *spins, int32
         if ((D[i] >> (2 * m)) & 1u) {
           if (seen == p) {
             C[i] |= 1u << (2 * m);
+            atomicOr(&rdirty[(i / W) >> 5], 1u << ((i / W) & 31));
+            atomicOr(&cdirty[(i % W) >> 5], 1u << ((i % W) & 31));
             break;
           }
           ++seen;
@@ -193,19 +214,29 @@ __global__ void __launch_bounds__(1024) pt_cluster_kernel(uint32_t *spins, int32
   //    order of passes reaches the same fixed point).  Passes alternate
   //    between rows and columns, one warp per ring, and spread the bits along
   //    whole runs of differing sites at once; the number of passes follows the
-  //    number of turns of the clusters' paths, not their length.
-  for (int pass = 0, quiet = 0; quiet < 2; ++pass) {
-    if (tid == 0) changed = 0;
-    __syncthreads();
+  //    number of turns of the clusters' paths, not their length.  A pass
+  //    spreads only the rings marked since they were last spread, and marks
+  //    the rings of the other orientation through the sites that gained bits;
+  //    growth ends when a pass after the first (the seeds mark both
+  //    orientations) sets no bit.
+  for (int pass = 0;; ++pass) {
     const bool rows = (pass & 1) == 0;
     const int rings = rows ? L : W;
+    uint32_t *dirty = rows ? rdirty : cdirty, *other = rows ? cdirty : rdirty;
+    if (tid == 0) changed = 0;
+    __syncthreads();
     bool any = false;
     for (int g = warp; g < rings; g += nw)
-      any |= rows ? ring_spread(C, D, g * W, W, 1) : ring_spread(C, D, g, L, W);
+      if ((dirty[g >> 5] >> (g & 31)) & 1u)
+        any |= rows ? ring_spread(C, D, g * W, W, 1, other) : ring_spread(C, D, g, L, W, other);
     if (any) changed = 1;
     __syncthreads();
-    quiet = changed ? 0 : quiet + 1;  // stop after a row pass and a column pass change nothing
+    for (int w = tid; w < (rows ? rwords : cwords); w += nt) dirty[w] = 0u;
+    const bool more = changed != 0 || pass == 0;
+    // every thread has read `changed` and cleared before the next pass marks
+    // this orientation again
     __syncthreads();
+    if (!more) break;
   }
   // 5. flip the clusters in both chains; recount the word's unsatisfied bonds
   SlicedCounter<NP> cntu;
@@ -244,7 +275,7 @@ cudaError_t pt_cluster(uint32_t *spins, int32_t *e_cur, const uint8_t *cbits, in
                        uint32_t key1, unsigned long long *flipped, cudaStream_t stream) {
   if (slots <= 0) return cudaSuccess;
   const int threads = 1024;
-  const size_t smem = 8 * (size_t)L * W;
+  const size_t smem = 8 * (size_t)L * W + 4 * (size_t)((L + 31) / 32 + (W + 31) / 32);
   const int per_thread = (L * W + threads - 1) / threads;  // sites per thread, 2 bonds each
   cudaError_t err;
   if (2 * per_thread < (1 << 6)) {

@@ -83,6 +83,9 @@ def test_tempering_rejects_bad_input(isg):
     (20, 16, [0.5, 1.0, 2.0], 5, 2, 3),
     (8, 6, [1.2], 9, 1, 1),
     (40, 30, [0.4, 0.9, 1.6, 2.4, 3.0], 4, 4, 5),
+    # rings longer than 1,024 sites: a lane's segment spans three words of ring marks
+    (4, 1100, [0.4, 1.0, 2.0], 3, 2, 2),
+    (1100, 4, [0.4, 1.0, 2.0], 3, 2, 2),
 ])
 def test_tempering_with_cluster_moves_bit_exact(isg, L, W, betas, rounds, per_round, icm):
     t = I.torus(L, W, 60 + L)
