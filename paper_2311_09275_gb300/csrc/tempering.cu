@@ -62,8 +62,10 @@ __global__ void __launch_bounds__(256) pt_exchange_kernel(
 // these maps compose associatively, so a warp scan of them gives every lane
 // its incoming carry; the wrap carry is the whole ring's G (the least fixed
 // point of k = G | (P & k)).  A site at ring position x that gains a bit
-// marks ring x of the other orientation in `mark` (one bit per ring).
-// Returns whether a bit was set.
+// marks ring x of the other orientation in `mark` (one bit per ring).  Bits
+// are only ever set (atomically: rings crossing this one may grow at the same
+// time; a bit they set after this ring read the site is marked for the next
+// pass by them).  Returns whether a bit was set.
 __device__ bool ring_spread(uint32_t *C, const uint32_t *D, int base, int len, int stride,
                             uint32_t *mark) {
   const int lane = (int)(threadIdx.x & 31u);
@@ -105,7 +107,7 @@ __device__ bool ring_spread(uint32_t *C, const uint32_t *D, int base, int len, i
       const uint32_t cur = C[i];
       const uint32_t v = cur | (D[i] & carry);
       if (v != cur) {
-        C[i] = v;
+        atomicOr(&C[i], v);  // rings of both orientations grow at once
         changed = true;
         if ((pos >> 5) != mw) {
           if (mm) atomicOr(&mark[mw], mm);
@@ -139,7 +141,8 @@ __global__ void __launch_bounds__(1024) pt_cluster_kernel(uint32_t *spins, int32
   // rings (rows, columns) holding sites that gained a bit since the ring was
   // last spread: only those can spread further
   const int rwords = (L + 31) / 32, cwords = (W + 31) / 32;
-  uint32_t *rdirty = sm + 2 * n, *cdirty = rdirty + rwords;
+  uint32_t *rdirty = sm + 2 * n, *cdirty = rdirty + rwords;  // two buffers each: this pass, next
+  uint32_t *rdirty1 = cdirty + cwords, *cdirty1 = rdirty1 + rwords;
   __shared__ int32_t wsum[32][16];
   __shared__ int64_t pick[16];
   __shared__ int changed;
@@ -147,7 +150,7 @@ __global__ void __launch_bounds__(1024) pt_cluster_kernel(uint32_t *spins, int32
   const int nt = (int)blockDim.x, tid = (int)threadIdx.x;
   const int chunk = (n + nt - 1) / nt;
   const int i0 = min(n, tid * chunk), i1 = min(n, i0 + chunk);
-  for (int w = (int)threadIdx.x; w < rwords + cwords; w += (int)blockDim.x) rdirty[w] = 0u;
+  for (int w = (int)threadIdx.x; w < 2 * (rwords + cwords); w += (int)blockDim.x) rdirty[w] = 0u;
   // 1. differing sites per pair, and this thread's count of them per pair
   int32_t cnt[16];
 #pragma unroll
@@ -211,30 +214,32 @@ __global__ void __launch_bounds__(1024) pt_cluster_kernel(uint32_t *spins, int32
   }
   __syncthreads();
   // 4. grow the clusters to their components (bits only ever get set, so any
-  //    order of passes reaches the same fixed point).  Passes alternate
-  //    between rows and columns, one warp per ring, and spread the bits along
-  //    whole runs of differing sites at once; the number of passes follows the
-  //    number of turns of the clusters' paths, not their length.  A pass
-  //    spreads only the rings marked since they were last spread, and marks
-  //    the rings of the other orientation through the sites that gained bits;
-  //    growth ends when a pass after the first (the seeds mark both
-  //    orientations) sets no bit.
+  //    order of updates reaches the same fixed point).  A pass spreads, one
+  //    warp per ring, the bits along whole runs of differing sites of every
+  //    row and column marked since it was last spread, rows and columns at
+  //    once; sites that gain bits mark the crossing rings for the next pass.
+  //    The number of passes follows the number of turns of the clusters'
+  //    paths, not their length; growth ends when a pass sets no bit.
   for (int pass = 0;; ++pass) {
-    const bool rows = (pass & 1) == 0;
-    const int rings = rows ? L : W;
-    uint32_t *dirty = rows ? rdirty : cdirty, *other = rows ? cdirty : rdirty;
+    uint32_t *rcur = (pass & 1) ? rdirty1 : rdirty, *ccur = (pass & 1) ? cdirty1 : cdirty;
+    uint32_t *rnxt = (pass & 1) ? rdirty : rdirty1, *cnxt = (pass & 1) ? cdirty : cdirty1;
     if (tid == 0) changed = 0;
     __syncthreads();
     bool any = false;
-    for (int g = warp; g < rings; g += nw)
-      if ((dirty[g >> 5] >> (g & 31)) & 1u)
-        any |= rows ? ring_spread(C, D, g * W, W, 1, other) : ring_spread(C, D, g, L, W, other);
+    for (int g = warp; g < L + W; g += nw) {
+      if (g < L) {
+        if ((rcur[g >> 5] >> (g & 31)) & 1u) any |= ring_spread(C, D, g * W, W, 1, cnxt);
+      } else {
+        const int c = g - L;
+        if ((ccur[c >> 5] >> (c & 31)) & 1u) any |= ring_spread(C, D, c, L, W, rnxt);
+      }
+    }
     if (any) changed = 1;
     __syncthreads();
-    for (int w = tid; w < (rows ? rwords : cwords); w += nt) dirty[w] = 0u;
-    const bool more = changed != 0 || pass == 0;
-    // every thread has read `changed` and cleared before the next pass marks
-    // this orientation again
+    for (int w = tid; w < rwords + cwords; w += nt) rcur[w] = 0u;  // rcur, ccur: adjacent
+    const bool more = changed != 0;
+    // every thread has read `changed` and cleared this pass's marks before the
+    // next pass marks them again
     __syncthreads();
     if (!more) break;
   }
@@ -275,7 +280,7 @@ cudaError_t pt_cluster(uint32_t *spins, int32_t *e_cur, const uint8_t *cbits, in
                        uint32_t key1, unsigned long long *flipped, cudaStream_t stream) {
   if (slots <= 0) return cudaSuccess;
   const int threads = 1024;
-  const size_t smem = 8 * (size_t)L * W + 4 * (size_t)((L + 31) / 32 + (W + 31) / 32);
+  const size_t smem = 8 * (size_t)L * W + 8 * (size_t)((L + 31) / 32 + (W + 31) / 32);
   const int per_thread = (L * W + threads - 1) / threads;  // sites per thread, 2 bonds each
   cudaError_t err;
   if (2 * per_thread < (1 << 6)) {
