@@ -124,6 +124,120 @@ __device__ bool ring_spread(uint32_t *C, const uint32_t *D, int base, int len, i
   return changed;
 }
 
+// ring_spread for rings of up to 32 x SEG sites with each lane's segment held
+// in registers across both directions (one shared-memory read per site); the
+// backward direction scans the lanes in descending order.  Same result as
+// ring_spread.
+template <int SEG>
+__device__ bool ring_spread_reg(uint32_t *C, const uint32_t *D, int base, int len, int stride,
+                                uint32_t *mark) {
+  const int lane = (int)(threadIdx.x & 31u);
+  const int seg = (len + 31) / 32;
+  const int x0 = min(len, lane * seg), cnt = min(len, x0 + seg) - x0;
+  uint32_t d[SEG], c[SEG], c_in[SEG];
+#pragma unroll
+  for (int j = 0; j < SEG; ++j) {
+    const int i = base + (x0 + j) * stride;
+    d[j] = j < cnt ? D[i] : 0u;
+    c[j] = j < cnt ? C[i] : 0u;
+    c_in[j] = c[j];
+  }
+  // forward: increasing positions, lanes in ascending order
+  {
+    uint32_t g = 0u, pm = 0xFFFFFFFFu;
+#pragma unroll
+    for (int j = 0; j < SEG; ++j)
+      if (j < cnt) {
+        g = c[j] | (d[j] & g);
+        pm &= d[j];
+      }
+    uint32_t G = g, Pm = pm;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t Ge = __shfl_up_sync(0xFFFFFFFFu, G, o);
+      const uint32_t Pe = __shfl_up_sync(0xFFFFFFFFu, Pm, o);
+      if (lane >= o) {
+        G = G | (Pm & Ge);
+        Pm = Pm & Pe;
+      }
+    }
+    const uint32_t g_all = __shfl_sync(0xFFFFFFFFu, G, 31);
+    uint32_t ge = __shfl_up_sync(0xFFFFFFFFu, G, 1), pe = __shfl_up_sync(0xFFFFFFFFu, Pm, 1);
+    if (lane == 0) {
+      ge = 0u;
+      pe = 0xFFFFFFFFu;
+    }
+    uint32_t carry = ge | (pe & g_all);
+#pragma unroll
+    for (int j = 0; j < SEG; ++j)
+      if (j < cnt) {
+        c[j] |= d[j] & carry;
+        carry = c[j];
+      }
+  }
+  // backward: decreasing positions, lanes in descending order
+  {
+    uint32_t g = 0u, pm = 0xFFFFFFFFu;
+#pragma unroll
+    for (int j = SEG - 1; j >= 0; --j)
+      if (j < cnt) {
+        g = c[j] | (d[j] & g);
+        pm &= d[j];
+      }
+    uint32_t G = g, Pm = pm;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t Ge = __shfl_down_sync(0xFFFFFFFFu, G, o);
+      const uint32_t Pe = __shfl_down_sync(0xFFFFFFFFu, Pm, o);
+      if (lane + o < 32) {
+        G = G | (Pm & Ge);
+        Pm = Pm & Pe;
+      }
+    }
+    const uint32_t g_all = __shfl_sync(0xFFFFFFFFu, G, 0);
+    uint32_t ge = __shfl_down_sync(0xFFFFFFFFu, G, 1), pe = __shfl_down_sync(0xFFFFFFFFu, Pm, 1);
+    if (lane == 31) {
+      ge = 0u;
+      pe = 0xFFFFFFFFu;
+    }
+    uint32_t carry = ge | (pe & g_all);
+#pragma unroll
+    for (int j = SEG - 1; j >= 0; --j)
+      if (j < cnt) {
+        c[j] |= d[j] & carry;
+        carry = c[j];
+      }
+  }
+  // write back the sites that gained bits, marking their crossing rings
+  bool changed = false;
+  int mw = -1;
+  uint32_t mm = 0u;
+#pragma unroll
+  for (int j = 0; j < SEG; ++j)
+    if (j < cnt && c[j] != c_in[j]) {
+      const int pos = x0 + j;
+      atomicOr(&C[base + pos * stride], c[j]);
+      changed = true;
+      if ((pos >> 5) != mw) {
+        if (mm) atomicOr(&mark[mw], mm);
+        mw = pos >> 5;
+        mm = 0u;
+      }
+      mm |= 1u << (pos & 31);
+    }
+  if (mm) atomicOr(&mark[mw], mm);
+  __syncwarp();
+  return changed;
+}
+
+// Ring update dispatched on the ring length.
+__device__ __forceinline__ bool ring_update(uint32_t *C, const uint32_t *D, int base, int len,
+                                            int stride, uint32_t *mark) {
+  if (len <= 128) return ring_spread_reg<4>(C, D, base, len, stride, mark);
+  if (len <= 256) return ring_spread_reg<8>(C, D, base, len, stride, mark);
+  return ring_spread(C, D, base, len, stride, mark);
+}
+
 // Houdayer cluster moves on one slot word per CTA (slots k0 + blockIdx.x):
 // chains 2m and 2m+1 (lanes) form pair m.  D[i] holds, at bit 2m, whether
 // the pair differs at site i; C[i] grows, at the same bits, the connected
@@ -228,10 +342,10 @@ __global__ void __launch_bounds__(1024) pt_cluster_kernel(uint32_t *spins, int32
     bool any = false;
     for (int g = warp; g < L + W; g += nw) {
       if (g < L) {
-        if ((rcur[g >> 5] >> (g & 31)) & 1u) any |= ring_spread(C, D, g * W, W, 1, cnxt);
+        if ((rcur[g >> 5] >> (g & 31)) & 1u) any |= ring_update(C, D, g * W, W, 1, cnxt);
       } else {
         const int c = g - L;
-        if ((ccur[c >> 5] >> (c & 31)) & 1u) any |= ring_spread(C, D, c, L, W, rnxt);
+        if ((ccur[c >> 5] >> (c & 31)) & 1u) any |= ring_update(C, D, c, L, W, rnxt);
       }
     }
     if (any) changed = 1;

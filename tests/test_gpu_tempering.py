@@ -83,7 +83,10 @@ def test_tempering_rejects_bad_input(isg):
     (20, 16, [0.5, 1.0, 2.0], 5, 2, 3),
     (8, 6, [1.2], 9, 1, 1),
     (40, 30, [0.4, 0.9, 1.6, 2.4, 3.0], 4, 4, 5),
-    # rings longer than 1,024 sites: a lane's segment spans three words of ring marks
+    # rings of 129..256 sites (8 sites per lane) and longer than 1,024 sites (a lane's
+    # segment spans three words of ring marks)
+    (6, 200, [0.4, 1.0, 2.0], 3, 2, 2),
+    (200, 6, [0.4, 1.0, 2.0], 3, 2, 2),
     (4, 1100, [0.4, 1.0, 2.0], 3, 2, 2),
     (1100, 4, [0.4, 1.0, 2.0], 3, 2, 2),
 ])
