@@ -127,17 +127,17 @@ __device__ __forceinline__ uint32_t field_unsat(uint32_t s0, int32_t hv) {
   return hv > 0 ? s0 : ~s0;
 }
 
-// One vertex of one replica word (and, FIELD, its local field hv): its 32
+// One vertex of one replica word (adjacency entries [p0, p1); and, FIELD, its
+// local field hv): its 32
 // uniforms are pre (drawn by the caller), or with LAZY filled by draw(uu)
 // only when some replica is uphill.  Returns the new word; accumulates the
 // accepted flips' d and U into the energy counters.
 template <int NP, bool FIELD, bool LAZY, typename Draw>
-__device__ __forceinline__ uint32_t update_vertex(const uint32_t *spin, int v, int i,
+__device__ __forceinline__ uint32_t update_vertex(const uint32_t *spin, int v, int p0, int p1,
                                                   const GmAdj &a, const uint32_t *row,
                                                   const uint4 (&pre)[8], Draw draw, int32_t hv,
                                                   SlicedCounter<NP> &cd, SlicedCounter<NP> &cu) {
   const uint32_t s0 = spin[v];
-  const int p0 = a.row[i], p1 = a.row[i + 1];
   int d = p1 - p0;
   uint32_t u[kPlanesU];
 #pragma unroll
@@ -392,8 +392,33 @@ __device__ void gm_word(const GraphMscSolve &s, const GraphMscLaunch &L, int wor
     cu.clear();
     for (int c = 0; c < nc; ++c) {
       const int lo = clo[c], hi = chi[c], ob = cob[c];
+      // adjacency in global memory: the next vertex's row bounds and id are
+      // loaded one iteration ahead, off the current vertex's dependent chain
+      int n0 = 0, n1 = 0, norig = 0;
+      if (!STAGED && lo + (int)threadIdx.x < hi) {
+        const int vn = lo + (int)threadIdx.x;
+        n0 = adj.row[vn];
+        n1 = adj.row[vn + 1];
+        norig = adj.orig[vn];
+      }
       for (int v = lo + threadIdx.x; v < hi; v += blockDim.x) {
         const int i = ob + (v - lo);
+        int p0, p1, og;
+        if (STAGED) {
+          p0 = adj.row[i];
+          p1 = adj.row[i + 1];
+          og = adj.orig[i];
+        } else {
+          p0 = n0;
+          p1 = n1;
+          og = norig;
+          const int vn = v + (int)blockDim.x;
+          if (vn < hi) {
+            n0 = adj.row[vn];
+            n1 = adj.row[vn + 1];
+            norig = adj.orig[vn];
+          }
+        }
         // improved replicas take their best state from v as it stood at the
         // end of the previous sweep (v has not been updated since)
         if (imp != 0u) {
@@ -401,13 +426,11 @@ __device__ void gm_word(const GraphMscSolve &s, const GraphMscLaunch &L, int wor
           else gbest[v] = (gbest[v] & ~imp) | (spin[v] & imp);
         }
         const int32_t hv = !has_field ? 0 : (STAGED ? lfield[i] : __ldg(&s.field[v]));
-        auto draw = [&](uint4 (&out)[8]) {
-          vertex_uniforms((uint32_t)adj.orig[i], bp, s.rk, out);
-        };
-        if (PREFETCH && !ready) vertex_uniforms((uint32_t)adj.orig[i], bp, s.rk, uu);
+        auto draw = [&](uint4 (&out)[8]) { vertex_uniforms((uint32_t)og, bp, s.rk, out); };
+        if (PREFETCH && !ready) vertex_uniforms((uint32_t)og, bp, s.rk, uu);
         ready = false;
         const uint32_t sn =
-            update_vertex<NP, FIELD, !PREFETCH>(spin, v, i, adj, row, uu, draw, hv, cd, cu);
+            update_vertex<NP, FIELD, !PREFETCH>(spin, v, p0, p1, adj, row, uu, draw, hv, cd, cu);
         if (K == 1) {
           spin[v] = sn;
         } else {
