@@ -16,7 +16,10 @@
 // A CTA stages the adjacency of the slices it owns in shared memory when it
 // fits, and then keeps their best state there too.  Per-replica energy
 // changes are accumulated in bit-sliced counters (sum over accepted flips of
-// d, and of U: the change is 2 (d - 2U)) and reduced once per sweep.
+// d, and of U: the change is 2 (d - 2U)) and reduced once per sweep.  The
+// uniforms do not depend on the spins: a thread draws those of its first
+// vertex of the next class between its arrival at the class barrier and the
+// wait for it, so that the Philox work overlaps the barrier.
 //
 // Local fields (instances whose weights are all +1): the term h s of vertex
 // v counts as |h| extra bonds to a fixed +1 spin with coupling sign(h), so d
@@ -50,7 +53,7 @@ __host__ __device__ __forceinline__ GmSmem gm_layout(int n, int K, int n_colours
   m.lbest = align16(m.lcol + sizeof(int32_t) * (size_t)own_nnz);
   m.lfield = align16(m.lbest + sizeof(uint32_t) * (size_t)own_n);
   m.ocls = align16(m.lfield + (fields ? sizeof(int32_t) * (size_t)own_n : 0));
-  m.trow = align16(m.ocls + sizeof(int32_t) * 3 * (size_t)n_colours);
+  m.trow = align16(m.ocls + sizeof(int32_t) * 3 * (size_t)n_colours);  // class slice table
   m.part = align16(m.trow + 2 * sizeof(uint32_t) * (size_t)kmax1);
   m.lane_acc = m.part + 2 * sizeof(int32_t) * 32 * (size_t)K;
   m.total = align16(m.lane_acc + sizeof(int32_t) * 32);

@@ -13,7 +13,9 @@
 // each class a CTA owns is a contiguous id range, so its adjacency is a
 // contiguous slice of the CSR: when it fits, the CTA stages those slices
 // (row offsets, neighbour ids, weights, original ids) in shared memory once,
-// and every neighbour gather of the sweep loop is a shared-memory load.
+// and every neighbour gather of the sweep loop is a shared-memory load.  A
+// thread draws the Philox blocks (and reads the field) of its first vertex of
+// the next class between its arrival at the class barrier and the wait for it.
 //
 // Local fields: for graphs whose weights are all +1, or all +1/-1, the four
 // lanes' counts of -1 neighbours are summed in one 32-bit add per neighbour

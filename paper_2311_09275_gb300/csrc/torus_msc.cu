@@ -13,7 +13,10 @@
 // intra-phase synchronisation; updated band-edge rows are written straight
 // into the neighbouring CTA's halo (distributed shared memory), and one
 // cluster barrier separates the phases.  Per-replica energy changes are
-// accumulated in bit-sliced counters and reduced once per sweep.
+// accumulated in bit-sliced counters and reduced once per sweep.  The
+// acceptance masks of a thread's first site of the next phase depend only on
+// its uniforms and the sweep's thresholds: they are built between the
+// thread's arrival at the phase barrier and the wait for it.
 #include <climits>
 
 #include "isg_device.cuh"
