@@ -339,6 +339,22 @@ def test_server_results_equal_solo_runs(isg):
     assert_same(got[k], orc)
 
 
+def test_server_smallest_last_instance(isg):
+    """A served graph re-coloured smallest-last runs its own classes: equal to the
+    oracle given the oracle's smallest-last colouring."""
+    g = I.random_graph(1500, 1499, 31)
+    c = oracle.csr_of(g)
+    col, _ = c.smallest_last_colouring()
+    betas = I.geometric_betas(0.1, 5.0, 180)
+    p = isg.problem_of(g, colouring=isg.COLOURING_SMALLEST_LAST)
+    srv = isg.Server(1 << 30, 2, 50)
+    srv.submit(p, 32, betas, 9)
+    out = srv.poll(30.0)
+    srv.close()
+    assert out is not None
+    assert_same(out[1], oracle.anneal(c, 32, betas, 9, colour=col))
+
+
 # ------------------------------------------------------------------ full sizes
 @pytest.mark.slow
 def test_torus_80x100_full_size_sampled(isg):

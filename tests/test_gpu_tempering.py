@@ -131,3 +131,15 @@ def test_tempering_on_graphs_bit_exact(isg, make, betas, rounds, per_round, clus
                                      cluster_ctas=cluster, threads=threads)
     assert res.stats()["kernel"] == 4
     assert_same_pt(res, orc, len(betas) - 1)
+
+
+def test_tempering_on_smallest_last_graph(isg):
+    """Tempering on a graph re-coloured smallest-last follows those classes."""
+    g = I.random_graph(800, 799, 12)
+    c = oracle.csr_of(g)
+    col, _ = c.smallest_last_colouring()
+    betas = [0.3, 0.8, 1.6]
+    orc = oracle.parallel_tempering(c, betas, 4, 3, 17, colour=col)
+    res = isg.isg_parallel_tempering(isg.problem_of(g, colouring=isg.COLOURING_SMALLEST_LAST),
+                                     betas, 4, 3, 17)
+    assert_same_pt(res, orc, len(betas) - 1)
