@@ -315,11 +315,12 @@ void isg_result_destroy(isg_result *r);
  * are admitted while a slot is free and their device state fits in
  * device_mem_budget bytes; admitted requests run together in chunks of one
  * persistent kernel launch; each runs until its target or its sweep budget.
- * A chunk gives every request of a unit kind (torus words, graph words,
- * graph quads) the same work: sweeps_per_chunk sweeps for a 10,000-spin
- * instance, proportionally more for smaller ones (at least 1), times a
- * per-kind factor that the server adapts after every chunk so that the kinds'
- * kernels, which run concurrently, take equal time.
+ * A chunk advances every request by sweeps_per_chunk x sqrt(10,000 / n)
+ * sweeps (n its spin count; at least 1), times a per-unit-kind factor (torus
+ * words, graph words, graph quads) that the server adapts after every chunk
+ * so that the kinds' kernels, which run concurrently, take equal time: a
+ * larger instance does more work per chunk than a smaller one, but not in
+ * proportion to its size.
  * A request's result equals isg_anneal of the same arguments, bit for bit.
  * max_slots >= 1, sweeps_per_chunk >= 1. */
 isg_status isg_server_create(size_t device_mem_budget, int32_t max_slots,

@@ -18,6 +18,7 @@
 // re-run from the chunk start to t* + 1.  Results are therefore identical to
 // isg_anneal of the same request, alone.
 #include <algorithm>
+#include <cmath>
 #include <chrono>
 #include <climits>
 #include <condition_variable>
@@ -529,11 +530,13 @@ void worker_main(isg_server *s) {
     size_t nstatus = 0;
     for (size_t k = 0; k < s->active.size(); ++k) {
       Slot *sl = s->active[k];
-      // chunks hold equal work per unit: sweeps_per_chunk is the count for a
-      // 10,000-spin instance, scaled inversely with the instance size and by
-      // the unit kind's balance factor
+      // sweeps_per_chunk is the count for a 10,000-spin instance, scaled by
+      // the inverse square root of the instance size (a larger instance does
+      // more work per pass, so its time-to-target does not grow in proportion
+      // to its size) and by the unit kind's balance factor
       const int64_t sweeps = std::max<int64_t>(
-          1, (int64_t)((double)s->chunk * 10000.0 / sl->rq.p->n * s->kind_scale[kind_of(sl)]));
+          1, (int64_t)((double)s->chunk * std::sqrt(10000.0 / sl->rq.p->n) *
+                       s->kind_scale[kind_of(sl)]));
       t_end[k] = (int32_t)std::min<int64_t>(sl->t + sweeps, sl->rq.S);
       sl->t_end = t_end[k];
       nstatus += 2 * (size_t)sl->res->units;
