@@ -1,8 +1,10 @@
-// tempering.cu -- the exchange step of parallel tempering on multi-spin-coded
-// state: replica word k holds 32 chains at temperature slot k, so exchanging
-// the configurations of chain c between slots k and k+1 moves bit c of every
-// site word between the two words (a masked swap), and swaps the chains'
-// energies.
+// tempering.cu -- the exchange step and the Houdayer cluster moves of
+// parallel tempering on multi-spin-coded state: replica word k holds 32 chains
+// at temperature slot k, so exchanging the configurations of chain c between
+// slots k and k+1 moves bit c of every site word between the two words (a
+// masked swap) and swaps the chains' energies; a cluster move flips, in both
+// chains of a pair within one word, the connected component of a drawn site
+// among the sites where they differ.
 #include "isg_device.cuh"
 #include "isg_kernels.h"
 
