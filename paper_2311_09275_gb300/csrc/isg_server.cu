@@ -4,8 +4,9 @@
 // queue until a slot is free and their device state fits the memory budget;
 // then their state is allocated and they join the active set.  Every
 // iteration runs one chunk of sweeps for all active requests with the
-// persistent unit kernels (torus replica words and CSR replica quads; one CTA
-// per unit, longest instances first), reads back each unit's stop sweep,
+// persistent unit kernels (torus replica words, graph replica words and CSR
+// replica quads, the three kinds on concurrent streams; one CTA per unit,
+// longest instances first), reads back each unit's stop sweep,
 // retires requests that reached their target or sweep budget, and admits new
 // ones.  Requests of different sizes and sweep positions therefore share each
 // launch.
