@@ -57,7 +57,7 @@ struct Slot {
   bool finished = false;
 };
 
-constexpr int kServeThreads = 256;
+constexpr int kServeThreads = 512;
 
 size_t state_bytes_of(const isg_result *r) {
   // spins, best, e_cur, e_best are the leading, contiguous part of the allocation
@@ -240,7 +240,7 @@ void admit(isg_server *s) {
     }
     r->ctas = 0;
     r->cluster = 1;
-    r->threads = 256;
+    r->threads = kServeThreads;
     s->used += sl->rq.bytes;
     s->active.push_back(sl);
     std::lock_guard<std::mutex> lock(s->mu);
