@@ -183,3 +183,18 @@ def test_set_colouring_rejects(isg):
     g = I.random_graph(50, 80, 2)
     info = isg.isg_problem_info(p, colors=True)
     assert np.array_equal(info["colors"], oracle.csr_of(g).greedy_colouring()[0])
+
+
+def test_server_argument_checks(isg):
+    """isg_server_create validates before any device work; NULL handles are EINVAL."""
+    for budget, slots, chunk in ((0, 4, 10), (1 << 30, 0, 10), (1 << 30, 4, 0)):
+        with pytest.raises(isg.IsgError) as e:
+            isg.Server(budget, slots, chunk)
+        assert e.value.status == isg.ISG_EINVAL
+    t = isg.problem_of(I.torus(8, 8, 1))
+    with pytest.raises(isg.IsgError) as e:
+        isg.isg_server_submit(None, t, 32, [0.5], 1)
+    assert e.value.status == isg.ISG_EINVAL
+    with pytest.raises(isg.IsgError) as e:
+        isg.isg_server_poll(None, 0.0)
+    assert e.value.status == isg.ISG_EINVAL

@@ -355,6 +355,38 @@ def test_server_smallest_last_instance(isg):
     assert_same(out[1], oracle.anneal(c, 32, betas, 9, colour=col))
 
 
+def test_server_rejects_bad_requests_and_times_out(isg):
+    """Submit-time checks (EINVAL, and EBUSY for a request larger than the whole
+    budget), poll timing out with nothing pending, and a request served after
+    rejected ones equal to its solo run."""
+    srv = isg.Server(1 << 20, 2, 10)                          # 1 MiB budget
+    t = isg.problem_of(I.torus(8, 8, 1))
+    for R, betas in ((0, [0.5]), (32, []), (32, [np.nan]), (32, [-1.0])):
+        with pytest.raises(isg.IsgError) as e:
+            srv.submit(t, R, betas, 1)
+        assert e.value.status == isg.ISG_EINVAL
+    with pytest.raises(isg.IsgError) as e:
+        srv.submit(t, 32, [0.5], 1, target=2 ** 40)           # outside int32
+    assert e.value.status == isg.ISG_EINVAL
+    big = isg.problem_of(I.torus(100, 200, 1))
+    with pytest.raises(isg.IsgError) as e:
+        srv.submit(big, 1024, np.full(1000, 0.5), 1)
+    assert e.value.status == isg.ISG_EBUSY
+    assert srv.poll(0.05) is None
+    betas = I.geometric_betas(0.2, 3.0, 20)
+    rid = srv.submit(t, 32, betas, 3)
+    out = srv.poll(30.0)
+    assert out is not None and out[0] == rid
+    assert srv.poll(0.01) is None
+    st = srv.stats()
+    assert st["submitted"] == st["completed"] == 1
+    srv.close()
+    solo = isg.isg_anneal(t, 32, betas, 3)
+    for x, y in zip(out[1].final(), solo.final()):
+        assert np.array_equal(x, y)
+    assert np.array_equal(out[1].best_all(), solo.best_all())
+
+
 # ------------------------------------------------------------------ full sizes
 @pytest.mark.slow
 def test_torus_80x100_full_size_sampled(isg):
