@@ -188,6 +188,20 @@ isg_status isg_anneal_ex(const isg_problem *p, int32_t replicas, const double *b
                          int32_t sweeps, uint64_t seed, int64_t target_energy,
                          const isg_options *opts, void *cuda_stream, isg_result **out);
 
+/* Resume a finished solve (checkpoint/resume in one process): run `sweeps`
+ * more sweeps at betas[0..sweeps-1] from the state the solve ended with, as
+ * sweeps S .. S + sweeps - 1 of one schedule (S = the sweeps run so far).  The
+ * random numbers are keyed by sweep index, so the result then equals, bit for
+ * bit, isg_anneal of the concatenated schedule with the same seed: final and
+ * best states, energies and sweeps done.  Same kernel and launch shape as the
+ * solve.  result must come from isg_anneal / isg_anneal_ex on problem p
+ * without a target energy (p still alive); it can be continued again.
+ * Enqueued on cuda_stream after the earlier sweeps have finished (this call
+ * waits for them).  EINVAL for NULL, another problem, a result with a target
+ * or of the batched, served or tempering forms, sweeps < 1 or a bad beta. */
+isg_status isg_anneal_continue(const isg_problem *p, isg_result *result, const double *betas,
+                               int32_t sweeps, void *cuda_stream);
+
 /* Anneal count instances with one persistent kernel (work list ordered
  * longest-first) captured in a CUDA graph.  All share replicas, betas and
  * sweeps; seeds[k] and targets[k] (targets may be NULL = none) are per

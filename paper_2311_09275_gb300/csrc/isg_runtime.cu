@@ -461,6 +461,7 @@ void result_free(isg_result *r) {
   cudaSetDevice(r->device);
   if (r->done) cudaEventSynchronize(r->done);
   if (r->base) cudaFreeAsync(r->base, r->stream);
+  if (r->d_table_ext) cudaFreeAsync(r->d_table_ext, r->stream);
   if (r->pt_mem) cudaFreeAsync(r->pt_mem, r->stream);
   if (r->pt_exec) cudaGraphExecDestroy(r->pt_exec);
   if (r->pt_graph) cudaGraphDestroy(r->pt_graph);
@@ -698,7 +699,8 @@ GraphMscSolve make_gm_solve(const isg_problem *p, const DeviceProblem *dp, const
 // adjacency in shared memory whenever it fits.
 cudaError_t launch_sweeps(const isg_problem *p, const DeviceProblem *dp, isg_result *r,
                           uint64_t seed, bool has_target, int64_t target, bool plain, int cluster,
-                          int threads, int qpc, int S, cudaStream_t stream, int &launches) {
+                          int threads, int qpc, int S, cudaStream_t stream, int &launches,
+                          int t_start = 0) {
   cudaError_t err = cudaSuccess;
   const bool gm = r->msc && r->relabelled;
   int own_n = 0, own_nnz = 0, planes = 0;
@@ -712,9 +714,9 @@ cudaError_t launch_sweeps(const isg_problem *p, const DeviceProblem *dp, isg_res
   r->staged = own_n > 0;
   const int passes = (has_target && r->units > 1) ? 2 : 1;
   for (int pass = 0; pass < passes && err == cudaSuccess; ++pass) {
-    const int first = plain ? 0 : -1;
+    const int first = plain ? t_start : -1;
     for (int t = first; t < (plain ? S : 0) && err == cudaSuccess; ++t) {
-      const int t0 = plain ? t : 0, t1 = plain ? t + 1 : S;
+      const int t0 = plain ? t : t_start, t1 = plain ? t + 1 : S;
       if (gm) {
         GraphMscSolve s = make_gm_solve(p, dp, r, seed, has_target && pass == 0, target);
         GraphMscLaunch l = {};
@@ -755,6 +757,25 @@ cudaError_t launch_sweeps(const isg_problem *p, const DeviceProblem *dp, isg_res
       ++launches;
       if (!plain) break;
     }
+  }
+  return err;
+}
+
+// Final and best states into int8 [R][n] in the caller's vertex order.
+cudaError_t unpack_result(const isg_problem *p, const DeviceProblem *dp, const isg_result *r,
+                          cudaStream_t stream) {
+  cudaError_t err;
+  if (r->msc && !r->relabelled) {
+    err = unpack_msc(r->d_spins, p->n, r->R, r->d_out, stream);
+    if (err == cudaSuccess) err = unpack_msc(r->d_best, p->n, r->R, r->d_out_best, stream);
+  } else if (r->msc) {
+    err = unpack_msc_relabel(r->d_spins, p->n, r->R, dp->orig, r->d_out, stream);
+    if (err == cudaSuccess)
+      err = unpack_msc_relabel(r->d_best, p->n, r->R, dp->orig, r->d_out_best, stream);
+  } else {
+    err = unpack_quads(r->d_spins, p->n, r->R, dp->orig, r->d_out, stream);
+    if (err == cudaSuccess)
+      err = unpack_quads(r->d_best, p->n, r->R, dp->orig, r->d_out_best, stream);
   }
   return err;
 }
@@ -925,17 +946,7 @@ isg_status anneal_impl(const isg_problem *p, int32_t R, const double *betas, int
     ++launches;
   }
   if (err == cudaSuccess) {
-    if (tmsc) {
-      err = unpack_msc(r->d_spins, p->n, R, r->d_out, stream);
-      if (err == cudaSuccess) err = unpack_msc(r->d_best, p->n, R, r->d_out_best, stream);
-    } else if (gm) {
-      err = unpack_msc_relabel(r->d_spins, p->n, R, dp->orig, r->d_out, stream);
-      if (err == cudaSuccess)
-        err = unpack_msc_relabel(r->d_best, p->n, R, dp->orig, r->d_out_best, stream);
-    } else {
-      err = unpack_quads(r->d_spins, p->n, R, dp->orig, r->d_out, stream);
-      if (err == cudaSuccess) err = unpack_quads(r->d_best, p->n, R, dp->orig, r->d_out_best, stream);
-    }
+    err = unpack_result(p, dp, r, stream);
     launches += 2;
   }
   if (err == cudaSuccess) err = cudaEventRecord(r->done, stream);
@@ -946,7 +957,87 @@ isg_status anneal_impl(const isg_problem *p, int32_t R, const double *betas, int
   }
   r->launches = launches;
   r->sweep_launches = sweep_launches;
+  if (!has_target) {
+    r->prob = p;
+    r->seed = seed;
+    r->betas.assign(betas, betas + S);
+    r->plain = plain;
+    r->qpc = qpc;
+  }
   *out = r;
+  return ISG_OK;
+}
+
+// Continue a solve for more sweeps: sweeps S .. S + extra - 1 of one longer
+// schedule, started from the state the solve ended with.  The threshold table
+// is rebuilt for the whole schedule (the kernels index it by sweep), and the
+// kernels resume from the device state as between the launches of a plain
+// solve, so the result equals one solve of the concatenated schedule.
+isg_status continue_impl(const isg_problem *p, isg_result *r, const double *betas,
+                         int32_t extra, cudaStream_t stream) {
+  if (!p || !r) return fail(ISG_EINVAL, "problem and result must not be NULL");
+  if (r->prob != p)
+    return fail(ISG_EINVAL, "the result is not an isg_anneal solve of this problem without a "
+                            "target energy");
+  if (extra < 1) return fail(ISG_EINVAL, "sweeps must be >= 1 (got %d)", extra);
+  isg_status st = check_betas(betas, extra);
+  if (st != ISG_OK) return st;
+  if ((int64_t)r->S + extra > INT32_MAX) return fail(ISG_EINVAL, "schedule longer than 2^31 - 1");
+  st = result_sync(r);  // the earlier sweeps have finished
+  if (st != ISG_OK) return st;
+  const bool tmsc = r->msc && !r->relabelled;
+  const DeviceProblem *dp = nullptr;
+  size_t uploaded = 0;
+  st = problem_device(p, tmsc ? kNeedTorus : kNeedCsr, &dp, &uploaded);
+  if (st != ISG_OK) return st;
+  std::vector<double> all(r->betas);
+  all.insert(all.end(), betas, betas + extra);
+  std::vector<int32_t> levels;
+  table_levels(p, tmsc, levels);
+  std::vector<uint32_t> table;
+  build_table(all.data(), (int32_t)all.size(), levels, table);
+  uint32_t *d_table = nullptr;
+  cudaError_t err = cudaMallocAsync(&d_table, 4 * table.size(), stream);
+  if (err != cudaSuccess)
+    return fail(ISG_ENOMEM, "device allocation of %zu bytes failed: %s", 4 * table.size(),
+                cudaGetErrorString(err));
+  err = cudaMemcpyAsync(d_table, table.data(), 4 * table.size(), cudaMemcpyHostToDevice, stream);
+  if (err != cudaSuccess) {
+    cudaFreeAsync(d_table, stream);
+    return cuda_fail(err, "uploading the threshold table");
+  }
+  if (r->d_table_ext) cudaFreeAsync(r->d_table_ext, stream);
+  r->d_table_ext = d_table;
+  r->d_table = d_table;
+  r->table_words = table.size();
+  r->h2d_bytes += (int64_t)uploaded + 4 * (int64_t)table.size();
+  const int32_t s_old = r->S;
+  r->S = (int32_t)all.size();
+  r->betas.swap(all);
+  r->stream = stream;
+  int launches = 0;
+  if (r->timed) err = cudaEventRecord(r->t0, stream);
+  if (err == cudaSuccess)
+    err = launch_sweeps(p, dp, r, r->seed, false, 0, r->plain, r->cluster, r->threads, r->qpc,
+                        r->S, stream, launches, s_old);
+  const int sweep_launches = launches;
+  if (r->timed && err == cudaSuccess) err = cudaEventRecord(r->t1, stream);
+  if (err == cudaSuccess) {
+    err = unpack_result(p, dp, r, stream);
+    launches += 2;
+  }
+  if (err == cudaSuccess) err = cudaEventRecord(r->done, stream);
+  {
+    std::lock_guard<std::mutex> lock(r->mu);
+    r->synced = false;
+  }
+  if (err != cudaSuccess) {
+    cudaStreamSynchronize(stream);
+    r->prob = nullptr;  // the state is no longer a valid solve
+    return cuda_fail(err, "launching the continued sweeps");
+  }
+  r->launches += launches;
+  r->sweep_launches += sweep_launches;
   return ISG_OK;
 }
 
@@ -1472,6 +1563,11 @@ isg_status isg_anneal_ex(const isg_problem *p, int32_t replicas, const double *b
                          const isg_options *opts, void *cuda_stream, isg_result **out) {
   return anneal_impl(p, replicas, betas, sweeps, seed, target_energy, opts,
                      (cudaStream_t)cuda_stream, out);
+}
+
+isg_status isg_anneal_continue(const isg_problem *p, isg_result *result, const double *betas,
+                               int32_t sweeps, void *cuda_stream) {
+  return continue_impl(p, result, betas, sweeps, (cudaStream_t)cuda_stream);
 }
 
 isg_status isg_energy(const isg_problem *p, const int8_t *spins, int32_t replicas,

@@ -99,6 +99,14 @@ struct isg_result {
   std::vector<int32_t> h_e_cur, h_e_best, h_done;
   int32_t hit_sweep = -1, sweeps_done = 0;
   float kernel_ms = -1.0f;
+  // a single isg_anneal solve without a target, kept for isg_anneal_continue:
+  // its instance, seed, schedule so far and launch shape (prob is null otherwise)
+  const isg_problem *prob = nullptr;
+  uint64_t seed = 0;
+  std::vector<double> betas;
+  bool plain = false;
+  int32_t qpc = 1;
+  uint32_t *d_table_ext = nullptr;         // threshold table of a continued schedule
 };
 
 namespace isg {

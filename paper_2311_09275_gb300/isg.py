@@ -66,6 +66,7 @@ _sig("isg_anneal", [_P, _i32, _P, _i32, _u64, _i64, _P, ctypes.POINTER(_P)])
 _sig("isg_anneal_ex", [_P, _i32, _P, _i32, _u64, _i64, ctypes.POINTER(isg_options), _P,
                        ctypes.POINTER(_P)])
 _sig("isg_anneal_batch", [_P, _i32, _i32, _P, _i32, _P, _P, _P, _P])
+_sig("isg_anneal_continue", [_P, _P, _P, _i32, _P])
 _sig("isg_autotune", [_P, _i32, _i32, _P, ctypes.POINTER(isg_options)])
 _sig("isg_energy", [_P, _P, _i32, _P])
 _sig("isg_energy_noalloc", [_i32, _P, _P, _P, _P, _i32, _P, _P])
@@ -282,6 +283,15 @@ def isg_anneal(p, replicas: int, betas, seed: int, target=None, stream=None, ker
                               ISG_NO_TARGET if target is None else int(target),
                               ctypes.byref(opts), _stream(stream), ctypes.byref(out)))
     return Result(out.value)
+
+
+def isg_anneal_continue(p, res, betas, stream=None) -> None:
+    """Run len(betas) more sweeps of the solve `res` (of problem p, no target):
+    afterwards `res` equals one solve of the concatenated schedule."""
+    b = _arr(betas, np.float64)
+    _check(_lib.isg_anneal_continue(_h(p), _h(res), _ptr(b), int(b.shape[0]), _stream(stream)))
+    if isinstance(res, Result):
+        res.sweeps += int(b.shape[0])
 
 
 def isg_autotune(p, replicas: int, probe_sweeps: int = 64, stream=None) -> dict:

@@ -198,3 +198,9 @@ def test_server_argument_checks(isg):
     with pytest.raises(isg.IsgError) as e:
         isg.isg_server_poll(None, 0.0)
     assert e.value.status == isg.ISG_EINVAL
+
+
+def test_continue_rejects_null(isg):
+    with pytest.raises(isg.IsgError) as e:
+        isg.isg_anneal_continue(None, None, [0.5])
+    assert e.value.status == isg.ISG_EINVAL

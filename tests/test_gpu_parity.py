@@ -299,6 +299,49 @@ def test_batch_with_targets(isg):
         assert_same(outs[k], orc)
 
 
+# ------------------------------------------------------------------ resume
+@pytest.mark.parametrize("make,kernel,R,cluster", [
+    (lambda: I.torus(12, 10, 5), 1, 70, 2),                       # torus words
+    (lambda: I.torus(8, 6, 5), 3, 40, 0),                         # one launch per sweep
+    (lambda: I.random_graph(600, 900, 5), 4, 64, 3),              # graph words
+    (lambda: I.random_graph(500, 700, 6, weight=3), 2, 37, 2),    # int8 quads, weight 3
+])
+def test_continue_equals_one_solve(isg, make, kernel, R, cluster):
+    """25 sweeps, then 35, then 30 more through isg_anneal_continue equal one
+    90-sweep solve of the same schedule, and the oracle's."""
+    prob = make()
+    p = isg.problem_of(prob)
+    betas = I.geometric_betas(0.1, 4.0, 90)
+    whole = isg.isg_anneal(p, R, betas, 17, kernel=kernel, cluster_ctas=cluster)
+    part = isg.isg_anneal(p, R, betas[:25], 17, kernel=kernel, cluster_ctas=cluster)
+    assert part.final(spins=False)[2] == 25
+    isg.isg_anneal_continue(p, part, betas[25:60])
+    isg.isg_anneal_continue(p, part, betas[60:])
+    assert part.sweeps == whole.sweeps == 90
+    for x, y in zip(part.final(), whole.final()):
+        assert np.array_equal(x, y)
+    assert np.array_equal(part.best_all(), whole.best_all())
+    assert np.array_equal(part.best(spins=False)[3], whole.best(spins=False)[3])
+    assert_same(part, oracle.anneal(oracle.csr_of(prob), R, betas, 17))
+
+
+def test_continue_rejects(isg):
+    t = isg.problem_of(I.torus(8, 8, 2))
+    other = isg.problem_of(I.torus(8, 8, 3))
+    betas = I.geometric_betas(0.2, 2.0, 20)
+    with_target = isg.isg_anneal(t, 32, betas, 1, target=-10 ** 6)
+    res = isg.isg_anneal(t, 32, betas, 1)
+    batch = isg.isg_anneal_batch([t], 32, betas, [1])[0]
+    for p, r, b in ((t, with_target, betas), (other, res, betas), (t, batch, betas),
+                    (t, res, []), (t, res, [np.inf])):
+        with pytest.raises(isg.IsgError) as e:
+            isg.isg_anneal_continue(p, r, b)
+        assert e.value.status == isg.ISG_EINVAL
+    isg.isg_anneal_continue(t, res, betas)                 # still usable after rejections
+    whole = isg.isg_anneal(t, 32, np.concatenate([betas, betas]), 1)
+    assert np.array_equal(res.best_all(), whole.best_all())
+
+
 # ------------------------------------------------------------------ served
 def test_server_results_equal_solo_runs(isg):
     """Requests of different kinds and sizes, submitted together so that they
