@@ -202,6 +202,21 @@ isg_status isg_anneal_ex(const isg_problem *p, int32_t replicas, const double *b
 isg_status isg_anneal_continue(const isg_problem *p, isg_result *result, const double *betas,
                                int32_t sweeps, void *cuda_stream);
 
+/* Restart a solve from a checkpoint (across processes): the states a solve of
+ * the same problem, replicas, seed and schedule held after sweeps_done sweeps,
+ * as read with isg_result_final (spins) and isg_result_best_all (best_spins):
+ * int8 [replicas][n], +1/-1, the caller's vertex order, caller-owned host
+ * memory.  Runs sweeps sweeps_done .. sweeps - 1 of betas[0..sweeps-1] and
+ * returns a result equal, bit for bit, to isg_anneal of the whole schedule
+ * (energies are recomputed from the states; the solve's kernel and shape
+ * follow opts as in isg_anneal_ex, and may differ from the first run's).  No
+ * target energy.  EINVAL for NULL, 1 > sweeps_done or sweeps_done > sweeps, a
+ * spin that is not +1/-1, and what isg_anneal_ex rejects. */
+isg_status isg_anneal_resume(const isg_problem *p, int32_t replicas, const double *betas,
+                             int32_t sweeps, uint64_t seed, int32_t sweeps_done,
+                             const int8_t *spins, const int8_t *best_spins,
+                             const isg_options *opts, void *cuda_stream, isg_result **out);
+
 /* Anneal count instances with one persistent kernel (work list ordered
  * longest-first) captured in a CUDA graph.  All share replicas, betas and
  * sweeps; seeds[k] and targets[k] (targets may be NULL = none) are per

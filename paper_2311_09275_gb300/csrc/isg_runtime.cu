@@ -820,14 +820,78 @@ bool served_graph_msc(const isg_problem *p, int threads) {
 
 // ------------------------------------------------------------------ anneal
 
+// Solve state of a checkpoint: int8 [R][n] final and best spins (+1/-1, the
+// caller's vertex order) after the first t_done sweeps of the schedule.
+struct ResumeState {
+  const int8_t *spins = nullptr, *best = nullptr;
+  int32_t t_done = 0;
+};
+
+// Pack a checkpoint into the result's device layout (the inverse of the
+// unpack kernels: 32-lane words or int8 quads, relabelled vertex order for the
+// colour-class kernels; padding lanes hold +1), with the energies of both
+// states and t_done as every unit's sweeps done.
+isg_status upload_resume(const isg_problem *p, isg_result *r, const ResumeState &rs,
+                         cudaStream_t stream) {
+  const size_t n = (size_t)p->n, R = (size_t)r->R, units = (size_t)r->units;
+  const size_t lanes = units * r->lanes;
+  for (const int8_t *a : {rs.spins, rs.best})
+    for (size_t x = 0; x < R * n; ++x)
+      if (a[x] != 1 && a[x] != -1) return fail(ISG_EINVAL, "spin %zu is not +1 or -1", x);
+  std::vector<int64_t> e64(R);
+  std::vector<int32_t> e_cur(lanes, 0), e_best(lanes, 0), done(units, rs.t_done);
+  isg_status st = isg_energy(p, rs.spins, (int32_t)R, e64.data());
+  if (st != ISG_OK) return st;
+  for (size_t q = 0; q < R; ++q) e_cur[q] = (int32_t)e64[q];
+  st = isg_energy(p, rs.best, (int32_t)R, e64.data());
+  if (st != ISG_OK) return st;
+  for (size_t q = 0; q < R; ++q) e_best[q] = (int32_t)e64[q];
+  auto pack = [&](const int8_t *a, std::vector<uint32_t> &w) {
+    w.assign(units * n, r->msc ? 0xFFFFFFFFu : 0x01010101u);
+    for (size_t q = 0; q < R; ++q)
+      for (size_t v = 0; v < n; ++v) {
+        const size_t i = r->relabelled ? (size_t)p->order[v] : v;
+        uint32_t &x = w[(q / r->lanes) * n + v];
+        if (r->msc) {
+          const uint32_t bit = 1u << (q & 31);
+          x = a[q * n + i] > 0 ? (x | bit) : (x & ~bit);
+        } else {
+          const int sh = 8 * (int)(q & 3);
+          x = (x & ~(0xFFu << sh)) | ((uint32_t)(uint8_t)a[q * n + i] << sh);
+        }
+      }
+  };
+  std::vector<uint32_t> ws, wb;
+  pack(rs.spins, ws);
+  pack(rs.best, wb);
+  cudaError_t err = cudaMemcpyAsync(r->d_spins, ws.data(), 4 * ws.size(), cudaMemcpyHostToDevice,
+                                    stream);
+  if (err == cudaSuccess)
+    err = cudaMemcpyAsync(r->d_best, wb.data(), 4 * wb.size(), cudaMemcpyHostToDevice, stream);
+  if (err == cudaSuccess)
+    err = cudaMemcpyAsync(r->d_e_cur, e_cur.data(), 4 * lanes, cudaMemcpyHostToDevice, stream);
+  if (err == cudaSuccess)
+    err = cudaMemcpyAsync(r->d_e_best, e_best.data(), 4 * lanes, cudaMemcpyHostToDevice, stream);
+  if (err == cudaSuccess)
+    err = cudaMemcpyAsync(r->d_done, done.data(), 4 * units, cudaMemcpyHostToDevice, stream);
+  if (err == cudaSuccess) err = cudaStreamSynchronize(stream);  // the host vectors go away
+  if (err != cudaSuccess) return cuda_fail(err, "uploading the checkpoint");
+  r->h2d_bytes += 4 * (int64_t)(ws.size() + wb.size() + 2 * lanes + units);
+  return ISG_OK;
+}
+
 isg_status anneal_impl(const isg_problem *p, int32_t R, const double *betas, int32_t S,
                        uint64_t seed, int64_t target, const isg_options *opts, cudaStream_t stream,
-                       isg_result **out) {
+                       isg_result **out, const ResumeState *rs = nullptr) {
   if (!p || !out) return fail(ISG_EINVAL, "problem and out must not be NULL");
   if (R < 1) return fail(ISG_EINVAL, "replicas must be >= 1 (got %d)", R);
   if (S < 1) return fail(ISG_EINVAL, "sweeps must be >= 1 (got %d)", S);
   isg_status st = check_betas(betas, S);
   if (st != ISG_OK) return st;
+  if (rs && (!rs->spins || !rs->best))
+    return fail(ISG_EINVAL, "checkpoint spins must not be NULL");
+  if (rs && (rs->t_done < 1 || rs->t_done > S))
+    return fail(ISG_EINVAL, "sweeps_done must be in [1, sweeps] (got %d)", rs->t_done);
   isg_options o = {};
   if (opts) o = *opts;
   int kernel = o.kernel;
@@ -930,6 +994,13 @@ isg_status anneal_impl(const isg_problem *p, int32_t R, const double *betas, int
     result_free(r);
     return cuda_fail(err, "preparing the solve");
   }
+  if (rs) {
+    st = upload_resume(p, r, *rs, stream);
+    if (st != ISG_OK) {
+      result_free(r);
+      return st;
+    }
+  }
   r->ctas = (msc ? r->units : (r->units + qpc - 1) / qpc) * cluster;
   r->cluster = cluster;
   r->threads = threads;
@@ -938,7 +1009,7 @@ isg_status anneal_impl(const isg_problem *p, int32_t R, const double *betas, int
   if (r->timed) err = cudaEventRecord(r->t0, stream);
   if (err == cudaSuccess)
     err = launch_sweeps(p, dp, r, seed, has_target, target, plain, cluster, threads, qpc, S, stream,
-                        launches);
+                        launches, rs ? rs->t_done : 0);
   const int sweep_launches = launches;
   if (r->timed && err == cudaSuccess) err = cudaEventRecord(r->t1, stream);
   if (err == cudaSuccess) {
@@ -1563,6 +1634,18 @@ isg_status isg_anneal_ex(const isg_problem *p, int32_t replicas, const double *b
                          const isg_options *opts, void *cuda_stream, isg_result **out) {
   return anneal_impl(p, replicas, betas, sweeps, seed, target_energy, opts,
                      (cudaStream_t)cuda_stream, out);
+}
+
+isg_status isg_anneal_resume(const isg_problem *p, int32_t replicas, const double *betas,
+                             int32_t sweeps, uint64_t seed, int32_t sweeps_done,
+                             const int8_t *spins, const int8_t *best_spins,
+                             const isg_options *opts, void *cuda_stream, isg_result **out) {
+  ResumeState rs;
+  rs.spins = spins;
+  rs.best = best_spins;
+  rs.t_done = sweeps_done;
+  return anneal_impl(p, replicas, betas, sweeps, seed, ISG_NO_TARGET, opts,
+                     (cudaStream_t)cuda_stream, out, &rs);
 }
 
 isg_status isg_anneal_continue(const isg_problem *p, isg_result *result, const double *betas,

@@ -67,6 +67,8 @@ _sig("isg_anneal_ex", [_P, _i32, _P, _i32, _u64, _i64, ctypes.POINTER(isg_option
                        ctypes.POINTER(_P)])
 _sig("isg_anneal_batch", [_P, _i32, _i32, _P, _i32, _P, _P, _P, _P])
 _sig("isg_anneal_continue", [_P, _P, _P, _i32, _P])
+_sig("isg_anneal_resume", [_P, _i32, _P, _i32, _u64, _i32, _P, _P, ctypes.POINTER(isg_options),
+                           _P, ctypes.POINTER(_P)])
 _sig("isg_autotune", [_P, _i32, _i32, _P, ctypes.POINTER(isg_options)])
 _sig("isg_energy", [_P, _P, _i32, _P])
 _sig("isg_energy_noalloc", [_i32, _P, _P, _P, _P, _i32, _P, _P])
@@ -292,6 +294,29 @@ def isg_anneal_continue(p, res, betas, stream=None) -> None:
     _check(_lib.isg_anneal_continue(_h(p), _h(res), _ptr(b), int(b.shape[0]), _stream(stream)))
     if isinstance(res, Result):
         res.sweeps += int(b.shape[0])
+
+
+def isg_anneal_resume(p, replicas: int, betas, seed: int, sweeps_done: int, spins, best_spins,
+                      stream=None, kernel: int = 0, cluster_ctas: int = 0, threads: int = 0,
+                      quads_per_cta: int = 0) -> Result:
+    """A solve restarted from a checkpoint (final and best int8 states after
+    `sweeps_done` sweeps); equal to one solve of the whole schedule."""
+    b = _arr(betas, np.float64)
+    s = _arr(spins, np.int8)
+    bs = _arr(best_spins, np.int8)
+    if s.size != int(replicas) * _lib_n(p) or bs.size != s.size:
+        raise ValueError("spins and best_spins must hold replicas x n values")
+    opts = isg_options(kernel, cluster_ctas, threads, 0, quads_per_cta)
+    out = _P()
+    _check(_lib.isg_anneal_resume(_h(p), int(replicas), _ptr(b), int(b.shape[0]),
+                                  int(seed) & 0xFFFFFFFFFFFFFFFF, int(sweeps_done), _ptr(s),
+                                  _ptr(bs), ctypes.byref(opts), _stream(stream),
+                                  ctypes.byref(out)))
+    return Result(out.value)
+
+
+def _lib_n(p) -> int:
+    return isg_problem_info(p)["n"]
 
 
 def isg_autotune(p, replicas: int, probe_sweeps: int = 64, stream=None) -> dict:

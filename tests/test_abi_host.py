@@ -204,3 +204,9 @@ def test_continue_rejects_null(isg):
     with pytest.raises(isg.IsgError) as e:
         isg.isg_anneal_continue(None, None, [0.5])
     assert e.value.status == isg.ISG_EINVAL
+
+
+def test_resume_rejects_null(isg):
+    with pytest.raises(isg.IsgError) as e:
+        isg.isg_anneal_resume(None, 4, [0.5, 0.5], 1, 1, np.ones(8, np.int8), np.ones(8, np.int8))
+    assert e.value.status == isg.ISG_EINVAL

@@ -325,6 +325,49 @@ def test_continue_equals_one_solve(isg, make, kernel, R, cluster):
     assert_same(part, oracle.anneal(oracle.csr_of(prob), R, betas, 17))
 
 
+@pytest.mark.parametrize("make,kernel,R,cluster", [
+    (lambda: I.torus(12, 10, 5), 1, 70, 2),
+    (lambda: I.torus(8, 6, 5), 3, 40, 0),
+    (lambda: I.random_graph(600, 900, 5), 4, 64, 3),
+    (lambda: I.random_graph(500, 700, 6, weight=3), 2, 37, 2),
+    (lambda: I.independent_set_instance(I.geometric_graph(300, 5.0, 2)), 2, 21, 1),  # fields
+])
+def test_resume_from_checkpoint_equals_one_solve(isg, make, kernel, R, cluster):
+    """Export the final and best states after 40 sweeps, restart from them in a
+    new solve (also on another cluster shape) and run to 90: equal to one
+    90-sweep solve."""
+    prob = make()
+    p = isg.problem_of(prob)
+    betas = I.geometric_betas(0.1, 4.0, 90)
+    whole = isg.isg_anneal(p, R, betas, 23, kernel=kernel, cluster_ctas=cluster)
+    first = isg.isg_anneal(p, R, betas[:40], 23, kernel=kernel, cluster_ctas=cluster)
+    spins, best = first.final()[0], first.best_all()
+    first.close()
+    for shape in (cluster, 1):
+        res = isg.isg_anneal_resume(p, R, betas, 23, 40, spins, best, kernel=kernel,
+                                    cluster_ctas=shape)
+        for x, y in zip(res.final(), whole.final()):
+            assert np.array_equal(x, y), shape
+        assert np.array_equal(res.best_all(), whole.best_all()), shape
+        assert np.array_equal(res.best(spins=False)[3], whole.best(spins=False)[3]), shape
+    assert_same(res, oracle.anneal(oracle.csr_of(prob), R, betas, 23))
+
+
+def test_resume_rejects(isg):
+    t = isg.problem_of(I.torus(8, 8, 2))
+    betas = I.geometric_betas(0.2, 2.0, 20)
+    ok = np.ones((32, 64), np.int8)
+    bad = ok.copy()
+    bad[3, 5] = 0
+    for done, s, b in ((0, ok, ok), (21, ok, ok), (5, bad, ok), (5, ok, bad)):
+        with pytest.raises(isg.IsgError) as e:
+            isg.isg_anneal_resume(t, 32, betas, 1, done, s, b)
+        assert e.value.status == isg.ISG_EINVAL
+    res = isg.isg_anneal_resume(t, 32, betas, 1, 20, ok, ok)     # nothing left to run
+    assert res.final(spins=False)[2] == 20
+    assert np.array_equal(res.best_all(), ok)
+
+
 def test_continue_rejects(isg):
     t = isg.problem_of(I.torus(8, 8, 2))
     other = isg.problem_of(I.torus(8, 8, 3))
