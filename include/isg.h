@@ -379,6 +379,14 @@ typedef struct {
     int64_t replays;      /* passes re-run to a multi-unit request's stop sweep */
 } isg_server_stats;
 
+/* Host-side fault injection for tests: the next `count` allocations of solve
+ * state (isg_anneal and its variants, served admissions) fail as if the
+ * device were out of memory, without any device work: the solve returns
+ * ISG_ENOMEM, and a served request is handed back with a result whose reads
+ * return ISG_ENOMEM while the server carries on.  count = 0 clears it.  Process
+ * wide.  EINVAL for count < 0. */
+isg_status isg_debug_fail_allocations(int32_t count);
+
 /* Counters of the server (a consistent snapshot).  EINVAL for NULL. */
 isg_status isg_server_get_stats(isg_server *s, isg_server_stats *out);
 

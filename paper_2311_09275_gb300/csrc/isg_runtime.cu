@@ -2,6 +2,7 @@
 // building and validation, colouring and colour-major relabelling,
 // acceptance tables, device residency, launch orchestration, results.
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -379,7 +380,17 @@ isg_status check_betas(const double *betas, int32_t sweeps) {
 
 // ------------------------------------------------------------------ results
 
+// Allocations of solve state still to fail (isg_debug_fail_allocations).
+std::atomic<int32_t> g_fail_allocations{0};
+
 isg_status result_alloc(isg_result *r, cudaStream_t stream) {
+  int32_t pending = g_fail_allocations.load();
+  while (pending > 0 && !g_fail_allocations.compare_exchange_weak(pending, pending - 1)) {
+  }
+  if (pending > 0) {
+    r->base = nullptr;
+    return fail(ISG_ENOMEM, "device allocation failed (injected by isg_debug_fail_allocations)");
+  }
   const size_t n = (size_t)r->n, R = (size_t)r->R, units = (size_t)r->units;
   const size_t lanes = units * r->lanes;
   auto al = [](size_t x) { return (x + 255) & ~size_t(255); };
@@ -1646,6 +1657,12 @@ isg_status isg_anneal_resume(const isg_problem *p, int32_t replicas, const doubl
   rs.t_done = sweeps_done;
   return anneal_impl(p, replicas, betas, sweeps, seed, ISG_NO_TARGET, opts,
                      (cudaStream_t)cuda_stream, out, &rs);
+}
+
+isg_status isg_debug_fail_allocations(int32_t count) {
+  if (count < 0) return fail(ISG_EINVAL, "count must be >= 0 (got %d)", count);
+  isg::g_fail_allocations.store(count);
+  return ISG_OK;
 }
 
 isg_status isg_anneal_continue(const isg_problem *p, isg_result *result, const double *betas,

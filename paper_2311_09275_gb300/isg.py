@@ -67,6 +67,7 @@ _sig("isg_anneal_ex", [_P, _i32, _P, _i32, _u64, _i64, ctypes.POINTER(isg_option
                        ctypes.POINTER(_P)])
 _sig("isg_anneal_batch", [_P, _i32, _i32, _P, _i32, _P, _P, _P, _P])
 _sig("isg_anneal_continue", [_P, _P, _P, _i32, _P])
+_sig("isg_debug_fail_allocations", [_i32])
 _sig("isg_anneal_resume", [_P, _i32, _P, _i32, _u64, _i32, _P, _P, ctypes.POINTER(isg_options),
                            _P, ctypes.POINTER(_P)])
 _sig("isg_autotune", [_P, _i32, _i32, _P, ctypes.POINTER(isg_options)])
@@ -317,6 +318,11 @@ def isg_anneal_resume(p, replicas: int, betas, seed: int, sweeps_done: int, spin
 
 def _lib_n(p) -> int:
     return isg_problem_info(p)["n"]
+
+
+def isg_debug_fail_allocations(count: int) -> None:
+    """Make the next `count` solve-state allocations fail with ISG_ENOMEM (tests)."""
+    _check(_lib.isg_debug_fail_allocations(int(count)))
 
 
 def isg_autotune(p, replicas: int, probe_sweeps: int = 64, stream=None) -> dict:

@@ -210,3 +210,11 @@ def test_resume_rejects_null(isg):
     with pytest.raises(isg.IsgError) as e:
         isg.isg_anneal_resume(None, 4, [0.5, 0.5], 1, 1, np.ones(8, np.int8), np.ones(8, np.int8))
     assert e.value.status == isg.ISG_EINVAL
+
+
+def test_debug_fail_allocations_arguments(isg):
+    with pytest.raises(isg.IsgError) as e:
+        isg.isg_debug_fail_allocations(-1)
+    assert e.value.status == isg.ISG_EINVAL
+    isg.isg_debug_fail_allocations(3)
+    isg.isg_debug_fail_allocations(0)

@@ -473,6 +473,42 @@ def test_server_rejects_bad_requests_and_times_out(isg):
     assert np.array_equal(out[1].best_all(), solo.best_all())
 
 
+def test_injected_allocation_failures(isg):
+    """Host-side fault injection, no device fault: a solve whose state allocation
+    fails returns ENOMEM and the library stays usable; a served request whose
+    admission fails comes back with ENOMEM while the requests after it finish,
+    each equal to its solo run."""
+    t = isg.problem_of(I.torus(12, 10, 4))
+    g = isg.problem_of(I.random_graph(400, 600, 4))
+    betas = I.geometric_betas(0.2, 3.0, 60)
+    try:
+        isg.isg_debug_fail_allocations(1)
+        with pytest.raises(isg.IsgError) as e:
+            isg.isg_anneal(t, 32, betas, 5)
+        assert e.value.status == isg.ISG_ENOMEM
+        solo_t = isg.isg_anneal(t, 32, betas, 5)          # the next allocation succeeds
+        solo_g = isg.isg_anneal(g, 32, betas, 6)
+        srv = isg.Server(1 << 30, 1, 20)                  # one slot: admitted in order
+        isg.isg_debug_fail_allocations(1)
+        ids = [srv.submit(t, 32, betas, 5), srv.submit(g, 32, betas, 6),
+               srv.submit(t, 32, betas, 5)]
+        got = {}
+        while len(got) < 3:
+            out = srv.poll(30.0)
+            assert out is not None, "server timed out"
+            got[ids.index(out[0])] = out[1]
+        srv.close()
+    finally:
+        isg.isg_debug_fail_allocations(0)
+    with pytest.raises(isg.IsgError) as e:
+        got[0].final()
+    assert e.value.status == isg.ISG_ENOMEM
+    for k, ref in ((1, solo_g), (2, solo_t)):
+        for x, y in zip(got[k].final(), ref.final()):
+            assert np.array_equal(x, y)
+        assert np.array_equal(got[k].best_all(), ref.best_all())
+
+
 # ------------------------------------------------------------------ full sizes
 @pytest.mark.slow
 def test_torus_80x100_full_size_sampled(isg):
