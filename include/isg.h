@@ -366,6 +366,13 @@ isg_status isg_server_submit(isg_server *s, const isg_problem *p, int32_t replic
 isg_status isg_server_poll(isg_server *s, uint64_t *request_id, isg_result **out,
                            double timeout_s);
 
+/* Cancel a queued or running request.  A queued one is handed back at once, a
+ * running one at the end of the chunk in progress (its state is dropped); in
+ * both cases isg_server_poll returns it with a result whose reads return
+ * ISG_ECANCELLED.  EINVAL for NULL or an id that is neither queued nor running
+ * (unknown, or already finished: its result is then the normal one). */
+isg_status isg_server_cancel(isg_server *s, uint64_t request_id);
+
 /* Stop the server; unfinished requests are dropped.  */
 isg_status isg_server_destroy(isg_server *s);
 
@@ -377,6 +384,7 @@ typedef struct {
     int32_t peak_active;  /* most requests resident at once so far */
     int64_t passes;       /* chunk passes run (one launch of the unit kernels each) */
     int64_t replays;      /* passes re-run to a multi-unit request's stop sweep */
+    int64_t cancelled;    /* requests handed back by isg_server_cancel */
 } isg_server_stats;
 
 /* Host-side fault injection for tests: the next `count` allocations of solve

@@ -25,6 +25,7 @@
 #include <condition_variable>
 #include <deque>
 #include <mutex>
+#include <set>
 #include <thread>
 #include <vector>
 
@@ -55,6 +56,7 @@ struct Slot {
   size_t state_bytes = 0;
   int32_t stop = -1;
   bool finished = false;
+  bool cancelled = false;  // retired by isg_server_cancel, without a result
 };
 
 constexpr int kServeThreads = 512;
@@ -116,7 +118,9 @@ struct isg_server {
   size_t cap_status = 0;
   isg_status worker_error = ISG_OK;
   // counters (under mu)
-  int64_t n_submitted = 0, n_completed = 0, n_passes = 0, n_replays = 0;
+  int64_t n_submitted = 0, n_completed = 0, n_passes = 0, n_replays = 0, n_cancelled = 0;
+  std::set<uint64_t> live;     // admitted requests not yet handed back
+  std::set<uint64_t> cancels;  // of those, the ones to retire at the next chunk boundary
   int32_t n_active = 0, peak_active = 0;
 };
 
@@ -184,6 +188,7 @@ void admit(isg_server *s) {
       if (!s->active.empty() && s->used + s->queue.front().bytes > s->budget) return;
       rq = std::move(s->queue.front());
       s->queue.pop_front();
+      s->live.insert(rq.id);  // cancellable from here on
     }
     Slot *sl = new Slot();
     sl->rq = std::move(rq);
@@ -232,6 +237,7 @@ void admit(isg_server *s) {
       r->sync_status = st;
       if (sl->snap) cudaFreeAsync(sl->snap, s->stream);
       std::lock_guard<std::mutex> lock(s->mu);
+      s->live.erase(sl->rq.id);
       s->done.emplace_back(sl->rq.id, r);
       ++s->n_completed;
       s->cv_done.notify_all();
@@ -574,6 +580,11 @@ void worker_main(isg_server *s) {
     // decide per request; collect the multi-unit requests that must re-run to t*
     std::vector<Slot *> redo;
     std::vector<int32_t> redo_end;
+    std::set<uint64_t> cancels;
+    {
+      std::lock_guard<std::mutex> lock(s->mu);
+      cancels.swap(s->cancels);
+    }
     off = 0;
     for (Slot *sl : s->active) {
       const int32_t u = sl->res->units;
@@ -581,7 +592,10 @@ void worker_main(isg_server *s) {
       for (int32_t q = 0; q < u; ++q)
         if (s->h_status[off + q] >= 0) tstar = std::min(tstar, s->h_status[off + q]);
       off += 2 * (size_t)u;
-      if (sl->res->has_target && tstar != INT_MAX) {
+      if (cancels.count(sl->rq.id)) {
+        sl->cancelled = true;
+        sl->finished = true;
+      } else if (sl->res->has_target && tstar != INT_MAX) {
         sl->stop = tstar;
         sl->finished = true;
         if (u > 1) {
@@ -611,7 +625,7 @@ void worker_main(isg_server *s) {
     std::vector<Slot *> fin;
     for (Slot *sl : s->active) (sl->finished ? fin : keep).push_back(sl);
     for (Slot *sl : fin)
-      if (err == cudaSuccess) err = finish_slot(s, sl);
+      if (err == cudaSuccess && !sl->cancelled) err = finish_slot(s, sl);
     if (err == cudaSuccess) err = cudaStreamSynchronize(s->stream);
     if (err != cudaSuccess) {
       s->worker_error = cuda_fail(err, "server retire");
@@ -623,10 +637,19 @@ void worker_main(isg_server *s) {
     for (Slot *sl : fin) {
       if (sl->snap) cudaFreeAsync(sl->snap, s->stream);
       s->used -= sl->rq.bytes;
+      if (sl->cancelled) {
+        // handed back without state: its reads return ISG_ECANCELLED
+        cudaFreeAsync(sl->res->base, s->stream);
+        sl->res->base = nullptr;
+        sl->res->synced = true;
+        sl->res->sync_status = ISG_ECANCELLED;
+      }
       sl->res->stream = nullptr;  // later frees go to the legacy stream
       std::lock_guard<std::mutex> lock(s->mu);
+      s->live.erase(sl->rq.id);
       s->done.emplace_back(sl->rq.id, sl->res);
       ++s->n_completed;
+      if (sl->cancelled) ++s->n_cancelled;
       delete sl;
     }
     s->active.swap(keep);
@@ -751,6 +774,34 @@ isg_status isg_server_get_stats(isg_server *s, isg_server_stats *out) {
   out->peak_active = s->peak_active;
   out->passes = s->n_passes;
   out->replays = s->n_replays;
+  out->cancelled = s->n_cancelled;
+  return ISG_OK;
+}
+
+isg_status isg_server_cancel(isg_server *s, uint64_t request_id) {
+  if (!s) return fail(ISG_EINVAL, "server must not be NULL");
+  std::lock_guard<std::mutex> lock(s->mu);
+  for (auto it = s->queue.begin(); it != s->queue.end(); ++it) {
+    if (it->id != request_id) continue;
+    // not admitted yet: handed back at once, with no device state
+    isg_result *r = new isg_result();
+    r->device = s->device;
+    r->n = it->p->n;
+    r->R = it->R;
+    r->S = it->S;
+    r->synced = true;
+    r->sync_status = ISG_ECANCELLED;
+    s->queue.erase(it);
+    s->done.emplace_back(request_id, r);
+    ++s->n_completed;
+    ++s->n_cancelled;
+    s->cv_done.notify_all();
+    return ISG_OK;
+  }
+  if (!s->live.count(request_id))
+    return fail(ISG_EINVAL, "request %llu is not queued or running (unknown or finished)",
+                (unsigned long long)request_id);
+  s->cancels.insert(request_id);
   return ISG_OK;
 }
 

@@ -45,7 +45,7 @@ class isg_stats(ctypes.Structure):
 
 class isg_server_stats(ctypes.Structure):
     _fields_ = [("submitted", _i64), ("completed", _i64), ("queued", _i32), ("active", _i32),
-                ("peak_active", _i32), ("passes", _i64), ("replays", _i64)]
+                ("peak_active", _i32), ("passes", _i64), ("replays", _i64), ("cancelled", _i64)]
 
 
 def _sig(name, args, res=ctypes.c_int):
@@ -84,6 +84,7 @@ _sig("isg_server_submit", [_P, _P, _i32, _P, _i32, _u64, _i64, ctypes.POINTER(_u
 _sig("isg_server_poll", [_P, ctypes.POINTER(_u64), ctypes.POINTER(_P), _dbl])
 _sig("isg_server_destroy", [_P])
 _sig("isg_server_get_stats", [_P, ctypes.POINTER(isg_server_stats)])
+_sig("isg_server_cancel", [_P, _u64])
 _sig("isg_integer_peaks", [_P, ctypes.POINTER(_dbl), ctypes.POINTER(_dbl)])
 _sig("isg_acceptance_table", [_P, _i32, _i32, _P])
 _sig("isg_philox_rates", [_P, ctypes.POINTER(_dbl), ctypes.POINTER(_dbl)])
@@ -484,6 +485,9 @@ class Server:
     def stats(self) -> dict:
         return isg_server_get_stats(self)
 
+    def cancel(self, request_id: int) -> None:
+        isg_server_cancel(self, request_id)
+
     def close(self):
         if self.handle:
             h, self.handle = self.handle, None
@@ -498,6 +502,10 @@ class Server:
 
 def isg_server_create(device_mem_budget: int, max_slots: int, sweeps_per_chunk: int) -> Server:
     return Server(device_mem_budget, max_slots, sweeps_per_chunk)
+
+
+def isg_server_cancel(s, request_id: int) -> None:
+    _check(_lib.isg_server_cancel(_h(s), int(request_id)))
 
 
 def isg_server_get_stats(s) -> dict:

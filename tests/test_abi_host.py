@@ -218,3 +218,9 @@ def test_debug_fail_allocations_arguments(isg):
     assert e.value.status == isg.ISG_EINVAL
     isg.isg_debug_fail_allocations(3)
     isg.isg_debug_fail_allocations(0)
+
+
+def test_server_cancel_rejects_null(isg):
+    with pytest.raises(isg.IsgError) as e:
+        isg.isg_server_cancel(None, 1)
+    assert e.value.status == isg.ISG_EINVAL

@@ -473,6 +473,46 @@ def test_server_rejects_bad_requests_and_times_out(isg):
     assert np.array_equal(out[1].best_all(), solo.best_all())
 
 
+def test_server_cancel(isg):
+    """A request cancelled while queued and one cancelled while running come
+    back with ECANCELLED; the request after them finishes equal to its solo run;
+    cancelling a finished or unknown id is EINVAL."""
+    import time
+    t = isg.problem_of(I.torus(40, 40, 7))
+    small = isg.problem_of(I.torus(8, 8, 7))
+    long_betas = I.geometric_betas(0.1, 3.0, 20000)
+    betas = I.geometric_betas(0.2, 3.0, 40)
+    srv = isg.Server(1 << 30, 1, 50)              # one slot: b and c wait behind a
+    a = srv.submit(t, 32, long_betas, 1)
+    b = srv.submit(small, 32, betas, 2)
+    c = srv.submit(small, 32, betas, 3)
+    srv.cancel(b)                                 # queued
+    t0 = time.time()
+    while srv.stats()["passes"] < 2 and time.time() - t0 < 30:
+        time.sleep(0.001)
+    srv.cancel(a)                                 # running
+    got = {}
+    while len(got) < 3:
+        out = srv.poll(60.0)
+        assert out is not None, "server timed out"
+        got[out[0]] = out[1]
+    for rid in (c, 10 ** 9):
+        with pytest.raises(isg.IsgError) as e:
+            srv.cancel(rid)
+        assert e.value.status == isg.ISG_EINVAL
+    st = srv.stats()
+    srv.close()
+    assert st["cancelled"] == 2 and st["completed"] == 3 and st["passes"] >= 2
+    for rid in (a, b):
+        with pytest.raises(isg.IsgError) as e:
+            got[rid].final()
+        assert e.value.status == isg.ISG_ECANCELLED
+    solo = isg.isg_anneal(small, 32, betas, 3)
+    for x, y in zip(got[c].final(), solo.final()):
+        assert np.array_equal(x, y)
+    assert np.array_equal(got[c].best_all(), solo.best_all())
+
+
 def test_injected_allocation_failures(isg):
     """Host-side fault injection, no device fault: a solve whose state allocation
     fails returns ENOMEM and the library stays usable; a served request whose
