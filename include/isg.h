@@ -31,7 +31,9 @@
  * replica's best state is checked at the end of every sweep (strictly lower
  * energy replaces it; the initial state is the first candidate).
  * Results are a pure function of (instance, replicas, betas, seed): they do
- * not depend on the kernel chosen, its blocking or the batch a solve is in.
+ * not depend on the kernel chosen, its blocking, the batch a solve is in, or
+ * whether the schedule ran in one call or was continued or restarted from a
+ * checkpoint (isg_anneal_continue, isg_anneal_resume).
  *
  * Conventions.
  *  - All input arrays are caller-owned HOST memory and are copied; the caller
