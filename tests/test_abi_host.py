@@ -224,3 +224,11 @@ def test_server_cancel_rejects_null(isg):
     with pytest.raises(isg.IsgError) as e:
         isg.isg_server_cancel(None, 1)
     assert e.value.status == isg.ISG_EINVAL
+
+
+def test_resume_checks_state_sizes(isg):
+    """The binding checks the checkpoint's size before any device work."""
+    p = isg.problem_of(I.torus(8, 8, 1))
+    with pytest.raises(ValueError):
+        isg.isg_anneal_resume(p, 32, [0.5, 0.5], 1, 1, np.ones((32, 63), np.int8),
+                              np.ones((32, 64), np.int8))
