@@ -104,6 +104,50 @@ def test_ferro_and_antiferro_ground_states():
     assert c.enumerate()[0] == -32 + 2
 
 
+def test_torus_orientation_hand_derived_energy():
+    """Sec. II.A torus geometry on a 4 x 6 torus (L != W): vertex i = r W + c,
+    j_right[i] couples i to (r, c+1 mod W) and j_down[i] to (r+1 mod L, c).
+    All couplings -1 except j_right[8] = +1 (bond 8-9) and j_down[16] = +1
+    (bond 16-22); spins +1 except s_9 = s_22 = -1.  By hand: the all-up energy
+    is 46 x (-1) + 2 x (+1) = -44; flipping s_9 negates its four bonds 8-9 (+1),
+    9-10, 3-9, 9-15 (-1 each): +4; flipping s_22 negates 21-22, 22-23, 22-4
+    (-1 each) and 16-22 (+1): +4; so E = -36.  With the two coupling arrays
+    swapped (or right read as left, or rows and columns transposed) neither
+    flipped spin touches a +1 bond and E = -28."""
+    L, W = 4, 6
+    jr = np.full(L * W, -1, np.int8)
+    jd = np.full(L * W, -1, np.int8)
+    jr[8] = 1
+    jd[16] = 1
+    s = np.ones(L * W, np.int8)
+    s[[9, 22]] = -1
+    assert oracle.torus_csr(L, W, jr, jd).energy(s) == -36
+    assert oracle.torus_csr(L, W, jd, jr).energy(s) == -28
+    # the same instance as an edge list written out by (r, c) here
+    u, v, w = [], [], []
+    for r in range(L):
+        for c in range(W):
+            i = r * W + c
+            u += [i, i]
+            v += [r * W + (c + 1) % W, ((r + 1) % L) * W + c]
+            w += [int(jr[i]), int(jd[i])]
+    ref = oracle.Csr(L * W, np.array(u, np.int32), np.array(v, np.int32), np.array(w, np.int32))
+    t = oracle.torus_csr(L, W, jr, jd)
+    assert np.array_equal(t.rowptr, ref.rowptr)
+    assert np.array_equal(t.col, ref.col) and np.array_equal(t.wt, ref.wt)
+
+
+@pytest.mark.parametrize("L,W,seed", [(4, 6, 1), (6, 4, 2), (8, 10, 3)])
+def test_torus_csr_equals_fixture_edge_list(L, W, seed):
+    """The oracle's own torus edge list and the input generator's edge list
+    (written separately, same geometry) give the same CSR for L != W."""
+    t = I.torus(L, W, seed)
+    a = oracle.torus_csr(L, W, t.j_right, t.j_down)
+    b = oracle.Csr(t.n, *t.edges())
+    assert np.array_equal(a.rowptr, b.rowptr)
+    assert np.array_equal(a.col, b.col) and np.array_equal(a.wt, b.wt)
+
+
 @pytest.mark.parametrize("n,seed", [(9, 1), (10, 2), (11, 3)])
 def test_ring_partition_function_closed_form(n, seed):
     """Ring with couplings J_i = +-1: Z(beta) = sum_E g(E) exp(-beta E) equals
@@ -314,6 +358,26 @@ def test_beta_zero_flips_every_spin():
     res = oracle.anneal(c, 16, np.zeros(1), sv.seed)
     assert np.array_equal(res.s_final, -s0)
     assert np.array_equal(res.e_final, [c.energy(s) for s in s0])
+
+
+@pytest.mark.parametrize("sweeps", [1, 2, 3])
+def test_best_state_needs_strict_improvement(sweeps):
+    """Best tracking is strict and happens at sweep ends only, with the initial
+    state as the first candidate.  At beta = 0 every sweep flips every spin, so
+    at each sweep end the energy equals E(s0) (spin-reversal symmetry): it never
+    strictly improves, and the best state stays s0 after any number of sweeps.
+    A non-strict comparison would return s_final = (-1)^S s0 instead, and a
+    check after every flip would return a lower, mid-sweep energy."""
+    for prob in (I.torus_20x20().problem, I.random_graph(200, 300, 4)):
+        c = oracle.csr_of(prob)
+        R = 16
+        s0 = oracle.initial_spins(c.n, np.arange(R), 11)
+        e0 = np.array([c.energy(s) for s in s0])
+        res = oracle.anneal(c, R, np.zeros(sweeps), 11)
+        assert np.array_equal(res.s_final, s0 * (-1) ** sweeps)
+        assert np.array_equal(res.e_final, e0)
+        assert np.array_equal(res.s_best, s0)
+        assert np.array_equal(res.e_best, e0)
 
 
 def test_zero_temperature_never_raises_energy():
