@@ -48,9 +48,14 @@ UNIT = "attempts/s"
 # compare (logic pipe).  The roofline takes the pipe whose share of the work
 # needs the longer time at its measured rate (isg_integer_peaks).
 ALGO_LOP3_PER_ATTEMPT = 20 / 4 + 1
-ALGO_MAD_PER_ATTEMPT = 20 / 4
+ALGO_MUL_PER_ATTEMPT = 20 / 4
+# Widening multiplies the torus kernel issues per attempt: per site and replica
+# word (32 attempts) the two of the site's round-1/2 prefix and 8 blocks x 8
+# remaining rounds x 2; the per-(block, sweep) prefix is shared by a whole band.
+EXEC_MUL_PER_ATTEMPT = (2 + 8 * 8 * 2) / 32
 SMSP_PER_SM = 4
 ALU_LANES_PER_SMSP = 16  # nominal: the logic pipe takes half a warp instruction per cycle
+MUL_LANES_PER_SMSP = 8   # nominal: a widening multiply holds the multiply pipe 4 cycles per warp
 KERNEL_NAMES = {1: "torus_kernel", 2: "csr_kernel", 3: "plain per-sweep launches",
                 4: "gm_kernel"}
 
@@ -393,11 +398,13 @@ def run_gpu(args):
     k_ms = statistics.mean(kernel_ms)
     rate = float(sv.attempts) / (k_ms / 1e3)                  # attempts/s of the sweep kernel
     t_lop3 = ALGO_LOP3_PER_ATTEMPT / pipes["lop3_per_s"]      # s per attempt at each pipe's peak
-    t_mad = ALGO_MAD_PER_ATTEMPT / pipes["mad_wide_per_s"]
-    if t_lop3 >= t_mad:
+    t_mul = ALGO_MUL_PER_ATTEMPT / pipes["mul_wide_per_s"]
+    if t_lop3 >= t_mul:
         pipe, ops, peak = "lop3 (logic pipe)", ALGO_LOP3_PER_ATTEMPT, pipes["lop3_per_s"]
     else:
-        pipe, ops, peak = "mad.wide.u32 (multiply pipe)", ALGO_MAD_PER_ATTEMPT, pipes["mad_wide_per_s"]
+        pipe, ops, peak = "mul.wide.u32 (multiply pipe)", ALGO_MUL_PER_ATTEMPT, pipes["mul_wide_per_s"]
+    nominal_mul = (props.multi_processor_count * SMSP_PER_SM * MUL_LANES_PER_SMSP *
+                   float(peaks.get("sm_max_mhz", 2070.0)) * 1e6)
     achieved = ops * rate
     kname = KERNEL_NAMES.get(stats["kernel"], "sweep kernel")
     traffic = profiled_traffic(name, kname)
@@ -420,15 +427,21 @@ def run_gpu(args):
                      "unit": "T instr/s", "frac": achieved / peak, "traffic": traffic,
                      "kernel": kname, "kernel_ms": k_ms, "pipe": pipe,
                      "algorithmic_per_attempt": {"lop3": ALGO_LOP3_PER_ATTEMPT,
-                                                 "mad.wide": ALGO_MAD_PER_ATTEMPT},
+                                                 "mul.wide": ALGO_MUL_PER_ATTEMPT},
                      "frac_per_pipe": {"lop3": ALGO_LOP3_PER_ATTEMPT * rate / pipes["lop3_per_s"],
-                                       "mad.wide": ALGO_MAD_PER_ATTEMPT * rate /
-                                       pipes["mad_wide_per_s"]},
+                                       "mul.wide": ALGO_MUL_PER_ATTEMPT * rate /
+                                       pipes["mul_wide_per_s"]},
+                     # the multiplies the torus kernel actually issues (rounds 1-2
+                     # factored) against the same peak
+                     "executed_mul_per_attempt": EXEC_MUL_PER_ATTEMPT,
+                     "frac_executed": (EXEC_MUL_PER_ATTEMPT * rate / pipes["mul_wide_per_s"]
+                                       if stats["kernel"] == 1 else None),
                      "peak_source": f"measured on this GPU by isg_integer_peaks: lop3 "
-                                    f"{pipes['lop3_per_s'] / 1e12:.2f}T/s, mad.wide "
-                                    f"{pipes['mad_wide_per_s'] / 1e12:.2f}T/s "
+                                    f"{pipes['lop3_per_s'] / 1e12:.2f}T/s, mul.wide "
+                                    f"{pipes['mul_wide_per_s'] / 1e12:.2f}T/s "
                                     f"({props.multi_processor_count} SMs)",
                      "nominal_lop3_peak": nominal_lop3 / 1e12,
+                     "nominal_mul_peak": nominal_mul / 1e12,
                      # the sweeps' own Philox code alone (and with the threshold masks):
                      # one uniform per attempt, so an upper bound on the attempt rate
                      "random_number_ceiling": {

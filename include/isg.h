@@ -294,7 +294,9 @@ isg_status isg_energy(const isg_problem *p, const int8_t *spins, int32_t replica
  * 512 KiB array inside the library that every device loading the library
  * keeps until the process exits.  replicas must be in [1, 2048] (EINVAL
  * otherwise).  The first call on a device looks up that array's device
- * address; make it before any stream capture.  All calls share the array, so
+ * address and keeps it for the life of the process (it assumes the device's
+ * primary context is not reset meanwhile); make that first call before any
+ * stream capture.  All calls share the array, so
  * calls whose work overlaps on the GPU (different streams, no ordering) race
  * and give wrong energies; calls ordered on one stream are fine. */
 isg_status isg_energy_noalloc(int32_t n, const int64_t *rowptr_dev, const int32_t *col_dev,
@@ -343,9 +345,13 @@ void isg_result_destroy(isg_result *r);
 /* ---------------------------------------------------------------- serving */
 
 /* A continuous-batching annealing server on the current device.  Requests
- * are admitted while a slot is free and their device state fits in
- * device_mem_budget bytes; admitted requests run together in chunks of one
- * persistent kernel launch; each runs until its target or its sweep budget.
+ * are admitted while a slot is free and their device state fits both in
+ * device_mem_budget bytes and in the device's free memory at admission
+ * (cudaMemGetInfo, less 256 MiB left for others; with nothing resident a
+ * request is admitted regardless, and comes back with a result whose reads
+ * return ISG_ENOMEM if its allocation fails).  Admitted requests run together
+ * in chunks of one persistent kernel launch; each runs until its target or
+ * its sweep budget.
  * A chunk advances every request by sweeps_per_chunk x sqrt(10,000 / n)
  * sweeps (n its spin count; at least 1), times a per-unit-kind factor (torus
  * words, graph words, graph quads) that the server adapts after every chunk
@@ -371,8 +377,10 @@ isg_status isg_server_poll(isg_server *s, uint64_t *request_id, isg_result **out
 /* Cancel a queued or running request.  A queued one is handed back at once, a
  * running one at the end of the chunk in progress (its state is dropped); in
  * both cases isg_server_poll returns it with a result whose reads return
- * ISG_ECANCELLED.  EINVAL for NULL or an id that is neither queued nor running
- * (unknown, or already finished: its result is then the normal one). */
+ * ISG_ECANCELLED: a cancel that returns ISG_OK always takes effect, even when
+ * the request would have reached its target or budget in that chunk.  EINVAL
+ * for NULL or an id that is neither queued nor running (unknown, or already
+ * decided finished at a chunk end: its result is then the normal one). */
 isg_status isg_server_cancel(isg_server *s, uint64_t request_id);
 
 /* Stop the server; unfinished requests are dropped.  */
@@ -415,13 +423,14 @@ isg_status isg_acceptance_table(const double *betas, int32_t sweeps, int32_t kma
 
 /* Measured throughput of the two integer instructions the sweep kernels are
  * built from, on the current device: three-input logic ops (lop3) and
- * widening 32x32->64 multiply-adds (mad.wide.u32), in thread-instructions per
- * second over the whole device.  The paper has no counterpart: these are the
- * denominators of the sweep kernels' roofline.  Runs two short kernels
- * (about 10 ms each) on cuda_stream (NULL = legacy default stream) and
- * synchronises with them; allocates 4 bytes per CTA, stream-ordered.  EINVAL
- * for NULL outputs, ECUDA if a launch fails. */
-isg_status isg_integer_peaks(void *cuda_stream, double *lop3_per_s, double *mad_wide_per_s);
+ * widening 32x32->64 multiplies by a constant (mul.wide.u32, the Philox
+ * product; each followed by one lop3, which runs on the other pipe), in
+ * thread-instructions per second over the whole device.  The paper has no
+ * counterpart: these are the denominators of the sweep kernels' roofline.
+ * Runs two short kernels (about 10 ms each) on cuda_stream (NULL = legacy
+ * default stream) and synchronises with them; allocates 4 bytes per CTA,
+ * stream-ordered.  EINVAL for NULL outputs, ECUDA if a launch fails. */
+isg_status isg_integer_peaks(void *cuda_stream, double *lop3_per_s, double *mul_wide_per_s);
 
 /* Measured rates, on the current device, of the sweep kernels' random numbers
  * alone: uniforms per second of the factored Philox4x32-10 stream the sweeps

@@ -22,6 +22,7 @@
 #include <cmath>
 #include <chrono>
 #include <climits>
+#include <cstdint>
 #include <condition_variable>
 #include <deque>
 #include <mutex>
@@ -178,18 +179,35 @@ cudaError_t grow(isg_server *s, size_t nt, size_t nc, size_t nstatus, size_t ng 
   return err;
 }
 
-// Admit queued requests while a slot and memory are free (worker thread).
+// Device memory an admission leaves free for everything else on the device
+// (the CUDA context's own needs, other streams' allocations).
+constexpr size_t kFreeHeadroom = size_t(256) << 20;
+
+// Admit queued requests while a slot and memory are free (worker thread): the
+// request's state must fit the server's budget and the device's free memory
+// (queried once per admission round, less the headroom).  With nothing
+// resident a request is admitted regardless; if its allocation then fails it
+// is handed back with ISG_ENOMEM.
 void admit(isg_server *s) {
+  size_t free_b = 0, total_b = 0;
+  if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) {
+    cudaGetLastError();
+    free_b = SIZE_MAX;  // unknown: the budget alone decides
+  }
   for (;;) {
     Request rq;
     {
       std::lock_guard<std::mutex> lock(s->mu);
       if (s->queue.empty() || (int32_t)s->active.size() >= s->max_slots) return;
-      if (!s->active.empty() && s->used + s->queue.front().bytes > s->budget) return;
+      const size_t need = s->queue.front().bytes;
+      if (!s->active.empty() &&
+          (s->used + need > s->budget || need > free_b || free_b - need < kFreeHeadroom))
+        return;
       rq = std::move(s->queue.front());
       s->queue.pop_front();
       s->live.insert(rq.id);  // cancellable from here on
     }
+    free_b = rq.bytes < free_b ? free_b - rq.bytes : 0;
     Slot *sl = new Slot();
     sl->rq = std::move(rq);
     const isg_problem *p = sl->rq.p;
@@ -238,6 +256,10 @@ void admit(isg_server *s) {
       if (sl->snap) cudaFreeAsync(sl->snap, s->stream);
       std::lock_guard<std::mutex> lock(s->mu);
       s->live.erase(sl->rq.id);
+      if (s->cancels.erase(sl->rq.id)) {  // cancelled while its admission failed
+        r->sync_status = ISG_ECANCELLED;
+        ++s->n_cancelled;
+      }
       s->done.emplace_back(sl->rq.id, r);
       ++s->n_completed;
       s->cv_done.notify_all();
@@ -580,33 +602,36 @@ void worker_main(isg_server *s) {
     // decide per request; collect the multi-unit requests that must re-run to t*
     std::vector<Slot *> redo;
     std::vector<int32_t> redo_end;
-    std::set<uint64_t> cancels;
     {
+      // Decided under the lock: a cancel that arrives before this block applies
+      // in this chunk; one that arrives after it finds a request finished here
+      // no longer live (EINVAL, normal result) and one still running queued for
+      // the next chunk.
       std::lock_guard<std::mutex> lock(s->mu);
-      cancels.swap(s->cancels);
-    }
-    off = 0;
-    for (Slot *sl : s->active) {
-      const int32_t u = sl->res->units;
-      int32_t tstar = INT_MAX;
-      for (int32_t q = 0; q < u; ++q)
-        if (s->h_status[off + q] >= 0) tstar = std::min(tstar, s->h_status[off + q]);
-      off += 2 * (size_t)u;
-      if (cancels.count(sl->rq.id)) {
-        sl->cancelled = true;
-        sl->finished = true;
-      } else if (sl->res->has_target && tstar != INT_MAX) {
-        sl->stop = tstar;
-        sl->finished = true;
-        if (u > 1) {
-          redo.push_back(sl);
-          redo_end.push_back(tstar + 1);
+      off = 0;
+      for (Slot *sl : s->active) {
+        const int32_t u = sl->res->units;
+        int32_t tstar = INT_MAX;
+        for (int32_t q = 0; q < u; ++q)
+          if (s->h_status[off + q] >= 0) tstar = std::min(tstar, s->h_status[off + q]);
+        off += 2 * (size_t)u;
+        if (s->cancels.erase(sl->rq.id)) {
+          sl->cancelled = true;
+          sl->finished = true;
+        } else if (sl->res->has_target && tstar != INT_MAX) {
+          sl->stop = tstar;
+          sl->finished = true;
+          if (u > 1) {
+            redo.push_back(sl);
+            redo_end.push_back(tstar + 1);
+          }
+        } else if (sl->t_end >= sl->rq.S) {
+          sl->stop = -1;
+          sl->finished = true;
+        } else {
+          sl->t = sl->t_end;
         }
-      } else if (sl->t_end >= sl->rq.S) {
-        sl->stop = -1;
-        sl->finished = true;
-      } else {
-        sl->t = sl->t_end;
+        if (sl->finished) s->live.erase(sl->rq.id);
       }
     }
     if (!redo.empty()) {
@@ -646,7 +671,6 @@ void worker_main(isg_server *s) {
       }
       sl->res->stream = nullptr;  // later frees go to the legacy stream
       std::lock_guard<std::mutex> lock(s->mu);
-      s->live.erase(sl->rq.id);
       s->done.emplace_back(sl->rq.id, sl->res);
       ++s->n_completed;
       if (sl->cancelled) ++s->n_cancelled;

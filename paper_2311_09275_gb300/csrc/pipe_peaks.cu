@@ -1,14 +1,13 @@
 // pipe_peaks.cu -- throughput of the two integer instructions the sweep kernels
 // are made of, measured on the device at hand: the three-input logic op
 // (lop3: Philox's XORs, the spin logic, the threshold masks) and the widening
-// 32x32->64 multiply-add (mad.wide.u32: Philox's products).  These rates are
-// the denominators of the sweep kernels' roofline.
+// 32x32->64 multiply by a constant (mul.wide.u32: Philox's products).  These
+// rates are the denominators of the sweep kernels' roofline.
 //
-// Each thread runs eight independent chains, one instruction per chain and
-// step; every step's eight results depend only on the previous step, so the
-// pipes, not latencies, set the rate once each SM holds enough warps.  A
-// second pair of kernels runs the sweeps' own Philox code alone, an upper
-// bound on any sweep's rate.
+// Each thread runs eight independent chains; every step's eight results
+// depend only on the previous step, so the pipes, not latencies, set the rate
+// once each SM holds enough warps.  A second pair of kernels runs the sweeps'
+// own Philox code alone, an upper bound on any sweep's rate.
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -29,9 +28,11 @@ __device__ __forceinline__ uint32_t lop3_xor(uint32_t a, uint32_t b, uint32_t c)
   return d;
 }
 
-__device__ __forceinline__ uint64_t mad_wide(uint32_t a, uint32_t b, uint64_t c) {
+// The Philox product: full 64-bit product of a word and a constant, with no
+// addend (a 64-bit addend costs extra instructions on both pipes).
+__device__ __forceinline__ uint64_t mul_wide_c(uint32_t a, uint32_t b) {
   uint64_t d;
-  asm volatile("mad.wide.u32 %0, %1, %2, %3;" : "=l"(d) : "r"(a), "r"(b), "l"(c));
+  asm volatile("mul.wide.u32 %0, %1, %2;" : "=l"(d) : "r"(a), "r"(b));
   return d;
 }
 
@@ -56,22 +57,29 @@ __global__ void __launch_bounds__(256) lop3_rate_kernel(uint32_t *sink, int iter
   if (acc == seed) sink[blockIdx.x] = acc;  // keeps the chains live
 }
 
+// Each step is one Philox half-round: the widening product of the chain word
+// and a constant, then the XOR of its two halves with a key word (lop3, on the
+// other pipe, at half the multiply's issue cost), exactly the sweeps' form.
 __global__ void __launch_bounds__(256) mad_rate_kernel(uint32_t *sink, int iters, uint32_t seed) {
-  uint64_t r[kChains];
-  const uint32_t mul = 0xD2511F53u ^ (seed & 1u);
+  uint32_t x[kChains];
+  const uint32_t mul = 0xD2511F53u ^ (seed & 2u);
+  const uint32_t key = 0x9E3779B9u * seed;
 #pragma unroll
-  for (int k = 0; k < kChains; ++k) r[k] = (uint64_t)(seed + threadIdx.x) << 32 | (k + 1u);
+  for (int k = 0; k < kChains; ++k) x[k] = (seed + threadIdx.x) * 0x85EBCA6Bu + k;
   for (int i = 0; i < iters; ++i) {
 #pragma unroll
     for (int u = 0; u < kUnroll; ++u) {
 #pragma unroll
-      for (int k = 0; k < kChains; ++k) r[k] = mad_wide((uint32_t)(r[k] >> 32), mul, r[k]);
+      for (int k = 0; k < kChains; ++k) {
+        const uint64_t p = mul_wide_c(x[k], mul);
+        x[k] = lop3_xor((uint32_t)(p >> 32), (uint32_t)p, key);
+      }
     }
   }
-  uint64_t acc = 0u;
+  uint32_t acc = 0u;
 #pragma unroll
-  for (int k = 0; k < kChains; ++k) acc ^= r[k];
-  if ((uint32_t)acc == seed) sink[blockIdx.x] = (uint32_t)(acc >> 32);
+  for (int k = 0; k < kChains; ++k) acc ^= x[k];
+  if (acc == seed) sink[blockIdx.x] = acc;
 }
 
 // The sweep's random numbers alone: per site the round-1/2 prefix and eight
@@ -165,8 +173,8 @@ extern "C" isg_status isg_philox_rates(void *cuda_stream, double *uniforms_per_s
 }
 
 extern "C" isg_status isg_integer_peaks(void *cuda_stream, double *lop3_per_s,
-                                        double *mad_wide_per_s) {
-  if (!lop3_per_s || !mad_wide_per_s) return fail(ISG_EINVAL, "outputs must not be NULL");
+                                        double *mul_wide_per_s) {
+  if (!lop3_per_s || !mul_wide_per_s) return fail(ISG_EINVAL, "outputs must not be NULL");
   cudaStream_t stream = (cudaStream_t)cuda_stream;
   const int blocks = sm_count() * 8, threads = 256, iters = 2048;
   const double per_launch = (double)blocks * threads * iters * kUnroll * kChains;
@@ -200,6 +208,6 @@ extern "C" isg_status isg_integer_peaks(void *cuda_stream, double *lop3_per_s,
   if (e1) cudaEventDestroy(e1);
   if (err != cudaSuccess) return cuda_fail(err, "measuring integer pipe rates");
   *lop3_per_s = rate[0];
-  *mad_wide_per_s = rate[1];
+  *mul_wide_per_s = rate[1];
   return ISG_OK;
 }

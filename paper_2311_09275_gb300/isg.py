@@ -421,10 +421,10 @@ def isg_philox_rates(stream=None) -> dict:
 
 
 def isg_integer_peaks(stream=None) -> dict:
-    """Measured device-wide rates (thread-instructions/s) of lop3 and mad.wide.u32."""
+    """Measured device-wide rates (thread-instructions/s) of lop3 and mul.wide.u32."""
     a, b = _dbl(), _dbl()
     _check(_lib.isg_integer_peaks(_stream(stream), ctypes.byref(a), ctypes.byref(b)))
-    return {"lop3_per_s": a.value, "mad_wide_per_s": b.value}
+    return {"lop3_per_s": a.value, "mul_wide_per_s": b.value}
 
 
 def isg_result_final(r: Result, spins: bool = True):

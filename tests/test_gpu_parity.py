@@ -513,6 +513,81 @@ def test_server_cancel(isg):
     assert np.array_equal(got[c].best_all(), solo.best_all())
 
 
+def test_server_cancel_racing_the_chunk_end(isg):
+    """Cancels that race the chunk end at which their requests finish: a cancel
+    that returns OK always hands its request back ECANCELLED, a cancel that
+    comes too late is EINVAL and its request comes back with the normal result
+    (equal to the solo run), and the cancel count equals the OK cancels."""
+    import random
+    import time
+    small = isg.problem_of(I.torus(16, 16, 3))
+    betas = I.geometric_betas(0.2, 3.0, 30)
+    srv = isg.Server(1 << 30, 4, 30)              # every request ends in its first chunk
+    rng = random.Random(5)
+    ok, ids = set(), []
+    for k in range(80):
+        rid = srv.submit(small, 32, betas, k + 1)
+        ids.append(rid)
+        time.sleep(rng.uniform(0.0, 0.003))
+        try:
+            srv.cancel(rid)
+            ok.add(rid)
+        except isg.IsgError as e:
+            assert e.status == isg.ISG_EINVAL
+    got = {}
+    while len(got) < len(ids):
+        out = srv.poll(60.0)
+        assert out is not None, "server timed out"
+        got[out[0]] = out[1]
+    st = srv.stats()
+    srv.close()
+    assert st["cancelled"] == len(ok) and st["completed"] == len(ids)
+    for k, rid in enumerate(ids):
+        if rid in ok:
+            with pytest.raises(isg.IsgError) as e:
+                got[rid].final()
+            assert e.value.status == isg.ISG_ECANCELLED
+        else:
+            solo = isg.isg_anneal(small, 32, betas, k + 1)
+            assert np.array_equal(got[rid].final()[1], solo.final()[1])
+            assert np.array_equal(got[rid].best_all(), solo.best_all())
+
+
+def test_server_admission_waits_for_free_device_memory(isg):
+    """Admission by free device memory: with the budget and slots ample but the
+    device nearly full, a second large request is held until the first is
+    retired, then served equal to its solo run."""
+    import torch
+    big = isg.problem_of(I.torus(100, 200, 4))
+    betas = I.geometric_betas(0.2, 3.0, 600)
+    R = 8192                                   # ~370 MB of state and output per request
+    srv = isg.Server(1 << 40, 8, 10)
+    free, _ = torch.cuda.mem_get_info()
+    hog = torch.empty(free - (900 << 20), dtype=torch.uint8, device="cuda")
+    try:
+        a = srv.submit(big, R, betas, 1)
+        b = srv.submit(big, R, betas, 2)
+        got = {}
+        while len(got) < 2:
+            out = srv.poll(120.0)
+            assert out is not None, "server timed out"
+            got[out[0]] = out[1]
+        st = srv.stats()
+        fa = got[a].final()[1]
+        fb = got[b].final()[1]
+        for r in got.values():
+            r.close()
+    finally:
+        srv.close()
+        del hog
+        torch.cuda.empty_cache()
+    assert st["peak_active"] == 1 and st["completed"] == 2
+    for seed, f in ((1, fa), (2, fb)):
+        solo = isg.isg_anneal(big, R, betas, seed)
+        assert np.array_equal(solo.final()[1], f)
+        solo.close()
+
+
 def test_injected_allocation_failures(isg):
     """Host-side fault injection, no device fault: a solve whose state allocation
     fails returns ENOMEM and the library stays usable; a served request whose
