@@ -193,15 +193,31 @@ def barrier(dist):
         dist.barrier()
 
 
+def global_best(e_best: int, local_replica: int, first_replica: int, dist, device):
+    """Final argmin of a replica-sharded solve: every rank's lowest best energy and
+    its global replica index (first_replica + local index) gathered to all ranks;
+    the overall best is the lowest energy, ties to the lowest global replica (the
+    rule of isg_best within one call)."""
+    mine = (int(e_best), int(first_replica) + int(local_replica))
+    if dist is None:
+        return mine
+    import torch
+    t = torch.tensor(mine, dtype=torch.int64, device=device)
+    allv = [torch.empty_like(t) for _ in range(dist.get_world_size())]
+    dist.all_gather(allv, t)
+    return min((int(x[0]), int(x[1])) for x in allv)
+
+
 COLOURINGS = {"greedy": 0, "smallest-last": 1}
 
 
 def workload(config: str, rank: int, sweeps: int | None = None, colouring: str = "greedy"):
-    """The Solve of this rank.  Ranks anneal the same instance with their own
-    seeds (independent replicas: weak scaling, no exchange).  `sweeps`
-    shortens the schedule (profiling runs only; the benchmark line uses the
-    full 10,000).  A graph workload coloured other than greedy by id names its
-    colouring."""
+    """The Solve of this rank and its first global replica.  Ranks anneal the
+    same instance with the same seed, rank k its own replicas [kR, (k+1)R)
+    (a replica-sharded solve of N x R replicas: weak scaling, no exchange but
+    the final argmin).  `sweeps` shortens the schedule (profiling runs only;
+    the benchmark line uses the full 10,000).  A graph workload coloured other
+    than greedy by id names its colouring."""
     if config == "torus":
         sv = I.torus_80x100(sweeps=sweeps or 10000)
         name = f"torus_80x100_R1024_S{sv.sweeps}_geometric_0.1_5.0"
@@ -215,8 +231,7 @@ def workload(config: str, rank: int, sweeps: int | None = None, colouring: str =
         raise ValueError(config)
     if colouring != "greedy" and config != "torus":
         name += "_" + colouring.replace("-", "_")
-    sv.seed = sv.seed + rank
-    return sv, name
+    return sv, name, rank * sv.replicas
 
 
 def oracle_colour(c, colouring: str):
@@ -269,7 +284,7 @@ def run_reference(args):
                           f"the oracle arm times the single-instance workloads (torus, random, "
                           f"mis); --config {args.config} has no oracle timing line"}))
         return
-    sv, name = workload(args.config, 0, args.sweeps, args.colouring)
+    sv, name, _ = workload(args.config, 0, args.sweeps, args.colouring)
     import oracle
     cores = os.cpu_count() or 1
     reps = min(sv.replicas, cores)
@@ -312,7 +327,7 @@ def run_gpu(args):
     device = torch.device("cuda", local)
     from paper_2311_09275_gb300 import isg
 
-    sv, name = workload(args.config, rank, args.sweeps, args.colouring)
+    sv, name, first = workload(args.config, rank, args.sweeps, args.colouring)
     stream = torch.cuda.current_stream()
     p = isg.problem_of(sv.problem, colouring=COLOURINGS[args.colouring])
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.int32, device=device)  # 512 MB > L2
@@ -326,7 +341,7 @@ def run_gpu(args):
 
     def step(time_kernels=True):
         return isg.isg_anneal(p, sv.replicas, sv.betas, sv.seed, stream=stream,
-                              time_kernels=time_kernels, **shape)
+                              time_kernels=time_kernels, first_replica=first, **shape)
 
     # launch-shape autotuning (untimed, part of warm-up); results never depend on it
     tuned = None
@@ -361,6 +376,9 @@ def run_gpu(args):
         kernel_ms.append(stats["sweep_kernel_ms"])
         launches += stats["launches"]
         sweep_launches += stats["sweep_launches"]
+    be, br, _, _, _ = results[-1].best(spins=False)       # outside the timed region
+    best_e, best_r = global_best(be, br, first, dist, device)
+    for r in results:
         r.close()
     dev_s = max_over_ranks(sum(step_ms) / 1e3, dist, device)
     attempts_rank = float(sv.attempts) * args.steps
@@ -416,13 +434,17 @@ def run_gpu(args):
         "data": "synthetic",
         "config": {"workload": name, "replicas": sv.replicas, "spins": sv.n,
                    "sweeps": sv.sweeps, "attempts_per_step": sv.attempts,
-                   "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
+                   "parallelism": (f"replica-sharded: rank k anneals replicas [k*{sv.replicas}, "
+                                   f"(k+1)*{sv.replicas}) of one solve" if world > 1
+                                   else "single GPU"),
                    "l2": "flushed (512 MB write) before every timed step",
                    "launch": {k: stats[k] for k in ("kernel", "ctas", "cluster_ctas", "threads")},
                    "autotuned": tuned is not None},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                 "d2h_bytes_per_step": int(d2h), "steps": e2e_steps},
         "gpu_launches": launches,
+        # the solve's overall best over all ranks' replicas (final argmin gather)
+        "global_best": {"energy": best_e, "replica": best_r, "replicas": sv.replicas * world},
         "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": peak / 1e12,
                      "unit": "T instr/s", "frac": achieved / peak, "traffic": traffic,
                      "kernel": kname, "kernel_ms": k_ms, "pipe": pipe,
@@ -453,33 +475,37 @@ def run_gpu(args):
     }
     if rank == 0 and world == 1 and not args.no_cpu:
         line["cpu_baseline"] = cpu_oracle_rate(sv, colouring=args.colouring)
+    if rank == 0 and world == 1 and args.config == "torus" and not args.no_forms:
+        # the batched and served forms on the same GPU, after the headline
+        # measurement and outside its timed region, each with its own clock sample
+        line["batched"] = batched_form(steps=3, warmup=1)
+        line["served"] = served_form()
     if rank == 0:
         print(json.dumps(line))
 
 
 # ---------------------------------------------------------------- batched form
-def run_batch(args):
+def batched_form(steps: int, warmup: int, sweeps: int = 2000):
     """512 uneven tori (even L, W in [16, 140]), 32 replicas, 2,000 sweeps, in
     one persistent kernel launched through a CUDA graph; against the plain form
     (one instance per launch sequence, one launch per sweep) on a size-stratified
-    sample of the same instances, and against one persistent launch per instance."""
+    sample of the same instances, and against one persistent launch per instance.
+    Returns the measurements (with their own clock samples) as a dict."""
     import torch
     from paper_2311_09275_gb300 import isg
-    torch.cuda.set_device(0)
     stream = torch.cuda.current_stream()
-    sweeps = args.sweeps or 2000
     batch = I.torus_batch(sweeps=sweeps)
     probs = [isg.problem_of(sv.problem) for sv in batch]
     betas, seeds = batch[0].betas, [sv.seed for sv in batch]
     attempts = float(sum(sv.attempts for sv in batch))
-    for _ in range(args.warmup):
+    for _ in range(warmup):
         for r in isg.isg_anneal_batch(probs, 32, betas, seeds, stream=stream):
             r.close()
     torch.cuda.synchronize()
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-          for _ in range(args.steps)]
-    with ClockSampler(0) as clocks:
-        for k in range(args.steps):
+          for _ in range(steps)]
+    with ClockSampler(torch.cuda.current_device()) as clocks:
+        for k in range(steps):
             ev[k][0].record(stream)
             outs = isg.isg_anneal_batch(probs, 32, betas, seeds, stream=stream)
             ev[k][1].record(stream)
@@ -487,50 +513,67 @@ def run_batch(args):
             stats = outs[0].stats()
             for r in outs:
                 r.close()
-    ms = [a.elapsed_time(b) for a, b in ev]
-    value = attempts * args.steps / (sum(ms) / 1e3)
-    # plain forms on a sample: every 32nd instance in size order
-    order = sorted(range(len(batch)), key=lambda k: batch[k].n)
-    sample = order[::32]
-    sample_attempts = float(sum(batch[k].attempts for k in sample))
-    rates = {}
-    for label, kernel in (("plain_one_launch_per_sweep", isg.KERNEL_PLAIN),
-                          ("one_persistent_launch_per_instance", isg.KERNEL_AUTO)):
-        torch.cuda.synchronize()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        rs = [isg.isg_anneal(probs[k], 32, betas, seeds[k], stream=stream, kernel=kernel)
-              for k in sample]
-        e1.record(stream)
-        torch.cuda.synchronize()
-        for r in rs:
-            r.close()
-        rates[label] = sample_attempts / (e0.elapsed_time(e1) / 1e3)
-    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": sum(ms) / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
-            "config": {"workload": f"batch512_tori_L_W_even_16_140_R32_S{sweeps}_geometric_0.1_5.0",
-                       "attempts_per_step": attempts, "launch": "CUDA graph: 1 persistent kernel "
-                       f"({stats['ctas']} CTAs x {stats['threads']} threads) + 1 unpack",
-                       "l2": "working set of each CTA in shared memory; inputs ~12 MB"},
+        ms = [a.elapsed_time(b) for a, b in ev]
+        value = attempts * steps / (sum(ms) / 1e3)
+        # plain forms on a sample: every 32nd instance in size order
+        order = sorted(range(len(batch)), key=lambda k: batch[k].n)
+        sample = order[::32]
+        sample_attempts = float(sum(batch[k].attempts for k in sample))
+        rates = {}
+        for label, kernel in (("plain_one_launch_per_sweep", isg.KERNEL_PLAIN),
+                              ("one_persistent_launch_per_instance", isg.KERNEL_AUTO)):
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            rs = [isg.isg_anneal(probs[k], 32, betas, seeds[k], stream=stream, kernel=kernel)
+                  for k in sample]
+            e1.record(stream)
+            torch.cuda.synchronize()
+            for r in rs:
+                r.close()
+            rates[label] = sample_attempts / (e0.elapsed_time(e1) / 1e3)
+    for p in probs:
+        p.close()
+    return {"workload": f"batch512_tori_L_W_even_16_140_R32_S{sweeps}_geometric_0.1_5.0",
+            "attempts_per_s": value, "unit": UNIT, "steps": steps, "warmup": warmup,
+            "ms_per_step": sum(ms) / steps, "attempts_per_step": attempts,
+            "launch": f"CUDA graph: 1 persistent kernel ({stats['ctas']} CTAs x "
+                      f"{stats['threads']} threads) + 1 unpack",
+            "gpu_launches_per_step": stats["launches"],
             "plain": {"sample": f"{len(sample)} instances (every 32nd by size)",
-                      "attempts_per_s": rates,
-                      "batched_over_plain": {k: value / v for k, v in rates.items()}},
-            "gpu_launches": stats["launches"], "clocks": clocks.summary()}
+                      "attempts_per_s": rates},
+            "batched_over_plain": {k: value / v for k, v in rates.items()},
+            "clocks": clocks.summary()}
+
+
+def run_batch(args):
+    import torch
+    torch.cuda.set_device(0)
+    b = batched_form(args.steps, args.warmup, args.sweeps or 2000)
+    line = {"metric": METRIC, "value": b["attempts_per_s"], "unit": UNIT, "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": b["ms_per_step"],
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
+            "data": "synthetic",
+            "config": {"workload": b["workload"], "attempts_per_step": b["attempts_per_step"],
+                       "launch": b["launch"],
+                       "l2": "working set of each CTA in shared memory; inputs ~12 MB"},
+            "plain": dict(b["plain"], batched_over_plain=b["batched_over_plain"]),
+            "gpu_launches": b["gpu_launches_per_step"], "clocks": b["clocks"]}
     print(json.dumps(line))
 
 
 # ---------------------------------------------------------------- served form
-def run_served(args):
+def served_form(count: int = 2000, sweeps: int = 10000, slots: int = 512, chunk: int = 250,
+                mem_gb: int = 32):
     """Poisson request stream (200/s): half +-1 tori 40..100 x 40..200, half
     random graphs of 2,000..20,000 vertices and mean degree 2..4; 32 replicas,
     10,000-sweep budget, target = the plain run's best over the full budget.
-    Reports p50/p99 time-to-target (arrival -> result) and throughput."""
+    Measures p50/p99 time-to-target (arrival -> result) and throughput; after
+    the timed stream, 16 evenly spaced requests are compared with the same
+    request run alone (tests/test_gpu_served_oracle.py checks a seeded sample of
+    64 served requests against the oracle).  Returns the measurements as a dict."""
     import torch
     from paper_2311_09275_gb300 import isg, metrics
-    torch.cuda.set_device(0)
-    count = args.requests
-    sweeps = args.sweeps or 10000
     reqs = I.served_stream(count=count, sweeps=sweeps)
     probs = [isg.problem_of(r.solve.problem) for r in reqs]
     # targets from plain runs of the full budget (batched through a server, untimed)
@@ -546,13 +589,14 @@ def run_served(args):
         got[1].close()
     srv.close()
     # timed served run
-    srv = isg.Server(args.mem_gb << 30, args.slots, args.chunk)
+    srv = isg.Server(mem_gb << 30, slots, chunk)
     t_submit, t_done, hit, attempts = {}, {}, {}, 0.0
     check = {j: None for j in range(0, count, max(1, count // 16))}
+    kept = {}
     t0 = time.perf_counter()
     k = 0
     ids = {}
-    with ClockSampler(0) as clocks:
+    with ClockSampler(torch.cuda.current_device()) as clocks:
         while len(t_done) < count:
             now = time.perf_counter() - t0
             while k < count and reqs[k].arrival_s <= now:
@@ -571,7 +615,7 @@ def run_served(args):
             hit[j] = got[1].best(spins=False)[4]
             attempts += reqs[j].solve.replicas * reqs[j].solve.n * done
             if j in check:
-                check[j] = got[1]  # compared with a solo run after the timed region
+                kept[j] = got[1]  # checked after the timed region
             else:
                 got[1].close()
     wall = time.perf_counter() - t0
@@ -579,29 +623,44 @@ def run_served(args):
     srv.close()
     # bit-exactness in the mix: sampled requests against the same request alone
     exact = 0
-    for j, res in check.items():
-        r = reqs[j].solve
+    for j in check:
+        res, r = kept[j], reqs[j].solve
         solo = isg.isg_anneal(probs[j], r.replicas, r.betas, r.seed, target=targets[j])
         same = all(np.array_equal(a, b) for a, b in zip(res.final(), solo.final()))
         same = same and np.array_equal(res.best_all(), solo.best_all())
         same = same and res.best(spins=False)[4] == solo.best(spins=False)[4]
         exact += int(same)
-        res.close()
         solo.close()
+    for res in kept.values():
+        res.close()
+    for p in probs:
+        p.close()
     ttt = [t_done[j] - t_submit[j] for j in range(count)]
-    line = {"metric": "time-to-target (served)", "value": metrics.percentile(ttt, 99), "unit": "s",
-            "n_gpus": 1, "steps": 1, "warmup": 0, "ms_per_step": wall * 1e3,
-            "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
-            "data": "synthetic",
-            "config": {"workload": f"served_poisson200_{count}req_R32_B{sweeps}",
-                       "slots": args.slots, "sweeps_per_chunk": args.chunk,
-                       "device_mem_budget_gb": args.mem_gb},
+    return {"workload": f"served_poisson200_{count}req_R32_B{sweeps}",
+            "slots": slots, "sweeps_per_chunk": chunk, "device_mem_budget_gb": mem_gb,
             "ttt_p50_s": metrics.percentile(ttt, 50), "ttt_p99_s": metrics.percentile(ttt, 99),
-            "throughput_attempts_per_s": attempts / wall, "requests_per_s": count / wall,
+            "attempts_per_s": attempts / wall, "requests_per_s": count / wall,
+            "wall_s": wall, "requests": count,
             "targets_hit": sum(1 for j in range(count) if hit[j] >= 0),
             "peak_resident_slots": sstats["peak_active"], "chunk_passes": sstats["passes"],
             "bit_exact_vs_alone": f"{exact}/{len(check)} sampled requests",
             "clocks": clocks.summary()}
+
+
+def run_served(args):
+    import torch
+    torch.cuda.set_device(0)
+    f = served_form(args.requests, args.sweeps or 10000, args.slots, args.chunk, args.mem_gb)
+    line = {"metric": "time-to-target (served)", "value": f["ttt_p99_s"], "unit": "s",
+            "n_gpus": 1, "steps": 1, "warmup": 0, "ms_per_step": f["wall_s"] * 1e3,
+            "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
+            "data": "synthetic",
+            "config": {"workload": f["workload"], "slots": f["slots"],
+                       "sweeps_per_chunk": f["sweeps_per_chunk"],
+                       "device_mem_budget_gb": f["device_mem_budget_gb"]}}
+    line.update({k: v for k, v in f.items() if k not in ("workload", "slots", "sweeps_per_chunk",
+                                                          "device_mem_budget_gb")})
+    line["throughput_attempts_per_s"] = f["attempts_per_s"]
     print(json.dumps(line))
 
 
@@ -744,6 +803,8 @@ def main():
     ap.add_argument("--mem-gb", type=int, default=32, help="served: device memory budget (GB)")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-tune", action="store_true", help="skip the launch-shape autotuner")
+    ap.add_argument("--no-forms", action="store_true",
+                    help="default workload: skip the batched and served measurements")
     ap.add_argument("--kernel", type=int, default=0,
                     help="kernel family (1 torus, 2 colour-class int8, 3 plain, 4 graph "
                          "multi-spin; 0 = tuned)")

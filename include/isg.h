@@ -163,6 +163,12 @@ typedef struct {
                               torus kernel); 0 = tuned/default */
     int32_t time_kernels;  /* nonzero: time the sweep launches with CUDA events */
     int32_t quads_per_cta; /* colour-class kernel: replica quads per CTA (1, 2); 0 = tuned/default */
+    int32_t first_replica; /* global index of this call's replica 0, a multiple of 32 (0 = the
+                              usual): local replica j draws the random numbers of replica
+                              first_replica + j, so calls at first_replica 0, R, 2R, ... on
+                              any devices together equal one solve of all their replicas
+                              (a replica-sharded solve; a target applies to this call's
+                              replicas only).  Results stay indexed 0..R-1 locally. */
 } isg_options;
 
 /* Anneal R = replicas independent chains for S = sweeps sweeps at inverse
@@ -336,6 +342,7 @@ typedef struct {
                                 vertices it updates in shared memory (the multi-spin graph
                                 kernel then sends a new word only to the cluster CTAs that
                                 update one of the vertex's neighbours), else 0 */
+    int32_t first_replica;   /* isg_options.first_replica of the solve (0 for other forms) */
 } isg_stats;
 
 isg_status isg_result_stats(const isg_result *r, isg_stats *stats);

@@ -255,7 +255,7 @@ __device__ void gm_word(const GraphMscSolve &s, const GraphMscLaunch &L, int wor
   int32_t *lane_acc = reinterpret_cast<int32_t *>(smem + lay.lane_acc);
   const uint32_t *wtab = s.table + (size_t)word * s.table_ws;  // this word's threshold rows
   const PhiloxKey key{s.key0, s.key1};
-  const uint32_t uword = (uint32_t)word;
+  const uint32_t uword = (uint32_t)(word + s.rng_word0);  // Philox counters only
   const int rem = s.replicas - 32 * word;
   const uint32_t valid = rem >= 32 ? 0xFFFFFFFFu : ((1u << rem) - 1u);
   uint32_t *gspin = s.spins + (size_t)word * n;

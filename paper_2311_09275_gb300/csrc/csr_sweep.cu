@@ -233,7 +233,7 @@ __device__ void csr_solve(const CsrSolve &s, const CsrLaunch &L, int quad0, int 
     } else if (resume) {
       w = s.spins[(size_t)gq * n + v];
     } else {
-      const uint4 u = philox10(make_uint4((uint32_t)s.orig[v], 0u, (uint32_t)gq, kTagInit), key);
+      const uint4 u = philox10(make_uint4((uint32_t)s.orig[v], 0u, (uint32_t)(gq + s.rng_quad0), kTagInit), key);
       w = ((u.x >> 31) ? 0x01u : 0xFFu) | (((u.y >> 31) ? 0x01u : 0xFFu) << 8) |
           (((u.z >> 31) ? 0x01u : 0xFFu) << 16) | (((u.w >> 31) ? 0x01u : 0xFFu) << 24);
     }
@@ -348,7 +348,8 @@ __device__ void csr_solve(const CsrSolve &s, const CsrLaunch &L, int quad0, int 
       const uint32_t ov = (uint32_t)adj.orig[cob[c] + threadIdx.x];
 #pragma unroll
       for (int q = 0; q < Q; ++q)
-        pu[q] = philox10(make_uint4(ov, (uint32_t)tt, (uint32_t)(quad0 + q), kTagSweep), key);
+        pu[q] = philox10(
+            make_uint4(ov, (uint32_t)tt, (uint32_t)(quad0 + q + s.rng_quad0), kTagSweep), key);
       if (MODE == 2 && s.field) phv = __ldg(&s.field[v]);
     }
   };
@@ -406,9 +407,11 @@ __device__ void csr_solve(const CsrSolve &s, const CsrLaunch &L, int quad0, int 
           for (int l = 0; l < 4; ++l) up |= (kk[q][l] > 0 ? 1u : 0u) << l;
           uint32_t acc = ~up & 0xFu;
           if (up != 0u) {
-            const uint4 u = ready ? pu[q]
-                                  : philox10(make_uint4(ov, (uint32_t)t, (uint32_t)(quad0 + q),
-                                                        kTagSweep), key);
+            const uint4 u =
+                ready ? pu[q]
+                      : philox10(make_uint4(ov, (uint32_t)t,
+                                            (uint32_t)(quad0 + q + s.rng_quad0), kTagSweep),
+                                 key);
             if ((up & 1u) && u.x < row[kk[q][0]]) acc |= 1u;
             if ((up & 2u) && u.y < row[kk[q][1]]) acc |= 2u;
             if ((up & 4u) && u.z < row[kk[q][2]]) acc |= 4u;

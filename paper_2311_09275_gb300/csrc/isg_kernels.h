@@ -36,6 +36,7 @@ struct TorusSolve {
   RoundKeys rk;              // round_keys(key0, key1)
   int32_t words;             // replica words of this solve
   int32_t replicas;          // R (lanes >= R of the last word are padding)
+  int32_t rng_word0;         // global replica word of word 0 (its Philox counters)
   uint32_t *spins;           // [words][L*W] state in/out
   uint32_t *best;            // [words][L*W]
   int32_t *e_cur;            // [words*32]
@@ -99,6 +100,7 @@ struct CsrSolve {
   uint32_t key0, key1;
   int32_t quads;               // ceil(R / 4)
   int32_t replicas;
+  int32_t rng_quad0;           // global replica quad of quad 0 (its Philox counters)
   uint32_t *spins;             // [quads][n]
   uint32_t *best;              // [quads][n]
   int32_t *e_cur;              // [quads*4]
@@ -160,6 +162,7 @@ struct GraphMscSolve {
   RoundKeys rk;
   int32_t words;
   int32_t replicas;
+  int32_t rng_word0;           // global replica word of word 0 (its Philox counters)
   uint32_t *spins;             // [words][n]
   uint32_t *best;              // [words][n]
   int32_t *e_cur;              // [words*32]

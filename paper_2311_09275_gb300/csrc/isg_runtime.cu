@@ -633,6 +633,7 @@ TorusSolve make_torus_solve(const isg_problem *p, const DeviceProblem *dp, const
   s.rk = round_keys(s.key0, s.key1);
   s.words = r->units;
   s.replicas = r->R;
+  s.rng_word0 = r->first_replica / 32;
   s.spins = r->d_spins;
   s.best = r->d_best;
   s.e_cur = r->d_e_cur;
@@ -661,6 +662,7 @@ CsrSolve make_csr_solve(const isg_problem *p, const DeviceProblem *dp, const isg
   s.key1 = (uint32_t)(seed >> 32);
   s.quads = r->units;
   s.replicas = r->R;
+  s.rng_quad0 = r->first_replica / 4;
   s.spins = r->d_spins;
   s.best = r->d_best;
   s.e_cur = r->d_e_cur;
@@ -692,6 +694,7 @@ GraphMscSolve make_gm_solve(const isg_problem *p, const DeviceProblem *dp, const
   s.rk = round_keys(s.key0, s.key1);
   s.words = r->units;
   s.replicas = r->R;
+  s.rng_word0 = r->first_replica / 32;
   s.spins = r->d_spins;
   s.best = r->d_best;
   s.e_cur = r->d_e_cur;
@@ -943,6 +946,9 @@ isg_status anneal_impl(const isg_problem *p, int32_t R, const double *betas, int
   // launch shape: explicit, else measured (isg_autotune), else the default rule
   if (o.quads_per_cta < 0 || o.quads_per_cta > 2)
     return fail(ISG_EINVAL, "quads_per_cta must be 0, 1 or 2");
+  if (o.first_replica < 0 || o.first_replica % 32 != 0 ||
+      (int64_t)o.first_replica + R > INT32_MAX)
+    return fail(ISG_EINVAL, "first_replica must be a multiple of 32 in [0, 2^31 - 1 - replicas]");
   const int units = msc ? (R + 31) / 32 : (R + 3) / 4;
   int cluster = plain ? 1 : o.cluster_ctas, threads = o.threads, qpc = o.quads_per_cta;
   if (tuned) {
@@ -976,6 +982,7 @@ isg_status anneal_impl(const isg_problem *p, int32_t R, const double *betas, int
   if (st != ISG_OK) return st;
 
   isg_result *r = new_result(p, R, S, msc, has_target, stream);
+  r->first_replica = o.first_replica;
   r->h2d_bytes = (int64_t)uploaded;
   r->relabelled = !tmsc;
   r->kernel = kernel;
@@ -1830,6 +1837,7 @@ isg_status isg_result_stats(const isg_result *r, isg_stats *stats) {
   stats->threads = r->threads;
   stats->h2d_bytes = r->h2d_bytes;
   stats->staged = r->staged;
+  stats->first_replica = r->first_replica;
   return ISG_OK;
 }
 

@@ -67,6 +67,7 @@ struct isg_result {
   cudaEvent_t done = nullptr, t0 = nullptr, t1 = nullptr;
   bool timed = false;
   int32_t n = 0, R = 0, S = 0;
+  int32_t first_replica = 0;               // global index of replica 0 (Philox counters)
   bool has_target = false;
   int32_t kernel = 0;
   bool msc = false;                        // 32-lane replica words (torus or graph kernel)

@@ -240,7 +240,7 @@ __device__ void torus_word(const TorusSolve &s, int word, int k, int K, int t_be
   uint8_t *cb = smem + lay.cb;
   int32_t *part = reinterpret_cast<int32_t *>(smem + lay.part);
   const PhiloxKey key{s.key0, s.key1};
-  const uint32_t uword = (uint32_t)word;
+  const uint32_t uword = (uint32_t)(word + s.rng_word0);  // Philox counters only
   const int rem = s.replicas - 32 * word;
   const uint32_t valid = rem >= 32 ? 0xFFFFFFFFu : ((1u << rem) - 1u);
   uint32_t *gspin = s.spins + (size_t)word * n;

@@ -28,7 +28,9 @@ def isg():
     return mod
 
 
-def assert_same(res, orc, reps=None, check_done=True):
+def assert_same(res, orc, reps=None, check_done=True, first_replica=0):
+    """res (replicas first_replica + 0..R-1, local indices) equals the oracle's
+    result orc (global replica ids)."""
     spins, e, done = res.final()
     best = res.best_all()
     be, br, bs, per, hit = res.best()
@@ -42,8 +44,8 @@ def assert_same(res, orc, reps=None, check_done=True):
         assert hit == orc.hit_sweep
     if reps is None:
         ob, orr = orc.best
-        assert (be, br) == (ob, orr)
-        assert np.array_equal(bs, orc.s_best[orr])
+        assert (be, br + first_replica) == (ob, orr)
+        assert np.array_equal(bs, orc.s_best[orr - first_replica])
 
 
 # ------------------------------------------------------------------ torus
@@ -439,6 +441,61 @@ def test_server_smallest_last_instance(isg):
     srv.close()
     assert out is not None
     assert_same(out[1], oracle.anneal(c, 32, betas, 9, colour=col))
+
+
+@pytest.mark.parametrize("kind", ["torus", "graph_msc", "csr", "plain"])
+def test_replica_shards_equal_one_solve(isg, kind):
+    """A replica-sharded solve (the multi-GPU partition by replica word): calls
+    at first_replica 0 and R (R a multiple of 32), concatenated, equal one call
+    of 2R replicas bit for bit, and the second shard equals the oracle's
+    replicas [R, 2R).  A first_replica that is not a multiple of 32 is EINVAL."""
+    R, S, seed = 64, 60, 17
+    if kind == "torus" or kind == "plain":
+        inst = I.torus(12, 10, 3)
+        kernel = {"torus": 1, "plain": 3}[kind]
+    elif kind == "graph_msc":
+        inst, kernel = I.random_graph(300, 450, 5), 4
+    else:
+        g = I.random_graph(240, 500, 6)
+        w = np.array([(-2, 1, 3, -1)[k % 4] for k in range(g.m)], np.int32)
+        inst, kernel = I.Graph(g.n, g.u, g.v, w), 2
+    p = isg.problem_of(inst)
+    betas = I.geometric_betas(0.2, 3.0, S)
+    whole = isg.isg_anneal(p, 2 * R, betas, seed, kernel=kernel)
+    parts = [isg.isg_anneal(p, R, betas, seed, kernel=kernel, first_replica=f) for f in (0, R)]
+    assert parts[1].stats()["first_replica"] == R
+    ws, we, wd = whole.final()
+    for k, part in enumerate(parts):
+        ps, pe, pd = part.final()
+        rows = slice(k * R, (k + 1) * R)
+        assert pd == wd
+        assert np.array_equal(ps, ws[rows]) and np.array_equal(pe, we[rows])
+        assert np.array_equal(part.best_all(), whole.best_all()[rows])
+        assert np.array_equal(part.best()[3], whole.best()[3][rows])
+    c = oracle.csr_of(inst)
+    assert_same(parts[1], oracle.anneal(c, list(range(R, 2 * R)), betas, seed), first_replica=R)
+    with pytest.raises(isg.IsgError) as e:
+        isg.isg_anneal(p, R, betas, seed, kernel=kernel, first_replica=16)
+    assert e.value.status == isg.ISG_EINVAL
+
+
+def test_replica_shard_continue_and_resume(isg):
+    """A shard keeps its replica offset through isg_anneal_continue and restarts
+    from its checkpoint with isg_anneal_resume (same first_replica)."""
+    inst = I.torus(16, 12, 9)
+    p = isg.problem_of(inst)
+    betas = I.geometric_betas(0.2, 3.0, 50)
+    R, f = 32, 96
+    whole = isg.isg_anneal(p, R, betas, 4, first_replica=f)
+    head = isg.isg_anneal(p, R, betas[:20], 4, first_replica=f)
+    spins, _, _ = head.final()
+    best = head.best_all()
+    isg.isg_anneal_continue(p, head, betas[20:])
+    back = isg.isg_anneal_resume(p, R, betas, 4, 20, spins, best, first_replica=f)
+    for r in (head, back):
+        for x, y in zip(r.final(), whole.final()):
+            assert np.array_equal(x, y)
+        assert np.array_equal(r.best_all(), whole.best_all())
 
 
 def test_server_rejects_bad_requests_and_times_out(isg):

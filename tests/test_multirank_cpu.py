@@ -1,6 +1,7 @@
 """Multi-process path of bench.py on CPU (gloo, world size 2): every rank anneals
-its own seed of the same workload (weak scaling, no data exchange), the job time
-is the maximum over ranks and the work is the sum over ranks."""
+its own replica range of the same solve (same seed; weak scaling, no data
+exchange), the job time is the maximum over ranks, the work is the sum over
+ranks, and the final argmin over (best energy, global replica) is gathered."""
 import os
 import socket
 import sys
@@ -28,13 +29,18 @@ def _rank_main(rank, world, port, out_dir):
     w, r, local, dist = bench.dist_setup(A())
     assert (w, r) == (world, rank)
     cpu = torch.device("cpu")
-    sv, name = bench.workload("torus", rank, sweeps=10)
+    sv, name, first = bench.workload("torus", rank, sweeps=10)
     t = 1.0 + 2.0 * rank                      # rank 1 is the slow one
     tmax = bench.max_over_ranks(t, dist, cpu)
     total = bench.sum_over_ranks(float(sv.attempts), dist, cpu)
+    # argmin gather: rank 1 strictly better; then a tie in energy, which goes to
+    # the lower global replica (rank 0's, although its local index is higher)
+    best = bench.global_best(-100 - rank, 7, first, dist, cpu)
+    tie = bench.global_best(-50, 9 if rank == 0 else 2, first, dist, cpu)
     bench.barrier(dist)
     with open(os.path.join(out_dir, f"rank{rank}.txt"), "w") as f:
-        f.write(f"{tmax} {total} {sv.seed} {name}\n")
+        f.write(f"{tmax} {total} {sv.seed} {name} {first} {best[0]} {best[1]} {tie[0]} "
+                f"{tie[1]}\n")
     dist.destroy_process_group()
 
 
@@ -44,11 +50,14 @@ def test_two_rank_weak_scaling_aggregation(tmp_path):
     mp.start_processes(_rank_main, args=(2, port, str(tmp_path)), nprocs=2, join=True,
                        start_method="spawn")
     rows = [open(tmp_path / f"rank{r}.txt").read().split() for r in range(2)]
-    for tmax, total, seed, name in rows:
+    for tmax, total, seed, name, first, be, br, te, tr in rows:
         assert float(tmax) == 3.0
         assert float(total) == 2 * 1024 * 8000 * 10
-    assert rows[0][2] != rows[1][2]          # ranks anneal different seeds
+        assert (int(be), int(br)) == (-101, 1024 + 7)      # rank 1's replica 7
+        assert (int(te), int(tr)) == (-50, 9)              # tie: rank 0's replica 9 < 1026
+    assert rows[0][2] == rows[1][2]          # one solve: the same seed
     assert rows[0][3] == rows[1][3]          # of the same workload
+    assert (int(rows[0][4]), int(rows[1][4])) == (0, 1024)   # replica ranges [0,1024), [1024,2048)
 
 
 def test_reference_arm_under_torchrun_prints_one_line():
