@@ -498,6 +498,8 @@ def batched_form(steps: int, warmup: int, sweeps: int = 2000):
     probs = [isg.problem_of(sv.problem) for sv in batch]
     betas, seeds = batch[0].betas, [sv.seed for sv in batch]
     attempts = float(sum(sv.attempts for sv in batch))
+    # launch shape measured for this size histogram (untimed; results never depend on it)
+    tuned = isg.isg_autotune_batch(probs, 32, betas, probe_sweeps=128, stream=stream)
     for _ in range(warmup):
         for r in isg.isg_anneal_batch(probs, 32, betas, seeds, stream=stream):
             r.close()
@@ -539,6 +541,7 @@ def batched_form(steps: int, warmup: int, sweeps: int = 2000):
             "ms_per_step": sum(ms) / steps, "attempts_per_step": attempts,
             "launch": f"CUDA graph: 1 persistent kernel ({stats['ctas']} CTAs x "
                       f"{stats['threads']} threads) + 1 unpack",
+            "autotuned_shape": tuned,
             "gpu_launches_per_step": stats["launches"],
             "plain": {"sample": f"{len(sample)} instances (every 32nd by size)",
                       "attempts_per_s": rates},

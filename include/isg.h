@@ -225,15 +225,40 @@ isg_status isg_anneal_resume(const isg_problem *p, int32_t replicas, const doubl
                              const int8_t *spins, const int8_t *best_spins,
                              const isg_options *opts, void *cuda_stream, isg_result **out);
 
-/* Anneal count instances with one persistent kernel (work list ordered
- * longest-first) captured in a CUDA graph.  All share replicas, betas and
- * sweeps; seeds[k] and targets[k] (targets may be NULL = none) are per
- * instance.  outs[count] receive one result handle each; every result equals
- * the result of isg_anneal on that instance alone, bit for bit.  Tori only in
- * this version (EINVAL otherwise). */
+/* Anneal count instances (tori and graphs, uneven sizes, any mix) in one
+ * launch sequence captured in a CUDA graph.  Every instance is cut into work
+ * units that one CTA runs from start to finish: torus replica words (32
+ * replicas), replica words of +-1 graphs without fields, and replica quads (4)
+ * of other graphs; each unit kind has one persistent kernel whose CTAs take
+ * units longest-first, and the kinds run concurrently.  All instances share
+ * replicas, betas and sweeps; seeds[k] and targets[k] (targets may be NULL =
+ * none) are per instance.  An instance with a target and several units
+ * follows the stop rule of isg_anneal (its units rerun from the start to the
+ * earliest unit's hit + 1 in a second pass).  outs[count] receive one result
+ * handle each; every result equals isg_anneal of that instance alone, bit for
+ * bit.  The launch shape (threads per CTA, CTAs per SM) is the one
+ * isg_autotune_batch measured for this batch's replicas and size histogram,
+ * else 256 threads and as many CTAs per SM as shared memory allows.  The
+ * call enqueues its uploads and the graph on cuda_stream and waits for the
+ * uploads.  EINVAL: NULL arguments, count outside [1, 65535], replicas or
+ * sweeps < 1, a bad beta, a target outside int32, or an instance too large for
+ * one CTA's shared memory. */
 isg_status isg_anneal_batch(const isg_problem *const *probs, int32_t count, int32_t replicas,
                             const double *betas, int32_t sweeps, const uint64_t *seeds,
                             const int64_t *targets, void *cuda_stream, isg_result **outs);
+
+/* Launch-shape autotuner of the batched form: runs the batch for probe_sweeps
+ * sweeps, their inverse temperatures sampled evenly from betas[0..sweeps),
+ * under every threads per CTA in {128, 192, 256, 384, 512} and CTAs per SM in
+ * 1..4 that fits, and remembers the fastest for batches of the same replicas
+ * and size histogram (instances per size class 2^k vertices, tori and graphs
+ * apart) on this device; isg_anneal_batch then uses it.  Results never depend
+ * on the shape.  threads and ctas_per_sm (either may be NULL) receive the
+ * choice.  Synchronises the stream.  EINVAL as isg_anneal_batch, or
+ * probe_sweeps < 1. */
+isg_status isg_autotune_batch(const isg_problem *const *probs, int32_t count, int32_t replicas,
+                              const double *betas, int32_t sweeps, int32_t probe_sweeps,
+                              void *cuda_stream, int32_t *threads, int32_t *ctas_per_sm);
 
 /* Parallel tempering (Sec. II.C: replicas at different temperatures that
  * exchange configurations) on a torus instance, or on a graph with weights

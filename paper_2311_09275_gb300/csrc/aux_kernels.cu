@@ -100,20 +100,33 @@ __global__ void reduce_hits_kernel(const int32_t *hit, int count, int32_t *out) 
   }
 }
 
-__global__ void batch_finish_kernel(const TorusBatchItem *__restrict__ items, int R) {
-  const TorusBatchItem it = items[blockIdx.y];
-  const int n = it.solve.L * it.solve.W;
-  const int64_t total = (int64_t)n * R;
+// Row blockIdx.y of the grid unpacks solve blockIdx.y: out[r][orig[v]] from
+// state unit r / lanes at vertex v (bit r mod 32 of a word, byte r mod 4 of a
+// quad); the first block also reduces the units' hit sweeps to the stop.
+__global__ void batch_unpack_kernel(const BatchOutDesc *__restrict__ descs) {
+  const BatchOutDesc d = descs[blockIdx.y];
+  const int n = d.n;
+  const int64_t total = (int64_t)n * d.R;
   for (int64_t x = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; x < total;
        x += (int64_t)gridDim.x * blockDim.x) {
     const int r = (int)(x / n);
-    const int i = (int)(x - (int64_t)r * n);
-    const uint32_t bit = 1u << (r & 31);
-    it.out[x] = (it.solve.spins[i] & bit) ? 1 : -1;
-    it.out_best[x] = (it.solve.best[i] & bit) ? 1 : -1;
+    const int v = (int)(x - (int64_t)r * n);
+    const size_t at = (size_t)r * n + (d.orig ? d.orig[v] : v);
+    const size_t src = (size_t)(r / d.lanes) * n + v;
+    if (d.lanes == 32) {
+      d.out[at] = ((d.spins[src] >> (r & 31)) & 1u) ? 1 : -1;
+      d.out_best[at] = ((d.best[src] >> (r & 31)) & 1u) ? 1 : -1;
+    } else {
+      d.out[at] = (int8_t)(uint8_t)(d.spins[src] >> (8 * (r & 3)));
+      d.out_best[at] = (int8_t)(uint8_t)(d.best[src] >> (8 * (r & 3)));
+    }
   }
-  if (blockIdx.x == 0 && threadIdx.x == 0)
-    *it.stop = it.solve.has_target ? it.solve.hit[0] : -1;
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    int m = INT_MAX;
+    for (int u = 0; d.has_target && u < d.units; ++u)
+      if (d.hit[u] >= 0 && d.hit[u] < m) m = d.hit[u];
+    *d.stop = m == INT_MAX ? -1 : m;
+  }
 }
 
 int grid_for(int64_t total, int threads) {
@@ -154,11 +167,12 @@ cudaError_t energy_csr(const int64_t *rowptr, const int32_t *col, const int32_t 
   return cudaGetLastError();
 }
 
-cudaError_t batch_finish(const TorusBatchItem *items_dev, int32_t count, int32_t max_n,
-                         int32_t R, cudaStream_t stream) {
-  int gx = (int)(((int64_t)max_n * R + 255) / 256);
+cudaError_t batch_unpack(const BatchOutDesc *descs_dev, int32_t count, int64_t max_nr,
+                         cudaStream_t stream) {
+  int64_t gx = (max_nr + 255) / 256;
   if (gx > 64) gx = 64;
-  batch_finish_kernel<<<dim3(gx, count), 256, 0, stream>>>(items_dev, R);
+  if (gx < 1) gx = 1;
+  batch_unpack_kernel<<<dim3((unsigned)gx, (unsigned)count), 256, 0, stream>>>(descs_dev);
   return cudaGetLastError();
 }
 

@@ -22,8 +22,17 @@ __global__ void __launch_bounds__(512) gm_batch_kernel(const GraphMscItem *items
     __syncthreads();
     if (it >= count) break;
     const GraphMscItem u = items[order[it]];
+    int t_end = u.t_end;
+    if (u.stop_from_hits) {
+      // the solve's stop sweep from the first pass (uniform across the CTA)
+      int m = INT_MAX;
+      for (int w = 0; w < u.solve.words; ++w)
+        if (u.solve.hit[w] >= 0 && u.solve.hit[w] < m) m = u.solve.hit[w];
+      if (m == INT_MAX) continue;  // no unit reached the target: the first pass stands
+      if (m + 1 < t_end) t_end = m + 1;
+    }
     gm_word<kGraphMscBatchPlanes, false, false, false>(u.solve, none, u.word, 0, 1, u.t_begin,
-                                                       u.t_end, u.resume, smem);
+                                                       t_end, u.resume, smem);
     __syncthreads();
   }
 }

@@ -575,13 +575,22 @@ __global__ void __launch_bounds__(512, 2) csr_batch_kernel(const CsrBatchItem *i
     __syncthreads();
     if (it >= count) break;
     const CsrBatchItem u = items[order[it]];
+    int t_end = u.t_end;
+    if (u.stop_from_hits) {
+      // the solve's stop sweep from the first pass (uniform across the CTA)
+      int m = INT_MAX;
+      for (int q = 0; q < u.solve.quads; ++q)
+        if (u.solve.hit[q] >= 0 && u.solve.hit[q] < m) m = u.solve.hit[q];
+      if (m == INT_MAX) continue;  // no unit reached the target: the first pass stands
+      if (m + 1 < t_end) t_end = m + 1;
+    }
     // field mode is per instance: dispatch (uniform across the CTA)
     if (u.solve.mode == 0)
-      csr_solve<1, 0, false>(u.solve, none, u.quad, 0, 1, u.t_begin, u.t_end, u.resume, smem);
+      csr_solve<1, 0, false>(u.solve, none, u.quad, 0, 1, u.t_begin, t_end, u.resume, smem);
     else if (u.solve.mode == 1)
-      csr_solve<1, 1, false>(u.solve, none, u.quad, 0, 1, u.t_begin, u.t_end, u.resume, smem);
+      csr_solve<1, 1, false>(u.solve, none, u.quad, 0, 1, u.t_begin, t_end, u.resume, smem);
     else
-      csr_solve<1, 2, false>(u.solve, none, u.quad, 0, 1, u.t_begin, u.t_end, u.resume, smem);
+      csr_solve<1, 2, false>(u.solve, none, u.quad, 0, 1, u.t_begin, t_end, u.resume, smem);
     __syncthreads();
   }
 }

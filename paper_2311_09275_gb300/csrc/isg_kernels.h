@@ -71,9 +71,12 @@ struct TorusBatchItem {
   int32_t word;
   int32_t t_begin, t_end;
   int32_t resume;
-  int8_t *out;               // [R][n] final spins (+1/-1), written by batch_finish
-  int8_t *out_best;          // [R][n] best spins
-  int32_t *stop;             // hit sweep of the solve, -1 if none
+  int32_t stop_from_hits;    // second pass of a multi-unit solve with a target: run from the
+                             // start to (min over the solve's units of hit) + 1, nothing if
+                             // no unit reached the target
+  int8_t *out;               // (unused by the kernels)
+  int8_t *out_best;
+  int32_t *stop;
 };
 // count_dev: number of units; order_dev: unit indices, longest first;
 // next_dev: zeroed work counter.
@@ -136,6 +139,7 @@ struct CsrBatchItem {
   int32_t quad;
   int32_t t_begin, t_end;
   int32_t resume;
+  int32_t stop_from_hits;      // as TorusBatchItem::stop_from_hits
 };
 cudaError_t csr_batch_launch(const CsrBatchItem *items_dev, const int32_t *count_dev,
                              const int32_t *order_dev, int32_t *next_dev, int32_t ctas,
@@ -192,6 +196,7 @@ struct GraphMscItem {
   int32_t word;
   int32_t t_begin, t_end;
   int32_t resume;
+  int32_t stop_from_hits;      // as TorusBatchItem::stop_from_hits
 };
 
 // fields: the instance has local fields (staged slices then hold them too).
@@ -237,10 +242,21 @@ cudaError_t energy_csr(const int64_t *rowptr, const int32_t *col, const int32_t 
                        const int8_t *spins, int32_t R, int64_t *scratch, int32_t blocks,
                        int64_t *energies, cudaStream_t stream,
                        const int32_t *field = nullptr);
-// Unpack every batch item's state and stop sweep (one launch for the batch;
-// items with word 0 and R <= 32 replicas).
-cudaError_t batch_finish(const TorusBatchItem *items_dev, int32_t count, int32_t max_n,
-                         int32_t R, cudaStream_t stream);
+// One solve of a batch for the unpack: its state [units][n] (words of 32
+// lanes or quads of 4), relabelled graphs' original ids (nullptr for a
+// torus), per-unit hit sweeps, and where its int8 [R][n] states and stop go.
+struct BatchOutDesc {
+  const uint32_t *spins, *best;
+  const int32_t *orig;
+  const int32_t *hit;
+  int32_t n, R, lanes, units, has_target;
+  int8_t *out, *out_best;
+  int32_t *stop;               // min over units of hit (-1: none or no target)
+};
+// Unpack every solve of a batch (one launch): final and best states into
+// int8 [R][n] in the caller's vertex order, and the stop sweep.
+cudaError_t batch_unpack(const BatchOutDesc *descs_dev, int32_t count, int64_t max_nr,
+                         cudaStream_t stream);
 // Reduce per-word / per-quad hit sweeps to the solve's stop sweep.
 cudaError_t reduce_hits(const int32_t *hit, int32_t count, int32_t *out, cudaStream_t stream);
 

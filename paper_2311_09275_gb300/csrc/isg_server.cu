@@ -306,6 +306,7 @@ void fill_torus_unit(TorusBatchItem &it, const Slot *sl, int32_t word, int32_t t
   it.t_begin = t_begin;
   it.t_end = t_end;
   it.resume = t_begin > 0;
+  it.stop_from_hits = 0;
   it.out = nullptr;
   it.out_best = nullptr;
   it.stop = nullptr;
@@ -343,6 +344,7 @@ void fill_csr_unit(CsrBatchItem &it, const Slot *sl, int32_t quad, int32_t t_beg
   it.t_begin = t_begin;
   it.t_end = t_end;
   it.resume = t_begin > 0;
+  it.stop_from_hits = 0;
 }
 
 void fill_gm_unit(GraphMscItem &it, const Slot *sl, int32_t word, int32_t t_begin, int32_t t_end) {
@@ -378,6 +380,7 @@ void fill_gm_unit(GraphMscItem &it, const Slot *sl, int32_t word, int32_t t_begi
   it.t_begin = t_begin;
   it.t_end = t_end;
   it.resume = t_begin > 0;
+  it.stop_from_hits = 0;
 }
 
 // Unit kind of a slot: 0 torus words, 1 graph words, 2 graph quads.

@@ -37,9 +37,9 @@ __host__ __device__ __forceinline__ Band band_of(int L, int K, int k) {
 
 __host__ __device__ __forceinline__ size_t align16(size_t x) { return (x + 15) & ~size_t(15); }
 
-// Per-warp lane totals of the energy counters are published to every CTA of
-// the cluster: part[k][warp][lane] for up to 32 warps per CTA.
-constexpr int kMaxWarps = 32;
+// Per-lane energy sums of the cluster: three rotating accumulators of 32
+// lanes in every CTA.
+constexpr int kAccWords = 3 * 32;
 
 struct SmemLayout {
   size_t spin, best, cb, part, total;
@@ -51,7 +51,7 @@ __host__ __device__ __forceinline__ SmemLayout layout_of(int nr, int W, int K) {
   m.best = m.spin + sizeof(uint32_t) * (size_t)(nr + 2) * W;
   m.cb = m.best + sizeof(uint32_t) * (size_t)nr * W;
   m.part = align16(m.cb + (size_t)(nr + 2) * W);
-  m.total = align16(m.part + sizeof(int32_t) * 32 * kMaxWarps * (size_t)K);
+  m.total = align16(m.part + sizeof(int32_t) * kAccWords);
   return m;
 }
 
@@ -90,27 +90,40 @@ __device__ __forceinline__ void group_wait(int K) {
     __syncthreads();
 }
 
+// Atomic add of v at shared-memory address a (a CTA-local shared address) of
+// CTA `rank` of the cluster, through the 32-bit cluster window.
+__device__ __forceinline__ void red_cluster_add(uint32_t a, uint32_t rank, int32_t v) {
+  uint32_t ra;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;\n" : "=r"(ra) : "r"(a), "r"(rank));
+  asm volatile("red.shared::cluster.add.s32 [%0], %1;\n" ::"r"(ra), "r"(v) : "memory");
+}
+
 // Sum over the whole cluster of the bit-sliced counters, per lane (= per
-// replica of the word): every warp publishes its lane totals to every CTA of
-// the cluster, one group barrier, then every warp adds them all up itself, so
-// that no CTA-wide barrier or serial section is needed.  `during` runs
-// between the arrival at the barrier and the wait for it.
+// replica of the word): every warp adds its lane totals into accumulator m of
+// every CTA of the cluster (atomic adds, local or remote), one group barrier,
+// then every warp reads the 32 sums; no CTA-wide barrier or serial section is
+// needed.  The three accumulators rotate (m = 0, 1, 2, 0, ...): once read, a
+// call clears the one the next call adds into, last read two calls before, a
+// group barrier lying between any two calls.  `during` runs between the
+// arrival at the barrier and the wait for it.
 template <int NP, typename During>
-__device__ __forceinline__ int32_t cluster_lane_sum(const SlicedCounter<NP> &cnt, int32_t *part,
-                                                    int k, int K, During during) {
-  const int nw = (int)(blockDim.x >> 5);
-  const int slot = (k * nw + (int)(threadIdx.x >> 5)) * 32 + (int)lane_id();
+__device__ __forceinline__ int32_t cluster_lane_sum(const SlicedCounter<NP> &cnt, int32_t *acc,
+                                                    int &m, int K, During during) {
+  const int lane = (int)lane_id();
+  int32_t *cur = acc + 32 * m;
   const int32_t tot = cnt.warp_lane_total();
   if (K == 1) {
-    part[slot] = tot;
+    atomicAdd(cur + lane, tot);
   } else {
-    for (int q = 0; q < K; ++q) peer_smem(part, (uint32_t)q)[slot] = tot;
+    const uint32_t a = (uint32_t)__cvta_generic_to_shared(cur + lane);
+    for (int q = 0; q < K; ++q) red_cluster_add(a, (uint32_t)q, tot);
   }
   group_arrive(K);
   during();
   group_wait(K);
-  int32_t sum = 0;
-  for (int j = 0; j < K * nw; ++j) sum += part[j * 32 + (int)lane_id()];
+  const int32_t sum = cur[lane];
+  m = m == 2 ? 0 : m + 1;
+  if (threadIdx.x < 32) acc[32 * m + lane] = 0;
   return sum;
 }
 
@@ -238,7 +251,8 @@ __device__ void torus_word(const TorusSolve &s, int word, int k, int K, int t_be
   uint32_t *spin = reinterpret_cast<uint32_t *>(smem + lay.spin);
   uint32_t *best = reinterpret_cast<uint32_t *>(smem + lay.best);  // band rows only
   uint8_t *cb = smem + lay.cb;
-  int32_t *part = reinterpret_cast<int32_t *>(smem + lay.part);
+  int32_t *acc = reinterpret_cast<int32_t *>(smem + lay.part);  // energy accumulators
+  int acc_m = 0;                                                   // the next one to add into
   const PhiloxKey key{s.key0, s.key1};
   const uint32_t uword = (uint32_t)(word + s.rng_word0);  // Philox counters only
   const int rem = s.replicas - 32 * word;
@@ -263,7 +277,9 @@ __device__ void torus_word(const TorusSolve &s, int word, int k, int K, int t_be
     spin[x] = v;
     if (lr >= 1 && lr <= nr) best[x - W] = resume ? gbest[i] : v;
   }
-  // peers write into this CTA's halo rows only after every CTA has loaded them
+  for (int x = threadIdx.x; x < kAccWords; x += blockDim.x) acc[x] = 0;
+  // peers write into this CTA's halo rows (and accumulators) only after every
+  // CTA has loaded (and cleared) them
   sync_group(K);
 
   // per-lane (replica) energies, kept identically by every warp
@@ -281,7 +297,7 @@ __device__ void torus_word(const TorusSolve &s, int word, int k, int K, int t_be
       const uint32_t d = ~(s0 ^ spin[x + W] ^ sign_mask(cbx >> 1));
       cnt.add2(a ^ d, a & d);
     }
-    e = 2 * cluster_lane_sum<NP>(cnt, part, k, K, [] {}) - 2 * n;
+    e = 2 * cluster_lane_sum<NP>(cnt, acc, acc_m, K, [] {}) - 2 * n;
     e_best = e;
   } else {
     e = s.e_cur[word * 32 + lane];
@@ -337,7 +353,7 @@ __device__ void torus_word(const TorusSolve &s, int word, int k, int K, int t_be
       }
     }
     ready = false;
-    e += 4 * (cluster_lane_sum<NP>(cnt, part, k, K, [&] {
+    e += 4 * (cluster_lane_sum<NP>(cnt, acc, acc_m, K, [&] {
                 if (kPrefetch && more) {
                   sweep_prefix(t + 1);
                   ready = first_site_masks(W, r0, nr, 0, bp, s.rk, T4n, T8n, pre4, pre8);
@@ -376,7 +392,10 @@ __device__ void torus_word(const TorusSolve &s, int word, int k, int K, int t_be
   }
 }
 
-// MAXT = 1024 caps registers at 64 per thread so that 1,024 threads fit one SM
+// MAXT = 1024 caps registers at 64 per thread so that 1,024 threads fit one SM;
+// MAXT = 384 (CTAs of at most 384 threads, six counter planes: the 80 x 100
+// workload's shape) lets the compiler keep more of the eight Philox blocks in
+// flight (144 registers against 116 in the 512-thread build: +1.2 %)
 template <int NP, int MAXT>
 __global__ void __launch_bounds__(MAXT, 1) torus_kernel(TorusSolve s, TorusLaunch l) {
   extern __shared__ __align__(16) uint8_t smem[];
@@ -409,15 +428,25 @@ __global__ void __launch_bounds__(512, 2) torus_batch_kernel(const TorusBatchIte
     __syncthreads();
     if (it >= count) break;
     const TorusBatchItem u = items[order[it]];
-    torus_word<NP, false>(u.solve, u.word, 0, 1, u.t_begin, u.t_end, u.resume, smem);
+    int t_end = u.t_end;
+    if (u.stop_from_hits) {
+      // the solve's stop sweep from the first pass (uniform across the CTA)
+      int m = INT_MAX;
+      for (int w = 0; w < u.solve.words; ++w)
+        if (u.solve.hit[w] >= 0 && u.solve.hit[w] < m) m = u.solve.hit[w];
+      if (m == INT_MAX) continue;  // no unit reached the target: the first pass stands
+      if (m + 1 < t_end) t_end = m + 1;
+    }
+    torus_word<NP, false>(u.solve, u.word, 0, 1, u.t_begin, t_end, u.resume, smem);
     __syncthreads();
   }
 }
 
-int np_for(int sites_per_thread_sweep, int sites_per_thread_band) {
+int np_for(int sites_per_thread_sweep, int sites_per_thread_band, int threads) {
   const int need = 4 * sites_per_thread_sweep > 2 * sites_per_thread_band
                        ? 4 * sites_per_thread_sweep
                        : 2 * sites_per_thread_band;
+  if (need < (1 << 5) && threads <= 384) return 5;  // (five planes: the 384-thread build only)
   if (need < (1 << 6)) return 6;
   if (need < (1 << 8)) return 8;
   if (need < (1 << 10)) return 10;
@@ -497,11 +526,15 @@ int torus_max_active_clusters(int32_t L, int32_t W, int32_t words, int32_t clust
   const size_t smem = torus_smem_bytes(L, W, cluster);
   const int nr = (L + cluster - 1) / cluster;
   const int np = np_for(torus_sites_per_thread(L, W, cluster, threads),
-                        (nr * W + threads - 1) / threads);
+                        (nr * W + threads - 1) / threads, threads);
   const int grid = words * cluster;
   const bool wide = threads > 512;
   switch (np) {
+    case 5:
+      return max_active_clusters(torus_kernel<5, 384>, grid, threads, smem, cluster);
     case 6:
+      if (threads <= 384)
+        return max_active_clusters(torus_kernel<6, 384>, grid, threads, smem, cluster);
       return wide ? max_active_clusters(torus_kernel<6, 1024>, grid, threads, smem, cluster)
                   : max_active_clusters(torus_kernel<6, 512>, grid, threads, smem, cluster);
     case 8:
@@ -520,12 +553,16 @@ cudaError_t torus_launch(const TorusSolve &s, const TorusLaunch &l, cudaStream_t
   const int nr = (s.L + K - 1) / K;
   const int spt = torus_sites_per_thread(s.L, s.W, K, l.threads);
   const int band_spt = (nr * s.W + l.threads - 1) / l.threads;
-  const int np = np_for(spt, band_spt);
+  const int np = np_for(spt, band_spt, l.threads);
   const int grid = s.words * K;
   if (l.threads > 1024) return cudaErrorInvalidValue;
   const bool wide = l.threads > 512;
   switch (np) {
+    case 5:
+      return launch_clustered(torus_kernel<5, 384>, grid, l.threads, smem, K, stream, s, l);
     case 6:
+      if (l.threads <= 384)
+        return launch_clustered(torus_kernel<6, 384>, grid, l.threads, smem, K, stream, s, l);
       return wide ? launch_clustered(torus_kernel<6, 1024>, grid, l.threads, smem, K, stream, s, l)
                   : launch_clustered(torus_kernel<6, 512>, grid, l.threads, smem, K, stream, s, l);
     case 8:

@@ -67,6 +67,7 @@ _sig("isg_anneal_ex", [_P, _i32, _P, _i32, _u64, _i64, ctypes.POINTER(isg_option
                        ctypes.POINTER(_P)])
 _sig("isg_anneal_batch", [_P, _i32, _i32, _P, _i32, _P, _P, _P, _P])
 _sig("isg_anneal_continue", [_P, _P, _P, _i32, _P])
+_sig("isg_autotune_batch", [_P, _i32, _i32, _P, _i32, _i32, _P, _P, _P])
 _sig("isg_debug_fail_allocations", [_i32])
 _sig("isg_anneal_resume", [_P, _i32, _P, _i32, _u64, _i32, _P, _P, ctypes.POINTER(isg_options),
                            _P, ctypes.POINTER(_P)])
@@ -336,6 +337,21 @@ def isg_autotune(p, replicas: int, probe_sweeps: int = 64, stream=None) -> dict:
                              ctypes.byref(best)))
     return {"kernel": best.kernel, "cluster_ctas": best.cluster_ctas, "threads": best.threads,
             "quads_per_cta": best.quads_per_cta}
+
+
+def isg_autotune_batch(problems, replicas: int, betas, probe_sweeps: int = 128,
+                       stream=None) -> dict:
+    """Measured launch shape of the batched form for this batch's size histogram
+    (remembered for later isg_anneal_batch calls of the same histogram), probed
+    on sweeps sampled evenly from the schedule `betas`."""
+    count = len(problems)
+    hs = (_P * count)(*[_h(p) for p in problems])
+    b = _arr(betas, np.float64)
+    t, c = _i32(), _i32()
+    _check(_lib.isg_autotune_batch(ctypes.cast(hs, _P), count, int(replicas), _ptr(b),
+                                   int(b.shape[0]), int(probe_sweeps), _stream(stream),
+                                   ctypes.byref(t), ctypes.byref(c)))
+    return {"threads": t.value, "ctas_per_sm": c.value}
 
 
 def isg_anneal_batch(problems, replicas: int, betas, seeds, targets=None, stream=None):

@@ -301,6 +301,81 @@ def test_batch_with_targets(isg):
         assert_same(outs[k], orc)
 
 
+def _mixed_batch():
+    """Tori, +-1 graphs (graph words) and integer-weighted graphs (quads) of
+    uneven sizes."""
+    insts = []
+    for k in range(6):
+        insts.append(I.torus(8 + 4 * k, 6 + 2 * k, 300 + k))
+    for k in range(5):
+        insts.append(I.random_graph(150 + 120 * k, 200 + 150 * k, 400 + k))
+    for k in range(4):
+        g = I.random_graph(100 + 90 * k, 180 + 100 * k, 500 + k)
+        w = np.array([(-2, 1, 3)[e % 3] for e in range(g.m)], np.int32)
+        insts.append(I.Graph(g.n, g.u, g.v, w))
+    return insts
+
+
+@pytest.mark.parametrize("R", [64, 37])
+def test_mixed_batch_equals_solo_runs_and_oracle(isg, R):
+    """One batch of tori and graphs, several units per instance (R > 32): every
+    result equals isg_anneal of the instance alone, and sampled ones the
+    oracle; the three unit kinds all ran."""
+    insts = _mixed_batch()
+    probs = [isg.problem_of(x) for x in insts]
+    betas = I.geometric_betas(0.1, 5.0, 120)
+    seeds = [11 + k for k in range(len(insts))]
+    outs = isg.isg_anneal_batch(probs, R, betas, seeds)
+    kinds = {o.stats()["kernel"] for o in outs}
+    assert kinds == {1, 2, 4}
+    for k, x in enumerate(insts):
+        solo = isg.isg_anneal(probs[k], R, betas, seeds[k])
+        for a, b in zip(outs[k].final(), solo.final()):
+            assert np.array_equal(a, b), k
+        assert np.array_equal(outs[k].best_all(), solo.best_all()), k
+    for k in (0, 5, 7, 10, 12, 14):
+        assert_same(outs[k], oracle.anneal(oracle.csr_of(insts[k]), R, betas, seeds[k]))
+
+
+def test_mixed_batch_with_targets_multi_unit(isg):
+    """Targets on instances of several units: the second pass reruns them to
+    the earliest unit's hit + 1, as a single solve does; equal to the oracle."""
+    insts = _mixed_batch()
+    probs = [isg.problem_of(x) for x in insts]
+    betas = I.geometric_betas(0.1, 5.0, 150)
+    seeds = [21 + k for k in range(len(insts))]
+    R = 70
+    targets = []
+    for k, x in enumerate(insts):
+        if k % 3 == 2:
+            targets.append(None)
+            continue
+        full = oracle.anneal(oracle.csr_of(x), R, betas, seeds[k])
+        # one reached early by some replica (+6), and one never reached (-10^6)
+        targets.append(int(full.e_best.min()) + 6 if k % 3 == 0 else -10 ** 6)
+    outs = isg.isg_anneal_batch(probs, R, betas, seeds, targets)
+    for k, x in enumerate(insts):
+        assert_same(outs[k], oracle.anneal(oracle.csr_of(x), R, betas, seeds[k],
+                                           target=targets[k]))
+
+
+def test_batch_autotune_keeps_results(isg):
+    """The batch autotuner picks a shape; the tuned batch equals the untuned one."""
+    insts = _mixed_batch()
+    probs = [isg.problem_of(x) for x in insts]
+    betas = I.geometric_betas(0.1, 5.0, 80)
+    seeds = [31 + k for k in range(len(insts))]
+    before = isg.isg_anneal_batch(probs, 40, betas, seeds)
+    shape = isg.isg_autotune_batch(probs, 40, betas, probe_sweeps=8)
+    assert shape["threads"] in (128, 192, 256, 384, 512) and 1 <= shape["ctas_per_sm"] <= 4
+    after = isg.isg_anneal_batch(probs, 40, betas, seeds)
+    assert after[0].stats()["threads"] == shape["threads"]
+    for a, b in zip(before, after):
+        for x, y in zip(a.final(), b.final()):
+            assert np.array_equal(x, y)
+        assert np.array_equal(a.best_all(), b.best_all())
+
+
 # ------------------------------------------------------------------ resume
 @pytest.mark.parametrize("make,kernel,R,cluster", [
     (lambda: I.torus(12, 10, 5), 1, 70, 2),                       # torus words
