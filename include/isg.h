@@ -283,13 +283,16 @@ isg_status isg_autotune_batch(const isg_problem *const *probs, int32_t count, in
  * in vertex order (D their number, u = word 0 of Philox(seed, (k, round, m,
  * 3))) seeds the cluster, its connected component among the differing sites,
  * which both chains flip (exchanging their spins there, so E_a + E_b is
- * unchanged); the chains' energies are then recomputed.  The result is read
+ * unchanged); the chains' energies are then recomputed.  On a graph the
+ * subgraph's edges are the instance's edges and the vertex order is the
+ * caller's.  The result is read
  * like isg_anneal's (R = 32 K, S = rounds * sweeps_per_round); exchange counts
  * by isg_result_exchanges, cluster sizes by isg_result_cluster_flips.  opts
  * may be NULL (kernel AUTO or TORUS_MSC; cluster/threads as isg_anneal).
  * EINVAL: neither a torus nor such a graph, K outside [1, 4096], rounds or
  * sweeps_per_round < 1, a bad beta, icm_slots outside [0, K], icm_slots > 0 on
- * a graph (cluster moves: tori only) or with n > 28,544. */
+ * a torus with n > 28,544 or on a graph with n > 19,029 (the sites' difference
+ * and cluster bits in shared memory). */
 isg_status isg_parallel_tempering(const isg_problem *p, int32_t temperatures,
                                   const double *betas, int32_t rounds, int32_t sweeps_per_round,
                                   int32_t icm_slots, uint64_t seed, const isg_options *opts,

@@ -234,6 +234,15 @@ cudaError_t pt_exchange(uint32_t *spins, int32_t *e_cur, int32_t n, int32_t K, i
 // Parallel tempering: one Houdayer cluster move per chain pair (lanes 2m,
 // 2m+1) on slot words k0 .. k0+slots-1 of an L x W torus state; flipped[k]
 // gains the cluster sizes.  Needs 8 L W bytes of shared memory per CTA.
+// Parallel tempering on a graph (multi-spin graph layout): one Houdayer move per
+// chain pair on slot words k0 .. k0+slots-1; needs pt_cluster_graph_smem(n)
+// bytes of shared memory per CTA (kmax: the instance's max degree + |h|).
+size_t pt_cluster_graph_smem(int32_t n);
+cudaError_t pt_cluster_graph(uint32_t *spins, int32_t *e_cur, int32_t n, const int32_t *rowptr,
+                             const int32_t *col, const int32_t *orig, const int32_t *field,
+                             int32_t kmax, int32_t k0, int32_t slots, int32_t round,
+                             uint32_t key0, uint32_t key1, unsigned long long *flipped,
+                             cudaStream_t stream);
 cudaError_t pt_cluster(uint32_t *spins, int32_t *e_cur, const uint8_t *cbits, int32_t L,
                        int32_t W, int32_t k0, int32_t slots, int32_t round, uint32_t key0,
                        uint32_t key1, unsigned long long *flipped, cudaStream_t stream);

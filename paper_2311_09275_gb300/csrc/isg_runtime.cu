@@ -1153,9 +1153,12 @@ isg_status tempering_impl(const isg_problem *p, int32_t K, const double *betas, 
   isg_status st = check_betas(betas, K);
   if (st != ISG_OK) return st;
   if (icm_slots < 0 || icm_slots > K) return fail(ISG_EINVAL, "icm_slots must be in [0, K]");
-  if (icm_slots > 0 && gm) return fail(ISG_EINVAL, "cluster moves run on torus instances");
-  if (icm_slots > 0 && 8 * (size_t)p->n > 227 * 1024 - 4096)
-    return fail(ISG_EINVAL, "cluster moves need 8 bytes of shared memory per site (n <= 28544)");
+  if (icm_slots > 0 && !gm && 8 * (size_t)p->n > 227 * 1024 - 4096)
+    return fail(ISG_EINVAL, "cluster moves on a torus need 8 bytes of shared memory per site "
+                            "(n <= 28544)");
+  if (icm_slots > 0 && gm && pt_cluster_graph_smem(p->n) > 227 * 1024 - 4096)
+    return fail(ISG_EINVAL, "cluster moves on a graph need 12 bytes of shared memory per vertex "
+                            "(n <= 19029)");
   isg_options o = {};
   if (opts) o = *opts;
   const int mkernel = gm ? ISG_KERNEL_GRAPH_MSC : ISG_KERNEL_TORUS_MSC;
@@ -1315,8 +1318,11 @@ isg_status tempering_impl(const isg_problem *p, int32_t K, const double *betas, 
         e = gm_launch(gs, l, st);
       }
       if (e == cudaSuccess && icm_slots > 0)
-        e = pt_cluster(r->d_spins, r->d_e_cur, dp->cbits, p->L, p->W, K - icm_slots, icm_slots,
-                       q, key0, key1, r->d_flipped, st);
+        e = gm ? pt_cluster_graph(r->d_spins, r->d_e_cur, p->n, dp->rowptr, dp->col, dp->orig,
+                                  dp->field_r, p->kmax, K - icm_slots, icm_slots, q, key0, key1,
+                                  r->d_flipped, st)
+               : pt_cluster(r->d_spins, r->d_e_cur, dp->cbits, p->L, p->W, K - icm_slots,
+                            icm_slots, q, key0, key1, r->d_flipped, st);
       if (e == cudaSuccess)
         e = pt_exchange(r->d_spins, r->d_e_cur, p->n, K, q % 2, q, key0, key1,
                         (const int8_t *)(pm + o_sgn), (const uint32_t *)(pm + o_x),

@@ -4,7 +4,8 @@
 // slots k and k+1 moves bit c of every site word between the two words (a
 // masked swap) and swaps the chains' energies; a cluster move flips, in both
 // chains of a pair within one word, the connected component of a drawn site
-// among the sites where they differ.
+// among the sites where they differ (on a torus by ring scans, on a graph by
+// passes over its adjacency).
 #include "isg_device.cuh"
 #include "isg_kernels.h"
 
@@ -389,7 +390,201 @@ __global__ void __launch_bounds__(1024) pt_cluster_kernel(uint32_t *spins, int32
   if (tid < 32) e_cur[32 * k + tid] = 2 * lane_tot[tid] - 2 * n;  // E = 2 U - 2n (torus)
 }
 
+// Houdayer cluster moves on graph slot words (the multi-spin graph layout:
+// vertices relabelled colour-major; col holds relabelled neighbours with bit 31
+// set for weight -1; orig maps a relabelled vertex to the caller's id), one
+// CTA per slot k0 + blockIdx.x.  As on the torus: D[v] has, at bit 2m, whether
+// pair m differs at v; the drawn site is the (u mod D)-th differing vertex in
+// the caller's vertex order; C[v] grows the connected component of the drawn
+// vertex among differing vertices, by passes over the vertices that can still
+// gain a bit, each taking the bits of its neighbours (in place, so a pass may
+// carry a bit over several edges; bits only get set, so the fixed point is the
+// component whatever the order); both chains flip C and the word's 32
+// energies are recounted over the edges (and the local fields, weights +1).
+template <int NP>
+__global__ void __launch_bounds__(1024) pt_cluster_graph_kernel(
+    uint32_t *spins, int32_t *e_cur, int n, const int32_t *rowptr, const int32_t *col,
+    const int32_t *orig, const int32_t *field, int k0, int round, PhiloxKey key,
+    unsigned long long *flipped) {
+  extern __shared__ __align__(16) uint32_t sm[];
+  const int k = k0 + (int)blockIdx.x;
+  uint32_t *D = sm, *C = sm + n;
+  int32_t *inv = reinterpret_cast<int32_t *>(sm + 2 * n);  // caller's id -> relabelled
+  __shared__ int32_t wsum[32][16];
+  __shared__ int64_t pick[16];
+  __shared__ int changed;
+  uint32_t *word = spins + (size_t)k * n;
+  const int nt = (int)blockDim.x, tid = (int)threadIdx.x;
+  const int lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
+  for (int v = tid; v < n; v += nt) {
+    const uint32_t w = word[v];
+    D[v] = (w ^ (w >> 1)) & 0x55555555u;
+    C[v] = 0u;
+    inv[orig[v]] = v;
+  }
+  __syncthreads();
+  // 1. differing vertices per pair, counted over this thread's chunk of the
+  //    caller's ids
+  const int chunk = (n + nt - 1) / nt;
+  const int i0 = min(n, tid * chunk), i1 = min(n, i0 + chunk);
+  int32_t cnt[16];
+#pragma unroll
+  for (int m = 0; m < 16; ++m) cnt[m] = 0;
+  for (int i = i0; i < i1; ++i) {
+    const uint32_t d = D[inv[i]];
+#pragma unroll
+    for (int m = 0; m < 16; ++m) cnt[m] += (d >> (2 * m)) & 1u;
+  }
+  // 2. exclusive prefix of the counts over threads (warp scan, then warp totals)
+  int32_t pre[16];
+#pragma unroll
+  for (int m = 0; m < 16; ++m) {
+    int32_t x = cnt[m];
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int32_t y = __shfl_up_sync(0xFFFFFFFFu, x, o);
+      if (lane >= o) x += y;
+    }
+    pre[m] = x - cnt[m];
+    if (lane == 31) wsum[warp][m] = x;
+  }
+  __syncthreads();
+  if (tid < 16) {
+    int64_t tot = 0;
+    for (int w = 0; w < nw; ++w) {
+      const int32_t v = wsum[w][tid];
+      wsum[w][tid] = (int32_t)tot;  // exclusive offset of warp w
+      tot += v;
+    }
+    // 3. the drawn vertex of pair m: the (u mod D)-th differing one
+    if (tot > 0) {
+      const uint4 u = philox10(make_uint4((uint32_t)k, (uint32_t)round, (uint32_t)tid, 3u), key);
+      pick[tid] = (int64_t)((uint64_t)u.x % (uint64_t)tot);
+    } else {
+      pick[tid] = -1;
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int m = 0; m < 16; ++m) {
+    const int64_t p = pick[m];
+    const int64_t lo = (int64_t)wsum[warp][m] + pre[m];
+    if (p >= lo && p < lo + cnt[m]) {
+      int64_t seen = lo;
+      for (int i = i0; i < i1; ++i) {
+        const int v = inv[i];
+        if ((D[v] >> (2 * m)) & 1u) {
+          if (seen == p) {
+            atomicOr(&C[v], 1u << (2 * m));
+            break;
+          }
+          ++seen;
+        }
+      }
+    }
+  }
+  __syncthreads();
+  // 4. grow the clusters: a differing vertex takes the bits of its neighbours
+  for (;;) {
+    if (tid == 0) changed = 0;
+    __syncthreads();
+    bool any = false;
+    for (int v = tid; v < n; v += nt) {
+      const uint32_t want = D[v] & ~C[v];
+      if (want == 0u) continue;
+      uint32_t nb = 0u;
+      for (int q = rowptr[v]; q < rowptr[v + 1]; ++q) nb |= C[col[q] & 0x7FFFFFFF];
+      const uint32_t add = want & nb;
+      if (add) {
+        atomicOr(&C[v], add);
+        any = true;
+      }
+    }
+    if (any) changed = 1;
+    __syncthreads();
+    const bool more = changed != 0;
+    __syncthreads();  // every thread has read `changed` before the next pass clears it
+    if (!more) break;
+  }
+  // 5. flip the clusters in both chains; recount the word's unsatisfied bonds
+  unsigned long long flips = 0;
+  for (int v = tid; v < n; v += nt) {
+    const uint32_t cl = C[v];
+    flips += __popc(cl);
+    if (cl) word[v] ^= cl | (cl << 1);
+  }
+  __syncthreads();  // global writes of this CTA visible to its own threads
+  SlicedCounter<NP> cntu;
+  cntu.clear();
+  int32_t bonds = 0;
+  for (int v = tid; v < n; v += nt) {
+    const uint32_t s0 = word[v];
+    for (int q = rowptr[v]; q < rowptr[v + 1]; ++q) {
+      const int e = col[q];
+      const int j = e & 0x7FFFFFFF;
+      if (j <= v) continue;  // each edge once
+      cntu.add_at(0, ~(s0 ^ word[j] ^ (uint32_t)(e >> 31)));
+      ++bonds;
+    }
+    if (field) {
+      // h s = +|h| or -|h|: |h| bonds, unsatisfied where h s = +|h|
+      const int32_t hv = field[v];
+      const int32_t ha = hv > 0 ? hv : -hv;
+      const uint32_t f = hv > 0 ? s0 : ~s0;
+#pragma unroll
+      for (int b = 0; b < 6; ++b)
+        if ((ha >> b) & 1) cntu.add_at(b, f);
+      bonds += ha;
+    }
+  }
+  const int32_t tot = cntu.warp_lane_total();
+  const int32_t wb = __reduce_add_sync(0xFFFFFFFFu, bonds);
+  __shared__ int32_t lane_tot[32];
+  __shared__ int32_t bond_tot;
+  if (tid < 32) lane_tot[tid] = 0;
+  if (tid == 0) bond_tot = 0;
+  __syncthreads();
+  atomicAdd(&lane_tot[lane], tot);
+  if (lane == 0) atomicAdd(&bond_tot, wb);
+  for (int o = 16; o > 0; o >>= 1) flips += __shfl_down_sync(0xFFFFFFFFu, flips, o);
+  if (lane == 0 && flips) atomicAdd(&flipped[k], flips);
+  __syncthreads();
+  if (tid < 32) e_cur[32 * k + tid] = 2 * lane_tot[tid] - bond_tot;  // E = 2 U - bonds
+}
+
 }  // namespace
+
+size_t pt_cluster_graph_smem(int32_t n) { return 12 * (size_t)n; }
+
+cudaError_t pt_cluster_graph(uint32_t *spins, int32_t *e_cur, int32_t n, const int32_t *rowptr,
+                             const int32_t *col, const int32_t *orig, const int32_t *field,
+                             int32_t kmax, int32_t k0, int32_t slots, int32_t round,
+                             uint32_t key0, uint32_t key1, unsigned long long *flipped,
+                             cudaStream_t stream) {
+  if (slots <= 0) return cudaSuccess;
+  const int threads = 1024;
+  const size_t smem = pt_cluster_graph_smem(n);
+  // a thread's unsatisfied-bond count: (vertices per thread) x (degree + |h|) <= kmax each
+  const int64_t per_thread = (int64_t)((n + threads - 1) / threads) * (kmax > 0 ? kmax : 1);
+  cudaError_t err;
+  if (per_thread < (1 << 10)) {
+    err = cudaFuncSetAttribute(pt_cluster_graph_kernel<10>,
+                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (err == cudaSuccess)
+      pt_cluster_graph_kernel<10><<<slots, threads, smem, stream>>>(
+          spins, e_cur, n, rowptr, col, orig, field, k0, round, PhiloxKey{key0, key1}, flipped);
+  } else if (per_thread < (1 << 14)) {
+    err = cudaFuncSetAttribute(pt_cluster_graph_kernel<14>,
+                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (err == cudaSuccess)
+      pt_cluster_graph_kernel<14><<<slots, threads, smem, stream>>>(
+          spins, e_cur, n, rowptr, col, orig, field, k0, round, PhiloxKey{key0, key1}, flipped);
+  } else {
+    return cudaErrorInvalidValue;
+  }
+  if (err != cudaSuccess) return err;
+  return cudaGetLastError();
+}
 
 cudaError_t pt_cluster(uint32_t *spins, int32_t *e_cur, const uint8_t *cbits, int32_t L,
                        int32_t W, int32_t k0, int32_t slots, int32_t round, uint32_t key0,

@@ -65,7 +65,10 @@ def test_tempering_rejects_bad_input(isg):
         isg.isg_parallel_tempering(isg.problem_of(gw), [0.5, 1.0], 2, 2, 1)  # weights not +-1
     g = isg.problem_of(I.random_graph(50, 60, 1))
     with pytest.raises(isg.IsgError):
-        isg.isg_parallel_tempering(g, [0.5, 1.0], 2, 2, 1, icm_slots=1)  # cluster moves: tori
+        isg.isg_parallel_tempering(g, [0.5, 1.0], 2, 2, 1, icm_slots=3)  # more than K slots
+    big = isg.problem_of(I.random_graph(20000, 20000, 2))
+    with pytest.raises(isg.IsgError):
+        isg.isg_parallel_tempering(big, [0.5, 1.0], 2, 2, 1, icm_slots=1)  # n > 19,029
     t = isg.problem_of(I.torus(8, 8, 1))
     with pytest.raises(isg.IsgError):
         isg.isg_parallel_tempering(t, [], 2, 2, 1)
@@ -143,3 +146,32 @@ def test_tempering_on_smallest_last_graph(isg):
     res = isg.isg_parallel_tempering(isg.problem_of(g, colouring=isg.COLOURING_SMALLEST_LAST),
                                      betas, 4, 3, 17)
     assert_same_pt(res, orc, len(betas) - 1)
+
+
+@pytest.mark.parametrize("make,betas,rounds,per_round,icm,cluster", [
+    (lambda: I.random_graph(300, 450, 31), [0.3, 0.8, 1.4, 2.2], 12, 3, 2, 0),
+    (lambda: I.random_graph(700, 1400, 32), [0.4, 1.0, 1.8], 10, 2, 3, 3),
+    (lambda: I.Graph(*_signed_edges(I.random_graph(400, 800, 33))), [0.5, 1.2, 2.0, 3.0, 4.0], 8,
+     2, 2, 0),
+    (lambda: I.independent_set_instance(I.geometric_graph(300, 6.0, 34)), [0.6, 1.5, 3.0], 10,
+     2, 3, 0),
+])
+def test_graph_houdayer_bit_exact(isg, make, betas, rounds, per_round, icm, cluster):
+    """Houdayer cluster moves on graph slot words (unweighted, +-1 weights, local
+    fields with weights +1): states, energies, exchange counts and cluster
+    sizes equal the oracle's, chain by chain."""
+    g = make()
+    c = oracle.csr_of(g)
+    orc = oracle.parallel_tempering(c, betas, rounds, per_round, 17, icm_slots=icm)
+    res = isg.isg_parallel_tempering(isg.problem_of(g), betas, rounds, per_round, 17,
+                                     icm_slots=icm, cluster_ctas=cluster)
+    assert_same_pt(res, orc, len(betas) - 1)
+    K = len(betas)
+    assert np.array_equal(isg.isg_result_cluster_flips(res, K), orc.flipped)
+    assert orc.flipped[K - icm:].sum() > 0                 # moves happened
+
+
+def _signed_edges(g):
+    """g's edges with seeded +-1 weights."""
+    w = np.where(I.draws(g.n, 5, np.arange(g.m)) >> np.uint64(63), 1, -1).astype(np.int32)
+    return g.n, g.u, g.v, w
