@@ -261,11 +261,13 @@ isg_status isg_autotune_batch(const isg_problem *const *probs, int32_t count, in
                               void *cuda_stream, int32_t *threads, int32_t *ctas_per_sm);
 
 /* Parallel tempering (Sec. II.C: replicas at different temperatures that
- * exchange configurations) on a torus instance, or on a graph with weights
- * +-1 and degree <= 63, or with local fields, weights all +1 and
- * degree + |h| <= 63 (the multi-spin graph kernel; vertex order
- * inside the state is the library's, results come back in the caller's
- * vertex order as everywhere else).  temperatures = K slots with
+ * exchange configurations) on any instance: a torus on the multi-spin torus
+ * kernel; a graph with weights +-1 (all +1 with local fields) and
+ * degree + |h| <= 63 on the multi-spin graph kernel; any other graph (general
+ * integer weights, fields with other weights) on the int8 colour-class kernel
+ * (slot k = quads 8k .. 8k+7).  Vertex order inside the state is the
+ * library's; results come back in the caller's vertex order as everywhere
+ * else.  temperatures = K slots with
  * inverse temperatures betas[K] (finite, >= 0, any order), 32 independent
  * chains per slot: R = 32 K replicas, replica r = 32 k + c is chain c at slot
  * k.  Each of `rounds` rounds runs sweeps_per_round sweeps of every replica at
@@ -288,11 +290,11 @@ isg_status isg_autotune_batch(const isg_problem *const *probs, int32_t count, in
  * caller's.  The result is read
  * like isg_anneal's (R = 32 K, S = rounds * sweeps_per_round); exchange counts
  * by isg_result_exchanges, cluster sizes by isg_result_cluster_flips.  opts
- * may be NULL (kernel AUTO or TORUS_MSC; cluster/threads as isg_anneal).
- * EINVAL: neither a torus nor such a graph, K outside [1, 4096], rounds or
- * sweeps_per_round < 1, a bad beta, icm_slots outside [0, K], icm_slots > 0 on
- * a torus with n > 28,544 or on a graph with n > 19,029 (the sites' difference
- * and cluster bits in shared memory). */
+ * may be NULL (kernel AUTO or the instance's kernel; cluster, threads and
+ * quads_per_cta as isg_anneal).  EINVAL: K outside [1, 4096], rounds or
+ * sweeps_per_round < 1, a bad beta, icm_slots outside [0, K], icm_slots > 0
+ * on an instance of the int8 kernel, on a torus with n > 28,544 or on a graph
+ * with n > 19,029 (the sites' difference and cluster bits in shared memory). */
 isg_status isg_parallel_tempering(const isg_problem *p, int32_t temperatures,
                                   const double *betas, int32_t rounds, int32_t sweeps_per_round,
                                   int32_t icm_slots, uint64_t seed, const isg_options *opts,

@@ -279,10 +279,15 @@ __device__ void csr_solve(const CsrSolve &s, const CsrLaunch &L, int quad0, int 
   }
   if (threadIdx.x < 4 * Q) lane_acc[threadIdx.x] = 0;
   const int kmax1 = s.kmax + 1;
+  // threshold rows: one schedule (row t for sweep t), or in parallel tempering
+  // one row per temperature slot of slot_quads quads (the same every sweep)
+  const uint32_t *wtab =
+      s.slot_quads ? s.table + (size_t)(quad0 / s.slot_quads) * kmax1 : s.table;
+  const size_t tstride = s.slot_quads ? 0 : (size_t)kmax1;
   // cached threshold rows: two buffers, the next sweep's row loaded a sweep ahead
   if (trow_n && t_begin < t_end)
     for (int i = threadIdx.x; i < trow_n; i += blockDim.x)
-      trow[(t_begin & 1) * trow_n + i] = s.table[(size_t)t_begin * kmax1 + i];
+      trow[(t_begin & 1) * trow_n + i] = wtab[(size_t)t_begin * tstride + i];
   // peers write into this CTA's copy of the quads only after every CTA has loaded it
   sync_group(K);
 
@@ -360,7 +365,7 @@ __device__ void csr_solve(const CsrSolve &s, const CsrLaunch &L, int quad0, int 
   uint32_t imp = 0u;  // lanes whose best state is the state at the start of sweep t
   constexpr int kPre = 2;  // entries per thread prefetched in registers (the rest: at the end)
   for (; t < t_end; ++t) {
-    const uint32_t *row = s.table + (size_t)t * kmax1;
+    const uint32_t *row = wtab + (size_t)t * tstride;
     const bool more = t + 1 < t_end;
     uint32_t pre[kPre];
     if (trow_n) {
@@ -368,7 +373,7 @@ __device__ void csr_solve(const CsrSolve &s, const CsrLaunch &L, int quad0, int 
 #pragma unroll
       for (int j = 0; j < kPre; ++j) {
         const int x = (int)threadIdx.x + j * (int)blockDim.x;
-        pre[j] = (more && x < trow_n) ? s.table[(size_t)(t + 1) * kmax1 + x] : 0u;
+        pre[j] = (more && x < trow_n) ? wtab[(size_t)(t + 1) * tstride + x] : 0u;
       }
     }
     // byte masks of the improved lanes of each quad
@@ -451,7 +456,7 @@ __device__ void csr_solve(const CsrSolve &s, const CsrLaunch &L, int quad0, int 
         if (x < trow_n) nrow[x] = pre[j];
       }
       for (int x = (int)threadIdx.x + kPre * (int)blockDim.x; x < trow_n; x += blockDim.x)
-        nrow[x] = s.table[(size_t)(t + 1) * kmax1 + x];
+        nrow[x] = wtab[(size_t)(t + 1) * tstride + x];
     }
     // sweep t is publication t + 1 (the initial energy is publication 0)
     int32_t *pbuf = part + ((t + 1) & 1) * 4 * Q * K;

@@ -99,7 +99,9 @@ struct CsrSolve {
   const int32_t *orig;         // [n] original id of each relabelled vertex
   const int32_t *field;        // [n] local fields h (relabelled order), or nullptr
   int32_t kmax;                // max_i (sum_j |w_ij| + |h_i|)
-  const uint32_t *table;       // [sweeps][kmax + 1]
+  const uint32_t *table;       // [sweeps][kmax + 1]; with slot_quads: [slots][kmax + 1]
+  int32_t slot_quads;          // 0: annealing (row t for sweep t); > 0: parallel tempering,
+                               // quad q at slot q / slot_quads, row slot every sweep
   uint32_t key0, key1;
   int32_t quads;               // ceil(R / 4)
   int32_t replicas;
@@ -234,6 +236,13 @@ cudaError_t pt_exchange(uint32_t *spins, int32_t *e_cur, int32_t n, int32_t K, i
 // Parallel tempering: one Houdayer cluster move per chain pair (lanes 2m,
 // 2m+1) on slot words k0 .. k0+slots-1 of an L x W torus state; flipped[k]
 // gains the cluster sizes.  Needs 8 L W bytes of shared memory per CTA.
+// Parallel tempering on int8 quad state (slot k = quads 8k .. 8k+7, chain c in
+// byte c mod 4 of quad 8k + c / 4): the exchange step of pt_exchange.
+cudaError_t pt_exchange_quads(uint32_t *quads, int32_t *e_cur, int32_t n, int32_t K,
+                              int32_t parity, int32_t round, uint32_t key0, uint32_t key1,
+                              const int8_t *sgn, const uint32_t *xtable, int32_t xlen,
+                              unsigned long long *accepted, cudaStream_t stream);
+
 // Parallel tempering on a graph (multi-spin graph layout): one Houdayer move per
 // chain pair on slot words k0 .. k0+slots-1; needs pt_cluster_graph_smem(n)
 // bytes of shared memory per CTA (kmax: the instance's max degree + |h|).

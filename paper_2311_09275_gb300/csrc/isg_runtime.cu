@@ -1141,12 +1141,11 @@ isg_status tempering_impl(const isg_problem *p, int32_t K, const double *betas, 
   if (!out) return fail(ISG_EINVAL, "out must not be NULL");
   *out = nullptr;
   if (!p) return fail(ISG_EINVAL, "problem must not be NULL");
-  // tori run on the multi-spin torus kernel, +-1 graphs on the multi-spin graph kernel
-  const bool gm = !p->torus;
-  if (gm && !graph_msc_ok(p))
-    return fail(ISG_EINVAL,
-                "parallel tempering needs a torus, or a graph with weights +-1 (all +1 with "
-                "local fields) and degree + |h| <= 63");
+  // tori run on the multi-spin torus kernel, +-1 graphs (all +1 with local
+  // fields) of degree + |h| <= 63 on the multi-spin graph kernel, other graphs
+  // (general integer weights, fields on other weights) on the int8 kernel
+  const bool gm = !p->torus && graph_msc_ok(p);
+  const bool quad = !p->torus && !gm;
   if (K < 1 || K > 4096) return fail(ISG_EINVAL, "temperatures must be in [1, 4096]");
   if (rounds < 1 || per_round < 1 || (int64_t)rounds * per_round > INT32_MAX)
     return fail(ISG_EINVAL, "rounds and sweeps_per_round must be >= 1 (product < 2^31)");
@@ -1156,14 +1155,20 @@ isg_status tempering_impl(const isg_problem *p, int32_t K, const double *betas, 
   if (icm_slots > 0 && !gm && 8 * (size_t)p->n > 227 * 1024 - 4096)
     return fail(ISG_EINVAL, "cluster moves on a torus need 8 bytes of shared memory per site "
                             "(n <= 28544)");
+  if (icm_slots > 0 && quad)
+    return fail(ISG_EINVAL, "cluster moves need a torus or a graph the multi-spin kernel takes "
+                            "(weights +-1, all +1 with local fields, degree + |h| <= 63)");
   if (icm_slots > 0 && gm && pt_cluster_graph_smem(p->n) > 227 * 1024 - 4096)
     return fail(ISG_EINVAL, "cluster moves on a graph need 12 bytes of shared memory per vertex "
                             "(n <= 19029)");
   isg_options o = {};
   if (opts) o = *opts;
-  const int mkernel = gm ? ISG_KERNEL_GRAPH_MSC : ISG_KERNEL_TORUS_MSC;
+  const int mkernel =
+      quad ? ISG_KERNEL_CSR : (gm ? ISG_KERNEL_GRAPH_MSC : ISG_KERNEL_TORUS_MSC);
   if (o.kernel != ISG_KERNEL_AUTO && o.kernel != mkernel)
-    return fail(ISG_EINVAL, "parallel tempering uses the multi-spin kernels");
+    return fail(ISG_EINVAL, "parallel tempering of this instance uses kernel %d", mkernel);
+  if (o.quads_per_cta < 0 || o.quads_per_cta > 2)
+    return fail(ISG_EINVAL, "quads_per_cta must be 0, 1 or 2");
   if (o.cluster_ctas < 0 || o.cluster_ctas > 16)
     return fail(ISG_EINVAL, "cluster_ctas must be in [0, 16]");
   if (o.threads != 0 && (o.threads < 32 || o.threads > 1024 || o.threads % 32))
@@ -1177,7 +1182,15 @@ isg_status tempering_impl(const isg_problem *p, int32_t K, const double *betas, 
     threads = t_threads;
   }
   int own_n = 0, own_nnz = 0, planes = 0;
-  if (!gm) {
+  // int8 kernel: 8 quads per slot; a CTA's 1 or 2 quads lie in one slot
+  const int qpc = quad ? (o.quads_per_cta > 0 ? o.quads_per_cta : 1) : 1;
+  if (quad) {
+    csr_shape((8 * K + qpc - 1) / qpc, max_class_size(p), cluster, threads);
+    if (csr_bytes(p, qpc, cluster, false) > 227 * 1024)
+      return fail(ISG_EINVAL, "instance with n = %d needs more shared memory than a CTA has",
+                  p->n);
+    if (csr_bytes(p, qpc, cluster, true) <= 227 * 1024) csr_own_sizes(p, cluster, own_n, own_nnz);
+  } else if (!gm) {
     torus_shape(p->L, p->W, K, cluster, threads);
     if (cluster > p->L) cluster = p->L;
     if (torus_smem_bytes(p->L, p->W, cluster) > 227 * 1024)
@@ -1195,16 +1208,16 @@ isg_status tempering_impl(const isg_problem *p, int32_t K, const double *betas, 
 
   const DeviceProblem *dp = nullptr;
   size_t uploaded = 0;
-  st = problem_device(p, gm ? kNeedCsr : kNeedTorus, &dp, &uploaded);
+  st = problem_device(p, p->torus ? kNeedTorus : kNeedCsr, &dp, &uploaded);
   if (st != ISG_OK) return st;
-  isg_result *r = new_result(p, R, S, true, false, stream);
+  isg_result *r = new_result(p, R, S, !quad, false, stream);
   r->h2d_bytes = (int64_t)uploaded;
-  r->relabelled = gm;
+  r->relabelled = !p->torus;
   r->kernel = mkernel;
   // [K][levels]: slot k's thresholds (torus: energy changes 4 and 8; graphs:
   // every half energy change k = 0..kmax)
   std::vector<int32_t> levels;
-  table_levels(p, !gm, levels);
+  table_levels(p, p->torus, levels);
   std::vector<uint32_t> table;
   build_table(betas, K, levels, table);
   r->table_words = table.size();
@@ -1213,7 +1226,16 @@ isg_status tempering_impl(const isg_problem *p, int32_t K, const double *betas, 
   // makes a = (beta_k - beta_{k+1}) (E_k - E_{k+1}) negative; the table ends
   // where every pair's threshold has reached 0 (|E| <= sum |w|)
   const int32_t pairs = K - 1;
-  const int64_t dmax = gm ? 2 * (int64_t)p->m : 4 * (int64_t)p->n;
+  // |E_k - E_{k+1}| <= 2 (sum |w| + sum |h|)
+  int64_t abs_sum = 0;
+  if (p->torus) {
+    abs_sum = 2 * (int64_t)p->n;
+  } else {
+    for (const int32_t w : p->wt) abs_sum += w < 0 ? -(int64_t)w : w;
+    abs_sum /= 2;  // each edge is in the CSR twice
+    for (const int32_t h : p->field) abs_sum += h < 0 ? -(int64_t)h : h;
+  }
+  const int64_t dmax = 2 * abs_sum;
   std::vector<int8_t> sgn(std::max(pairs, 1), 0);
   int64_t xlen = 1;
   for (int32_t k = 0; k < pairs; ++k) {
@@ -1272,7 +1294,7 @@ isg_status tempering_impl(const isg_problem *p, int32_t K, const double *betas, 
     result_free(r);
     return cuda_fail(err, "preparing parallel tempering");
   }
-  r->ctas = K * cluster;
+  r->ctas = (quad ? (8 * K + qpc - 1) / qpc : K) * cluster;
   r->cluster = cluster;
   r->threads = threads;
   r->staged = own_n > 0;
@@ -1280,7 +1302,11 @@ isg_status tempering_impl(const isg_problem *p, int32_t K, const double *betas, 
   // one row of thresholds per word, the same every sweep
   TorusSolve s = {};
   GraphMscSolve gs = {};
-  if (!gm) {
+  CsrSolve qs = {};
+  if (quad) {
+    qs = make_csr_solve(p, dp, r, seed, false, 0);
+    qs.slot_quads = 8;
+  } else if (!gm) {
     s = make_torus_solve(p, dp, r, seed, false, 0);
     s.table_ws = 2;
     s.table_ts = 0;
@@ -1297,7 +1323,18 @@ isg_status tempering_impl(const isg_problem *p, int32_t K, const double *betas, 
   auto enqueue_rounds = [&](cudaStream_t st) {
     cudaError_t e = cudaSuccess;
     for (int32_t q = 0; q < rounds && e == cudaSuccess; ++q) {
-      if (!gm) {
+      if (quad) {
+        CsrLaunch l = {};
+        l.t_begin = q * per_round;
+        l.t_end = (q + 1) * per_round;
+        l.resume = q > 0;
+        l.cluster = cluster;
+        l.threads = threads;
+        l.quads_per_cta = qpc;
+        l.own_n = own_n;
+        l.own_nnz = own_nnz;
+        e = csr_launch(qs, l, st);
+      } else if (!gm) {
         TorusLaunch l = {};
         l.t_begin = q * per_round;
         l.t_end = (q + 1) * per_round;
@@ -1324,9 +1361,9 @@ isg_status tempering_impl(const isg_problem *p, int32_t K, const double *betas, 
                : pt_cluster(r->d_spins, r->d_e_cur, dp->cbits, p->L, p->W, K - icm_slots,
                             icm_slots, q, key0, key1, r->d_flipped, st);
       if (e == cudaSuccess)
-        e = pt_exchange(r->d_spins, r->d_e_cur, p->n, K, q % 2, q, key0, key1,
-                        (const int8_t *)(pm + o_sgn), (const uint32_t *)(pm + o_x),
-                        (int32_t)xlen, r->d_accepted, st);
+        e = (quad ? pt_exchange_quads : pt_exchange)(
+            r->d_spins, r->d_e_cur, p->n, K, q % 2, q, key0, key1, (const int8_t *)(pm + o_sgn),
+            (const uint32_t *)(pm + o_x), (int32_t)xlen, r->d_accepted, st);
     }
     return e;
   };
@@ -1346,11 +1383,13 @@ isg_status tempering_impl(const isg_problem *p, int32_t K, const double *betas, 
   if (r->timed && err == cudaSuccess) err = cudaEventRecord(r->t1, stream);
   if (err == cudaSuccess) err = reduce_hits(r->d_hit, r->units, r->d_stop, stream);
   if (err == cudaSuccess)
-    err = gm ? unpack_msc_relabel(r->d_spins, p->n, R, dp->orig, r->d_out, stream)
-             : unpack_msc(r->d_spins, p->n, R, r->d_out, stream);
+    err = quad ? unpack_quads(r->d_spins, p->n, R, dp->orig, r->d_out, stream)
+               : gm ? unpack_msc_relabel(r->d_spins, p->n, R, dp->orig, r->d_out, stream)
+                    : unpack_msc(r->d_spins, p->n, R, r->d_out, stream);
   if (err == cudaSuccess)
-    err = gm ? unpack_msc_relabel(r->d_best, p->n, R, dp->orig, r->d_out_best, stream)
-             : unpack_msc(r->d_best, p->n, R, r->d_out_best, stream);
+    err = quad ? unpack_quads(r->d_best, p->n, R, dp->orig, r->d_out_best, stream)
+               : gm ? unpack_msc_relabel(r->d_best, p->n, R, dp->orig, r->d_out_best, stream)
+                    : unpack_msc(r->d_best, p->n, R, r->d_out_best, stream);
   launches += 3;
   if (err == cudaSuccess) err = cudaEventRecord(r->done, stream);
   if (err != cudaSuccess) {

@@ -58,6 +58,54 @@ __global__ void __launch_bounds__(256) pt_exchange_kernel(
   }
 }
 
+// The same exchange on int8 quad state (4 chains per uint32, one byte each):
+// slot k holds quads 8k .. 8k+7, chain c in byte c mod 4 of quad 8k + c / 4.
+__global__ void __launch_bounds__(256) pt_exchange_quads_kernel(
+    uint32_t *quads, int32_t *e_cur, int n, int K, int parity, int round, PhiloxKey key,
+    const int8_t *sgn, const uint32_t *xtable, int xlen, unsigned long long *accepted) {
+  const int k = parity + 2 * (int)blockIdx.x;
+  if (k + 1 >= K) return;
+  __shared__ uint32_t s_mask;
+  if (threadIdx.x < 32) {
+    const int c = (int)threadIdx.x;
+    const int32_t ek = e_cur[32 * k + c], ek1 = e_cur[32 * (k + 1) + c];
+    const int64_t de = (int64_t)ek - ek1;
+    bool swap = sgn[k] == 0 || de == 0 || (sgn[k] > 0) == (de > 0);
+    if (!swap) {
+      const int64_t d = de < 0 ? -de : de;
+      const uint32_t thr = d < xlen ? xtable[(size_t)k * xlen + d] : 0u;
+      const uint4 u = philox10(make_uint4((uint32_t)k, (uint32_t)round, (uint32_t)c >> 2,
+                                          kTagExchange), key);
+      const uint32_t uc = (c & 3) == 0 ? u.x : (c & 3) == 1 ? u.y : (c & 3) == 2 ? u.z : u.w;
+      swap = uc < thr;
+    }
+    const uint32_t mask = __ballot_sync(0xFFFFFFFFu, swap);
+    if (swap) {
+      e_cur[32 * k + c] = ek1;
+      e_cur[32 * (k + 1) + c] = ek;
+    }
+    if (c == 0) {
+      s_mask = mask;
+      if (mask) atomicAdd(&accepted[k], (unsigned long long)__popc(mask));
+    }
+  }
+  __syncthreads();
+  const uint32_t mask = s_mask;
+  if (mask == 0u) return;
+  for (int x = threadIdx.x; x < 8 * n; x += blockDim.x) {
+    const int j = x / n, v = x - j * n;  // quad j of the slot, vertex v
+    const uint32_t m4 = (mask >> (4 * j)) & 0xFu;
+    if (m4 == 0u) continue;
+    const uint32_t bm = ((m4 & 1u) ? 0xFFu : 0u) | ((m4 & 2u) ? 0xFF00u : 0u) |
+                        ((m4 & 4u) ? 0xFF0000u : 0u) | ((m4 & 8u) ? 0xFF000000u : 0u);
+    uint32_t *a = quads + (size_t)(8 * k + j) * n + v;
+    uint32_t *b = quads + (size_t)(8 * (k + 1) + j) * n + v;
+    const uint32_t t = (*a ^ *b) & bm;
+    *a ^= t;
+    *b ^= t;
+  }
+}
+
 // One warp spreads cluster bits along a ring of `len` sites (base + x*stride,
 // x = 0..len-1, closed by a wrap edge) through runs of differing sites, in
 // both directions.  Each lane owns a segment; a segment maps an incoming
@@ -609,6 +657,18 @@ cudaError_t pt_cluster(uint32_t *spins, int32_t *e_cur, const uint8_t *cbits, in
                                                               flipped);
   }
   if (err != cudaSuccess) return err;
+  return cudaGetLastError();
+}
+
+cudaError_t pt_exchange_quads(uint32_t *quads, int32_t *e_cur, int32_t n, int32_t K,
+                              int32_t parity, int32_t round, uint32_t key0, uint32_t key1,
+                              const int8_t *sgn, const uint32_t *xtable, int32_t xlen,
+                              unsigned long long *accepted, cudaStream_t stream) {
+  const int pairs = (K - parity) / 2;
+  if (pairs <= 0) return cudaSuccess;
+  pt_exchange_quads_kernel<<<pairs, 256, 0, stream>>>(quads, e_cur, n, K, parity, round,
+                                                       PhiloxKey{key0, key1}, sgn, xtable, xlen,
+                                                       accepted);
   return cudaGetLastError();
 }
 

@@ -394,11 +394,12 @@ def isg_energy_noalloc(n: int, rowptr_dev: int, col_dev: int, w_dev: int, spins_
 
 def isg_parallel_tempering(p, betas, rounds: int, sweeps_per_round: int, seed: int,
                            stream=None, cluster_ctas: int = 0, threads: int = 0,
-                           time_kernels: bool = False, icm_slots: int = 0) -> "Result":
+                           time_kernels: bool = False, icm_slots: int = 0,
+                           quads_per_cta: int = 0) -> "Result":
     """Parallel tempering over len(betas) slots x 32 chains (replica r = 32 k + c),
     with Houdayer cluster moves on the last icm_slots slots."""
     b = _arr(betas, np.float64)
-    opts = isg_options(0, cluster_ctas, threads, 1 if time_kernels else 0, 0, 0)
+    opts = isg_options(0, cluster_ctas, threads, 1 if time_kernels else 0, quads_per_cta, 0)
     out = _P()
     _check(_lib.isg_parallel_tempering(_h(p), int(b.shape[0]), _ptr(b), int(rounds),
                                        int(sweeps_per_round), int(icm_slots),

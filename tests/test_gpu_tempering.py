@@ -61,8 +61,8 @@ def test_tempering_full_size_ladder(isg):
 def test_tempering_rejects_bad_input(isg):
     gw = I.random_graph(50, 60, 1)
     gw = I.Graph(gw.n, gw.u, gw.v, np.full(gw.m, 2, np.int32))
-    with pytest.raises(isg.IsgError):
-        isg.isg_parallel_tempering(isg.problem_of(gw), [0.5, 1.0], 2, 2, 1)  # weights not +-1
+    with pytest.raises(isg.IsgError):   # cluster moves need the multi-spin kernels
+        isg.isg_parallel_tempering(isg.problem_of(gw), [0.5, 1.0], 2, 2, 1, icm_slots=1)
     g = isg.problem_of(I.random_graph(50, 60, 1))
     with pytest.raises(isg.IsgError):
         isg.isg_parallel_tempering(g, [0.5, 1.0], 2, 2, 1, icm_slots=3)  # more than K slots
@@ -175,3 +175,36 @@ def _signed_edges(g):
     """g's edges with seeded +-1 weights."""
     w = np.where(I.draws(g.n, 5, np.arange(g.m)) >> np.uint64(63), 1, -1).astype(np.int32)
     return g.n, g.u, g.v, w
+
+
+@pytest.mark.parametrize("make,betas,rounds,per_round,cluster,qpc", [
+    (lambda: _weighted(I.random_graph(300, 600, 41), (-2, 1, 3)), [0.2, 0.5, 0.9, 1.4], 8, 3,
+     0, 0),
+    (lambda: _weighted(I.random_graph(500, 900, 42), (1, -1, 2, -3, 5)), [0.3, 0.7, 1.2], 6, 2,
+     3, 2),
+    # local fields on +-1 weights (the multi-spin graph kernel takes fields only with +1)
+    (lambda: _fields(I.Graph(*_signed_edges(I.random_graph(350, 700, 43))), 44),
+     [0.4, 0.8, 1.6, 2.4, 3.2], 7, 2, 2, 1),
+])
+def test_tempering_on_int8_kernel_bit_exact(isg, make, betas, rounds, per_round, cluster, qpc):
+    """Parallel tempering of instances the multi-spin kernels do not take
+    (general integer weights; local fields with +-1 weights), on the int8
+    colour-class kernel with 8 quads per slot: equal to the oracle chain by
+    chain, including the exchange counts."""
+    g = make()
+    c = oracle.csr_of(g)
+    orc = oracle.parallel_tempering(c, betas, rounds, per_round, 23)
+    res = isg.isg_parallel_tempering(isg.problem_of(g), betas, rounds, per_round, 23,
+                                     cluster_ctas=cluster, quads_per_cta=qpc)
+    assert res.stats()["kernel"] == 2
+    assert_same_pt(res, orc, len(betas) - 1)
+    assert orc.accepted.sum() > 0
+
+
+def _weighted(g, ws):
+    return I.Graph(g.n, g.u, g.v, np.array([ws[e % len(ws)] for e in range(g.m)], np.int32))
+
+
+def _fields(g, seed):
+    h = (I.draws(seed, 6, np.arange(g.n)) % np.uint64(7)).astype(np.int32) - 3
+    return I.Graph(g.n, g.u, g.v, g.w, h)
