@@ -237,9 +237,108 @@ __device__ __forceinline__ void sweep_phase(uint32_t *spin, uint32_t *best, cons
   }
 }
 
+// Software-pipelined colour phase (a thread with at most kPipeSites sites per
+// phase): at each of its positions the thread updates its site of colour c
+// with the masks drawn earlier (mc4, mc8) and draws the masks of the other
+// colour's site at the same position for the next phase (into mo4, mo8, with
+// that phase's block prefixes bp and thresholds To4, To8): the random numbers
+// do not depend on the spins, so the independent Philox work of one site and
+// the dependent spin logic of another share one straight-line loop body that
+// the compiler interleaves.  Both masks are always built (a threshold of 0
+// gives an empty mask).
+constexpr int kPipeSites = 3;
+
+template <int NP>
+__device__ __forceinline__ void pipe_phase(uint32_t *spin, uint32_t *best, const uint8_t *cb,
+                                           uint32_t *up_peer, uint32_t *down_peer, int W, int r0,
+                                           int nr, int c, const BlockPrefix (&bp)[8],
+                                           const RoundKeys &rk, uint32_t To4, uint32_t To8,
+                                           uint32_t imp, SlicedCounter<NP> &cnt,
+                                           const uint32_t (&mc4)[kPipeSites],
+                                           const uint32_t (&mc8)[kPipeSites],
+                                           uint32_t (&mo4)[kPipeSites],
+                                           uint32_t (&mo8)[kPipeSites]) {
+  const int half = W >> 1;
+  const int step_rows = blockDim.x / half;
+  const int step_cols = blockDim.x - step_rows * half;
+  int lr = 1 + (int)threadIdx.x / half;
+  int j = (int)threadIdx.x - (lr - 1) * half;
+#pragma unroll
+  for (int i = 0; i < kPipeSites; ++i) {
+    if (lr <= nr) {
+      const int gr = r0 + lr - 1;
+      const int par = (c + gr) & 1;
+      const int col = 2 * j + par;
+      // the other colour's site at this position, for the next phase
+      site_masks<true>((uint32_t)(gr * W + 2 * j + (par ^ 1)), bp, rk, To4, To8, mo4[i], mo8[i]);
+      const int x = lr * W + col;
+      const int xl = (col == 0) ? x + W - 1 : x - 1;
+      const int xr = (col == W - 1) ? x - W + 1 : x + 1;
+      const uint32_t s0 = spin[x];
+      if (imp != 0u) {
+        uint32_t &bx = best[x - W];
+        bx = (bx & ~imp) | (s0 & imp);
+      }
+      const uint32_t cbx = cb[x];
+      const uint32_t a = ~(s0 ^ spin[xr] ^ sign_mask(cbx));
+      const uint32_t b = ~(s0 ^ spin[xl] ^ sign_mask(cb[xl]));
+      const uint32_t cu = ~(s0 ^ spin[x - W] ^ sign_mask(cb[x - W] >> 1));
+      const uint32_t d = ~(s0 ^ spin[x + W] ^ sign_mask(cbx >> 1));
+      const uint32_t s1 = a ^ b, c1 = a & b, s2 = cu ^ d, c2 = cu & d;
+      const uint32_t u0 = s1 ^ s2;
+      const uint32_t u1 = (c1 ^ c2) | (s1 & s2);
+      const uint32_t u2 = c1 & c2;
+      const uint32_t eq0 = ~(u0 | u1 | u2);
+      const uint32_t eq1 = u0 & ~u1;
+      const uint32_t ge2 = u1 | u2;
+      const uint32_t acc = ge2 | (eq1 & mc4[i]) | (eq0 & mc8[i]);
+      const uint32_t sn = s0 ^ acc;
+      spin[x] = sn;
+      if (lr == 1) up_peer[col] = sn;
+      if (lr == nr) down_peer[col] = sn;
+      cnt.add3(acc & u0, (acc & (u0 ^ u1)) | ~acc, acc & eq0);
+    }
+    j += step_cols;
+    lr += step_rows;
+    if (j >= half) {
+      j -= half;
+      ++lr;
+    }
+  }
+}
+
+// The masks of this thread's sites of colour c (the pipeline's first phase).
+__device__ __forceinline__ void pipe_prologue(int W, int r0, int nr, int c,
+                                              const BlockPrefix (&bp)[8], const RoundKeys &rk,
+                                              uint32_t T4, uint32_t T8,
+                                              uint32_t (&m4)[kPipeSites],
+                                              uint32_t (&m8)[kPipeSites]) {
+  const int half = W >> 1;
+  const int step_rows = blockDim.x / half;
+  const int step_cols = blockDim.x - step_rows * half;
+  int lr = 1 + (int)threadIdx.x / half;
+  int j = (int)threadIdx.x - (lr - 1) * half;
+#pragma unroll
+  for (int i = 0; i < kPipeSites; ++i) {
+    m4[i] = m8[i] = 0u;
+    if (lr <= nr) {
+      const int gr = r0 + lr - 1;
+      site_masks<true>((uint32_t)(gr * W + 2 * j + ((c + gr) & 1)), bp, rk, T4, T8, m4[i], m8[i]);
+    }
+    j += step_cols;
+    lr += step_rows;
+    if (j >= half) {
+      j -= half;
+      ++lr;
+    }
+  }
+}
+
 // kPrefetch: draw the first site's masks of each phase during the barrier
 // before it (off in the 64-register build, where the extra live state spills).
-template <int NP, bool kPrefetch>
+// kPipe: the software-pipelined phases (every thread has at most kPipeSites
+// sites per phase).
+template <int NP, bool kPrefetch, bool kPipe = false>
 __device__ void torus_word(const TorusSolve &s, int word, int k, int K, int t_begin, int t_end,
                            int resume, uint8_t *smem) {
   const int L = s.L, W = s.W, n = L * W;
@@ -322,15 +421,55 @@ __device__ void torus_word(const TorusSolve &s, int word, int k, int K, int t_be
 #pragma unroll
     for (int q = 0; q < 8; ++q) bp[q] = block_prefix(8u * uword + (uint32_t)q, (uint32_t)tt, s.rk);
   };
+  if (kPipe) {
+    // masks of colour 0 (m0) and colour 1 (m1) of this thread's sites, each
+    // drawn during the phase before the one that uses them
+    uint32_t m04[kPipeSites], m08[kPipeSites], m14[kPipeSites], m18[kPipeSites];
+    if (t < t_end) {
+      sweep_prefix(t);
+      pipe_prologue(W, r0, nr, 0, bp, s.rk, T4n, T8n, m04, m08);
+    }
+    for (; t < t_end; ++t) {
+      const uint32_t T4 = T4n, T8 = T8n;
+      const bool more = t + 1 < t_end;
+      if (more) {
+        T4n = trow[(size_t)(t + 1) * s.table_ts];
+        T8n = trow[(size_t)(t + 1) * s.table_ts + 1];
+      }
+      cnt.clear();
+      // colour 0 of sweep t; draws colour 1 of sweep t
+      pipe_phase<NP>(spin, best, cb, up_peer, down_peer, W, r0, nr, 0, bp, s.rk, T4, T8, imp,
+                     cnt, m04, m08, m14, m18);
+      group_arrive(K);
+      if (more) sweep_prefix(t + 1);
+      group_wait(K);
+      // colour 1 of sweep t; draws colour 0 of sweep t + 1 (unused after the last)
+      pipe_phase<NP>(spin, best, cb, up_peer, down_peer, W, r0, nr, 1, bp, s.rk, T4n, T8n, imp,
+                     cnt, m14, m18, m04, m08);
+      e += 4 * (cluster_lane_sum<NP>(cnt, acc, acc_m, K, [] {}) - 2 * n);
+      const bool better = e < e_best;
+      if (better) e_best = e;
+      imp = __ballot_sync(0xFFFFFFFFu, better) & valid;
+      if (s.has_target) {
+        const int32_t mn =
+            __reduce_min_sync(0xFFFFFFFFu, ((valid >> lane) & 1u) ? e_best : INT_MAX);
+        if (mn <= s.target) {
+          hit = t;
+          ++t;
+          break;
+        }
+      }
+    }
+  }
   // masks of this thread's first site of the next phase, drawn while the
   // group barrier before that phase completes (they do not depend on spins)
   uint32_t pre4 = 0u, pre8 = 0u;
   bool ready = false;
-  if (kPrefetch && t < t_end) {
+  if (!kPipe && kPrefetch && t < t_end) {
     sweep_prefix(t);
     ready = first_site_masks(W, r0, nr, 0, bp, s.rk, T4n, T8n, pre4, pre8);
   }
-  for (; t < t_end; ++t) {
+  for (; !kPipe && t < t_end; ++t) {
     const uint32_t T4 = T4n, T8 = T8n;
     const bool more = t + 1 < t_end;
     if (more) {
@@ -396,7 +535,7 @@ __device__ void torus_word(const TorusSolve &s, int word, int k, int K, int t_be
 // MAXT = 384 (CTAs of at most 384 threads, six counter planes: the 80 x 100
 // workload's shape) lets the compiler keep more of the eight Philox blocks in
 // flight (144 registers against 116 in the 512-thread build: +1.2 %)
-template <int NP, int MAXT>
+template <int NP, int MAXT, bool PIPE = false>
 __global__ void __launch_bounds__(MAXT, 1) torus_kernel(TorusSolve s, TorusLaunch l) {
   extern __shared__ __align__(16) uint8_t smem[];
   const int K = l.cluster;
@@ -409,7 +548,7 @@ __global__ void __launch_bounds__(MAXT, 1) torus_kernel(TorusSolve s, TorusLaunc
       if (s.hit[w] >= 0 && s.hit[w] < m) m = s.hit[w];
     if (m != INT_MAX && m + 1 < t_end) t_end = m + 1;
   }
-  torus_word<NP, (MAXT <= 512)>(s, word, k, K, l.t_begin, t_end, l.resume, smem);
+  torus_word<NP, (MAXT <= 512), PIPE>(s, word, k, K, l.t_begin, t_end, l.resume, smem);
 }
 
 // One CTA per unit with a CTA-wide barrier (nothing to overlap): no mask
@@ -557,10 +696,17 @@ cudaError_t torus_launch(const TorusSolve &s, const TorusLaunch &l, cudaStream_t
   const int grid = s.words * K;
   if (l.threads > 1024) return cudaErrorInvalidValue;
   const bool wide = l.threads > 512;
+  // software-pipelined phases when every thread has at most kPipeSites sites per phase
+  const bool pipe = l.threads <= 384 && spt / 2 <= kPipeSites;
   switch (np) {
     case 5:
-      return launch_clustered(torus_kernel<5, 384>, grid, l.threads, smem, K, stream, s, l);
+      return pipe ? launch_clustered(torus_kernel<5, 384, true>, grid, l.threads, smem, K,
+                                     stream, s, l)
+                  : launch_clustered(torus_kernel<5, 384>, grid, l.threads, smem, K, stream, s, l);
     case 6:
+      if (l.threads <= 384 && pipe)
+        return launch_clustered(torus_kernel<6, 384, true>, grid, l.threads, smem, K, stream, s,
+                                l);
       if (l.threads <= 384)
         return launch_clustered(torus_kernel<6, 384>, grid, l.threads, smem, K, stream, s, l);
       return wide ? launch_clustered(torus_kernel<6, 1024>, grid, l.threads, smem, K, stream, s, l)
