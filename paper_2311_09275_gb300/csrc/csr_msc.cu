@@ -40,8 +40,8 @@ __global__ void __launch_bounds__(512) gm_batch_kernel(const GraphMscItem *items
 }  // namespace
 
 size_t gm_smem_bytes(int32_t n, int32_t cluster, int32_t n_colours, int32_t own_n,
-                     int32_t own_nnz, int32_t kmax1, bool fields) {
-  return gm_layout(n, cluster, n_colours, own_n, own_nnz, kmax1, fields).total;
+                     int32_t own_nnz, int32_t own_lv, int32_t kmax1, bool fields) {
+  return gm_layout(n, cluster, n_colours, own_n, own_nnz, own_lv, kmax1, fields).total;
 }
 
 int gm_planes(int32_t max_count) {

@@ -40,11 +40,14 @@ constexpr int kPlanesU = 6;  // per-lane bond counts up to 63 (degree <= 63)
 __host__ __device__ __forceinline__ size_t align16(size_t x) { return (x + 15) & ~size_t(15); }
 
 struct GmSmem {
-  size_t spin, lrow, lorig, lcol, lbest, lfield, ocls, trow, part, lane_acc, total;
+  size_t spin, lrow, lorig, lcol, lbest, lfield, lmoff, lmask, ocls, trow, part, lane_acc, total;
 };
 
+// own_n, own_nnz, own_lv: the largest owned vertex, adjacency and threshold-
+// level count of any rank (0: adjacency not staged, and no mask table).
 __host__ __device__ __forceinline__ GmSmem gm_layout(int n, int K, int n_colours, int own_n,
-                                                     int own_nnz, int kmax1, bool fields) {
+                                                     int own_nnz, int own_lv, int kmax1,
+                                                     bool fields) {
   GmSmem m;
   m.spin = 0;
   m.lrow = align16(sizeof(uint32_t) * (size_t)n);
@@ -52,8 +55,11 @@ __host__ __device__ __forceinline__ GmSmem gm_layout(int n, int K, int n_colours
   m.lcol = align16(m.lorig + sizeof(int32_t) * (size_t)own_n);
   m.lbest = align16(m.lcol + sizeof(int32_t) * (size_t)own_nnz);
   m.lfield = align16(m.lbest + sizeof(uint32_t) * (size_t)own_n);
-  m.ocls = align16(m.lfield + (fields ? sizeof(int32_t) * (size_t)own_n : 0));
-  m.trow = align16(m.ocls + sizeof(int32_t) * 3 * (size_t)n_colours);  // class slice table
+  m.lmoff = align16(m.lfield + (fields ? sizeof(int32_t) * (size_t)own_n : 0));
+  m.lmask = align16(m.lmoff + (own_n ? sizeof(int32_t) * ((size_t)own_n + 1) : 0));
+  m.ocls = align16(m.lmask + 2 * sizeof(uint32_t) * (size_t)own_lv);
+  // class slice table: slice bounds, first slot, and mask work of each class's window
+  m.trow = align16(m.ocls + sizeof(int32_t) * (4 * (size_t)n_colours + 1));
   m.part = align16(m.trow + 2 * sizeof(uint32_t) * (size_t)kmax1);
   m.lane_acc = m.part + 2 * sizeof(int32_t) * 32 * (size_t)K;
   m.total = align16(m.lane_acc + sizeof(int32_t) * 32);
@@ -124,21 +130,52 @@ __device__ __forceinline__ void vertex_uniforms(uint32_t orig, const BlockPrefix
   for (int q = 0; q < 8; ++q) uu[q] = philox10_factored(sp, bp[q], rk);
 }
 
+// Smallest of a vertex's 32 uniforms.  A level whose threshold does not
+// exceed it accepts none of its replicas, so its 32 compares can be skipped
+// without changing the result (late in an annealing schedule, when the
+// thresholds are small, this is the usual case).
+__device__ __forceinline__ uint32_t uniform_min(const uint4 (&uu)[8]) {
+  uint32_t m[8];
+#pragma unroll
+  for (int q = 0; q < 8; ++q) m[q] = min(min(uu[q].x, uu[q].y), min(uu[q].z, uu[q].w));
+  return min(min(min(m[0], m[1]), min(m[2], m[3])), min(min(m[4], m[5]), min(m[6], m[7])));
+}
+
+// Lanes whose uniform is below T.
+__device__ __forceinline__ uint32_t uniforms_below(const uint4 (&uu)[8], uint32_t T) {
+  uint32_t m0 = 0u, m1 = 0u;
+#pragma unroll
+  for (int q = 0; q < 8; ++q) {
+    uint32_t &m = (q & 1) ? m1 : m0;
+    if (uu[q].x < T) m |= 1u << (4 * q);
+    if (uu[q].y < T) m |= 2u << (4 * q);
+    if (uu[q].z < T) m |= 4u << (4 * q);
+    if (uu[q].w < T) m |= 8u << (4 * q);
+  }
+  return m0 | m1;
+}
+
 // Lanes where the field term h s of a vertex with word s0 is +|h| (bit 1 =
 // spin +1), counted as unsatisfied extra bonds.
 __device__ __forceinline__ uint32_t field_unsat(uint32_t s0, int32_t hv) {
   return hv > 0 ? s0 : ~s0;
 }
 
+// Acceptance sources of update_vertex.
+enum GmAccept { kAcceptPre = 0, kAcceptLazy = 1, kAcceptMasks = 2 };
+
 // One vertex of one replica word (adjacency entries [p0, p1); and, FIELD, its
-// local field hv): its 32
-// uniforms are pre (drawn by the caller), or with LAZY filled by draw(uu)
-// only when some replica is uphill.  Returns the new word; accumulates the
-// accepted flips' d and U into the energy counters.
-template <int NP, bool FIELD, bool LAZY, typename Draw>
+// local field hv).  Its acceptance masks come from its 32 uniforms, pre
+// (kAcceptPre: drawn by the caller) or filled by draw(uu) only when some
+// replica is uphill (kAcceptLazy), or are read per level from mk (kAcceptMasks:
+// mk[lv] = lanes whose uniform is below the threshold of k = d - 2 lv, built
+// ahead of the phase).  Returns the new word; accumulates the accepted flips'
+// d and U into the energy counters.
+template <int NP, bool FIELD, int ACCEPT, typename Draw>
 __device__ __forceinline__ uint32_t update_vertex(const uint32_t *spin, int v, int p0, int p1,
                                                   const GmAdj &a, const uint32_t *row,
-                                                  const uint4 (&pre)[8], Draw draw, int32_t hv,
+                                                  const uint4 (&pre)[8], Draw draw,
+                                                  const uint32_t *mk, int32_t hv,
                                                   SlicedCounter<NP> &cd, SlicedCounter<NP> &cu) {
   const uint32_t s0 = spin[v];
   int d = p1 - p0;
@@ -177,37 +214,41 @@ __device__ __forceinline__ uint32_t update_vertex(const uint32_t *spin, int v, i
   // uphill lanes: U <= (d - 1) / 2, i.e. k = d - 2U > 0; those at level U
   // flip when their uniform is below the threshold of k = d - 2U
   const int levels = (d + 1) / 2;
-  auto below = [&](const uint4 (&uu)[8], uint32_t T) {
-    uint32_t m0 = 0u, m1 = 0u;
-#pragma unroll
-    for (int q = 0; q < 8; ++q) {
-      uint32_t &m = (q & 1) ? m1 : m0;
-      if (uu[q].x < T) m |= 1u << (4 * q);
-      if (uu[q].y < T) m |= 2u << (4 * q);
-      if (uu[q].z < T) m |= 4u << (4 * q);
-      if (uu[q].w < T) m |= 8u << (4 * q);
-    }
-    return m0 | m1;
-  };
   uint32_t acc;
-  if (LAZY) {
+  if (ACCEPT == kAcceptMasks) {
+    uint32_t up = 0u, yes = 0u;
+    for (int lv = 0; lv < levels; ++lv) {
+      const uint32_t eq = count_equals(u, lv);
+      up |= eq;
+      yes |= eq & mk[lv];
+    }
+    acc = ~up | yes;
+  } else if (ACCEPT == kAcceptLazy) {
     uint32_t up = 0u;
     for (int lv = 0; lv < levels; ++lv) up |= count_equals(u, lv);
     acc = ~up;
     if (up != 0u) {
       uint4 uu[8];
       draw(uu);
+      const uint32_t umin = uniform_min(uu);
       for (int lv = 0; lv < levels; ++lv) {
+        const uint32_t T = row[d - 2 * lv];
+        if (T <= umin) continue;
         const uint32_t eq = count_equals(u, lv);
-        if (eq != 0u) acc |= eq & below(uu, row[d - 2 * lv]);
+        if (eq != 0u) acc |= eq & uniforms_below(uu, T);
       }
     }
   } else {
-    acc = 0xFFFFFFFFu;
+    // the uphill lanes are rejected unless their level's threshold admits them
+    uint32_t up = 0u, yes = 0u;
+    const uint32_t umin = uniform_min(pre);
     for (int lv = 0; lv < levels; ++lv) {
       const uint32_t eq = count_equals(u, lv);
-      if (eq != 0u) acc &= ~eq | below(pre, row[d - 2 * lv]);
+      up |= eq;
+      const uint32_t T = row[d - 2 * lv];
+      if (eq != 0u && T > umin) yes |= eq & uniforms_below(pre, T);
     }
+    acc = ~up | yes;
   }
   // energy change of the accepted lanes: 2 (d - 2U); d <= 63 (6 bits)
   uint32_t da[kPlanesU];
@@ -234,15 +275,31 @@ __device__ __forceinline__ void group_wait(int K) {
     __syncthreads();
 }
 
-// PREFETCH: draw the next phase's first uniforms during the group barrier
-// (off in the unit kernel, whose CTA-wide barrier leaves nothing to overlap).
+// Threads with no vertex to update in class c nor in the class after its
+// window (the next sweep's first class after the last): those numbered at
+// least the larger slice length.
+__device__ __forceinline__ int window_idle(const int32_t *clo, const int32_t *chi, int c, int nc,
+                                           int B) {
+  const int nn = c + 1 < nc ? c + 1 : 0;
+  return max(B - max(chi[c] - clo[c], chi[nn] - clo[nn]), 0);
+}
+
+// STAGED (adjacency of the owned slices in shared memory): the acceptance
+// masks of every owned vertex for sweep t + 1 are built during sweep t, a
+// share in each class's barrier window (by threads idle in that class and the
+// next, as far as they go), into a table of two sweeps; the update then reads
+// masks instead of drawing uniforms.  Otherwise, PREFETCH: draw the next
+// phase's first uniforms during the group barrier (off in the unit kernel,
+// whose CTA-wide barrier leaves nothing to overlap).
 template <int NP, bool STAGED, bool FIELD, bool PREFETCH = true>
 __device__ void gm_word(const GraphMscSolve &s, const GraphMscLaunch &L, int word, int k, int K,
                         int t_begin, int t_end, int resume, uint8_t *smem) {
+  constexpr bool PF = PREFETCH && !STAGED;
   const int n = s.n;
   const int nc = s.n_colours;
-  const GmSmem lay = gm_layout(n, K, nc, STAGED ? L.own_n : 0, STAGED ? L.own_nnz : 0, s.kmax1,
-                               FIELD);
+  const int B = (int)blockDim.x;
+  const GmSmem lay = gm_layout(n, K, nc, STAGED ? L.own_n : 0, STAGED ? L.own_nnz : 0,
+                               STAGED ? L.own_lv : 0, s.kmax1, FIELD);
   const bool has_field = FIELD && s.field != nullptr;
   uint32_t *spin = reinterpret_cast<uint32_t *>(smem + lay.spin);
   // per class: this rank's slice [clo, chi) and the slot of its first vertex
@@ -250,6 +307,7 @@ __device__ void gm_word(const GraphMscSolve &s, const GraphMscLaunch &L, int wor
   int32_t *clo = reinterpret_cast<int32_t *>(smem + lay.ocls);
   int32_t *chi = clo + nc;
   int32_t *cob = chi + nc;
+  int32_t *qlo = cob + nc;  // staged: mask work [qlo[c], qlo[c + 1]) in class c's window
   uint32_t *trow = reinterpret_cast<uint32_t *>(smem + lay.trow);
   int32_t *part = reinterpret_cast<int32_t *>(smem + lay.part);
   int32_t *lane_acc = reinterpret_cast<int32_t *>(smem + lay.lane_acc);
@@ -279,6 +337,25 @@ __device__ void gm_word(const GraphMscSolve &s, const GraphMscLaunch &L, int wor
       cob[c] = STAGED ? ov : lo;
       ov += hi - lo;
     }
+    if (STAGED) {
+      // the owned slots' mask work over the class windows: in proportion to
+      // the threads idle across each window while they can take it all, else
+      // one item per idle thread and the rest spread evenly
+      int64_t idle = 0;
+      for (int c = 0; c < nc; ++c) idle += window_idle(clo, chi, c, nc, B);
+      const int extra = idle >= ov ? 0 : ov - (int)idle;
+      int64_t acc = 0;
+      for (int c = 0; c < nc; ++c) {
+        qlo[c] = (extra || idle == 0) ? (int)acc : (int)(ov * acc / idle);
+        acc += window_idle(clo, chi, c, nc, B);
+        if (extra) acc += extra / nc + (c < extra % nc ? 1 : 0);
+      }
+      qlo[nc] = ov;
+      // a thread builds its share of the last window after arriving at the
+      // sweep's last barrier, so the next barrier it reaches lies after the
+      // next sweep's first class: that window takes no slot of the first class
+      if (nc > 1) qlo[nc - 1] = max(qlo[nc - 1], chi[0] - clo[0]);
+    }
   }
   __syncthreads();
   GmAdj adj;
@@ -286,6 +363,10 @@ __device__ void gm_word(const GraphMscSolve &s, const GraphMscLaunch &L, int wor
   // global memory)
   uint32_t *lbest = reinterpret_cast<uint32_t *>(smem + lay.lbest);
   int32_t *lfield = reinterpret_cast<int32_t *>(smem + lay.lfield);
+  // staged: each owned slot's first entry in the mask table (two sweeps of
+  // L.own_lv words), one per threshold level (d + |h| + 1) / 2
+  int32_t *lmoff = reinterpret_cast<int32_t *>(smem + lay.lmoff);
+  uint32_t *lmask = reinterpret_cast<uint32_t *>(smem + lay.lmask);
   if (STAGED) {
     int32_t *lrow = reinterpret_cast<int32_t *>(smem + lay.lrow);
     int32_t *lorig = reinterpret_cast<int32_t *>(smem + lay.lorig);
@@ -307,14 +388,41 @@ __device__ void gm_word(const GraphMscSolve &s, const GraphMscLaunch &L, int wor
       ebase += e1 - e0;
     }
     adj = {lrow, lcol, lorig};
+    __syncthreads();
+    if (threadIdx.x < 32) {
+      // exclusive prefix of the slots' level counts: a contiguous chunk per lane
+      const int cnt = qlo[nc];
+      const int chunk = (cnt + 31) / 32;
+      const int a0 = min(lane * chunk, cnt), a1 = min(a0 + chunk, cnt);
+      auto levels_of = [&](int i) {
+        int d = lrow[i + 1] - lrow[i];
+        if (FIELD) d += abs(lfield[i]);
+        return (d + 1) / 2;
+      };
+      int sum = 0;
+      for (int i = a0; i < a1; ++i) sum += levels_of(i);
+      int incl = sum;
+#pragma unroll
+      for (int off = 1; off < 32; off <<= 1) {
+        const int y = __shfl_up_sync(0xFFFFFFFFu, incl, off);
+        if (lane >= off) incl += y;
+      }
+      int run = incl - sum;
+      for (int i = a0; i < a1; ++i) {
+        lmoff[i] = run;
+        run += levels_of(i);
+      }
+      if (lane == 31) lmoff[cnt] = incl;
+    }
   } else {
     adj = {s.rowptr, s.col, s.orig};
   }
   if (threadIdx.x < 32) lane_acc[threadIdx.x] = 0;
   // threshold rows: two buffers, the next sweep's row prefetched a sweep ahead
-  if (t_begin < t_end)
+  // (staged: the masks are built a sweep ahead, and the rows two sweeps ahead)
+  for (int tt = t_begin; tt < min(t_end, t_begin + (STAGED ? 2 : 1)); ++tt)
     for (int x = threadIdx.x; x < s.kmax1; x += blockDim.x)
-      trow[(t_begin & 1) * s.kmax1 + x] = wtab[(size_t)t_begin * s.table_ts + x];
+      trow[(tt & 1) * s.kmax1 + x] = wtab[(size_t)tt * s.table_ts + x];
   // peers write into this CTA's copy of the word only after every CTA has loaded it
   sync_group(K);
 
@@ -369,13 +477,42 @@ __device__ void gm_word(const GraphMscSolve &s, const GraphMscLaunch &L, int wor
     for (int q = 0; q < 8; ++q) bp[q] = block_prefix(8u * uword + (uint32_t)q, (uint32_t)tt, s.rk);
   };
   auto draw_first = [&](int c) {
-    if (!PREFETCH) return;
+    if (!PF) return;
     ready = clo[c] + (int)threadIdx.x < chi[c];
     if (ready) vertex_uniforms((uint32_t)adj.orig[cob[c] + threadIdx.x], bp, s.rk, uu);
   };
-  if (PREFETCH && t_begin < t_end) {
+  if (PF && t_begin < t_end) {
     sweep_prefix(t_begin);
     draw_first(0);
+  }
+  // staged: the masks of slot j for sweep tt (block prefixes bp of sweep tt,
+  // thresholds mrow), and the share of them built in class c's window
+  auto masks_of = [&](int j, const uint32_t *mrow, uint32_t *mout) {
+    int d = adj.row[j + 1] - adj.row[j];
+    if (FIELD) d += abs(lfield[j]);
+    const int levels = (d + 1) / 2;
+    if (levels == 0) return;
+    uint4 w[8];
+    vertex_uniforms((uint32_t)adj.orig[j], bp, s.rk, w);
+    const uint32_t umin = uniform_min(w);
+    uint32_t *o = mout + lmoff[j];
+    for (int lv = 0; lv < levels; ++lv) {
+      const uint32_t T = mrow[d - 2 * lv];
+      o[lv] = T > umin ? uniforms_below(w, T) : 0u;
+    }
+  };
+  auto mask_window = [&](int c, int tt) {
+    // items go to threads in descending order: first those idle in this
+    // class and the next, last those with a vertex in both
+    const uint32_t *mrow = trow + (tt & 1) * s.kmax1;
+    uint32_t *mout = lmask + (size_t)(tt & 1) * L.own_lv;
+    for (int j = qlo[c] + B - 1 - (int)threadIdx.x; j < qlo[c + 1]; j += B) masks_of(j, mrow, mout);
+  };
+  if (STAGED && t_begin < t_end) {
+    sweep_prefix(t_begin);
+    for (int j = threadIdx.x; j < qlo[nc]; j += B)
+      masks_of(j, trow + (t_begin & 1) * s.kmax1, lmask + (size_t)(t_begin & 1) * L.own_lv);
+    __syncthreads();
   }
 
   int t = t_begin;
@@ -384,12 +521,17 @@ __device__ void gm_word(const GraphMscSolve &s, const GraphMscLaunch &L, int wor
   const int x0 = (int)threadIdx.x, x1 = (int)(threadIdx.x + blockDim.x);
   for (; t < t_end; ++t) {
     const uint32_t *row = trow + (t & 1) * s.kmax1;
-    // next sweep's thresholds (kmax1 <= 64 <= 2 x threads)
     const bool more = t + 1 < t_end;
-    const uint32_t *gnext = wtab + (size_t)(t + 1) * s.table_ts;
-    const uint32_t p0 = (more && x0 < s.kmax1) ? gnext[x0] : 0u;
-    const uint32_t p1 = (more && x1 < s.kmax1) ? gnext[x1] : 0u;
-    if (!PREFETCH) sweep_prefix(t);
+    // thresholds of sweep t + 1 (staged: t + 2) into registers now, into the
+    // free row buffer at the end of the sweep (kmax1 <= 64 <= 2 x threads)
+    constexpr int ahead = STAGED ? 2 : 1;
+    const bool more_a = t + ahead < t_end;
+    const uint32_t *gnext = wtab + (size_t)(t + ahead) * s.table_ts;
+    const uint32_t p0 = (more_a && x0 < s.kmax1) ? gnext[x0] : 0u;
+    const uint32_t p1 = (more_a && x1 < s.kmax1) ? gnext[x1] : 0u;
+    if (!PREFETCH && !STAGED) sweep_prefix(t);
+    if (STAGED && more) sweep_prefix(t + 1);  // for the masks of sweep t + 1
+    const uint32_t *mcur = lmask + (size_t)(t & 1) * (STAGED ? L.own_lv : 0);
     SlicedCounter<NP> cd, cu;
     cd.clear();
     cu.clear();
@@ -410,7 +552,7 @@ __device__ void gm_word(const GraphMscSolve &s, const GraphMscLaunch &L, int wor
         if (STAGED) {
           p0 = adj.row[i];
           p1 = adj.row[i + 1];
-          og = adj.orig[i];
+          og = 0;  // the masks are already built
         } else {
           p0 = n0;
           p1 = n1;
@@ -430,10 +572,11 @@ __device__ void gm_word(const GraphMscSolve &s, const GraphMscLaunch &L, int wor
         }
         const int32_t hv = !has_field ? 0 : (STAGED ? lfield[i] : __ldg(&s.field[v]));
         auto draw = [&](uint4 (&out)[8]) { vertex_uniforms((uint32_t)og, bp, s.rk, out); };
-        if (PREFETCH && !ready) vertex_uniforms((uint32_t)og, bp, s.rk, uu);
+        if (PF && !ready) vertex_uniforms((uint32_t)og, bp, s.rk, uu);
         ready = false;
-        const uint32_t sn =
-            update_vertex<NP, FIELD, !PREFETCH>(spin, v, p0, p1, adj, row, uu, draw, hv, cd, cu);
+        constexpr int accept = STAGED ? kAcceptMasks : (PF ? kAcceptPre : kAcceptLazy);
+        const uint32_t sn = update_vertex<NP, FIELD, accept>(
+            spin, v, p0, p1, adj, row, uu, draw, STAGED ? mcur + lmoff[i] : nullptr, hv, cd, cu);
         if (K == 1) {
           spin[v] = sn;
         } else {
@@ -444,11 +587,12 @@ __device__ void gm_word(const GraphMscSolve &s, const GraphMscLaunch &L, int wor
       if (c + 1 < nc) {
         group_arrive(K);
         draw_first(c + 1);
+        if (STAGED && more) mask_window(c, t + 1);
         group_wait(K);
       }
     }
-    if (more) {
-      uint32_t *nrow = trow + ((t + 1) & 1) * s.kmax1;
+    if (more_a) {
+      uint32_t *nrow = trow + ((t + ahead) & 1) * s.kmax1;
       if (x0 < s.kmax1) nrow[x0] = p0;
       if (x1 < s.kmax1) nrow[x1] = p1;
     }
@@ -466,11 +610,13 @@ __device__ void gm_word(const GraphMscSolve &s, const GraphMscLaunch &L, int wor
       }
     }
     group_arrive(K);
-    if (PREFETCH && more) {
+    if (PF && more) {
       sweep_prefix(t + 1);
       draw_first(0);
     }
+    if (STAGED && more) mask_window(nc - 1, t + 1);
     group_wait(K);
+    if (STAGED && nc == 1) __syncthreads();  // one class: its masks were built just now
     int32_t dsum = 0;
     for (int r = 0; r < K; ++r) dsum += pbuf[r * 32 + lane];
     e += dsum;
@@ -555,7 +701,7 @@ template <bool FIELD>
 cudaError_t gm_launch_impl(const GraphMscSolve &s, const GraphMscLaunch &l, cudaStream_t stream) {
   const bool staged = l.own_n > 0;
   const size_t smem = gm_layout(s.n, l.cluster, s.n_colours, staged ? l.own_n : 0,
-                                staged ? l.own_nnz : 0, s.kmax1, FIELD)
+                                staged ? l.own_nnz : 0, staged ? l.own_lv : 0, s.kmax1, FIELD)
                           .total;
   const int grid = s.words * l.cluster;
   switch (l.planes * 2 + (staged ? 1 : 0)) {

@@ -75,7 +75,7 @@ int kind_of(const isg_problem *p, int threads) {
 size_t unit_smem(const isg_problem *p, int kind) {
   if (kind == kTorusKind) return torus_batch_max_smem(p->L, p->W);
   if (kind == kGraphWordKind)
-    return gm_smem_bytes(p->n, 1, p->n_colours, 0, 0, p->kmax + 1, !p->field.empty());
+    return gm_smem_bytes(p->n, 1, p->n_colours, 0, 0, 0, p->kmax + 1, !p->field.empty());
   return csr_smem_bytes(p->n, 1, 1, p->n_colours, 0, 0, p->mode, p->kmax);
 }
 

@@ -186,6 +186,7 @@ struct GraphMscLaunch {
   int32_t cluster;             // CTAs sharing one word (each holds a full copy)
   int32_t threads;
   int32_t own_n, own_nnz;      // largest owned slice of any rank; 0 = adjacency not staged
+  int32_t own_lv;              // staged: largest owned sum of threshold levels (d + |h| + 1) / 2
   int32_t planes;              // bit planes of the energy counters (6..14)
 };
 
@@ -201,9 +202,10 @@ struct GraphMscItem {
   int32_t stop_from_hits;      // as TorusBatchItem::stop_from_hits
 };
 
-// fields: the instance has local fields (staged slices then hold them too).
+// fields: the instance has local fields (staged slices then hold them too);
+// own_lv sizes the staged kernel's mask table (0 when not staged).
 size_t gm_smem_bytes(int32_t n, int32_t cluster, int32_t n_colours, int32_t own_n,
-                     int32_t own_nnz, int32_t kmax1, bool fields);
+                     int32_t own_nnz, int32_t own_lv, int32_t kmax1, bool fields);
 // Smallest supported plane count holding counts up to max_count (-1: none).
 int gm_planes(int32_t max_count);
 cudaError_t gm_launch(const GraphMscSolve &s, const GraphMscLaunch &l, cudaStream_t stream);

@@ -572,6 +572,25 @@ void csr_own_sizes(const isg_problem *p, int K, int &own_n, int &own_nnz) {
   }
 }
 
+// Mask table of the staged graph kernel: the largest sum over any rank's owned
+// vertices of their threshold levels (d + |h| + 1) / 2 (one mask word each).
+int gm_own_levels(const isg_problem *p, int K) {
+  int own_lv = 0;
+  for (int k = 0; k < K; ++k) {
+    int64_t lv = 0;
+    for (int32_t c = 0; c < p->n_colours; ++c) {
+      const int64_t a = p->class_start[c], len = p->class_start[c + 1] - a;
+      const int64_t lo = a + len * k / K, hi = a + len * (k + 1) / K;
+      for (int64_t v = lo; v < hi; ++v) {
+        const int64_t h = p->field_r.empty() ? 0 : std::abs((int64_t)p->field_r[v]);
+        lv += (p->rowptr_r[v + 1] - p->rowptr_r[v] + h + 1) / 2;
+      }
+    }
+    own_lv = std::max<int>(own_lv, (int)lv);
+  }
+  return own_lv;
+}
+
 // Shared memory of the colour-class kernel; staged = adjacency in shared memory.
 size_t csr_bytes(const isg_problem *p, int qpc, int K, bool staged) {
   int own_n = 0, own_nnz = 0;
@@ -594,9 +613,13 @@ bool graph_msc_ok(const isg_problem *p) {
 
 // Shared memory of the graph kernel; staged = adjacency in shared memory.
 size_t gm_bytes(const isg_problem *p, int K, bool staged) {
-  int own_n = 0, own_nnz = 0;
-  if (staged) csr_own_sizes(p, K, own_n, own_nnz);
-  return gm_smem_bytes(p->n, K, p->n_colours, own_n, own_nnz, p->kmax + 1, !p->field.empty());
+  int own_n = 0, own_nnz = 0, own_lv = 0;
+  if (staged) {
+    csr_own_sizes(p, K, own_n, own_nnz);
+    own_lv = gm_own_levels(p, K);
+  }
+  return gm_smem_bytes(p->n, K, p->n_colours, own_n, own_nnz, own_lv, p->kmax + 1,
+                       !p->field.empty());
 }
 
 // Energy-counter planes of the graph kernel: a thread's accepted degree sum
@@ -717,11 +740,14 @@ cudaError_t launch_sweeps(const isg_problem *p, const DeviceProblem *dp, isg_res
                           int t_start = 0) {
   cudaError_t err = cudaSuccess;
   const bool gm = r->msc && r->relabelled;
-  int own_n = 0, own_nnz = 0, planes = 0;
+  int own_n = 0, own_nnz = 0, own_lv = 0, planes = 0;
   if (!r->msc && csr_bytes(p, qpc, cluster, true) <= 227 * 1024)
     csr_own_sizes(p, cluster, own_n, own_nnz);
   if (gm) {
-    if (gm_bytes(p, cluster, true) <= 227 * 1024) csr_own_sizes(p, cluster, own_n, own_nnz);
+    if (gm_bytes(p, cluster, true) <= 227 * 1024) {
+      csr_own_sizes(p, cluster, own_n, own_nnz);
+      own_lv = gm_own_levels(p, cluster);
+    }
     planes = gm_planes_for(p, cluster, threads);
     if (planes < 0) return cudaErrorInvalidConfiguration;
   }
@@ -742,6 +768,7 @@ cudaError_t launch_sweeps(const isg_problem *p, const DeviceProblem *dp, isg_res
         l.threads = threads;
         l.own_n = own_n;
         l.own_nnz = own_nnz;
+        l.own_lv = own_lv;
         l.planes = planes;
         err = gm_launch(s, l, stream);
       } else if (r->msc) {
@@ -1181,7 +1208,7 @@ isg_status tempering_impl(const isg_problem *p, int32_t K, const double *betas, 
     cluster = t_cluster;
     threads = t_threads;
   }
-  int own_n = 0, own_nnz = 0, planes = 0;
+  int own_n = 0, own_nnz = 0, own_lv = 0, planes = 0;
   // int8 kernel: 8 quads per slot; a CTA's 1 or 2 quads lie in one slot
   const int qpc = quad ? (o.quads_per_cta > 0 ? o.quads_per_cta : 1) : 1;
   if (quad) {
@@ -1203,7 +1230,10 @@ isg_status tempering_impl(const isg_problem *p, int32_t K, const double *betas, 
     planes = gm_planes_for(p, cluster, threads);
     if (planes < 0)
       return fail(ISG_EINVAL, "too many vertices per thread for the graph kernel's counters");
-    if (gm_bytes(p, cluster, true) <= 227 * 1024) csr_own_sizes(p, cluster, own_n, own_nnz);
+    if (gm_bytes(p, cluster, true) <= 227 * 1024) {
+      csr_own_sizes(p, cluster, own_n, own_nnz);
+      own_lv = gm_own_levels(p, cluster);
+    }
   }
 
   const DeviceProblem *dp = nullptr;
@@ -1351,6 +1381,7 @@ isg_status tempering_impl(const isg_problem *p, int32_t K, const double *betas, 
         l.threads = threads;
         l.own_n = own_n;
         l.own_nnz = own_nnz;
+        l.own_lv = own_lv;
         l.planes = planes;
         e = gm_launch(gs, l, st);
       }

@@ -411,7 +411,7 @@ cudaError_t run_units(isg_server *s, const std::vector<Slot *> &slots,
       } else if (sl->res->msc) {
         fill_gm_unit(s->h_g[ig], sl, u, sl->t, t_end[k]);
         ord_g.emplace_back(p->n, (int32_t)ig++);
-        smem_g = std::max(smem_g, gm_smem_bytes(p->n, 1, p->n_colours, 0, 0, p->kmax + 1,
+        smem_g = std::max(smem_g, gm_smem_bytes(p->n, 1, p->n_colours, 0, 0, 0, p->kmax + 1,
                                                 !p->field.empty()));
       } else {
         fill_csr_unit(s->h_c[ic], sl, u, sl->t, t_end[k]);

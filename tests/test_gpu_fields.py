@@ -77,6 +77,40 @@ def test_fields_graph_msc_bit_exact(isg, name, R, cluster, threads):
     assert res.stats()["kernel"] == 4 and res.stats()["staged"] == 1
 
 
+def star_forest_with_fields():
+    """20 stars of 8 leaves among 220 isolated vertices, all weights +1, fields
+    |h| <= 3.  Leaves (ids 0-159) and isolated vertices (180-399) form the first
+    greedy colour class, the hubs (160-179) the second: almost every vertex is
+    updated in the first class."""
+    hub = np.repeat(np.arange(160, 180, dtype=np.int32), 8)
+    leaf = np.arange(160, dtype=np.int32)
+    h = np.array([(2, -1, 0, 3, -3, 1, -2)[i % 7] for i in range(400)], np.int32)
+    return I.Graph(400, leaf, hub, np.ones(160, np.int32), h)
+
+
+def edgeless_with_fields():
+    """No edges, fields |h| <= 4: one colour class."""
+    h = np.array([(4, -1, 2, 0, -3, 1)[i % 6] for i in range(300)], np.int32)
+    z = np.zeros(0, np.int32)
+    return I.Graph(300, z, z, z, h)
+
+
+@pytest.mark.parametrize("make", [star_forest_with_fields, edgeless_with_fields])
+@pytest.mark.parametrize("R,cluster,threads", [(40, 1, 64), (40, 4, 128), (70, 8, 96)])
+def test_graph_msc_mask_windows_bit_exact(isg, make, R, cluster, threads):
+    """The staged graph kernel builds each vertex's acceptance masks for sweep
+    t + 1 during sweep t, shared out over the class barrier windows: a first
+    class holding nearly every vertex, and a single class, where the sweep's
+    last window and the next sweep's first class meet."""
+    g = make()
+    betas = I.geometric_betas(0.1, 5.0, 90)
+    orc = oracle.anneal(oracle.csr_of(g), R, betas, 29, check_energy=True)
+    res = isg.isg_anneal(isg.problem_of(g), R, betas, 29, kernel=4, cluster_ctas=cluster,
+                         threads=threads)
+    assert res.stats()["kernel"] == 4 and res.stats()["staged"] == 1
+    assert_same(res, orc)
+
+
 @pytest.mark.parametrize("R,cluster,threads", [(40, 1, 256), (70, 4, 512)])
 def test_fields_graph_msc_unstaged_bit_exact(isg, R, cluster, threads):
     """Fields read from global memory: 12,000 vertices of mean degree 25 with
