@@ -275,20 +275,11 @@ __device__ __forceinline__ void group_wait(int K) {
     __syncthreads();
 }
 
-// Threads with no vertex to update in class c nor in the class after its
-// window (the next sweep's first class after the last): those numbered at
-// least the larger slice length.
-__device__ __forceinline__ int window_idle(const int32_t *clo, const int32_t *chi, int c, int nc,
-                                           int B) {
-  const int nn = c + 1 < nc ? c + 1 : 0;
-  return max(B - max(chi[c] - clo[c], chi[nn] - clo[nn]), 0);
-}
 
 // STAGED (adjacency of the owned slices in shared memory): the acceptance
-// masks of every owned vertex for sweep t + 1 are built during sweep t, a
-// share in each class's barrier window (by threads idle in that class and the
-// next, as far as they go), into a table of two sweeps; the update then reads
-// masks instead of drawing uniforms.  Otherwise, PREFETCH: draw the next
+// masks of every owned vertex for sweep t + 1 are built during sweep t, an
+// even share in each class's barrier window, into a table of two sweeps; the
+// update then reads masks instead of drawing uniforms.  Otherwise, PREFETCH: draw the next
 // phase's first uniforms during the group barrier (off in the unit kernel,
 // whose CTA-wide barrier leaves nothing to overlap).
 template <int NP, bool STAGED, bool FIELD, bool PREFETCH = true>
@@ -338,18 +329,10 @@ __device__ void gm_word(const GraphMscSolve &s, const GraphMscLaunch &L, int wor
       ov += hi - lo;
     }
     if (STAGED) {
-      // the owned slots' mask work over the class windows: in proportion to
-      // the threads idle across each window while they can take it all, else
-      // one item per idle thread and the rest spread evenly
-      int64_t idle = 0;
-      for (int c = 0; c < nc; ++c) idle += window_idle(clo, chi, c, nc, B);
-      const int extra = idle >= ov ? 0 : ov - (int)idle;
-      int64_t acc = 0;
-      for (int c = 0; c < nc; ++c) {
-        qlo[c] = (extra || idle == 0) ? (int)acc : (int)(ov * acc / idle);
-        acc += window_idle(clo, chi, c, nc, B);
-        if (extra) acc += extra / nc + (c < extra % nc ? 1 : 0);
-      }
+      // the owned slots' mask work, an even share per class window (measured
+      // faster than shares weighted by the threads idle in the window's
+      // classes: those put two items in a row on some threads)
+      for (int c = 0; c < nc; ++c) qlo[c] = (int)((int64_t)ov * c / nc);
       qlo[nc] = ov;
       // a thread builds its share of the last window after arriving at the
       // sweep's last barrier, so the next barrier it reaches lies after the
