@@ -170,6 +170,47 @@ def test_graph_msc_bit_exact(isg, name, R, cluster, threads):
     assert st["kernel"] == 4 and st["staged"] == 1  # words sent only where they are read
 
 
+def hub_graph():
+    """A 400-vertex random graph plus a hub (vertex 0) of degree 63, the most the
+    multi-spin graph kernel takes: 32 threshold levels on one vertex word."""
+    g = I.random_graph(400, 600, 21)
+    pairs = {(int(a), int(b)) for a, b in zip(g.u, g.v)}
+    pairs = {(a, b) for a, b in pairs if a != 0 and b != 0}
+    nbrs = range(7, 7 + 6 * 63, 6)
+    pairs |= {(0, j) for j in nbrs}
+    u, v = zip(*sorted(pairs))
+    return I.Graph(400, np.array(u, np.int32), np.array(v, np.int32), np.ones(len(u), np.int32))
+
+
+def dense_pm1_graph():
+    """300 vertices, 3,000 edges of weight +-1 (mean degree 20)."""
+    g = I.random_graph(300, 3000, 22)
+    w = np.where(I.draws(22, 7, np.arange(g.m)) >> np.uint64(63), 1, -1).astype(np.int32)
+    return I.Graph(g.n, g.u, g.v, w)
+
+
+def many_colours_graph():
+    """200 vertices, 2,500 edges: about ten greedy colour classes."""
+    return I.random_graph(200, 2500, 23)
+
+
+@pytest.mark.parametrize("make", [hub_graph, dense_pm1_graph, many_colours_graph])
+@pytest.mark.parametrize("R,cluster,threads", [(45, 2, 32), (32, 5, 96), (70, 3, 224),
+                                               (33, 12, 512)])
+def test_graph_msc_mask_table_shapes_bit_exact(isg, make, R, cluster, threads):
+    """The staged graph kernel's table of acceptance masks (one word per
+    threshold level of every owned vertex, built a sweep ahead): high degrees,
+    many levels and classes, small and large CTAs, ragged replica counts."""
+    g = make()
+    betas = I.geometric_betas(0.1, 5.0, 60)
+    orc = oracle.anneal(oracle.csr_of(g), R, betas, 37, check_energy=True)
+    res = isg.isg_anneal(isg.problem_of(g), R, betas, 37, kernel=4, cluster_ctas=cluster,
+                         threads=threads)
+    st = res.stats()
+    assert st["kernel"] == 4 and st["staged"] == 1
+    assert_same(res, orc)
+
+
 @pytest.mark.parametrize("R,cluster,threads", [(40, 1, 256), (70, 4, 512)])
 def test_graph_msc_unstaged_bit_exact(isg, R, cluster, threads):
     """Adjacency too large for shared memory (12,000 vertices, mean degree 25):
