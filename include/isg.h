@@ -370,8 +370,8 @@ typedef struct {
                                 and the instance arrays uploaded for it (0 if resident) */
     int32_t staged;          /* colour-class kernels: 1 if each CTA holds the adjacency of the
                                 vertices it updates in shared memory (the multi-spin graph
-                                kernel then sends a new word only to the cluster CTAs that
-                                update one of the vertex's neighbours), else 0 */
+                                kernel then also keeps its vertices' acceptance masks for the
+                                next sweep there), else 0 */
     int32_t first_replica;   /* isg_options.first_replica of the solve (0 for other forms) */
 } isg_stats;
 

@@ -167,7 +167,7 @@ def test_graph_msc_bit_exact(isg, name, R, cluster, threads):
                          threads=threads)
     assert_same(res, orc)
     st = res.stats()
-    assert st["kernel"] == 4 and st["staged"] == 1  # words sent only where they are read
+    assert st["kernel"] == 4 and st["staged"] == 1  # adjacency and mask table in shared memory
 
 
 def hub_graph():
