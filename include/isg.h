@@ -169,6 +169,18 @@ typedef struct {
                               any devices together equal one solve of all their replicas
                               (a replica-sharded solve; a target applies to this call's
                               replicas only).  Results stay indexed 0..R-1 locally. */
+    int32_t mask_chunk;    /* multi-spin graph kernel with its adjacency in shared memory
+                              (isg_stats.staged), solves without a target: the acceptance
+                              masks (32 uniforms against each threshold level of a vertex)
+                              are built either inside the sweep kernel (-1) or for chunks
+                              of up to mask_chunk sweeps (> 0) by a second kernel, on
+                              device memory and the SMs the sweep kernel leaves idle, on a
+                              low-priority stream one chunk ahead of the sweep kernel,
+                              when the tables of two chunks fit 1 GiB of device memory
+                              (else inside the kernel).  The results are the same.
+                              0 = automatic: precomputed in chunks of at most 96 MiB of
+                              masks (a chunk table that stays in L2), when such a chunk
+                              holds at least 64 sweeps.  EINVAL below -1. */
 } isg_options;
 
 /* Anneal R = replicas independent chains for S = sweeps sweeps at inverse
@@ -373,6 +385,8 @@ typedef struct {
                                 kernel then also keeps its vertices' acceptance masks for the
                                 next sweep there), else 0 */
     int32_t first_replica;   /* isg_options.first_replica of the solve (0 for other forms) */
+    int32_t mask_chunks;     /* chunks of precomputed acceptance masks (isg_options.mask_chunk);
+                                0: built inside the sweep kernel */
 } isg_stats;
 
 isg_status isg_result_stats(const isg_result *r, isg_stats *stats);

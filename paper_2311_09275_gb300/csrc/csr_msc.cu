@@ -1,6 +1,7 @@
 // csr_msc.cu -- host entry points of the multi-spin-coded colour-class sweep
 // (kernels in csr_msc.cuh): shared-memory sizes, counter planes, launches
-// without local fields, and the persistent unit kernel.
+// without local fields, the persistent unit kernel, and the kernel that
+// precomputes acceptance masks for the staged sweep kernel.
 #include "csr_msc.cuh"
 
 namespace isg {
@@ -37,6 +38,38 @@ __global__ void __launch_bounds__(512) gm_batch_kernel(const GraphMscItem *items
   }
 }
 
+// Acceptance masks of sweeps [t0, t0 + nt) for every replica word and vertex,
+// for the staged graph kernel to read instead of drawing them: one CTA per
+// (sweep, word), masks of vertex v (relabelled) at out[(sweep - t0, word)
+// table of gl words][gloff[v] + level], one word per threshold level
+// (d + |h| + 1) / 2, as the sweep kernel builds them itself.
+__global__ void __launch_bounds__(256) gm_mask_kernel(GraphMscSolve s, const int32_t *gloff,
+                                                      int64_t gl, int32_t t0, uint32_t *out) {
+  const int w = (int)(blockIdx.x % (unsigned)s.words);
+  const int tt = (int)(blockIdx.x / (unsigned)s.words);
+  const int t = t0 + tt;
+  const uint32_t uword = (uint32_t)(w + s.rng_word0);
+  BlockPrefix bp[8];
+#pragma unroll
+  for (int q = 0; q < 8; ++q) bp[q] = block_prefix(8u * uword + (uint32_t)q, (uint32_t)t, s.rk);
+  const uint32_t *row = s.table + (size_t)w * s.table_ws + (size_t)t * s.table_ts;
+  uint32_t *o = out + ((int64_t)tt * s.words + w) * gl;
+  for (int v = threadIdx.x; v < s.n; v += blockDim.x) {
+    int d = s.rowptr[v + 1] - s.rowptr[v];
+    if (s.field) d += abs(s.field[v]);
+    const int levels = (d + 1) / 2;
+    if (levels == 0) continue;
+    uint4 u[8];
+    vertex_uniforms((uint32_t)s.orig[v], bp, s.rk, u);
+    const uint32_t umin = uniform_min(u);
+    uint32_t *ov = o + gloff[v];
+    for (int lv = 0; lv < levels; ++lv) {
+      const uint32_t T = __ldg(row + d - 2 * lv);
+      ov[lv] = T > umin ? uniforms_below(u, T) : 0u;
+    }
+  }
+}
+
 }  // namespace
 
 size_t gm_smem_bytes(int32_t n, int32_t cluster, int32_t n_colours, int32_t own_n,
@@ -52,6 +85,14 @@ int gm_planes(int32_t max_count) {
 
 cudaError_t gm_launch(const GraphMscSolve &s, const GraphMscLaunch &l, cudaStream_t stream) {
   return s.field ? gm_launch_fields(s, l, stream) : gm_launch_impl<false>(s, l, stream);
+}
+
+cudaError_t gm_mask_launch(const GraphMscSolve &s, const int32_t *gloff_dev, int64_t gl, int32_t t0,
+                           int32_t nt, uint32_t *out_dev, cudaStream_t stream) {
+  const int64_t grid = (int64_t)nt * s.words;
+  if (nt < 1 || grid > INT32_MAX) return cudaErrorInvalidValue;
+  gm_mask_kernel<<<(unsigned)grid, 256, 0, stream>>>(s, gloff_dev, gl, t0, out_dev);
+  return cudaGetLastError();
 }
 
 cudaError_t gm_batch_launch(const GraphMscItem *items_dev, const int32_t *count_dev,

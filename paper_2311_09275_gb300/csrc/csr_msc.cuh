@@ -161,6 +161,17 @@ __device__ __forceinline__ uint32_t field_unsat(uint32_t s0, int32_t hv) {
   return hv > 0 ? s0 : ~s0;
 }
 
+// 4-byte asynchronous copy from global to shared memory (both 4-byte
+// aligned), completed by cp_async_wait_all in the issuing thread.
+__device__ __forceinline__ void cp_async4(uint32_t *dst_smem, const uint32_t *src_gmem) {
+  const uint32_t d = (uint32_t)__cvta_generic_to_shared(dst_smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(d), "l"(src_gmem) : "memory");
+}
+
+__device__ __forceinline__ void cp_async_wait_all() {
+  asm volatile("cp.async.wait_all;\n" ::: "memory");
+}
+
 // Acceptance sources of update_vertex.
 enum GmAccept { kAcceptPre = 0, kAcceptLazy = 1, kAcceptMasks = 2 };
 
@@ -279,13 +290,17 @@ __device__ __forceinline__ void group_wait(int K) {
 // STAGED (adjacency of the owned slices in shared memory): the acceptance
 // masks of every owned vertex for sweep t + 1 are built during sweep t, an
 // even share in each class's barrier window, into a table of two sweeps; the
-// update then reads masks instead of drawing uniforms.  Otherwise, PREFETCH: draw the next
+// update then reads masks instead of drawing uniforms.  PRE (staged, masks
+// precomputed in device memory by gm_mask_kernel, at L.gmask): each thread
+// instead copies a few of the next sweep's mask words into the table
+// asynchronously, awaited before the sweep's last barrier.  Otherwise, PREFETCH: draw the next
 // phase's first uniforms during the group barrier (off in the unit kernel,
 // whose CTA-wide barrier leaves nothing to overlap).
-template <int NP, bool STAGED, bool FIELD, bool PREFETCH = true>
+template <int NP, bool STAGED, bool FIELD, bool PREFETCH = true, bool PRE = false>
 __device__ void gm_word(const GraphMscSolve &s, const GraphMscLaunch &L, int word, int k, int K,
                         int t_begin, int t_end, int resume, uint8_t *smem) {
   constexpr bool PF = PREFETCH && !STAGED;
+  constexpr bool MG = STAGED && PRE;
   const int n = s.n;
   const int nc = s.n_colours;
   const int B = (int)blockDim.x;
@@ -491,10 +506,26 @@ __device__ void gm_word(const GraphMscSolve &s, const GraphMscLaunch &L, int wor
     uint32_t *mout = lmask + (size_t)(tt & 1) * L.own_lv;
     for (int j = qlo[c] + B - 1 - (int)threadIdx.x; j < qlo[c + 1]; j += B) masks_of(j, mrow, mout);
   };
+  // precomputed masks: word q of the owned table (class-major over the owned
+  // slices, like the slots) sits at src(q) in a sweep's table of all vertices
+  const int own_words = STAGED ? lmoff[qlo[nc]] : 0;
+  auto src_of = [&](int q) {
+    int c = 0;
+    while (c + 1 < nc && q >= lmoff[cob[c + 1]]) ++c;
+    return L.gloff[clo[c]] + (q - lmoff[cob[c]]);
+  };
+  auto gmask_of = [&](int tt) {
+    return L.gmask + ((int64_t)(tt - L.gmask_t0) * s.words + word) * L.gmask_gl;
+  };
   if (STAGED && t_begin < t_end) {
-    sweep_prefix(t_begin);
-    for (int j = threadIdx.x; j < qlo[nc]; j += B)
-      masks_of(j, trow + (t_begin & 1) * s.kmax1, lmask + (size_t)(t_begin & 1) * L.own_lv);
+    uint32_t *m0 = lmask + (size_t)(t_begin & 1) * L.own_lv;
+    if (MG) {
+      const uint32_t *g = gmask_of(t_begin);
+      for (int q = threadIdx.x; q < own_words; q += B) m0[q] = g[src_of(q)];
+    } else {
+      sweep_prefix(t_begin);
+      for (int j = threadIdx.x; j < qlo[nc]; j += B) masks_of(j, trow + (t_begin & 1) * s.kmax1, m0);
+    }
     __syncthreads();
   }
 
@@ -513,7 +544,14 @@ __device__ void gm_word(const GraphMscSolve &s, const GraphMscLaunch &L, int wor
     const uint32_t p0 = (more_a && x0 < s.kmax1) ? gnext[x0] : 0u;
     const uint32_t p1 = (more_a && x1 < s.kmax1) ? gnext[x1] : 0u;
     if (!PREFETCH && !STAGED) sweep_prefix(t);
-    if (STAGED && more) sweep_prefix(t + 1);  // for the masks of sweep t + 1
+    if (STAGED && more && !MG) sweep_prefix(t + 1);  // for the masks of sweep t + 1
+    if (MG && more) {
+      // precomputed masks of sweep t + 1: asynchronous copies into the table
+      // buffer this sweep does not read, awaited before the sweep's last barrier
+      const uint32_t *g = gmask_of(t + 1);
+      uint32_t *mn = lmask + (size_t)((t + 1) & 1) * L.own_lv;
+      for (int q = threadIdx.x; q < own_words; q += B) cp_async4(mn + q, g + src_of(q));
+    }
     const uint32_t *mcur = lmask + (size_t)(t & 1) * (STAGED ? L.own_lv : 0);
     SlicedCounter<NP> cd, cu;
     cd.clear();
@@ -570,7 +608,7 @@ __device__ void gm_word(const GraphMscSolve &s, const GraphMscLaunch &L, int wor
       if (c + 1 < nc) {
         group_arrive(K);
         draw_first(c + 1);
-        if (STAGED && more) mask_window(c, t + 1);
+        if (STAGED && more && !MG) mask_window(c, t + 1);
         group_wait(K);
       }
     }
@@ -579,6 +617,7 @@ __device__ void gm_word(const GraphMscSolve &s, const GraphMscLaunch &L, int wor
       if (x0 < s.kmax1) nrow[x0] = p0;
       if (x1 < s.kmax1) nrow[x1] = p1;
     }
+    if (MG && more) cp_async_wait_all();
     // per-lane energy change, summed over the CTA and published to every CTA
     int32_t *pbuf = part + ((t + 1) & 1) * 32 * K;
     atomicAdd(&lane_acc[lane], 2 * (cd.warp_lane_total() - 2 * cu.warp_lane_total()));
@@ -597,9 +636,9 @@ __device__ void gm_word(const GraphMscSolve &s, const GraphMscLaunch &L, int wor
       sweep_prefix(t + 1);
       draw_first(0);
     }
-    if (STAGED && more) mask_window(nc - 1, t + 1);
+    if (STAGED && more && !MG) mask_window(nc - 1, t + 1);
     group_wait(K);
-    if (STAGED && nc == 1) __syncthreads();  // one class: its masks were built just now
+    if (STAGED && nc == 1 && !MG) __syncthreads();  // one class: its masks were built just now
     int32_t dsum = 0;
     for (int r = 0; r < K; ++r) dsum += pbuf[r * 32 + lane];
     e += dsum;
@@ -639,7 +678,7 @@ __device__ void gm_word(const GraphMscSolve &s, const GraphMscLaunch &L, int wor
   }
 }
 
-template <int NP, bool STAGED, bool FIELD>
+template <int NP, bool STAGED, bool FIELD, bool PRE = false>
 __global__ void __launch_bounds__(512) gm_kernel(GraphMscSolve s, GraphMscLaunch l) {
   extern __shared__ __align__(16) uint8_t smem[];
   const int K = l.cluster;
@@ -652,7 +691,7 @@ __global__ void __launch_bounds__(512) gm_kernel(GraphMscSolve s, GraphMscLaunch
       if (s.hit[w] >= 0 && s.hit[w] < m) m = s.hit[w];
     if (m != INT_MAX && m + 1 < t_end) t_end = m + 1;
   }
-  gm_word<NP, STAGED, FIELD>(s, l, word, k, K, l.t_begin, t_end, l.resume, smem);
+  gm_word<NP, STAGED, FIELD, true, PRE>(s, l, word, k, K, l.t_begin, t_end, l.resume, smem);
 }
 
 template <typename Kern>
@@ -687,11 +726,14 @@ cudaError_t gm_launch_impl(const GraphMscSolve &s, const GraphMscLaunch &l, cuda
                                 staged ? l.own_nnz : 0, staged ? l.own_lv : 0, s.kmax1, FIELD)
                           .total;
   const int grid = s.words * l.cluster;
-  switch (l.planes * 2 + (staged ? 1 : 0)) {
+  const bool pre = staged && l.gmask != nullptr;
+  switch (l.planes * 4 + (staged ? 1 : 0) + (pre ? 2 : 0)) {
 #define ISG_GM_CASE(NPV)                                                                     \
-  case NPV * 2 + 1:                                                                          \
+  case NPV * 4 + 3:                                                                          \
+    return launch_gm(gm_kernel<NPV, true, FIELD, true>, grid, s, l, smem, stream);           \
+  case NPV * 4 + 1:                                                                          \
     return launch_gm(gm_kernel<NPV, true, FIELD>, grid, s, l, smem, stream);                 \
-  case NPV * 2:                                                                              \
+  case NPV * 4:                                                                              \
     return launch_gm(gm_kernel<NPV, false, FIELD>, grid, s, l, smem, stream);
     ISG_GM_CASE(6) ISG_GM_CASE(8) ISG_GM_CASE(10) ISG_GM_CASE(12) ISG_GM_CASE(14)
 #undef ISG_GM_CASE

@@ -188,6 +188,13 @@ struct GraphMscLaunch {
   int32_t own_n, own_nnz;      // largest owned slice of any rank; 0 = adjacency not staged
   int32_t own_lv;              // staged: largest owned sum of threshold levels (d + |h| + 1) / 2
   int32_t planes;              // bit planes of the energy counters (6..14)
+  // staged: acceptance masks of sweeps [gmask_t0, t_end) precomputed by
+  // gm_mask_launch ([sweep - gmask_t0][word][gmask_gl] words, vertex v's at
+  // gloff[v]), or nullptr to build them in the kernel
+  const uint32_t *gmask;
+  const int32_t *gloff;        // [n + 1] prefix of the levels in relabelled order
+  int64_t gmask_gl;            // gloff[n]
+  int32_t gmask_t0;
 };
 
 // Bit planes of the persistent unit kernel's energy counters: a unit's
@@ -209,6 +216,10 @@ size_t gm_smem_bytes(int32_t n, int32_t cluster, int32_t n_colours, int32_t own_
 // Smallest supported plane count holding counts up to max_count (-1: none).
 int gm_planes(int32_t max_count);
 cudaError_t gm_launch(const GraphMscSolve &s, const GraphMscLaunch &l, cudaStream_t stream);
+// Acceptance masks of sweeps [t0, t0 + nt) of every word of the solve into
+// out_dev ([nt][words][gl] uint32, the layout GraphMscLaunch::gmask reads).
+cudaError_t gm_mask_launch(const GraphMscSolve &s, const int32_t *gloff_dev, int64_t gl, int32_t t0,
+                           int32_t nt, uint32_t *out_dev, cudaStream_t stream);
 cudaError_t gm_batch_launch(const GraphMscItem *items_dev, const int32_t *count_dev,
                             const int32_t *order_dev, int32_t *next_dev, int32_t ctas,
                             int32_t threads, size_t smem, cudaStream_t stream);

@@ -285,6 +285,7 @@ void free_device(isg_problem *p) {
     cudaFree(d.wt_o);
     cudaFree(d.field_r);
     cudaFree(d.field_o);
+    cudaFree(d.gloff);
     cudaSetDevice(prev);
   }
   p->dev.clear();
@@ -337,8 +338,19 @@ isg_status problem_device(const isg_problem *cp, unsigned need, const DeviceProb
     if (err == cudaSuccess) err = upload(&d->orig, p->order.data(), p->order.size());
     if (err == cudaSuccess && !p->field_r.empty())
       err = upload(&d->field_r, p->field_r.data(), p->field_r.size());
+    // the staged graph kernel's precomputed masks: one word per threshold level
+    std::vector<int32_t> gloff(p->n + 1, 0);
+    int64_t gl = 0;
+    for (int32_t v = 0; v < p->n; ++v) {
+      gloff[v] = (int32_t)std::min<int64_t>(gl, INT32_MAX);
+      const int64_t h = p->field_r.empty() ? 0 : std::abs((int64_t)p->field_r[v]);
+      gl += (p->rowptr_r[v + 1] - p->rowptr_r[v] + h + 1) / 2;
+    }
+    gloff[p->n] = (int32_t)std::min<int64_t>(gl, INT32_MAX);
+    d->gl = gl;
+    if (err == cudaSuccess) err = upload(&d->gloff, gloff.data(), gloff.size());
     bytes += 4 * (p->class_start.size() + p->rowptr_r.size() + p->col_r.size() +
-                  p->wt_r.size() + p->order.size() + p->field_r.size());
+                  p->wt_r.size() + p->order.size() + p->field_r.size() + gloff.size());
     if (err == cudaSuccess) d->have |= kNeedCsr;
   }
   if (err == cudaSuccess && (need & kNeedEnergy) && !(d->have & kNeedEnergy)) {
@@ -477,6 +489,10 @@ void result_free(isg_result *r) {
   if (r->pt_exec) cudaGraphExecDestroy(r->pt_exec);
   if (r->pt_graph) cudaGraphDestroy(r->pt_graph);
   if (r->pt_capture) cudaStreamDestroy(r->pt_capture);
+  if (r->pm_sweeps) cudaStreamDestroy(r->pm_sweeps);
+  if (r->pm_masks) cudaStreamDestroy(r->pm_masks);
+  for (cudaEvent_t e : r->pm_ev)
+    if (e) cudaEventDestroy(e);
   if (r->done) cudaEventDestroy(r->done);
   if (r->t0) cudaEventDestroy(r->t0);
   if (r->t1) cudaEventDestroy(r->t1);
@@ -729,6 +745,90 @@ GraphMscSolve make_gm_solve(const isg_problem *p, const DeviceProblem *dp, const
   return s;
 }
 
+// Device memory for the tables of precomputed graph masks: at most this for
+// the two chunks' tables, and chunks chosen automatically hold one table of
+// at most kMaskChunkBytes (that stays in L2 while it is read: measured
+// faster than larger chunks).
+constexpr int64_t kMaskTableBytes = int64_t(1) << 30;
+constexpr int64_t kMaskChunkBytes = int64_t(96) << 20;
+
+// Sweeps [t_start, S) of a staged graph solve without a target, with the
+// acceptance masks precomputed: chunk k's masks are built by gm_mask_launch
+// on a low-priority stream into one of two tables (the table of chunk k - 2
+// once its sweeps are done), and the sweep kernel runs chunk k on a
+// high-priority stream once they are ready.  The sweep kernel leaves SMs idle
+// (one cluster per GPC), which the mask kernel fills; the priorities let the
+// sweep kernel's clusters start first when both wait.  Only stream order and
+// events connect the two kernels.  cudaErrorMemoryAllocation: the table does
+// not fit (nothing was enqueued).
+cudaError_t launch_premasked(const isg_problem *p, const DeviceProblem *dp, isg_result *r,
+                             uint64_t seed, int cluster, int threads, int own_n, int own_nnz,
+                             int own_lv, int planes, int C, int S, int t_start,
+                             cudaStream_t stream, int &launches) {
+  const size_t chunk_bytes = (size_t)C * (size_t)dp->gl * (size_t)r->units * 4;
+  void *buf = nullptr;
+  cudaError_t err = cudaMallocAsync(&buf, 2 * chunk_bytes, stream);
+  if (err != cudaSuccess) {
+    cudaGetLastError();
+    return cudaErrorMemoryAllocation;
+  }
+  if (!r->pm_sweeps) {
+    int least = 0, greatest = 0;
+    err = cudaDeviceGetStreamPriorityRange(&least, &greatest);
+    if (err == cudaSuccess)
+      err = cudaStreamCreateWithPriority(&r->pm_sweeps, cudaStreamNonBlocking, greatest);
+    if (err == cudaSuccess)
+      err = cudaStreamCreateWithPriority(&r->pm_masks, cudaStreamNonBlocking, least);
+    for (int i = 0; i < 6 && err == cudaSuccess; ++i)
+      err = cudaEventCreateWithFlags(&r->pm_ev[i], cudaEventDisableTiming);
+  }
+  cudaStream_t hs = r->pm_sweeps, ms = r->pm_masks;
+  cudaEvent_t *ev = r->pm_ev;  // start, end, masks ready (2), sweeps done (2)
+  if (err == cudaSuccess) err = cudaEventRecord(ev[0], stream);
+  if (err == cudaSuccess) err = cudaStreamWaitEvent(hs, ev[0], 0);
+  if (err == cudaSuccess) err = cudaStreamWaitEvent(ms, ev[0], 0);
+  const GraphMscSolve s = make_gm_solve(p, dp, r, seed, false, 0);
+  int k = 0;
+  for (int a = t_start; a < S && err == cudaSuccess; a += C, ++k) {
+    const int b = std::min(S, a + C);
+    uint32_t *tab = (uint32_t *)((char *)buf + (size_t)(k & 1) * chunk_bytes);
+    if (k >= 2) err = cudaStreamWaitEvent(ms, ev[4 + (k & 1)], 0);
+    if (err == cudaSuccess) err = gm_mask_launch(s, dp->gloff, dp->gl, a, b - a, tab, ms);
+    if (err == cudaSuccess) err = cudaEventRecord(ev[2 + (k & 1)], ms);
+    if (err == cudaSuccess) err = cudaStreamWaitEvent(hs, ev[2 + (k & 1)], 0);
+    if (err == cudaSuccess) {
+      GraphMscLaunch l = {};
+      l.t_begin = a;
+      l.t_end = b;
+      l.resume = a > 0;
+      l.cluster = cluster;
+      l.threads = threads;
+      l.own_n = own_n;
+      l.own_nnz = own_nnz;
+      l.own_lv = own_lv;
+      l.planes = planes;
+      l.gmask = tab;
+      l.gloff = dp->gloff;
+      l.gmask_gl = dp->gl;
+      l.gmask_t0 = a;
+      err = gm_launch(s, l, hs);
+    }
+    if (err == cudaSuccess) err = cudaEventRecord(ev[4 + (k & 1)], hs);
+    launches += 2;
+  }
+  r->mask_chunks = k;
+  if (err == cudaSuccess) err = cudaEventRecord(ev[1], hs);
+  if (err == cudaSuccess) err = cudaStreamWaitEvent(stream, ev[1], 0);
+  if (err != cudaSuccess) {
+    // nothing may still use the table when it is freed
+    if (hs) cudaStreamSynchronize(hs);
+    if (ms) cudaStreamSynchronize(ms);
+    cudaStreamSynchronize(stream);
+  }
+  cudaFreeAsync(buf, stream);
+  return err;
+}
+
 // Enqueue the sweeps [0, S) of a prepared result under the given shape:
 // one persistent launch, or one launch per sweep (plain); with a target and
 // several independently scheduled units, a second pass replays every unit to
@@ -752,6 +852,22 @@ cudaError_t launch_sweeps(const isg_problem *p, const DeviceProblem *dp, isg_res
     if (planes < 0) return cudaErrorInvalidConfiguration;
   }
   r->staged = own_n > 0;
+  r->mask_chunks = 0;
+  if (gm && own_n > 0 && !has_target && !plain && r->mask_chunk >= 0 && dp->gl > 0 &&
+      S > t_start) {
+    // precomputed masks, in chunks whose two tables fit kMaskTableBytes
+    // (chosen here: a table of at most kMaskChunkBytes and at least 64 sweeps)
+    const int64_t per_sweep = dp->gl * (int64_t)r->units * 4;
+    const int64_t left = S - t_start;
+    const int64_t C = r->mask_chunk > 0 ? std::min<int64_t>(r->mask_chunk, left)
+                                        : std::min<int64_t>(left, kMaskChunkBytes / per_sweep);
+    if (C >= 1 && 2 * C * per_sweep <= kMaskTableBytes && (r->mask_chunk > 0 || C >= 64)) {
+      err = launch_premasked(p, dp, r, seed, cluster, threads, own_n, own_nnz, own_lv, planes,
+                             (int)C, S, t_start, stream, launches);
+      if (err != cudaErrorMemoryAllocation) return err;
+      err = cudaSuccess;  // no room for the table: the sweep kernel builds the masks
+    }
+  }
   const int passes = (has_target && r->units > 1) ? 2 : 1;
   for (int pass = 0; pass < passes && err == cudaSuccess; ++pass) {
     const int first = plain ? t_start : -1;
@@ -973,6 +1089,7 @@ isg_status anneal_impl(const isg_problem *p, int32_t R, const double *betas, int
   // launch shape: explicit, else measured (isg_autotune), else the default rule
   if (o.quads_per_cta < 0 || o.quads_per_cta > 2)
     return fail(ISG_EINVAL, "quads_per_cta must be 0, 1 or 2");
+  if (o.mask_chunk < -1) return fail(ISG_EINVAL, "mask_chunk must be -1, 0 or positive");
   if (o.first_replica < 0 || o.first_replica % 32 != 0 ||
       (int64_t)o.first_replica + R > INT32_MAX)
     return fail(ISG_EINVAL, "first_replica must be a multiple of 32 in [0, 2^31 - 1 - replicas]");
@@ -1010,6 +1127,7 @@ isg_status anneal_impl(const isg_problem *p, int32_t R, const double *betas, int
 
   isg_result *r = new_result(p, R, S, msc, has_target, stream);
   r->first_replica = o.first_replica;
+  r->mask_chunk = o.mask_chunk;
   r->h2d_bytes = (int64_t)uploaded;
   r->relabelled = !tmsc;
   r->kernel = kernel;
@@ -1914,6 +2032,7 @@ isg_status isg_result_stats(const isg_result *r, isg_stats *stats) {
   stats->h2d_bytes = r->h2d_bytes;
   stats->staged = r->staged;
   stats->first_replica = r->first_replica;
+  stats->mask_chunks = r->mask_chunks;
   return ISG_OK;
 }
 

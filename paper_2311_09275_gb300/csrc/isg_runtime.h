@@ -29,6 +29,8 @@ struct DeviceProblem {
   int32_t *col = nullptr;
   int32_t *wt = nullptr;
   int32_t *field_r = nullptr;      // local fields, relabelled order (nullptr: none)
+  int32_t *gloff = nullptr;        // [n + 1] prefix of the threshold levels (d + |h| + 1) / 2
+  int64_t gl = 0;                  // gloff[n]: mask words of one replica word and sweep
   int32_t *orig = nullptr;         // relabelled -> original id
   int64_t *rowptr_o = nullptr;     // CSR in original ids (energy checks)
   int32_t *col_o = nullptr;
@@ -107,6 +109,12 @@ struct isg_result {
   std::vector<double> betas;
   bool plain = false;
   int32_t qpc = 1;
+  int32_t mask_chunk = 0;                  // isg_options.mask_chunk of the solve
+  int32_t mask_chunks = 0;                 // chunks of precomputed masks launched
+  // precomputed graph masks: the sweep kernel's high-priority stream, the mask
+  // kernel's low-priority stream, and their events (created on first use)
+  cudaStream_t pm_sweeps = nullptr, pm_masks = nullptr;
+  cudaEvent_t pm_ev[6] = {};
   uint32_t *d_table_ext = nullptr;         // threshold table of a continued schedule
 };
 

@@ -33,14 +33,15 @@ _i32, _i64, _u64, _dbl, _sz = ctypes.c_int32, ctypes.c_int64, ctypes.c_uint64, c
 
 class isg_options(ctypes.Structure):
     _fields_ = [("kernel", _i32), ("cluster_ctas", _i32), ("threads", _i32),
-                ("time_kernels", _i32), ("quads_per_cta", _i32), ("first_replica", _i32)]
+                ("time_kernels", _i32), ("quads_per_cta", _i32), ("first_replica", _i32),
+                ("mask_chunk", _i32)]
 
 
 class isg_stats(ctypes.Structure):
     _fields_ = [("sweep_kernel_ms", ctypes.c_float), ("launches", _i32),
                 ("sweep_launches", _i32), ("kernel", _i32), ("ctas", _i32),
                 ("cluster_ctas", _i32), ("threads", _i32), ("h2d_bytes", _i64),
-                ("staged", _i32), ("first_replica", _i32)]
+                ("staged", _i32), ("first_replica", _i32), ("mask_chunks", _i32)]
 
 
 class isg_server_stats(ctypes.Structure):
@@ -279,12 +280,13 @@ class Result:
 
 def isg_anneal(p, replicas: int, betas, seed: int, target=None, stream=None, kernel: int = 0,
                cluster_ctas: int = 0, threads: int = 0, time_kernels: bool = False,
-               quads_per_cta: int = 0, first_replica: int = 0) -> Result:
+               quads_per_cta: int = 0, first_replica: int = 0, mask_chunk: int = 0) -> Result:
     """Anneal `replicas` replicas (global indices first_replica + 0..replicas-1,
-    first_replica a multiple of 32) through isg_anneal_ex."""
+    first_replica a multiple of 32) through isg_anneal_ex; mask_chunk as in
+    isg_options (-1: the graph kernel builds its acceptance masks itself)."""
     b = _arr(betas, np.float64)
     opts = isg_options(kernel, cluster_ctas, threads, 1 if time_kernels else 0, quads_per_cta,
-                       first_replica)
+                       first_replica, mask_chunk)
     out = _P()
     _check(_lib.isg_anneal_ex(_h(p), int(replicas), _ptr(b), int(b.shape[0]),
                               int(seed) & 0xFFFFFFFFFFFFFFFF,
@@ -304,7 +306,8 @@ def isg_anneal_continue(p, res, betas, stream=None) -> None:
 
 def isg_anneal_resume(p, replicas: int, betas, seed: int, sweeps_done: int, spins, best_spins,
                       stream=None, kernel: int = 0, cluster_ctas: int = 0, threads: int = 0,
-                      quads_per_cta: int = 0, first_replica: int = 0) -> Result:
+                      quads_per_cta: int = 0, first_replica: int = 0,
+                      mask_chunk: int = 0) -> Result:
     """A solve restarted from a checkpoint (final and best int8 states after
     `sweeps_done` sweeps); equal to one solve of the whole schedule."""
     b = _arr(betas, np.float64)
@@ -312,7 +315,7 @@ def isg_anneal_resume(p, replicas: int, betas, seed: int, sweeps_done: int, spin
     bs = _arr(best_spins, np.int8)
     if s.size != int(replicas) * _lib_n(p) or bs.size != s.size:
         raise ValueError("spins and best_spins must hold replicas x n values")
-    opts = isg_options(kernel, cluster_ctas, threads, 0, quads_per_cta, first_replica)
+    opts = isg_options(kernel, cluster_ctas, threads, 0, quads_per_cta, first_replica, mask_chunk)
     out = _P()
     _check(_lib.isg_anneal_resume(_h(p), int(replicas), _ptr(b), int(b.shape[0]),
                                   int(seed) & 0xFFFFFFFFFFFFFFFF, int(sweeps_done), _ptr(s),

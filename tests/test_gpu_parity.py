@@ -211,6 +211,59 @@ def test_graph_msc_mask_table_shapes_bit_exact(isg, make, R, cluster, threads):
     assert_same(res, orc)
 
 
+@pytest.mark.parametrize("make", [GRAPHS["random_sparse"], pm1_graph, GRAPHS["isolated"],
+                                  hub_graph])
+@pytest.mark.parametrize("mask_chunk,cluster,threads,chunks", [
+    (-1, 4, 128, 0),     # built inside the sweep kernel
+    (0, 2, 256, 0),      # automatic: 45 sweeps are too few to precompute
+    (1, 3, 96, 45),      # one sweep per chunk
+    (7, 5, 64, 7),       # six chunks of 7 and one of 3
+    (1000, 12, 512, 1),  # the whole schedule in one chunk
+])
+def test_graph_msc_precomputed_masks_bit_exact(isg, make, mask_chunk, cluster, threads, chunks):
+    """The staged graph kernel with the acceptance masks precomputed by a second
+    kernel on its own stream, chunk by chunk, or built in the sweep kernel:
+    equal to the oracle bit for bit."""
+    g = make()
+    betas = I.geometric_betas(0.1, 5.0, 45)
+    orc = oracle.anneal(oracle.csr_of(g), 70, betas, 41, check_energy=True)
+    res = isg.isg_anneal(isg.problem_of(g), 70, betas, 41, kernel=4, cluster_ctas=cluster,
+                         threads=threads, mask_chunk=mask_chunk)
+    st = res.stats()
+    assert st["staged"] == 1 and st["mask_chunks"] == chunks
+    assert_same(res, orc)
+
+
+def test_graph_msc_precomputed_masks_continue_resume_target(isg):
+    """Precomputed masks across isg_anneal_continue (the solve's chunk length
+    carries over) and isg_anneal_resume, equal to one solve with the masks built
+    in the kernel; a solve with a target builds them in the kernel."""
+    g = pm1_graph()
+    p = isg.problem_of(g)
+    betas = I.geometric_betas(0.1, 4.0, 80)
+    whole = isg.isg_anneal(p, 64, betas, 29, kernel=4, cluster_ctas=3, mask_chunk=-1)
+    part = isg.isg_anneal(p, 64, betas[:30], 29, kernel=4, cluster_ctas=3, mask_chunk=9)
+    assert part.stats()["mask_chunks"] == 4
+    isg.isg_anneal_continue(p, part, betas[30:])
+    assert part.stats()["mask_chunks"] == 6
+    for x, y in zip(part.final(), whole.final()):
+        assert np.array_equal(x, y)
+    assert np.array_equal(part.best_all(), whole.best_all())
+    first = isg.isg_anneal(p, 64, betas[:50], 29, kernel=4, cluster_ctas=3, mask_chunk=-1)
+    res = isg.isg_anneal_resume(p, 64, betas, 29, 50, first.final()[0], first.best_all(),
+                                kernel=4, cluster_ctas=2, mask_chunk=11)
+    assert res.stats()["mask_chunks"] == 3
+    for x, y in zip(res.final(), whole.final()):
+        assert np.array_equal(x, y)
+    assert np.array_equal(res.best_all(), whole.best_all())
+    assert_same(res, oracle.anneal(oracle.csr_of(g), 64, betas, 29))
+    target = int(whole.best(spins=False)[0]) + 8
+    hit = isg.isg_anneal(p, 64, betas, 29, target=target, kernel=4, cluster_ctas=3,
+                         mask_chunk=9)
+    assert hit.stats()["mask_chunks"] == 0
+    assert_same(hit, oracle.anneal(oracle.csr_of(g), 64, betas, 29, target=target))
+
+
 @pytest.mark.parametrize("R,cluster,threads", [(40, 1, 256), (70, 4, 512)])
 def test_graph_msc_unstaged_bit_exact(isg, R, cluster, threads):
     """Adjacency too large for shared memory (12,000 vertices, mean degree 25):
