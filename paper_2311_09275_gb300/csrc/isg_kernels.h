@@ -53,10 +53,22 @@ struct TorusLaunch {
   int32_t stop_from_hits;    // 1: end at min over words of hit[] + 1 (second pass)
   int32_t cluster;           // CTAs per replica word (band split of the rows)
   int32_t threads;
+  // software-pipelined build only: the acceptance masks of the sweeps
+  // [t_begin, t_begin + pre_count), precomputed by torus_mask_launch, at
+  // pre_tab[t - t_begin][word][2][L*W] (nullptr: all drawn)
+  const uint32_t *pre_tab;
+  int32_t pre_count;
 };
 
 // Dynamic shared memory one CTA needs for a torus solve split over `cluster` CTAs.
 size_t torus_smem_bytes(int32_t L, int32_t W, int32_t cluster);
+// Whether torus_launch runs the software-pipelined build for this shape (the
+// one that reads TorusLaunch::pre_tab; the others draw every mask).
+bool torus_pipelined(int32_t L, int32_t W, int32_t cluster, int32_t threads);
+// Masks of the sweeps [a, a + count) of every word of the solve into out_dev
+// ([count][words][2][L*W] uint32, the layout TorusLaunch::pre_tab reads).
+cudaError_t torus_mask_launch(const TorusSolve &s, int32_t a, int32_t count, uint32_t *out_dev,
+                              cudaStream_t stream);
 // Largest number of sites a thread updates per sweep under this launch shape.
 int32_t torus_sites_per_thread(int32_t L, int32_t W, int32_t cluster, int32_t threads);
 cudaError_t torus_launch(const TorusSolve &s, const TorusLaunch &l, cudaStream_t stream);

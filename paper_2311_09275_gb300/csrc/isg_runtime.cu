@@ -751,6 +751,10 @@ GraphMscSolve make_gm_solve(const isg_problem *p, const DeviceProblem *dp, const
 // faster than larger chunks).
 constexpr int64_t kMaskTableBytes = int64_t(1) << 30;
 constexpr int64_t kMaskChunkBytes = int64_t(96) << 20;
+// Torus: one chunk's table of precomputed masks chosen automatically (80x100
+// at 1,024 replicas: 32 sweeps of 2 MB, chunks of 160 sweeps; measured best
+// among 120-320).
+constexpr int64_t kTorusChunkBytes = int64_t(64) << 20;
 
 // Sweeps [t_start, S) of a staged graph solve without a target, with the
 // acceptance masks precomputed: chunk k's masks are built by gm_mask_launch
@@ -829,6 +833,81 @@ cudaError_t launch_premasked(const isg_problem *p, const DeviceProblem *dp, isg_
   return err;
 }
 
+// Sweeps [t_start, S) of a torus solve without a target in the software-
+// pipelined build, in chunks of C sweeps, with the masks of the first
+// ceil(len / E) sweeps of every chunk after the first precomputed: the sweep
+// kernel's clusters leave SMs idle, and torus_mask_launch fills them, on a
+// low-priority stream, with the masks of chunk j + 1 while the sweep kernel
+// runs chunk j on a high-priority stream.  Chunk j >= 1 reads table j mod 2,
+// whose masks wait for the sweeps of chunk j - 2.  Stream order and events
+// only.  cudaErrorMemoryAllocation: the tables do not fit (nothing enqueued).
+cudaError_t launch_torus_premasked(const isg_problem *p, const DeviceProblem *dp, isg_result *r,
+                                   uint64_t seed, int cluster, int threads, int E, int C, int S,
+                                   int t_start, cudaStream_t stream, int &launches) {
+  const size_t per_sweep = (size_t)2 * (size_t)p->n * (size_t)r->units * 4;
+  const size_t chunk_bytes = (size_t)((C + E - 1) / E) * per_sweep;
+  void *buf = nullptr;
+  cudaError_t err = cudaMallocAsync(&buf, 2 * chunk_bytes, stream);
+  if (err != cudaSuccess) {
+    cudaGetLastError();
+    return cudaErrorMemoryAllocation;
+  }
+  if (!r->pm_sweeps) {
+    int least = 0, greatest = 0;
+    err = cudaDeviceGetStreamPriorityRange(&least, &greatest);
+    if (err == cudaSuccess)
+      err = cudaStreamCreateWithPriority(&r->pm_sweeps, cudaStreamNonBlocking, greatest);
+    if (err == cudaSuccess)
+      err = cudaStreamCreateWithPriority(&r->pm_masks, cudaStreamNonBlocking, least);
+    for (int i = 0; i < 6 && err == cudaSuccess; ++i)
+      err = cudaEventCreateWithFlags(&r->pm_ev[i], cudaEventDisableTiming);
+  }
+  cudaStream_t hs = r->pm_sweeps, ms = r->pm_masks;
+  cudaEvent_t *ev = r->pm_ev;  // start, end, masks ready (2), sweeps done (2)
+  if (err == cudaSuccess) err = cudaEventRecord(ev[0], stream);
+  if (err == cudaSuccess) err = cudaStreamWaitEvent(hs, ev[0], 0);
+  if (err == cudaSuccess) err = cudaStreamWaitEvent(ms, ev[0], 0);
+  const TorusSolve s = make_torus_solve(p, dp, r, seed, false, 0);
+  const int chunks = (S - t_start + C - 1) / C;
+  auto table = [&](int j) { return (uint32_t *)((char *)buf + (size_t)(j & 1) * chunk_bytes); };
+  for (int j = 0; j < chunks && err == cudaSuccess; ++j) {
+    const int a = t_start + j * C, b = std::min(S, a + C);
+    if (j + 1 < chunks) {
+      // the next chunk's masks, beside this chunk's sweeps
+      const int a1 = b, b1 = std::min(S, a1 + C);
+      if (j + 1 >= 3) err = cudaStreamWaitEvent(ms, ev[4 + ((j + 1) & 1)], 0);
+      if (err == cudaSuccess)
+        err = torus_mask_launch(s, a1, (b1 - a1 + E - 1) / E, table(j + 1), ms);
+      if (err == cudaSuccess) err = cudaEventRecord(ev[2 + ((j + 1) & 1)], ms);
+      ++launches;
+    }
+    if (err == cudaSuccess && j >= 1) err = cudaStreamWaitEvent(hs, ev[2 + (j & 1)], 0);
+    if (err == cudaSuccess) {
+      TorusLaunch l = {};
+      l.t_begin = a;
+      l.t_end = b;
+      l.resume = a > 0;
+      l.cluster = cluster;
+      l.threads = threads;
+      l.pre_tab = j >= 1 ? table(j) : nullptr;
+      l.pre_count = j >= 1 ? (b - a + E - 1) / E : 0;
+      err = torus_launch(s, l, hs);
+    }
+    if (err == cudaSuccess) err = cudaEventRecord(ev[4 + (j & 1)], hs);
+    ++launches;
+  }
+  r->mask_chunks = chunks - 1;
+  if (err == cudaSuccess) err = cudaEventRecord(ev[1], hs);
+  if (err == cudaSuccess) err = cudaStreamWaitEvent(stream, ev[1], 0);
+  if (err != cudaSuccess) {
+    if (hs) cudaStreamSynchronize(hs);
+    if (ms) cudaStreamSynchronize(ms);
+    cudaStreamSynchronize(stream);
+  }
+  cudaFreeAsync(buf, stream);
+  return err;
+}
+
 // Enqueue the sweeps [0, S) of a prepared result under the given shape:
 // one persistent launch, or one launch per sweep (plain); with a target and
 // several independently scheduled units, a second pass replays every unit to
@@ -866,6 +945,31 @@ cudaError_t launch_sweeps(const isg_problem *p, const DeviceProblem *dp, isg_res
                              (int)C, S, t_start, stream, launches);
       if (err != cudaErrorMemoryAllocation) return err;
       err = cudaSuccess;  // no room for the table: the sweep kernel builds the masks
+    }
+  }
+  if (r->msc && !gm && !has_target && !plain && r->mask_chunk >= 0 && S > t_start &&
+      torus_pipelined(p->L, p->W, cluster, threads)) {
+    // masks of one sweep in E precomputed on the SMs the clusters leave idle:
+    // E from the busy and idle SM counts (a sweep with its masks read costs
+    // about 0.3 of one that draws them, and the mask kernel draws about 1.3
+    // times as fast per SM as the sweep kernel consumes)
+    const int busy = r->units * cluster, idle = sm_count() - busy;
+    if (idle > 0) {
+      const int E = std::max(1, (int)std::lround(1.0 + 0.75 * busy / idle));
+      const int64_t per_sweep = (int64_t)2 * p->n * r->units * 4;
+      const int64_t left = S - t_start;
+      // chosen here: a table of at most kTorusChunkBytes, and at least four chunks
+      int64_t C = r->mask_chunk > 0 ? (int64_t)r->mask_chunk
+                                    : std::min<int64_t>(std::max<int64_t>(1, kTorusChunkBytes /
+                                                                                 per_sweep) * E,
+                                                        (left + 3) / 4);
+      C = std::max<int64_t>(C, 2);
+      if (C < left && 2 * ((C + E - 1) / E) * per_sweep <= kMaskTableBytes) {
+        err = launch_torus_premasked(p, dp, r, seed, cluster, threads, E, (int)C, S, t_start,
+                                     stream, launches);
+        if (err != cudaErrorMemoryAllocation) return err;
+        err = cudaSuccess;  // no room for the tables: the sweep kernel draws every mask
+      }
     }
   }
   const int passes = (has_target && r->units > 1) ? 2 : 1;
@@ -1584,6 +1688,10 @@ isg_status autotune_impl(const isg_problem *p, int32_t R, int32_t probe, cudaStr
   std::vector<uint32_t> table;
   build_table(betas.data(), probe, levels, table);
   r->table_words = table.size();
+  // shapes are ranked on the sweep kernel alone: a probe's few sweeps would
+  // make chunks of precomputed masks too short to compare (the chosen shape
+  // then precomputes in solves where that pays)
+  r->mask_chunk = -1;
   st = result_alloc(r, stream);
   if (st != ISG_OK) {
     delete r;

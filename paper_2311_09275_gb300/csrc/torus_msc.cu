@@ -18,6 +18,7 @@
 // its uniforms and the sweep's thresholds: they are built between the
 // thread's arrival at the phase barrier and the wait for it.
 #include <climits>
+#include <type_traits>
 
 #include "isg_device.cuh"
 #include "isg_kernels.h"
@@ -248,7 +249,10 @@ __device__ __forceinline__ void sweep_phase(uint32_t *spin, uint32_t *best, cons
 // gives an empty mask).
 constexpr int kPipeSites = 3;
 
-template <int NP>
+// LOAD: the other colour's masks are read from a precomputed table (q4, q8:
+// that sweep's two mask planes of this word, indexed by site) instead of
+// drawn; they are first used in the next phase, which hides the load.
+template <int NP, bool LOAD>
 __device__ __forceinline__ void pipe_phase(uint32_t *spin, uint32_t *best, const uint8_t *cb,
                                            uint32_t *up_peer, uint32_t *down_peer, int W, int r0,
                                            int nr, int c, const BlockPrefix (&bp)[8],
@@ -257,7 +261,8 @@ __device__ __forceinline__ void pipe_phase(uint32_t *spin, uint32_t *best, const
                                            const uint32_t (&mc4)[kPipeSites],
                                            const uint32_t (&mc8)[kPipeSites],
                                            uint32_t (&mo4)[kPipeSites],
-                                           uint32_t (&mo8)[kPipeSites]) {
+                                           uint32_t (&mo8)[kPipeSites], const uint32_t *q4,
+                                           const uint32_t *q8) {
   const int half = W >> 1;
   const int step_rows = blockDim.x / half;
   const int step_cols = blockDim.x - step_rows * half;
@@ -270,7 +275,13 @@ __device__ __forceinline__ void pipe_phase(uint32_t *spin, uint32_t *best, const
       const int par = (c + gr) & 1;
       const int col = 2 * j + par;
       // the other colour's site at this position, for the next phase
-      site_masks<true>((uint32_t)(gr * W + 2 * j + (par ^ 1)), bp, rk, To4, To8, mo4[i], mo8[i]);
+      const uint32_t osite = (uint32_t)(gr * W + 2 * j + (par ^ 1));
+      if (LOAD) {
+        mo4[i] = __ldg(q4 + osite);
+        mo8[i] = __ldg(q8 + osite);
+      } else {
+        site_masks<true>(osite, bp, rk, To4, To8, mo4[i], mo8[i]);
+      }
       const int x = lr * W + col;
       const int xl = (col == 0) ? x + W - 1 : x - 1;
       const int xr = (col == W - 1) ? x - W + 1 : x + 1;
@@ -307,12 +318,15 @@ __device__ __forceinline__ void pipe_phase(uint32_t *spin, uint32_t *best, const
   }
 }
 
-// The masks of this thread's sites of colour c (the pipeline's first phase).
+// The masks of this thread's sites of colour c (the pipeline's first phase),
+// drawn, or with LOAD read from a precomputed table as in pipe_phase.
+template <bool LOAD>
 __device__ __forceinline__ void pipe_prologue(int W, int r0, int nr, int c,
                                               const BlockPrefix (&bp)[8], const RoundKeys &rk,
                                               uint32_t T4, uint32_t T8,
                                               uint32_t (&m4)[kPipeSites],
-                                              uint32_t (&m8)[kPipeSites]) {
+                                              uint32_t (&m8)[kPipeSites], const uint32_t *q4,
+                                              const uint32_t *q8) {
   const int half = W >> 1;
   const int step_rows = blockDim.x / half;
   const int step_cols = blockDim.x - step_rows * half;
@@ -323,7 +337,13 @@ __device__ __forceinline__ void pipe_prologue(int W, int r0, int nr, int c,
     m4[i] = m8[i] = 0u;
     if (lr <= nr) {
       const int gr = r0 + lr - 1;
-      site_masks<true>((uint32_t)(gr * W + 2 * j + ((c + gr) & 1)), bp, rk, T4, T8, m4[i], m8[i]);
+      const uint32_t site = (uint32_t)(gr * W + 2 * j + ((c + gr) & 1));
+      if (LOAD) {
+        m4[i] = __ldg(q4 + site);
+        m8[i] = __ldg(q8 + site);
+      } else {
+        site_masks<true>(site, bp, rk, T4, T8, m4[i], m8[i]);
+      }
     }
     j += step_cols;
     lr += step_rows;
@@ -338,9 +358,13 @@ __device__ __forceinline__ void pipe_prologue(int W, int r0, int nr, int c,
 // before it (off in the 64-register build, where the extra live state spills).
 // kPipe: the software-pipelined phases (every thread has at most kPipeSites
 // sites per phase).
-template <int NP, bool kPrefetch, bool kPipe = false>
+// PRE (pipelined build only): the masks of the sweeps [t_begin, t_begin +
+// pre_count), precomputed by torus_mask_kernel, are read from pre_tab
+// [t - t_begin][word][2 planes][L*W] instead of drawn.
+template <int NP, bool kPrefetch, bool kPipe = false, bool PRE = false>
 __device__ void torus_word(const TorusSolve &s, int word, int k, int K, int t_begin, int t_end,
-                           int resume, uint8_t *smem) {
+                           int resume, uint8_t *smem, const uint32_t *pre_tab = nullptr,
+                           int pre_count = 0) {
   const int L = s.L, W = s.W, n = L * W;
   const Band band = band_of(L, K, k);
   const int r0 = band.r0, nr = band.nr;
@@ -425,11 +449,23 @@ __device__ void torus_word(const TorusSolve &s, int word, int k, int K, int t_be
     // masks of colour 0 (m0) and colour 1 (m1) of this thread's sites, each
     // drawn during the phase before the one that uses them
     uint32_t m04[kPipeSites], m08[kPipeSites], m14[kPipeSites], m18[kPipeSites];
+    // PRE: sweeps [t_begin, t_pre) read their masks from the table
+    const int t_pre = (PRE && pre_tab != nullptr) ? min(t_end, t_begin + pre_count) : t_begin;
+    auto planes = [&](int tt) {
+      return pre_tab + ((int64_t)(tt - t_begin) * s.words + word) * 2 * n;
+    };
     if (t < t_end) {
       sweep_prefix(t);
-      pipe_prologue(W, r0, nr, 0, bp, s.rk, T4n, T8n, m04, m08);
+      if (PRE && t < t_pre)
+        pipe_prologue<true>(W, r0, nr, 0, bp, s.rk, T4n, T8n, m04, m08, planes(t), planes(t) + n);
+      else
+        pipe_prologue<false>(W, r0, nr, 0, bp, s.rk, T4n, T8n, m04, m08, nullptr, nullptr);
     }
-    for (; t < t_end; ++t) {
+    bool stop = false;
+    // one sweep; LOAD0: the masks phase 0 prepares (colour 1 of sweep t) come
+    // from the table, LOAD1: those phase 1 prepares (colour 0 of sweep t + 1)
+    auto sweep = [&](auto load0, auto load1) {
+      constexpr bool LOAD0 = decltype(load0)::value, LOAD1 = decltype(load1)::value;
       const uint32_t T4 = T4n, T8 = T8n;
       const bool more = t + 1 < t_end;
       if (more) {
@@ -437,15 +473,17 @@ __device__ void torus_word(const TorusSolve &s, int word, int k, int K, int t_be
         T8n = trow[(size_t)(t + 1) * s.table_ts + 1];
       }
       cnt.clear();
-      // colour 0 of sweep t; draws colour 1 of sweep t
-      pipe_phase<NP>(spin, best, cb, up_peer, down_peer, W, r0, nr, 0, bp, s.rk, T4, T8, imp,
-                     cnt, m04, m08, m14, m18);
+      // colour 0 of sweep t; prepares colour 1 of sweep t
+      pipe_phase<NP, LOAD0>(spin, best, cb, up_peer, down_peer, W, r0, nr, 0, bp, s.rk, T4, T8,
+                            imp, cnt, m04, m08, m14, m18, LOAD0 ? planes(t) : nullptr,
+                            LOAD0 ? planes(t) + n : nullptr);
       group_arrive(K);
       if (more) sweep_prefix(t + 1);
       group_wait(K);
-      // colour 1 of sweep t; draws colour 0 of sweep t + 1 (unused after the last)
-      pipe_phase<NP>(spin, best, cb, up_peer, down_peer, W, r0, nr, 1, bp, s.rk, T4n, T8n, imp,
-                     cnt, m14, m18, m04, m08);
+      // colour 1 of sweep t; prepares colour 0 of sweep t + 1 (unused after the last)
+      pipe_phase<NP, LOAD1>(spin, best, cb, up_peer, down_peer, W, r0, nr, 1, bp, s.rk, T4n,
+                            T8n, imp, cnt, m14, m18, m04, m08, LOAD1 ? planes(t + 1) : nullptr,
+                            LOAD1 ? planes(t + 1) + n : nullptr);
       e += 4 * (cluster_lane_sum<NP>(cnt, acc, acc_m, K, [] {}) - 2 * n);
       const bool better = e < e_best;
       if (better) e_best = e;
@@ -455,11 +493,19 @@ __device__ void torus_word(const TorusSolve &s, int word, int k, int K, int t_be
             __reduce_min_sync(0xFFFFFFFFu, ((valid >> lane) & 1u) ? e_best : INT_MAX);
         if (mn <= s.target) {
           hit = t;
-          ++t;
-          break;
+          stop = true;
         }
       }
+    };
+    if (PRE) {
+      // masks read for both phases, then the sweep whose successor draws them
+      for (; !stop && t + 1 < t_pre; ++t) sweep(std::true_type{}, std::true_type{});
+      if (!stop && t < t_pre) {
+        sweep(std::true_type{}, std::false_type{});
+        ++t;
+      }
     }
+    for (; !stop && t < t_end; ++t) sweep(std::false_type{}, std::false_type{});
   }
   // masks of this thread's first site of the next phase, drawn while the
   // group barrier before that phase completes (they do not depend on spins)
@@ -535,7 +581,7 @@ __device__ void torus_word(const TorusSolve &s, int word, int k, int K, int t_be
 // MAXT = 384 (CTAs of at most 384 threads, six counter planes: the 80 x 100
 // workload's shape) lets the compiler keep more of the eight Philox blocks in
 // flight (144 registers against 116 in the 512-thread build: +1.2 %)
-template <int NP, int MAXT, bool PIPE = false>
+template <int NP, int MAXT, bool PIPE = false, bool PRE = false>
 __global__ void __launch_bounds__(MAXT, 1) torus_kernel(TorusSolve s, TorusLaunch l) {
   extern __shared__ __align__(16) uint8_t smem[];
   const int K = l.cluster;
@@ -548,7 +594,8 @@ __global__ void __launch_bounds__(MAXT, 1) torus_kernel(TorusSolve s, TorusLaunc
       if (s.hit[w] >= 0 && s.hit[w] < m) m = s.hit[w];
     if (m != INT_MAX && m + 1 < t_end) t_end = m + 1;
   }
-  torus_word<NP, (MAXT <= 512), PIPE>(s, word, k, K, l.t_begin, t_end, l.resume, smem);
+  torus_word<NP, (MAXT <= 512), PIPE, PRE>(s, word, k, K, l.t_begin, t_end, l.resume, smem,
+                                           l.pre_tab, l.pre_count);
 }
 
 // One CTA per unit with a CTA-wide barrier (nothing to overlap): no mask
@@ -578,6 +625,31 @@ __global__ void __launch_bounds__(512, 2) torus_batch_kernel(const TorusBatchIte
     }
     torus_word<NP, false>(u.solve, u.word, 0, 1, u.t_begin, t_end, u.resume, smem);
     __syncthreads();
+  }
+}
+
+// Acceptance masks of the sweeps a, a + 1, ... for every word and site of a
+// torus solve, for the pipelined sweep kernel to read instead of drawing
+// them: one CTA per (sweep, word); site i's masks at out[(t - a, word)]
+// [plane][i], plane 0 against the threshold of an energy change of 4, plane 1
+// of 8, as site_masks builds them.
+__global__ void __launch_bounds__(256) torus_mask_kernel(TorusSolve s, int32_t a, uint32_t *out) {
+  const int w = (int)(blockIdx.x % (unsigned)s.words);
+  const int p = (int)(blockIdx.x / (unsigned)s.words);
+  const int t = a + p;
+  const int n = s.L * s.W;
+  const uint32_t uword = (uint32_t)(w + s.rng_word0);
+  BlockPrefix bp[8];
+#pragma unroll
+  for (int q = 0; q < 8; ++q) bp[q] = block_prefix(8u * uword + (uint32_t)q, (uint32_t)t, s.rk);
+  const uint32_t *row = s.table + (size_t)w * s.table_ws + (size_t)t * s.table_ts;
+  const uint32_t T4 = row[0], T8 = row[1];
+  uint32_t *o = out + ((int64_t)p * s.words + w) * 2 * n;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    uint32_t r4, r8;
+    site_masks<true>((uint32_t)i, bp, s.rk, T4, T8, r4, r8);
+    o[i] = r4;
+    o[n + i] = r8;
   }
 }
 
@@ -686,6 +758,21 @@ int torus_max_active_clusters(int32_t L, int32_t W, int32_t words, int32_t clust
   }
 }
 
+bool torus_pipelined(int32_t L, int32_t W, int32_t cluster, int32_t threads) {
+  const int nr = (L + cluster - 1) / cluster;
+  const int spt = torus_sites_per_thread(L, W, cluster, threads);
+  const int np = np_for(spt, (nr * W + threads - 1) / threads, threads);
+  return threads <= 384 && spt / 2 <= kPipeSites && (np == 5 || np == 6);
+}
+
+cudaError_t torus_mask_launch(const TorusSolve &s, int32_t a, int32_t count, uint32_t *out_dev,
+                              cudaStream_t stream) {
+  const int64_t grid = (int64_t)count * s.words;
+  if (count < 1 || grid > INT32_MAX) return cudaErrorInvalidValue;
+  torus_mask_kernel<<<(unsigned)grid, 256, 0, stream>>>(s, a, out_dev);
+  return cudaGetLastError();
+}
+
 cudaError_t torus_launch(const TorusSolve &s, const TorusLaunch &l, cudaStream_t stream) {
   const int K = l.cluster;
   const size_t smem = torus_smem_bytes(s.L, s.W, K);
@@ -698,12 +785,19 @@ cudaError_t torus_launch(const TorusSolve &s, const TorusLaunch &l, cudaStream_t
   const bool wide = l.threads > 512;
   // software-pipelined phases when every thread has at most kPipeSites sites per phase
   const bool pipe = l.threads <= 384 && spt / 2 <= kPipeSites;
+  const bool pre = pipe && l.pre_tab != nullptr && l.pre_count > 0;
   switch (np) {
     case 5:
+      if (pre)
+        return launch_clustered(torus_kernel<5, 384, true, true>, grid, l.threads, smem, K,
+                                stream, s, l);
       return pipe ? launch_clustered(torus_kernel<5, 384, true>, grid, l.threads, smem, K,
                                      stream, s, l)
                   : launch_clustered(torus_kernel<5, 384>, grid, l.threads, smem, K, stream, s, l);
     case 6:
+      if (l.threads <= 384 && pre)
+        return launch_clustered(torus_kernel<6, 384, true, true>, grid, l.threads, smem, K,
+                                stream, s, l);
       if (l.threads <= 384 && pipe)
         return launch_clustered(torus_kernel<6, 384, true>, grid, l.threads, smem, K, stream, s,
                                 l);

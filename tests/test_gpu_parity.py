@@ -125,6 +125,25 @@ def test_torus_beta_zero_and_huge(isg):
         assert_same(isg.isg_anneal(p, 40, betas, 5), orc)
 
 
+@pytest.mark.parametrize("L,W,R,cluster,threads", [
+    (24, 30, 96, 2, 64),      # 6 CTAs: nearly every SM idle, every sweep after chunk 0 read
+    (40, 40, 1024, 2, 160),   # 64 CTAs: every second sweep read
+])
+@pytest.mark.parametrize("mask_chunk", [-1, 0, 1, 7])
+def test_torus_precomputed_masks_bit_exact(isg, L, W, R, cluster, threads, mask_chunk):
+    """The pipelined torus kernel reading the acceptance masks of some sweeps
+    from tables that a second kernel builds on the SMs its clusters leave idle
+    (chunks of mask_chunk sweeps; 0 chosen automatically, -1 none): equal to
+    the oracle bit for bit."""
+    t = I.torus(L, W, 13)
+    betas = I.geometric_betas(0.1, 5.0, 45)
+    orc = oracle.anneal(oracle.csr_of(t), R, betas, 43)
+    res = isg.isg_anneal(isg.problem_of(t), R, betas, 43, kernel=1, cluster_ctas=cluster,
+                         threads=threads, mask_chunk=mask_chunk)
+    assert (res.stats()["mask_chunks"] > 0) == (mask_chunk != -1)
+    assert_same(res, orc)
+
+
 # ------------------------------------------------------------------ graphs
 GRAPHS = {
     "random_sparse": lambda: I.random_graph(500, 700, 4),
