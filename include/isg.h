@@ -142,10 +142,9 @@ void isg_problem_destroy(isg_problem *p);
 /* ---------------------------------------------------------------- annealing */
 
 /* Kernel families.  AUTO picks the multi-spin-coded torus kernel for tori,
- * the multi-spin-coded graph kernel for graphs without local fields whose
- * weights are all +1 or -1 and whose degrees are <= 63, and the int8 CSR
- * colour-class kernel otherwise (GRAPH_MSC also takes fields when every weight
- * is +1 and degree + |h| <= 63);
+ * the multi-spin-coded graph kernel for graphs whose weights are all +1 or -1
+ * (all +1 when there are local fields) and whose degree + |h| is <= 63, and
+ * the int8 CSR colour-class kernel otherwise;
  * PLAIN runs one kernel launch per sweep (state kept in device memory between
  * launches), the one-instance-per-launch baseline of the batched form. */
 typedef enum {

@@ -1163,11 +1163,11 @@ isg_status anneal_impl(const isg_problem *p, int32_t R, const double *betas, int
                      shape_lookup(p, R, t_kernel, t_cluster, t_threads, t_qpc);
   if (tuned) kernel = t_kernel;
   if (kernel == ISG_KERNEL_AUTO)
-    // instances with fields run faster on the int8 kernel (d + |h| costs the
-    // multi-spin kernel a threshold mask per level)
+    // the multi-spin graph kernel also takes unit-weight instances with fields
+    // (measured faster than the int8 kernel on them since its staged build
+    // keeps the threshold masks of the next sweep in shared memory)
     kernel = p->torus ? ISG_KERNEL_TORUS_MSC
-                      : (graph_msc_ok(p) && p->field.empty() ? ISG_KERNEL_GRAPH_MSC
-                                                             : ISG_KERNEL_CSR);
+                      : (graph_msc_ok(p) ? ISG_KERNEL_GRAPH_MSC : ISG_KERNEL_CSR);
   if (kernel < ISG_KERNEL_AUTO || kernel > ISG_KERNEL_GRAPH_MSC)
     return fail(ISG_EINVAL, "unknown kernel %d", kernel);
   if (kernel == ISG_KERNEL_TORUS_MSC && !p->torus)

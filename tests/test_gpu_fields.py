@@ -132,9 +132,9 @@ def test_fields_auto_and_plain_kernels(isg):
     orc = oracle.anneal(oracle.csr_of(g), 24, betas, 2)
     p = isg.problem_of(g)
     auto = isg.isg_anneal(p, 24, betas, 2)
-    assert auto.stats()["kernel"] == 2          # fields -> int8 colour-class kernel
+    assert auto.stats()["kernel"] == 4          # unit weights, fields -> multi-spin graph kernel
     assert_same(auto, orc)
-    assert_same(isg.isg_anneal(p, 24, betas, 2, kernel=4), orc)
+    assert_same(isg.isg_anneal(p, 24, betas, 2, kernel=2), orc)
     assert_same(isg.isg_anneal(p, 24, betas, 2, kernel=3), orc)
 
 
