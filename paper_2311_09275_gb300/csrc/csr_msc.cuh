@@ -40,7 +40,8 @@ constexpr int kPlanesU = 6;  // per-lane bond counts up to 63 (degree <= 63)
 __host__ __device__ __forceinline__ size_t align16(size_t x) { return (x + 15) & ~size_t(15); }
 
 struct GmSmem {
-  size_t spin, lrow, lorig, lcol, lbest, lfield, lmoff, lmask, ocls, trow, part, lane_acc, total;
+  size_t spin, lrow, lorig, lcol, lbest, lfield, lmoff, lmask, ocls, trow, part, lane_acc, bars,
+      total;
 };
 
 // own_n, own_nnz, own_lv: the largest owned vertex, adjacency and threshold-
@@ -58,11 +59,13 @@ __host__ __device__ __forceinline__ GmSmem gm_layout(int n, int K, int n_colours
   m.lmoff = align16(m.lfield + (fields ? sizeof(int32_t) * (size_t)own_n : 0));
   m.lmask = align16(m.lmoff + (own_n ? sizeof(int32_t) * ((size_t)own_n + 1) : 0));
   m.ocls = align16(m.lmask + 2 * sizeof(uint32_t) * (size_t)own_lv);
-  // class slice table: slice bounds, first slot, and mask work of each class's window
-  m.trow = align16(m.ocls + sizeof(int32_t) * (4 * (size_t)n_colours + 1));
+  // class slice table: slice bounds, first slot, mask work of each class's window,
+  // and the bytes the peers send in each class
+  m.trow = align16(m.ocls + sizeof(int32_t) * (5 * (size_t)n_colours + 1));
   m.part = align16(m.trow + 2 * sizeof(uint32_t) * (size_t)kmax1);
   m.lane_acc = m.part + 2 * sizeof(int32_t) * 32 * (size_t)K;
-  m.total = align16(m.lane_acc + sizeof(int32_t) * 32);
+  m.bars = align16(m.lane_acc + sizeof(int32_t) * 32);  // two mbarriers and an error flag
+  m.total = align16(m.bars + 32);
   return m;
 }
 
@@ -171,6 +174,56 @@ __device__ __forceinline__ void cp_async4(uint32_t *dst_smem, const uint32_t *sr
 __device__ __forceinline__ void cp_async_wait_all() {
   asm volatile("cp.async.wait_all;\n" ::: "memory");
 }
+
+// Cluster data flow between the CTAs that share a word: a CTA sends each new
+// word to its peers with st.async, which completes on the receiver's
+// mbarrier, so a receiver knows that a class is complete in its copy once the
+// expected bytes have arrived and its own threads have arrived.
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(bar), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+  asm volatile(
+      "{\n .reg .b64 st;\n mbarrier.arrive.release.cta.shared::cta.b64 st, [%0];\n}\n" ::"r"(
+          bar)
+      : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile(
+      "{\n .reg .b64 st;\n mbarrier.arrive.expect_tx.release.cta.shared::cta.b64 st, [%0], "
+      "%1;\n}\n" ::"r"(bar),
+      "r"(bytes)
+      : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], "
+      "%2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// v into CTA `rank`'s copy of the shared word at local address a, completing
+// 4 bytes on that CTA's mbarrier at local address bar.
+__device__ __forceinline__ void st_async_u32(uint32_t a, uint32_t rank, uint32_t v,
+                                             uint32_t bar) {
+  uint32_t ra, rb;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;\n" : "=r"(ra) : "r"(a), "r"(rank));
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;\n" : "=r"(rb) : "r"(bar), "r"(rank));
+  asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.u32 [%0], %1, [%2];\n" ::"r"(
+                   ra),
+               "r"(v), "r"(rb)
+               : "memory");
+}
+
+// try_wait attempts before a wait counts as failed (far beyond any phase)
+constexpr uint32_t kDataflowWaitLimit = 1u << 22;
 
 // Acceptance sources of update_vertex.
 enum GmAccept { kAcceptPre = 0, kAcceptLazy = 1, kAcceptMasks = 2 };
@@ -314,6 +367,11 @@ __device__ void gm_word(const GraphMscSolve &s, const GraphMscLaunch &L, int wor
   int32_t *chi = clo + nc;
   int32_t *cob = chi + nc;
   int32_t *qlo = cob + nc;  // staged: mask work [qlo[c], qlo[c + 1]) in class c's window
+  int32_t *expb = qlo + nc + 1;  // bytes the peers send into this copy in class c
+  // clusters: this CTA's two mbarriers (alternating class phases) and error flag
+  uint64_t *bars = reinterpret_cast<uint64_t *>(smem + lay.bars);
+  int *dferr = reinterpret_cast<int *>(smem + lay.bars + 16);
+  const uint32_t bar0 = (uint32_t)__cvta_generic_to_shared(bars);
   uint32_t *trow = reinterpret_cast<uint32_t *>(smem + lay.trow);
   int32_t *part = reinterpret_cast<int32_t *>(smem + lay.part);
   int32_t *lane_acc = reinterpret_cast<int32_t *>(smem + lay.lane_acc);
@@ -342,6 +400,13 @@ __device__ void gm_word(const GraphMscSolve &s, const GraphMscLaunch &L, int wor
       chi[c] = hi;
       cob[c] = STAGED ? ov : lo;
       ov += hi - lo;
+      expb[c] = 4 * ((s.class_start[c + 1] - s.class_start[c]) - (hi - lo));
+    }
+    if (MG && K > 1) {
+      mbar_init(bar0, (uint32_t)B);
+      mbar_init(bar0 + 8, (uint32_t)B);
+      *dferr = 0;
+      asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
     }
     if (STAGED) {
       // the owned slots' mask work, an even share per class window (measured
@@ -533,6 +598,37 @@ __device__ void gm_word(const GraphMscSolve &s, const GraphMscLaunch &L, int wor
   int hit = -1;
   uint32_t imp = 0u;  // replicas whose best state is the state at the start of sweep t
   const int x0 = (int)threadIdx.x, x1 = (int)(threadIdx.x + blockDim.x);
+  // clusters with precomputed masks: class phases ordered by data flow
+  // (st.async into the peers' copies, completing on their mbarriers) instead
+  // of cluster barriers (measured faster there; with the masks built in the
+  // kernel, whose window work runs while other warps wait, it was not).  A peer
+  // starts class c + 1 only once this CTA's whole class c has arrived, which
+  // this CTA sends only after all its reads of class c, so no peer runs more
+  // than one phase ahead and two alternating mbarriers suffice.  A wait that
+  // gives up sets the error flag (read by the host as done = -1); later waits
+  // are skipped, so the kernel still ends.
+  const bool DF = MG && K > 1;
+  int gph = 0;       // class phases so far: mbarrier gph & 1
+  uint32_t par = 0;  // each mbarrier's current phase parity
+  auto df_arrive = [&](int bytes) {
+    const uint32_t bar = bar0 + 8u * (uint32_t)(gph & 1);
+    if (threadIdx.x == 0) mbar_arrive_expect_tx(bar, (uint32_t)bytes);
+    else mbar_arrive(bar);
+  };
+  auto df_wait = [&]() {
+    const int i = gph & 1;
+    const uint32_t bar = bar0 + 8u * (uint32_t)i;
+    uint32_t tries = 0;
+    while (!mbar_try_wait(bar, (par >> i) & 1u)) {
+      if (*(volatile int *)dferr) break;
+      if (++tries >= kDataflowWaitLimit) {
+        atomicExch(dferr, 1);
+        break;
+      }
+    }
+    par ^= 1u << i;
+    ++gph;
+  };
   for (; t < t_end; ++t) {
     const uint32_t *row = trow + (t & 1) * s.kmax1;
     const bool more = t + 1 < t_end;
@@ -600,16 +696,24 @@ __device__ void gm_word(const GraphMscSolve &s, const GraphMscLaunch &L, int wor
             spin, v, p0, p1, adj, row, uu, draw, STAGED ? mcur + lmoff[i] : nullptr, hv, cd, cu);
         if (K == 1) {
           spin[v] = sn;
+        } else if (DF) {
+          spin[v] = sn;
+          const uint32_t a = (uint32_t)__cvta_generic_to_shared(spin + v);
+          const uint32_t bar = bar0 + 8u * (uint32_t)(gph & 1);
+          for (int r = 0; r < K; ++r)
+            if (r != k) st_async_u32(a, (uint32_t)r, sn, bar);
         } else {
           const uint32_t a = (uint32_t)__cvta_generic_to_shared(spin + v);
           for (int r = 0; r < K; ++r) st_cluster_u32(a, (uint32_t)r, sn);
         }
       }
       if (c + 1 < nc) {
-        group_arrive(K);
+        if (DF) df_arrive(expb[c]);
+        else group_arrive(K);
         draw_first(c + 1);
         if (STAGED && more && !MG) mask_window(c, t + 1);
-        group_wait(K);
+        if (DF) df_wait();
+        else group_wait(K);
       }
     }
     if (more_a) {
@@ -627,17 +731,26 @@ __device__ void gm_word(const GraphMscSolve &s, const GraphMscLaunch &L, int wor
       lane_acc[threadIdx.x] = 0;
       if (K == 1) {
         pbuf[threadIdx.x] = x;
-      } else {
+      } else if (!DF) {
         for (int r = 0; r < K; ++r) peer_smem(pbuf, (uint32_t)r)[k * 32 + threadIdx.x] = x;
+      } else {
+        pbuf[k * 32 + threadIdx.x] = x;
+        const uint32_t a = (uint32_t)__cvta_generic_to_shared(pbuf + k * 32 + threadIdx.x);
+        const uint32_t bar = bar0 + 8u * (uint32_t)(gph & 1);
+        for (int r = 0; r < K; ++r)
+          if (r != k) st_async_u32(a, (uint32_t)r, x, bar);
       }
     }
-    group_arrive(K);
+    // the last class and the peers' partial sums complete the sweep's last phase
+    if (DF) df_arrive(expb[nc - 1] + 4 * 32 * (K - 1));
+    else group_arrive(K);
     if (PF && more) {
       sweep_prefix(t + 1);
       draw_first(0);
     }
     if (STAGED && more && !MG) mask_window(nc - 1, t + 1);
-    group_wait(K);
+    if (DF) df_wait();
+    else group_wait(K);
     if (STAGED && nc == 1 && !MG) __syncthreads();  // one class: its masks were built just now
     int32_t dsum = 0;
     for (int r = 0; r < K; ++r) dsum += pbuf[r * 32 + lane];
@@ -656,7 +769,9 @@ __device__ void gm_word(const GraphMscSolve &s, const GraphMscLaunch &L, int wor
     }
   }
 
-  // every update of the cluster precedes the last group barrier
+  // every update of the cluster precedes the last group barrier (with data
+  // flow: one cluster barrier, after which no CTA sends to another)
+  if (DF) cluster_barrier();
   for (int c = 0; c < nc; ++c) {
     const int lo = clo[c], hi = chi[c];
     for (int v = lo + threadIdx.x; v < hi; v += blockDim.x) {
@@ -675,6 +790,10 @@ __device__ void gm_word(const GraphMscSolve &s, const GraphMscLaunch &L, int wor
       if (s.has_target && hit >= 0) s.hit[word] = hit;
       s.done[word] = t;
     }
+  }
+  if (DF) {
+    cluster_barrier();  // after rank 0's done store
+    if (threadIdx.x == 0 && *(volatile int *)dferr) atomicMin(&s.done[word], -1);
   }
 }
 

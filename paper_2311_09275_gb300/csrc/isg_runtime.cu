@@ -472,7 +472,15 @@ isg_status result_sync(const isg_result *cr) {
   }
   r->hit_sweep = r->has_target ? stop : -1;
   r->sweeps_done = 0;
-  for (int32_t u = 0; u < r->units; ++u) r->sweeps_done = std::max(r->sweeps_done, r->h_done[u]);
+  for (int32_t u = 0; u < r->units; ++u) {
+    if (r->h_done[u] < 0) {
+      // the graph kernel's wait for a class from its cluster peers gave up
+      r->sync_status = fail(ISG_ECUDA, "replica word %d: a wait for its cluster peers timed out",
+                            u);
+      return r->sync_status;
+    }
+    r->sweeps_done = std::max(r->sweeps_done, r->h_done[u]);
+  }
   r->sync_status = ISG_OK;
   return ISG_OK;
 }
@@ -1688,10 +1696,12 @@ isg_status autotune_impl(const isg_problem *p, int32_t R, int32_t probe, cudaStr
   std::vector<uint32_t> table;
   build_table(betas.data(), probe, levels, table);
   r->table_words = table.size();
-  // shapes are ranked on the sweep kernel alone: a probe's few sweeps would
-  // make chunks of precomputed masks too short to compare (the chosen shape
-  // then precomputes in solves where that pays)
-  r->mask_chunk = -1;
+  // tori: shapes are ranked with every mask drawn, since a probe's few sweeps
+  // would make the torus chunks too short to compare (the chosen shape then
+  // precomputes in solves where that pays); graphs: with the masks chosen as
+  // in a solve (a probe of 64 or more sweeps makes one chunk of precomputed
+  // masks, whose build and data-flow synchronisation favour other shapes)
+  r->mask_chunk = p->torus ? -1 : 0;
   st = result_alloc(r, stream);
   if (st != ISG_OK) {
     delete r;
