@@ -558,13 +558,13 @@ namespace {
 // Measured choices: (device, torus?, L or n, W or nnz, replicas)
 //   -> (kernel, cluster, threads, quads/CTA)
 std::mutex g_shape_mu;
-std::map<std::array<int64_t, 5>, std::array<int, 4>> g_shapes;
+std::map<std::array<int64_t, 6>, std::array<int, 4>> g_shapes;  // tuned shapes by shape_key
 
-std::array<int64_t, 5> shape_key(const isg_problem *p, int replicas) {
+std::array<int64_t, 6> shape_key(const isg_problem *p, int replicas) {
   int dev = 0;
   cudaGetDevice(&dev);
   return {dev, p->torus ? 1 : 0, p->torus ? p->L : p->n, p->torus ? p->W : p->rowptr[p->n],
-          replicas};
+          replicas, p->colouring};
 }
 
 bool shape_lookup(const isg_problem *p, int replicas, int &kernel, int &cluster, int &threads,
