@@ -764,6 +764,22 @@ constexpr int64_t kMaskChunkBytes = int64_t(96) << 20;
 // among 120-320).
 constexpr int64_t kTorusChunkBytes = int64_t(64) << 20;
 
+// The result's two streams for precomputed masks (sweep kernel at the
+// greatest priority, mask kernel at the least) and their events, created on
+// first use and kept until the result is freed.
+cudaError_t premask_streams(isg_result *r) {
+  if (r->pm_sweeps) return cudaSuccess;
+  int least = 0, greatest = 0;
+  cudaError_t err = cudaDeviceGetStreamPriorityRange(&least, &greatest);
+  if (err == cudaSuccess)
+    err = cudaStreamCreateWithPriority(&r->pm_sweeps, cudaStreamNonBlocking, greatest);
+  if (err == cudaSuccess)
+    err = cudaStreamCreateWithPriority(&r->pm_masks, cudaStreamNonBlocking, least);
+  for (int i = 0; i < 6 && err == cudaSuccess; ++i)
+    err = cudaEventCreateWithFlags(&r->pm_ev[i], cudaEventDisableTiming);
+  return err;
+}
+
 // Sweeps [t_start, S) of a staged graph solve without a target, with the
 // acceptance masks precomputed: chunk k's masks are built by gm_mask_launch
 // on a low-priority stream into one of two tables (the table of chunk k - 2
@@ -784,16 +800,7 @@ cudaError_t launch_premasked(const isg_problem *p, const DeviceProblem *dp, isg_
     cudaGetLastError();
     return cudaErrorMemoryAllocation;
   }
-  if (!r->pm_sweeps) {
-    int least = 0, greatest = 0;
-    err = cudaDeviceGetStreamPriorityRange(&least, &greatest);
-    if (err == cudaSuccess)
-      err = cudaStreamCreateWithPriority(&r->pm_sweeps, cudaStreamNonBlocking, greatest);
-    if (err == cudaSuccess)
-      err = cudaStreamCreateWithPriority(&r->pm_masks, cudaStreamNonBlocking, least);
-    for (int i = 0; i < 6 && err == cudaSuccess; ++i)
-      err = cudaEventCreateWithFlags(&r->pm_ev[i], cudaEventDisableTiming);
-  }
+  err = premask_streams(r);
   cudaStream_t hs = r->pm_sweeps, ms = r->pm_masks;
   cudaEvent_t *ev = r->pm_ev;  // start, end, masks ready (2), sweeps done (2)
   if (err == cudaSuccess) err = cudaEventRecord(ev[0], stream);
@@ -860,16 +867,7 @@ cudaError_t launch_torus_premasked(const isg_problem *p, const DeviceProblem *dp
     cudaGetLastError();
     return cudaErrorMemoryAllocation;
   }
-  if (!r->pm_sweeps) {
-    int least = 0, greatest = 0;
-    err = cudaDeviceGetStreamPriorityRange(&least, &greatest);
-    if (err == cudaSuccess)
-      err = cudaStreamCreateWithPriority(&r->pm_sweeps, cudaStreamNonBlocking, greatest);
-    if (err == cudaSuccess)
-      err = cudaStreamCreateWithPriority(&r->pm_masks, cudaStreamNonBlocking, least);
-    for (int i = 0; i < 6 && err == cudaSuccess; ++i)
-      err = cudaEventCreateWithFlags(&r->pm_ev[i], cudaEventDisableTiming);
-  }
+  err = premask_streams(r);
   cudaStream_t hs = r->pm_sweeps, ms = r->pm_masks;
   cudaEvent_t *ev = r->pm_ev;  // start, end, masks ready (2), sweeps done (2)
   if (err == cudaSuccess) err = cudaEventRecord(ev[0], stream);
