@@ -281,6 +281,9 @@ def test_graph_msc_precomputed_masks_continue_resume_target(isg):
                          mask_chunk=9)
     assert hit.stats()["mask_chunks"] == 0
     assert_same(hit, oracle.anneal(oracle.csr_of(g), 64, betas, 29, target=target))
+    with pytest.raises(isg.IsgError) as e:
+        isg.isg_anneal(p, 64, betas, 29, kernel=4, mask_chunk=-2)
+    assert e.value.status == isg.ISG_EINVAL
 
 
 @pytest.mark.parametrize("R,cluster,threads", [(40, 1, 256), (70, 4, 512)])
