@@ -95,6 +95,24 @@ def edgeless_with_fields():
     return I.Graph(300, z, z, z, h)
 
 
+@pytest.mark.parametrize("make", [unit_with_fields, star_forest_with_fields])
+@pytest.mark.parametrize("R,cluster,threads,mask_chunk", [(40, 1, 128, 9), (70, 5, 96, 9),
+                                                          (64, 12, 256, 1000)])
+def test_fields_graph_msc_precomputed_masks_bit_exact(isg, make, R, cluster, threads,
+                                                      mask_chunk):
+    """Local fields with the graph kernel's acceptance masks precomputed by a
+    second kernel (levels (d + |h| + 1) / 2 per vertex), in chunks of mask_chunk
+    sweeps, one CTA per word or a cluster with data-flow class phases."""
+    g = make()
+    betas = I.geometric_betas(0.1, 5.0, 45)
+    orc = oracle.anneal(oracle.csr_of(g), R, betas, 31, check_energy=True)
+    res = isg.isg_anneal(isg.problem_of(g), R, betas, 31, kernel=4, cluster_ctas=cluster,
+                         threads=threads, mask_chunk=mask_chunk)
+    st = res.stats()
+    assert st["kernel"] == 4 and st["staged"] == 1 and st["mask_chunks"] > 0
+    assert_same(res, orc)
+
+
 @pytest.mark.parametrize("make", [star_forest_with_fields, edgeless_with_fields])
 @pytest.mark.parametrize("R,cluster,threads", [(40, 1, 64), (40, 4, 128), (70, 8, 96)])
 def test_graph_msc_mask_windows_bit_exact(isg, make, R, cluster, threads):

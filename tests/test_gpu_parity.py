@@ -128,6 +128,7 @@ def test_torus_beta_zero_and_huge(isg):
 @pytest.mark.parametrize("L,W,R,cluster,threads", [
     (24, 30, 96, 2, 64),      # 6 CTAs: nearly every SM idle, every sweep after chunk 0 read
     (40, 40, 1024, 2, 160),   # 64 CTAs: every second sweep read
+    (16, 20, 64, 1, 64),      # one CTA per word
 ])
 @pytest.mark.parametrize("mask_chunk", [-1, 0, 1, 7])
 def test_torus_precomputed_masks_bit_exact(isg, L, W, R, cluster, threads, mask_chunk):
@@ -238,6 +239,7 @@ def test_graph_msc_mask_table_shapes_bit_exact(isg, make, R, cluster, threads):
     (1, 3, 96, 45),      # one sweep per chunk
     (7, 5, 64, 7),       # six chunks of 7 and one of 3
     (1000, 12, 512, 1),  # the whole schedule in one chunk
+    (7, 1, 256, 7),      # one CTA per word: CTA barriers, no data flow
 ])
 def test_graph_msc_precomputed_masks_bit_exact(isg, make, mask_chunk, cluster, threads, chunks):
     """The staged graph kernel with the acceptance masks precomputed by a second
