@@ -43,7 +43,7 @@ __host__ __device__ __forceinline__ size_t align16(size_t x) { return (x + 15) &
 constexpr int kAccWords = 3 * 32;
 
 struct SmemLayout {
-  size_t spin, best, cb, part, total;
+  size_t spin, best, cb, part, bars, total;
 };
 
 __host__ __device__ __forceinline__ SmemLayout layout_of(int nr, int W, int K) {
@@ -52,7 +52,8 @@ __host__ __device__ __forceinline__ SmemLayout layout_of(int nr, int W, int K) {
   m.best = m.spin + sizeof(uint32_t) * (size_t)(nr + 2) * W;
   m.cb = m.best + sizeof(uint32_t) * (size_t)nr * W;
   m.part = align16(m.cb + (size_t)(nr + 2) * W);
-  m.total = align16(m.part + sizeof(int32_t) * kAccWords);
+  m.bars = align16(m.part + sizeof(int32_t) * kAccWords);  // two mbarriers, an error flag
+  m.total = align16(m.bars + 32);
   return m;
 }
 
@@ -90,6 +91,64 @@ __device__ __forceinline__ void group_wait(int K) {
   else
     __syncthreads();
 }
+
+// Data flow between the CTAs of a word (pipelined build): halo cells are
+// sent with st.async and the energy sums with red.async, both completing on
+// the receiver's mbarrier, so a CTA starts its next phase once its own
+// threads and the expected bytes have arrived.  Addresses here are 32-bit
+// shared::cluster addresses (mapa of a CTA-local one).
+__device__ __forceinline__ uint32_t map_rank(uint32_t a, uint32_t rank) {
+  uint32_t r;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;\n" : "=r"(r) : "r"(a), "r"(rank));
+  return r;
+}
+
+__device__ __forceinline__ void st_async_cl(uint32_t a, uint32_t v, uint32_t bar) {
+  asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.u32 [%0], %1, [%2];\n" ::"r"(
+                   a),
+               "r"(v), "r"(bar)
+               : "memory");
+}
+
+__device__ __forceinline__ void red_async_add_cl(uint32_t a, int32_t v, uint32_t bar) {
+  asm volatile(
+      "red.async.relaxed.cluster.shared::cluster.mbarrier::complete_tx::bytes.add.s32 [%0], %1, "
+      "[%2];\n" ::"r"(a),
+      "r"(v), "r"(bar)
+      : "memory");
+}
+
+__device__ __forceinline__ void bar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(bar), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void bar_arrive(uint32_t bar, bool expect, uint32_t bytes) {
+  if (expect)
+    asm volatile(
+        "{\n .reg .b64 st;\n mbarrier.arrive.expect_tx.release.cta.shared::cta.b64 st, [%0], "
+        "%1;\n}\n" ::"r"(bar),
+        "r"(bytes)
+        : "memory");
+  else
+    asm volatile(
+        "{\n .reg .b64 st;\n mbarrier.arrive.release.cta.shared::cta.b64 st, [%0];\n}\n" ::"r"(
+            bar)
+        : "memory");
+}
+
+__device__ __forceinline__ bool bar_try_wait(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], "
+      "%2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// try_wait attempts before a wait counts as failed (far beyond any phase)
+constexpr uint32_t kTorusWaitLimit = 1u << 22;
 
 // Atomic add of v at shared-memory address a (a CTA-local shared address) of
 // CTA `rank` of the cluster, through the 32-bit cluster window.
@@ -252,9 +311,13 @@ constexpr int kPipeSites = 3;
 // LOAD: the other colour's masks are read from a precomputed table (q4, q8:
 // that sweep's two mask planes of this word, indexed by site) instead of
 // drawn; they are first used in the next phase, which hides the load.
+// The band's boundary rows go to the neighbours' halo rows with st.async
+// (up_halo, down_halo: their halo rows' cluster addresses; up_bar, down_bar:
+// their mbarriers of this phase).
 template <int NP, bool LOAD>
 __device__ __forceinline__ void pipe_phase(uint32_t *spin, uint32_t *best, const uint8_t *cb,
-                                           uint32_t *up_peer, uint32_t *down_peer, int W, int r0,
+                                           uint32_t up_halo, uint32_t down_halo, uint32_t up_bar,
+                                           uint32_t down_bar, int W, int r0,
                                            int nr, int c, const BlockPrefix (&bp)[8],
                                            const RoundKeys &rk, uint32_t To4, uint32_t To8,
                                            uint32_t imp, SlicedCounter<NP> &cnt,
@@ -305,8 +368,8 @@ __device__ __forceinline__ void pipe_phase(uint32_t *spin, uint32_t *best, const
       const uint32_t acc = ge2 | (eq1 & mc4[i]) | (eq0 & mc8[i]);
       const uint32_t sn = s0 ^ acc;
       spin[x] = sn;
-      if (lr == 1) up_peer[col] = sn;
-      if (lr == nr) down_peer[col] = sn;
+      if (lr == 1) st_async_cl(up_halo + 4u * (uint32_t)col, sn, up_bar);
+      if (lr == nr) st_async_cl(down_halo + 4u * (uint32_t)col, sn, down_bar);
       cnt.add3(acc & u0, (acc & (u0 ^ u1)) | ~acc, acc & eq0);
     }
     j += step_cols;
@@ -401,6 +464,15 @@ __device__ void torus_word(const TorusSolve &s, int word, int k, int K, int t_be
     if (lr >= 1 && lr <= nr) best[x - W] = resume ? gbest[i] : v;
   }
   for (int x = threadIdx.x; x < kAccWords; x += blockDim.x) acc[x] = 0;
+  // pipelined build: this CTA's mbarriers (alternating phases) and error flag
+  const uint32_t bar_l = (uint32_t)__cvta_generic_to_shared(smem + lay.bars);
+  int *dferr = reinterpret_cast<int *>(smem + lay.bars + 16);
+  if (kPipe && threadIdx.x == 0) {
+    bar_init(bar_l, blockDim.x);
+    bar_init(bar_l + 8, blockDim.x);
+    *dferr = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+  }
   // peers write into this CTA's halo rows (and accumulators) only after every
   // CTA has loaded (and cleared) them
   sync_group(K);
@@ -462,6 +534,39 @@ __device__ void torus_word(const TorusSolve &s, int word, int k, int K, int t_be
         pipe_prologue<false>(W, r0, nr, 0, bp, s.rk, T4n, T8n, m04, m08, nullptr, nullptr);
     }
     bool stop = false;
+    // Phases ordered by data flow: a CTA sends its boundary rows' new cells to
+    // the neighbours' halos (st.async) and, at a sweep's end, its warps' energy
+    // sums to every CTA's accumulator (red.async), all completing on the
+    // receiver's mbarrier; it waits on its own for its threads and the bytes
+    // expected: one colour's cells of its two halo rows (W words), plus the
+    // peers' sums at a sweep's end.  A neighbour completes a phase only after
+    // every boundary cell it reads from this CTA has been updated, and so after
+    // this CTA's reads of the halo next to it: no write can overtake a read,
+    // and no CTA runs more than one phase ahead (two mbarriers).  A wait that
+    // gives up sets the error flag (done = -1 for the host); later waits are
+    // skipped, and one cluster barrier ends the kernel.
+    const uint32_t up_halo = map_rank(
+        (uint32_t)__cvta_generic_to_shared(spin + (size_t)(band_of(L, K, kup).nr + 1) * W),
+        (uint32_t)kup);
+    const uint32_t down_halo = map_rank((uint32_t)__cvta_generic_to_shared(spin), (uint32_t)kdown);
+    const uint32_t up_bar0 = map_rank(bar_l, (uint32_t)kup);
+    const uint32_t down_bar0 = map_rank(bar_l, (uint32_t)kdown);
+    const uint32_t energy_bytes = 4u * 32u * (blockDim.x / 32u) * (uint32_t)(K - 1);
+    int gph = 0;       // phases so far: mbarrier gph & 1
+    uint32_t par = 0;  // each mbarrier's current phase parity
+    auto df_wait = [&]() {
+      const int i = gph & 1;
+      uint32_t tries = 0;
+      while (!bar_try_wait(bar_l + 8u * (uint32_t)i, (par >> i) & 1u)) {
+        if (*(volatile int *)dferr) break;
+        if (++tries >= kTorusWaitLimit) {
+          atomicExch(dferr, 1);
+          break;
+        }
+      }
+      par ^= 1u << i;
+      ++gph;
+    };
     // one sweep; LOAD0: the masks phase 0 prepares (colour 1 of sweep t) come
     // from the table, LOAD1: those phase 1 prepares (colour 0 of sweep t + 1)
     auto sweep = [&](auto load0, auto load1) {
@@ -474,17 +579,36 @@ __device__ void torus_word(const TorusSolve &s, int word, int k, int K, int t_be
       }
       cnt.clear();
       // colour 0 of sweep t; prepares colour 1 of sweep t
-      pipe_phase<NP, LOAD0>(spin, best, cb, up_peer, down_peer, W, r0, nr, 0, bp, s.rk, T4, T8,
-                            imp, cnt, m04, m08, m14, m18, LOAD0 ? planes(t) : nullptr,
-                            LOAD0 ? planes(t) + n : nullptr);
-      group_arrive(K);
+      uint32_t pb = 8u * (uint32_t)(gph & 1);
+      pipe_phase<NP, LOAD0>(spin, best, cb, up_halo, down_halo, up_bar0 + pb, down_bar0 + pb, W,
+                            r0, nr, 0, bp, s.rk, T4, T8, imp, cnt, m04, m08, m14, m18,
+                            LOAD0 ? planes(t) : nullptr, LOAD0 ? planes(t) + n : nullptr);
+      bar_arrive(bar_l + pb, threadIdx.x == 0, 4u * (uint32_t)W);
       if (more) sweep_prefix(t + 1);
-      group_wait(K);
+      df_wait();
       // colour 1 of sweep t; prepares colour 0 of sweep t + 1 (unused after the last)
-      pipe_phase<NP, LOAD1>(spin, best, cb, up_peer, down_peer, W, r0, nr, 1, bp, s.rk, T4n,
-                            T8n, imp, cnt, m14, m18, m04, m08, LOAD1 ? planes(t + 1) : nullptr,
-                            LOAD1 ? planes(t + 1) + n : nullptr);
-      e += 4 * (cluster_lane_sum<NP>(cnt, acc, acc_m, K, [] {}) - 2 * n);
+      pb = 8u * (uint32_t)(gph & 1);
+      pipe_phase<NP, LOAD1>(spin, best, cb, up_halo, down_halo, up_bar0 + pb, down_bar0 + pb, W,
+                            r0, nr, 1, bp, s.rk, T4n, T8n, imp, cnt, m14, m18, m04, m08,
+                            LOAD1 ? planes(t + 1) : nullptr, LOAD1 ? planes(t + 1) + n : nullptr);
+      // the sweep's energy change: every warp's lane sums into every CTA's
+      // accumulator acc_m (three rotate: the one the next sweep adds into is
+      // cleared once this one is read)
+      {
+        int32_t *cur = acc + 32 * acc_m;
+        const int32_t tot = cnt.warp_lane_total();
+        const uint32_t a = (uint32_t)__cvta_generic_to_shared(cur + lane);
+        for (int q = 0; q < K; ++q)
+          if (q != k)
+            red_async_add_cl(map_rank(a, (uint32_t)q), tot, map_rank(bar_l + pb, (uint32_t)q));
+        atomicAdd(cur + lane, tot);
+        bar_arrive(bar_l + pb, threadIdx.x == 0, 4u * (uint32_t)W + energy_bytes);
+        df_wait();
+        const int32_t sum = cur[lane];
+        acc_m = acc_m == 2 ? 0 : acc_m + 1;
+        if (threadIdx.x < 32) acc[32 * acc_m + lane] = 0;
+        e += 4 * (sum - 2 * n);
+      }
       const bool better = e < e_best;
       if (better) e_best = e;
       imp = __ballot_sync(0xFFFFFFFFu, better) & valid;
@@ -574,6 +698,10 @@ __device__ void torus_word(const TorusSolve &s, int word, int k, int K, int t_be
       if (s.has_target && hit >= 0) s.hit[word] = hit;
       s.done[word] = t;
     }
+  }
+  if (kPipe) {
+    cluster_barrier();  // no CTA leaves while another may still send to it
+    if (threadIdx.x == 0 && *(volatile int *)dferr) atomicMin(&s.done[word], -1);
   }
 }
 
